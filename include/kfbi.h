@@ -1,0 +1,230 @@
+/*
+ * kfbi.h - C ABI of the GB300 kernel-free boundary integral (KFBI) library for
+ * the FitzHugh-Nagumo bidomain equations (Gao, Cai, Henriquez, Ying,
+ * "A kernel-free boundary integral method for the bidomain equations").
+ *
+ * Conventions for every entry point:
+ *  - Returns KFBI_OK (0) or a positive KFBI_ERR_* code; never throws.  The
+ *    message of the last failure on the calling thread is kfbi_last_error().
+ *  - Pointers named *_dev are CUDA device pointers owned by the caller; all
+ *    other pointers are host pointers owned by the caller and only read during
+ *    the call.  The library owns its workspace and tables (freed by
+ *    kfbi_destroy).
+ *  - Box grids cover [lo, hi]^dim with N intervals per axis, h = (hi - lo)/N.
+ *    Grid fields hold the (N-1)^dim interior nodes x_k = lo + k h, k = 1..N-1,
+ *    row-major [z][y][x] (x fastest), float64, contiguous.  Box-boundary
+ *    nodes carry the Dirichlet value 0 of the interface problems (Section 5.1).
+ *  - Interface-node vectors (densities psi, Neumann data g^N, limits) hold M
+ *    float64 values in the order of kfbi_geometry.nodes.
+ *  - Work is enqueued on kfbi_opts.stream (NULL = the legacy default stream).
+ *    Entry points that iterate (GMRES, Strang steps) synchronise that stream
+ *    to read residuals; all others only enqueue.
+ */
+#ifndef KFBI_H
+#define KFBI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+#define KFBI_OK 0
+#define KFBI_ERR_ARG 1            /* bad argument or unsupported size            */
+#define KFBI_ERR_GEOMETRY 2       /* domain touches the box, stencil leaves grid */
+#define KFBI_ERR_NOT_CONVERGED 3  /* outputs written, stats valid               */
+#define KFBI_ERR_NAN 4            /* non-finite residual                         */
+#define KFBI_ERR_CUDA 5           /* CUDA runtime failure                        */
+#define KFBI_ERR_OOM 6            /* device allocation failed                    */
+#define KFBI_ERR_NEWTON 7         /* backward-Euler Newton hit its iteration cap */
+
+/* geometry kinds (domain Omega inside the box) */
+#define KFBI_ELLIPSE2 1    /* params: a, b, cos, sin of the rotation          */
+#define KFBI_ELLIPSOID3 2  /* params: a, b, c                                 */
+#define KFBI_STAR3 3       /* params: A, B of r = A + B sin(3 theta) cos(2 phi) */
+#define KFBI_SHELL3 4      /* params: outer a, b, c, inner a, b, c            */
+
+/* surface-component point-location maps of 3-D cube-sphere meshes */
+#define KFBI_MAP_RADIAL 0
+#define KFBI_MAP_ELLIPSOID 1
+
+/* precision of the integral evaluations */
+#define KFBI_FP64 0          /* all transforms and corrections in float64        */
+#define KFBI_MIXED 1         /* float32 transforms inside GMRES, float64 Arnoldi,
+                                residuals and outer refinement                   */
+#define KFBI_MIXED_LEARNED 2 /* KFBI_MIXED + learned warm start of the density   */
+
+#define KFBI_GMRES 0
+#define KFBI_RICHARDSON 1
+
+#define KFBI_MAX_COMP 4
+
+/*
+ * Interface description (Section 6: quasi-uniform interface nodes; Section
+ * 5.3 / Fig. 1: three-dimensional surfaces given by a triangle mesh).
+ *  nodes   [M][dim]       interface nodes.  2-D: counter-clockwise, equally
+ *                         spaced in the curve parameter t_i = 2 pi i / M.
+ *  tri     [n_tri][3]     3-D only: triangles of cube-sphere meshes of
+ *                         resolution cube_n, one mesh per surface component,
+ *                         triangle ((f n + j) n + i) 2 + half of component c
+ *                         at comp_tri_offset[c] (face f, quad (i, j), half 0 =
+ *                         (v_ij, v_i+1j, v_ij+1), half 1 = (v_i+1j, v_i+1j+1, v_ij+1)).
+ *  cube_t  [cube_n + 1]   equiangular face coordinates (-1 ... 1).
+ */
+typedef struct {
+  int dim;
+  int kind;
+  double params[16];
+  int n_nodes;
+  const double* nodes;
+  int n_tri;
+  const int32_t* tri;
+  int cube_n;
+  const double* cube_t;
+  int n_comp;
+  int comp_map[KFBI_MAX_COMP];
+  double comp_axes[KFBI_MAX_COMP][3];
+  int comp_vert_offset[KFBI_MAX_COMP];
+  int comp_n_vert[KFBI_MAX_COMP];
+  int comp_tri_offset[KFBI_MAX_COMP];
+} kfbi_geometry;
+
+typedef struct {
+  int dim;
+  int N;
+  double lo;
+  double hi;
+} kfbi_grid;
+
+typedef struct {
+  int precision;   /* KFBI_FP64 / KFBI_MIXED / KFBI_MIXED_LEARNED            */
+  int solver;      /* KFBI_GMRES / KFBI_RICHARDSON                           */
+  double tol;      /* relative residual ||g - A psi|| / ||g||                */
+  int restart;     /* GMRES restart length (<= 64)                           */
+  int max_iter;    /* total operator applications allowed                    */
+  double gamma;    /* Richardson parameter (0.8 in Section 7)               */
+  void* stream;    /* cudaStream_t                                           */
+} kfbi_opts;
+
+typedef struct {
+  int iters;            /* operator applications inside the Krylov solver     */
+  int outer;            /* outer refinement sweeps (mixed precision)          */
+  double rel_res;       /* solver's residual estimate ||r|| / ||g||           */
+  double true_rel_res;  /* recomputed ||g^N - du^+/dn|| / ||g|| (or -1)       */
+  double init_rel_res;  /* residual of the initial guess                      */
+  double ms;            /* wall time of the call                              */
+} kfbi_stats;
+
+typedef struct {
+  double H, theta, alpha, zeta, Cm, beta;   /* FitzHugh-Nagumo, Section 7 */
+} kfbi_fhn;
+
+typedef struct {
+  int M;               /* interface nodes                       */
+  int n_irregular;     /* irregular grid nodes                  */
+  int n_crossings;     /* interface / grid-line crossings       */
+  int n_inside;        /* grid nodes inside Omega               */
+  size_t device_bytes; /* workspace and tables held on the GPU  */
+} kfbi_info;
+
+typedef struct kfbi_handle kfbi_handle;
+
+const char* kfbi_last_error(void);
+
+/*
+ * Setup (Section 6): classify the box nodes against the domain (bit-exact
+ * level sets), list the irregular nodes and grid-line crossings, build the
+ * correction and interpolation tables, sine-transform tables and workspace.
+ * dt, sigma_i, sigma_e fix lambda = (2 Cm beta / dt)(1/sigma_i + 1/sigma_e) of
+ * the implicit-midpoint diffusion step (Section 3, Eq. pde1) used by
+ * bidomain_step with the FitzHugh-Nagumo parameters given there.
+ * Errors: KFBI_ERR_ARG (unsupported N or dim), KFBI_ERR_GEOMETRY, KFBI_ERR_OOM.
+ */
+int kfbi_create(const kfbi_geometry* geom, const kfbi_grid* grid, double sigma_i, double sigma_e,
+                double dt, const kfbi_opts* opts, kfbi_handle** out);
+void kfbi_destroy(kfbi_handle* h);
+int kfbi_query(kfbi_handle* h, kfbi_info* info);
+int kfbi_set_opts(kfbi_handle* h, const kfbi_opts* opts);
+
+/*
+ * Neumann boundary value problem (Sections 4-5, Algorithm 1 with GMRES):
+ *   Lap u - lambda u = f in Omega,  du/dn = gN on the boundary,
+ * f given on every box node (its continuous extension, Section 5.1).
+ * psi_dev: in = initial density (warm start), out = converged density.
+ * u_dev:   out = u = v_V + v_B on every box node.
+ * Returns KFBI_ERR_NOT_CONVERGED (outputs still written) if max_iter is hit.
+ */
+int kfbi_solve_neumann(kfbi_handle* h, double lambda, const double* f_dev, const double* gN_dev,
+                       double* u_dev, double* psi_dev, kfbi_stats* stats);
+
+/*
+ * nsteps Strang steps (Section 3): forward-Euler reaction over dt/2, implicit
+ * midpoint diffusion over dt (backward Euler over dt/2 for w, then
+ * V = 2 w - V), backward-Euler reaction over dt/2 (Newton, |dV| < 1e-10, cap 50).
+ * V_dev, w_dev: in/out state on all box nodes; ue_dev (may be NULL): out
+ * extracellular potential with zero mean over Omega.  The density of the last
+ * diffusion solve is kept in the handle and warm-starts the next one.
+ * per_step: nsteps entries or NULL.
+ */
+int bidomain_step(kfbi_handle* h, const kfbi_fhn* p, double* V_dev, double* w_dev, double* ue_dev,
+                  int nsteps, kfbi_stats* per_step);
+
+/* ------------------------------------------------------------------
+ * Step-level entry points (one per row of the hot path), used for parity
+ * checks and benchmarks.  All act on the handle's geometry and grid.
+ * ------------------------------------------------------------------ */
+
+/* Export setup results to host buffers (NULL to skip any):
+ * inside [(N-1)^dim] uint8; irregular [n_irregular] int32 flat indices
+ * (increasing); crossing_axis/crossing_lo [n_crossings] int32 and crossing_z
+ * [n_crossings] float64, sorted by (axis, lower node); center [M][dim] int32
+ * 1-based node indices; sign [M][dim] int8.                                  */
+int kfbi_export_setup(kfbi_handle* h, uint8_t* inside, int32_t* irregular, int32_t* crossing_axis,
+                      int32_t* crossing_lo, double* crossing_z, int32_t* center, int8_t* sign);
+
+/* Export the precomputed linear rows of the hot path (NULL to skip any):
+ * node_wn [M][P] Taylor weights of dv/dn on the stencil values (P = 6 / 10);
+ * node_cnt [M], node_pid [M][17], node_w [M][17]: each node's jump row on the
+ * density vector (psi in 3-D, [psi; spline moments] in 2-D);
+ * cross_cnt [n_crossings], cross_pid/cross_wlo/cross_whi [n_crossings][16]:
+ * each crossing's correction row for its lower and upper end node.          */
+int kfbi_export_tables(kfbi_handle* h, double* node_wn, int32_t* node_cnt, int32_t* node_pid, double* node_w,
+                       int32_t* cross_cnt, int32_t* cross_pid, double* cross_wlo, double* cross_whi);
+
+/* Box solve (Sections 5.2-5.3): v = L_h^{-1} r, 5/7-point operator with zero
+ * Dirichlet data, by sine transforms.  precision KFBI_FP64 or KFBI_MIXED
+ * (float32 transforms).                                                     */
+int kfbi_box_solve(kfbi_handle* h, int precision, double lambda, const double* r_dev, double* v_dev);
+
+/* Irregular-node correction (Section 5.3, Eq. correct): rhs_dev (grid, fully
+ * written) = 0 at regular nodes, summed corrections from the jumps of the
+ * single layer with density psi at irregular nodes.                          */
+int kfbi_correction(kfbi_handle* h, const double* psi_dev, double* rhs_dev);
+
+/* Interface limit (Section 5.4): out[i] = dv^+/dn at node i from the Taylor
+ * system, with the single-layer jumps of psi_dev (NULL = no jumps).          */
+int kfbi_interface_limit(kfbi_handle* h, const double* v_dev, const double* psi_dev, double* out_dev);
+
+/* Matrix-vector product of the boundary integral equation (Algorithm 1):
+ * out = A psi = dv_B^+/dn.                                                   */
+int kfbi_apply_A(kfbi_handle* h, int precision, double lambda, const double* psi_dev, double* out_dev);
+
+/* Right-hand side g = gN - dv_V^+/dn with v_V the box solve of f.           */
+int kfbi_rhs_g(kfbi_handle* h, double lambda, const double* f_dev, const double* gN_dev, double* g_dev);
+
+/* GMRES / Richardson on A psi = g alone (tol = 0 runs exactly max_iter
+ * applications).                                                             */
+int kfbi_solve_bie(kfbi_handle* h, double lambda, const double* g_dev, double* psi_dev, kfbi_stats* stats);
+
+/* Pointwise FitzHugh-Nagumo half steps (Section 3, Eqs. ode1/ode2) over n
+ * values: forward Euler (k = dt/2) and backward Euler with Newton.  The
+ * backward step returns KFBI_ERR_NEWTON if any node hit the iteration cap.    */
+int kfbi_react_fe(const kfbi_fhn* p, double k, double* V_dev, double* w_dev, int64_t n, void* stream);
+int kfbi_react_be(const kfbi_fhn* p, double k, double* V_dev, double* w_dev, int64_t n, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KFBI_H */

@@ -1,0 +1,588 @@
+// C ABI of the KFBI library and its host orchestration: handle lifecycle,
+// the boundary integral operator A psi (Algorithm 1), GMRES / simple
+// iteration on A psi = g (Section 4), the Neumann solve and the Strang step
+// (Section 3).  All arithmetic runs in the kernels of dst.cu, ops.cu and
+// setup.cu; the host only sequences launches and reads one residual per
+// Krylov iteration.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace kfbi {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int small_size(int m);
+int small_res(int m);
+int small_g(int m);
+int small_hcol(int m);
+int small_nrm2(int m);
+int small_y(int m);
+int arnoldi_add(kfbi_handle* h, double* small, int m, int n);
+int launch_init_arnoldi(kfbi_handle* h, double* small, int m);
+
+namespace {
+
+int64_t grid_points(const kfbi_handle* h) {
+  const int64_t n1 = h->grid.N - 1;
+  return h->grid.dim == 3 ? n1 * n1 * n1 : n1 * n1;
+}
+
+int64_t padded_points(const kfbi_handle* h) {
+  const int64_t N = h->grid.N;
+  return h->grid.dim == 3 ? N * N * N : N * N;
+}
+
+// density vector x seen by the correction and jump rows: psi (3-D) or
+// [psi; spline moments] (2-D)
+int density_vector(kfbi_handle* h, const double* psi, const double** x) {
+  if (h->grid.dim == 2) {
+    int rc = launch_spline(h, psi, h->w.xvec);
+    if (rc) return rc;
+    *x = h->w.xvec;
+  } else {
+    *x = psi;
+  }
+  return KFBI_OK;
+}
+
+// out = base + sgn * A psi    (A psi = dv_B^+/dn of the single layer)
+int apply_A(kfbi_handle* h, int prec, double lambda, const double* psi, double* out, double sgn, const double* base) {
+  const double* x;
+  int rc = density_vector(h, psi, &x);
+  if (rc) return rc;
+  if ((rc = launch_correction(h, x, h->w.corr))) return rc;
+  SolveArgs sa;
+  sa.corr = h->w.corr;
+  sa.lambda = lambda;
+  if (prec == KFBI_FP64) {
+    if ((rc = box_solve64(h, sa, h->w.grid64))) return rc;
+    return launch_limit64(h, h->w.grid64, x, base, sgn, out);
+  }
+  if ((rc = box_solve32(h, sa, h->w.grid32))) return rc;
+  return launch_limit32(h, h->w.grid32, x, base, sgn, out);
+}
+
+// g = gN - dv_V^+/dn, v_V the box solve of alpha * src
+int rhs_g(kfbi_handle* h, double lambda, const double* src, double alpha, const double* gN, double* g) {
+  SolveArgs sa;
+  sa.src = src;
+  sa.alpha = alpha;
+  sa.lambda = lambda;
+  int rc = box_solve64(h, sa, h->w.grid64);
+  if (rc) return rc;
+  return launch_limit64(h, h->w.grid64, nullptr, gN, -1.0, g);
+}
+
+int read_scalar(kfbi_handle* h, const double* dev, double* out) {
+  KFBI_CUDA(cudaMemcpyAsync(h->w.host_small, dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  KFBI_CUDA(cudaStreamSynchronize(h->stream));
+  *out = h->w.host_small[0];
+  return KFBI_OK;
+}
+
+int norm2(kfbi_handle* h, const double* v, double* slot, double* out) {
+  int rc = vec_dots(h, v, 1, h->t.M, v, slot);
+  if (rc) return rc;
+  double s;
+  if ((rc = read_scalar(h, slot, &s))) return rc;
+  *out = std::sqrt(s);
+  return KFBI_OK;
+}
+
+// GMRES(m) with CGS2 Arnoldi on A psi = g; psi in: initial guess, out: solution
+int gmres(kfbi_handle* h, int prec, double lambda, const double* g, double* psi, kfbi_stats* st) {
+  const int M = h->t.M;
+  const int m = h->opts.restart;
+  const double tol = h->opts.tol;
+  const int max_iter = h->opts.max_iter;
+  double* V = h->w.vecs;
+  const int ld = M;
+  double* wv = h->w.tmp;
+  double* r = h->w.r;
+  double* s = h->w.small;
+  int rc;
+  double gnorm;
+  if ((rc = norm2(h, g, s + small_nrm2(m), &gnorm))) return rc;
+  if (gnorm == 0.0) gnorm = 1.0;
+  int it = 0;
+  double rel = 0.0;
+  bool first = true;
+  for (;;) {
+    if ((rc = apply_A(h, prec, lambda, psi, r, -1.0, g))) return rc;  // r = g - A psi
+    if ((rc = vec_dots(h, r, 1, M, r, s + small_nrm2(m)))) return rc;
+    double b2;
+    if ((rc = read_scalar(h, s + small_nrm2(m), &b2))) return rc;
+    const double beta = std::sqrt(b2);
+    rel = beta / gnorm;
+    if (first) {
+      st->init_rel_res = rel;
+      first = false;
+    }
+    if (!std::isfinite(rel)) {
+      set_error("non-finite residual in GMRES");
+      return KFBI_ERR_NAN;
+    }
+    if (rel <= tol || it >= max_iter || beta == 0.0) break;
+    if ((rc = launch_init_arnoldi(h, s, m))) return rc;
+    if ((rc = vec_scale_by_norm(h, V, r, s + small_nrm2(m), M))) return rc;
+    int jd = 0;
+    for (int j = 0; j < m; ++j) {
+      double* vj = V + (size_t)j * ld;
+      if ((rc = apply_A(h, prec, lambda, vj, wv, 1.0, nullptr))) return rc;
+      ++it;
+      // classical Gram-Schmidt, twice
+      if ((rc = vec_dots(h, V, j + 1, ld, wv, s + small_hcol(m)))) return rc;
+      if ((rc = vec_update(h, wv, V, j + 1, ld, s + small_hcol(m), -1.0))) return rc;
+      if ((rc = vec_dots(h, V, j + 1, ld, wv, s + small_y(m)))) return rc;
+      if ((rc = vec_update(h, wv, V, j + 1, ld, s + small_y(m), -1.0))) return rc;
+      if ((rc = arnoldi_add(h, s, m, j + 1))) return rc;
+      if ((rc = vec_dots(h, wv, 1, M, wv, s + small_nrm2(m)))) return rc;
+      if ((rc = vec_scale_by_norm(h, V + (size_t)(j + 1) * ld, wv, s + small_nrm2(m), M))) return rc;
+      if ((rc = arnoldi_givens(h, s, j, m))) return rc;
+      double res;
+      if ((rc = read_scalar(h, s + small_res(m), &res))) return rc;
+      rel = res / gnorm;
+      jd = j + 1;
+      if (!std::isfinite(rel)) {
+        set_error("non-finite residual in GMRES");
+        return KFBI_ERR_NAN;
+      }
+      if (rel <= tol || it >= max_iter) break;
+    }
+    if ((rc = arnoldi_solve(h, s, jd, m))) return rc;
+    if ((rc = vec_update(h, psi, V, jd, ld, s + small_y(m), 1.0))) return rc;
+    if (rel <= tol || it >= max_iter) break;
+  }
+  st->iters = it;
+  st->rel_res = rel;
+  return rel <= tol ? KFBI_OK : KFBI_ERR_NOT_CONVERGED;
+}
+
+int richardson(kfbi_handle* h, int prec, double lambda, const double* g, double* psi, kfbi_stats* st) {
+  const int M = h->t.M;
+  double* r = h->w.r;
+  double* s = h->w.small;
+  const int m = h->opts.restart;
+  int rc;
+  double gnorm;
+  if ((rc = norm2(h, g, s + small_nrm2(m), &gnorm))) return rc;
+  if (gnorm == 0.0) gnorm = 1.0;
+  int it = 0;
+  double rel = 0.0;
+  for (;;) {
+    if ((rc = apply_A(h, prec, lambda, psi, r, -1.0, g))) return rc;
+    double rn;
+    if ((rc = norm2(h, r, s + small_nrm2(m), &rn))) return rc;
+    rel = rn / gnorm;
+    if (it == 0) st->init_rel_res = rel;
+    if (!std::isfinite(rel)) {
+      set_error("non-finite residual in the simple iteration");
+      return KFBI_ERR_NAN;
+    }
+    if (rel <= h->opts.tol || it >= h->opts.max_iter) break;
+    if ((rc = vec_axpby(h, psi, 2.0 * h->opts.gamma, r, 1.0, M))) return rc;
+    ++it;
+  }
+  st->iters = it;
+  st->rel_res = rel;
+  return rel <= h->opts.tol ? KFBI_OK : KFBI_ERR_NOT_CONVERGED;
+}
+
+int solve_bie(kfbi_handle* h, int prec, double lambda, const double* g, double* psi, kfbi_stats* st) {
+  if (h->opts.solver == KFBI_RICHARDSON) return richardson(h, prec, lambda, g, psi, st);
+  return gmres(h, prec, lambda, g, psi, st);
+}
+
+int check_handle(kfbi_handle* h) {
+  if (h == nullptr) {
+    kfbi::set_error("null handle");
+    return KFBI_ERR_ARG;
+  }
+  return KFBI_OK;
+}
+
+double elapsed_ms(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace
+}  // namespace kfbi
+
+using namespace kfbi;
+
+extern "C" {
+
+const char* kfbi_last_error(void) { return kfbi::g_err; }
+
+int kfbi_create(const kfbi_geometry* geom, const kfbi_grid* grid, double sigma_i, double sigma_e, double dt,
+                const kfbi_opts* opts, kfbi_handle** out) {
+  if (!geom || !grid || !out || !opts) {
+    set_error("null argument");
+    return KFBI_ERR_ARG;
+  }
+  *out = nullptr;
+  if (grid->dim != 2 && grid->dim != 3) {
+    set_error("dim must be 2 or 3");
+    return KFBI_ERR_ARG;
+  }
+  if (geom->dim != grid->dim || !dst_supported(grid->N) || (grid->dim == 2 && grid->N < 16)) {
+    set_error("unsupported grid: N=%d dim=%d (N in 8,16,32,64,128,256,384,512; 2-D needs N >= 16)", grid->N,
+              grid->dim);
+    return KFBI_ERR_ARG;
+  }
+  if (geom->n_nodes < 8 || geom->nodes == nullptr || !(grid->hi > grid->lo)) {
+    set_error("bad geometry or grid extents");
+    return KFBI_ERR_ARG;
+  }
+  if (grid->dim == 3 && (geom->tri == nullptr || geom->n_tri <= 0 || geom->cube_t == nullptr || geom->n_comp < 1 ||
+                         geom->n_comp > KFBI_MAX_COMP)) {
+    set_error("3-D geometry needs a triangle mesh and cube-sphere tables");
+    return KFBI_ERR_ARG;
+  }
+  if (opts->restart < 1 || opts->restart > MAX_RESTART || !(sigma_i > 0) || !(sigma_e > 0) || !(dt > 0)) {
+    set_error("bad options (restart in 1..%d, positive conductivities and dt)", MAX_RESTART);
+    return KFBI_ERR_ARG;
+  }
+  kfbi_handle* h = new kfbi_handle();
+  h->opts = *opts;
+  h->stream = (cudaStream_t)opts->stream;
+  h->sigma_i = sigma_i;
+  h->sigma_e = sigma_e;
+  h->dt = dt;
+  h->lambda = (2.0 / dt) * (1.0 / sigma_i + 1.0 / sigma_e);
+  GeomParams& gp = h->gp;
+  memset(&gp, 0, sizeof(gp));
+  gp.dim = geom->dim;
+  gp.kind = geom->kind;
+  gp.n_comp = grid->dim == 3 ? geom->n_comp : 1;
+  for (int i = 0; i < 16; ++i) gp.p[i] = geom->params[i];
+  for (int c = 0; c < KFBI_MAX_COMP; ++c) {
+    gp.comp_map[c] = geom->comp_map[c];
+    for (int k = 0; k < 3; ++k) gp.comp_axes[c][k] = geom->comp_axes[c][k];
+    gp.comp_tri_offset[c] = geom->comp_tri_offset[c];
+    gp.comp_vert_offset[c] = geom->comp_vert_offset[c];
+  }
+  gp.cube_n = geom->cube_n;
+  h->grid.dim = grid->dim;
+  h->grid.N = grid->N;
+  h->grid.lo = grid->lo;
+  h->grid.h = (grid->hi - grid->lo) / grid->N;
+  int rc;
+  auto fail = [&](int code) {
+    kfbi_destroy(h);
+    return code;
+  };
+  if ((rc = dalloc(h, &h->w.err, 4))) return fail(rc);
+  if ((rc = setup_build(h, geom))) return fail(rc);
+  const int M = h->t.M, m = opts->restart;
+  const int64_t P = padded_points(h);
+  if ((rc = dalloc(h, &h->w.grid64, (size_t)P))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.grid32, (size_t)P))) return fail(rc);
+  if (cudaMemsetAsync(h->w.grid64, 0, sizeof(double) * (size_t)P, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->w.grid32, 0, sizeof(float) * (size_t)P, h->stream) != cudaSuccess) {
+    set_error("cudaMemset failed");
+    return fail(KFBI_ERR_CUDA);
+  }
+  if ((rc = dalloc(h, &h->w.corr, (size_t)h->t.n_irr))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.xvec, (size_t)2 * M))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.vecs, (size_t)(m + 1) * M))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.small, (size_t)small_size(MAX_RESTART)))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.partial, (size_t)152 * (MAX_RESTART + 2) + 16))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.g, (size_t)M))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.r, (size_t)M))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.tmp, (size_t)M))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.tmp2, (size_t)M))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.psi_prev, (size_t)M))) return fail(rc);
+  cudaMemsetAsync(h->w.psi_prev, 0, sizeof(double) * (size_t)M, h->stream);
+  if (cudaMallocHost((void**)&h->w.host_small, 64 * sizeof(double)) != cudaSuccess) {
+    set_error("cudaMallocHost failed");
+    return fail(KFBI_ERR_OOM);
+  }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    set_error("setup failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return fail(KFBI_ERR_CUDA);
+  }
+  *out = h;
+  return KFBI_OK;
+}
+
+void kfbi_destroy(kfbi_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  for (void* p : h->allocations) cudaFree(p);
+  if (h->w.host_small) cudaFreeHost(h->w.host_small);
+  delete h;
+}
+
+int kfbi_query(kfbi_handle* h, kfbi_info* info) {
+  if (int rc = check_handle(h)) return rc;
+  if (!info) {
+    set_error("null info");
+    return KFBI_ERR_ARG;
+  }
+  info->M = h->t.M;
+  info->n_irregular = h->t.n_irr;
+  info->n_crossings = h->t.n_int;
+  info->n_inside = h->t.n_inside;
+  info->device_bytes = h->device_bytes;
+  return KFBI_OK;
+}
+
+int kfbi_set_opts(kfbi_handle* h, const kfbi_opts* opts) {
+  if (int rc = check_handle(h)) return rc;
+  if (!opts || opts->restart < 1 || opts->restart > MAX_RESTART) {
+    set_error("bad options");
+    return KFBI_ERR_ARG;
+  }
+  if (opts->restart > h->opts.restart) {
+    set_error("restart cannot grow after kfbi_create");
+    return KFBI_ERR_ARG;
+  }
+  h->opts = *opts;
+  h->stream = (cudaStream_t)opts->stream;
+  return KFBI_OK;
+}
+
+int kfbi_export_setup(kfbi_handle* h, uint8_t* inside, int32_t* irregular, int32_t* crossing_axis,
+                      int32_t* crossing_lo, double* crossing_z, int32_t* center, int8_t* sign) {
+  if (int rc = check_handle(h)) return rc;
+  const Tables& t = h->t;
+  const int d = h->grid.dim;
+  cudaStream_t st = h->stream;
+  if (inside) KFBI_CUDA(cudaMemcpyAsync(inside, t.inside, (size_t)grid_points(h), cudaMemcpyDeviceToHost, st));
+  if (irregular) KFBI_CUDA(cudaMemcpyAsync(irregular, t.irr, sizeof(int32_t) * t.n_irr, cudaMemcpyDeviceToHost, st));
+  if (crossing_axis)
+    KFBI_CUDA(cudaMemcpyAsync(crossing_axis, t.c_axis, sizeof(int32_t) * t.n_int, cudaMemcpyDeviceToHost, st));
+  if (crossing_lo) KFBI_CUDA(cudaMemcpyAsync(crossing_lo, t.c_lo, sizeof(int32_t) * t.n_int, cudaMemcpyDeviceToHost, st));
+  if (crossing_z) KFBI_CUDA(cudaMemcpyAsync(crossing_z, t.c_z, sizeof(double) * t.n_int, cudaMemcpyDeviceToHost, st));
+  if (center) KFBI_CUDA(cudaMemcpyAsync(center, t.n_center, sizeof(int32_t) * t.M * d, cudaMemcpyDeviceToHost, st));
+  if (sign) KFBI_CUDA(cudaMemcpyAsync(sign, t.n_sign, sizeof(int8_t) * t.M * d, cudaMemcpyDeviceToHost, st));
+  KFBI_CUDA(cudaStreamSynchronize(st));
+  return KFBI_OK;
+}
+
+int kfbi_export_tables(kfbi_handle* h, double* node_wn, int32_t* node_cnt, int32_t* node_pid, double* node_w,
+                       int32_t* cross_cnt, int32_t* cross_pid, double* cross_wlo, double* cross_whi) {
+  if (int rc = check_handle(h)) return rc;
+  const Tables& t = h->t;
+  cudaStream_t st = h->stream;
+  const size_t M = t.M, NI = t.n_int, R = PATCH_MAX + 1;
+  if (node_wn) KFBI_CUDA(cudaMemcpyAsync(node_wn, t.n_wn, sizeof(double) * M * t.P, cudaMemcpyDeviceToHost, st));
+  if (node_cnt) KFBI_CUDA(cudaMemcpyAsync(node_cnt, t.n_dcnt, sizeof(int32_t) * M, cudaMemcpyDeviceToHost, st));
+  if (node_pid) KFBI_CUDA(cudaMemcpyAsync(node_pid, t.n_dpid, sizeof(int32_t) * M * R, cudaMemcpyDeviceToHost, st));
+  if (node_w) KFBI_CUDA(cudaMemcpyAsync(node_w, t.n_dw, sizeof(double) * M * R, cudaMemcpyDeviceToHost, st));
+  if (cross_cnt) KFBI_CUDA(cudaMemcpyAsync(cross_cnt, t.c_cnt, sizeof(int32_t) * NI, cudaMemcpyDeviceToHost, st));
+  if (cross_pid)
+    KFBI_CUDA(cudaMemcpyAsync(cross_pid, t.c_pid, sizeof(int32_t) * NI * PATCH_MAX, cudaMemcpyDeviceToHost, st));
+  if (cross_wlo)
+    KFBI_CUDA(cudaMemcpyAsync(cross_wlo, t.c_wlo, sizeof(double) * NI * PATCH_MAX, cudaMemcpyDeviceToHost, st));
+  if (cross_whi)
+    KFBI_CUDA(cudaMemcpyAsync(cross_whi, t.c_whi, sizeof(double) * NI * PATCH_MAX, cudaMemcpyDeviceToHost, st));
+  KFBI_CUDA(cudaStreamSynchronize(st));
+  return KFBI_OK;
+}
+
+int kfbi_box_solve(kfbi_handle* h, int precision, double lambda, const double* r_dev, double* v_dev) {
+  if (int rc = check_handle(h)) return rc;
+  if (!r_dev || !v_dev) {
+    set_error("null field");
+    return KFBI_ERR_ARG;
+  }
+  SolveArgs sa;
+  sa.src = r_dev;
+  sa.lambda = lambda;
+  sa.out_user = v_dev;
+  if (precision == KFBI_FP64) return box_solve64(h, sa, h->w.grid64);
+  return box_solve32(h, sa, h->w.grid32);
+}
+
+int kfbi_correction(kfbi_handle* h, const double* psi_dev, double* rhs_dev) {
+  if (int rc = check_handle(h)) return rc;
+  const double* x;
+  int rc = density_vector(h, psi_dev, &x);
+  if (rc) return rc;
+  if ((rc = launch_correction(h, x, h->w.corr))) return rc;
+  return launch_scatter_grid(h, h->w.corr, rhs_dev);
+}
+
+int kfbi_interface_limit(kfbi_handle* h, const double* v_dev, const double* psi_dev, double* out_dev) {
+  if (int rc = check_handle(h)) return rc;
+  // place v in the padded grid (x passes of a zero-lambda identity are not
+  // needed: copy through a solve-free scatter)
+  int rc;
+  const double* x = nullptr;
+  if (psi_dev) {
+    if ((rc = density_vector(h, psi_dev, &x))) return rc;
+  }
+  const int N = h->grid.N, n1 = N - 1;
+  // user -> padded copy (rows of n1 values into rows of N)
+  if (h->grid.dim == 3) {
+    cudaMemcpy3DParms prm = {};
+    prm.srcPtr = make_cudaPitchedPtr((void*)v_dev, sizeof(double) * n1, n1, n1);
+    prm.dstPtr = make_cudaPitchedPtr((void*)h->w.grid64, sizeof(double) * N, N, N);
+    prm.dstPos = make_cudaPos(sizeof(double), 1, 1);
+    prm.extent = make_cudaExtent(sizeof(double) * n1, n1, n1);
+    prm.kind = cudaMemcpyDeviceToDevice;
+    KFBI_CUDA(cudaMemcpy3DAsync(&prm, h->stream));
+  } else {
+    KFBI_CUDA(cudaMemcpy2DAsync(h->w.grid64 + N + 1, sizeof(double) * N, v_dev, sizeof(double) * n1,
+                                sizeof(double) * n1, n1, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  return launch_limit64(h, h->w.grid64, x, nullptr, 1.0, out_dev);
+}
+
+int kfbi_apply_A(kfbi_handle* h, int precision, double lambda, const double* psi_dev, double* out_dev) {
+  if (int rc = check_handle(h)) return rc;
+  return apply_A(h, precision, lambda, psi_dev, out_dev, 1.0, nullptr);
+}
+
+int kfbi_rhs_g(kfbi_handle* h, double lambda, const double* f_dev, const double* gN_dev, double* g_dev) {
+  if (int rc = check_handle(h)) return rc;
+  return rhs_g(h, lambda, f_dev, 1.0, gN_dev, g_dev);
+}
+
+int kfbi_solve_bie(kfbi_handle* h, double lambda, const double* g_dev, double* psi_dev, kfbi_stats* stats) {
+  if (int rc = check_handle(h)) return rc;
+  kfbi_stats st{};
+  auto t0 = std::chrono::steady_clock::now();
+  int rc = solve_bie(h, KFBI_FP64, lambda, g_dev, psi_dev, &st);
+  st.ms = elapsed_ms(t0);
+  st.true_rel_res = -1.0;
+  if (stats) *stats = st;
+  return rc;
+}
+
+int kfbi_solve_neumann(kfbi_handle* h, double lambda, const double* f_dev, const double* gN_dev, double* u_dev,
+                       double* psi_dev, kfbi_stats* stats) {
+  if (int rc = check_handle(h)) return rc;
+  if (!f_dev || !gN_dev || !u_dev || !psi_dev) {
+    set_error("null argument");
+    return KFBI_ERR_ARG;
+  }
+  kfbi_stats st{};
+  auto t0 = std::chrono::steady_clock::now();
+  int rc = rhs_g(h, lambda, f_dev, 1.0, gN_dev, h->w.g);
+  if (rc) return rc;
+  const int solve_rc = solve_bie(h, KFBI_FP64, lambda, h->w.g, psi_dev, &st);
+  if (solve_rc != KFBI_OK && solve_rc != KFBI_ERR_NOT_CONVERGED) return solve_rc;
+  // u = v_V + v_B(psi) in one solve of the combined right-hand side
+  const double* x;
+  if ((rc = density_vector(h, psi_dev, &x))) return rc;
+  if ((rc = launch_correction(h, x, h->w.corr))) return rc;
+  SolveArgs sa;
+  sa.src = f_dev;
+  sa.corr = h->w.corr;
+  sa.lambda = lambda;
+  sa.out_user = u_dev;
+  if ((rc = box_solve64(h, sa, h->w.grid64))) return rc;
+  // true residual g^N - du^+/dn relative to ||g||
+  if ((rc = launch_limit64(h, h->w.grid64, x, gN_dev, -1.0, h->w.r))) return rc;
+  double rn, gn;
+  double* slot = h->w.small + small_nrm2(h->opts.restart);
+  if ((rc = norm2(h, h->w.r, slot, &rn))) return rc;
+  if ((rc = norm2(h, h->w.g, slot, &gn))) return rc;
+  st.true_rel_res = gn > 0 ? rn / gn : rn;
+  st.ms = elapsed_ms(t0);
+  if (stats) *stats = st;
+  return solve_rc;
+}
+
+int bidomain_step(kfbi_handle* h, const kfbi_fhn* p, double* V_dev, double* w_dev, double* ue_dev, int nsteps,
+                  kfbi_stats* per_step) {
+  if (int rc = check_handle(h)) return rc;
+  if (!p || !V_dev || !w_dev || nsteps < 0) {
+    set_error("null argument");
+    return KFBI_ERR_ARG;
+  }
+  const int64_t n = grid_points(h);
+  const double lam = (2.0 * p->Cm * p->beta / h->dt) * (1.0 / h->sigma_i + 1.0 / h->sigma_e);
+  const double k = 0.5 * h->dt;
+  int rc;
+  int final_rc = KFBI_OK;
+  KFBI_CUDA(cudaMemsetAsync(h->w.err, 0, sizeof(int), h->stream));
+  for (int s = 0; s < nsteps; ++s) {
+    kfbi_stats st{};
+    auto t0 = std::chrono::steady_clock::now();
+    if ((rc = launch_react_fe(p, k, V_dev, w_dev, n, h->stream))) return rc;
+    // g = -dv_V^+/dn with v_V = L_h^{-1}(-lam V)
+    if ((rc = rhs_g(h, lam, V_dev, -lam, nullptr, h->w.g))) return rc;
+    const int src = solve_bie(h, KFBI_FP64, lam, h->w.g, h->w.psi_prev, &st);
+    if (src != KFBI_OK && src != KFBI_ERR_NOT_CONVERGED) return src;
+    if (src == KFBI_ERR_NOT_CONVERGED) final_rc = src;
+    // V <- 2 (v_V + v_B(psi)) - V, one solve of the combined right-hand side
+    const double* x;
+    if ((rc = density_vector(h, h->w.psi_prev, &x))) return rc;
+    if ((rc = launch_correction(h, x, h->w.corr))) return rc;
+    SolveArgs sa;
+    sa.src = V_dev;
+    sa.alpha = -lam;
+    sa.corr = h->w.corr;
+    sa.lambda = lam;
+    sa.out_user = V_dev;
+    sa.aux = V_dev;
+    sa.beta = 2.0;
+    sa.gamma = -1.0;
+    if ((rc = box_solve64(h, sa, h->w.grid64))) return rc;
+    if ((rc = launch_react_be(p, k, V_dev, w_dev, n, h->w.err, h->stream))) return rc;
+    st.true_rel_res = -1.0;
+    st.ms = elapsed_ms(t0);
+    if (per_step) per_step[s] = st;
+  }
+  if (ue_dev) {
+    if ((rc = launch_ue(h, V_dev, ue_dev))) return rc;
+  }
+  int herr = 0;
+  KFBI_CUDA(cudaMemcpyAsync(&herr, h->w.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  KFBI_CUDA(cudaStreamSynchronize(h->stream));
+  if (herr & DEVERR_NEWTON) {
+    set_error("backward-Euler Newton iteration hit its cap");
+    return KFBI_ERR_NEWTON;
+  }
+  return final_rc;
+}
+
+int kfbi_react_fe(const kfbi_fhn* p, double k, double* V_dev, double* w_dev, int64_t n, void* stream) {
+  if (!p || !V_dev || !w_dev || n < 0) {
+    set_error("null argument");
+    return KFBI_ERR_ARG;
+  }
+  return launch_react_fe(p, k, V_dev, w_dev, n, (cudaStream_t)stream);
+}
+
+int kfbi_react_be(const kfbi_fhn* p, double k, double* V_dev, double* w_dev, int64_t n, void* stream) {
+  if (!p || !V_dev || !w_dev || n < 0) {
+    set_error("null argument");
+    return KFBI_ERR_ARG;
+  }
+  int* err = nullptr;
+  KFBI_CUDA(cudaMallocAsync((void**)&err, sizeof(int), (cudaStream_t)stream));
+  KFBI_CUDA(cudaMemsetAsync(err, 0, sizeof(int), (cudaStream_t)stream));
+  int rc = launch_react_be(p, k, V_dev, w_dev, n, err, (cudaStream_t)stream);
+  int herr = 0;
+  cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  cudaFreeAsync(err, (cudaStream_t)stream);
+  KFBI_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  if (rc) return rc;
+  if (herr & DEVERR_NEWTON) {
+    set_error("backward-Euler Newton iteration hit its cap");
+    return KFBI_ERR_NEWTON;
+  }
+  return KFBI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,481 @@
+// Box solver of the corrected 5/7-point system by sine transforms
+// (Sections 5.2-5.3: the correction leaves the symmetric definite matrix
+// unchanged, so an FFT-based fast Poisson/Helmholtz solver applies).
+//
+//   v = (2/N)^d S( mu^{-1} o S r ),   S_{kp} = sin(pi k p / N),  k, p = 1..N-1,
+//   mu_p = sum_a mu1[p_a] - lambda,  mu1[p] = -(4/h^2) sin^2(pi p / (2N)).
+//
+// Work arrays are padded to N^d with index 0 of every axis holding the zero
+// Dirichlet value, so every line of the DST-I of length N-1 is a length-N row
+// starting at an aligned address.  Each 1-D DST-I of length N-1 runs in shared
+// memory as: sine pre-fold into a real sequence of length N, complex Stockham
+// FFT of length N/2 (radix 8/4/2/3 butterflies in registers), split into the
+// real DFT, and a prefix sum for the odd outputs.  A block owns a tile of W
+// independent lines laid out [transform index][line] so that every butterfly
+// stage is vectorised across the lines (consecutive threads touch consecutive
+// words).  Passes:
+//   x forward  : assembles r = alpha*src + corrections (irregular nodes) while
+//                loading, transforms along x;
+//   y forward  : strided rows, coalesced W-wide segments;
+//   z solve    : forward DST, spectral divide, inverse DST in one pass;
+//   y forward  : (the DST-I is its own inverse up to the folded scale);
+//   x inverse  : transforms along x and writes the padded grid and/or a user
+//                layout output  beta*v + gamma*aux.
+// In 2-D the middle pass is the y solve.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace kfbi {
+namespace {
+
+constexpr int NT = 256;
+
+template <typename T, int N>
+struct Cfg {
+  static constexpr int W = sizeof(T) == 8 ? (N >= 384 ? 16 : (N < 32 ? N : 32))
+                                          : (N >= 384 ? 32 : (N < 64 ? N : 64));
+  static constexpr int RS = W + 1;
+  static constexpr int L = N / 2;
+  static constexpr int G = NT / W;
+  static constexpr size_t smem_elems = (size_t)N * RS + (size_t)G * W + 4 * N;
+};
+
+__host__ __device__ constexpr int pick_radix(int L) {
+  return (L % 8 == 0) ? 8 : (L % 4 == 0) ? 4 : (L % 2 == 0) ? 2 : (L % 3 == 0) ? 3 : 0;
+}
+
+// ---------------------------------------------------------------- butterflies
+template <typename T, int R>
+struct Dft;
+
+template <typename T>
+struct Dft<T, 2> {
+  static __device__ __forceinline__ void run(T* xr, T* xi) {
+    T ar = xr[0] + xr[1], ai = xi[0] + xi[1];
+    xr[1] = xr[0] - xr[1];
+    xi[1] = xi[0] - xi[1];
+    xr[0] = ar;
+    xi[0] = ai;
+  }
+};
+
+// b_p = sum_q a_q e^{+2 pi i p q / 4}
+template <typename T>
+struct Dft<T, 4> {
+  static __device__ __forceinline__ void run(T* xr, T* xi) {
+    T t0r = xr[0] + xr[2], t0i = xi[0] + xi[2];
+    T t1r = xr[0] - xr[2], t1i = xi[0] - xi[2];
+    T t2r = xr[1] + xr[3], t2i = xi[1] + xi[3];
+    T t3r = xr[1] - xr[3], t3i = xi[1] - xi[3];
+    xr[0] = t0r + t2r;
+    xi[0] = t0i + t2i;
+    xr[2] = t0r - t2r;
+    xi[2] = t0i - t2i;
+    // b1 = t1 + i t3, b3 = t1 - i t3
+    xr[1] = t1r - t3i;
+    xi[1] = t1i + t3r;
+    xr[3] = t1r + t3i;
+    xi[3] = t1i - t3r;
+  }
+};
+
+template <typename T>
+struct Dft<T, 8> {
+  static __device__ __forceinline__ void run(T* xr, T* xi) {
+    T er[4] = {xr[0], xr[2], xr[4], xr[6]}, ei[4] = {xi[0], xi[2], xi[4], xi[6]};
+    T orr[4] = {xr[1], xr[3], xr[5], xr[7]}, oi[4] = {xi[1], xi[3], xi[5], xi[7]};
+    Dft<T, 4>::run(er, ei);
+    Dft<T, 4>::run(orr, oi);
+    const T c = (T)0.70710678118654752440;
+    // w8^p O_p with w8 = e^{+i pi/4}
+    T w1r = c * (orr[1] - oi[1]), w1i = c * (orr[1] + oi[1]);
+    T w2r = -oi[2], w2i = orr[2];
+    T w3r = -c * (orr[3] + oi[3]), w3i = c * (orr[3] - oi[3]);
+    xr[0] = er[0] + orr[0];
+    xi[0] = ei[0] + oi[0];
+    xr[4] = er[0] - orr[0];
+    xi[4] = ei[0] - oi[0];
+    xr[1] = er[1] + w1r;
+    xi[1] = ei[1] + w1i;
+    xr[5] = er[1] - w1r;
+    xi[5] = ei[1] - w1i;
+    xr[2] = er[2] + w2r;
+    xi[2] = ei[2] + w2i;
+    xr[6] = er[2] - w2r;
+    xi[6] = ei[2] - w2i;
+    xr[3] = er[3] + w3r;
+    xi[3] = ei[3] + w3i;
+    xr[7] = er[3] - w3r;
+    xi[7] = ei[3] - w3i;
+  }
+};
+
+template <typename T>
+struct Dft<T, 3> {
+  static __device__ __forceinline__ void run(T* xr, T* xi) {
+    const T s3 = (T)0.86602540378443864676;
+    T tr = xr[1] + xr[2], ti = xi[1] + xi[2];
+    T ur = xr[1] - xr[2], ui = xi[1] - xi[2];
+    T mr = xr[0] - (T)0.5 * tr, mi = xi[0] - (T)0.5 * ti;
+    xr[0] = xr[0] + tr;
+    xi[0] = xi[0] + ti;
+    // b1 = m + i s3 u, b2 = m - i s3 u
+    xr[1] = mr - s3 * ui;
+    xi[1] = mi + s3 * ur;
+    xr[2] = mr + s3 * ui;
+    xi[2] = mi - s3 * ur;
+  }
+};
+
+// One in-place Stockham stage of radix R on the complex sequence stored in
+// rows (2m, 2m+1) of every column.  All reads precede all writes.
+template <typename T, int N, int R>
+__device__ __forceinline__ void fft_stage(T* s, const T* tw, int Ls) {
+  using C = Cfg<T, N>;
+  constexpr int L = C::L, W = C::W, RS = C::RS;
+  constexpr int NB = (L / R) * W;
+  constexpr int PER = NB > 0 ? (NB + NT - 1) / NT : 1;  // stages never taken for small L still compile
+  T xr[PER][R], xi[PER][R];
+#pragma unroll
+  for (int b = 0; b < PER; ++b) {
+    const int idx = threadIdx.x + b * NT;
+    if (idx < NB) {
+      const int c = idx % W, j = idx / W, k = j % Ls;
+      const int tstep = (L / (R * Ls)) * k;
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int m = j + q * (L / R);
+        T ar = s[(2 * m) * RS + c], ai = s[(2 * m + 1) * RS + c];
+        if (q > 0) {
+          const int e = 4 * ((tstep * q) % L);
+          const T wr = tw[2 * e], wi = tw[2 * e + 1];
+          const T t = ar * wr - ai * wi;
+          ai = ar * wi + ai * wr;
+          ar = t;
+        }
+        xr[b][q] = ar;
+        xi[b][q] = ai;
+      }
+      Dft<T, R>::run(xr[b], xi[b]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < PER; ++b) {
+    const int idx = threadIdx.x + b * NT;
+    if (idx < NB) {
+      const int c = idx % W, j = idx / W, k = j % Ls;
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int p = 0; p < R; ++p) {
+        const int m = base + p * Ls;
+        s[(2 * m) * RS + c] = xr[b][p];
+        s[(2 * m + 1) * RS + c] = xi[b][p];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// DST-I of every column of the tile s[N][RS] (rows 1..N-1 in, rows 1..N-1
+// out, row 0 holds 0).  tw = e^{i pi j / N}, j = 0..2N-1 (interleaved re, im);
+// tot = scan scratch [G][W].
+template <typename T, int N>
+__device__ void dst1_tile(T* s, const T* tw, T* tot) {
+  using C = Cfg<T, N>;
+  constexpr int L = C::L, W = C::W, RS = C::RS, G = C::G;
+  // sine pre-fold: y_j = sin(j pi/N)(x_j + x_{N-j}) + (x_j - x_{N-j})/2
+  for (int idx = threadIdx.x; idx < (N / 2 + 1) * W; idx += NT) {
+    const int c = idx % W, j = idx / W;
+    if (j == 0) {
+      s[c] = (T)0;
+    } else if (j == N / 2) {
+      s[j * RS + c] *= (T)2;
+    } else {
+      const T a = s[j * RS + c], b = s[(N - j) * RS + c];
+      const T sj = tw[2 * j + 1];
+      const T t1 = sj * (a + b), t2 = (T)0.5 * (a - b);
+      s[j * RS + c] = t1 + t2;
+      s[(N - j) * RS + c] = t1 - t2;
+    }
+  }
+  __syncthreads();
+  // complex FFT of length L = N/2 on z_m = y_{2m} + i y_{2m+1}
+  {
+    int Lrem = L, Ls = 1;
+    while (Lrem > 1) {
+      const int r = pick_radix(Lrem);
+      if (r == 8) fft_stage<T, N, 8>(s, tw, Ls);
+      else if (r == 4) fft_stage<T, N, 4>(s, tw, Ls);
+      else if (r == 2) fft_stage<T, N, 2>(s, tw, Ls);
+      else fft_stage<T, N, 3>(s, tw, Ls);
+      Ls *= r;
+      Lrem /= r;
+    }
+  }
+  // real-DFT split: Y_k = (A + conj B)/2 - i w_k (A - conj B)/2, A = Z_k,
+  // B = Z_{L-k}, w_k = e^{2 pi i k / N}; store I_k in row 2k, R_k in row 2k+1
+  for (int idx = threadIdx.x; idx < (L / 2 + 1) * W; idx += NT) {
+    const int c = idx % W, k = idx / W;
+    if (k == 0) {
+      const T a = s[c], b = s[RS + c];
+      s[c] = (T)0;
+      s[RS + c] = (T)0.5 * (a + b);  // F_1 = R_0 / 2
+    } else {
+      const int kk = L - k;
+      const T Ar = s[(2 * k) * RS + c], Ai = s[(2 * k + 1) * RS + c];
+      const T Br = s[(2 * kk) * RS + c], Bi = s[(2 * kk + 1) * RS + c];
+      {
+        const T wr = tw[2 * (2 * k)], wi = tw[2 * (2 * k) + 1];
+        const T Sr = Ar + Br, Si = Ai - Bi, Dr = Ar - Br, Di = Ai + Bi;
+        const T Yr = (T)0.5 * (Sr + wr * Di + wi * Dr);
+        const T Yi = (T)0.5 * (Si - wr * Dr + wi * Di);
+        s[(2 * k) * RS + c] = Yi;
+        s[(2 * k + 1) * RS + c] = Yr;
+      }
+      if (kk != k) {
+        const T wr = tw[2 * (2 * kk)], wi = tw[2 * (2 * kk) + 1];
+        const T Sr = Br + Ar, Si = Bi - Ai, Dr = Br - Ar, Di = Bi + Ai;
+        const T Yr = (T)0.5 * (Sr + wr * Di + wi * Dr);
+        const T Yi = (T)0.5 * (Si - wr * Dr + wi * Di);
+        s[(2 * kk) * RS + c] = Yi;
+        s[(2 * kk + 1) * RS + c] = Yr;
+      }
+    }
+  }
+  __syncthreads();
+  // odd outputs: F_{2k+1} = F_{2k-1} + R_k (column-wise inclusive scan)
+  {
+    constexpr int SEG = (L + G - 1) / G;
+    const int c = threadIdx.x % W, g = threadIdx.x / W;
+    const int k0 = g * SEG;
+    const int k1 = (k0 + SEG < L) ? k0 + SEG : L;
+    T acc = (T)0;
+    for (int k = k0; k < k1; ++k) {
+      acc += s[(2 * k + 1) * RS + c];
+      s[(2 * k + 1) * RS + c] = acc;
+    }
+    tot[g * W + c] = acc;
+    __syncthreads();
+    T off = (T)0;
+    for (int g2 = 0; g2 < g; ++g2) off += tot[g2 * W + c];
+    for (int k = k0; k < k1; ++k) s[(2 * k + 1) * RS + c] += off;
+    __syncthreads();
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void load_twiddles(T* tw_s, const T* tw_g) {
+  for (int i = threadIdx.x; i < 4 * N; i += NT) tw_s[i] = tw_g[i];
+}
+
+// ------------------------------------------------------------- x forward
+// Tile: W consecutive lines y0..y0+W-1 of plane z; assembles
+// r = alpha*src + corrections on the fly.
+template <typename T, int N, int DIM>
+__global__ void __launch_bounds__(NT) k_xfwd(T* __restrict__ a, const double* __restrict__ src, double alpha,
+                                             const double* __restrict__ corr, const int32_t* __restrict__ irr,
+                                             const int32_t* __restrict__ line_start, const T* __restrict__ tw_g) {
+  using C = Cfg<T, N>;
+  constexpr int W = C::W, RS = C::RS, n1 = N - 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  T* tot = s + N * RS;
+  T* tw = tot + C::G * W;
+  load_twiddles<T, N>(tw, tw_g);
+  const int y0 = blockIdx.x * W;
+  const int z = DIM == 3 ? blockIdx.y + 1 : 0;
+  for (int idx = threadIdx.x; idx < N * W; idx += NT) {
+    const int x = idx % N, c = idx / N, y = y0 + c;
+    T v = (T)0;
+    if (src != nullptr && x > 0 && y > 0) {
+      const size_t line = DIM == 3 ? (size_t)(z - 1) * n1 + (y - 1) : (size_t)(y - 1);
+      v = (T)(alpha * src[line * n1 + (x - 1)]);
+    }
+    s[x * RS + c] = v;
+  }
+  __syncthreads();
+  if (corr != nullptr && threadIdx.x < W) {
+    const int c = threadIdx.x, y = y0 + c;
+    if (y > 0) {
+      const int line = DIM == 3 ? (z - 1) * n1 + (y - 1) : (y - 1);
+      const int i0 = line_start[line], i1 = line_start[line + 1];
+      for (int i = i0; i < i1; ++i) {
+        const int x = irr[i] % n1 + 1;
+        s[x * RS + c] += (T)corr[i];
+      }
+    }
+  }
+  __syncthreads();
+  dst1_tile<T, N>(s, tw, tot);
+  const size_t plane = (size_t)z * N * N;
+  for (int idx = threadIdx.x; idx < N * W; idx += NT) {
+    const int x = idx % N, c = idx / N;
+    a[plane + (size_t)(y0 + c) * N + x] = s[x * RS + c];
+  }
+}
+
+// ------------------------------------------------------------- x inverse
+template <typename T, int N, int DIM>
+__global__ void __launch_bounds__(NT) k_xinv(T* __restrict__ a, bool keep, double* __restrict__ out,
+                                             const double* __restrict__ aux, double beta, double gamma,
+                                             const T* __restrict__ tw_g) {
+  using C = Cfg<T, N>;
+  constexpr int W = C::W, RS = C::RS, n1 = N - 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  T* tot = s + N * RS;
+  T* tw = tot + C::G * W;
+  load_twiddles<T, N>(tw, tw_g);
+  const int y0 = blockIdx.x * W;
+  const int z = DIM == 3 ? blockIdx.y + 1 : 0;
+  const size_t plane = (size_t)z * N * N;
+  for (int idx = threadIdx.x; idx < N * W; idx += NT) {
+    const int x = idx % N, c = idx / N;
+    s[x * RS + c] = a[plane + (size_t)(y0 + c) * N + x];
+  }
+  __syncthreads();
+  dst1_tile<T, N>(s, tw, tot);
+  for (int idx = threadIdx.x; idx < N * W; idx += NT) {
+    const int x = idx % N, c = idx / N, y = y0 + c;
+    const T v = s[x * RS + c];
+    if (keep) a[plane + (size_t)y * N + x] = v;
+    if (out != nullptr && x > 0 && y > 0) {
+      const size_t line = DIM == 3 ? (size_t)(z - 1) * n1 + (y - 1) : (size_t)(y - 1);
+      const size_t o = line * n1 + (x - 1);
+      double r = beta * (double)v;
+      if (aux != nullptr) r += gamma * aux[o];
+      out[o] = r;
+    }
+  }
+}
+
+// --------------------------------------------------- strided (y / z) passes
+// Tile rows = transform index k (stride row_stride), columns x0..x0+W-1 of
+// plane q = blockIdx.y + qoff.  SOLVE = forward DST, spectral multiply,
+// inverse DST.
+template <typename T, int N, bool SOLVE, int DIM>
+__global__ void __launch_bounds__(NT) k_strided(T* __restrict__ a, size_t row_stride, size_t plane_stride, int qoff,
+                                                const T* __restrict__ mu1, T lambda, T scale,
+                                                const T* __restrict__ tw_g) {
+  using C = Cfg<T, N>;
+  constexpr int W = C::W, RS = C::RS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  T* tot = s + N * RS;
+  T* tw = tot + C::G * W;
+  load_twiddles<T, N>(tw, tw_g);
+  const int x0 = blockIdx.x * W;
+  const int q = blockIdx.y + qoff;
+  T* base = a + (size_t)q * plane_stride + x0;
+  for (int idx = threadIdx.x; idx < N * W; idx += NT) {
+    const int c = idx % W, k = idx / W;
+    s[k * RS + c] = base[(size_t)k * row_stride + c];
+  }
+  __syncthreads();
+  dst1_tile<T, N>(s, tw, tot);
+  if (SOLVE) {
+    const T muq = DIM == 3 ? mu1[q] : (T)0;
+    for (int idx = threadIdx.x; idx < N * W; idx += NT) {
+      const int c = idx % W, k = idx / W, p = x0 + c;
+      T v = (T)0;
+      if (k > 0 && p > 0) v = s[k * RS + c] * (scale / (mu1[k] + mu1[p] + muq - lambda));
+      s[k * RS + c] = v;
+    }
+    __syncthreads();
+    dst1_tile<T, N>(s, tw, tot);
+  }
+  for (int idx = threadIdx.x; idx < N * W; idx += NT) {
+    const int c = idx % W, k = idx / W;
+    base[(size_t)k * row_stride + c] = s[k * RS + c];
+  }
+}
+
+// opt each kernel into its dynamic shared-memory size once per process
+template <typename K>
+int prep(K kernel, size_t smem) {
+  static const void* done[256];
+  static int ndone = 0;
+  const void* key = (const void*)kernel;
+  for (int i = 0; i < ndone; ++i)
+    if (done[i] == key) return KFBI_OK;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) {
+    set_error("cudaFuncSetAttribute failed: %s", cudaGetErrorString(e));
+    return KFBI_ERR_CUDA;
+  }
+  if (ndone < 256) done[ndone++] = key;
+  return KFBI_OK;
+}
+
+template <typename T, int N>
+int run_solve(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1, const T* tw) {
+  using C = Cfg<T, N>;
+  constexpr int W = C::W;
+  const size_t smem = C::smem_elems * sizeof(T);
+  const int dim = h->grid.dim;
+  cudaStream_t st = h->stream;
+  const Tables& t = h->t;
+  const T lam = (T)sa.lambda;
+  const T scale = (T)(dim == 3 ? (2.0 / N) * (2.0 / N) * (2.0 / N) : (2.0 / N) * (2.0 / N));
+  const size_t NN = (size_t)N * N;
+  int rc;
+  if (dim == 3) {
+    dim3 grid(N / W, N - 1);
+    if ((rc = prep(k_xfwd<T, N, 3>, smem))) return rc;
+    k_xfwd<T, N, 3><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.corr, t.irr, t.line_start, tw);
+    if ((rc = prep(k_strided<T, N, false, 3>, smem))) return rc;
+    k_strided<T, N, false, 3><<<grid, NT, smem, st>>>(work, N, NN, 1, mu1, lam, scale, tw);
+    if ((rc = prep(k_strided<T, N, true, 3>, smem))) return rc;
+    k_strided<T, N, true, 3><<<grid, NT, smem, st>>>(work, NN, N, 1, mu1, lam, scale, tw);
+    k_strided<T, N, false, 3><<<grid, NT, smem, st>>>(work, N, NN, 1, mu1, lam, scale, tw);
+    if ((rc = prep(k_xinv<T, N, 3>, smem))) return rc;
+    k_xinv<T, N, 3><<<grid, NT, smem, st>>>(work, true, sa.out_user, sa.aux, sa.beta, sa.gamma, tw);
+  } else {
+    dim3 grid(N / W, 1);
+    if ((rc = prep(k_xfwd<T, N, 2>, smem))) return rc;
+    k_xfwd<T, N, 2><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.corr, t.irr, t.line_start, tw);
+    if ((rc = prep(k_strided<T, N, true, 2>, smem))) return rc;
+    k_strided<T, N, true, 2><<<grid, NT, smem, st>>>(work, N, 0, 0, mu1, lam, scale, tw);
+    if ((rc = prep(k_xinv<T, N, 2>, smem))) return rc;
+    k_xinv<T, N, 2><<<grid, NT, smem, st>>>(work, true, sa.out_user, sa.aux, sa.beta, sa.gamma, tw);
+  }
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+template <typename T>
+int dispatch(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1, const T* tw) {
+  switch (h->grid.N) {
+    case 8: return run_solve<T, 8>(h, sa, work, mu1, tw);
+    case 16: return run_solve<T, 16>(h, sa, work, mu1, tw);
+    case 32: return run_solve<T, 32>(h, sa, work, mu1, tw);
+    case 64: return run_solve<T, 64>(h, sa, work, mu1, tw);
+    case 128: return run_solve<T, 128>(h, sa, work, mu1, tw);
+    case 256: return run_solve<T, 256>(h, sa, work, mu1, tw);
+    case 384: return run_solve<T, 384>(h, sa, work, mu1, tw);
+    case 512: return run_solve<T, 512>(h, sa, work, mu1, tw);
+    default:
+      set_error("unsupported grid size N=%d", h->grid.N);
+      return KFBI_ERR_ARG;
+  }
+}
+
+}  // namespace
+
+int dst_supported(int N) {
+  return N == 8 || N == 16 || N == 32 || N == 64 || N == 128 || N == 256 || N == 384 || N == 512;
+}
+
+int box_solve64(kfbi_handle* h, const SolveArgs& a, double* work) {
+  return dispatch<double>(h, a, work, h->t.mu, h->t.tw64);
+}
+
+int box_solve32(kfbi_handle* h, const SolveArgs& a, float* work) {
+  return dispatch<float>(h, a, work, h->t.mu32, h->t.tw32);
+}
+
+}  // namespace kfbi

@@ -1,0 +1,196 @@
+// Internal declarations shared by the CUDA translation units of the KFBI
+// library: the handle, device tables, launch helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "kfbi.h"
+
+namespace kfbi {
+
+constexpr int PATCH_MAX = 16;   // points of one local surface fit
+constexpr int MAX_RESTART = 64;
+
+// error-word bits written by device code
+constexpr int DEVERR_GEOMETRY = 1;
+constexpr int DEVERR_NEWTON = 2;
+constexpr int DEVERR_SINGULAR = 4;
+
+void set_error(const char* fmt, ...);
+
+#define KFBI_CUDA(call)                                                           \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      ::kfbi::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
+                        __FILE__, __LINE__);                                      \
+      return KFBI_ERR_CUDA;                                                       \
+    }                                                                             \
+  } while (0)
+
+#define KFBI_CHECK_LAUNCH()                                                       \
+  do {                                                                            \
+    cudaError_t e_ = cudaGetLastError();                                          \
+    if (e_ != cudaSuccess) {                                                      \
+      ::kfbi::set_error("kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                      \
+      return KFBI_ERR_CUDA;                                                       \
+    }                                                                             \
+  } while (0)
+
+// Geometry parameters copied to the device (plain values, passed by value).
+struct GeomParams {
+  int dim, kind, n_comp;
+  double p[16];
+  int comp_map[KFBI_MAX_COMP];
+  double comp_axes[KFBI_MAX_COMP][3];
+  int comp_tri_offset[KFBI_MAX_COMP];
+  int comp_vert_offset[KFBI_MAX_COMP];
+  int cube_n;
+};
+
+struct GridParams {
+  int dim, N;
+  double lo, h;
+};
+
+// Sparse tables of the hot path (all device pointers).
+struct Tables {
+  // irregular nodes, increasing user-layout flat index
+  int n_irr = 0;
+  int32_t* irr = nullptr;
+  int32_t* irr_arm = nullptr;     // [n_irr][6] arm codes: crossing*2 + end (end 0 = lower node)
+  int8_t* irr_narm = nullptr;     // [n_irr]
+  int32_t* line_start = nullptr;  // [(N-1)^(dim-1) + 1] first irregular index of each x-line
+  // crossings, sorted by (axis, lower node)
+  int n_int = 0;
+  int32_t* c_axis = nullptr;
+  int32_t* c_lo = nullptr;        // user-layout flat index of the lower node
+  int8_t* c_comp = nullptr;
+  double* c_z = nullptr;
+  int32_t* c_cnt = nullptr;       // entries of the crossing's density row
+  int32_t* c_pid = nullptr;       // [n_int][PATCH_MAX] indices into x = psi (3-D) or [psi; m] (2-D)
+  double* c_wlo = nullptr;        // [n_int][PATCH_MAX] correction weights for the lower node
+  double* c_whi = nullptr;        // [n_int][PATCH_MAX] correction weights for the upper node
+  // interface nodes
+  int M = 0;
+  int P = 0;                      // stencil points (6 or 10)
+  int32_t* n_base = nullptr;      // padded-layout index of the stencil centre
+  int8_t* n_sign = nullptr;       // [M][dim]
+  int32_t* n_center = nullptr;    // [M][dim] 1-based node indices
+  double* n_wn = nullptr;         // [M][P] weights of dv/dn on the stencil values
+  int32_t* n_dcnt = nullptr;      // [M] entries of the node's jump row
+  int32_t* n_dpid = nullptr;      // [M][PATCH_MAX + 1]
+  double* n_dw = nullptr;         // [M][PATCH_MAX + 1]
+  // 2-D periodic spline: moments m = G psi
+  double* spline_G = nullptr;     // [M][M]
+  // transform tables
+  double* mu = nullptr;           // [N] eigenvalues of the 1-D second difference (index 0 unused)
+  double* tw64 = nullptr;         // [2N] complex e^{i pi j / N}
+  float* mu32 = nullptr;
+  float* tw32 = nullptr;
+  uint8_t* inside = nullptr;      // [(N-1)^dim]
+  int n_inside = 0;
+};
+
+struct Workspace {
+  double* grid64 = nullptr;       // padded N^dim work grid
+  double* grid64b = nullptr;      // second padded grid (volume solution)
+  float* grid32 = nullptr;        // padded N^dim float grid
+  double* corr = nullptr;         // [n_irr] correction values
+  float* corr32 = nullptr;
+  double* xvec = nullptr;         // [2M] density vector (psi, spline moments)
+  double* vecs = nullptr;         // GMRES basis [(restart+1)][M] + scratch
+  double* small = nullptr;        // GMRES Hessenberg/Givens on device
+  double* partial = nullptr;      // reduction partial sums
+  double* g = nullptr;            // [M]
+  double* r = nullptr;            // [M]
+  double* tmp = nullptr;          // [M]
+  double* tmp2 = nullptr;         // [M]
+  double* psi_prev = nullptr;     // [M] density of the previous diffusion solve
+  double* host_small = nullptr;   // pinned host scalars
+  int* err = nullptr;             // device error word
+  int restart_cap = 0;
+};
+
+}  // namespace kfbi
+
+struct kfbi_handle {
+  kfbi::GeomParams gp;
+  kfbi::GridParams grid;
+  kfbi::Tables t;
+  kfbi::Workspace w;
+  kfbi_opts opts;
+  double sigma_i, sigma_e, dt, lambda;
+  cudaStream_t stream;
+  size_t device_bytes = 0;
+  std::vector<void*> allocations;
+  bool have_prev = false;
+};
+
+namespace kfbi {
+
+// allocation helper: records the pointer for kfbi_destroy
+template <typename T>
+int dalloc(kfbi_handle* h, T** p, size_t count) {
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+    return KFBI_ERR_OOM;
+  }
+  h->allocations.push_back((void*)*p);
+  h->device_bytes += count * sizeof(T);
+  return KFBI_OK;
+}
+
+// ---- launchers implemented in the .cu files ----
+
+// setup.cu
+int setup_build(kfbi_handle* h, const kfbi_geometry* geom);
+
+// dst.cu: box solve of r -> v on the padded grids
+//  src     : optional user-layout float64 field added with weight alpha
+//  corr    : optional compact corrections at the irregular nodes (float64)
+//  out_user: optional user-layout float64 output  out = beta*v + gamma*aux
+//  keep    : true = leave the solution in the padded work grid
+struct SolveArgs {
+  const double* src = nullptr;
+  double alpha = 1.0;
+  const double* corr = nullptr;
+  double* out_user = nullptr;
+  const double* aux = nullptr;
+  double beta = 1.0;
+  double gamma = 0.0;
+  double lambda = 0.0;
+};
+int box_solve64(kfbi_handle* h, const SolveArgs& a, double* work);
+int box_solve32(kfbi_handle* h, const SolveArgs& a, float* work);
+int dst_supported(int N);
+
+// ops.cu
+int launch_correction(kfbi_handle* h, const double* x, double* corr);
+int launch_spline(kfbi_handle* h, const double* psi, double* x);
+int launch_limit64(kfbi_handle* h, const double* grid, const double* x, const double* base, double sgn, double* out);
+int launch_limit32(kfbi_handle* h, const float* grid, const double* x, const double* base, double sgn, double* out);
+int launch_scatter_grid(kfbi_handle* h, const double* corr, double* grid_user);
+int launch_padded_to_user(kfbi_handle* h, const double* padded, double* user);
+
+// GMRES vector kernels (ops.cu)
+int vec_dots(kfbi_handle* h, const double* V, int nvec, int ld, const double* w, double* out_dev);
+int vec_update(kfbi_handle* h, double* w, const double* V, int nvec, int ld, const double* coef_dev, double sign);
+int vec_axpby(kfbi_handle* h, double* y, double a, const double* x, double b, int n);
+int vec_scale_by_norm(kfbi_handle* h, double* v, const double* w, const double* norm_dev, int n);
+int vec_copy(kfbi_handle* h, double* dst, const double* src, int n);
+int arnoldi_givens(kfbi_handle* h, double* small, int j, int ldh);
+int arnoldi_solve(kfbi_handle* h, double* small, int k, int ldh);
+
+int launch_react_fe(const kfbi_fhn* p, double k, double* V, double* w, int64_t n, cudaStream_t s);
+int launch_react_be(const kfbi_fhn* p, double k, double* V, double* w, int64_t n, int* err, cudaStream_t s);
+int launch_ue(kfbi_handle* h, const double* V, double* ue);
+
+}  // namespace kfbi

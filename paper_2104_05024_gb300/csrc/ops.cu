@@ -1,0 +1,434 @@
+// Hot-path kernels other than the transforms:
+//  - irregular-node correction (Section 5.3, Eq. correct) as a gather over
+//    each irregular node's crossing arms of precomputed density rows;
+//  - periodic-spline moments of the density (2-D boundary representation);
+//  - interface limits dv^+/dn (Section 5.4) as a 6/10-point gather from the
+//    padded solution grid plus the node's own jump row;
+//  - Krylov vector kernels (dot products, updates, Givens rotations);
+//  - FitzHugh-Nagumo forward/backward Euler half steps (Sections 3, 7);
+//  - extracellular potential with zero mean over Omega.
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+
+namespace kfbi {
+namespace {
+
+constexpr int RED_BLOCKS = 152;  // one partial sum per SM for the dot products
+
+__global__ void k_correction(Tables t, const double* __restrict__ x, double* __restrict__ corr) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.n_irr) return;
+  const int na = t.irr_narm[i];
+  double acc = 0.0;
+  for (int a = 0; a < na; ++a) {
+    const int code = t.irr_arm[(size_t)i * 6 + a];
+    const int c = code >> 1;
+    const double* w = (code & 1) ? t.c_whi : t.c_wlo;
+    const int K = t.c_cnt[c];
+    const size_t o = (size_t)c * PATCH_MAX;
+    for (int q = 0; q < K; ++q) acc += w[o + q] * x[t.c_pid[o + q]];
+  }
+  corr[i] = acc;
+}
+
+// x = [psi; m] with m_i = sum_j gcol[(i - j) mod M] psi_j
+__global__ void k_spline(const double* __restrict__ gcol, const double* __restrict__ psi, double* __restrict__ x, int M) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  double acc = 0.0;
+  for (int j = 0; j < M; ++j) {
+    int k = i - j;
+    if (k < 0) k += M;
+    acc += gcol[k] * psi[j];
+  }
+  x[i] = psi[i];
+  x[M + i] = acc;
+}
+
+// out_i = base_i + sgn * (sum_j wn_ij v(p_j) + sum_k dw_ik x[dpid_ik])
+template <typename T>
+__global__ void k_limit(Tables t, GridParams gr, const T* __restrict__ grid, const double* __restrict__ x,
+                        const double* __restrict__ base, double sgn, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.M) return;
+  const int d = gr.dim, N = gr.N;
+  const int64_t sx = 1, sy = N, sz = (int64_t)N * N;
+  const int64_t c = t.n_base[i];
+  const int s0 = t.n_sign[(size_t)i * d], s1 = t.n_sign[(size_t)i * d + 1];
+  const double* wn = t.n_wn + (size_t)i * t.P;
+  double acc = wn[0] * (double)grid[c] + wn[1] * (double)grid[c - sx] + wn[2] * (double)grid[c + sx] +
+               wn[3] * (double)grid[c - sy] + wn[4] * (double)grid[c + sy];
+  if (d == 2) {
+    acc += wn[5] * (double)grid[c + s0 * sx + s1 * sy];
+  } else {
+    const int s2 = t.n_sign[(size_t)i * d + 2];
+    acc += wn[5] * (double)grid[c - sz] + wn[6] * (double)grid[c + sz];
+    acc += wn[7] * (double)grid[c + s0 * sx + s1 * sy];
+    acc += wn[8] * (double)grid[c + s0 * sx + s2 * sz];
+    acc += wn[9] * (double)grid[c + s1 * sy + s2 * sz];
+  }
+  if (x != nullptr) {
+    const size_t o = (size_t)i * (PATCH_MAX + 1);
+    const int K = t.n_dcnt[i];
+    for (int k = 0; k < K; ++k) acc += t.n_dw[o + k] * x[t.n_dpid[o + k]];
+  }
+  out[i] = (base != nullptr ? base[i] : 0.0) + sgn * acc;
+}
+
+__global__ void k_scatter(Tables t, const double* __restrict__ corr, double* __restrict__ g, int64_t total) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < total; f += (int64_t)gridDim.x * blockDim.x)
+    g[f] = 0.0;
+}
+__global__ void k_scatter2(Tables t, const double* __restrict__ corr, double* __restrict__ g) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < t.n_irr) g[t.irr[i]] = corr[i];
+}
+
+__global__ void k_pad_to_user(GridParams gr, const double* __restrict__ p, double* __restrict__ u, int64_t total) {
+  const int N = gr.N, n1 = N - 1;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < total; f += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(f % n1) + 1, y = (int)((f / n1) % n1) + 1;
+    const int z = gr.dim == 3 ? (int)(f / ((int64_t)n1 * n1)) + 1 : 0;
+    u[f] = p[((int64_t)z * N + y) * N + x];
+  }
+}
+
+// ---------------------------------------------------------------- Krylov
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// partial[k][b] = sum over block b's slice of V_k . w
+__global__ void k_dots_partial(const double* __restrict__ V, int ld, const double* __restrict__ w, int n,
+                               double* __restrict__ partial) {
+  const int k = blockIdx.y;
+  const double* v = V + (size_t)k * ld;
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc += v[i] * w[i];
+  __shared__ double ws[32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+    if (threadIdx.x == 0) partial[(size_t)k * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+__global__ void k_dots_final(const double* __restrict__ partial, int nb, int nvec, double* __restrict__ out) {
+  const int k = blockIdx.x;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += partial[(size_t)k * nb + b];
+  __shared__ double ws[32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+    if (threadIdx.x == 0) out[k] = s;
+  }
+}
+
+// w += sign * sum_k coef[k] V_k
+__global__ void k_update(double* __restrict__ w, const double* __restrict__ V, int nvec, int ld,
+                         const double* __restrict__ coef, double sign, int n) {
+  __shared__ double cs[MAX_RESTART + 2];
+  for (int k = threadIdx.x; k < nvec; k += blockDim.x) cs[k] = coef[k];
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int k = 0; k < nvec; ++k) acc += cs[k] * V[(size_t)k * ld + i];
+    w[i] += sign * acc;
+  }
+}
+
+__global__ void k_axpby(double* __restrict__ y, double a, const double* __restrict__ x, double b, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = a * x[i] + b * y[i];
+}
+
+__global__ void k_scale_norm(double* __restrict__ v, const double* __restrict__ w, const double* __restrict__ nrm2, int n) {
+  const double s = sqrt(nrm2[0]);
+  const double inv = s > 0.0 ? 1.0 / s : 0.0;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = w[i] * inv;
+}
+
+// small-vector layout (doubles): H column-major [(m+1) x m] at 0, cs at HS,
+// sn at HS+m, g at HS+2m, hcol at HS+3m+1, nrm2 at HS+4m+2, result at HS+4m+3
+struct SmallLayout {
+  int m;
+  __host__ __device__ int H() const { return 0; }
+  __host__ __device__ int cs() const { return (m + 1) * m; }
+  __host__ __device__ int sn() const { return cs() + m; }
+  __host__ __device__ int g() const { return sn() + m; }
+  __host__ __device__ int hcol() const { return g() + m + 1; }
+  __host__ __device__ int nrm2() const { return hcol() + m + 2; }
+  __host__ __device__ int res() const { return nrm2() + 2; }
+  __host__ __device__ int y() const { return res() + 2; }
+  __host__ __device__ int total() const { return y() + m + 2; }
+};
+
+// column j of H from hcol and sqrt(nrm2); apply rotations; new rotation; |g_{j+1}|
+__global__ void k_givens(double* s, int m, int j) {
+  SmallLayout L{m};
+  double* H = s + L.H();
+  double* cs = s + L.cs();
+  double* sn = s + L.sn();
+  double* g = s + L.g();
+  const double* hc = s + L.hcol();
+  double col[MAX_RESTART + 2];
+  for (int i = 0; i <= j; ++i) col[i] = hc[i];
+  col[j + 1] = sqrt(s[L.nrm2()]);
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double den = hypot(col[j], col[j + 1]);
+  cs[j] = col[j] / den;
+  sn[j] = col[j + 1] / den;
+  col[j] = den;
+  col[j + 1] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  for (int i = 0; i <= j + 1; ++i) H[(size_t)j * (m + 1) + i] = col[i];
+  s[L.res()] = fabs(g[j + 1]);
+}
+
+// y = R^{-1} g for the leading k x k block
+__global__ void k_backsolve(double* s, int m, int k) {
+  SmallLayout L{m};
+  const double* H = s + L.H();
+  const double* g = s + L.g();
+  double* y = s + L.y();
+  for (int i = k - 1; i >= 0; --i) {
+    double a = g[i];
+    for (int c = i + 1; c < k; ++c) a -= H[(size_t)c * (m + 1) + i] * y[c];
+    y[i] = a / H[(size_t)i * (m + 1) + i];
+  }
+}
+
+__global__ void k_init_arnoldi(double* s, int m) {
+  SmallLayout L{m};
+  const int i = threadIdx.x;
+  if (i <= m) s[L.g() + i] = i == 0 ? sqrt(s[L.nrm2()]) : 0.0;
+}
+
+__global__ void k_add_small(double* s, int m, int n) {
+  // hcol += second-pass coefficients stored right after it (CGS2)
+  SmallLayout L{m};
+  const int i = threadIdx.x;
+  if (i < n) s[L.hcol() + i] += s[L.y() + i];
+}
+
+// ------------------------------------------------------------- reaction
+__global__ void k_react_fe(kfbi_fhn p, double k, double* __restrict__ V, double* __restrict__ w, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = V[i], q = w[i];
+    const double cubic = v * (v - p.theta) * (1.0 - v);
+    const double Iion = p.H * (q - cubic);
+    V[i] = v + k * (-Iion / p.Cm);
+    w[i] = q + k * (p.alpha * v - p.zeta * q);
+  }
+}
+
+__global__ void k_react_be(kfbi_fhn p, double k, double* __restrict__ V, double* __restrict__ w, int64_t n,
+                           int* err) {
+  const double c = k * p.H / p.Cm;
+  const double den = 1.0 + k * p.zeta;
+  const double r = k * p.alpha / den;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v0 = V[i], q0 = w[i];
+    double v = v0;
+    bool ok = false;
+    for (int it = 0; it < 50; ++it) {
+      const double q1 = (q0 + k * p.alpha * v) / den;
+      const double cubic = v * (v - p.theta) * (1.0 - v);
+      const double F = v - v0 - c * (cubic - q1);
+      const double dcubic = -3.0 * v * v + 2.0 * (1.0 + p.theta) * v - p.theta;
+      const double dF = 1.0 - c * (dcubic - r);
+      const double dv = F / dF;
+      v -= dv;
+      if (fabs(dv) < 1e-10) {
+        ok = true;
+        break;
+      }
+    }
+    if (!ok) atomicOr(err, DEVERR_NEWTON);
+    V[i] = v;
+    w[i] = (q0 + k * p.alpha * v) / den;
+  }
+}
+
+// sum of V over inside nodes -> partial sums
+__global__ void k_masked_sum(const double* __restrict__ V, const uint8_t* __restrict__ inside, int64_t n,
+                             double* __restrict__ partial) {
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (inside[i]) acc += V[i];
+  __shared__ double ws[32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_ue(const double* __restrict__ V, const double* __restrict__ sum, double inv_count, double si,
+                     double se, double* __restrict__ ue, int64_t n) {
+  const double mean = sum[0] * inv_count;
+  const double f = si / (si + se);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    ue[i] = f * (mean - V[i]);
+}
+
+int grid_blocks(int64_t n, int bs) {
+  int64_t b = (n + bs - 1) / bs;
+  if (b > 152 * 16) b = 152 * 16;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+int small_size(int m) { return SmallLayout{m}.total(); }
+int small_res(int m) { return SmallLayout{m}.res(); }
+int small_g(int m) { return SmallLayout{m}.g(); }
+int small_hcol(int m) { return SmallLayout{m}.hcol(); }
+int small_nrm2(int m) { return SmallLayout{m}.nrm2(); }
+int small_y(int m) { return SmallLayout{m}.y(); }
+
+int launch_correction(kfbi_handle* h, const double* x, double* corr) {
+  if (h->t.n_irr == 0) return KFBI_OK;
+  k_correction<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->t, x, corr);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+int launch_spline(kfbi_handle* h, const double* psi, double* x) {
+  const int M = h->t.M;
+  k_spline<<<(M + 127) / 128, 128, 0, h->stream>>>(h->t.spline_G, psi, x, M);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+int launch_limit64(kfbi_handle* h, const double* grid, const double* x, const double* base, double sgn, double* out) {
+  k_limit<double><<<(h->t.M + 127) / 128, 128, 0, h->stream>>>(h->t, h->grid, grid, x, base, sgn, out);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+int launch_limit32(kfbi_handle* h, const float* grid, const double* x, const double* base, double sgn, double* out) {
+  k_limit<float><<<(h->t.M + 127) / 128, 128, 0, h->stream>>>(h->t, h->grid, grid, x, base, sgn, out);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+int launch_scatter_grid(kfbi_handle* h, const double* corr, double* grid_user) {
+  const int n1 = h->grid.N - 1;
+  const int64_t total = h->grid.dim == 3 ? (int64_t)n1 * n1 * n1 : (int64_t)n1 * n1;
+  k_scatter<<<grid_blocks(total, 256), 256, 0, h->stream>>>(h->t, corr, grid_user, total);
+  if (h->t.n_irr > 0) k_scatter2<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->t, corr, grid_user);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+int launch_padded_to_user(kfbi_handle* h, const double* padded, double* user) {
+  const int n1 = h->grid.N - 1;
+  const int64_t total = h->grid.dim == 3 ? (int64_t)n1 * n1 * n1 : (int64_t)n1 * n1;
+  k_pad_to_user<<<grid_blocks(total, 256), 256, 0, h->stream>>>(h->grid, padded, user, total);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+int vec_dots(kfbi_handle* h, const double* V, int nvec, int ld, const double* w, double* out_dev) {
+  const int n = h->t.M;
+  int nb = (n + 255) / 256;
+  if (nb > RED_BLOCKS) nb = RED_BLOCKS;
+  k_dots_partial<<<dim3(nb, nvec), 256, 0, h->stream>>>(V, ld, w, n, h->w.partial);
+  k_dots_final<<<nvec, 256, 0, h->stream>>>(h->w.partial, nb, nvec, out_dev);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+int vec_update(kfbi_handle* h, double* w, const double* V, int nvec, int ld, const double* coef_dev, double sign) {
+  const int n = h->t.M;
+  k_update<<<grid_blocks(n, 256), 256, 0, h->stream>>>(w, V, nvec, ld, coef_dev, sign, n);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+int vec_axpby(kfbi_handle* h, double* y, double a, const double* x, double b, int n) {
+  k_axpby<<<(n + 255) / 256, 256, 0, h->stream>>>(y, a, x, b, n);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+int vec_scale_by_norm(kfbi_handle* h, double* v, const double* w, const double* norm_dev, int n) {
+  k_scale_norm<<<(n + 255) / 256, 256, 0, h->stream>>>(v, w, norm_dev, n);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+int vec_copy(kfbi_handle* h, double* dst, const double* src, int n) {
+  KFBI_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, h->stream));
+  return KFBI_OK;
+}
+
+int arnoldi_givens(kfbi_handle* h, double* small, int j, int m) {
+  k_givens<<<1, 1, 0, h->stream>>>(small, m, j);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+int arnoldi_solve(kfbi_handle* h, double* small, int k, int m) {
+  k_backsolve<<<1, 1, 0, h->stream>>>(small, m, k);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+int arnoldi_add(kfbi_handle* h, double* small, int m, int n) {
+  k_add_small<<<1, 128, 0, h->stream>>>(small, m, n);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+int launch_init_arnoldi(kfbi_handle* h, double* small, int m) {
+  k_init_arnoldi<<<1, 128, 0, h->stream>>>(small, m);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+int launch_react_fe(const kfbi_fhn* p, double k, double* V, double* w, int64_t n, cudaStream_t s) {
+  k_react_fe<<<grid_blocks(n, 256), 256, 0, s>>>(*p, k, V, w, n);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+int launch_react_be(const kfbi_fhn* p, double k, double* V, double* w, int64_t n, int* err, cudaStream_t s) {
+  k_react_be<<<grid_blocks(n, 256), 256, 0, s>>>(*p, k, V, w, n, err);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+int launch_ue(kfbi_handle* h, const double* V, double* ue) {
+  const int n1 = h->grid.N - 1;
+  const int64_t total = h->grid.dim == 3 ? (int64_t)n1 * n1 * n1 : (int64_t)n1 * n1;
+  const int nb = RED_BLOCKS;
+  k_masked_sum<<<nb, 256, 0, h->stream>>>(V, h->t.inside, total, h->w.partial);
+  k_dots_final<<<1, 256, 0, h->stream>>>(h->w.partial, nb, 1, h->w.partial + nb);
+  k_ue<<<grid_blocks(total, 256), 256, 0, h->stream>>>(V, h->w.partial + nb, 1.0 / (double)h->t.n_inside,
+                                                       h->sigma_i, h->sigma_e, ue, total);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+}  // namespace kfbi

@@ -1,0 +1,1091 @@
+// Setup of the KFBI tables (Section 6: classify the grid nodes, locate the
+// crossings of the interface with grid lines, compute normals, tangents and
+// curvatures there and at the interface nodes).
+//
+// This translation unit is compiled with -fmad=false: level sets, node
+// coordinates, cell indices and bisection midpoints use only correctly rounded
+// +, -, *, / and sqrt in a fixed order, so classification, crossings and
+// interface-to-cell indexing are reproducible bit for bit by any IEEE
+// implementation that evaluates the same expressions.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace kfbi {
+namespace {
+
+constexpr int BISECT_ITERS = 64;
+
+// ------------------------------------------------------------ level sets
+__host__ __device__ inline double phi_ellipse2(double x, double y, const double* p) {
+  const double xr = p[2] * x + p[3] * y;
+  const double yr = p[2] * y - p[3] * x;
+  const double u = xr / p[0];
+  const double v = yr / p[1];
+  return (u * u + v * v) - 1.0;
+}
+
+__host__ __device__ inline double phi_ellipsoid(double x, double y, double z, double a, double b, double c) {
+  const double u = x / a;
+  const double v = y / b;
+  const double w = z / c;
+  return ((u * u + v * v) + w * w) - 1.0;
+}
+
+__host__ __device__ inline double phi_star(double x, double y, double z, double A, double B) {
+  const double x2 = x * x;
+  const double y2 = y * y;
+  const double z2 = z * z;
+  const double s2 = x2 + y2;
+  const double r2 = s2 + z2;
+  const double rho = sqrt(r2);
+  double g = 0.0;
+  if (s2 > 0.0) {
+    const double s = sqrt(s2);
+    g = ((x2 - y2) / s2) * ((s / rho) * (3.0 - 4.0 * (s2 / r2)));
+  }
+  return (rho - A) - B * g;
+}
+
+__host__ __device__ inline double comp_phi(const GeomParams& g, int comp, double x, double y, double z) {
+  switch (g.kind) {
+    case KFBI_ELLIPSE2: return phi_ellipse2(x, y, g.p);
+    case KFBI_ELLIPSOID3: return phi_ellipsoid(x, y, z, g.p[0], g.p[1], g.p[2]);
+    case KFBI_STAR3: return phi_star(x, y, z, g.p[0], g.p[1]);
+    default: {
+      const int o = comp == 0 ? 0 : 3;
+      return phi_ellipsoid(x, y, z, g.p[o], g.p[o + 1], g.p[o + 2]);
+    }
+  }
+}
+
+// enclosed side of one surface: Phi <= 0, except the hole of the shell (Phi < 0)
+__host__ __device__ inline bool comp_pred(const GeomParams& g, int comp, double x, double y, double z) {
+  const double ph = comp_phi(g, comp, x, y, z);
+  if (g.kind == KFBI_SHELL3 && comp == 1) return ph < 0.0;
+  return ph <= 0.0;
+}
+
+__host__ __device__ inline bool inside_pt(const GeomParams& g, double x, double y, double z) {
+  if (g.kind == KFBI_SHELL3) return comp_pred(g, 0, x, y, z) && !comp_pred(g, 1, x, y, z);
+  return comp_pred(g, 0, x, y, z);
+}
+
+__host__ __device__ inline double node_coord(const GridParams& gr, int k) { return gr.lo + (double)k * gr.h; }
+
+// --------------------------------------------------------------- 2-jets
+struct Jet {
+  double v, g[3], H[3][3];
+};
+
+__host__ __device__ inline Jet jconst(double c) {
+  Jet r;
+  r.v = c;
+  for (int i = 0; i < 3; ++i) {
+    r.g[i] = 0.0;
+    for (int j = 0; j < 3; ++j) r.H[i][j] = 0.0;
+  }
+  return r;
+}
+__host__ __device__ inline Jet jvar(double x, int k) {
+  Jet r = jconst(x);
+  r.g[k] = 1.0;
+  return r;
+}
+__host__ __device__ inline Jet jadd(const Jet& a, const Jet& b) {
+  Jet r;
+  r.v = a.v + b.v;
+  for (int i = 0; i < 3; ++i) {
+    r.g[i] = a.g[i] + b.g[i];
+    for (int j = 0; j < 3; ++j) r.H[i][j] = a.H[i][j] + b.H[i][j];
+  }
+  return r;
+}
+__host__ __device__ inline Jet jscale(const Jet& a, double s) {
+  Jet r;
+  r.v = a.v * s;
+  for (int i = 0; i < 3; ++i) {
+    r.g[i] = a.g[i] * s;
+    for (int j = 0; j < 3; ++j) r.H[i][j] = a.H[i][j] * s;
+  }
+  return r;
+}
+__host__ __device__ inline Jet jaddc(const Jet& a, double c) {
+  Jet r = a;
+  r.v = a.v + c;
+  return r;
+}
+__host__ __device__ inline Jet jmul(const Jet& a, const Jet& b) {
+  Jet r;
+  r.v = a.v * b.v;
+  for (int i = 0; i < 3; ++i) {
+    r.g[i] = a.g[i] * b.v + b.g[i] * a.v;
+    for (int j = 0; j < 3; ++j)
+      r.H[i][j] = a.H[i][j] * b.v + b.H[i][j] * a.v + a.g[i] * b.g[j] + b.g[i] * a.g[j];
+  }
+  return r;
+}
+__host__ __device__ inline Jet jrecip(const Jet& a) {
+  Jet r;
+  const double q = 1.0 / a.v;
+  r.v = q;
+  for (int i = 0; i < 3; ++i) {
+    r.g[i] = -a.g[i] * q * q;
+    for (int j = 0; j < 3; ++j) r.H[i][j] = -a.H[i][j] * q * q + 2.0 * a.g[i] * a.g[j] * q * q * q;
+  }
+  return r;
+}
+__host__ __device__ inline Jet jdiv(const Jet& a, const Jet& b) { return jmul(a, jrecip(b)); }
+__host__ __device__ inline Jet jsqrt(const Jet& a) {
+  Jet r;
+  const double s = sqrt(a.v);
+  r.v = s;
+  for (int i = 0; i < 3; ++i) {
+    r.g[i] = a.g[i] / (2.0 * s);
+    for (int j = 0; j < 3; ++j) r.H[i][j] = a.H[i][j] / (2.0 * s) - a.g[i] * a.g[j] / (4.0 * s * s * s);
+  }
+  return r;
+}
+
+__host__ __device__ Jet phi_jet(const GeomParams& gp, int comp, const double* P) {
+  const int d = gp.dim;
+  Jet X = jvar(P[0], 0), Y = jvar(P[1], 1);
+  Jet Z = d == 3 ? jvar(P[2], 2) : jconst(0.0);
+  const double* p = gp.p;
+  if (gp.kind == KFBI_ELLIPSE2) {
+    Jet u = jscale(jadd(jscale(X, p[2]), jscale(Y, p[3])), 1.0 / p[0]);
+    Jet v = jscale(jadd(jscale(Y, p[2]), jscale(X, -p[3])), 1.0 / p[1]);
+    return jaddc(jadd(jmul(u, u), jmul(v, v)), -1.0);
+  }
+  if (gp.kind == KFBI_ELLIPSOID3 || gp.kind == KFBI_SHELL3) {
+    const int o = (gp.kind == KFBI_SHELL3 && comp == 1) ? 3 : 0;
+    Jet u = jscale(X, 1.0 / p[o]), v = jscale(Y, 1.0 / p[o + 1]), w = jscale(Z, 1.0 / p[o + 2]);
+    return jaddc(jadd(jadd(jmul(u, u), jmul(v, v)), jmul(w, w)), -1.0);
+  }
+  // star body; the B term is dropped on the polar axis (see the oracle's reading)
+  const double A = p[0], B = p[1];
+  Jet x2 = jmul(X, X), y2 = jmul(Y, Y), z2 = jmul(Z, Z);
+  Jet s2 = jadd(x2, y2);
+  Jet r2 = jadd(s2, z2);
+  Jet out = jaddc(jsqrt(r2), -A);
+  if (s2.v > 0.0) {
+    Jet t1 = jdiv(jadd(x2, jscale(y2, -1.0)), s2);
+    Jet t2 = jdiv(jsqrt(s2), jsqrt(r2));
+    Jet t3 = jaddc(jscale(jdiv(s2, r2), -4.0), 3.0);
+    Jet gterm = jmul(t1, jmul(t2, t3));
+    out = jadd(out, jscale(gterm, -B));
+  }
+  return out;
+}
+
+// outward normal of Omega and shape operator S = P Hess P / |grad| at P
+__host__ __device__ void normal_shape(const GeomParams& gp, int comp, const double* P, double* n, double S[3][3]) {
+  const int d = gp.dim;
+  Jet J = phi_jet(gp, comp, P);
+  double gn = 0.0;
+  for (int i = 0; i < d; ++i) gn += J.g[i] * J.g[i];
+  gn = sqrt(gn);
+  for (int i = 0; i < 3; ++i) n[i] = i < d ? J.g[i] / gn : 0.0;
+  double Pm[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) Pm[i][j] = (i < d && j < d) ? ((i == j ? 1.0 : 0.0) - n[i] * n[j]) : 0.0;
+  double T[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double a = 0.0;
+      for (int k = 0; k < 3; ++k) a += Pm[i][k] * J.H[k][j];
+      T[i][j] = a;
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double a = 0.0;
+      for (int k = 0; k < 3; ++k) a += T[i][k] * Pm[k][j];
+      S[i][j] = a / gn;
+    }
+  if (gp.kind == KFBI_SHELL3 && comp == 1) {
+    for (int i = 0; i < 3; ++i) {
+      n[i] = -n[i];
+      for (int j = 0; j < 3; ++j) S[i][j] = -S[i][j];
+    }
+  }
+}
+
+// Gaussian elimination with partial pivoting: solve A x = b in place (n <= 10)
+__host__ __device__ bool gauss_solve(double* A, double* b, int n, int lda) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    double best = fabs(A[c * lda + c]);
+    for (int r = c + 1; r < n; ++r) {
+      const double v = fabs(A[r * lda + c]);
+      if (v > best) {
+        best = v;
+        piv = r;
+      }
+    }
+    if (best == 0.0) return false;
+    if (piv != c) {
+      for (int k = 0; k < n; ++k) {
+        const double t = A[c * lda + k];
+        A[c * lda + k] = A[piv * lda + k];
+        A[piv * lda + k] = t;
+      }
+      const double t = b[c];
+      b[c] = b[piv];
+      b[piv] = t;
+    }
+    for (int r = c + 1; r < n; ++r) {
+      const double f = A[r * lda + c] / A[c * lda + c];
+      if (f != 0.0) {
+        for (int k = c; k < n; ++k) A[r * lda + k] -= f * A[c * lda + k];
+        b[r] -= f * b[c];
+      }
+    }
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    double a = b[r];
+    for (int k = r + 1; k < n; ++k) a -= A[r * lda + k] * b[k];
+    b[r] = a / A[r * lda + r];
+  }
+  return true;
+}
+
+// ------------------------------------------------------------- kernels
+__global__ void k_classify(GeomParams gp, GridParams gr, uint8_t* inside, int64_t total) {
+  const int n1 = gr.N - 1;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < total; f += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(f % n1) + 1;
+    const int y = (int)((f / n1) % n1) + 1;
+    const int z = gr.dim == 3 ? (int)(f / ((int64_t)n1 * n1)) + 1 : 0;
+    const double X = node_coord(gr, x), Y = node_coord(gr, y), Z = gr.dim == 3 ? node_coord(gr, z) : 0.0;
+    inside[f] = inside_pt(gp, X, Y, Z) ? 1 : 0;
+  }
+}
+
+__host__ __device__ inline int64_t axis_stride(int a, int n1) {
+  return a == 0 ? 1 : (a == 1 ? (int64_t)n1 : (int64_t)n1 * n1);
+}
+__host__ __device__ inline int axis_index(int64_t f, int a, int n1) {
+  return (int)((f / axis_stride(a, n1)) % n1);
+}
+
+// flags: irregular (mode 0) or crossing edges along axis `a` (mode 1)
+__global__ void k_flags(GridParams gr, const uint8_t* inside, int64_t total, int mode, int a, uint8_t* flag, int* err) {
+  const int n1 = gr.N - 1;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < total; f += (int64_t)gridDim.x * blockDim.x) {
+    const uint8_t me = inside[f];
+    if (mode == 0) {
+      bool irr = false;
+      for (int ax = 0; ax < gr.dim; ++ax) {
+        const int k = axis_index(f, ax, n1);
+        const int64_t st = axis_stride(ax, n1);
+        const uint8_t lo = k > 0 ? inside[f - st] : 0;
+        const uint8_t hi = k < n1 - 1 ? inside[f + st] : 0;
+        if (lo != me || hi != me) irr = true;
+        if (me && (k == 0 || k == n1 - 1)) atomicOr(err, DEVERR_GEOMETRY);
+      }
+      flag[f] = irr ? 1 : 0;
+    } else {
+      const int k = axis_index(f, a, n1);
+      flag[f] = (k < n1 - 1 && inside[f + axis_stride(a, n1)] != me) ? 1 : 0;
+    }
+  }
+}
+
+// two-pass ordered compaction of flags into increasing indices
+constexpr int CB = 1024;
+__global__ void k_count(const uint8_t* flag, int64_t total, int* counts) {
+  __shared__ int s;
+  if (threadIdx.x == 0) s = 0;
+  __syncthreads();
+  const int64_t f = blockIdx.x * (int64_t)CB + threadIdx.x;
+  const int c = __syncthreads_count(f < total && flag[f]);
+  if (threadIdx.x == 0) counts[blockIdx.x] = c;
+}
+__global__ void k_write(const uint8_t* flag, int64_t total, const int* offsets, int32_t* out) {
+  __shared__ int warp_tot[CB / 32];
+  const int64_t f = blockIdx.x * (int64_t)CB + threadIdx.x;
+  const bool on = f < total && flag[f];
+  const unsigned bal = __ballot_sync(0xffffffffu, on);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) warp_tot[wid] = __popc(bal);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int w = 0; w < CB / 32; ++w) {
+      const int t = warp_tot[w];
+      warp_tot[w] = acc;
+      acc += t;
+    }
+  }
+  __syncthreads();
+  if (on) {
+    const int pos = offsets[blockIdx.x] + warp_tot[wid] + __popc(bal & ((1u << lane) - 1u));
+    out[pos] = (int32_t)f;
+  }
+}
+
+// crossing points by bisection on the surface whose predicate changes
+__global__ void k_bisect(GeomParams gp, GridParams gr, const int32_t* c_lo, const int32_t* c_axis, int n, double* c_z,
+                         int8_t* c_comp, int* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int n1 = gr.N - 1;
+  const int64_t f = c_lo[i];
+  const int a = c_axis[i];
+  int k[3] = {(int)(f % n1) + 1, (int)((f / n1) % n1) + 1, gr.dim == 3 ? (int)(f / ((int64_t)n1 * n1)) + 1 : 0};
+  double X[3] = {node_coord(gr, k[0]), node_coord(gr, k[1]), gr.dim == 3 ? node_coord(gr, k[2]) : 0.0};
+  double Xh[3] = {X[0], X[1], X[2]};
+  Xh[a] = node_coord(gr, k[a] + 1);
+  const int ncomp = gp.kind == KFBI_SHELL3 ? 2 : 1;
+  int comp = -1;
+  for (int c = 0; c < ncomp; ++c) {
+    if (comp_pred(gp, c, X[0], X[1], X[2]) != comp_pred(gp, c, Xh[0], Xh[1], Xh[2])) {
+      if (comp >= 0) atomicOr(err, DEVERR_GEOMETRY);
+      comp = c;
+    }
+  }
+  if (comp < 0) {
+    atomicOr(err, DEVERR_GEOMETRY);
+    comp = 0;
+  }
+  double lo = X[a], hi = Xh[a];
+  const bool plo = comp_pred(gp, comp, X[0], X[1], X[2]);
+  double P[3] = {X[0], X[1], X[2]};
+  for (int it = 0; it < BISECT_ITERS; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    P[a] = mid;
+    if (comp_pred(gp, comp, P[0], P[1], P[2]) == plo) lo = mid;
+    else hi = mid;
+  }
+  c_z[i] = 0.5 * (lo + hi);
+  c_comp[i] = (int8_t)comp;
+}
+
+// ---- local quadratic surface fit (3-D) ----
+__host__ __device__ void tangent_basis(const double* n, double* t1, double* t2) {
+  int k = 0;
+  double best = fabs(n[0]);
+  for (int ax = 1; ax < 3; ++ax)
+    if (fabs(n[ax]) < best) {
+      best = fabs(n[ax]);
+      k = ax;
+    }
+  double e[3] = {0.0, 0.0, 0.0};
+  e[k] = 1.0;
+  t1[0] = e[1] * n[2] - e[2] * n[1];
+  t1[1] = e[2] * n[0] - e[0] * n[2];
+  t1[2] = e[0] * n[1] - e[1] * n[0];
+  const double l = sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+  for (int i = 0; i < 3; ++i) t1[i] /= l;
+  t2[0] = n[1] * t1[2] - n[2] * t1[1];
+  t2[1] = n[2] * t1[0] - n[0] * t1[2];
+  t2[2] = n[0] * t1[1] - n[1] * t1[0];
+}
+
+// weights w0[K] (value) and wg[3][K] (surface gradient) of the quadratic fit at z
+__host__ __device__ bool fit_weights(const double* nodes, const int* ids, int K, const double* z, const double* n, double* w0,
+                            double (*wg)[PATCH_MAX]) {
+  double t1[3], t2[3];
+  tangent_basis(n, t1, t2);
+  double s[PATCH_MAX], t[PATCH_MAX];
+  double ell = 0.0;
+  for (int k = 0; k < K; ++k) {
+    const double* X = nodes + 3 * (size_t)ids[k];
+    const double D0 = X[0] - z[0], D1 = X[1] - z[1], D2 = X[2] - z[2];
+    ell = fmax(ell, sqrt(D0 * D0 + D1 * D1 + D2 * D2));
+    s[k] = D0 * t1[0] + D1 * t1[1] + D2 * t1[2];
+    t[k] = D0 * t2[0] + D1 * t2[1] + D2 * t2[2];
+  }
+  for (int k = 0; k < K; ++k) {
+    s[k] /= ell;
+    t[k] /= ell;
+  }
+  double V[PATCH_MAX][6];
+  for (int k = 0; k < K; ++k) {
+    V[k][0] = 1.0;
+    V[k][1] = s[k];
+    V[k][2] = t[k];
+    V[k][3] = s[k] * s[k];
+    V[k][4] = s[k] * t[k];
+    V[k][5] = t[k] * t[k];
+  }
+  // rows r = 0, 1, 2 of the (pseudo-)inverse
+  double rows[3][PATCH_MAX];
+  if (K == 6) {
+    for (int r = 0; r < 3; ++r) {
+      double A[36], b[6];
+      for (int i = 0; i < 6; ++i) {
+        for (int j = 0; j < 6; ++j) A[i * 6 + j] = V[j][i];  // V^T
+        b[i] = i == r ? 1.0 : 0.0;
+      }
+      if (!gauss_solve(A, b, 6, 6)) return false;
+      for (int k = 0; k < 6; ++k) rows[r][k] = b[k];
+    }
+  } else {
+    double Gm[36];
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) {
+        double a = 0.0;
+        for (int k = 0; k < K; ++k) a += V[k][i] * V[k][j];
+        Gm[i * 6 + j] = a;
+      }
+    for (int r = 0; r < 3; ++r) {
+      double A[36], b[6];
+      for (int i = 0; i < 36; ++i) A[i] = Gm[i];
+      for (int i = 0; i < 6; ++i) b[i] = i == r ? 1.0 : 0.0;
+      if (!gauss_solve(A, b, 6, 6)) return false;
+      for (int k = 0; k < K; ++k) {
+        double a = 0.0;
+        for (int l = 0; l < 6; ++l) a += V[k][l] * b[l];
+        rows[r][k] = a;
+      }
+    }
+  }
+  for (int k = 0; k < K; ++k) {
+    w0[k] = rows[0][k];
+    for (int i = 0; i < 3; ++i) wg[i][k] = (t1[i] * rows[1][k] + t2[i] * rows[2][k]) / ell;
+  }
+  return true;
+}
+
+__host__ __device__ int locate_tri(const GeomParams& gp, const double* cube_t, int comp, const double* P) {
+  double q[3] = {P[0], P[1], P[2]};
+  if (gp.comp_map[comp] == KFBI_MAP_ELLIPSOID) {
+    q[0] = P[0] / gp.comp_axes[comp][0];
+    q[1] = P[1] / gp.comp_axes[comp][1];
+    q[2] = P[2] / gp.comp_axes[comp][2];
+  }
+  int k = 0;
+  double best = fabs(q[0]);
+  for (int ax = 1; ax < 3; ++ax)
+    if (fabs(q[ax]) > best) {
+      best = fabs(q[ax]);
+      k = ax;
+    }
+  const int face = 2 * k + (q[k] < 0.0 ? 1 : 0);
+  const double u = q[(k + 1) % 3] / best;
+  const double v = q[(k + 2) % 3] / best;
+  const int n = gp.cube_n;
+  int i = 0, j = 0;
+  for (int m = 1; m < n; ++m) {
+    if (cube_t[m] <= u) i = m;
+    if (cube_t[m] <= v) j = m;
+  }
+  const double fu = (u - cube_t[i]) / (cube_t[i + 1] - cube_t[i]);
+  const double fv = (v - cube_t[j]) / (cube_t[j + 1] - cube_t[j]);
+  const int half = (fu + fv > 1.0) ? 1 : 0;
+  return gp.comp_tri_offset[comp] + (((face * n + j) * n + i) * 2 + half);
+}
+
+struct DensityInputs {
+  const double* nodes;      // [M][dim]
+  const int32_t* patch_ids; // [n_tri][PATCH_MAX]
+  const int32_t* patch_cnt; // [n_tri]
+  const double* cube_t;
+  int M;
+};
+
+// per crossing: density row (psi at z and its surface-gradient component along
+// the crossing axis) folded with the jump formula into correction weights for
+// both end nodes
+__host__ __device__ int crossing_row(const GeomParams& gp, const GridParams& gr, const DensityInputs& di,
+                                     const uint8_t* inside, const Tables& t, int i) {
+  int errbits = 0;
+  const int n1 = gr.N - 1, d = gr.dim;
+  const int64_t f = t.c_lo[i];
+  const int a = t.c_axis[i];
+  const int comp = t.c_comp[i];
+  int k[3] = {(int)(f % n1) + 1, (int)((f / n1) % n1) + 1, d == 3 ? (int)(f / ((int64_t)n1 * n1)) + 1 : 0};
+  double P[3] = {node_coord(gr, k[0]), node_coord(gr, k[1]), d == 3 ? node_coord(gr, k[2]) : 0.0};
+  const double xl = P[a], xh = node_coord(gr, k[a] + 1);
+  const double z = t.c_z[i];
+  P[a] = z;
+  double n[3], S[3][3];
+  normal_shape(gp, comp, P, n, S);
+  double trS = 0.0;
+  for (int q = 0; q < d; ++q) trS += S[q][q];
+  const double na = n[a];
+  const double Saa = S[a][a] - trS * na * na;  // [d_aa v] = psi Saa' + 2 n_a g_a
+  // density row: psi(z) = sum w0 x[pid], g_a = sum wa x[pid]
+  int pid[PATCH_MAX];
+  double w0[PATCH_MAX], wa[PATCH_MAX];
+  int K = 0;
+  if (d == 2) {
+    const double* p = gp.p;
+    const double xr = p[2] * P[0] + p[3] * P[1];
+    const double yr = p[2] * P[1] - p[3] * P[0];
+    const double twopi = 6.283185307179586476925286766559;
+    double tt = atan2(yr / p[1], xr / p[0]);
+    if (tt < 0.0) tt += twopi;
+    if (tt >= twopi) tt -= twopi;
+    const int M = di.M;
+    const double D = twopi / M;
+    int s = (int)floor(tt / D);
+    if (s > M - 1) s = M - 1;
+    if (s < 0) s = 0;
+    const double u = (tt - s * D) / D, w = 1.0 - u;
+    const int sp = (s + 1) % M;
+    const double speed = sqrt((p[0] * yr / p[1]) * (p[0] * yr / p[1]) + (p[1] * xr / p[0]) * (p[1] * xr / p[0]));
+    const double tau_a = a == 0 ? -n[1] : n[0];
+    const double ga = tau_a / speed;
+    K = 4;
+    pid[0] = s;
+    pid[1] = sp;
+    pid[2] = M + s;
+    pid[3] = M + sp;
+    w0[0] = w;
+    w0[1] = u;
+    w0[2] = (D * D / 6.0) * (w * w * w - w);
+    w0[3] = (D * D / 6.0) * (u * u * u - u);
+    wa[0] = -ga / D;
+    wa[1] = ga / D;
+    wa[2] = -ga * (D / 6.0) * (3.0 * w * w - 1.0);
+    wa[3] = ga * (D / 6.0) * (3.0 * u * u - 1.0);
+  } else {
+    const int tri = locate_tri(gp, di.cube_t, comp, P);
+    K = di.patch_cnt[tri];
+    int ids[PATCH_MAX];
+    for (int q = 0; q < K; ++q) ids[q] = di.patch_ids[(size_t)tri * PATCH_MAX + q];
+    double wg[3][PATCH_MAX];
+    if (!fit_weights(di.nodes, ids, K, P, n, w0, wg)) errbits |= DEVERR_SINGULAR;
+    for (int q = 0; q < K; ++q) {
+      pid[q] = ids[q];
+      wa[q] = wg[a][q];
+    }
+  }
+  // correction of end node e: -sigma_e/h^2 * (psi (n_a d + Saa d^2/2) + g_a n_a d^2), d = x_other - z
+  const double ih2 = 1.0 / (gr.h * gr.h);
+  const int64_t fh = f + axis_stride(a, n1);
+  const double sl = inside[f] ? -ih2 : ih2;
+  const double sh = inside[fh] ? -ih2 : ih2;
+  const double dl = xh - z, dh = xl - z;
+  const double cpl = sl * (na * dl + 0.5 * Saa * dl * dl), cgl = sl * (na * dl * dl);
+  const double cph = sh * (na * dh + 0.5 * Saa * dh * dh), cgh = sh * (na * dh * dh);
+  t.c_cnt[i] = K;
+  for (int q = 0; q < PATCH_MAX; ++q) {
+    const bool on = q < K;
+    t.c_pid[(size_t)i * PATCH_MAX + q] = on ? pid[q] : 0;
+    t.c_wlo[(size_t)i * PATCH_MAX + q] = on ? cpl * w0[q] + cgl * wa[q] : 0.0;
+    t.c_whi[(size_t)i * PATCH_MAX + q] = on ? cph * w0[q] + cgh * wa[q] : 0.0;
+  }
+  return errbits;
+}
+
+__global__ void k_crossing_rows(GeomParams gp, GridParams gr, DensityInputs di, const uint8_t* inside, Tables t,
+                                int* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.n_int) return;
+  const int e = crossing_row(gp, gr, di, inside, t, i);
+  if (e) atomicOr(err, e);
+}
+
+// per interface node: stencil centre/signs, Taylor weights of dv/dn, and the
+// coefficients A_i, B_i of the node's own jump terms (AB [M][4])
+__host__ __device__ int node_stencil_row(const GeomParams& gp, const GridParams& gr, const DensityInputs& di,
+                                         const uint8_t* inside, double* AB, const Tables& t, int i) {
+  int errbits = 0;
+  const int d = gr.dim, N = gr.N, n1 = N - 1;
+  double q[3] = {di.nodes[(size_t)i * d], di.nodes[(size_t)i * d + 1], d == 3 ? di.nodes[(size_t)i * d + 2] : 0.0};
+  int c[3] = {0, 0, 0}, sg[3] = {1, 1, 1};
+  for (int ax = 0; ax < d; ++ax) {
+    const double tt = (q[ax] - gr.lo) / gr.h;
+    c[ax] = (int)floor(tt + 0.5);
+    const double xc = gr.lo + (double)c[ax] * gr.h;
+    sg[ax] = q[ax] >= xc ? 1 : -1;
+    if (c[ax] < 2 || c[ax] > N - 2) errbits |= DEVERR_GEOMETRY;
+    t.n_center[(size_t)i * d + ax] = c[ax];
+    t.n_sign[(size_t)i * d + ax] = (int8_t)sg[ax];
+  }
+  if (errbits) return errbits;
+  t.n_base[i] = (int32_t)(((int64_t)(d == 3 ? c[2] : 0) * N + c[1]) * N + c[0]);
+  int comp = 0;
+  for (int cc = 1; cc < gp.n_comp; ++cc)
+    if (i >= gp.comp_vert_offset[cc]) comp = cc;
+  double n[3], S[3][3];
+  normal_shape(gp, comp, q, n, S);
+  double trS = 0.0;
+  for (int a = 0; a < d; ++a) trS += S[a][a];
+  // stencil offsets in the oracle's order
+  const int P = d == 2 ? 6 : 10;
+  int off[10][3];
+  int np = 0;
+  off[np][0] = off[np][1] = off[np][2] = 0;
+  ++np;
+  for (int a = 0; a < d; ++a)
+    for (int st = -1; st <= 1; st += 2) {
+      off[np][0] = off[np][1] = off[np][2] = 0;
+      off[np][a] = st;
+      ++np;
+    }
+  for (int a = 0; a < d; ++a)
+    for (int b = a + 1; b < d; ++b) {
+      off[np][0] = off[np][1] = off[np][2] = 0;
+      off[np][a] = sg[a];
+      off[np][b] = sg[b];
+      ++np;
+    }
+  double A[100], rhs[10];
+  double xi[10][3];
+  bool out[10];
+  for (int j = 0; j < P; ++j) {
+    double sx[3];
+    for (int a = 0; a < 3; ++a) {
+      xi[j][a] = a < d ? (gr.lo + (double)(c[a] + off[j][a]) * gr.h) - q[a] : 0.0;
+      sx[a] = xi[j][a] / gr.h;
+    }
+    double* row = A + j * P;  // row j of the Taylor matrix (stored transposed below)
+    int col = 0;
+    row[col++] = 1.0;
+    for (int a = 0; a < d; ++a) row[col++] = sx[a];
+    for (int a = 0; a < d; ++a) row[col++] = 0.5 * sx[a] * sx[a];
+    for (int a = 0; a < d; ++a)
+      for (int b = a + 1; b < d; ++b) row[col++] = sx[a] * sx[b];
+    int64_t f = (int64_t)(c[0] + off[j][0] - 1) + (int64_t)(c[1] + off[j][1] - 1) * n1;
+    if (d == 3) f += (int64_t)(c[2] + off[j][2] - 1) * n1 * n1;
+    out[j] = inside[f] == 0;
+  }
+  // wn solves A^T wn = n_ext / h with n_ext = (0, n_1..n_d, 0...)
+  double At[100];
+  for (int r = 0; r < P; ++r)
+    for (int cc = 0; cc < P; ++cc) At[r * P + cc] = A[cc * P + r];
+  for (int r = 0; r < P; ++r) rhs[r] = (r >= 1 && r <= d) ? n[r - 1] / gr.h : 0.0;
+  if (!gauss_solve(At, rhs, P, P)) errbits |= DEVERR_SINGULAR;
+  double Ai = 0.0, Bi[3] = {0.0, 0.0, 0.0};
+  for (int j = 0; j < P; ++j) {
+    t.n_wn[(size_t)i * P + j] = rhs[j];
+    if (!out[j]) continue;
+    double nx = 0.0;
+    for (int a = 0; a < d; ++a) nx += n[a] * xi[j][a];
+    double quad = 0.0;
+    for (int a = 0; a < d; ++a)
+      for (int b = 0; b < d; ++b) quad += xi[j][a] * (S[a][b] - trS * n[a] * n[b]) * xi[j][b];
+    Ai += rhs[j] * (nx + 0.5 * quad);
+    for (int a = 0; a < d; ++a) Bi[a] += rhs[j] * nx * xi[j][a];
+  }
+  AB[(size_t)i * 4 + 0] = Ai;
+  for (int a = 0; a < 3; ++a) AB[(size_t)i * 4 + 1 + a] = Bi[a];
+  return errbits;
+}
+
+// the node's jump row on x = psi (3-D) or [psi; m] (2-D):
+//   A_i psi_i + B_i . grad_Gamma psi(q_i)
+__host__ __device__ int node_density_row(const GeomParams& gp, const GridParams& gr, const DensityInputs& di,
+                                         const int32_t* vtri, const double* AB, const Tables& t, int i) {
+  int errbits = 0;
+  const int d = gr.dim;
+  double q[3] = {di.nodes[(size_t)i * d], di.nodes[(size_t)i * d + 1], d == 3 ? di.nodes[(size_t)i * d + 2] : 0.0};
+  int comp = 0;
+  for (int cc = 1; cc < gp.n_comp; ++cc)
+    if (i >= gp.comp_vert_offset[cc]) comp = cc;
+  double n[3], S[3][3];
+  normal_shape(gp, comp, q, n, S);
+  const double Ai = AB[(size_t)i * 4];
+  const double Bi[3] = {AB[(size_t)i * 4 + 1], AB[(size_t)i * 4 + 2], AB[(size_t)i * 4 + 3]};
+  const size_t o = (size_t)i * (PATCH_MAX + 1);
+  if (d == 2) {
+    const int M = di.M;
+    const double twopi = 6.283185307179586476925286766559;
+    const double D = twopi / M;
+    const double* p = gp.p;
+    const double xr = p[2] * q[0] + p[3] * q[1];
+    const double yr = p[2] * q[1] - p[3] * q[0];
+    const double speed = sqrt((p[0] * yr / p[1]) * (p[0] * yr / p[1]) + (p[1] * xr / p[0]) * (p[1] * xr / p[0]));
+    const double tau0 = -n[1], tau1 = n[0];
+    const double b = (Bi[0] * tau0 + Bi[1] * tau1) / speed;
+    const int ip = (i + 1) % M;
+    t.n_dcnt[i] = 4;
+    t.n_dpid[o + 0] = i;
+    t.n_dw[o + 0] = Ai - b / D;
+    t.n_dpid[o + 1] = ip;
+    t.n_dw[o + 1] = b / D;
+    t.n_dpid[o + 2] = M + i;
+    t.n_dw[o + 2] = -b * D / 3.0;
+    t.n_dpid[o + 3] = M + ip;
+    t.n_dw[o + 3] = -b * D / 6.0;
+    for (int k = 4; k < PATCH_MAX + 1; ++k) {
+      t.n_dpid[o + k] = 0;
+      t.n_dw[o + k] = 0.0;
+    }
+  } else {
+    const int tri = vtri[i];
+    const int K = di.patch_cnt[tri];
+    int ids[PATCH_MAX];
+    for (int k = 0; k < K; ++k) ids[k] = di.patch_ids[(size_t)tri * PATCH_MAX + k];
+    double w0[PATCH_MAX], wg[3][PATCH_MAX];
+    if (!fit_weights(di.nodes, ids, K, q, n, w0, wg)) errbits |= DEVERR_SINGULAR;
+    t.n_dcnt[i] = K + 1;
+    t.n_dpid[o] = i;
+    t.n_dw[o] = Ai;
+    for (int k = 0; k < PATCH_MAX; ++k) {
+      const bool on = k < K;
+      t.n_dpid[o + 1 + k] = on ? ids[k] : 0;
+      t.n_dw[o + 1 + k] = on ? Bi[0] * wg[0][k] + Bi[1] * wg[1][k] + Bi[2] * wg[2][k] : 0.0;
+    }
+  }
+  return errbits;
+}
+
+__global__ void k_node_stencil(GeomParams gp, GridParams gr, DensityInputs di, const uint8_t* inside, double* AB,
+                               Tables t, int* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.M) return;
+  const int e = node_stencil_row(gp, gr, di, inside, AB, t, i);
+  if (e) atomicOr(err, e);
+}
+
+__global__ void k_node_density(GeomParams gp, GridParams gr, DensityInputs di, const int32_t* vtri, const double* AB,
+                               Tables t, int* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.M) return;
+  const int e = node_density_row(gp, gr, di, vtri, AB, t, i);
+  if (e) atomicOr(err, e);
+}
+
+// per irregular node: its crossing arms (binary search in the per-axis lists)
+__global__ void k_irr_arms(GridParams gr, const uint8_t* inside, Tables t, const int* axis_off, int* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.n_irr) return;
+  const int n1 = gr.N - 1;
+  const int64_t f = t.irr[i];
+  const uint8_t me = inside[f];
+  int na = 0;
+  for (int a = 0; a < gr.dim; ++a) {
+    const int k = axis_index(f, a, n1);
+    const int64_t st = axis_stride(a, n1);
+    for (int side = 0; side < 2; ++side) {
+      int64_t lo;
+      if (side == 0) {
+        if (k == 0 || inside[f - st] == me) continue;
+        lo = f - st;
+      } else {
+        if (k == n1 - 1 || inside[f + st] == me) continue;
+        lo = f;
+      }
+      int b = axis_off[a], e = axis_off[a + 1];
+      while (b < e) {
+        const int m = (b + e) / 2;
+        if (t.c_lo[m] < lo) b = m + 1;
+        else e = m;
+      }
+      if (b >= axis_off[a + 1] || t.c_lo[b] != lo) {
+        atomicOr(err, DEVERR_GEOMETRY);
+        continue;
+      }
+      // end 0 = lower node of the crossing, end 1 = upper node
+      t.irr_arm[(size_t)i * 6 + na] = b * 2 + (side == 0 ? 1 : 0);
+      ++na;
+    }
+  }
+  t.irr_narm[i] = (int8_t)na;
+}
+
+__global__ void k_line_start(const int32_t* irr, int n_irr, int n1, int n_lines, int32_t* line_start) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n_irr) return;
+  const int li = i < n_irr ? irr[i] / n1 : n_lines;
+  const int prev = i == 0 ? -1 : irr[i - 1] / n1;
+  for (int l = prev + 1; l <= li; ++l) line_start[l] = i;
+}
+
+int blocks_for(int64_t n, int bs) { return (int)std::min<int64_t>((n + bs - 1) / bs, 1 << 20); }
+
+// ordered compaction of flag[0..total) -> out (device), returns count
+int compact(kfbi_handle* h, const uint8_t* flag, int64_t total, int32_t** out, int* count) {
+  const int nb = (int)((total + CB - 1) / CB);
+  int* counts = nullptr;
+  KFBI_CUDA(cudaMalloc(&counts, sizeof(int) * (size_t)nb));
+  k_count<<<nb, CB, 0, h->stream>>>(flag, total, counts);
+  std::vector<int> hc(nb);
+  KFBI_CUDA(cudaMemcpyAsync(hc.data(), counts, sizeof(int) * (size_t)nb, cudaMemcpyDeviceToHost, h->stream));
+  KFBI_CUDA(cudaStreamSynchronize(h->stream));
+  int acc = 0;
+  for (int b = 0; b < nb; ++b) {
+    const int c = hc[b];
+    hc[b] = acc;
+    acc += c;
+  }
+  *count = acc;
+  int rc = dalloc(h, out, (size_t)acc);
+  if (rc) {
+    cudaFree(counts);
+    return rc;
+  }
+  KFBI_CUDA(cudaMemcpyAsync(counts, hc.data(), sizeof(int) * (size_t)nb, cudaMemcpyHostToDevice, h->stream));
+  k_write<<<nb, CB, 0, h->stream>>>(flag, total, counts, *out);
+  KFBI_CUDA(cudaStreamSynchronize(h->stream));
+  cudaFree(counts);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+// surface-fit point lists of every triangle (six-point patch, or the vertex
+// ring of the triangle when one of its points has valence other than 6)
+int host_patches(const kfbi_geometry* g, std::vector<int32_t>& ids, std::vector<int32_t>& cnt,
+                 std::vector<int32_t>& vtri) {
+  const int nt = g->n_tri, nv = g->n_nodes;
+  const int32_t* T = g->tri;
+  std::unordered_map<int64_t, std::vector<std::pair<int, int>>> edges;
+  edges.reserve((size_t)nt * 2);
+  auto key = [](int u, int v) { return (int64_t)std::min(u, v) * (int64_t)(1 << 30) + std::max(u, v); };
+  std::vector<int> val(nv, 0);
+  std::vector<std::vector<int>> vt(nv);
+  for (int t = 0; t < nt; ++t) {
+    const int a = T[3 * t], b = T[3 * t + 1], c = T[3 * t + 2];
+    edges[key(a, b)].push_back({t, c});
+    edges[key(b, c)].push_back({t, a});
+    edges[key(c, a)].push_back({t, b});
+    for (int k = 0; k < 3; ++k) {
+      val[T[3 * t + k]]++;
+      vt[T[3 * t + k]].push_back(t);
+    }
+  }
+  ids.assign((size_t)nt * PATCH_MAX, 0);
+  cnt.assign(nt, 0);
+  vtri.assign(nv, 0);
+  for (int v = 0; v < nv; ++v) {
+    if (vt[v].empty()) {
+      set_error("interface node %d belongs to no triangle", v);
+      return KFBI_ERR_ARG;
+    }
+    vtri[v] = *std::min_element(vt[v].begin(), vt[v].end());
+  }
+  for (int t = 0; t < nt; ++t) {
+    const int a = T[3 * t], b = T[3 * t + 1], c = T[3 * t + 2];
+    int six[6] = {a, b, c, -1, -1, -1};
+    const int pairs[3][2] = {{a, b}, {b, c}, {c, a}};
+    for (int s = 0; s < 3; ++s) {
+      auto it = edges.find(key(pairs[s][0], pairs[s][1]));
+      if (it == edges.end() || it->second.size() != 2) {
+        set_error("surface mesh is not a closed manifold");
+        return KFBI_ERR_ARG;
+      }
+      const auto& l = it->second;
+      six[3 + s] = l[0].first != t ? l[0].second : l[1].second;
+    }
+    bool regular = true;
+    for (int k = 0; k < 6; ++k)
+      if (val[six[k]] != 6) regular = false;
+    if (regular) {
+      for (int k = 0; k < 6; ++k) ids[(size_t)t * PATCH_MAX + k] = six[k];
+      cnt[t] = 6;
+    } else {
+      std::vector<int> ring;
+      for (int k = 0; k < 3; ++k)
+        for (int tt : vt[T[3 * t + k]])
+          for (int m = 0; m < 3; ++m) ring.push_back(T[3 * tt + m]);
+      std::sort(ring.begin(), ring.end());
+      ring.erase(std::unique(ring.begin(), ring.end()), ring.end());
+      if (ring.size() > (size_t)PATCH_MAX || ring.size() < 6) {
+        set_error("unsupported vertex ring of %zu points", ring.size());
+        return KFBI_ERR_ARG;
+      }
+      for (size_t k = 0; k < ring.size(); ++k) ids[(size_t)t * PATCH_MAX + k] = ring[k];
+      cnt[t] = (int)ring.size();
+    }
+  }
+  return KFBI_OK;
+}
+
+// first column of G = C^{-1} (6/D^2) second-difference, C = circulant(4, 1, 1)
+void host_spline_column(int M, std::vector<double>& gcol) {
+  const double D = 2.0 * M_PI / M;
+  std::vector<double> rhs(M, 0.0);
+  rhs[0] = -2.0 * 6.0 / (D * D);
+  rhs[1 % M] += 6.0 / (D * D);
+  rhs[(M - 1) % M] += 6.0 / (D * D);
+  // cyclic tridiagonal solve (Sherman-Morrison) of  x_{i-1} + 4 x_i + x_{i+1} = rhs_i
+  const double gam = -4.0;
+  std::vector<double> bb(M, 4.0), u(M, 0.0), y(M), z(M), cp(M);
+  bb[0] = 4.0 - gam;
+  bb[M - 1] = 4.0 - 1.0 * 1.0 / gam;
+  auto thomas = [&](const std::vector<double>& r, std::vector<double>& x) {
+    cp[0] = 1.0 / bb[0];
+    x[0] = r[0] / bb[0];
+    for (int i = 1; i < M; ++i) {
+      const double m = bb[i] - cp[i - 1];
+      cp[i] = 1.0 / m;
+      x[i] = (r[i] - x[i - 1]) / m;
+    }
+    for (int i = M - 2; i >= 0; --i) x[i] -= cp[i] * x[i + 1];
+  };
+  thomas(rhs, y);
+  u[0] = gam;
+  u[M - 1] = 1.0;
+  thomas(u, z);
+  const double fact = (y[0] + y[M - 1] / gam) / (1.0 + z[0] + z[M - 1] / gam);
+  gcol.resize(M);
+  for (int i = 0; i < M; ++i) gcol[i] = y[i] - fact * z[i];
+}
+
+template <typename T>
+int upload(kfbi_handle* h, T** dst, const T* src, size_t n) {
+  int rc = dalloc(h, dst, n);
+  if (rc) return rc;
+  KFBI_CUDA(cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+  return KFBI_OK;
+}
+
+}  // namespace
+
+int setup_build(kfbi_handle* h, const kfbi_geometry* geom) {
+  const GridParams gr = h->grid;
+  GeomParams& gp = h->gp;
+  const int d = gr.dim, N = gr.N, n1 = N - 1;
+  const int64_t total = d == 3 ? (int64_t)n1 * n1 * n1 : (int64_t)n1 * n1;
+  Tables& t = h->t;
+  cudaStream_t st = h->stream;
+  int rc;
+
+  int* err = h->w.err;
+  KFBI_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  if ((rc = dalloc(h, &t.inside, (size_t)total))) return rc;
+  k_classify<<<blocks_for(total, 256), 256, 0, st>>>(gp, gr, t.inside, total);
+  uint8_t* flag = nullptr;
+  KFBI_CUDA(cudaMalloc(&flag, (size_t)total));
+  k_flags<<<blocks_for(total, 256), 256, 0, st>>>(gr, t.inside, total, 0, 0, flag, err);
+  KFBI_CHECK_LAUNCH();
+  if ((rc = compact(h, flag, total, &t.irr, &t.n_irr))) {
+    cudaFree(flag);
+    return rc;
+  }
+  // crossings along each axis, concatenated in axis order
+  std::vector<int32_t*> parts(d, nullptr);
+  std::vector<int> pc(d, 0);
+  int axis_off_h[4] = {0, 0, 0, 0};
+  for (int a = 0; a < d; ++a) {
+    k_flags<<<blocks_for(total, 256), 256, 0, st>>>(gr, t.inside, total, 1, a, flag, err);
+    if ((rc = compact(h, flag, total, &parts[a], &pc[a]))) {
+      cudaFree(flag);
+      return rc;
+    }
+    axis_off_h[a + 1] = axis_off_h[a] + pc[a];
+  }
+  cudaFree(flag);
+  t.n_int = axis_off_h[d];
+  if ((rc = dalloc(h, &t.c_lo, (size_t)t.n_int))) return rc;
+  if ((rc = dalloc(h, &t.c_axis, (size_t)t.n_int))) return rc;
+  {
+    std::vector<int32_t> ax(t.n_int);
+    for (int a = 0; a < d; ++a) {
+      KFBI_CUDA(cudaMemcpyAsync(t.c_lo + axis_off_h[a], parts[a], sizeof(int32_t) * pc[a], cudaMemcpyDeviceToDevice, st));
+      for (int i = axis_off_h[a]; i < axis_off_h[a + 1]; ++i) ax[i] = a;
+    }
+    KFBI_CUDA(cudaMemcpyAsync(t.c_axis, ax.data(), sizeof(int32_t) * t.n_int, cudaMemcpyHostToDevice, st));
+    KFBI_CUDA(cudaStreamSynchronize(st));
+  }
+  int* axis_off = nullptr;
+  if ((rc = upload(h, &axis_off, axis_off_h, 4))) return rc;
+  if ((rc = dalloc(h, &t.c_z, (size_t)t.n_int))) return rc;
+  if ((rc = dalloc(h, &t.c_comp, (size_t)t.n_int))) return rc;
+  if (t.n_int > 0) k_bisect<<<(t.n_int + 127) / 128, 128, 0, st>>>(gp, gr, t.c_lo, t.c_axis, t.n_int, t.c_z, t.c_comp, err);
+  KFBI_CHECK_LAUNCH();
+
+  // irregular arms and x-line offsets
+  if ((rc = dalloc(h, &t.irr_arm, (size_t)t.n_irr * 6))) return rc;
+  if ((rc = dalloc(h, &t.irr_narm, (size_t)t.n_irr))) return rc;
+  if (t.n_irr > 0) k_irr_arms<<<(t.n_irr + 127) / 128, 128, 0, st>>>(gr, t.inside, t, axis_off, err);
+  const int n_lines = d == 3 ? n1 * n1 : n1;
+  if ((rc = dalloc(h, &t.line_start, (size_t)n_lines + 1))) return rc;
+  k_line_start<<<(t.n_irr + 1 + 127) / 128, 128, 0, st>>>(t.irr, t.n_irr, n1, n_lines, t.line_start);
+  KFBI_CHECK_LAUNCH();
+
+  // density inputs
+  t.M = geom->n_nodes;
+  t.P = d == 2 ? 6 : 10;
+  DensityInputs di{};
+  di.M = t.M;
+  double* nodes_d = nullptr;
+  if ((rc = upload(h, &nodes_d, geom->nodes, (size_t)t.M * d))) return rc;
+  di.nodes = nodes_d;
+  int32_t* vtri_d = nullptr;
+  if (d == 3) {
+    std::vector<int32_t> ids, cnt, vtri;
+    if ((rc = host_patches(geom, ids, cnt, vtri))) return rc;
+    int32_t *ids_d = nullptr, *cnt_d = nullptr;
+    double* ct_d = nullptr;
+    if ((rc = upload(h, &ids_d, ids.data(), ids.size()))) return rc;
+    if ((rc = upload(h, &cnt_d, cnt.data(), cnt.size()))) return rc;
+    if ((rc = upload(h, &vtri_d, vtri.data(), vtri.size()))) return rc;
+    if ((rc = upload(h, &ct_d, geom->cube_t, (size_t)geom->cube_n + 1))) return rc;
+    di.patch_ids = ids_d;
+    di.patch_cnt = cnt_d;
+    di.cube_t = ct_d;
+  } else {
+    std::vector<double> gcol;
+    host_spline_column(t.M, gcol);
+    if ((rc = upload(h, &t.spline_G, gcol.data(), gcol.size()))) return rc;
+  }
+  if ((rc = dalloc(h, &t.c_cnt, (size_t)t.n_int))) return rc;
+  if ((rc = dalloc(h, &t.c_pid, (size_t)t.n_int * PATCH_MAX))) return rc;
+  if ((rc = dalloc(h, &t.c_wlo, (size_t)t.n_int * PATCH_MAX))) return rc;
+  if ((rc = dalloc(h, &t.c_whi, (size_t)t.n_int * PATCH_MAX))) return rc;
+  if (t.n_int > 0) k_crossing_rows<<<(t.n_int + 63) / 64, 64, 0, st>>>(gp, gr, di, t.inside, t, err);
+  KFBI_CHECK_LAUNCH();
+  if ((rc = dalloc(h, &t.n_base, (size_t)t.M))) return rc;
+  if ((rc = dalloc(h, &t.n_sign, (size_t)t.M * d))) return rc;
+  if ((rc = dalloc(h, &t.n_center, (size_t)t.M * d))) return rc;
+  if ((rc = dalloc(h, &t.n_wn, (size_t)t.M * t.P))) return rc;
+  if ((rc = dalloc(h, &t.n_dcnt, (size_t)t.M))) return rc;
+  if ((rc = dalloc(h, &t.n_dpid, (size_t)t.M * (PATCH_MAX + 1)))) return rc;
+  if ((rc = dalloc(h, &t.n_dw, (size_t)t.M * (PATCH_MAX + 1)))) return rc;
+  {
+    double* AB = nullptr;
+    KFBI_CUDA(cudaMalloc(&AB, sizeof(double) * 4 * (size_t)t.M));
+    k_node_stencil<<<(t.M + 63) / 64, 64, 0, st>>>(gp, gr, di, t.inside, AB, t, err);
+    int herr = 0;
+    KFBI_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KFBI_CUDA(cudaStreamSynchronize(st));
+    if (!(herr & DEVERR_GEOMETRY))
+      k_node_density<<<(t.M + 63) / 64, 64, 0, st>>>(gp, gr, di, vtri_d, AB, t, err);
+    KFBI_CUDA(cudaStreamSynchronize(st));
+    cudaFree(AB);
+    KFBI_CHECK_LAUNCH();
+  }
+
+  // transform tables
+  {
+    std::vector<double> mu(N), tw(4 * (size_t)N);
+    for (int k = 0; k < N; ++k) {
+      const double s = std::sin(M_PI * k / (2.0 * N));
+      mu[k] = -(4.0 / (gr.h * gr.h)) * s * s;
+    }
+    for (int j = 0; j < 2 * N; ++j) {
+      tw[2 * j] = std::cos(M_PI * j / N);
+      tw[2 * j + 1] = std::sin(M_PI * j / N);
+    }
+    std::vector<float> mu32(mu.begin(), mu.end()), tw32(tw.begin(), tw.end());
+    if ((rc = upload(h, &t.mu, mu.data(), mu.size()))) return rc;
+    if ((rc = upload(h, &t.tw64, tw.data(), tw.size()))) return rc;
+    if ((rc = upload(h, &t.mu32, mu32.data(), mu32.size()))) return rc;
+    if ((rc = upload(h, &t.tw32, tw32.data(), tw32.size()))) return rc;
+  }
+  // inside count
+  {
+    std::vector<uint8_t> ins((size_t)total);
+    KFBI_CUDA(cudaMemcpyAsync(ins.data(), t.inside, (size_t)total, cudaMemcpyDeviceToHost, st));
+    int herr = 0;
+    KFBI_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KFBI_CUDA(cudaStreamSynchronize(st));
+    int64_t cnt = 0;
+    for (auto v : ins) cnt += v;
+    t.n_inside = (int)cnt;
+    if (herr & DEVERR_GEOMETRY) {
+      set_error("geometry: the domain touches the box boundary, a grid edge crosses two surfaces, or an "
+                "interpolation stencil leaves the interior grid");
+      return KFBI_ERR_GEOMETRY;
+    }
+    if (herr & DEVERR_SINGULAR) {
+      set_error("singular local system in the surface fit or the Taylor stencil");
+      return KFBI_ERR_GEOMETRY;
+    }
+  }
+  return KFBI_OK;
+}
+
+}  // namespace kfbi

@@ -1,0 +1,275 @@
+"""Python binding of the KFBI C ABI (include/kfbi.h): argument marshalling only.
+
+Every numeric step runs in the CUDA kernels of libkfbi.so; this module only
+converts torch CUDA tensors and numpy geometry arrays into the C structs and
+pointers the library expects.  Importing it without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libkfbi.so")
+
+OK, ERR_ARG, ERR_GEOMETRY, ERR_NOT_CONVERGED, ERR_NAN, ERR_CUDA, ERR_OOM, ERR_NEWTON = range(8)
+ELLIPSE2, ELLIPSOID3, STAR3, SHELL3 = 1, 2, 3, 4
+FP64, MIXED, MIXED_LEARNED = 0, 1, 2
+GMRES, RICHARDSON = 0, 1
+MAX_COMP = 4
+
+
+class Geometry(C.Structure):
+    _fields_ = [("dim", C.c_int), ("kind", C.c_int), ("params", C.c_double * 16), ("n_nodes", C.c_int),
+                ("nodes", C.POINTER(C.c_double)), ("n_tri", C.c_int), ("tri", C.POINTER(C.c_int32)),
+                ("cube_n", C.c_int), ("cube_t", C.POINTER(C.c_double)), ("n_comp", C.c_int),
+                ("comp_map", C.c_int * MAX_COMP), ("comp_axes", (C.c_double * 3) * MAX_COMP),
+                ("comp_vert_offset", C.c_int * MAX_COMP), ("comp_n_vert", C.c_int * MAX_COMP),
+                ("comp_tri_offset", C.c_int * MAX_COMP)]
+
+
+class GridStruct(C.Structure):
+    _fields_ = [("dim", C.c_int), ("N", C.c_int), ("lo", C.c_double), ("hi", C.c_double)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("solver", C.c_int), ("tol", C.c_double), ("restart", C.c_int),
+                ("max_iter", C.c_int), ("gamma", C.c_double), ("stream", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("rel_res", C.c_double), ("true_rel_res", C.c_double),
+                ("init_rel_res", C.c_double), ("ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class FHNStruct(C.Structure):
+    _fields_ = [("H", C.c_double), ("theta", C.c_double), ("alpha", C.c_double), ("zeta", C.c_double),
+                ("Cm", C.c_double), ("beta", C.c_double)]
+
+
+class Info(C.Structure):
+    _fields_ = [("M", C.c_int), ("n_irregular", C.c_int), ("n_crossings", C.c_int), ("n_inside", C.c_int),
+                ("device_bytes", C.c_size_t)]
+
+
+EXPORTS = [
+    "kfbi_last_error", "kfbi_create", "kfbi_destroy", "kfbi_query", "kfbi_set_opts", "kfbi_solve_neumann",
+    "bidomain_step", "kfbi_export_setup", "kfbi_box_solve", "kfbi_correction", "kfbi_interface_limit",
+    "kfbi_apply_A", "kfbi_rhs_g", "kfbi_solve_bie", "kfbi_react_fe", "kfbi_react_be", "kfbi_export_tables",
+]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libkfbi.so (raises OSError when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"libkfbi.so not built ({path}); run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
+    lib.kfbi_last_error.restype = C.c_char_p
+    lib.kfbi_create.argtypes = [C.POINTER(Geometry), C.POINTER(GridStruct), C.c_double, C.c_double, C.c_double,
+                                C.POINTER(Opts), C.POINTER(vp)]
+    lib.kfbi_destroy.argtypes = [vp]
+    lib.kfbi_destroy.restype = None
+    lib.kfbi_query.argtypes = [vp, C.POINTER(Info)]
+    lib.kfbi_set_opts.argtypes = [vp, C.POINTER(Opts)]
+    lib.kfbi_solve_neumann.argtypes = [vp, C.c_double, vp, vp, vp, vp, C.POINTER(Stats)]
+    lib.bidomain_step.argtypes = [vp, C.POINTER(FHNStruct), vp, vp, vp, ip, C.POINTER(Stats)]
+    lib.kfbi_export_setup.argtypes = [vp] + [vp] * 7
+    lib.kfbi_export_tables.argtypes = [vp] + [vp] * 8
+    lib.kfbi_box_solve.argtypes = [vp, ip, C.c_double, vp, vp]
+    lib.kfbi_correction.argtypes = [vp, vp, vp]
+    lib.kfbi_interface_limit.argtypes = [vp, vp, vp, vp]
+    lib.kfbi_apply_A.argtypes = [vp, ip, C.c_double, vp, vp]
+    lib.kfbi_rhs_g.argtypes = [vp, C.c_double, vp, vp, vp]
+    lib.kfbi_solve_bie.argtypes = [vp, C.c_double, vp, vp, C.POINTER(Stats)]
+    lib.kfbi_react_fe.argtypes = [C.POINTER(FHNStruct), C.c_double, vp, vp, C.c_int64, vp]
+    lib.kfbi_react_be.argtypes = [C.POINTER(FHNStruct), C.c_double, vp, vp, C.c_int64, vp]
+    for name in EXPORTS:
+        if name != "kfbi_last_error" and name != "kfbi_destroy":
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+class KFBIError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"KFBI error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc, allow=()):
+    if rc != OK and rc not in allow:
+        raise KFBIError(rc, load().kfbi_last_error().decode())
+    return rc
+
+
+def _ptr(t, dtype_name="float64"):
+    """Device pointer of a contiguous CUDA tensor (None passes NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous() or str(t.dtype) != "torch." + dtype_name:
+        raise ValueError(f"expected a contiguous CUDA {dtype_name} tensor, got {t.dtype} on {t.device}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def fhn_struct(p) -> FHNStruct:
+    return FHNStruct(p.H, p.theta, p.alpha, p.zeta, p.Cm, p.beta)
+
+
+class KFBI:
+    """Handle over one geometry, grid and conductivity/time-step setting.
+
+    geom: any object with dim, kind, params, nodes [M, dim] and, in 3-D, tri,
+    cube_n, cube_t and components (map_type, axes, vert_offset, n_vert,
+    tri_offset) -- e.g. kfbi_workloads.geometry.Geometry."""
+
+    def __init__(self, geom, grid, sigma_i=1.0, sigma_e=2.0, dt=0.05, precision=FP64, solver=GMRES, tol=1e-10,
+                 restart=50, max_iter=500, gamma=0.8, lo=-1.0, hi=1.0):
+        lib = load()
+        self._keep = []
+        g = Geometry()
+        g.dim, g.kind = int(geom.dim), int(geom.kind)
+        for i, v in enumerate(np.asarray(geom.params, dtype=np.float64)[:16]):
+            g.params[i] = float(v)
+        nodes = np.ascontiguousarray(geom.nodes, dtype=np.float64)
+        self._keep.append(nodes)
+        g.n_nodes = nodes.shape[0]
+        g.nodes = nodes.ctypes.data_as(C.POINTER(C.c_double))
+        if g.dim == 3:
+            tri = np.ascontiguousarray(geom.tri, dtype=np.int32)
+            ct = np.ascontiguousarray(geom.cube_t, dtype=np.float64)
+            self._keep += [tri, ct]
+            g.n_tri = tri.shape[0]
+            g.tri = tri.ctypes.data_as(C.POINTER(C.c_int32))
+            g.cube_n = int(geom.cube_n)
+            g.cube_t = ct.ctypes.data_as(C.POINTER(C.c_double))
+            g.n_comp = len(geom.components)
+            for c, comp in enumerate(geom.components):
+                g.comp_map[c] = int(comp.map_type)
+                for k in range(3):
+                    g.comp_axes[c][k] = float(comp.axes[k])
+                g.comp_vert_offset[c] = int(comp.vert_offset)
+                g.comp_n_vert[c] = int(comp.n_vert)
+                g.comp_tri_offset[c] = int(comp.tri_offset)
+        else:
+            g.n_comp = 1
+        self.dim, self.N = int(grid.dim), int(grid.N)
+        gs = GridStruct(self.dim, self.N, float(getattr(grid, "lo", lo)), float(getattr(grid, "hi", hi)))
+        self.opts = Opts(precision, solver, tol, restart, max_iter, gamma, _stream())
+        h = C.c_void_p()
+        _check(lib.kfbi_create(C.byref(g), C.byref(gs), sigma_i, sigma_e, dt, C.byref(self.opts), C.byref(h)))
+        self._h = h
+        self.M = g.n_nodes
+        info = Info()
+        _check(lib.kfbi_query(h, C.byref(info)))
+        self.info = {k: getattr(info, k) for k, _ in info._fields_}
+
+    # ------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            load().kfbi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_opts(self, **kw):
+        for k, v in kw.items():
+            setattr(self.opts, k, v)
+        self.opts.stream = _stream()
+        _check(load().kfbi_set_opts(self._h, C.byref(self.opts)))
+
+    @property
+    def grid_shape(self):
+        return (self.N - 1,) * self.dim
+
+    def export_setup(self):
+        n1 = self.N - 1
+        i = self.info
+        inside = np.empty((n1,) * self.dim, dtype=np.uint8)
+        irr = np.empty(i["n_irregular"], dtype=np.int32)
+        ax = np.empty(i["n_crossings"], dtype=np.int32)
+        lo = np.empty(i["n_crossings"], dtype=np.int32)
+        z = np.empty(i["n_crossings"], dtype=np.float64)
+        cen = np.empty((self.M, self.dim), dtype=np.int32)
+        sg = np.empty((self.M, self.dim), dtype=np.int8)
+        p = lambda a: C.c_void_p(a.ctypes.data)  # noqa: E731
+        _check(load().kfbi_export_setup(self._h, p(inside), p(irr), p(ax), p(lo), p(z), p(cen), p(sg)))
+        return {"inside": inside.astype(bool), "irregular": irr, "axis": ax, "lo": lo, "z": z, "center": cen,
+                "sign": sg}
+
+    def export_tables(self):
+        M, NI, P = self.M, self.info["n_crossings"], 6 if self.dim == 2 else 10
+        out = {"node_wn": np.empty((M, P)), "node_cnt": np.empty(M, np.int32), "node_pid": np.empty((M, 17), np.int32),
+               "node_w": np.empty((M, 17)), "cross_cnt": np.empty(NI, np.int32),
+               "cross_pid": np.empty((NI, 16), np.int32), "cross_wlo": np.empty((NI, 16)),
+               "cross_whi": np.empty((NI, 16))}
+        p = lambda a: C.c_void_p(a.ctypes.data)  # noqa: E731
+        _check(load().kfbi_export_tables(self._h, *[p(out[k]) for k in out]))
+        return out
+
+    def box_solve(self, r, v, lam, precision=FP64):
+        self.set_opts()
+        _check(load().kfbi_box_solve(self._h, precision, lam, _ptr(r), _ptr(v)))
+
+    def correction(self, psi, rhs):
+        self.set_opts()
+        _check(load().kfbi_correction(self._h, _ptr(psi), _ptr(rhs)))
+
+    def interface_limit(self, v, psi, out):
+        self.set_opts()
+        _check(load().kfbi_interface_limit(self._h, _ptr(v), _ptr(psi), _ptr(out)))
+
+    def apply_A(self, psi, out, lam, precision=FP64):
+        self.set_opts()
+        _check(load().kfbi_apply_A(self._h, precision, lam, _ptr(psi), _ptr(out)))
+
+    def rhs_g(self, f, gN, g, lam):
+        self.set_opts()
+        _check(load().kfbi_rhs_g(self._h, lam, _ptr(f), _ptr(gN), _ptr(g)))
+
+    def solve_bie(self, g, psi, lam, **opts):
+        self.set_opts(**opts)
+        st = Stats()
+        _check(load().kfbi_solve_bie(self._h, lam, _ptr(g), _ptr(psi), C.byref(st)), allow=(ERR_NOT_CONVERGED,))
+        return st.as_dict()
+
+    def solve_neumann(self, f, gN, u, psi, lam, **opts):
+        self.set_opts(**opts)
+        st = Stats()
+        _check(load().kfbi_solve_neumann(self._h, lam, _ptr(f), _ptr(gN), _ptr(u), _ptr(psi), C.byref(st)),
+               allow=(ERR_NOT_CONVERGED,))
+        return st.as_dict()
+
+    def bidomain_step(self, fhn, V, w, ue=None, nsteps=1, **opts):
+        self.set_opts(**opts)
+        stats = (Stats * max(1, nsteps))()
+        _check(load().bidomain_step(self._h, C.byref(fhn_struct(fhn)), _ptr(V), _ptr(w), _ptr(ue), nsteps, stats),
+               allow=(ERR_NOT_CONVERGED,))
+        return [stats[i].as_dict() for i in range(nsteps)]
+
+
+def react_fe(fhn, k, V, w):
+    _check(load().kfbi_react_fe(C.byref(fhn_struct(fhn)), k, _ptr(V), _ptr(w), V.numel(), _stream()))
+
+
+def react_be(fhn, k, V, w):
+    _check(load().kfbi_react_be(C.byref(fhn_struct(fhn)), k, _ptr(V), _ptr(w), V.numel(), _stream()))

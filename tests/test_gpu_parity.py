@@ -1,0 +1,201 @@
+"""GPU parity: every step of the hot path, called through the C ABI, against
+the CPU oracle on the same seeded inputs.
+
+Bars: classification, irregular-node lists, crossings and interface-to-cell
+indices bit-exact; float64 fields within 1e-10 relative L-infinity (the
+float64 transforms reach ~1e-14); float32 box solves within 2e-5."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from kfbi_workloads import configs as C, geometry as G  # noqa: E402
+from oracle import boxsolve, krylov, reaction  # noqa: E402
+from oracle.kfbi import KFBI as OK  # noqa: E402
+from oracle.bidomain import Bidomain, extracellular  # noqa: E402
+from paper_2104_05024_gb300 import kfbi as K  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+TOL64 = 1e-10
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def cuda(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+CASES = {
+    "ellipse128": lambda: (G.ellipse_config0(256), C.Grid(2, 128)),
+    "ellipse64": lambda: (G.ellipse_config0(128), C.Grid(2, 64)),
+    "star32": lambda: (G.star_config1(C.surface_res(32)), C.Grid(3, 32)),
+    "star64": lambda: (G.star_config1(C.surface_res(64)), C.Grid(3, 64)),
+    "shell64": lambda: (G.shell_config2(C.surface_res(64)), C.Grid(3, 64)),
+    "sphere32": lambda: (G.sphere3(0.6, 8), C.Grid(3, 32)),
+}
+
+_cache = {}
+
+
+def pair(name):
+    if name not in _cache:
+        geom, grid = CASES[name]()
+        _cache[name] = (geom, grid, OK(geom, grid), K.KFBI(geom, grid, tol=1e-12))
+    return _cache[name]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_setup_bit_exact(name):
+    geom, grid, o, g = pair(name)
+    s = g.export_setup()
+    assert np.array_equal(s["inside"], o.inside)
+    assert np.array_equal(s["irregular"], o.irregular.astype(np.int32))
+    assert np.array_equal(s["axis"], o.ints["axis"].astype(np.int32))
+    assert np.array_equal(s["lo"], o.ints["lo"].astype(np.int32))
+    assert np.array_equal(s["z"].view(np.uint64), o.ints["z"].view(np.uint64))
+    assert np.array_equal(s["center"], o.center.astype(np.int32))
+    assert np.array_equal(s["sign"], o.sign.astype(np.int8))
+    assert g.info["n_inside"] == int(o.inside.sum())
+
+
+@pytest.mark.parametrize("name,lam", [("ellipse128", 60.0), ("star32", 40.0), ("shell64", 60.0), ("ellipse64", 0.0)])
+def test_box_solve(name, lam):
+    geom, grid, o, g = pair(name)
+    r = np.random.default_rng(7).standard_normal(grid.shape)
+    ref = boxsolve.solve(r, lam, grid)
+    v = torch.empty(grid.shape, dtype=torch.float64, device=DEV)
+    g.box_solve(cuda(r), v, lam, precision=K.FP64)
+    assert rel(v.cpu().numpy(), ref) < 1e-12
+    g.box_solve(cuda(r), v, lam, precision=K.MIXED)
+    assert rel(v.cpu().numpy(), ref) < 2e-5
+
+
+@pytest.mark.parametrize("N", [8, 16, 128])
+def test_box_solve_sizes(N):
+    # geometry-free sizes: small tiles (one column tile) and the 128^3 pipeline
+    geom = G.sphere3(0.3, 4) if N >= 16 else G.sphere3(0.45, 2)
+    grid = C.Grid(3, N)
+    if N == 8:
+        pytest.skip("8^3 grid cannot hold an interface two cells from the box")
+    g = K.KFBI(geom, grid)
+    r = np.random.default_rng(N).standard_normal(grid.shape)
+    v = torch.empty(grid.shape, dtype=torch.float64, device=DEV)
+    g.box_solve(cuda(r), v, 40.0)
+    assert rel(v.cpu().numpy(), boxsolve.solve(r, 40.0, grid)) < 1e-12
+
+
+def _smooth_density(geom):
+    X = geom.nodes
+    return 1.0 + 0.5 * X[:, 0] - 0.3 * X[:, 1] ** 2 + (0.2 * X[:, 2] if geom.dim == 3 else 0.0)
+
+
+@pytest.mark.parametrize("name", ["ellipse128", "star32", "shell64"])
+def test_correction(name):
+    geom, grid, o, g = pair(name)
+    psi = _smooth_density(geom)
+    ref = o.correction_from_psi(psi)
+    out = torch.empty(grid.shape, dtype=torch.float64, device=DEV)
+    g.correction(cuda(psi), out)
+    assert rel(out.cpu().numpy(), ref) < TOL64
+
+
+@pytest.mark.parametrize("name", ["ellipse128", "star32", "shell64"])
+def test_interface_limit(name):
+    geom, grid, o, g = pair(name)
+    X = np.stack(np.broadcast_arrays(*grid.coords()), -1)
+    v = np.cos(2 * X[..., 0]) * np.exp(0.5 * X[..., 1]) + (X[..., 2] ** 2 if grid.dim == 3 else 0)
+    psi = _smooth_density(geom)
+    _, (jg, jH) = o.jumps(psi)
+    ref = o.interp(v, (np.zeros(geom.M), jg, jH))
+    out = torch.empty(geom.M, dtype=torch.float64, device=DEV)
+    g.interface_limit(cuda(v), cuda(psi), out)
+    assert rel(out.cpu().numpy(), ref) < TOL64
+    g.interface_limit(cuda(v), None, out)
+    assert rel(out.cpu().numpy(), o.interp(v)) < TOL64
+
+
+@pytest.mark.parametrize("name,lam", [("ellipse128", 60.0), ("star32", 40.0), ("shell64", 60.0)])
+def test_apply_A_and_rhs(name, lam):
+    geom, grid, o, g = pair(name)
+    psi = _smooth_density(geom)
+    out = torch.empty(geom.M, dtype=torch.float64, device=DEV)
+    g.apply_A(cuda(psi), out, lam)
+    ref = o.apply_A(psi, lam)
+    assert rel(out.cpu().numpy(), ref) < TOL64
+    g.apply_A(cuda(psi), out, lam, precision=K.MIXED)
+    assert rel(out.cpu().numpy(), ref) < 1e-4
+    f, u, gN = C.manufactured(geom, grid, lam)
+    gd = torch.empty(geom.M, dtype=torch.float64, device=DEV)
+    g.rhs_g(cuda(f), cuda(gN), gd, lam)
+    assert rel(gd.cpu().numpy(), o.rhs_g(o.volume(f, lam), gN)) < TOL64
+
+
+@pytest.mark.parametrize("name,lam", [("ellipse64", 60.0), ("star32", 40.0)])
+def test_gmres_fixed_iterations(name, lam):
+    geom, grid, o, g = pair(name)
+    rng = np.random.default_rng(3)
+    gv = rng.standard_normal(geom.M)
+    for its in (1, 4, 7):
+        x, info = krylov.gmres(lambda v: o.apply_A(v, lam), gv, np.zeros(geom.M), 0.0, max_iter=its)
+        psi = torch.zeros(geom.M, dtype=torch.float64, device=DEV)
+        st = g.solve_bie(cuda(gv), psi, lam, tol=0.0, max_iter=its)
+        assert st["iters"] == its
+        assert rel(psi.cpu().numpy(), x) < TOL64
+        assert abs(st["rel_res"] - info["rel_res"]) < 1e-9 * max(info["rel_res"], 1e-3)
+
+
+@pytest.mark.parametrize("name,lam", [("ellipse128", 60.0), ("star64", 40.0), ("shell64", 60.0), ("sphere32", 40.0)])
+def test_solve_neumann_manufactured(name, lam):
+    geom, grid, o, g = pair(name)
+    f, u_ex, gN = C.manufactured(geom, grid, lam)
+    u_ref, psi_ref, info = o.solve_neumann(f, gN, lam, tol=1e-12)
+    u = torch.empty(grid.shape, dtype=torch.float64, device=DEV)
+    psi = torch.zeros(geom.M, dtype=torch.float64, device=DEV)
+    st = g.solve_neumann(cuda(f), cuda(gN), u, psi, lam, tol=1e-12, max_iter=500)
+    assert abs(st["iters"] - info["iters"]) <= 1
+    assert st["true_rel_res"] < 1e-11
+    assert rel(u.cpu().numpy(), u_ref) < TOL64
+    assert rel(psi.cpu().numpy(), psi_ref) < TOL64
+
+
+def test_reaction_half_steps():
+    rng = np.random.default_rng(11)
+    V0 = rng.uniform(-0.3, 1.2, 100_003)
+    q0 = rng.uniform(-0.1, 0.3, V0.size)
+    for fhn, k in ((C.FHN_CONFIG, 0.025), (C.FHN_PAPER, 0.002)):
+        V, q = cuda(V0), cuda(q0)
+        K.react_fe(fhn, k, V, q)
+        Vr, qr = reaction.forward_euler(V0, q0, k, fhn)
+        assert rel(V.cpu().numpy(), Vr) < 1e-15 and rel(q.cpu().numpy(), qr) < 1e-15
+        V, q = cuda(V0), cuda(q0)
+        K.react_be(fhn, k, V, q)
+        Vr, qr, ok = reaction.backward_euler(V0, q0, k, fhn)
+        assert ok.all()
+        assert rel(V.cpu().numpy(), Vr) < 1e-12 and rel(q.cpu().numpy(), qr) < 1e-12
+
+
+def test_strang_config0_short():
+    """Config 0 (2-D ellipse, 128^2) for 5 Strang steps against the oracle,
+    with a 1e-12 GMRES tolerance on both sides."""
+    geom, grid, cfg, V0, w0 = C.config0()
+    cfg = C.StrangConfig(sigma_i=1.0, sigma_e=2.0, dt=0.05, steps=5, tol=1e-12)
+    lam = C.helmholtz_lambda(cfg)
+    bd = Bidomain(geom, grid, cfg, C.FHN_CONFIG, lam)
+    V, w = V0.copy(), w0.copy()
+    for _ in range(cfg.steps):
+        V, w, _ = bd.step(V, w)
+    ue_ref = extracellular(V, bd.k.inside, cfg.sigma_i, cfg.sigma_e)
+    h = K.KFBI(geom, grid, sigma_i=1.0, sigma_e=2.0, dt=0.05, tol=1e-12)
+    Vd, wd, ued = cuda(V0), cuda(w0), torch.empty(grid.shape, dtype=torch.float64, device=DEV)
+    stats = h.bidomain_step(C.FHN_CONFIG, Vd, wd, ued, nsteps=cfg.steps, tol=1e-12)
+    assert all(s["rel_res"] <= 1e-12 for s in stats)
+    assert rel(Vd.cpu().numpy(), V) < TOL64
+    assert rel(wd.cpu().numpy(), w) < TOL64
+    assert rel(ued.cpu().numpy(), ue_ref) < TOL64
