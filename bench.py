@@ -1,0 +1,303 @@
+#!/usr/bin/env python
+"""Benchmark: Strang steps per second of the FitzHugh-Nagumo bidomain model on
+the 256^3 prolate-shell workload, each diffusion solve converged to a 1e-8
+GMRES residual, through the KFBI library's C ABI on one GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl kfbi|reference]
+
+One JSON line on rank 0.  Multi-GPU runs are independent replicas (one
+stimulus location per rank, no data-path collective); `value` sums the ranks.
+The reference arm times the CPU oracle on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Strang steps/s at 256^3 to 1e-8 residual (mixed/learned vs FP64); FFT HBM GB/s"
+UNIT = "steps/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# FP64 arithmetic peak of a GB300 from its unit counts and clock: 152 SMs x
+# 2 FP64 FMA/clk/SM (4 flop) x 2.07 GHz, the 1.25 TFLOP/s class figure.
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(N, rank):
+    from kfbi_workloads import configs as C
+    geom, grid, cfg, V0, w0 = C.config2(N=N)
+    if rank > 0:
+        c = C.midwall_centers([rank - 1])[0]
+        V0 = C.ball_stimulus(grid, c, 0.1)
+    return geom, grid, cfg, V0, w0
+
+
+# ----------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import torch
+
+    import paper_2104_05024_gb300.kfbi as K
+    from kfbi_workloads import configs as C
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    precision = {"fp64": K.FP64, "mixed": K.MIXED, "learned": K.MIXED_LEARNED}[args.precision]
+
+    geom, grid, cfg, V0, w0 = workload(args.N, rank)
+    t0 = time.time()
+    h = K.KFBI(geom, grid, sigma_i=cfg.sigma_i, sigma_e=cfg.sigma_e, dt=cfg.dt, tol=cfg.tol, precision=precision,
+               restart=50, max_iter=400)
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+    fhn = C.FHN_CONFIG
+    V = torch.tensor(V0, device=dev)
+    w = torch.tensor(w0, device=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        h.bidomain_step(fhn, V, w, None, nsteps=1)
+    barrier()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = K.launch_count()
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(stream)
+        stats = h.bidomain_step(fhn, V, w, None, nsteps=args.steps)
+        e1.record(stream)
+        barrier()
+    launches = K.launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    ms_step = ms / args.steps
+    if dist is not None:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    iters = [s["iters"] for s in stats]
+
+    # ---- dominant kernel: one pass of the transform, timed alone with events
+    pk, kind = peaks()
+    reps = 20
+    pass_ms = {}
+    prec_pass = K.FP64 if precision == K.FP64 else K.MIXED
+    lam = C.helmholtz_lambda(cfg)
+    for p in (0, 1, 2, 3):
+        for _ in range(3):
+            h.transform_pass(p, lam, prec_pass)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            h.transform_pass(p, lam, prec_pass)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pass_ms[p] = a.elapsed_time(b) / reps
+    N = args.N
+    lines = (N - 1) * (N - 1)
+    fl_dst = 2.5 * N * np.log2(N)            # real-FFT flop count of one DST-I line
+    z_flops = 2 * lines * fl_dst + 3.0 * (N - 1) ** 3
+    z_s = pass_ms[2] / 1e3
+    esize = 8 if prec_pass == K.FP64 else 4
+    z_bytes = 2.0 * N ** 3 * esize           # read + write of the padded grid
+    if prec_pass == K.FP64:
+        roof = {"kernel": "k_strided<double,256,SOLVE> (z pass: DST, divide, DST)", "bound": "alu",
+                "achieved": z_flops / z_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz"}
+    else:
+        roof = {"kernel": "k_strided<float,256,SOLVE> (z pass: DST, divide, DST)", "bound": "hbm",
+                "achieved": z_bytes / z_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "peak_source": kind}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["pass_ms"] = {k: round(v, 4) for k, v in pass_ms.items()}
+    roof["hbm_gbs_per_pass"] = {k: round(2.0 * N ** 3 * esize / (v / 1e3) / 1e9, 1) for k, v in pass_ms.items()}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e_steps = max(1, min(args.steps, 5))
+    Vh = torch.empty(V.shape, dtype=torch.float64, pin_memory=True)
+    wh = torch.empty(w.shape, dtype=torch.float64, pin_memory=True)
+    Vh.copy_(V)
+    wh.copy_(w)
+    barrier()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(e2e_steps):
+        V.copy_(Vh, non_blocking=True)
+        w.copy_(wh, non_blocking=True)
+        h.bidomain_step(fhn, V, w, None, nsteps=1)
+        Vh.copy_(V, non_blocking=True)
+        wh.copy_(w, non_blocking=True)
+    b.record(stream)
+    barrier()
+    e2e_ms = a.elapsed_time(b) / e2e_steps
+    nbytes = V.numel() * 8 * 2
+
+    result = {
+        "metric": METRIC, "value": world * 1000.0 / ms_step, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if precision == K.FP64 else "f32+f64", "data": "synthetic",
+        "config": {"workload": f"config 2: FHN bidomain, prolate shell, {N}^3 grid, dt 0.05, GMRES tol 1e-8",
+                   "N": N, "M": geom.M, "precision": args.precision, "parallelism": "replicas" if world > 1 else "1gpu",
+                   "l2": "inputs larger than L2 (V and w: %.0f MB each)" % (V.numel() * 8 / 1e6),
+                   "setup_s": round(setup_s, 2), "n_irregular": h.info["n_irregular"],
+                   "n_crossings": h.info["n_crossings"]},
+        "gmres_iters_per_step": float(np.mean(iters)),
+        "roofline": roof,
+        "clocks": clk.summary(),
+        "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes},
+        "gpu_launches": int(launches),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(args.N, steps=1)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    h.close()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+# -------------------------------------------------------------- CPU oracle
+
+def cpu_baseline(N, steps=1):
+    """Oracle Strang steps on the host cores (setup excluded from the time)."""
+    from kfbi_workloads import configs as C
+    from oracle.bidomain import Bidomain
+    geom, grid, cfg, V0, w0 = workload(N, 0)
+    lam = C.helmholtz_lambda(cfg)
+    t0 = time.time()
+    bd = Bidomain(geom, grid, cfg, C.FHN_CONFIG, lam)
+    setup = time.time() - t0
+    V, w = V0.copy(), w0.copy()
+    t0 = time.time()
+    for _ in range(steps):
+        V, w, _ = bd.step(V, w)
+    dt = time.time() - t0
+    return {"value": steps / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{steps} Strang step(s) of the {N}^3 workload after a {setup:.0f} s oracle setup "
+                      "(numpy/scipy FP64, scipy.fft workers = all cores)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps = max(1, min(args.steps, 2))
+    cb = cpu_baseline(args.N, steps=steps)
+    cb["sample"] += f"; timed {steps} of the requested {args.steps} steps"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": 0, "steps": steps,
+        "warmup": 0, "ms_per_step": 1000.0 / cb["value"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"config 2: FHN bidomain, prolate shell, {args.N}^3 grid, dt 0.05, GMRES tol 1e-8",
+                   "N": args.N, "precision": "fp64"},
+        "cpu_baseline": cb,
+        "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="kfbi", choices=["kfbi", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "learned"])
+    ap.add_argument("--N", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

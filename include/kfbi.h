@@ -218,6 +218,17 @@ int kfbi_rhs_g(kfbi_handle* h, double lambda, const double* f_dev, const double*
  * applications).                                                             */
 int kfbi_solve_bie(kfbi_handle* h, double lambda, const double* g_dev, double* psi_dev, kfbi_stats* stats);
 
+/* One pass of the box solver on the handle's padded work grid, for timing
+ * the transform kernels in isolation: pass 0 = x forward (no right-hand
+ * side), 1 = y forward, 2 = z solve (forward, spectral divide, inverse; the
+ * y solve in 2-D), 3 = x inverse.  precision KFBI_FP64 or KFBI_MIXED.  The
+ * grid content is arbitrary afterwards.                                      */
+int kfbi_transform_pass(kfbi_handle* h, int precision, int pass, double lambda);
+
+/* Number of kernels this library has launched in the process so far
+ * (instrumentation; every launch site adds its kernel count).                */
+int64_t kfbi_launch_count(void);
+
 /* Pointwise FitzHugh-Nagumo half steps (Section 3, Eqs. ode1/ode2) over n
  * values: forward Euler (k = dt/2) and backward Euler with Newton.  The
  * backward step returns KFBI_ERR_NEWTON if any node hit the iteration cap.    */

@@ -17,6 +17,7 @@
 namespace kfbi {
 
 static thread_local char g_err[1024] = "";
+std::atomic<long long> g_launches{0};
 
 void set_error(const char* fmt, ...) {
   va_list ap;
@@ -555,6 +556,17 @@ int bidomain_step(kfbi_handle* h, const kfbi_fhn* p, double* V_dev, double* w_de
   }
   return final_rc;
 }
+
+int kfbi_transform_pass(kfbi_handle* h, int precision, int pass, double lambda) {
+  if (int rc = check_handle(h)) return rc;
+  if (pass < 0 || pass > 3) {
+    set_error("pass must be 0..3");
+    return KFBI_ERR_ARG;
+  }
+  return transform_pass(h, precision, pass, lambda);
+}
+
+int64_t kfbi_launch_count(void) { return (int64_t)g_launches.load(); }
 
 int kfbi_react_fe(const kfbi_fhn* p, double k, double* V_dev, double* w_dev, int64_t n, void* stream) {
   if (!p || !V_dev || !w_dev || n < 0) {

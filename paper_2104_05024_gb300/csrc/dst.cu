@@ -443,6 +443,50 @@ int run_solve(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1, const 
     if ((rc = prep(k_xinv<T, N, 2>, smem))) return rc;
     k_xinv<T, N, 2><<<grid, NT, smem, st>>>(work, true, sa.out_user, sa.aux, sa.beta, sa.gamma, tw);
   }
+  KFBI_CHECK_LAUNCH_N(dim == 3 ? 5 : 3);
+  return KFBI_OK;
+}
+
+// one pass of the solver on the padded work grid (timing of single kernels)
+template <typename T, int N>
+int run_pass(kfbi_handle* h, int pass, double lambda, T* work, const T* mu1, const T* tw) {
+  using C = Cfg<T, N>;
+  constexpr int W = C::W;
+  const size_t smem = C::smem_elems * sizeof(T);
+  const int dim = h->grid.dim;
+  cudaStream_t st = h->stream;
+  const Tables& t = h->t;
+  const T lam = (T)lambda;
+  const T scale = (T)(dim == 3 ? (2.0 / N) * (2.0 / N) * (2.0 / N) : (2.0 / N) * (2.0 / N));
+  const size_t NN = (size_t)N * N;
+  dim3 grid(N / W, dim == 3 ? N - 1 : 1);
+  int rc;
+  if (dim == 3) {
+    if (pass == 0) {
+      if ((rc = prep(k_xfwd<T, N, 3>, smem))) return rc;
+      k_xfwd<T, N, 3><<<grid, NT, smem, st>>>(work, nullptr, 1.0, nullptr, t.irr, t.line_start, tw);
+    } else if (pass == 1) {
+      if ((rc = prep(k_strided<T, N, false, 3>, smem))) return rc;
+      k_strided<T, N, false, 3><<<grid, NT, smem, st>>>(work, N, NN, 1, mu1, lam, scale, tw);
+    } else if (pass == 2) {
+      if ((rc = prep(k_strided<T, N, true, 3>, smem))) return rc;
+      k_strided<T, N, true, 3><<<grid, NT, smem, st>>>(work, NN, N, 1, mu1, lam, scale, tw);
+    } else {
+      if ((rc = prep(k_xinv<T, N, 3>, smem))) return rc;
+      k_xinv<T, N, 3><<<grid, NT, smem, st>>>(work, true, nullptr, nullptr, 1.0, 0.0, tw);
+    }
+  } else {
+    if (pass == 0) {
+      if ((rc = prep(k_xfwd<T, N, 2>, smem))) return rc;
+      k_xfwd<T, N, 2><<<grid, NT, smem, st>>>(work, nullptr, 1.0, nullptr, t.irr, t.line_start, tw);
+    } else if (pass == 1 || pass == 2) {
+      if ((rc = prep(k_strided<T, N, true, 2>, smem))) return rc;
+      k_strided<T, N, true, 2><<<grid, NT, smem, st>>>(work, N, 0, 0, mu1, lam, scale, tw);
+    } else {
+      if ((rc = prep(k_xinv<T, N, 2>, smem))) return rc;
+      k_xinv<T, N, 2><<<grid, NT, smem, st>>>(work, true, nullptr, nullptr, 1.0, 0.0, tw);
+    }
+  }
   KFBI_CHECK_LAUNCH();
   return KFBI_OK;
 }
@@ -464,7 +508,29 @@ int dispatch(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1, const T
   }
 }
 
+template <typename T>
+int dispatch_pass(kfbi_handle* h, int pass, double lambda, T* work, const T* mu1, const T* tw) {
+  switch (h->grid.N) {
+    case 8: return run_pass<T, 8>(h, pass, lambda, work, mu1, tw);
+    case 16: return run_pass<T, 16>(h, pass, lambda, work, mu1, tw);
+    case 32: return run_pass<T, 32>(h, pass, lambda, work, mu1, tw);
+    case 64: return run_pass<T, 64>(h, pass, lambda, work, mu1, tw);
+    case 128: return run_pass<T, 128>(h, pass, lambda, work, mu1, tw);
+    case 256: return run_pass<T, 256>(h, pass, lambda, work, mu1, tw);
+    case 384: return run_pass<T, 384>(h, pass, lambda, work, mu1, tw);
+    case 512: return run_pass<T, 512>(h, pass, lambda, work, mu1, tw);
+    default:
+      set_error("unsupported grid size N=%d", h->grid.N);
+      return KFBI_ERR_ARG;
+  }
+}
+
 }  // namespace
+
+int transform_pass(kfbi_handle* h, int precision, int pass, double lambda) {
+  if (precision == KFBI_FP64) return dispatch_pass<double>(h, pass, lambda, h->w.grid64, h->t.mu, h->t.tw64);
+  return dispatch_pass<float>(h, pass, lambda, h->w.grid32, h->t.mu32, h->t.tw32);
+}
 
 int dst_supported(int N) {
   return N == 8 || N == 16 || N == 32 || N == 64 || N == 128 || N == 256 || N == 384 || N == 512;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -22,6 +23,10 @@ constexpr int DEVERR_SINGULAR = 4;
 
 void set_error(const char* fmt, ...);
 
+// kernels launched by this library (instrumentation for benchmarks)
+extern std::atomic<long long> g_launches;
+#define KFBI_COUNT(n) (::kfbi::g_launches.fetch_add((n), std::memory_order_relaxed))
+
 #define KFBI_CUDA(call)                                                           \
   do {                                                                            \
     cudaError_t e_ = (call);                                                      \
@@ -32,8 +37,11 @@ void set_error(const char* fmt, ...);
     }                                                                             \
   } while (0)
 
-#define KFBI_CHECK_LAUNCH()                                                       \
+#define KFBI_CHECK_LAUNCH() KFBI_CHECK_LAUNCH_N(1)
+// after a launcher that issued n kernels: count them and surface launch errors
+#define KFBI_CHECK_LAUNCH_N(n)                                                    \
   do {                                                                            \
+    KFBI_COUNT(n);                                                                \
     cudaError_t e_ = cudaGetLastError();                                          \
     if (e_ != cudaSuccess) {                                                      \
       ::kfbi::set_error("kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_), \
@@ -171,6 +179,7 @@ struct SolveArgs {
 int box_solve64(kfbi_handle* h, const SolveArgs& a, double* work);
 int box_solve32(kfbi_handle* h, const SolveArgs& a, float* work);
 int dst_supported(int N);
+int transform_pass(kfbi_handle* h, int precision, int pass, double lambda);
 
 // ops.cu
 int launch_correction(kfbi_handle* h, const double* x, double* corr);

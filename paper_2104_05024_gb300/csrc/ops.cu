@@ -337,7 +337,7 @@ int launch_scatter_grid(kfbi_handle* h, const double* corr, double* grid_user) {
   const int64_t total = h->grid.dim == 3 ? (int64_t)n1 * n1 * n1 : (int64_t)n1 * n1;
   k_scatter<<<grid_blocks(total, 256), 256, 0, h->stream>>>(h->t, corr, grid_user, total);
   if (h->t.n_irr > 0) k_scatter2<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->t, corr, grid_user);
-  KFBI_CHECK_LAUNCH();
+  KFBI_CHECK_LAUNCH_N(h->t.n_irr > 0 ? 2 : 1);
   return KFBI_OK;
 }
 
@@ -355,7 +355,7 @@ int vec_dots(kfbi_handle* h, const double* V, int nvec, int ld, const double* w,
   if (nb > RED_BLOCKS) nb = RED_BLOCKS;
   k_dots_partial<<<dim3(nb, nvec), 256, 0, h->stream>>>(V, ld, w, n, h->w.partial);
   k_dots_final<<<nvec, 256, 0, h->stream>>>(h->w.partial, nb, nvec, out_dev);
-  KFBI_CHECK_LAUNCH();
+  KFBI_CHECK_LAUNCH_N(2);
   return KFBI_OK;
 }
 
@@ -427,7 +427,7 @@ int launch_ue(kfbi_handle* h, const double* V, double* ue) {
   k_dots_final<<<1, 256, 0, h->stream>>>(h->w.partial, nb, 1, h->w.partial + nb);
   k_ue<<<grid_blocks(total, 256), 256, 0, h->stream>>>(V, h->w.partial + nb, 1.0 / (double)h->t.n_inside,
                                                        h->sigma_i, h->sigma_e, ue, total);
-  KFBI_CHECK_LAUNCH();
+  KFBI_CHECK_LAUNCH_N(3);
   return KFBI_OK;
 }
 

@@ -61,7 +61,12 @@ EXPORTS = [
     "kfbi_last_error", "kfbi_create", "kfbi_destroy", "kfbi_query", "kfbi_set_opts", "kfbi_solve_neumann",
     "bidomain_step", "kfbi_export_setup", "kfbi_box_solve", "kfbi_correction", "kfbi_interface_limit",
     "kfbi_apply_A", "kfbi_rhs_g", "kfbi_solve_bie", "kfbi_react_fe", "kfbi_react_be", "kfbi_export_tables",
+    "kfbi_transform_pass", "kfbi_launch_count",
 ]
+
+
+def launch_count() -> int:
+    return int(load().kfbi_launch_count())
 
 _lib = None
 
@@ -94,9 +99,12 @@ def load(path: str = LIB_PATH):
     lib.kfbi_solve_bie.argtypes = [vp, C.c_double, vp, vp, C.POINTER(Stats)]
     lib.kfbi_react_fe.argtypes = [C.POINTER(FHNStruct), C.c_double, vp, vp, C.c_int64, vp]
     lib.kfbi_react_be.argtypes = [C.POINTER(FHNStruct), C.c_double, vp, vp, C.c_int64, vp]
+    lib.kfbi_transform_pass.argtypes = [vp, ip, ip, C.c_double]
     for name in EXPORTS:
-        if name != "kfbi_last_error" and name != "kfbi_destroy":
+        if name not in ("kfbi_last_error", "kfbi_destroy", "kfbi_launch_count"):
             getattr(lib, name).restype = C.c_int
+    lib.kfbi_launch_count.restype = C.c_int64
+    lib.kfbi_launch_count.argtypes = []
     _lib = lib
     return lib
 
@@ -225,6 +233,9 @@ class KFBI:
         p = lambda a: C.c_void_p(a.ctypes.data)  # noqa: E731
         _check(load().kfbi_export_tables(self._h, *[p(out[k]) for k in out]))
         return out
+
+    def transform_pass(self, pass_id, lam=0.0, precision=FP64):
+        _check(load().kfbi_transform_pass(self._h, precision, pass_id, lam))
 
     def box_solve(self, r, v, lam, precision=FP64):
         self.set_opts()

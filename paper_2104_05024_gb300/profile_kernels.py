@@ -1,0 +1,48 @@
+"""Launch the hot-path kernels of one workload a few times each, for ncu.
+
+    python -m paper_2104_05024_gb300.profile_kernels [--N 256] [--precision fp64|mixed] [--reps 3]
+
+Sets up the prolate-shell workload (configs 2/3 geometry), then runs each
+transform pass of the box solver, one irregular-node correction and one
+interface-limit gather `reps` times on the library's stream.  No timing is
+reported: this only gives a profiler a short, representative launch list.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    import torch
+
+    from kfbi_workloads import configs as C
+    from paper_2104_05024_gb300 import kfbi as K
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--N", type=int, default=256)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args()
+    prec = K.FP64 if a.precision == "fp64" else K.MIXED
+    geom, grid, cfg, V0, w0 = C.config2(N=a.N)
+    h = K.KFBI(geom, grid, tol=cfg.tol)
+    lam = C.helmholtz_lambda(cfg)
+    dev = torch.device("cuda:0")
+    psi = torch.ones(geom.M, dtype=torch.float64, device=dev)
+    out = torch.empty(geom.M, dtype=torch.float64, device=dev)
+    for _ in range(a.reps):
+        for p in (0, 1, 2, 3):
+            h.transform_pass(p, lam, prec)
+        h.apply_A(psi, out, lam, prec)
+    torch.cuda.synchronize()
+    print("ok")
+
+
+if __name__ == "__main__":
+    main()
