@@ -229,6 +229,32 @@ int kfbi_transform_pass(kfbi_handle* h, int precision, int pass, double lambda);
  * (instrumentation; every launch site adds its kernel count).                */
 int64_t kfbi_launch_count(void);
 
+/*
+ * Box solve for callers that cannot allocate device memory (the paper has no
+ * counterpart).  Same operation and result as kfbi_box_solve with precision
+ * KFBI_FP64 -- v = L_h^{-1} r on the (N-1)^dim interior nodes of [lo, hi]^dim
+ * with zero Dirichlet data -- but without a handle and without any device
+ * allocation: some callers run where every byte of device memory belongs to a
+ * pool or arena they do not control, or where allocation after start-up is
+ * forbidden, so neither they nor a library called by them may call
+ * cudaMalloc.  The padded work grid and the transform tables live in one
+ * static device array of KFBI_NOALLOC_MAX_POINTS + 2560 doubles (about 2 MiB)
+ * that every GPU loading this library holds until the process exits.
+ *  - N^dim must not exceed KFBI_NOALLOC_MAX_POINTS (3-D: N <= 64; 2-D:
+ *    N <= 512; N in 8, 16, 32, 64, 128, 256, 384, 512), else KFBI_ERR_ARG.
+ *  - The first call on a device (with that device current) looks up the
+ *    array's device address with cudaGetSymbolAddress; make that first call
+ *    before any stream capture.
+ *  - Every call shares the array, which keeps the last call's contents, so
+ *    calls that overlap on the GPU (other streams, other host threads using
+ *    the same device) race and must be serialised by the caller.
+ *  - r_dev, v_dev: caller-owned device fields, float64, (N-1)^dim, [z][y][x].
+ *  - Work is enqueued on `stream`; the call does not synchronise.
+ */
+#define KFBI_NOALLOC_MAX_POINTS 262144
+int kfbi_box_solve_noalloc(int dim, int N, double lo, double hi, double lambda, const double* r_dev,
+                           double* v_dev, void* stream);
+
 /* Pointwise FitzHugh-Nagumo half steps (Section 3, Eqs. ode1/ode2) over n
  * values: forward Euler (k = dt/2) and backward Euler with Newton.  The
  * backward step returns KFBI_ERR_NEWTON if any node hit the iteration cap.    */

@@ -24,6 +24,7 @@ SOURCES = {
     "setup.cu": ["-fmad=false"],
     "ops.cu": [],
     "capi.cu": [],
+    "noalloc.cu": [],
     "mlp.cu": [],
 }
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

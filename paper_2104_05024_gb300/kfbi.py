@@ -61,8 +61,13 @@ EXPORTS = [
     "kfbi_last_error", "kfbi_create", "kfbi_destroy", "kfbi_query", "kfbi_set_opts", "kfbi_solve_neumann",
     "bidomain_step", "kfbi_export_setup", "kfbi_box_solve", "kfbi_correction", "kfbi_interface_limit",
     "kfbi_apply_A", "kfbi_rhs_g", "kfbi_solve_bie", "kfbi_react_fe", "kfbi_react_be", "kfbi_export_tables",
-    "kfbi_transform_pass", "kfbi_launch_count",
+    "kfbi_transform_pass", "kfbi_launch_count", "kfbi_box_solve_noalloc",
 ]
+
+
+def box_solve_noalloc(r, v, lam, dim, N, lo=-1.0, hi=1.0):
+    """Box solve through the allocation-free entry point (static scratch)."""
+    _check(load().kfbi_box_solve_noalloc(dim, N, lo, hi, lam, _ptr(r), _ptr(v), _stream()))
 
 
 def launch_count() -> int:
@@ -100,6 +105,7 @@ def load(path: str = LIB_PATH):
     lib.kfbi_react_fe.argtypes = [C.POINTER(FHNStruct), C.c_double, vp, vp, C.c_int64, vp]
     lib.kfbi_react_be.argtypes = [C.POINTER(FHNStruct), C.c_double, vp, vp, C.c_int64, vp]
     lib.kfbi_transform_pass.argtypes = [vp, ip, ip, C.c_double]
+    lib.kfbi_box_solve_noalloc.argtypes = [ip, ip, C.c_double, C.c_double, C.c_double, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("kfbi_last_error", "kfbi_destroy", "kfbi_launch_count"):
             getattr(lib, name).restype = C.c_int
