@@ -55,6 +55,8 @@ extern "C" {
 #define KFBI_MIXED 1         /* float32 transforms inside GMRES, float64 Arnoldi,
                                 residuals and outer refinement                   */
 #define KFBI_MIXED_LEARNED 2 /* KFBI_MIXED + learned warm start of the density   */
+#define KFBI_FP32 3          /* kfbi_box_solve / kfbi_transform_pass only: plain
+                                float32 transforms without refinement             */
 
 #define KFBI_GMRES 0
 #define KFBI_RICHARDSON 1
@@ -111,6 +113,7 @@ typedef struct {
 typedef struct {
   int iters;            /* operator applications inside the Krylov solver     */
   int outer;            /* outer refinement sweeps (mixed precision)          */
+  int warmstart;        /* initial guess: 0 previous density, 1 learned       */
   double rel_res;       /* solver's residual estimate ||r|| / ||g||           */
   double true_rel_res;  /* recomputed ||g^N - du^+/dn|| / ||g|| (or -1)       */
   double init_rel_res;  /* residual of the initial guess                      */
@@ -130,6 +133,7 @@ typedef struct {
 } kfbi_info;
 
 typedef struct kfbi_handle kfbi_handle;
+typedef struct kfbi_mlp kfbi_mlp;
 
 const char* kfbi_last_error(void);
 
@@ -194,8 +198,10 @@ int kfbi_export_tables(kfbi_handle* h, double* node_wn, int32_t* node_cnt, int32
                        int32_t* cross_cnt, int32_t* cross_pid, double* cross_wlo, double* cross_whi);
 
 /* Box solve (Sections 5.2-5.3): v = L_h^{-1} r, 5/7-point operator with zero
- * Dirichlet data, by sine transforms.  precision KFBI_FP64 or KFBI_MIXED
- * (float32 transforms).                                                     */
+ * Dirichlet data, by sine transforms.  precision KFBI_FP64 (float64
+ * transforms), KFBI_MIXED / KFBI_MIXED_LEARNED (float32 transforms refined
+ * by three rounds of the float64 residual: float64-accurate) or KFBI_FP32
+ * (float32 transforms only).                                                */
 int kfbi_box_solve(kfbi_handle* h, int precision, double lambda, const double* r_dev, double* v_dev);
 
 /* Irregular-node correction (Section 5.3, Eq. correct): rhs_dev (grid, fully
@@ -217,6 +223,39 @@ int kfbi_rhs_g(kfbi_handle* h, double lambda, const double* f_dev, const double*
 /* GMRES / Richardson on A psi = g alone (tol = 0 runs exactly max_iter
  * applications).                                                             */
 int kfbi_solve_bie(kfbi_handle* h, double lambda, const double* g_dev, double* psi_dev, kfbi_stats* stats);
+
+/* ------------------------------------------------------------------
+ * Learned warm start (the workload's mixed + learned form; not in the paper).
+ * A point-wise network on the interface nodes: features (psi^{n-1},
+ * psi^{n-2}, g^n, x, y, z, n_x, n_y, n_z), normalised by
+ * norm = [mean[9], std[9], out_mean, out_std]; 4 hidden layers of width 128
+ * with SiLU; output o; psi^n predicted as psi^{n-1} + out_std o + out_mean.
+ * Parameters (float32, packed W0[128][9], b0[128], W1[128][128], b1, W2, b2,
+ * W3, b3, W4[1][128], b4[1]) are kept as float32 masters with bfloat16 copies
+ * for the tensor-core products (float32 accumulation).  Training uses the
+ * loss 0.5 mean (o - t)^2 on normalised targets t and Adam (0.9, 0.999, 1e-8).
+ * ------------------------------------------------------------------ */
+int kfbi_mlp_num_params(void);
+/* params_host [kfbi_mlp_num_params()], norm_host [20]; max_batch rows per
+ * call; work on `stream`.                                                    */
+int kfbi_mlp_create(const float* params_host, const float* norm_host, int max_batch, void* stream, kfbi_mlp** out);
+void kfbi_mlp_destroy(kfbi_mlp* m);
+int kfbi_mlp_get(kfbi_mlp* m, float* params_host);
+/* o_dev[B] = network output for raw features F_dev [B][9] (float32).        */
+int kfbi_mlp_forward(kfbi_mlp* m, const float* F_dev, int B, float* o_dev);
+/* loss and (optionally) the gradient of every parameter to host memory.     */
+int kfbi_mlp_grad(kfbi_mlp* m, const float* F_dev, const float* t_dev, int B, float* loss_host, float* grad_host);
+/* one forward + backward + Adam step with learning rate lr.                 */
+int kfbi_mlp_train_step(kfbi_mlp* m, const float* F_dev, const float* t_dev, int B, float lr, float* loss_host);
+/* Attach (or detach with NULL) a network to a 3-D handle.  With precision
+ * KFBI_MIXED_LEARNED, bidomain_step then predicts each diffusion solve's
+ * initial density from the two previous densities and g^n, and keeps it only
+ * when its float32 residual ||g - A psi|| is below that of the previous
+ * density (the plain warm start stays the fallback).                         */
+int kfbi_set_warmstart(kfbi_handle* h, kfbi_mlp* m);
+/* After a Strang step: psi_dev <- psi^n, psi_prev_dev <- psi^{n-1} and
+ * g_dev <- g^n of the last diffusion solve (each may be NULL).               */
+int kfbi_get_densities(kfbi_handle* h, double* psi_dev, double* psi_prev_dev, double* g_dev);
 
 /* One pass of the box solver on the handle's padded work grid, for timing
  * the transform kernels in isolation: pass 0 = x forward (no right-hand

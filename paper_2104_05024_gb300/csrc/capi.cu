@@ -6,6 +6,7 @@
 // Krylov iteration.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -104,12 +105,56 @@ int norm2(kfbi_handle* h, const double* v, double* slot, double* out) {
   return KFBI_OK;
 }
 
+// float64-accurate box solve from float32 transforms (iterative refinement
+// with the float64 5/7-point residual): u = L_h^{-1}(alpha*src + corr) on the
+// user layout.  Each round gains about -log10(kappa(L_h) eps_32) digits.
+constexpr int REFINE_ROUNDS = 3;
+
+int refined_solve(kfbi_handle* h, const double* src, double alpha, const double* corr, double lambda, double* u) {
+  SolveArgs sa;
+  sa.src = src;
+  sa.alpha = alpha;
+  sa.corr = corr;
+  sa.lambda = lambda;
+  sa.out_user = u;
+  int rc = box_solve32(h, sa, h->w.grid32);
+  if (rc) return rc;
+  for (int r = 0; r < REFINE_ROUNDS; ++r) {
+    if ((rc = launch_residual(h, src, alpha, corr, u, lambda, h->w.res64))) return rc;
+    SolveArgs sr;
+    sr.src = h->w.res64;
+    sr.lambda = lambda;
+    sr.out_user = u;
+    sr.aux = u;
+    sr.beta = 1.0;
+    sr.gamma = 1.0;
+    if ((rc = box_solve32(h, sr, h->w.grid32))) return rc;
+  }
+  return KFBI_OK;
+}
+
+// out = base + sgn * A psi with a float64-accurate (refined) box solve
+int apply_A_acc(kfbi_handle* h, double lambda, const double* psi, double* out, double sgn, const double* base) {
+  const double* x;
+  int rc = density_vector(h, psi, &x);
+  if (rc) return rc;
+  if ((rc = launch_correction(h, x, h->w.corr))) return rc;
+  if ((rc = refined_solve(h, nullptr, 1.0, h->w.corr, lambda, h->w.u64))) return rc;
+  return launch_limit_user(h, h->w.u64, x, base, sgn, out);
+}
+
+// g = gN - dv_V^+/dn with the refined volume solve
+int rhs_g_acc(kfbi_handle* h, double lambda, const double* src, double alpha, const double* gN, double* g) {
+  int rc = refined_solve(h, src, alpha, nullptr, lambda, h->w.u64);
+  if (rc) return rc;
+  return launch_limit_user(h, h->w.u64, nullptr, gN, -1.0, g);
+}
+
 // GMRES(m) with CGS2 Arnoldi on A psi = g; psi in: initial guess, out: solution
-int gmres(kfbi_handle* h, int prec, double lambda, const double* g, double* psi, kfbi_stats* st) {
+int gmres(kfbi_handle* h, int prec, double lambda, const double* g, double* psi, kfbi_stats* st, double tol,
+          int max_iter) {
   const int M = h->t.M;
   const int m = h->opts.restart;
-  const double tol = h->opts.tol;
-  const int max_iter = h->opts.max_iter;
   double* V = h->w.vecs;
   const int ld = M;
   double* wv = h->w.tmp;
@@ -203,9 +248,53 @@ int richardson(kfbi_handle* h, int prec, double lambda, const double* g, double*
   return rel <= h->opts.tol ? KFBI_OK : KFBI_ERR_NOT_CONVERGED;
 }
 
+// GMRES with iterative refinement (Carson and Higham): the outer residual
+// r = g - A psi uses float64-accurate box solves, the inner correction solve
+// A delta = r runs GMRES with float32 box solves and float64 Arnoldi.
+int gmres_ir(kfbi_handle* h, double lambda, const double* g, double* psi, kfbi_stats* st) {
+  const int M = h->t.M;
+  double* r = h->w.r2;
+  double* delta = h->w.tmp2;
+  double* slot = h->w.small + small_nrm2(h->opts.restart);
+  const double tol = h->opts.tol;
+  int rc;
+  double gnorm;
+  if ((rc = norm2(h, g, slot, &gnorm))) return rc;
+  if (gnorm == 0.0) gnorm = 1.0;
+  int inner_total = 0, outer = 0;
+  double rel = 0.0;
+  for (;;) {
+    if ((rc = apply_A_acc(h, lambda, psi, r, -1.0, g))) return rc;
+    double rn;
+    if ((rc = norm2(h, r, slot, &rn))) return rc;
+    rel = rn / gnorm;
+    if (outer == 0) st->init_rel_res = rel;
+    if (!std::isfinite(rel)) {
+      set_error("non-finite residual in GMRES-IR");
+      return KFBI_ERR_NAN;
+    }
+    if (rel <= tol || inner_total >= h->opts.max_iter || outer >= 20) break;
+    // inner tolerance relative to ||r||: four digits, or just what the target needs
+    double tin = std::max(1e-4, 0.3 * tol * gnorm / rn);
+    if (tin > 0.5) tin = 0.5;
+    KFBI_CUDA(cudaMemsetAsync(delta, 0, sizeof(double) * (size_t)M, h->stream));
+    kfbi_stats in{};
+    rc = gmres(h, KFBI_MIXED, lambda, r, delta, &in, tin, h->opts.max_iter - inner_total);
+    if (rc != KFBI_OK && rc != KFBI_ERR_NOT_CONVERGED) return rc;
+    inner_total += in.iters;
+    if ((rc = vec_axpby(h, psi, 1.0, delta, 1.0, M))) return rc;
+    ++outer;
+  }
+  st->iters = inner_total;
+  st->outer = outer;
+  st->rel_res = rel;
+  return rel <= tol ? KFBI_OK : KFBI_ERR_NOT_CONVERGED;
+}
+
 int solve_bie(kfbi_handle* h, int prec, double lambda, const double* g, double* psi, kfbi_stats* st) {
   if (h->opts.solver == KFBI_RICHARDSON) return richardson(h, prec, lambda, g, psi, st);
-  return gmres(h, prec, lambda, g, psi, st);
+  if (prec != KFBI_FP64) return gmres_ir(h, lambda, g, psi, st);
+  return gmres(h, prec, lambda, g, psi, st, h->opts.tol, h->opts.max_iter);
 }
 
 int check_handle(kfbi_handle* h) {
@@ -308,6 +397,13 @@ int kfbi_create(const kfbi_geometry* geom, const kfbi_grid* grid, double sigma_i
   if ((rc = dalloc(h, &h->w.tmp, (size_t)M))) return fail(rc);
   if ((rc = dalloc(h, &h->w.tmp2, (size_t)M))) return fail(rc);
   if ((rc = dalloc(h, &h->w.psi_prev, (size_t)M))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.r2, (size_t)M))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.psi_prev2, (size_t)M))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.psi_save, (size_t)M))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.psi_learn, (size_t)M))) return fail(rc);
+  cudaMemsetAsync(h->w.psi_prev2, 0, sizeof(double) * (size_t)M, h->stream);
+  if ((rc = dalloc(h, &h->w.u64, (size_t)grid_points(h)))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.res64, (size_t)grid_points(h)))) return fail(rc);
   cudaMemsetAsync(h->w.psi_prev, 0, sizeof(double) * (size_t)M, h->stream);
   if (cudaMallocHost((void**)&h->w.host_small, 64 * sizeof(double)) != cudaSuccess) {
     set_error("cudaMallocHost failed");
@@ -409,6 +505,8 @@ int kfbi_box_solve(kfbi_handle* h, int precision, double lambda, const double* r
   sa.lambda = lambda;
   sa.out_user = v_dev;
   if (precision == KFBI_FP64) return box_solve64(h, sa, h->w.grid64);
+  if (precision == KFBI_MIXED || precision == KFBI_MIXED_LEARNED)
+    return refined_solve(h, r_dev, 1.0, nullptr, lambda, v_dev);
   return box_solve32(h, sa, h->w.grid32);
 }
 
@@ -477,22 +575,29 @@ int kfbi_solve_neumann(kfbi_handle* h, double lambda, const double* f_dev, const
   }
   kfbi_stats st{};
   auto t0 = std::chrono::steady_clock::now();
-  int rc = rhs_g(h, lambda, f_dev, 1.0, gN_dev, h->w.g);
+  const int prec = h->opts.precision == KFBI_FP64 ? KFBI_FP64 : KFBI_MIXED;
+  int rc = prec == KFBI_FP64 ? rhs_g(h, lambda, f_dev, 1.0, gN_dev, h->w.g)
+                             : rhs_g_acc(h, lambda, f_dev, 1.0, gN_dev, h->w.g);
   if (rc) return rc;
-  const int solve_rc = solve_bie(h, KFBI_FP64, lambda, h->w.g, psi_dev, &st);
+  const int solve_rc = solve_bie(h, prec, lambda, h->w.g, psi_dev, &st);
   if (solve_rc != KFBI_OK && solve_rc != KFBI_ERR_NOT_CONVERGED) return solve_rc;
   // u = v_V + v_B(psi) in one solve of the combined right-hand side
   const double* x;
   if ((rc = density_vector(h, psi_dev, &x))) return rc;
   if ((rc = launch_correction(h, x, h->w.corr))) return rc;
-  SolveArgs sa;
-  sa.src = f_dev;
-  sa.corr = h->w.corr;
-  sa.lambda = lambda;
-  sa.out_user = u_dev;
-  if ((rc = box_solve64(h, sa, h->w.grid64))) return rc;
-  // true residual g^N - du^+/dn relative to ||g||
-  if ((rc = launch_limit64(h, h->w.grid64, x, gN_dev, -1.0, h->w.r))) return rc;
+  if (prec == KFBI_FP64) {
+    SolveArgs sa;
+    sa.src = f_dev;
+    sa.corr = h->w.corr;
+    sa.lambda = lambda;
+    sa.out_user = u_dev;
+    if ((rc = box_solve64(h, sa, h->w.grid64))) return rc;
+    // true residual g^N - du^+/dn relative to ||g||
+    if ((rc = launch_limit64(h, h->w.grid64, x, gN_dev, -1.0, h->w.r))) return rc;
+  } else {
+    if ((rc = refined_solve(h, f_dev, 1.0, h->w.corr, lambda, u_dev))) return rc;
+    if ((rc = launch_limit_user(h, u_dev, x, gN_dev, -1.0, h->w.r))) return rc;
+  }
   double rn, gn;
   double* slot = h->w.small + small_nrm2(h->opts.restart);
   if ((rc = norm2(h, h->w.r, slot, &rn))) return rc;
@@ -520,25 +625,53 @@ int bidomain_step(kfbi_handle* h, const kfbi_fhn* p, double* V_dev, double* w_de
     kfbi_stats st{};
     auto t0 = std::chrono::steady_clock::now();
     if ((rc = launch_react_fe(p, k, V_dev, w_dev, n, h->stream))) return rc;
+    const int prec = h->opts.precision == KFBI_FP64 ? KFBI_FP64 : KFBI_MIXED;
     // g = -dv_V^+/dn with v_V = L_h^{-1}(-lam V)
-    if ((rc = rhs_g(h, lam, V_dev, -lam, nullptr, h->w.g))) return rc;
-    const int src = solve_bie(h, KFBI_FP64, lam, h->w.g, h->w.psi_prev, &st);
+    rc = prec == KFBI_FP64 ? rhs_g(h, lam, V_dev, -lam, nullptr, h->w.g)
+                           : rhs_g_acc(h, lam, V_dev, -lam, nullptr, h->w.g);
+    if (rc) return rc;
+    // initial density: the previous one, or the learned prediction when its
+    // float32 residual is smaller
+    if ((rc = vec_copy(h, h->w.psi_save, h->w.psi_prev, h->t.M))) return rc;
+    if (h->opts.precision == KFBI_MIXED_LEARNED && h->warm != nullptr && h->n_hist >= 2) {
+      if ((rc = mlp_warmstart(h->warm, h->stream, h->w.psi_prev, h->w.psi_prev2, h->w.g, h->t.nodes, h->t.n_normal,
+                              h->t.M, h->w.psi_learn)))
+        return rc;
+      double rl, rp;
+      double* slot = h->w.small + small_nrm2(h->opts.restart);
+      if ((rc = apply_A(h, KFBI_FP32, lam, h->w.psi_learn, h->w.r, -1.0, h->w.g))) return rc;
+      if ((rc = norm2(h, h->w.r, slot, &rl))) return rc;
+      if ((rc = apply_A(h, KFBI_FP32, lam, h->w.psi_prev, h->w.r, -1.0, h->w.g))) return rc;
+      if ((rc = norm2(h, h->w.r, slot, &rp))) return rc;
+      if (rl < rp) {
+        if ((rc = vec_copy(h, h->w.psi_prev, h->w.psi_learn, h->t.M))) return rc;
+        st.warmstart = 1;
+      }
+    }
+    const int src = solve_bie(h, prec, lam, h->w.g, h->w.psi_prev, &st);
     if (src != KFBI_OK && src != KFBI_ERR_NOT_CONVERGED) return src;
+    if ((rc = vec_copy(h, h->w.psi_prev2, h->w.psi_save, h->t.M))) return rc;
+    ++h->n_hist;
     if (src == KFBI_ERR_NOT_CONVERGED) final_rc = src;
     // V <- 2 (v_V + v_B(psi)) - V, one solve of the combined right-hand side
     const double* x;
     if ((rc = density_vector(h, h->w.psi_prev, &x))) return rc;
     if ((rc = launch_correction(h, x, h->w.corr))) return rc;
-    SolveArgs sa;
-    sa.src = V_dev;
-    sa.alpha = -lam;
-    sa.corr = h->w.corr;
-    sa.lambda = lam;
-    sa.out_user = V_dev;
-    sa.aux = V_dev;
-    sa.beta = 2.0;
-    sa.gamma = -1.0;
-    if ((rc = box_solve64(h, sa, h->w.grid64))) return rc;
+    if (prec == KFBI_FP64) {
+      SolveArgs sa;
+      sa.src = V_dev;
+      sa.alpha = -lam;
+      sa.corr = h->w.corr;
+      sa.lambda = lam;
+      sa.out_user = V_dev;
+      sa.aux = V_dev;
+      sa.beta = 2.0;
+      sa.gamma = -1.0;
+      if ((rc = box_solve64(h, sa, h->w.grid64))) return rc;
+    } else {
+      if ((rc = refined_solve(h, V_dev, -lam, h->w.corr, lam, h->w.u64))) return rc;
+      if ((rc = launch_lincomb(h, V_dev, 2.0, h->w.u64, -1.0, n))) return rc;
+    }
     if ((rc = launch_react_be(p, k, V_dev, w_dev, n, h->w.err, h->stream))) return rc;
     st.true_rel_res = -1.0;
     st.ms = elapsed_ms(t0);
@@ -555,6 +688,25 @@ int bidomain_step(kfbi_handle* h, const kfbi_fhn* p, double* V_dev, double* w_de
     return KFBI_ERR_NEWTON;
   }
   return final_rc;
+}
+
+int kfbi_set_warmstart(kfbi_handle* h, kfbi_mlp* m) {
+  if (int rc = check_handle(h)) return rc;
+  if (m != nullptr && h->grid.dim != 3) {
+    set_error("the learned warm start needs a 3-D geometry");
+    return KFBI_ERR_ARG;
+  }
+  h->warm = m;
+  return KFBI_OK;
+}
+
+int kfbi_get_densities(kfbi_handle* h, double* psi_dev, double* psi_prev_dev, double* g_dev) {
+  if (int rc = check_handle(h)) return rc;
+  const size_t n = sizeof(double) * (size_t)h->t.M;
+  if (psi_dev) KFBI_CUDA(cudaMemcpyAsync(psi_dev, h->w.psi_prev, n, cudaMemcpyDeviceToDevice, h->stream));
+  if (psi_prev_dev) KFBI_CUDA(cudaMemcpyAsync(psi_prev_dev, h->w.psi_prev2, n, cudaMemcpyDeviceToDevice, h->stream));
+  if (g_dev) KFBI_CUDA(cudaMemcpyAsync(g_dev, h->w.g, n, cudaMemcpyDeviceToDevice, h->stream));
+  return KFBI_OK;
 }
 
 int kfbi_transform_pass(kfbi_handle* h, int precision, int pass, double lambda) {

@@ -131,9 +131,10 @@ struct Dft<T, 3> {
 };
 
 // One in-place Stockham stage of radix R on the complex sequence stored in
-// rows (2m, 2m+1) of every column.  All reads precede all writes.
-template <typename T, int N, int R>
-__device__ __forceinline__ void fft_stage(T* s, const T* tw, int Ls) {
+// rows (2m, 2m+1) of every column.  All reads precede all writes.  Ls is a
+// compile-time constant so every index division is a shift or a constant.
+template <typename T, int N, int R, int Ls>
+__device__ __forceinline__ void fft_stage(T* s, const T* tw) {
   using C = Cfg<T, N>;
   constexpr int L = C::L, W = C::W, RS = C::RS;
   constexpr int NB = (L / R) * W;
@@ -180,6 +181,20 @@ __device__ __forceinline__ void fft_stage(T* s, const T* tw, int Ls) {
   __syncthreads();
 }
 
+// the stage sequence of a length-Lrem transform, unrolled at compile time
+template <typename T, int N, int Ls, int Lrem>
+struct Stages {
+  static __device__ __forceinline__ void run(T* s, const T* tw) {
+    constexpr int R = pick_radix(Lrem);
+    fft_stage<T, N, R, Ls>(s, tw);
+    Stages<T, N, Ls * R, Lrem / R>::run(s, tw);
+  }
+};
+template <typename T, int N, int Ls>
+struct Stages<T, N, Ls, 1> {
+  static __device__ __forceinline__ void run(T*, const T*) {}
+};
+
 // DST-I of every column of the tile s[N][RS] (rows 1..N-1 in, rows 1..N-1
 // out, row 0 holds 0).  tw = e^{i pi j / N}, j = 0..2N-1 (interleaved re, im);
 // tot = scan scratch [G][W].
@@ -204,18 +219,7 @@ __device__ void dst1_tile(T* s, const T* tw, T* tot) {
   }
   __syncthreads();
   // complex FFT of length L = N/2 on z_m = y_{2m} + i y_{2m+1}
-  {
-    int Lrem = L, Ls = 1;
-    while (Lrem > 1) {
-      const int r = pick_radix(Lrem);
-      if (r == 8) fft_stage<T, N, 8>(s, tw, Ls);
-      else if (r == 4) fft_stage<T, N, 4>(s, tw, Ls);
-      else if (r == 2) fft_stage<T, N, 2>(s, tw, Ls);
-      else fft_stage<T, N, 3>(s, tw, Ls);
-      Ls *= r;
-      Lrem /= r;
-    }
-  }
+  Stages<T, N, 1, L>::run(s, tw);
   // real-DFT split: Y_k = (A + conj B)/2 - i w_k (A - conj B)/2, A = Z_k,
   // B = Z_{L-k}, w_k = e^{2 pi i k / N}; store I_k in row 2k, R_k in row 2k+1
   for (int idx = threadIdx.x; idx < (L / 2 + 1) * W; idx += NT) {

@@ -103,6 +103,8 @@ struct Tables {
   float* tw32 = nullptr;
   uint8_t* inside = nullptr;      // [(N-1)^dim]
   int n_inside = 0;
+  double* nodes = nullptr;        // [M][dim] interface nodes
+  double* n_normal = nullptr;     // [M][3] outward normals at the nodes
 };
 
 struct Workspace {
@@ -120,6 +122,12 @@ struct Workspace {
   double* tmp = nullptr;          // [M]
   double* tmp2 = nullptr;         // [M]
   double* psi_prev = nullptr;     // [M] density of the previous diffusion solve
+  double* r2 = nullptr;           // [M] outer residual of GMRES-IR
+  double* psi_prev2 = nullptr;    // [M] density of the solve before the previous one
+  double* psi_save = nullptr;     // [M]
+  double* psi_learn = nullptr;    // [M] learned initial guess
+  double* u64 = nullptr;          // user-layout float64 grid (refined solutions)
+  double* res64 = nullptr;        // user-layout float64 grid (refinement residuals)
   double* host_small = nullptr;   // pinned host scalars
   int* err = nullptr;             // device error word
   int restart_cap = 0;
@@ -138,6 +146,8 @@ struct kfbi_handle {
   size_t device_bytes = 0;
   std::vector<void*> allocations;
   bool have_prev = false;
+  int n_hist = 0;                 // completed diffusion solves (density history)
+  kfbi_mlp* warm = nullptr;       // learned warm start (not owned)
 };
 
 namespace kfbi {
@@ -187,6 +197,10 @@ int launch_spline(kfbi_handle* h, const double* psi, double* x);
 int launch_limit64(kfbi_handle* h, const double* grid, const double* x, const double* base, double sgn, double* out);
 int launch_limit32(kfbi_handle* h, const float* grid, const double* x, const double* base, double sgn, double* out);
 int launch_scatter_grid(kfbi_handle* h, const double* corr, double* grid_user);
+int launch_limit_user(kfbi_handle* h, const double* u, const double* x, const double* base, double sgn, double* out);
+int launch_residual(kfbi_handle* h, const double* src, double alpha, const double* corr, const double* u, double lambda,
+                    double* res);
+int launch_lincomb(kfbi_handle* h, double* y, double a, const double* x, double b, int64_t n);
 int launch_padded_to_user(kfbi_handle* h, const double* padded, double* user);
 
 // GMRES vector kernels (ops.cu)
@@ -197,6 +211,10 @@ int vec_scale_by_norm(kfbi_handle* h, double* v, const double* w, const double* 
 int vec_copy(kfbi_handle* h, double* dst, const double* src, int n);
 int arnoldi_givens(kfbi_handle* h, double* small, int j, int ldh);
 int arnoldi_solve(kfbi_handle* h, double* small, int k, int ldh);
+
+// mlp.cu
+int mlp_warmstart(kfbi_mlp* m, cudaStream_t st, const double* p1, const double* p2, const double* g,
+                  const double* nodes, const double* normals, int M, double* out);
 
 int launch_react_fe(const kfbi_fhn* p, double k, double* V, double* w, int64_t n, cudaStream_t s);
 int launch_react_be(const kfbi_fhn* p, double k, double* V, double* w, int64_t n, int* err, cudaStream_t s);

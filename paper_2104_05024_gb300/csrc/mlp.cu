@@ -1,0 +1,478 @@
+// Point-wise MLP of the learned density warm start: 9 features per interface
+// node (psi^{n-1}, psi^{n-2}, g^n, x, n), 4 hidden layers of width 128 with
+// SiLU, one output o; psi^n is predicted as psi^{n-1} + s_out o + m_out.
+// bfloat16 weights and activations, float32 accumulation on the tensor cores
+// (wmma bf16 16x16x16 fragments), float32 master weights with Adam.  The
+// network only supplies GMRES's initial guess; the solver tolerance still
+// fixes the converged density.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <mma.h>
+
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+
+using bf16 = __nv_bfloat16;
+
+namespace kfbi {
+namespace {
+
+constexpr int NIN = 9, KIN = 16, WID = 128, NL = 5;  // 4 hidden + output
+constexpr int TILE = 64;
+
+struct Offsets {
+  size_t w[NL], b[NL], total;
+  Offsets() {
+    const int in[NL] = {NIN, WID, WID, WID, WID};
+    const int out[NL] = {WID, WID, WID, WID, 1};
+    size_t o = 0;
+    for (int l = 0; l < NL; ++l) {
+      w[l] = o;
+      o += (size_t)in[l] * out[l];
+      b[l] = o;
+      o += out[l];
+    }
+    total = o;
+  }
+};
+
+__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + expf(-z)); }
+__device__ __forceinline__ float dsilu_f(float z) {
+  const float s = 1.0f / (1.0f + expf(-z));
+  return s * (1.0f + z * (1.0f - s));
+}
+
+// C[M x N] (=, or += by atomics for split-K) A[M x K] B[K x N]; bf16 operands,
+// float32 accumulation.  A row-major: A[m lda + k]; col-major: A[k lda + m].
+// B row-major: B[k ldb + n]; col-major: B[n ldb + k].  M, N, K multiples of 16.
+template <typename LA, typename LB, bool ATOMIC>
+__global__ void __launch_bounds__(128) k_gemm(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B, int ldb,
+                                              float* __restrict__ C, int ldc, int M, int N, int K, int kchunk) {
+  using namespace nvcuda;
+  const int warp = threadIdx.x >> 5, wy = warp >> 1, wx = warp & 1;
+  const int m0 = blockIdx.y * TILE + wy * 32, n0 = blockIdx.x * TILE + wx * 32;
+  const int k0 = blockIdx.z * kchunk;
+  const int k1 = min(K, k0 + kchunk);
+  wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) wmma::fill_fragment(acc[i][j], 0.0f);
+  const bool a_row = std::is_same<LA, wmma::row_major>::value;
+  const bool b_row = std::is_same<LB, wmma::row_major>::value;
+  for (int k = k0; k < k1; k += 16) {
+    wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, LA> fa[2];
+    wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, LB> fb[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int m = m0 + i * 16;
+      if (m < M) wmma::load_matrix_sync(fa[i], a_row ? A + (size_t)m * lda + k : A + (size_t)k * lda + m, lda);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int n = n0 + j * 16;
+      if (n < N) wmma::load_matrix_sync(fb[j], b_row ? B + (size_t)k * ldb + n : B + (size_t)n * ldb + k, ldb);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+        if (m0 + i * 16 < M && n0 + j * 16 < N) wmma::mma_sync(acc[i][j], fa[i], fb[j], acc[i][j]);
+  }
+  __shared__ float stage[4][16 * 16];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int m = m0 + i * 16, n = n0 + j * 16;
+      if (m >= M || n >= N) continue;
+      if (!ATOMIC) {
+        wmma::store_matrix_sync(C + (size_t)m * ldc + n, acc[i][j], ldc, wmma::mem_row_major);
+      } else {
+        wmma::store_matrix_sync(stage[warp], acc[i][j], 16, wmma::mem_row_major);
+        __syncwarp();
+        for (int e = threadIdx.x & 31; e < 256; e += 32)
+          atomicAdd(C + (size_t)(m + e / 16) * ldc + n + (e % 16), stage[warp][e]);
+        __syncwarp();
+      }
+    }
+}
+
+// normalised bfloat16 features [Bp][16] from raw float32 features [B][9]
+__global__ void k_feat_raw(const float* __restrict__ F, int B, int Bp, const float* __restrict__ norm, bf16* X) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Bp * KIN) return;
+  const int b = i / KIN, c = i % KIN;
+  float v = 0.0f;
+  if (b < B && c < NIN) v = (F[(size_t)b * NIN + c] - norm[c]) / norm[NIN + c];
+  X[i] = __float2bfloat16_rn(v);
+}
+
+// the same from the solver state (psi^{n-1}, psi^{n-2}, g^n, nodes, normals)
+__global__ void k_feat_state(const double* __restrict__ p1, const double* __restrict__ p2, const double* __restrict__ g,
+                             const double* __restrict__ nodes, const double* __restrict__ normals, int B, int Bp,
+                             const float* __restrict__ norm, bf16* X, float* Fraw) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= Bp) return;
+  float f[NIN];
+  if (b < B) {
+    f[0] = (float)p1[b];
+    f[1] = (float)p2[b];
+    f[2] = (float)g[b];
+    for (int k = 0; k < 3; ++k) {
+      f[3 + k] = (float)nodes[(size_t)b * 3 + k];
+      f[6 + k] = (float)normals[(size_t)b * 3 + k];
+    }
+  }
+  for (int c = 0; c < KIN; ++c) {
+    float v = 0.0f;
+    if (b < B && c < NIN) v = (f[c] - norm[c]) / norm[NIN + c];
+    X[(size_t)b * KIN + c] = __float2bfloat16_rn(v);
+    if (Fraw != nullptr && b < B && c < NIN) Fraw[(size_t)b * NIN + c] = f[c];
+  }
+}
+
+__global__ void k_bias_act(float* __restrict__ Z, const float* __restrict__ bias, bf16* __restrict__ A, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float z = Z[i] + bias[i % WID];
+  Z[i] = z;
+  A[i] = __float2bfloat16_rn(silu_f(z));
+}
+
+// o_b = sum_j A3[b][j] w4[j] + b4 (one warp per row)
+__global__ void k_out(const bf16* __restrict__ A, const bf16* __restrict__ w4, const float* __restrict__ b4, float* o,
+                      int Bp) {
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= Bp) return;
+  float acc = 0.0f;
+  for (int j = lane; j < WID; j += 32) acc += __bfloat162float(A[(size_t)row * WID + j]) * __bfloat162float(w4[j]);
+  for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
+  if (lane == 0) o[row] = acc + b4[0];
+}
+
+// output-layer delta d4 = (o - t)/B and the loss partial sums
+__global__ void k_delta_out(const float* __restrict__ o, const float* __restrict__ t, int B, int Bp, float* d4,
+                            float* loss) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  float r = 0.0f;
+  if (b < B) r = o[b] - t[b];
+  if (b < Bp) d4[b] = r / (float)B;
+  float sq = r * r;
+  for (int s = 16; s > 0; s >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, s);
+  if ((threadIdx.x & 31) == 0 && sq != 0.0f) atomicAdd(loss, sq);
+}
+
+// gradients of the output layer and delta of the last hidden layer
+__global__ void k_back_out(const float* __restrict__ d4, const bf16* __restrict__ A3, const float* __restrict__ Z3,
+                           const bf16* __restrict__ w4, float* gw4, float* gb4, float* d, bf16* db, int Bp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Bp * WID) return;
+  const int b = i / WID, j = i % WID;
+  const float dq = __bfloat162float(__float2bfloat16_rn(d4[b]));
+  atomicAdd(gw4 + j, dq * __bfloat162float(A3[i]));
+  if (j == 0 && d4[b] != 0.0f) atomicAdd(gb4, d4[b]);
+  const float v = dq * __bfloat162float(w4[j]) * dsilu_f(Z3[i]);
+  d[i] = v;
+  db[i] = __float2bfloat16_rn(v);
+}
+
+__global__ void k_dsilu(const float* __restrict__ da, const float* __restrict__ Z, float* d, bf16* db, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float v = da[i] * dsilu_f(Z[i]);
+  d[i] = v;
+  db[i] = __float2bfloat16_rn(v);
+}
+
+// bias gradient: column sums of d [Bp][128]
+__global__ void k_colsum(const float* __restrict__ d, int Bp, float* g) {
+  const int j = threadIdx.x % WID;
+  float acc = 0.0f;
+  for (int b = blockIdx.x * (blockDim.x / WID) + threadIdx.x / WID; b < Bp; b += gridDim.x * (blockDim.x / WID))
+    acc += d[(size_t)b * WID + j];
+  atomicAdd(g + j, acc);
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       int n, float lr, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = 0.9f * m[i] + 0.1f * gi;
+  const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+}
+
+// bfloat16 weight copies (W0 padded from 9 to 16 input columns)
+__global__ void k_refresh(const float* __restrict__ p, Offsets off, bf16* W0, bf16* W1, bf16* W2, bf16* W3, bf16* w4) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < WID * KIN) {
+    const int r = i / KIN, c = i % KIN;
+    W0[i] = __float2bfloat16_rn(c < NIN ? p[off.w[0] + (size_t)r * NIN + c] : 0.0f);
+  }
+  if (i < WID * WID) {
+    W1[i] = __float2bfloat16_rn(p[off.w[1] + i]);
+    W2[i] = __float2bfloat16_rn(p[off.w[2] + i]);
+    W3[i] = __float2bfloat16_rn(p[off.w[3] + i]);
+  }
+  if (i < WID) w4[i] = __float2bfloat16_rn(p[off.w[4] + i]);
+}
+
+// W0 gradient: columns 0..8 of the padded [128][16] product
+__global__ void k_unpad_w0(const float* __restrict__ g16, float* gw0) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < WID * NIN) gw0[i] += g16[(i / NIN) * KIN + i % NIN];
+}
+
+// psi0 = psi1 + s_out o + m_out
+__global__ void k_predict(const double* __restrict__ p1, const float* __restrict__ o, const float* __restrict__ norm,
+                          double* out, int B) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B) out[b] = p1[b] + (double)(norm[2 * NIN + 1] * o[b] + norm[2 * NIN]);
+}
+
+}  // namespace
+}  // namespace kfbi
+
+struct kfbi_mlp {
+  kfbi::Offsets off;
+  int bmax = 0, bpmax = 0;
+  cudaStream_t stream = nullptr;
+  float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr, *norm = nullptr;
+  bf16 *W0 = nullptr, *W[3] = {nullptr, nullptr, nullptr}, *w4 = nullptr;
+  bf16* X = nullptr;
+  bf16* A[4] = {nullptr, nullptr, nullptr, nullptr};
+  float* Z[4] = {nullptr, nullptr, nullptr, nullptr};
+  float *o = nullptr, *d4 = nullptr, *d = nullptr, *da = nullptr, *g16 = nullptr, *loss = nullptr;
+  bf16* db = nullptr;
+  int step = 0;
+  std::vector<void*> allocs;
+};
+
+namespace kfbi {
+namespace {
+
+template <typename T>
+int malloc_mlp(kfbi_mlp* m, T** p, size_t n) {
+  if (cudaMalloc((void**)p, sizeof(T) * (n ? n : 1)) != cudaSuccess) {
+    set_error("cudaMalloc failed for the MLP workspace");
+    return KFBI_ERR_OOM;
+  }
+  m->allocs.push_back((void*)*p);
+  return KFBI_OK;
+}
+
+int blocks(size_t n, int bs) { return (int)((n + bs - 1) / bs); }
+
+// forward over rows already placed in m->X; leaves o, Z, A
+int mlp_forward_rows(kfbi_mlp* m, int Bp) {
+  using namespace nvcuda;
+  cudaStream_t st = m->stream;
+  const dim3 g(WID / TILE, Bp / TILE, 1);
+  k_gemm<wmma::row_major, wmma::col_major, false><<<g, 128, 0, st>>>(m->X, KIN, m->W0, KIN, m->Z[0], WID, Bp, WID, KIN, KIN);
+  k_bias_act<<<blocks((size_t)Bp * WID, 256), 256, 0, st>>>(m->Z[0], m->p + m->off.b[0], m->A[0], Bp * WID);
+  for (int l = 1; l < 4; ++l) {
+    k_gemm<wmma::row_major, wmma::col_major, false><<<g, 128, 0, st>>>(m->A[l - 1], WID, m->W[l - 1], WID, m->Z[l], WID,
+                                                                       Bp, WID, WID, WID);
+    k_bias_act<<<blocks((size_t)Bp * WID, 256), 256, 0, st>>>(m->Z[l], m->p + m->off.b[l], m->A[l], Bp * WID);
+  }
+  k_out<<<blocks((size_t)Bp * 32, 256), 256, 0, st>>>(m->A[3], m->w4, m->p + m->off.b[4], m->o, Bp);
+  KFBI_CHECK_LAUNCH_N(9);
+  return KFBI_OK;
+}
+
+int mlp_prepare_raw(kfbi_mlp* m, const float* F, int B, int* Bp) {
+  if (B < 1 || B > m->bmax) {
+    set_error("batch %d outside 1..%d", B, m->bmax);
+    return KFBI_ERR_ARG;
+  }
+  *Bp = (B + TILE - 1) / TILE * TILE;
+  k_feat_raw<<<blocks((size_t)*Bp * KIN, 256), 256, 0, m->stream>>>(F, B, *Bp, m->norm, m->X);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+// gradients of 0.5 mean (o - t)^2 into m->g (rows already forwarded)
+int mlp_backward(kfbi_mlp* m, const float* t, int B, int Bp) {
+  using namespace nvcuda;
+  cudaStream_t st = m->stream;
+  const Offsets& off = m->off;
+  KFBI_CUDA(cudaMemsetAsync(m->g, 0, sizeof(float) * off.total, st));
+  KFBI_CUDA(cudaMemsetAsync(m->loss, 0, sizeof(float), st));
+  KFBI_CUDA(cudaMemsetAsync(m->g16, 0, sizeof(float) * WID * KIN, st));
+  k_delta_out<<<blocks(Bp, 256), 256, 0, st>>>(m->o, t, B, Bp, m->d4, m->loss);
+  k_back_out<<<blocks((size_t)Bp * WID, 256), 256, 0, st>>>(m->d4, m->A[3], m->Z[3], m->w4, m->g + off.w[4],
+                                                            m->g + off.b[4], m->d, m->db, Bp);
+  int launched = 2;
+  const int kch = 1024;
+  for (int l = 3; l >= 0; --l) {
+    // weight gradient d^T A_{l-1} (split over rows, float32 atomics)
+    const dim3 gg(l == 0 ? 1 : WID / TILE, WID / TILE, (Bp + kch - 1) / kch);
+    if (l > 0) {
+      k_gemm<wmma::col_major, wmma::row_major, true><<<gg, 128, 0, st>>>(m->db, WID, m->A[l - 1], WID, m->g + off.w[l],
+                                                                         WID, WID, WID, Bp, kch);
+    } else {
+      k_gemm<wmma::col_major, wmma::row_major, true><<<gg, 128, 0, st>>>(m->db, WID, m->X, KIN, m->g16, KIN, WID, KIN,
+                                                                         Bp, kch);
+      k_unpad_w0<<<blocks(WID * NIN, 256), 256, 0, st>>>(m->g16, m->g + off.w[0]);
+      ++launched;
+    }
+    k_colsum<<<64, 256, 0, st>>>(m->d, Bp, m->g + off.b[l]);
+    launched += 2;
+    if (l > 0) {
+      const dim3 g2(WID / TILE, Bp / TILE, 1);
+      k_gemm<wmma::row_major, wmma::row_major, false><<<g2, 128, 0, st>>>(m->db, WID, m->W[l - 1], WID, m->da, WID, Bp,
+                                                                          WID, WID, WID);
+      k_dsilu<<<blocks((size_t)Bp * WID, 256), 256, 0, st>>>(m->da, m->Z[l - 1], m->d, m->db, Bp * WID);
+      launched += 2;
+    }
+  }
+  KFBI_CHECK_LAUNCH_N(launched);
+  return KFBI_OK;
+}
+
+int mlp_refresh(kfbi_mlp* m) {
+  k_refresh<<<blocks(WID * WID, 256), 256, 0, m->stream>>>(m->p, m->off, m->W0, m->W[0], m->W[1], m->W[2], m->w4);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+}  // namespace
+
+// warm start used by bidomain_step: psi0 = psi1 + network(psi1, psi2, g, x, n)
+int mlp_warmstart(kfbi_mlp* m, cudaStream_t st, const double* p1, const double* p2, const double* g,
+                  const double* nodes, const double* normals, int M, double* out) {
+  if (M > m->bmax) {
+    set_error("warm start: %d nodes exceed the network's batch capacity %d", M, m->bmax);
+    return KFBI_ERR_ARG;
+  }
+  cudaStream_t saved = m->stream;
+  m->stream = st;
+  const int Bp = (M + TILE - 1) / TILE * TILE;
+  k_feat_state<<<blocks(Bp, 128), 128, 0, st>>>(p1, p2, g, nodes, normals, M, Bp, m->norm, m->X, nullptr);
+  KFBI_CHECK_LAUNCH();
+  int rc = mlp_forward_rows(m, Bp);
+  if (rc == KFBI_OK) {
+    k_predict<<<blocks(M, 256), 256, 0, st>>>(p1, m->o, m->norm, out, M);
+    KFBI_CHECK_LAUNCH();
+  }
+  m->stream = saved;
+  return rc;
+}
+
+}  // namespace kfbi
+
+using namespace kfbi;
+
+extern "C" {
+
+int kfbi_mlp_create(const float* params_host, const float* norm_host, int max_batch, void* stream, kfbi_mlp** out) {
+  if (!params_host || !norm_host || !out || max_batch < 1) {
+    set_error("null argument or empty batch");
+    return KFBI_ERR_ARG;
+  }
+  kfbi_mlp* m = new kfbi_mlp();
+  m->stream = (cudaStream_t)stream;
+  m->bmax = max_batch;
+  m->bpmax = (max_batch + TILE - 1) / TILE * TILE;
+  const size_t P = m->off.total, Bp = m->bpmax;
+  int rc = 0;
+  auto fail = [&](int code) {
+    kfbi_mlp_destroy(m);
+    return code;
+  };
+  if ((rc = malloc_mlp(m, &m->p, P)) || (rc = malloc_mlp(m, &m->g, P)) || (rc = malloc_mlp(m, &m->m, P)) ||
+      (rc = malloc_mlp(m, &m->v, P)) || (rc = malloc_mlp(m, &m->norm, 2 * NIN + 2)) ||
+      (rc = malloc_mlp(m, &m->W0, WID * KIN)) || (rc = malloc_mlp(m, &m->w4, WID)) ||
+      (rc = malloc_mlp(m, &m->X, Bp * KIN)) || (rc = malloc_mlp(m, &m->o, Bp)) || (rc = malloc_mlp(m, &m->d4, Bp)) ||
+      (rc = malloc_mlp(m, &m->d, Bp * WID)) || (rc = malloc_mlp(m, &m->da, Bp * WID)) ||
+      (rc = malloc_mlp(m, &m->db, Bp * WID)) || (rc = malloc_mlp(m, &m->g16, WID * KIN)) ||
+      (rc = malloc_mlp(m, &m->loss, 1)))
+    return fail(rc);
+  for (int l = 0; l < 3; ++l)
+    if ((rc = malloc_mlp(m, &m->W[l], WID * WID))) return fail(rc);
+  for (int l = 0; l < 4; ++l)
+    if ((rc = malloc_mlp(m, &m->A[l], Bp * WID)) || (rc = malloc_mlp(m, &m->Z[l], Bp * WID))) return fail(rc);
+  cudaStream_t st = m->stream;
+  if (cudaMemcpyAsync(m->p, params_host, sizeof(float) * P, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(m->norm, norm_host, sizeof(float) * (2 * NIN + 2), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(m->m, 0, sizeof(float) * P, st) != cudaSuccess ||
+      cudaMemsetAsync(m->v, 0, sizeof(float) * P, st) != cudaSuccess) {
+    set_error("MLP upload failed");
+    return fail(KFBI_ERR_CUDA);
+  }
+  if ((rc = mlp_refresh(m))) return fail(rc);
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    set_error("MLP setup failed");
+    return fail(KFBI_ERR_CUDA);
+  }
+  *out = m;
+  return KFBI_OK;
+}
+
+void kfbi_mlp_destroy(kfbi_mlp* m) {
+  if (!m) return;
+  cudaStreamSynchronize(m->stream);
+  for (void* p : m->allocs) cudaFree(p);
+  delete m;
+}
+
+int kfbi_mlp_num_params(void) { return (int)Offsets().total; }
+
+int kfbi_mlp_get(kfbi_mlp* m, float* params_host) {
+  if (!m || !params_host) {
+    set_error("null argument");
+    return KFBI_ERR_ARG;
+  }
+  KFBI_CUDA(cudaMemcpyAsync(params_host, m->p, sizeof(float) * m->off.total, cudaMemcpyDeviceToHost, m->stream));
+  KFBI_CUDA(cudaStreamSynchronize(m->stream));
+  return KFBI_OK;
+}
+
+int kfbi_mlp_forward(kfbi_mlp* m, const float* F_dev, int B, float* o_dev) {
+  if (!m || !F_dev || !o_dev) {
+    set_error("null argument");
+    return KFBI_ERR_ARG;
+  }
+  int Bp, rc;
+  if ((rc = mlp_prepare_raw(m, F_dev, B, &Bp))) return rc;
+  if ((rc = mlp_forward_rows(m, Bp))) return rc;
+  KFBI_CUDA(cudaMemcpyAsync(o_dev, m->o, sizeof(float) * B, cudaMemcpyDeviceToDevice, m->stream));
+  return KFBI_OK;
+}
+
+int kfbi_mlp_grad(kfbi_mlp* m, const float* F_dev, const float* t_dev, int B, float* loss_host, float* grad_host) {
+  if (!m || !F_dev || !t_dev) {
+    set_error("null argument");
+    return KFBI_ERR_ARG;
+  }
+  int Bp, rc;
+  if ((rc = mlp_prepare_raw(m, F_dev, B, &Bp))) return rc;
+  if ((rc = mlp_forward_rows(m, Bp))) return rc;
+  if ((rc = mlp_backward(m, t_dev, B, Bp))) return rc;
+  float l = 0.0f;
+  KFBI_CUDA(cudaMemcpyAsync(&l, m->loss, sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+  if (grad_host)
+    KFBI_CUDA(cudaMemcpyAsync(grad_host, m->g, sizeof(float) * m->off.total, cudaMemcpyDeviceToHost, m->stream));
+  KFBI_CUDA(cudaStreamSynchronize(m->stream));
+  if (loss_host) *loss_host = 0.5f * l / (float)B;
+  return KFBI_OK;
+}
+
+int kfbi_mlp_train_step(kfbi_mlp* m, const float* F_dev, const float* t_dev, int B, float lr, float* loss_host) {
+  int rc = kfbi_mlp_grad(m, F_dev, t_dev, B, loss_host, nullptr);
+  if (rc) return rc;
+  ++m->step;
+  const float c1 = 1.0f - powf(0.9f, (float)m->step), c2 = 1.0f - powf(0.999f, (float)m->step);
+  k_adam<<<blocks(m->off.total, 256), 256, 0, m->stream>>>(m->p, m->g, m->m, m->v, (int)m->off.total, lr, c1, c2);
+  KFBI_CHECK_LAUNCH();
+  return mlp_refresh(m);
+}
+
+}  // extern "C"

@@ -76,6 +76,68 @@ __global__ void k_limit(Tables t, GridParams gr, const T* __restrict__ grid, con
   out[i] = (base != nullptr ? base[i] : 0.0) + sgn * acc;
 }
 
+// same limit from a user-layout (N-1)^d grid (zero outside the interior)
+__global__ void k_limit_user(Tables t, GridParams gr, const double* __restrict__ u, const double* __restrict__ x,
+                             const double* __restrict__ base, double sgn, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.M) return;
+  const int d = gr.dim, n1 = gr.N - 1;
+  const int* c = t.n_center + (size_t)i * d;
+  const int8_t* sg = t.n_sign + (size_t)i * d;
+  const double* wn = t.n_wn + (size_t)i * t.P;
+  const int cx = c[0], cy = c[1], cz = d == 3 ? c[2] : 1;
+  auto at = [&](int dx, int dy, int dz) -> double {
+    const int64_t f = (int64_t)(cx + dx - 1) + (int64_t)(cy + dy - 1) * n1 + (d == 3 ? (int64_t)(cz + dz - 1) * n1 * n1 : 0);
+    return u[f];
+  };
+  double acc = wn[0] * at(0, 0, 0) + wn[1] * at(-1, 0, 0) + wn[2] * at(1, 0, 0) + wn[3] * at(0, -1, 0) +
+               wn[4] * at(0, 1, 0);
+  if (d == 2) {
+    acc += wn[5] * at(sg[0], sg[1], 0);
+  } else {
+    acc += wn[5] * at(0, 0, -1) + wn[6] * at(0, 0, 1);
+    acc += wn[7] * at(sg[0], sg[1], 0) + wn[8] * at(sg[0], 0, sg[2]) + wn[9] * at(0, sg[1], sg[2]);
+  }
+  if (x != nullptr) {
+    const size_t o = (size_t)i * (PATCH_MAX + 1);
+    const int K = t.n_dcnt[i];
+    for (int k = 0; k < K; ++k) acc += t.n_dw[o + k] * x[t.n_dpid[o + k]];
+  }
+  out[i] = (base != nullptr ? base[i] : 0.0) + sgn * acc;
+}
+
+// res = alpha*src - (L_h u) on the user layout, L_h the 5/7-point operator
+// with zero Dirichlet data (float64 residual of the refined box solve)
+__global__ void k_residual(GridParams gr, const double* __restrict__ src, double alpha, const double* __restrict__ u,
+                           double lambda, double* __restrict__ res, int64_t total) {
+  const int n1 = gr.N - 1;
+  const double ih2 = 1.0 / (gr.h * gr.h);
+  const double diag = -2.0 * gr.dim * ih2 - lambda;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < total; f += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(f % n1), y = (int)((f / n1) % n1);
+    const double uc = u[f];
+    double nb = (x > 0 ? u[f - 1] : 0.0) + (x < n1 - 1 ? u[f + 1] : 0.0);
+    nb += (y > 0 ? u[f - n1] : 0.0) + (y < n1 - 1 ? u[f + n1] : 0.0);
+    if (gr.dim == 3) {
+      const int z = (int)(f / ((int64_t)n1 * n1));
+      const int64_t s = (int64_t)n1 * n1;
+      nb += (z > 0 ? u[f - s] : 0.0) + (z < n1 - 1 ? u[f + s] : 0.0);
+    }
+    const double Lu = nb * ih2 + diag * uc;
+    res[f] = (src != nullptr ? alpha * src[f] : 0.0) - Lu;
+  }
+}
+
+__global__ void k_scatter_add(Tables t, const double* __restrict__ corr, double* __restrict__ g) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < t.n_irr) g[t.irr[i]] += corr[i];
+}
+
+__global__ void k_lincomb(double* __restrict__ y, double a, const double* __restrict__ x, double b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+
 __global__ void k_scatter(Tables t, const double* __restrict__ corr, double* __restrict__ g, int64_t total) {
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < total; f += (int64_t)gridDim.x * blockDim.x)
     g[f] = 0.0;
@@ -328,6 +390,29 @@ int launch_limit64(kfbi_handle* h, const double* grid, const double* x, const do
 
 int launch_limit32(kfbi_handle* h, const float* grid, const double* x, const double* base, double sgn, double* out) {
   k_limit<float><<<(h->t.M + 127) / 128, 128, 0, h->stream>>>(h->t, h->grid, grid, x, base, sgn, out);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+int launch_limit_user(kfbi_handle* h, const double* u, const double* x, const double* base, double sgn, double* out) {
+  k_limit_user<<<(h->t.M + 127) / 128, 128, 0, h->stream>>>(h->t, h->grid, u, x, base, sgn, out);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+int launch_residual(kfbi_handle* h, const double* src, double alpha, const double* corr, const double* u, double lambda,
+                    double* res) {
+  const int n1 = h->grid.N - 1;
+  const int64_t total = h->grid.dim == 3 ? (int64_t)n1 * n1 * n1 : (int64_t)n1 * n1;
+  k_residual<<<grid_blocks(total, 256), 256, 0, h->stream>>>(h->grid, src, alpha, u, lambda, res, total);
+  if (corr != nullptr && h->t.n_irr > 0)
+    k_scatter_add<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->t, corr, res);
+  KFBI_CHECK_LAUNCH_N(corr != nullptr && h->t.n_irr > 0 ? 2 : 1);
+  return KFBI_OK;
+}
+
+int launch_lincomb(kfbi_handle* h, double* y, double a, const double* x, double b, int64_t n) {
+  k_lincomb<<<grid_blocks(n, 256), 256, 0, h->stream>>>(y, a, x, b, n);
   KFBI_CHECK_LAUNCH();
   return KFBI_OK;
 }

@@ -685,6 +685,7 @@ __host__ __device__ int node_density_row(const GeomParams& gp, const GridParams&
     if (i >= gp.comp_vert_offset[cc]) comp = cc;
   double n[3], S[3][3];
   normal_shape(gp, comp, q, n, S);
+  for (int k = 0; k < 3; ++k) t.n_normal[(size_t)i * 3 + k] = n[k];
   const double Ai = AB[(size_t)i * 4];
   const double Bi[3] = {AB[(size_t)i * 4 + 1], AB[(size_t)i * 4 + 2], AB[(size_t)i * 4 + 3]};
   const size_t o = (size_t)i * (PATCH_MAX + 1);
@@ -1003,6 +1004,7 @@ int setup_build(kfbi_handle* h, const kfbi_geometry* geom) {
   double* nodes_d = nullptr;
   if ((rc = upload(h, &nodes_d, geom->nodes, (size_t)t.M * d))) return rc;
   di.nodes = nodes_d;
+  t.nodes = nodes_d;
   int32_t* vtri_d = nullptr;
   if (d == 3) {
     std::vector<int32_t> ids, cnt, vtri;
@@ -1034,6 +1036,7 @@ int setup_build(kfbi_handle* h, const kfbi_geometry* geom) {
   if ((rc = dalloc(h, &t.n_dcnt, (size_t)t.M))) return rc;
   if ((rc = dalloc(h, &t.n_dpid, (size_t)t.M * (PATCH_MAX + 1)))) return rc;
   if ((rc = dalloc(h, &t.n_dw, (size_t)t.M * (PATCH_MAX + 1)))) return rc;
+  if ((rc = dalloc(h, &t.n_normal, (size_t)t.M * 3))) return rc;
   {
     double* AB = nullptr;
     KFBI_CUDA(cudaMalloc(&AB, sizeof(double) * 4 * (size_t)t.M));

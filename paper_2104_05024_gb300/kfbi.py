@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libkfbi.so")
 
 OK, ERR_ARG, ERR_GEOMETRY, ERR_NOT_CONVERGED, ERR_NAN, ERR_CUDA, ERR_OOM, ERR_NEWTON = range(8)
 ELLIPSE2, ELLIPSOID3, STAR3, SHELL3 = 1, 2, 3, 4
-FP64, MIXED, MIXED_LEARNED = 0, 1, 2
+FP64, MIXED, MIXED_LEARNED, FP32 = 0, 1, 2, 3
 GMRES, RICHARDSON = 0, 1
 MAX_COMP = 4
 
@@ -40,7 +40,8 @@ class Opts(C.Structure):
 
 
 class Stats(C.Structure):
-    _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("rel_res", C.c_double), ("true_rel_res", C.c_double),
+    _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("warmstart", C.c_int), ("rel_res", C.c_double),
+                ("true_rel_res", C.c_double),
                 ("init_rel_res", C.c_double), ("ms", C.c_double)]
 
     def as_dict(self):
@@ -61,8 +62,58 @@ EXPORTS = [
     "kfbi_last_error", "kfbi_create", "kfbi_destroy", "kfbi_query", "kfbi_set_opts", "kfbi_solve_neumann",
     "bidomain_step", "kfbi_export_setup", "kfbi_box_solve", "kfbi_correction", "kfbi_interface_limit",
     "kfbi_apply_A", "kfbi_rhs_g", "kfbi_solve_bie", "kfbi_react_fe", "kfbi_react_be", "kfbi_export_tables",
-    "kfbi_transform_pass", "kfbi_launch_count", "kfbi_box_solve_noalloc",
+    "kfbi_transform_pass", "kfbi_launch_count", "kfbi_box_solve_noalloc", "kfbi_mlp_num_params",
+    "kfbi_mlp_create", "kfbi_mlp_destroy", "kfbi_mlp_get", "kfbi_mlp_forward", "kfbi_mlp_grad",
+    "kfbi_mlp_train_step", "kfbi_set_warmstart", "kfbi_get_densities",
 ]
+
+
+class MLP:
+    """Device copy of the warm-start network (float32 masters, bf16 copies)."""
+
+    def __init__(self, params, norm, max_batch):
+        lib = load()
+        self.params = np.ascontiguousarray(params, dtype=np.float32)
+        self.norm = np.ascontiguousarray(norm, dtype=np.float32)
+        if self.params.size != lib.kfbi_mlp_num_params() or self.norm.size != 20:
+            raise ValueError("parameter or normalisation vector has the wrong size")
+        h = C.c_void_p()
+        _check(lib.kfbi_mlp_create(self.params.ctypes.data_as(C.POINTER(C.c_float)),
+                                   self.norm.ctypes.data_as(C.POINTER(C.c_float)), int(max_batch), _stream(),
+                                   C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().kfbi_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get(self):
+        out = np.empty(load().kfbi_mlp_num_params(), np.float32)
+        _check(load().kfbi_mlp_get(self._h, out.ctypes.data_as(C.POINTER(C.c_float))))
+        return out
+
+    def forward(self, F, o):
+        _check(load().kfbi_mlp_forward(self._h, _ptr(F, "float32"), F.shape[0], _ptr(o, "float32")))
+
+    def grad(self, F, t):
+        g = np.empty(load().kfbi_mlp_num_params(), np.float32)
+        loss = C.c_float()
+        _check(load().kfbi_mlp_grad(self._h, _ptr(F, "float32"), _ptr(t, "float32"), F.shape[0], C.byref(loss),
+                                    g.ctypes.data_as(C.POINTER(C.c_float))))
+        return loss.value, g
+
+    def train_step(self, F, t, lr):
+        loss = C.c_float()
+        _check(load().kfbi_mlp_train_step(self._h, _ptr(F, "float32"), _ptr(t, "float32"), F.shape[0], lr,
+                                          C.byref(loss)))
+        return loss.value
 
 
 def box_solve_noalloc(r, v, lam, dim, N, lo=-1.0, hi=1.0):
@@ -106,8 +157,19 @@ def load(path: str = LIB_PATH):
     lib.kfbi_react_be.argtypes = [C.POINTER(FHNStruct), C.c_double, vp, vp, C.c_int64, vp]
     lib.kfbi_transform_pass.argtypes = [vp, ip, ip, C.c_double]
     lib.kfbi_box_solve_noalloc.argtypes = [ip, ip, C.c_double, C.c_double, C.c_double, vp, vp, vp]
+    fp = C.POINTER(C.c_float)
+    lib.kfbi_mlp_num_params.argtypes = []
+    lib.kfbi_mlp_create.argtypes = [fp, fp, ip, vp, C.POINTER(vp)]
+    lib.kfbi_mlp_destroy.argtypes = [vp]
+    lib.kfbi_mlp_destroy.restype = None
+    lib.kfbi_mlp_get.argtypes = [vp, fp]
+    lib.kfbi_mlp_forward.argtypes = [vp, vp, ip, vp]
+    lib.kfbi_mlp_grad.argtypes = [vp, vp, vp, ip, fp, fp]
+    lib.kfbi_mlp_train_step.argtypes = [vp, vp, vp, ip, C.c_float, fp]
+    lib.kfbi_set_warmstart.argtypes = [vp, vp]
+    lib.kfbi_get_densities.argtypes = [vp, vp, vp, vp]
     for name in EXPORTS:
-        if name not in ("kfbi_last_error", "kfbi_destroy", "kfbi_launch_count"):
+        if name not in ("kfbi_last_error", "kfbi_destroy", "kfbi_launch_count", "kfbi_mlp_destroy"):
             getattr(lib, name).restype = C.c_int
     lib.kfbi_launch_count.restype = C.c_int64
     lib.kfbi_launch_count.argtypes = []
@@ -239,6 +301,14 @@ class KFBI:
         p = lambda a: C.c_void_p(a.ctypes.data)  # noqa: E731
         _check(load().kfbi_export_tables(self._h, *[p(out[k]) for k in out]))
         return out
+
+    def set_warmstart(self, mlp):
+        self._warm = mlp
+        _check(load().kfbi_set_warmstart(self._h, None if mlp is None else mlp._h))
+
+    def get_densities(self, psi=None, psi_prev=None, g=None):
+        self.set_opts()
+        _check(load().kfbi_get_densities(self._h, _ptr(psi), _ptr(psi_prev), _ptr(g)))
 
     def transform_pass(self, pass_id, lam=0.0, precision=FP64):
         _check(load().kfbi_transform_pass(self._h, precision, pass_id, lam))
