@@ -133,6 +133,10 @@ def run_gpu(args):
     torch.cuda.synchronize()
     setup_s = time.time() - t0
     fhn = C.FHN_CONFIG
+    learn_info = None
+    if precision == K.MIXED_LEARNED:
+        learn_info, mlp = train_warmstart(args, geom, grid, cfg, dev)
+        h.set_warmstart(mlp)
     V = torch.tensor(V0, device=dev)
     w = torch.tensor(w0, device=dev)
 
@@ -154,6 +158,7 @@ def run_gpu(args):
         e1.record(stream)
         barrier()
     launches = K.launch_count() - l0
+    V_main, w_main = V.clone(), w.clone()
     ms = e0.elapsed_time(e1)
     ms_step = ms / args.steps
     if dist is not None:
@@ -218,6 +223,36 @@ def run_gpu(args):
     e2e_ms = a.elapsed_time(b) / e2e_steps
     nbytes = V.numel() * 8 * 2
 
+    # the other forms on the same workload and protocol (plain float64, mixed)
+    forms = {args.precision: {"steps_per_s": 1000.0 / ms_step, "gmres_iters_per_step": float(np.mean(iters))}}
+    if args.compare:
+        for name, p in (("fp64", K.FP64), ("mixed", K.MIXED), ("learned", K.MIXED_LEARNED)):
+            if name in forms or (p == K.MIXED_LEARNED and learn_info is None):
+                continue
+            h2 = K.KFBI(geom, grid, sigma_i=cfg.sigma_i, sigma_e=cfg.sigma_e, dt=cfg.dt, tol=cfg.tol, precision=p,
+                        restart=50, max_iter=400)
+            V2, w2 = torch.tensor(V0, device=dev), torch.tensor(w0, device=dev)
+            for _ in range(args.warmup):
+                h2.bidomain_step(fhn, V2, w2, None, nsteps=1)
+            barrier()
+            a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a2.record(stream)
+            st2 = h2.bidomain_step(fhn, V2, w2, None, nsteps=args.steps)
+            b2.record(stream)
+            barrier()
+            forms[name] = {"steps_per_s": 1000.0 * args.steps / a2.elapsed_time(b2),
+                           "gmres_iters_per_step": float(np.mean([s["iters"] for s in st2]))}
+            if name == "fp64":
+                # field differences of this form's state against the float64 state after the same steps
+                forms["max_abs_diff_vs_fp64"] = {"V": float((V_main - V2).abs().max()),
+                                                 "w": float((w_main - w2).abs().max()),
+                                                 "V_max": float(V2.abs().max())}
+            h2.close()
+    if "fp64" in forms:
+        for name in ("mixed", "learned"):
+            if name in forms:
+                forms[name]["speedup_vs_fp64"] = forms[name]["steps_per_s"] / forms["fp64"]["steps_per_s"]
+
     result = {
         "metric": METRIC, "value": world * 1000.0 / ms_step, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -228,6 +263,9 @@ def run_gpu(args):
                    "setup_s": round(setup_s, 2), "n_irregular": h.info["n_irregular"],
                    "n_crossings": h.info["n_crossings"]},
         "gmres_iters_per_step": float(np.mean(iters)),
+        "outer_per_step": float(np.mean([s["outer"] for s in stats])),
+        "forms": forms,
+        "learned": learn_info if learn_info is None else dict(learn_info, used=int(sum(s["warmstart"] for s in stats))),
         "roofline": roof,
         "clocks": clk.summary(),
         "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": nbytes,
@@ -242,6 +280,38 @@ def run_gpu(args):
     h.close()
     if rank == 0:
         print(json.dumps(result), flush=True)
+
+
+def train_warmstart(args, geom, grid, cfg, dev):
+    """Train the warm-start network on densities of runs with the 8 training
+    stimulus locations (untimed); the timed run's stimulus is held out."""
+    import torch
+
+    import paper_2104_05024_gb300.kfbi as K
+    from paper_2104_05024_gb300 import warmstart as WS
+    from kfbi_workloads import configs as C
+
+    t0 = time.time()
+    normals = C.analytic_normals(geom)
+    Fs, Ts = [], []
+    for c in C.midwall_centers(C.TRAIN_SEEDS):
+        h = K.KFBI(geom, grid, sigma_i=cfg.sigma_i, sigma_e=cfg.sigma_e, dt=cfg.dt, tol=cfg.tol, precision=K.MIXED,
+                   restart=50, max_iter=400)
+        V = torch.tensor(C.ball_stimulus(grid, c, 0.1), device=dev)
+        w = torch.zeros_like(V)
+        F, T = WS.collect(h, C.FHN_CONFIG, V, w, args.train_steps, geom.nodes, normals)
+        Fs.append(F)
+        Ts.append(T)
+        h.close()
+    F, T = torch.cat(Fs), torch.cat(Ts)
+    norm = WS.fit_norm(F, T)
+    mlp = K.MLP(WS.init_params(0), norm, max(8192, geom.M))
+    losses = WS.train(mlp, F, T, norm, epochs=args.train_epochs, batch=4096, lr=2e-3)
+    torch.cuda.synchronize()
+    info = {"train_rows": int(F.shape[0]), "train_seeds": len(C.TRAIN_SEEDS), "steps_per_seed": args.train_steps,
+            "epochs": args.train_epochs, "loss_first_last": [round(losses[0], 5), round(losses[-1], 5)],
+            "train_s": round(time.time() - t0, 1)}
+    return info, mlp
 
 
 # -------------------------------------------------------------- CPU oracle
@@ -289,9 +359,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="kfbi", choices=["kfbi", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "learned"])
+    ap.add_argument("--precision", default="learned", choices=["fp64", "mixed", "learned"])
+    ap.add_argument("--no-compare", dest="compare", action="store_false",
+                    help="skip timing the other precision forms on the same workload")
     ap.add_argument("--N", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--train-steps", type=int, default=12, help="Strang steps per training stimulus (learned form)")
+    ap.add_argument("--train-epochs", type=int, default=8)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

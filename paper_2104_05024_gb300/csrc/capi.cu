@@ -108,7 +108,7 @@ int norm2(kfbi_handle* h, const double* v, double* slot, double* out) {
 // float64-accurate box solve from float32 transforms (iterative refinement
 // with the float64 5/7-point residual): u = L_h^{-1}(alpha*src + corr) on the
 // user layout.  Each round gains about -log10(kappa(L_h) eps_32) digits.
-constexpr int REFINE_ROUNDS = 3;
+constexpr int REFINE_ROUNDS = 2;
 
 int refined_solve(kfbi_handle* h, const double* src, double alpha, const double* corr, double lambda, double* u) {
   SolveArgs sa;
@@ -251,7 +251,10 @@ int richardson(kfbi_handle* h, int prec, double lambda, const double* g, double*
 // GMRES with iterative refinement (Carson and Higham): the outer residual
 // r = g - A psi uses float64-accurate box solves, the inner correction solve
 // A delta = r runs GMRES with float32 box solves and float64 Arnoldi.
-int gmres_ir(kfbi_handle* h, double lambda, const double* g, double* psi, kfbi_stats* st) {
+// fallback (optional): an alternative initial guess whose residual norm is
+// fallback_res; it replaces psi when psi's first residual is larger.
+int gmres_ir(kfbi_handle* h, double lambda, const double* g, double* psi, kfbi_stats* st,
+             const double* fallback = nullptr, double fallback_res = 0.0) {
   const int M = h->t.M;
   double* r = h->w.r2;
   double* delta = h->w.tmp2;
@@ -267,6 +270,14 @@ int gmres_ir(kfbi_handle* h, double lambda, const double* g, double* psi, kfbi_s
     if ((rc = apply_A_acc(h, lambda, psi, r, -1.0, g))) return rc;
     double rn;
     if ((rc = norm2(h, r, slot, &rn))) return rc;
+    if (outer == 0 && fallback != nullptr && rn > fallback_res) {
+      // the residual judges the guess: go back to the alternative
+      if ((rc = vec_copy(h, psi, fallback, M))) return rc;
+      fallback = nullptr;
+      st->warmstart = 0;
+      continue;
+    }
+    fallback = nullptr;
     rel = rn / gnorm;
     if (outer == 0) st->init_rel_res = rel;
     if (!std::isfinite(rel)) {
@@ -387,6 +398,7 @@ int kfbi_create(const kfbi_geometry* geom, const kfbi_grid* grid, double sigma_i
     set_error("cudaMemset failed");
     return fail(KFBI_ERR_CUDA);
   }
+  if ((rc = make_tma_maps(h))) return fail(rc);
   if ((rc = dalloc(h, &h->w.corr, (size_t)h->t.n_irr))) return fail(rc);
   if ((rc = dalloc(h, &h->w.xvec, (size_t)2 * M))) return fail(rc);
   if ((rc = dalloc(h, &h->w.vecs, (size_t)(m + 1) * M))) return fail(rc);
@@ -401,6 +413,8 @@ int kfbi_create(const kfbi_geometry* geom, const kfbi_grid* grid, double sigma_i
   if ((rc = dalloc(h, &h->w.psi_prev2, (size_t)M))) return fail(rc);
   if ((rc = dalloc(h, &h->w.psi_save, (size_t)M))) return fail(rc);
   if ((rc = dalloc(h, &h->w.psi_learn, (size_t)M))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.g_prev, (size_t)M))) return fail(rc);
+  cudaMemsetAsync(h->w.g_prev, 0, sizeof(double) * (size_t)M, h->stream);
   cudaMemsetAsync(h->w.psi_prev2, 0, sizeof(double) * (size_t)M, h->stream);
   if ((rc = dalloc(h, &h->w.u64, (size_t)grid_points(h)))) return fail(rc);
   if ((rc = dalloc(h, &h->w.res64, (size_t)grid_points(h)))) return fail(rc);
@@ -603,6 +617,15 @@ int kfbi_solve_neumann(kfbi_handle* h, double lambda, const double* f_dev, const
   if ((rc = norm2(h, h->w.r, slot, &rn))) return rc;
   if ((rc = norm2(h, h->w.g, slot, &gn))) return rc;
   st.true_rel_res = gn > 0 ? rn / gn : rn;
+  {
+    int herr = 0;
+    KFBI_CUDA(cudaMemcpyAsync(&herr, h->w.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    KFBI_CUDA(cudaStreamSynchronize(h->stream));
+    if (herr & DEVERR_TIMEOUT) {
+      set_error("a bounded wait on a TMA transfer gave up; results are invalid");
+      return KFBI_ERR_CUDA;
+    }
+  }
   st.ms = elapsed_ms(t0);
   if (stats) *stats = st;
   return solve_rc;
@@ -633,24 +656,29 @@ int bidomain_step(kfbi_handle* h, const kfbi_fhn* p, double* V_dev, double* w_de
     // initial density: the previous one, or the learned prediction when its
     // float32 residual is smaller
     if ((rc = vec_copy(h, h->w.psi_save, h->w.psi_prev, h->t.M))) return rc;
-    if (h->opts.precision == KFBI_MIXED_LEARNED && h->warm != nullptr && h->n_hist >= 2) {
+    const double* fallback = nullptr;
+    double fallback_res = 0.0;
+    if (h->opts.precision == KFBI_MIXED_LEARNED && h->opts.solver == KFBI_GMRES && h->warm != nullptr &&
+        h->n_hist >= 2) {
       if ((rc = mlp_warmstart(h->warm, h->stream, h->w.psi_prev, h->w.psi_prev2, h->w.g, h->t.nodes, h->t.n_normal,
                               h->t.M, h->w.psi_learn)))
         return rc;
-      double rl, rp;
+      // residual of the previous density: A psi^{n-1} = g^{n-1} up to the
+      // previous tolerance, so g^n - A psi^{n-1} = g^n - g^{n-1} needs no solve
       double* slot = h->w.small + small_nrm2(h->opts.restart);
-      if ((rc = apply_A(h, KFBI_FP32, lam, h->w.psi_learn, h->w.r, -1.0, h->w.g))) return rc;
-      if ((rc = norm2(h, h->w.r, slot, &rl))) return rc;
-      if ((rc = apply_A(h, KFBI_FP32, lam, h->w.psi_prev, h->w.r, -1.0, h->w.g))) return rc;
-      if ((rc = norm2(h, h->w.r, slot, &rp))) return rc;
-      if (rl < rp) {
-        if ((rc = vec_copy(h, h->w.psi_prev, h->w.psi_learn, h->t.M))) return rc;
-        st.warmstart = 1;
-      }
+      if ((rc = vec_copy(h, h->w.tmp, h->w.g_prev, h->t.M))) return rc;
+      if ((rc = vec_axpby(h, h->w.tmp, 1.0, h->w.g, -1.0, h->t.M))) return rc;
+      if ((rc = norm2(h, h->w.tmp, slot, &fallback_res))) return rc;
+      if ((rc = vec_copy(h, h->w.psi_prev, h->w.psi_learn, h->t.M))) return rc;
+      fallback = h->w.psi_save;
+      st.warmstart = 1;
     }
-    const int src = solve_bie(h, prec, lam, h->w.g, h->w.psi_prev, &st);
+    const int src = fallback != nullptr
+                        ? gmres_ir(h, lam, h->w.g, h->w.psi_prev, &st, fallback, fallback_res)
+                        : solve_bie(h, prec, lam, h->w.g, h->w.psi_prev, &st);
     if (src != KFBI_OK && src != KFBI_ERR_NOT_CONVERGED) return src;
     if ((rc = vec_copy(h, h->w.psi_prev2, h->w.psi_save, h->t.M))) return rc;
+    if ((rc = vec_copy(h, h->w.g_prev, h->w.g, h->t.M))) return rc;
     ++h->n_hist;
     if (src == KFBI_ERR_NOT_CONVERGED) final_rc = src;
     // V <- 2 (v_V + v_B(psi)) - V, one solve of the combined right-hand side
@@ -683,6 +711,10 @@ int bidomain_step(kfbi_handle* h, const kfbi_fhn* p, double* V_dev, double* w_de
   int herr = 0;
   KFBI_CUDA(cudaMemcpyAsync(&herr, h->w.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   KFBI_CUDA(cudaStreamSynchronize(h->stream));
+  if (herr & DEVERR_TIMEOUT) {
+    set_error("a bounded wait on a TMA transfer gave up; results are invalid");
+    return KFBI_ERR_CUDA;
+  }
   if (herr & DEVERR_NEWTON) {
     set_error("backward-Euler Newton iteration hit its cap");
     return KFBI_ERR_NEWTON;

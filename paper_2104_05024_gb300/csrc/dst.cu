@@ -24,6 +24,8 @@
 // In 2-D the middle pass is the y solve.
 #include <cuda_runtime.h>
 
+#include <cudaTypedefs.h>
+
 #include <cmath>
 
 #include "internal.cuh"
@@ -33,15 +35,26 @@ namespace {
 
 constexpr int NT = 256;
 
-template <typename T, int N>
-struct Cfg {
-  static constexpr int W = sizeof(T) == 8 ? (N >= 384 ? 16 : (N < 32 ? N : 32))
-                                          : (N >= 384 ? 32 : (N < 64 ? N : 64));
-  static constexpr int RS = W + 1;
+// Tile geometry: N transform rows by W independent lines, row stride RS
+// (W + 1 pads against bank conflicts of transposed loads; W for dense TMA
+// tiles), G threads per line in the scan.
+template <typename T_, int N_, int W_, int RS_>
+struct Tile {
+  using T = T_;
+  static constexpr int N = N_, W = W_, RS = RS_;
   static constexpr int L = N / 2;
   static constexpr int G = NT / W;
   static constexpr size_t smem_elems = (size_t)N * RS + (size_t)G * W + 4 * N;
 };
+
+template <typename T, int N>
+struct WSel {
+  static constexpr int W = sizeof(T) == 8 ? (N >= 384 ? 16 : (N < 32 ? N : 32))
+                                          : (N >= 384 ? 32 : (N < 64 ? N : 64));
+};
+
+template <typename T, int N>
+struct Cfg : Tile<T, N, WSel<T, N>::W, WSel<T, N>::W + 1> {};
 
 __host__ __device__ constexpr int pick_radix(int L) {
   return (L % 8 == 0) ? 8 : (L % 4 == 0) ? 4 : (L % 2 == 0) ? 2 : (L % 3 == 0) ? 3 : 0;
@@ -133,9 +146,9 @@ struct Dft<T, 3> {
 // One in-place Stockham stage of radix R on the complex sequence stored in
 // rows (2m, 2m+1) of every column.  All reads precede all writes.  Ls is a
 // compile-time constant so every index division is a shift or a constant.
-template <typename T, int N, int R, int Ls>
-__device__ __forceinline__ void fft_stage(T* s, const T* tw) {
-  using C = Cfg<T, N>;
+template <typename C, int R, int Ls>
+__device__ __forceinline__ void fft_stage(typename C::T* s, const typename C::T* tw) {
+  using T = typename C::T;
   constexpr int L = C::L, W = C::W, RS = C::RS;
   constexpr int NB = (L / R) * W;
   constexpr int PER = NB > 0 ? (NB + NT - 1) / NT : 1;  // stages never taken for small L still compile
@@ -182,26 +195,26 @@ __device__ __forceinline__ void fft_stage(T* s, const T* tw) {
 }
 
 // the stage sequence of a length-Lrem transform, unrolled at compile time
-template <typename T, int N, int Ls, int Lrem>
+template <typename C, int Ls, int Lrem>
 struct Stages {
-  static __device__ __forceinline__ void run(T* s, const T* tw) {
+  static __device__ __forceinline__ void run(typename C::T* s, const typename C::T* tw) {
     constexpr int R = pick_radix(Lrem);
-    fft_stage<T, N, R, Ls>(s, tw);
-    Stages<T, N, Ls * R, Lrem / R>::run(s, tw);
+    fft_stage<C, R, Ls>(s, tw);
+    Stages<C, Ls * R, Lrem / R>::run(s, tw);
   }
 };
-template <typename T, int N, int Ls>
-struct Stages<T, N, Ls, 1> {
-  static __device__ __forceinline__ void run(T*, const T*) {}
+template <typename C, int Ls>
+struct Stages<C, Ls, 1> {
+  static __device__ __forceinline__ void run(typename C::T*, const typename C::T*) {}
 };
 
 // DST-I of every column of the tile s[N][RS] (rows 1..N-1 in, rows 1..N-1
 // out, row 0 holds 0).  tw = e^{i pi j / N}, j = 0..2N-1 (interleaved re, im);
 // tot = scan scratch [G][W].
-template <typename T, int N>
-__device__ void dst1_tile(T* s, const T* tw, T* tot) {
-  using C = Cfg<T, N>;
-  constexpr int L = C::L, W = C::W, RS = C::RS, G = C::G;
+template <typename C>
+__device__ void dst1_tile(typename C::T* s, const typename C::T* tw, typename C::T* tot) {
+  using T = typename C::T;
+  constexpr int N = C::N, L = C::L, W = C::W, RS = C::RS, G = C::G;
   // sine pre-fold: y_j = sin(j pi/N)(x_j + x_{N-j}) + (x_j - x_{N-j})/2
   for (int idx = threadIdx.x; idx < (N / 2 + 1) * W; idx += NT) {
     const int c = idx % W, j = idx / W;
@@ -219,7 +232,7 @@ __device__ void dst1_tile(T* s, const T* tw, T* tot) {
   }
   __syncthreads();
   // complex FFT of length L = N/2 on z_m = y_{2m} + i y_{2m+1}
-  Stages<T, N, 1, L>::run(s, tw);
+  Stages<C, 1, L>::run(s, tw);
   // real-DFT split: Y_k = (A + conj B)/2 - i w_k (A - conj B)/2, A = Z_k,
   // B = Z_{L-k}, w_k = e^{2 pi i k / N}; store I_k in row 2k, R_k in row 2k+1
   for (int idx = threadIdx.x; idx < (L / 2 + 1) * W; idx += NT) {
@@ -314,7 +327,7 @@ __global__ void __launch_bounds__(NT) k_xfwd(T* __restrict__ a, const double* __
     }
   }
   __syncthreads();
-  dst1_tile<T, N>(s, tw, tot);
+  dst1_tile<Cfg<T, N>>(s, tw, tot);
   const size_t plane = (size_t)z * N * N;
   for (int idx = threadIdx.x; idx < N * W; idx += NT) {
     const int x = idx % N, c = idx / N;
@@ -342,7 +355,7 @@ __global__ void __launch_bounds__(NT) k_xinv(T* __restrict__ a, bool keep, doubl
     s[x * RS + c] = a[plane + (size_t)(y0 + c) * N + x];
   }
   __syncthreads();
-  dst1_tile<T, N>(s, tw, tot);
+  dst1_tile<Cfg<T, N>>(s, tw, tot);
   for (int idx = threadIdx.x; idx < N * W; idx += NT) {
     const int x = idx % N, c = idx / N, y = y0 + c;
     const T v = s[x * RS + c];
@@ -380,7 +393,7 @@ __global__ void __launch_bounds__(NT) k_strided(T* __restrict__ a, size_t row_st
     s[k * RS + c] = base[(size_t)k * row_stride + c];
   }
   __syncthreads();
-  dst1_tile<T, N>(s, tw, tot);
+  dst1_tile<Cfg<T, N>>(s, tw, tot);
   if (SOLVE) {
     const T muq = DIM == 3 ? mu1[q] : (T)0;
     for (int idx = threadIdx.x; idx < N * W; idx += NT) {
@@ -390,12 +403,152 @@ __global__ void __launch_bounds__(NT) k_strided(T* __restrict__ a, size_t row_st
       s[k * RS + c] = v;
     }
     __syncthreads();
-    dst1_tile<T, N>(s, tw, tot);
+    dst1_tile<Cfg<T, N>>(s, tw, tot);
   }
   for (int idx = threadIdx.x; idx < N * W; idx += NT) {
     const int c = idx % W, k = idx / W;
     base[(size_t)k * row_stride + c] = s[k * RS + c];
   }
+}
+
+// ------------------------------------------- TMA-fed strided passes (float32)
+// Persistent blocks walk over [N x 32] tiles of the padded float grid.  One
+// thread issues a TMA tensor load of the next tile into the other shared
+// buffer (completion counted on an mbarrier) while all threads transform the
+// current tile; the finished tile goes back by a TMA tensor store.  Every
+// wait is bounded: on timeout the block records DEVERR_TIMEOUT and returns.
+constexpr int TMA_W = 32;
+constexpr long TMA_WAIT_CAP = 1L << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_store3(const CUtensorMap* map, const void* src, int x, int y, int z) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(z), "r"(smem_addr(src))
+               : "memory");
+}
+__device__ __forceinline__ void tma_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void tma_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void tma_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+template <int N>
+using TmaTile = Tile<float, N, TMA_W, TMA_W>;
+
+template <int N>
+constexpr size_t tma_smem_bytes() {
+  return (2 * (size_t)N * TMA_W + (size_t)TmaTile<N>::G * TMA_W + 4 * (size_t)N) * sizeof(float) + 2 * sizeof(uint64_t);
+}
+
+// mode 0: tiles [y][x-chunk] of plane z = q; mode 1: tiles [z][x-chunk] of row y = q
+template <int N, bool SOLVE>
+__global__ void __launch_bounds__(NT, 2) k_strided_tma(const __grid_constant__ CUtensorMap map, int mode,
+                                                    const float* __restrict__ mu1, float lambda, float scale,
+                                                    const float* __restrict__ tw_g, int* __restrict__ err) {
+  using C = TmaTile<N>;
+  constexpr int W = TMA_W, NX = N / TMA_W;
+  constexpr int ntiles = NX * (N - 1);
+  constexpr uint32_t bytes = (uint32_t)(N * W * sizeof(float));
+  extern __shared__ __align__(128) unsigned char smem_tma[];
+  float* buf0 = reinterpret_cast<float*>(smem_tma);
+  float* buf1 = buf0 + N * W;
+  float* tot = buf1 + N * W;
+  float* tw = tot + C::G * W;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tw + 4 * N);
+  for (int i = threadIdx.x; i < 4 * N; i += NT) tw[i] = tw_g[i];
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto coords = [&](int t, int& x, int& y, int& z) {
+    const int q = t / NX + 1;
+    x = (t % NX) * W;
+    y = mode == 0 ? 0 : q;
+    z = mode == 0 ? q : 0;
+  };
+  int t = blockIdx.x;
+  if (t < ntiles && threadIdx.x == 0) {
+    int x, y, z;
+    coords(t, x, y, z);
+    mbar_expect_tx(&bar[0], bytes);
+    tma_load3(buf0, &map, &bar[0], x, y, z);
+  }
+  for (int i = 0; t < ntiles; t += gridDim.x, ++i) {
+    const int b = i & 1;
+    float* s = b ? buf1 : buf0;
+    float* s_next = b ? buf0 : buf1;
+    const int tn = t + gridDim.x;
+    if (threadIdx.x == 0 && tn < ntiles) {
+      tma_wait_read_all();  // the store of the previous tile has left s_next
+      int x, y, z;
+      coords(tn, x, y, z);
+      mbar_expect_tx(&bar[b ^ 1], bytes);
+      tma_load3(s_next, &map, &bar[b ^ 1], x, y, z);
+    }
+    bool ok = false;
+    for (long it = 0; it < TMA_WAIT_CAP; ++it)
+      if (mbar_try_wait(&bar[b], (uint32_t)((i >> 1) & 1))) {
+        ok = true;
+        break;
+      }
+    if (!ok) {
+      if (threadIdx.x == 0) atomicOr(err, DEVERR_TIMEOUT);
+      return;
+    }
+    // one DST body, run twice around the spectral divide when solving (keeps
+    // a single inlined copy and the register count of the plain pass)
+#pragma unroll 1
+    for (int rep = 0; rep < (SOLVE ? 2 : 1); ++rep) {
+      dst1_tile<C>(s, tw, tot);
+      if (SOLVE && rep == 0) {
+        const int q = t / NX + 1, x0 = (t % NX) * W;
+        const float muq = mu1[q];
+        for (int idx = threadIdx.x; idx < N * W; idx += NT) {
+          const int c = idx % W, k = idx / W, p = x0 + c;
+          float v = 0.0f;
+          if (k > 0 && p > 0) v = s[k * W + c] * (scale / (mu1[k] + mu1[p] + muq - lambda));
+          s[k * W + c] = v;
+        }
+        __syncthreads();
+      }
+    }
+    fence_async_shared();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int x, y, z;
+      coords(t, x, y, z);
+      tma_store3(&map, s, x, y, z);
+      tma_commit();
+    }
+  }
+  if (threadIdx.x == 0) tma_wait_all();
 }
 
 // opt each kernel into its dynamic shared-memory size once per process
@@ -415,6 +568,47 @@ int prep(K kernel, size_t smem) {
   return KFBI_OK;
 }
 
+// one strided 3-D pass (mode 0: along y, mode 1: along z); float32 grids of
+// 32 <= N <= 256 go through the TMA-fed persistent kernel
+template <typename T, int N>
+int launch_strided3(kfbi_handle* h, int mode, bool solve, T* work, const T* mu1, T lam, T scale, const T* tw) {
+  using C = Cfg<T, N>;
+  cudaStream_t st = h->stream;
+  int rc;
+  if constexpr (sizeof(T) == 4 && N >= TMA_W && N <= 256) {
+    if (h->tma) {
+      constexpr size_t smem = tma_smem_bytes<N>();
+      const CUtensorMap& map = mode == 0 ? h->tmap_y32 : h->tmap_z32;
+      int dev = 0, sms = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      const int tiles = (N / TMA_W) * (N - 1);
+      const int grid = tiles < 2 * sms ? tiles : 2 * sms;
+      if (solve) {
+        if ((rc = prep(k_strided_tma<N, true>, smem))) return rc;
+        k_strided_tma<N, true><<<grid, NT, smem, st>>>(map, mode, mu1, lam, scale, tw, h->w.err);
+      } else {
+        if ((rc = prep(k_strided_tma<N, false>, smem))) return rc;
+        k_strided_tma<N, false><<<grid, NT, smem, st>>>(map, mode, mu1, lam, scale, tw, h->w.err);
+      }
+      return KFBI_OK;
+    }
+  }
+  const size_t smem = C::smem_elems * sizeof(T);
+  const size_t NN = (size_t)N * N;
+  dim3 grid(N / C::W, N - 1);
+  if (solve) {
+    if ((rc = prep(k_strided<T, N, true, 3>, smem))) return rc;
+    k_strided<T, N, true, 3><<<grid, NT, smem, st>>>(work, mode == 0 ? N : NN, mode == 0 ? NN : N, 1, mu1, lam,
+                                                     scale, tw);
+  } else {
+    if ((rc = prep(k_strided<T, N, false, 3>, smem))) return rc;
+    k_strided<T, N, false, 3><<<grid, NT, smem, st>>>(work, mode == 0 ? N : NN, mode == 0 ? NN : N, 1, mu1, lam,
+                                                      scale, tw);
+  }
+  return KFBI_OK;
+}
+
 template <typename T, int N>
 int run_solve(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1, const T* tw) {
   using C = Cfg<T, N>;
@@ -425,17 +619,14 @@ int run_solve(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1, const 
   const Tables& t = h->t;
   const T lam = (T)sa.lambda;
   const T scale = (T)(dim == 3 ? (2.0 / N) * (2.0 / N) * (2.0 / N) : (2.0 / N) * (2.0 / N));
-  const size_t NN = (size_t)N * N;
   int rc;
   if (dim == 3) {
     dim3 grid(N / W, N - 1);
     if ((rc = prep(k_xfwd<T, N, 3>, smem))) return rc;
     k_xfwd<T, N, 3><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.corr, t.irr, t.line_start, tw);
-    if ((rc = prep(k_strided<T, N, false, 3>, smem))) return rc;
-    k_strided<T, N, false, 3><<<grid, NT, smem, st>>>(work, N, NN, 1, mu1, lam, scale, tw);
-    if ((rc = prep(k_strided<T, N, true, 3>, smem))) return rc;
-    k_strided<T, N, true, 3><<<grid, NT, smem, st>>>(work, NN, N, 1, mu1, lam, scale, tw);
-    k_strided<T, N, false, 3><<<grid, NT, smem, st>>>(work, N, NN, 1, mu1, lam, scale, tw);
+    if ((rc = launch_strided3<T, N>(h, 0, false, work, mu1, lam, scale, tw))) return rc;
+    if ((rc = launch_strided3<T, N>(h, 1, true, work, mu1, lam, scale, tw))) return rc;
+    if ((rc = launch_strided3<T, N>(h, 0, false, work, mu1, lam, scale, tw))) return rc;
     if ((rc = prep(k_xinv<T, N, 3>, smem))) return rc;
     k_xinv<T, N, 3><<<grid, NT, smem, st>>>(work, true, sa.out_user, sa.aux, sa.beta, sa.gamma, tw);
   } else {
@@ -470,15 +661,14 @@ int run_pass(kfbi_handle* h, int pass, double lambda, T* work, const T* mu1, con
       if ((rc = prep(k_xfwd<T, N, 3>, smem))) return rc;
       k_xfwd<T, N, 3><<<grid, NT, smem, st>>>(work, nullptr, 1.0, nullptr, t.irr, t.line_start, tw);
     } else if (pass == 1) {
-      if ((rc = prep(k_strided<T, N, false, 3>, smem))) return rc;
-      k_strided<T, N, false, 3><<<grid, NT, smem, st>>>(work, N, NN, 1, mu1, lam, scale, tw);
+      if ((rc = launch_strided3<T, N>(h, 0, false, work, mu1, lam, scale, tw))) return rc;
     } else if (pass == 2) {
-      if ((rc = prep(k_strided<T, N, true, 3>, smem))) return rc;
-      k_strided<T, N, true, 3><<<grid, NT, smem, st>>>(work, NN, N, 1, mu1, lam, scale, tw);
+      if ((rc = launch_strided3<T, N>(h, 1, true, work, mu1, lam, scale, tw))) return rc;
     } else {
       if ((rc = prep(k_xinv<T, N, 3>, smem))) return rc;
       k_xinv<T, N, 3><<<grid, NT, smem, st>>>(work, true, nullptr, nullptr, 1.0, 0.0, tw);
     }
+    (void)NN;
   } else {
     if (pass == 0) {
       if ((rc = prep(k_xfwd<T, N, 2>, smem))) return rc;
@@ -530,6 +720,39 @@ int dispatch_pass(kfbi_handle* h, int pass, double lambda, T* work, const T* mu1
 }
 
 }  // namespace
+
+// TMA descriptors of the padded float32 grid for the strided passes (3-D,
+// 32 <= N <= 256): boxes of 32 x-values by N rows along y or along z.
+int make_tma_maps(kfbi_handle* h) {
+  h->tma = false;
+  const int N = h->grid.N;
+  if (h->grid.dim != 3 || N < TMA_W || N > 256) return KFBI_OK;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || fn == nullptr) {
+    cudaGetLastError();
+    return KFBI_OK;  // no tensor maps: the strided passes keep their plain loads
+  }
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)N};
+  const cuuint64_t strides[2] = {(cuuint64_t)N * sizeof(float), (cuuint64_t)N * N * sizeof(float)};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const cuuint32_t box_y[3] = {(cuuint32_t)TMA_W, (cuuint32_t)N, 1};
+  const cuuint32_t box_z[3] = {(cuuint32_t)TMA_W, 1, (cuuint32_t)N};
+  CUresult r1 = encode(&h->tmap_y32, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->w.grid32, dims, strides, box_y, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r2 = encode(&h->tmap_z32, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->w.grid32, dims, strides, box_z, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d, %d)", (int)r1, (int)r2);
+    return KFBI_ERR_CUDA;
+  }
+  h->tma = true;
+  return KFBI_OK;
+}
 
 int transform_pass(kfbi_handle* h, int precision, int pass, double lambda) {
   if (precision == KFBI_FP64) return dispatch_pass<double>(h, pass, lambda, h->w.grid64, h->t.mu, h->t.tw64);

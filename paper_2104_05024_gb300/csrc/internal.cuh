@@ -2,6 +2,7 @@
 // library: the handle, device tables, launch helpers.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -20,6 +21,7 @@ constexpr int MAX_RESTART = 64;
 constexpr int DEVERR_GEOMETRY = 1;
 constexpr int DEVERR_NEWTON = 2;
 constexpr int DEVERR_SINGULAR = 4;
+constexpr int DEVERR_TIMEOUT = 8;   // a bounded wait on a TMA transfer gave up
 
 void set_error(const char* fmt, ...);
 
@@ -126,6 +128,7 @@ struct Workspace {
   double* psi_prev2 = nullptr;    // [M] density of the solve before the previous one
   double* psi_save = nullptr;     // [M]
   double* psi_learn = nullptr;    // [M] learned initial guess
+  double* g_prev = nullptr;       // [M] right-hand side of the previous diffusion solve
   double* u64 = nullptr;          // user-layout float64 grid (refined solutions)
   double* res64 = nullptr;        // user-layout float64 grid (refinement residuals)
   double* host_small = nullptr;   // pinned host scalars
@@ -148,6 +151,9 @@ struct kfbi_handle {
   bool have_prev = false;
   int n_hist = 0;                 // completed diffusion solves (density history)
   kfbi_mlp* warm = nullptr;       // learned warm start (not owned)
+  // TMA descriptors of the float32 padded grid: [N x 32] tiles along y and z
+  CUtensorMap tmap_y32, tmap_z32;
+  bool tma = false;
 };
 
 namespace kfbi {
@@ -190,6 +196,7 @@ int box_solve64(kfbi_handle* h, const SolveArgs& a, double* work);
 int box_solve32(kfbi_handle* h, const SolveArgs& a, float* work);
 int dst_supported(int N);
 int transform_pass(kfbi_handle* h, int precision, int pass, double lambda);
+int make_tma_maps(kfbi_handle* h);
 
 // ops.cu
 int launch_correction(kfbi_handle* h, const double* x, double* corr);

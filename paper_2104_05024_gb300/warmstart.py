@@ -19,6 +19,26 @@ def _torch():
     return torch
 
 
+N_IN, WIDTH, N_HIDDEN = 9, 128, 4
+
+
+def init_params(seed: int = 0) -> np.ndarray:
+    """Packed float32 parameters: uniform He initialisation of the hidden
+    layers (bound sqrt(6 / fan_in)), zero biases and a zero output layer, so
+    the untrained network returns the previous density."""
+    rng = np.random.default_rng(seed)
+    dims = [N_IN] + [WIDTH] * N_HIDDEN + [1]
+    out = []
+    for l in range(len(dims) - 1):
+        fan_in, fan_out = dims[l], dims[l + 1]
+        if fan_out > 1:
+            out.append(rng.uniform(-np.sqrt(6.0 / fan_in), np.sqrt(6.0 / fan_in), fan_out * fan_in))
+        else:
+            out.append(np.zeros(fan_out * fan_in))
+        out.append(np.zeros(fan_out))
+    return np.concatenate(out).astype(np.float32)
+
+
 def collect(h: K.KFBI, fhn, V, w, steps, nodes, normals, first=3):
     """Advance (V, w) by `steps` Strang steps on handle h and return the rows
     (F [rows, 9] float32, T [rows] float32 raw targets) of steps >= first."""

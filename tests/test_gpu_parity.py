@@ -75,9 +75,12 @@ def test_box_solve(name, lam):
     assert rel(v.cpu().numpy(), ref) < 1e-12
     g.box_solve(cuda(r), v, lam, precision=K.FP32)
     assert rel(v.cpu().numpy(), ref) < 2e-5
-    # float32 transforms refined by float64 residuals reach float64 accuracy
+    # float32 transforms refined by two rounds of float64 residuals reach the
+    # float64 parity bar
     g.box_solve(cuda(r), v, lam, precision=K.MIXED)
-    assert rel(v.cpu().numpy(), ref) < 1e-11
+    err = rel(v.cpu().numpy(), ref)
+    print(f"refined float32 box solve {name}: rel err {err:.2e}")
+    assert err < TOL64
 
 
 @pytest.mark.parametrize("N", [8, 16, 128])
