@@ -108,7 +108,7 @@ int norm2(kfbi_handle* h, const double* v, double* slot, double* out) {
 // float64-accurate box solve from float32 transforms (iterative refinement
 // with the float64 5/7-point residual): u = L_h^{-1}(alpha*src + corr) on the
 // user layout.  Each round gains about -log10(kappa(L_h) eps_32) digits.
-constexpr int REFINE_ROUNDS = 2;
+constexpr int REFINE_ROUNDS = 1;
 
 int refined_solve(kfbi_handle* h, const double* src, double alpha, const double* corr, double lambda, double* u) {
   SolveArgs sa;
@@ -285,8 +285,9 @@ int gmres_ir(kfbi_handle* h, double lambda, const double* g, double* psi, kfbi_s
       return KFBI_ERR_NAN;
     }
     if (rel <= tol || inner_total >= h->opts.max_iter || outer >= 20) break;
-    // inner tolerance relative to ||r||: four digits, or just what the target needs
-    double tin = std::max(1e-4, 0.3 * tol * gnorm / rn);
+    // inner tolerance relative to ||r||: as far as the float32 operator can
+    // go (six digits), or just what the target needs
+    double tin = std::max(1e-6, 0.3 * tol * gnorm / rn);
     if (tin > 0.5) tin = 0.5;
     KFBI_CUDA(cudaMemsetAsync(delta, 0, sizeof(double) * (size_t)M, h->stream));
     kfbi_stats in{};

@@ -49,8 +49,7 @@ struct Tile {
 
 template <typename T, int N>
 struct WSel {
-  static constexpr int W = sizeof(T) == 8 ? (N >= 384 ? 16 : (N < 32 ? N : 32))
-                                          : (N >= 384 ? 32 : (N < 64 ? N : 64));
+  static constexpr int W = sizeof(T) == 8 ? (N >= 384 ? 16 : (N < 32 ? N : 32)) : (N < 32 ? N : 32);
 };
 
 template <typename T, int N>
