@@ -256,6 +256,12 @@ int kfbi_set_warmstart(kfbi_handle* h, kfbi_mlp* m);
 /* After a Strang step: psi_dev <- psi^n, psi_prev_dev <- psi^{n-1} and
  * g_dev <- g^n of the last diffusion solve (each may be NULL).               */
 int kfbi_get_densities(kfbi_handle* h, double* psi_dev, double* psi_prev_dev, double* g_dev);
+/* Restore the density history saved by kfbi_get_densities (checkpoint /
+ * resume): n_solves is the number of diffusion solves the history stands for
+ * (0 clears it).  With the same state (V, w) a resumed float64 run repeats
+ * the uninterrupted one bit for bit.                                         */
+int kfbi_set_densities(kfbi_handle* h, const double* psi_dev, const double* psi_prev_dev, const double* g_dev,
+                       int n_solves);
 
 /* One pass of the box solver on the handle's padded work grid, for timing
  * the transform kernels in isolation: pass 0 = x forward (no right-hand

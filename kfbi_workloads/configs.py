@@ -157,10 +157,10 @@ def gaussian_rhs(grid: Grid, seed: int = 0, count: int = 32) -> np.ndarray:
     amp, width, cen = gaussian_bumps(seed, count)
     ax = grid.axis()
     e = [np.exp(-((ax[None, :] - cen[:, a:a + 1]) ** 2) / (2.0 * width[:, None] ** 2)) for a in range(3)]
-    f = np.zeros(grid.shape)
-    for k in range(count):
-        f += amp[k] * (e[2][k][:, None, None] * e[1][k][None, :, None] * e[0][k][None, None, :])
-    return f
+    n = ax.size
+    # [z*y, k] @ [k, x]: the bump sum as one matrix product
+    zy = (amp[:, None, None] * e[2][:, :, None] * e[1][:, None, :]).reshape(count, n * n)
+    return (zy.T @ e[0]).reshape(n, n, n)
 
 
 # ------------------------------------------------------- manufactured solutions

@@ -107,8 +107,10 @@ int norm2(kfbi_handle* h, const double* v, double* slot, double* out) {
 
 // float64-accurate box solve from float32 transforms (iterative refinement
 // with the float64 5/7-point residual): u = L_h^{-1}(alpha*src + corr) on the
-// user layout.  Each round gains about -log10(kappa(L_h) eps_32) digits.
-constexpr int REFINE_ROUNDS = 1;
+// user layout.  Each round gains about -log10(kappa(L_h) eps_32) digits: one
+// round leaves a relative error near 1e-12 at 256^3 and 1e-10 at 512^3, so
+// GMRES tolerances below 1e-9 take a second round.
+int refine_rounds(const kfbi_handle* h) { return h->opts.tol < 1e-9 ? 2 : 1; }
 
 int refined_solve(kfbi_handle* h, const double* src, double alpha, const double* corr, double lambda, double* u) {
   SolveArgs sa;
@@ -119,7 +121,8 @@ int refined_solve(kfbi_handle* h, const double* src, double alpha, const double*
   sa.out_user = u;
   int rc = box_solve32(h, sa, h->w.grid32);
   if (rc) return rc;
-  for (int r = 0; r < REFINE_ROUNDS; ++r) {
+  const int rounds = refine_rounds(h);
+  for (int r = 0; r < rounds; ++r) {
     if ((rc = launch_residual(h, src, alpha, corr, u, lambda, h->w.res64))) return rc;
     SolveArgs sr;
     sr.src = h->w.res64;
@@ -739,6 +742,32 @@ int kfbi_get_densities(kfbi_handle* h, double* psi_dev, double* psi_prev_dev, do
   if (psi_dev) KFBI_CUDA(cudaMemcpyAsync(psi_dev, h->w.psi_prev, n, cudaMemcpyDeviceToDevice, h->stream));
   if (psi_prev_dev) KFBI_CUDA(cudaMemcpyAsync(psi_prev_dev, h->w.psi_prev2, n, cudaMemcpyDeviceToDevice, h->stream));
   if (g_dev) KFBI_CUDA(cudaMemcpyAsync(g_dev, h->w.g, n, cudaMemcpyDeviceToDevice, h->stream));
+  return KFBI_OK;
+}
+
+int kfbi_set_densities(kfbi_handle* h, const double* psi_dev, const double* psi_prev_dev, const double* g_dev,
+                       int n_solves) {
+  if (int rc = check_handle(h)) return rc;
+  if (n_solves < 0) {
+    set_error("negative solve count");
+    return KFBI_ERR_ARG;
+  }
+  const size_t n = sizeof(double) * (size_t)h->t.M;
+  if (n_solves == 0) {
+    KFBI_CUDA(cudaMemsetAsync(h->w.psi_prev, 0, n, h->stream));
+    KFBI_CUDA(cudaMemsetAsync(h->w.psi_prev2, 0, n, h->stream));
+    KFBI_CUDA(cudaMemsetAsync(h->w.g_prev, 0, n, h->stream));
+  } else {
+    if (!psi_dev || !psi_prev_dev || !g_dev) {
+      set_error("null density history");
+      return KFBI_ERR_ARG;
+    }
+    KFBI_CUDA(cudaMemcpyAsync(h->w.psi_prev, psi_dev, n, cudaMemcpyDeviceToDevice, h->stream));
+    KFBI_CUDA(cudaMemcpyAsync(h->w.psi_prev2, psi_prev_dev, n, cudaMemcpyDeviceToDevice, h->stream));
+    KFBI_CUDA(cudaMemcpyAsync(h->w.g_prev, g_dev, n, cudaMemcpyDeviceToDevice, h->stream));
+    KFBI_CUDA(cudaMemcpyAsync(h->w.g, g_dev, n, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  h->n_hist = n_solves;
   return KFBI_OK;
 }
 

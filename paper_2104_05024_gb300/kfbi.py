@@ -64,7 +64,7 @@ EXPORTS = [
     "kfbi_apply_A", "kfbi_rhs_g", "kfbi_solve_bie", "kfbi_react_fe", "kfbi_react_be", "kfbi_export_tables",
     "kfbi_transform_pass", "kfbi_launch_count", "kfbi_box_solve_noalloc", "kfbi_mlp_num_params",
     "kfbi_mlp_create", "kfbi_mlp_destroy", "kfbi_mlp_get", "kfbi_mlp_forward", "kfbi_mlp_grad",
-    "kfbi_mlp_train_step", "kfbi_set_warmstart", "kfbi_get_densities",
+    "kfbi_mlp_train_step", "kfbi_set_warmstart", "kfbi_get_densities", "kfbi_set_densities",
 ]
 
 
@@ -168,6 +168,7 @@ def load(path: str = LIB_PATH):
     lib.kfbi_mlp_train_step.argtypes = [vp, vp, vp, ip, C.c_float, fp]
     lib.kfbi_set_warmstart.argtypes = [vp, vp]
     lib.kfbi_get_densities.argtypes = [vp, vp, vp, vp]
+    lib.kfbi_set_densities.argtypes = [vp, vp, vp, vp, ip]
     for name in EXPORTS:
         if name not in ("kfbi_last_error", "kfbi_destroy", "kfbi_launch_count", "kfbi_mlp_destroy"):
             getattr(lib, name).restype = C.c_int
@@ -309,6 +310,27 @@ class KFBI:
     def get_densities(self, psi=None, psi_prev=None, g=None):
         self.set_opts()
         _check(load().kfbi_get_densities(self._h, _ptr(psi), _ptr(psi_prev), _ptr(g)))
+
+    def set_densities(self, psi, psi_prev, g, n_solves):
+        self.set_opts()
+        _check(load().kfbi_set_densities(self._h, _ptr(psi), _ptr(psi_prev), _ptr(g), int(n_solves)))
+
+    def checkpoint(self, V, w, n_solves):
+        """Host copy of everything a resumed run needs: state, density history,
+        solve count (the caller stores it, e.g. with numpy.savez)."""
+        import torch
+        M = self.M
+        psi, psi1, g = (torch.empty(M, dtype=torch.float64, device=V.device) for _ in range(3))
+        self.get_densities(psi, psi1, g)
+        return {"V": V.cpu().numpy(), "w": w.cpu().numpy(), "psi": psi.cpu().numpy(), "psi_prev": psi1.cpu().numpy(),
+                "g": g.cpu().numpy(), "n_solves": int(n_solves)}
+
+    def restore(self, ck, device):
+        """Inverse of checkpoint(): returns (V, w) on the device."""
+        import torch
+        t = {k: torch.tensor(ck[k], dtype=torch.float64, device=device) for k in ("V", "w", "psi", "psi_prev", "g")}
+        self.set_densities(t["psi"], t["psi_prev"], t["g"], int(ck["n_solves"]))
+        return t["V"], t["w"]
 
     def transform_pass(self, pass_id, lam=0.0, precision=FP64):
         _check(load().kfbi_transform_pass(self._h, precision, pass_id, lam))
