@@ -137,12 +137,13 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    precision = {"fp64": K.FP64, "mixed": K.MIXED, "learned": K.MIXED_LEARNED}[args.precision]
+    precision = {"fp64": K.FP64, "mixed": K.MIXED, "projection": K.MIXED, "learned": K.MIXED_LEARNED}[args.precision]
+    warm = K.WARM_PROJECTION if args.precision == "projection" else K.WARM_PREVIOUS
 
     geom, grid, cfg, V0, w0 = workload(args.N, rank)
     t0 = time.time()
     h = K.KFBI(geom, grid, sigma_i=cfg.sigma_i, sigma_e=cfg.sigma_e, dt=cfg.dt, tol=cfg.tol, precision=precision,
-               restart=50, max_iter=400)
+               restart=50, max_iter=400, warm=warm)
     torch.cuda.synchronize()
     setup_s = time.time() - t0
     fhn = C.FHN_CONFIG
@@ -237,11 +238,14 @@ def run_gpu(args):
     # the other forms on the same workload and protocol (plain float64, mixed)
     forms = {args.precision: {"steps_per_s": 1000.0 / ms_step, "gmres_iters_per_step": float(np.mean(iters))}}
     if args.compare:
-        for name, p in (("fp64", K.FP64), ("mixed", K.MIXED), ("learned", K.MIXED_LEARNED)):
+        for name, p, wm in (("fp64", K.FP64, K.WARM_PREVIOUS), ("mixed", K.MIXED, K.WARM_PREVIOUS),
+                            ("projection", K.MIXED, K.WARM_PROJECTION), ("learned", K.MIXED_LEARNED, None)):
             if name in forms or (p == K.MIXED_LEARNED and learn_info is None):
                 continue
             h2 = K.KFBI(geom, grid, sigma_i=cfg.sigma_i, sigma_e=cfg.sigma_e, dt=cfg.dt, tol=cfg.tol, precision=p,
-                        restart=50, max_iter=400)
+                        restart=50, max_iter=400, warm=wm or K.WARM_PREVIOUS)
+            if p == K.MIXED_LEARNED:
+                h2.set_warmstart(mlp)
             V2, w2 = torch.tensor(V0, device=dev), torch.tensor(w0, device=dev)
             for _ in range(args.warmup):
                 h2.bidomain_step(fhn, V2, w2, None, nsteps=1)
@@ -260,7 +264,7 @@ def run_gpu(args):
                                                  "V_max": float(V2.abs().max())}
             h2.close()
     if "fp64" in forms:
-        for name in ("mixed", "learned"):
+        for name in ("mixed", "projection", "learned"):
             if name in forms:
                 forms[name]["speedup_vs_fp64"] = forms[name]["steps_per_s"] / forms["fp64"]["steps_per_s"]
 
@@ -456,9 +460,10 @@ def run_heldout(args):
         V0 = torch.tensor(C.ball_stimulus(grid, c, 0.1), device=dev)
         row = {"seed": seed, "center": [round(x, 4) for x in c]}
         out = {}
-        for name, prec in (("previous", K.MIXED), ("learned", K.MIXED_LEARNED)):
+        for name, prec, wm in (("previous", K.MIXED, K.WARM_PREVIOUS), ("projection", K.MIXED, K.WARM_PROJECTION),
+                               ("learned", K.MIXED_LEARNED, K.WARM_PREVIOUS)):
             h = K.KFBI(geom, grid, sigma_i=cfg.sigma_i, sigma_e=cfg.sigma_e, dt=cfg.dt, tol=cfg.tol, precision=prec,
-                       restart=50, max_iter=400)
+                       restart=50, max_iter=400, warm=wm)
             if prec == K.MIXED_LEARNED:
                 h.set_warmstart(mlp)
             V, w = V0.clone(), torch.zeros_like(V0)
@@ -468,8 +473,10 @@ def run_heldout(args):
                          "guess_used": int(sum(s["warmstart"] for s in st))}
             out[name] = V
             h.close()
-        row["speedup"] = round(row["learned"]["steps_per_s"] / row["previous"]["steps_per_s"], 3)
-        row["max_abs_diff_V"] = float((out["learned"] - out["previous"]).abs().max())
+        row["speedup_vs_previous"] = {k: round(row[k]["steps_per_s"] / row["previous"]["steps_per_s"], 3)
+                                      for k in ("projection", "learned")}
+        row["max_abs_diff_V_vs_previous"] = {k: float((out[k] - out["previous"]).abs().max())
+                                             for k in ("projection", "learned")}
         rows.append(row)
     mlp.close()
     print(json.dumps({"metric": "held-out stimuli: GMRES iterations and Strang steps/s, learned vs previous guess",
@@ -523,7 +530,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="kfbi", choices=["kfbi", "reference"])
-    ap.add_argument("--precision", default="learned", choices=["fp64", "mixed", "learned"])
+    ap.add_argument("--precision", default="learned", choices=["fp64", "mixed", "projection", "learned"],
+                    help="fp64 / mixed: previous-density start; projection: mixed with the history projection; "
+                         "learned: projection corrected by the network")
     ap.add_argument("--no-compare", dest="compare", action="store_false",
                     help="skip timing the other precision forms on the same workload")
     ap.add_argument("--N", type=int, default=256)

@@ -61,6 +61,14 @@ extern "C" {
 #define KFBI_GMRES 0
 #define KFBI_RICHARDSON 1
 
+/* initial density of each diffusion solve in bidomain_step */
+#define KFBI_WARM_PREVIOUS 0   /* the previous solve's density                */
+#define KFBI_WARM_PROJECTION 1 /* least-squares combination of the last
+                                  KFBI_HISTORY densities, chosen by their known
+                                  right-hand sides, plus one step of the simple
+                                  iteration (Section 4)                        */
+#define KFBI_HISTORY 8
+
 #define KFBI_MAX_COMP 4
 
 /*
@@ -108,12 +116,15 @@ typedef struct {
   int max_iter;    /* total operator applications allowed                    */
   double gamma;    /* Richardson parameter (0.8 in Section 7)               */
   void* stream;    /* cudaStream_t                                           */
+  int warm;        /* KFBI_WARM_PREVIOUS / KFBI_WARM_PROJECTION (the learned
+                      form always starts from the projection)               */
 } kfbi_opts;
 
 typedef struct {
   int iters;            /* operator applications inside the Krylov solver     */
   int outer;            /* outer refinement sweeps (mixed precision)          */
-  int warmstart;        /* initial guess: 0 previous density, 1 learned       */
+  int warmstart;        /* initial guess kept: 0 previous density or
+                           projection, 1 learned                            */
   double rel_res;       /* solver's residual estimate ||r|| / ||g||           */
   double true_rel_res;  /* recomputed ||g^N - du^+/dn|| / ||g|| (or -1)       */
   double init_rel_res;  /* residual of the initial guess                      */
@@ -262,6 +273,17 @@ int kfbi_get_densities(kfbi_handle* h, double* psi_dev, double* psi_prev_dev, do
  * the uninterrupted one bit for bit.                                         */
 int kfbi_set_densities(kfbi_handle* h, const double* psi_dev, const double* psi_prev_dev, const double* g_dev,
                        int n_solves);
+/* The density history of the projection warm start: KFBI_HISTORY slots of
+ * M doubles each (psi and its right-hand side g; the density of solve s sits
+ * in slot s mod KFBI_HISTORY) and the number of solves it stands for.  get
+ * copies out (device buffers of KFBI_HISTORY*M doubles, n_solves on the
+ * host); set restores them (checkpoint / resume).                          */
+int kfbi_get_history(kfbi_handle* h, double* psi_hist_dev, double* g_hist_dev, int* n_solves);
+int kfbi_set_history(kfbi_handle* h, const double* psi_hist_dev, const double* g_hist_dev, int n_solves);
+/* After a projection (or learned) step: the projected density psi_F and its
+ * residual r_F = g - A psi_F (known without an operator application from the
+ * history's right-hand sides), M doubles each, device.                      */
+int kfbi_get_projection(kfbi_handle* h, double* psiF_dev, double* rF_dev);
 
 /* One pass of the box solver on the handle's padded work grid, for timing
  * the transform kernels in isolation: pass 0 = x forward (no right-hand

@@ -153,9 +153,13 @@ int rhs_g_acc(kfbi_handle* h, double lambda, const double* src, double alpha, co
   return launch_limit_user(h, h->w.u64, nullptr, gN, -1.0, g);
 }
 
-// GMRES(m) with CGS2 Arnoldi on A psi = g; psi in: initial guess, out: solution
+// GMRES(m) with CGS2 Arnoldi on A psi = g; psi in: initial guess, out: solution.
+// zero_guess: psi is known to be zero, so the first residual is g itself.
+// fallback (optional): an alternative initial guess with known residual norm
+// fallback_res (relative to nothing: ||g - A fallback||); it replaces psi
+// when psi's first residual is larger.
 int gmres(kfbi_handle* h, int prec, double lambda, const double* g, double* psi, kfbi_stats* st, double tol,
-          int max_iter) {
+          int max_iter, bool zero_guess = false, const double* fallback = nullptr, double fallback_res = 0.0) {
   const int M = h->t.M;
   const int m = h->opts.restart;
   double* V = h->w.vecs;
@@ -171,11 +175,24 @@ int gmres(kfbi_handle* h, int prec, double lambda, const double* g, double* psi,
   double rel = 0.0;
   bool first = true;
   for (;;) {
-    if ((rc = apply_A(h, prec, lambda, psi, r, -1.0, g))) return rc;  // r = g - A psi
+    if (first && zero_guess) {
+      if ((rc = vec_copy(h, r, g, M))) return rc;
+    } else if ((rc = apply_A(h, prec, lambda, psi, r, -1.0, g))) {  // r = g - A psi
+      return rc;
+    }
     if ((rc = vec_dots(h, r, 1, M, r, s + small_nrm2(m)))) return rc;
     double b2;
     if ((rc = read_scalar(h, s + small_nrm2(m), &b2))) return rc;
     const double beta = std::sqrt(b2);
+    if (first && fallback != nullptr && beta > fallback_res) {
+      // the residual judges the guess: go back to the alternative
+      if ((rc = vec_copy(h, psi, fallback, M))) return rc;
+      fallback = nullptr;
+      zero_guess = false;
+      st->warmstart = 0;
+      continue;
+    }
+    fallback = nullptr;
     rel = beta / gnorm;
     if (first) {
       st->init_rel_res = rel;
@@ -294,7 +311,7 @@ int gmres_ir(kfbi_handle* h, double lambda, const double* g, double* psi, kfbi_s
     if (tin > 0.5) tin = 0.5;
     KFBI_CUDA(cudaMemsetAsync(delta, 0, sizeof(double) * (size_t)M, h->stream));
     kfbi_stats in{};
-    rc = gmres(h, KFBI_MIXED, lambda, r, delta, &in, tin, h->opts.max_iter - inner_total);
+    rc = gmres(h, KFBI_MIXED, lambda, r, delta, &in, tin, h->opts.max_iter - inner_total, true);
     if (rc != KFBI_OK && rc != KFBI_ERR_NOT_CONVERGED) return rc;
     inner_total += in.iters;
     if ((rc = vec_axpby(h, psi, 1.0, delta, 1.0, M))) return rc;
@@ -306,10 +323,91 @@ int gmres_ir(kfbi_handle* h, double lambda, const double* g, double* psi, kfbi_s
   return rel <= tol ? KFBI_OK : KFBI_ERR_NOT_CONVERGED;
 }
 
-int solve_bie(kfbi_handle* h, int prec, double lambda, const double* g, double* psi, kfbi_stats* st) {
+int solve_bie(kfbi_handle* h, int prec, double lambda, const double* g, double* psi, kfbi_stats* st,
+              const double* fallback = nullptr, double fallback_res = 0.0) {
   if (h->opts.solver == KFBI_RICHARDSON) return richardson(h, prec, lambda, g, psi, st);
-  if (prec != KFBI_FP64) return gmres_ir(h, lambda, g, psi, st);
-  return gmres(h, prec, lambda, g, psi, st, h->opts.tol, h->opts.max_iter);
+  if (prec != KFBI_FP64) return gmres_ir(h, lambda, g, psi, st, fallback, fallback_res);
+  return gmres(h, prec, lambda, g, psi, st, h->opts.tol, h->opts.max_iter, false, fallback, fallback_res);
+}
+
+// ------------------------------------------------ projection warm start
+// The densities psi_s of earlier solves and their right-hand sides g_s
+// satisfy A psi_s = g_s to the solver tolerance, so for any coefficients c
+// the residual of psi_F = sum c_s psi_s is g - sum c_s g_s without applying
+// A.  c minimises that residual (normal equations of the k <= KFBI_HISTORY
+// stored g_s, Cholesky on the host, columns that are numerically dependent
+// on earlier ones dropped).
+int project_history(kfbi_handle* h, const double* g, double* rF_norm) {
+  const int M = h->t.M;
+  const int k = h->hist_count < KFBI_HISTORY ? h->hist_count : KFBI_HISTORY;
+  double* G = h->w.proj;             // [k][k]
+  double* b = G + KFBI_HISTORY * KFBI_HISTORY;
+  double* cdev = b + KFBI_HISTORY;
+  int rc;
+  if ((rc = vec_copy(h, h->w.rF, g, M))) return rc;
+  KFBI_CUDA(cudaMemsetAsync(h->w.psiF, 0, sizeof(double) * (size_t)M, h->stream));
+  if (k > 0) {
+    for (int i = 0; i < k; ++i)
+      if ((rc = vec_dots(h, h->w.hist_g, k, M, h->w.hist_g + (size_t)i * M, G + i * k))) return rc;
+    if ((rc = vec_dots(h, h->w.hist_g, k, M, g, b))) return rc;
+    double* hs = h->w.host_small;
+    KFBI_CUDA(cudaMemcpyAsync(hs, G, sizeof(double) * (size_t)(KFBI_HISTORY * KFBI_HISTORY + KFBI_HISTORY),
+                              cudaMemcpyDeviceToHost, h->stream));
+    KFBI_CUDA(cudaStreamSynchronize(h->stream));
+    double A[KFBI_HISTORY][KFBI_HISTORY], L[KFBI_HISTORY][KFBI_HISTORY] = {}, y[KFBI_HISTORY] = {},
+                                          c[KFBI_HISTORY] = {}, rhs[KFBI_HISTORY];
+    bool keep[KFBI_HISTORY];
+    double dmax = 0.0;
+    for (int i = 0; i < k; ++i) {
+      for (int j = 0; j < k; ++j) A[i][j] = hs[i * k + j];
+      rhs[i] = hs[KFBI_HISTORY * KFBI_HISTORY + i];
+      dmax = std::max(dmax, A[i][i]);
+    }
+    // Cholesky with dependent columns skipped
+    for (int j = 0; j < k; ++j) {
+      double d = A[j][j];
+      for (int p = 0; p < j; ++p)
+        if (keep[p]) d -= L[j][p] * L[j][p];
+      keep[j] = d > 1e-13 * dmax && dmax > 0.0;
+      if (!keep[j]) continue;
+      L[j][j] = std::sqrt(d);
+      for (int i = j + 1; i < k; ++i) {
+        double v = A[i][j];
+        for (int p = 0; p < j; ++p)
+          if (keep[p]) v -= L[i][p] * L[j][p];
+        L[i][j] = v / L[j][j];
+      }
+    }
+    for (int i = 0; i < k; ++i) {
+      if (!keep[i]) continue;
+      double v = rhs[i];
+      for (int p = 0; p < i; ++p)
+        if (keep[p]) v -= L[i][p] * y[p];
+      y[i] = v / L[i][i];
+    }
+    for (int i = k - 1; i >= 0; --i) {
+      if (!keep[i]) continue;
+      double v = y[i];
+      for (int p = i + 1; p < k; ++p)
+        if (keep[p]) v -= L[p][i] * c[p];
+      c[i] = v / L[i][i];
+    }
+    for (int i = 0; i < k; ++i) hs[i] = c[i];
+    KFBI_CUDA(cudaMemcpyAsync(cdev, hs, sizeof(double) * (size_t)k, cudaMemcpyHostToDevice, h->stream));
+    if ((rc = vec_update(h, h->w.psiF, h->w.hist_psi, k, M, cdev, 1.0))) return rc;
+    if ((rc = vec_update(h, h->w.rF, h->w.hist_g, k, M, cdev, -1.0))) return rc;
+  }
+  return norm2(h, h->w.rF, h->w.small + small_nrm2(h->opts.restart), rF_norm);
+}
+
+int push_history(kfbi_handle* h, const double* psi, const double* g) {
+  const int M = h->t.M;
+  const size_t slot = (size_t)(h->hist_count % KFBI_HISTORY) * M;
+  int rc;
+  if ((rc = vec_copy(h, h->w.hist_psi + slot, psi, M))) return rc;
+  if ((rc = vec_copy(h, h->w.hist_g + slot, g, M))) return rc;
+  ++h->hist_count;
+  return KFBI_OK;
 }
 
 int check_handle(kfbi_handle* h) {
@@ -423,7 +521,12 @@ int kfbi_create(const kfbi_geometry* geom, const kfbi_grid* grid, double sigma_i
   if ((rc = dalloc(h, &h->w.u64, (size_t)grid_points(h)))) return fail(rc);
   if ((rc = dalloc(h, &h->w.res64, (size_t)grid_points(h)))) return fail(rc);
   cudaMemsetAsync(h->w.psi_prev, 0, sizeof(double) * (size_t)M, h->stream);
-  if (cudaMallocHost((void**)&h->w.host_small, 64 * sizeof(double)) != cudaSuccess) {
+  if ((rc = dalloc(h, &h->w.hist_psi, (size_t)KFBI_HISTORY * M))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.hist_g, (size_t)KFBI_HISTORY * M))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.psiF, (size_t)M))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.rF, (size_t)M))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.proj, (size_t)KFBI_HISTORY * (KFBI_HISTORY + 2)))) return fail(rc);
+  if (cudaMallocHost((void**)&h->w.host_small, 128 * sizeof(double)) != cudaSuccess) {
     set_error("cudaMallocHost failed");
     return fail(KFBI_ERR_OOM);
   }
@@ -662,8 +765,15 @@ int bidomain_step(kfbi_handle* h, const kfbi_fhn* p, double* V_dev, double* w_de
     if ((rc = vec_copy(h, h->w.psi_save, h->w.psi_prev, h->t.M))) return rc;
     const double* fallback = nullptr;
     double fallback_res = 0.0;
-    if (h->opts.precision == KFBI_MIXED_LEARNED && h->opts.solver == KFBI_GMRES && h->warm != nullptr &&
-        h->n_hist >= 2) {
+    const bool learned = h->opts.precision == KFBI_MIXED_LEARNED && h->warm != nullptr;
+    if ((h->opts.warm == KFBI_WARM_PROJECTION || learned) && h->opts.solver == KFBI_GMRES && h->hist_count >= 1) {
+      // psi_F from the history, then one step of the simple iteration
+      // psi_F + 2 gamma r_F; psi_F itself (residual known) is the fallback
+      if ((rc = project_history(h, h->w.g, &fallback_res))) return rc;
+      if ((rc = vec_copy(h, h->w.psi_prev, h->w.psiF, h->t.M))) return rc;
+      if ((rc = vec_axpby(h, h->w.psi_prev, 2.0 * h->opts.gamma, h->w.rF, 1.0, h->t.M))) return rc;
+      fallback = h->w.psiF;
+    } else if (learned && h->opts.solver == KFBI_GMRES && h->n_hist >= 2) {
       if ((rc = mlp_warmstart(h->warm, h->stream, h->w.psi_prev, h->w.psi_prev2, h->w.g, h->t.nodes, h->t.n_normal,
                               h->t.M, h->w.psi_learn)))
         return rc;
@@ -677,12 +787,11 @@ int bidomain_step(kfbi_handle* h, const kfbi_fhn* p, double* V_dev, double* w_de
       fallback = h->w.psi_save;
       st.warmstart = 1;
     }
-    const int src = fallback != nullptr
-                        ? gmres_ir(h, lam, h->w.g, h->w.psi_prev, &st, fallback, fallback_res)
-                        : solve_bie(h, prec, lam, h->w.g, h->w.psi_prev, &st);
+    const int src = solve_bie(h, prec, lam, h->w.g, h->w.psi_prev, &st, fallback, fallback_res);
     if (src != KFBI_OK && src != KFBI_ERR_NOT_CONVERGED) return src;
     if ((rc = vec_copy(h, h->w.psi_prev2, h->w.psi_save, h->t.M))) return rc;
     if ((rc = vec_copy(h, h->w.g_prev, h->w.g, h->t.M))) return rc;
+    if ((rc = push_history(h, h->w.psi_prev, h->w.g))) return rc;
     ++h->n_hist;
     if (src == KFBI_ERR_NOT_CONVERGED) final_rc = src;
     // V <- 2 (v_V + v_B(psi)) - V, one solve of the combined right-hand side
@@ -768,6 +877,57 @@ int kfbi_set_densities(kfbi_handle* h, const double* psi_dev, const double* psi_
     KFBI_CUDA(cudaMemcpyAsync(h->w.g, g_dev, n, cudaMemcpyDeviceToDevice, h->stream));
   }
   h->n_hist = n_solves;
+  h->hist_count = 0;  // the projection history starts again from this state
+  return KFBI_OK;
+}
+
+int kfbi_get_history(kfbi_handle* h, double* psi_hist_dev, double* g_hist_dev, int* n_solves) {
+  if (int rc = check_handle(h)) return rc;
+  const size_t n = sizeof(double) * (size_t)KFBI_HISTORY * h->t.M;
+  if (psi_hist_dev) KFBI_CUDA(cudaMemcpyAsync(psi_hist_dev, h->w.hist_psi, n, cudaMemcpyDeviceToDevice, h->stream));
+  if (g_hist_dev) KFBI_CUDA(cudaMemcpyAsync(g_hist_dev, h->w.hist_g, n, cudaMemcpyDeviceToDevice, h->stream));
+  if (n_solves) *n_solves = h->hist_count;
+  return KFBI_OK;
+}
+
+int kfbi_set_history(kfbi_handle* h, const double* psi_hist_dev, const double* g_hist_dev, int n_solves) {
+  if (int rc = check_handle(h)) return rc;
+  if (n_solves < 0 || (n_solves > 0 && (!psi_hist_dev || !g_hist_dev))) {
+    set_error("bad density history");
+    return KFBI_ERR_ARG;
+  }
+  const int M = h->t.M;
+  const size_t n = sizeof(double) * (size_t)KFBI_HISTORY * M;
+  if (n_solves > 0) {
+    KFBI_CUDA(cudaMemcpyAsync(h->w.hist_psi, psi_hist_dev, n, cudaMemcpyDeviceToDevice, h->stream));
+    KFBI_CUDA(cudaMemcpyAsync(h->w.hist_g, g_hist_dev, n, cudaMemcpyDeviceToDevice, h->stream));
+    // the previous-density state follows from the two latest slots
+    const size_t s1 = (size_t)((n_solves - 1) % KFBI_HISTORY) * M;
+    int rc;
+    if ((rc = vec_copy(h, h->w.psi_prev, h->w.hist_psi + s1, M))) return rc;
+    if ((rc = vec_copy(h, h->w.g, h->w.hist_g + s1, M))) return rc;
+    if ((rc = vec_copy(h, h->w.g_prev, h->w.hist_g + s1, M))) return rc;
+    if (n_solves >= 2) {
+      const size_t s2 = (size_t)((n_solves - 2) % KFBI_HISTORY) * M;
+      if ((rc = vec_copy(h, h->w.psi_prev2, h->w.hist_psi + s2, M))) return rc;
+    } else {
+      KFBI_CUDA(cudaMemsetAsync(h->w.psi_prev2, 0, sizeof(double) * (size_t)M, h->stream));
+    }
+  } else {
+    KFBI_CUDA(cudaMemsetAsync(h->w.psi_prev, 0, sizeof(double) * (size_t)M, h->stream));
+    KFBI_CUDA(cudaMemsetAsync(h->w.psi_prev2, 0, sizeof(double) * (size_t)M, h->stream));
+    KFBI_CUDA(cudaMemsetAsync(h->w.g_prev, 0, sizeof(double) * (size_t)M, h->stream));
+  }
+  h->hist_count = n_solves;
+  h->n_hist = n_solves;
+  return KFBI_OK;
+}
+
+int kfbi_get_projection(kfbi_handle* h, double* psiF_dev, double* rF_dev) {
+  if (int rc = check_handle(h)) return rc;
+  const size_t n = sizeof(double) * (size_t)h->t.M;
+  if (psiF_dev) KFBI_CUDA(cudaMemcpyAsync(psiF_dev, h->w.psiF, n, cudaMemcpyDeviceToDevice, h->stream));
+  if (rF_dev) KFBI_CUDA(cudaMemcpyAsync(rF_dev, h->w.rF, n, cudaMemcpyDeviceToDevice, h->stream));
   return KFBI_OK;
 }
 

@@ -28,6 +28,7 @@
 
 #include <cmath>
 
+#include "dst_reg.cuh"
 #include "internal.cuh"
 
 namespace kfbi {
@@ -44,7 +45,8 @@ struct Tile {
   static constexpr int N = N_, W = W_, RS = RS_;
   static constexpr int L = N / 2;
   static constexpr int G = NT / W;
-  static constexpr size_t smem_elems = (size_t)N * RS + (size_t)G * W + 4 * N;
+  // tile, scan totals, twiddles e^{i pi j/N} (2N complex), sines (register path)
+  static constexpr size_t smem_elems = (size_t)N * RS + (size_t)G * W + 4 * N + N;
 };
 
 template <typename T, int N>
@@ -288,6 +290,41 @@ __device__ __forceinline__ void load_twiddles(T* tw_s, const T* tw_g) {
   for (int i = threadIdx.x; i < 4 * N; i += NT) tw_s[i] = tw_g[i];
 }
 
+// float32 tiles of 32 <= N <= 256 lines take the register-resident DST
+template <typename T, int N>
+constexpr bool kRegDst = sizeof(T) == 4 && N >= 32 && N <= 256;
+
+// sines sin(pi j / N) for the register path's pre-fold (imaginary parts of tw)
+template <typename T, int N>
+__device__ __forceinline__ void load_sines(T* sinv, const T* tw_g) {
+  if constexpr (kRegDst<T, N>)
+    for (int i = threadIdx.x; i < N; i += NT) sinv[i] = tw_g[2 * i + 1];
+}
+
+// the DST-I of every column of the tile, rows 1..N-1 (post: map of the
+// outputs, register path only)
+template <typename C, class Post = regdst::Identity>
+__device__ __forceinline__ void dst_tile(typename C::T* s, const typename C::T* tw, const typename C::T* sinv,
+                                         typename C::T* tot, const Post& post = Post()) {
+  if constexpr (kRegDst<typename C::T, C::N>) {
+    regdst::dst1_tile_reg<regdst::Geo<C::N, C::RS>>(s, sinv, reinterpret_cast<const regdst::cf2*>(tw), tot, post);
+  } else {
+    dst1_tile<C>(s, tw, tot);
+  }
+}
+
+// spectral divide v * scale / (mu1[j] + mu1[p] + mu1[q] - lambda) applied to
+// the forward transform's outputs as they are written (register path)
+struct DivPost {
+  const float* mu;  // mu1 in shared memory
+  float base;       // mu1[p] + mu1[q] - lambda
+  float scale;
+  bool zero;        // boundary column p = 0
+  __device__ __forceinline__ float operator()(int j, float v) const {
+    return zero ? 0.0f : v * __fdividef(scale, mu[j] + base);
+  }
+};
+
 // ------------------------------------------------------------- x forward
 // Tile: W consecutive lines y0..y0+W-1 of plane z; assembles
 // r = alpha*src + corrections on the fly.
@@ -301,7 +338,9 @@ __global__ void __launch_bounds__(NT) k_xfwd(T* __restrict__ a, const double* __
   T* s = reinterpret_cast<T*>(smem_raw);
   T* tot = s + N * RS;
   T* tw = tot + C::G * W;
+  T* sinv = tw + 4 * N;
   load_twiddles<T, N>(tw, tw_g);
+  load_sines<T, N>(sinv, tw_g);
   const int y0 = blockIdx.x * W;
   const int z = DIM == 3 ? blockIdx.y + 1 : 0;
   for (int idx = threadIdx.x; idx < N * W; idx += NT) {
@@ -326,7 +365,7 @@ __global__ void __launch_bounds__(NT) k_xfwd(T* __restrict__ a, const double* __
     }
   }
   __syncthreads();
-  dst1_tile<Cfg<T, N>>(s, tw, tot);
+  dst_tile<C>(s, tw, sinv, tot);
   const size_t plane = (size_t)z * N * N;
   for (int idx = threadIdx.x; idx < N * W; idx += NT) {
     const int x = idx % N, c = idx / N;
@@ -345,7 +384,9 @@ __global__ void __launch_bounds__(NT) k_xinv(T* __restrict__ a, bool keep, doubl
   T* s = reinterpret_cast<T*>(smem_raw);
   T* tot = s + N * RS;
   T* tw = tot + C::G * W;
+  T* sinv = tw + 4 * N;
   load_twiddles<T, N>(tw, tw_g);
+  load_sines<T, N>(sinv, tw_g);
   const int y0 = blockIdx.x * W;
   const int z = DIM == 3 ? blockIdx.y + 1 : 0;
   const size_t plane = (size_t)z * N * N;
@@ -354,7 +395,7 @@ __global__ void __launch_bounds__(NT) k_xinv(T* __restrict__ a, bool keep, doubl
     s[x * RS + c] = a[plane + (size_t)(y0 + c) * N + x];
   }
   __syncthreads();
-  dst1_tile<Cfg<T, N>>(s, tw, tot);
+  dst_tile<C>(s, tw, sinv, tot);
   for (int idx = threadIdx.x; idx < N * W; idx += NT) {
     const int x = idx % N, c = idx / N, y = y0 + c;
     const T v = s[x * RS + c];
@@ -383,7 +424,9 @@ __global__ void __launch_bounds__(NT) k_strided(T* __restrict__ a, size_t row_st
   T* s = reinterpret_cast<T*>(smem_raw);
   T* tot = s + N * RS;
   T* tw = tot + C::G * W;
+  T* sinv = tw + 4 * N;
   load_twiddles<T, N>(tw, tw_g);
+  load_sines<T, N>(sinv, tw_g);
   const int x0 = blockIdx.x * W;
   const int q = blockIdx.y + qoff;
   T* base = a + (size_t)q * plane_stride + x0;
@@ -392,17 +435,27 @@ __global__ void __launch_bounds__(NT) k_strided(T* __restrict__ a, size_t row_st
     s[k * RS + c] = base[(size_t)k * row_stride + c];
   }
   __syncthreads();
-  dst1_tile<Cfg<T, N>>(s, tw, tot);
-  if (SOLVE) {
-    const T muq = DIM == 3 ? mu1[q] : (T)0;
-    for (int idx = threadIdx.x; idx < N * W; idx += NT) {
-      const int c = idx % W, k = idx / W, p = x0 + c;
-      T v = (T)0;
-      if (k > 0 && p > 0) v = s[k * RS + c] * (scale / (mu1[k] + mu1[p] + muq - lambda));
-      s[k * RS + c] = v;
+  const T muq = DIM == 3 ? mu1[q] : (T)0;
+  if constexpr (kRegDst<T, N>) {
+    if (SOLVE) {
+      const int p = x0 + (int)(threadIdx.x & 31);
+      // mu1 is read from global memory here (L1-resident, N values)
+      const DivPost post{mu1, mu1[p] + muq - lambda, scale, p == 0};
+      dst_tile<C>(s, tw, sinv, tot, post);
     }
-    __syncthreads();
-    dst1_tile<Cfg<T, N>>(s, tw, tot);
+    dst_tile<C>(s, tw, sinv, tot);
+  } else {
+    dst1_tile<C>(s, tw, tot);
+    if (SOLVE) {
+      for (int idx = threadIdx.x; idx < N * W; idx += NT) {
+        const int c = idx % W, k = idx / W, p = x0 + c;
+        T v = (T)0;
+        if (k > 0 && p > 0) v = s[k * RS + c] * (scale / (mu1[k] + mu1[p] + muq - lambda));
+        s[k * RS + c] = v;
+      }
+      __syncthreads();
+      dst1_tile<C>(s, tw, tot);
+    }
   }
   for (int idx = threadIdx.x; idx < N * W; idx += NT) {
     const int c = idx % W, k = idx / W;
@@ -418,6 +471,7 @@ __global__ void __launch_bounds__(NT) k_strided(T* __restrict__ a, size_t row_st
 // wait is bounded: on timeout the block records DEVERR_TIMEOUT and returns.
 constexpr int TMA_W = 32;
 constexpr long TMA_WAIT_CAP = 1L << 22;
+constexpr int TMA_BLOCKS = 2;  // resident blocks per SM (at 3 the register DST spills)
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -459,14 +513,15 @@ __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy
 template <int N>
 using TmaTile = Tile<float, N, TMA_W, TMA_W>;
 
+// two tiles, scan totals, twiddles, sines, mu1, two mbarriers
 template <int N>
 constexpr size_t tma_smem_bytes() {
-  return (2 * (size_t)N * TMA_W + (size_t)TmaTile<N>::G * TMA_W + 4 * (size_t)N) * sizeof(float) + 2 * sizeof(uint64_t);
+  return (2 * (size_t)N * TMA_W + (size_t)TmaTile<N>::G * TMA_W + 6 * (size_t)N) * sizeof(float) + 2 * sizeof(uint64_t);
 }
 
 // mode 0: tiles [y][x-chunk] of plane z = q; mode 1: tiles [z][x-chunk] of row y = q
 template <int N, bool SOLVE>
-__global__ void __launch_bounds__(NT, 2) k_strided_tma(const __grid_constant__ CUtensorMap map, int mode,
+__global__ void __launch_bounds__(NT, TMA_BLOCKS) k_strided_tma(const __grid_constant__ CUtensorMap map, int mode,
                                                     const float* __restrict__ mu1, float lambda, float scale,
                                                     const float* __restrict__ tw_g, int* __restrict__ err) {
   using C = TmaTile<N>;
@@ -478,8 +533,14 @@ __global__ void __launch_bounds__(NT, 2) k_strided_tma(const __grid_constant__ C
   float* buf1 = buf0 + N * W;
   float* tot = buf1 + N * W;
   float* tw = tot + C::G * W;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(tw + 4 * N);
+  float* sinv = tw + 4 * N;
+  float* mus = sinv + N;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(mus + N);
   for (int i = threadIdx.x; i < 4 * N; i += NT) tw[i] = tw_g[i];
+  for (int i = threadIdx.x; i < N; i += NT) {
+    sinv[i] = tw_g[2 * i + 1];
+    mus[i] = mu1[i];
+  }
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -521,23 +582,13 @@ __global__ void __launch_bounds__(NT, 2) k_strided_tma(const __grid_constant__ C
       if (threadIdx.x == 0) atomicOr(err, DEVERR_TIMEOUT);
       return;
     }
-    // one DST body, run twice around the spectral divide when solving (keeps
-    // a single inlined copy and the register count of the plain pass)
-#pragma unroll 1
-    for (int rep = 0; rep < (SOLVE ? 2 : 1); ++rep) {
-      dst1_tile<C>(s, tw, tot);
-      if (SOLVE && rep == 0) {
-        const int q = t / NX + 1, x0 = (t % NX) * W;
-        const float muq = mu1[q];
-        for (int idx = threadIdx.x; idx < N * W; idx += NT) {
-          const int c = idx % W, k = idx / W, p = x0 + c;
-          float v = 0.0f;
-          if (k > 0 && p > 0) v = s[k * W + c] * (scale / (mu1[k] + mu1[p] + muq - lambda));
-          s[k * W + c] = v;
-        }
-        __syncthreads();
-      }
+    if (SOLVE) {
+      // forward DST with the spectral divide applied to its outputs
+      const int q = t / NX + 1, p = (t % NX) * W + (int)(threadIdx.x & 31);
+      const DivPost post{mus, mus[p] + mus[q] - lambda, scale, p == 0};
+      regdst::dst1_tile_reg<regdst::Geo<N, W>>(s, sinv, reinterpret_cast<const regdst::cf2*>(tw), tot, post);
     }
+    regdst::dst1_tile_reg<regdst::Geo<N, W>>(s, sinv, reinterpret_cast<const regdst::cf2*>(tw), tot);
     fence_async_shared();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -582,7 +633,7 @@ int launch_strided3(kfbi_handle* h, int mode, bool solve, T* work, const T* mu1,
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       const int tiles = (N / TMA_W) * (N - 1);
-      const int grid = tiles < 2 * sms ? tiles : 2 * sms;
+      const int grid = tiles < TMA_BLOCKS * sms ? tiles : TMA_BLOCKS * sms;
       if (solve) {
         if ((rc = prep(k_strided_tma<N, true>, smem))) return rc;
         k_strided_tma<N, true><<<grid, NT, smem, st>>>(map, mode, mu1, lam, scale, tw, h->w.err);

@@ -131,6 +131,11 @@ struct Workspace {
   double* g_prev = nullptr;       // [M] right-hand side of the previous diffusion solve
   double* u64 = nullptr;          // user-layout float64 grid (refined solutions)
   double* res64 = nullptr;        // user-layout float64 grid (refinement residuals)
+  double* hist_psi = nullptr;     // [KFBI_HISTORY][M] densities of past solves
+  double* hist_g = nullptr;       // [KFBI_HISTORY][M] their right-hand sides
+  double* psiF = nullptr;         // [M] projected density
+  double* rF = nullptr;           // [M] its residual
+  double* proj = nullptr;         // Gram matrix, right side, coefficients
   double* host_small = nullptr;   // pinned host scalars
   int* err = nullptr;             // device error word
   int restart_cap = 0;
@@ -150,6 +155,7 @@ struct kfbi_handle {
   std::vector<void*> allocations;
   bool have_prev = false;
   int n_hist = 0;                 // completed diffusion solves (density history)
+  int hist_count = 0;             // solves held in the projection history ring
   kfbi_mlp* warm = nullptr;       // learned warm start (not owned)
   // TMA descriptors of the float32 padded grid: [N x 32] tiles along y and z
   CUtensorMap tmap_y32, tmap_z32;

@@ -108,21 +108,22 @@ __global__ void k_limit_user(Tables t, GridParams gr, const double* __restrict__
 
 // res = alpha*src - (L_h u) on the user layout, L_h the 5/7-point operator
 // with zero Dirichlet data (float64 residual of the refined box solve)
+// r = alpha*src - L_h u on the user layout; one block row per (y, z) grid line
+// so no index needs a 64-bit division.
 __global__ void k_residual(GridParams gr, const double* __restrict__ src, double alpha, const double* __restrict__ u,
-                           double lambda, double* __restrict__ res, int64_t total) {
+                           double lambda, double* __restrict__ res) {
   const int n1 = gr.N - 1;
   const double ih2 = 1.0 / (gr.h * gr.h);
   const double diag = -2.0 * gr.dim * ih2 - lambda;
-  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < total; f += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(f % n1), y = (int)((f / n1) % n1);
+  const int y = blockIdx.x, z = blockIdx.y;
+  const int64_t s = (int64_t)n1 * n1;
+  const int64_t base = (int64_t)z * s + (int64_t)y * n1;
+  for (int x = threadIdx.x; x < n1; x += blockDim.x) {
+    const int64_t f = base + x;
     const double uc = u[f];
     double nb = (x > 0 ? u[f - 1] : 0.0) + (x < n1 - 1 ? u[f + 1] : 0.0);
     nb += (y > 0 ? u[f - n1] : 0.0) + (y < n1 - 1 ? u[f + n1] : 0.0);
-    if (gr.dim == 3) {
-      const int z = (int)(f / ((int64_t)n1 * n1));
-      const int64_t s = (int64_t)n1 * n1;
-      nb += (z > 0 ? u[f - s] : 0.0) + (z < n1 - 1 ? u[f + s] : 0.0);
-    }
+    if (gr.dim == 3) nb += (z > 0 ? u[f - s] : 0.0) + (z < n1 - 1 ? u[f + s] : 0.0);
     const double Lu = nb * ih2 + diag * uc;
     res[f] = (src != nullptr ? alpha * src[f] : 0.0) - Lu;
   }
@@ -290,32 +291,54 @@ __global__ void k_add_small(double* s, int m, int n) {
 }
 
 // ------------------------------------------------------------- reaction
+// FP64 work is scarce on this part (2 FMA per SM per clock), so the pointwise
+// kernels keep float64 for what must be float64 and fold the constants: the
+// forward-Euler half step has no division left.
 __global__ void k_react_fe(kfbi_fhn p, double k, double* __restrict__ V, double* __restrict__ w, int64_t n) {
+  const double a = k * p.H / p.Cm, ka = k * p.alpha, kz = k * p.zeta;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double v = V[i], q = w[i];
     const double cubic = v * (v - p.theta) * (1.0 - v);
-    const double Iion = p.H * (q - cubic);
-    V[i] = v + k * (-Iion / p.Cm);
-    w[i] = q + k * (p.alpha * v - p.zeta * q);
+    V[i] = v - a * (q - cubic);
+    w[i] = q + (ka * v - kz * q);
   }
 }
 
+// Backward-Euler half step: w is eliminated (w1 = (w0 + k alpha v) / (1 + k
+// zeta)) and Newton solves the cubic in v.  Float32 Newton steps first bring
+// v to float32 resolution; float64 steps then use the exact float64 residual
+// with the float32 derivative (a quasi-Newton step whose contraction factor
+// is the derivative's relative error, ~1e-7), which converges to float64
+// resolution in two steps without any float64 division.  Converged means a
+// float64 step below 1e-10, as in the plain Newton iteration.
 __global__ void k_react_be(kfbi_fhn p, double k, double* __restrict__ V, double* __restrict__ w, int64_t n,
                            int* err) {
   const double c = k * p.H / p.Cm;
   const double den = 1.0 + k * p.zeta;
-  const double r = k * p.alpha / den;
+  const double inv_den = 1.0 / den;
+  const double ka = k * p.alpha;
+  const float cf = (float)c, rf = (float)(ka / den), thf = (float)p.theta, kaf = (float)ka, idf = (float)inv_den;
+  const float th1 = 2.0f * (1.0f + thf);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double v0 = V[i], q0 = w[i];
-    double v = v0;
+    const float v0f = (float)v0, q0f = (float)q0;
+    float vf = v0f;
+    for (int it = 0; it < 12; ++it) {
+      const float q1 = (q0f + kaf * vf) * idf;
+      const float Fv = vf - v0f - cf * (vf * (vf - thf) * (1.0f - vf) - q1);
+      const float dF = 1.0f - cf * ((-3.0f * vf + th1) * vf - thf - rf);
+      const float dv = Fv / dF;
+      vf -= dv;
+      if (fabsf(dv) <= 1e-6f * fmaxf(1.0f, fabsf(vf))) break;
+    }
+    double v = vf;
     bool ok = false;
     for (int it = 0; it < 50; ++it) {
-      const double q1 = (q0 + k * p.alpha * v) / den;
-      const double cubic = v * (v - p.theta) * (1.0 - v);
-      const double F = v - v0 - c * (cubic - q1);
-      const double dcubic = -3.0 * v * v + 2.0 * (1.0 + p.theta) * v - p.theta;
-      const double dF = 1.0 - c * (dcubic - r);
-      const double dv = F / dF;
+      const float xf = (float)v;
+      const double rdF = (double)(1.0f / (1.0f - cf * ((-3.0f * xf + th1) * xf - thf - rf)));
+      const double q1 = (q0 + ka * v) * inv_den;
+      const double F = v - v0 - c * (v * (v - p.theta) * (1.0 - v) - q1);
+      const double dv = F * rdF;
       v -= dv;
       if (fabs(dv) < 1e-10) {
         ok = true;
@@ -324,7 +347,7 @@ __global__ void k_react_be(kfbi_fhn p, double k, double* __restrict__ V, double*
     }
     if (!ok) atomicOr(err, DEVERR_NEWTON);
     V[i] = v;
-    w[i] = (q0 + k * p.alpha * v) / den;
+    w[i] = (q0 + ka * v) * inv_den;
   }
 }
 
@@ -403,8 +426,7 @@ int launch_limit_user(kfbi_handle* h, const double* u, const double* x, const do
 int launch_residual(kfbi_handle* h, const double* src, double alpha, const double* corr, const double* u, double lambda,
                     double* res) {
   const int n1 = h->grid.N - 1;
-  const int64_t total = h->grid.dim == 3 ? (int64_t)n1 * n1 * n1 : (int64_t)n1 * n1;
-  k_residual<<<grid_blocks(total, 256), 256, 0, h->stream>>>(h->grid, src, alpha, u, lambda, res, total);
+  k_residual<<<dim3(n1, h->grid.dim == 3 ? n1 : 1), 128, 0, h->stream>>>(h->grid, src, alpha, u, lambda, res);
   if (corr != nullptr && h->t.n_irr > 0)
     k_scatter_add<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->t, corr, res);
   KFBI_CHECK_LAUNCH_N(corr != nullptr && h->t.n_irr > 0 ? 2 : 1);

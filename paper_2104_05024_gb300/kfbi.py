@@ -18,6 +18,8 @@ OK, ERR_ARG, ERR_GEOMETRY, ERR_NOT_CONVERGED, ERR_NAN, ERR_CUDA, ERR_OOM, ERR_NE
 ELLIPSE2, ELLIPSOID3, STAR3, SHELL3 = 1, 2, 3, 4
 FP64, MIXED, MIXED_LEARNED, FP32 = 0, 1, 2, 3
 GMRES, RICHARDSON = 0, 1
+WARM_PREVIOUS, WARM_PROJECTION = 0, 1
+HISTORY = 8
 MAX_COMP = 4
 
 
@@ -36,7 +38,7 @@ class GridStruct(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("solver", C.c_int), ("tol", C.c_double), ("restart", C.c_int),
-                ("max_iter", C.c_int), ("gamma", C.c_double), ("stream", C.c_void_p)]
+                ("max_iter", C.c_int), ("gamma", C.c_double), ("stream", C.c_void_p), ("warm", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -65,6 +67,7 @@ EXPORTS = [
     "kfbi_transform_pass", "kfbi_launch_count", "kfbi_box_solve_noalloc", "kfbi_mlp_num_params",
     "kfbi_mlp_create", "kfbi_mlp_destroy", "kfbi_mlp_get", "kfbi_mlp_forward", "kfbi_mlp_grad",
     "kfbi_mlp_train_step", "kfbi_set_warmstart", "kfbi_get_densities", "kfbi_set_densities",
+    "kfbi_get_history", "kfbi_set_history", "kfbi_get_projection",
 ]
 
 
@@ -169,6 +172,9 @@ def load(path: str = LIB_PATH):
     lib.kfbi_set_warmstart.argtypes = [vp, vp]
     lib.kfbi_get_densities.argtypes = [vp, vp, vp, vp]
     lib.kfbi_set_densities.argtypes = [vp, vp, vp, vp, ip]
+    lib.kfbi_get_history.argtypes = [vp, vp, vp, C.POINTER(C.c_int)]
+    lib.kfbi_set_history.argtypes = [vp, vp, vp, ip]
+    lib.kfbi_get_projection.argtypes = [vp, vp, vp]
     for name in EXPORTS:
         if name not in ("kfbi_last_error", "kfbi_destroy", "kfbi_launch_count", "kfbi_mlp_destroy"):
             getattr(lib, name).restype = C.c_int
@@ -216,7 +222,7 @@ class KFBI:
     tri_offset) -- e.g. kfbi_workloads.geometry.Geometry."""
 
     def __init__(self, geom, grid, sigma_i=1.0, sigma_e=2.0, dt=0.05, precision=FP64, solver=GMRES, tol=1e-10,
-                 restart=50, max_iter=500, gamma=0.8, lo=-1.0, hi=1.0):
+                 restart=50, max_iter=500, gamma=0.8, lo=-1.0, hi=1.0, warm=WARM_PREVIOUS):
         lib = load()
         self._keep = []
         g = Geometry()
@@ -247,7 +253,7 @@ class KFBI:
             g.n_comp = 1
         self.dim, self.N = int(grid.dim), int(grid.N)
         gs = GridStruct(self.dim, self.N, float(getattr(grid, "lo", lo)), float(getattr(grid, "hi", hi)))
-        self.opts = Opts(precision, solver, tol, restart, max_iter, gamma, _stream())
+        self.opts = Opts(precision, solver, tol, restart, max_iter, gamma, _stream(), warm)
         h = C.c_void_p()
         _check(lib.kfbi_create(C.byref(g), C.byref(gs), sigma_i, sigma_e, dt, C.byref(self.opts), C.byref(h)))
         self._h = h
@@ -315,21 +321,38 @@ class KFBI:
         self.set_opts()
         _check(load().kfbi_set_densities(self._h, _ptr(psi), _ptr(psi_prev), _ptr(g), int(n_solves)))
 
-    def checkpoint(self, V, w, n_solves):
-        """Host copy of everything a resumed run needs: state, density history,
-        solve count (the caller stores it, e.g. with numpy.savez)."""
+    def get_history(self, psi_hist, g_hist):
+        n = C.c_int()
+        self.set_opts()
+        _check(load().kfbi_get_history(self._h, _ptr(psi_hist), _ptr(g_hist), C.byref(n)))
+        return n.value
+
+    def set_history(self, psi_hist, g_hist, n_solves):
+        self.set_opts()
+        _check(load().kfbi_set_history(self._h, _ptr(psi_hist), _ptr(g_hist), int(n_solves)))
+
+    def get_projection(self, psiF, rF):
+        self.set_opts()
+        _check(load().kfbi_get_projection(self._h, _ptr(psiF), _ptr(rF)))
+
+    def checkpoint(self, V, w):
+        """Host copy of everything a resumed run needs: the state (V, w) and
+        the density history with its solve count (the caller stores it, e.g.
+        with numpy.savez)."""
         import torch
-        M = self.M
-        psi, psi1, g = (torch.empty(M, dtype=torch.float64, device=V.device) for _ in range(3))
-        self.get_densities(psi, psi1, g)
-        return {"V": V.cpu().numpy(), "w": w.cpu().numpy(), "psi": psi.cpu().numpy(), "psi_prev": psi1.cpu().numpy(),
-                "g": g.cpu().numpy(), "n_solves": int(n_solves)}
+        shape = (HISTORY, self.M)
+        ph = torch.empty(shape, dtype=torch.float64, device=V.device)
+        gh = torch.empty_like(ph)
+        n = self.get_history(ph, gh)
+        torch.cuda.synchronize(V.device)
+        return {"V": V.cpu().numpy(), "w": w.cpu().numpy(), "psi_hist": ph.cpu().numpy(), "g_hist": gh.cpu().numpy(),
+                "n_solves": n}
 
     def restore(self, ck, device):
         """Inverse of checkpoint(): returns (V, w) on the device."""
         import torch
-        t = {k: torch.tensor(ck[k], dtype=torch.float64, device=device) for k in ("V", "w", "psi", "psi_prev", "g")}
-        self.set_densities(t["psi"], t["psi_prev"], t["g"], int(ck["n_solves"]))
+        t = {k: torch.tensor(ck[k], dtype=torch.float64, device=device) for k in ("V", "w", "psi_hist", "g_hist")}
+        self.set_history(t["psi_hist"], t["g_hist"], int(ck["n_solves"]))
         return t["V"], t["w"]
 
     def transform_pass(self, pass_id, lam=0.0, precision=FP64):

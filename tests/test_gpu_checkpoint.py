@@ -27,11 +27,12 @@ def _case(name):
 
 
 @pytest.mark.parametrize("name", ["ellipse128", "shell64"])
-@pytest.mark.parametrize("precision", [K.FP64, K.MIXED])
-def test_resume_bit_identical(tmp_path, name, precision):
+@pytest.mark.parametrize("precision,warm", [(K.FP64, K.WARM_PREVIOUS), (K.MIXED, K.WARM_PREVIOUS),
+                                            (K.FP64, K.WARM_PROJECTION), (K.MIXED, K.WARM_PROJECTION)])
+def test_resume_bit_identical(tmp_path, name, precision, warm):
     geom, grid, V0, w0 = _case(name)
-    total, split = 6, 3
-    kw = dict(sigma_i=1.0, sigma_e=2.0, dt=0.05, tol=1e-10, precision=precision)
+    total, split = 12, 9     # the split falls after the history ring has wrapped
+    kw = dict(sigma_i=1.0, sigma_e=2.0, dt=0.05, tol=1e-10, precision=precision, warm=warm)
 
     h = K.KFBI(geom, grid, **kw)
     Va, wa = _cuda(V0), _cuda(w0)
@@ -41,7 +42,8 @@ def test_resume_bit_identical(tmp_path, name, precision):
     h = K.KFBI(geom, grid, **kw)
     Vb, wb = _cuda(V0), _cuda(w0)
     h.bidomain_step(C.FHN_CONFIG, Vb, wb, None, nsteps=split)
-    ck = h.checkpoint(Vb, wb, split)
+    ck = h.checkpoint(Vb, wb)
+    assert ck["n_solves"] == split
     h.close()
     path = tmp_path / "ck.npz"
     np.savez(path, **ck)
@@ -64,7 +66,7 @@ def test_resume_without_history():
     h = K.KFBI(geom, grid, **kw)
     V, w = _cuda(V0), _cuda(w0)
     h.bidomain_step(C.FHN_CONFIG, V, w, None, nsteps=2)
-    ck = h.checkpoint(V, w, 2)
+    ck = h.checkpoint(V, w)
     ref = h.bidomain_step(C.FHN_CONFIG, V, w, None, nsteps=1)
     h.close()
 
