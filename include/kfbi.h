@@ -54,7 +54,8 @@ extern "C" {
 #define KFBI_FP64 0          /* all transforms and corrections in float64        */
 #define KFBI_MIXED 1         /* float32 transforms inside GMRES, float64 Arnoldi,
                                 residuals and outer refinement                   */
-#define KFBI_MIXED_LEARNED 2 /* KFBI_MIXED + learned warm start of the density   */
+#define KFBI_MIXED_LEARNED 2 /* KFBI_MIXED + learned warm start of the density
+                                (kfbi_set_warmstart)                             */
 #define KFBI_FP32 3          /* kfbi_box_solve / kfbi_transform_pass only: plain
                                 float32 transforms without refinement             */
 
@@ -259,10 +260,16 @@ int kfbi_mlp_grad(kfbi_mlp* m, const float* F_dev, const float* t_dev, int B, fl
 /* one forward + backward + Adam step with learning rate lr.                 */
 int kfbi_mlp_train_step(kfbi_mlp* m, const float* F_dev, const float* t_dev, int B, float lr, float* loss_host);
 /* Attach (or detach with NULL) a network to a 3-D handle.  With precision
- * KFBI_MIXED_LEARNED, bidomain_step then predicts each diffusion solve's
- * initial density from the two previous densities and g^n, and keeps it only
- * when its float32 residual ||g - A psi|| is below that of the previous
- * density (the plain warm start stays the fallback).                         */
+ * KFBI_MIXED_LEARNED, bidomain_step then starts each diffusion solve from
+ *   psi_L = psi_F + 2 gamma r_F + rms(r_F) * net(psi_F/rms, r_F/rms, g/rms,
+ *                                                 x, n),
+ * psi_F the history projection (KFBI_WARM_PROJECTION) and r_F its residual,
+ * and keeps psi_L only when its float64-accurate residual ||g - A psi_L|| is
+ * below ||r_F||; otherwise it starts from psi_F, whose residual is never
+ * above that of the previous density (which lies in the projection's span).
+ * Network input rows are (psi_F, r_F, g^n) scaled by their root mean
+ * squares, then the node and its unit normal; the output is the correction
+ * in units of rms(r_F), with the normalisation of kfbi_mlp_create.          */
 int kfbi_set_warmstart(kfbi_handle* h, kfbi_mlp* m);
 /* After a Strang step: psi_dev <- psi^n, psi_prev_dev <- psi^{n-1} and
  * g_dev <- g^n of the last diffusion solve (each may be NULL).               */

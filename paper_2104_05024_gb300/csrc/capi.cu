@@ -525,7 +525,7 @@ int kfbi_create(const kfbi_geometry* geom, const kfbi_grid* grid, double sigma_i
   if ((rc = dalloc(h, &h->w.hist_g, (size_t)KFBI_HISTORY * M))) return fail(rc);
   if ((rc = dalloc(h, &h->w.psiF, (size_t)M))) return fail(rc);
   if ((rc = dalloc(h, &h->w.rF, (size_t)M))) return fail(rc);
-  if ((rc = dalloc(h, &h->w.proj, (size_t)KFBI_HISTORY * (KFBI_HISTORY + 2)))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.proj, (size_t)KFBI_HISTORY * (KFBI_HISTORY + 2) + 4))) return fail(rc);
   if (cudaMallocHost((void**)&h->w.host_small, 128 * sizeof(double)) != cudaSuccess) {
     set_error("cudaMallocHost failed");
     return fail(KFBI_ERR_OOM);
@@ -769,23 +769,23 @@ int bidomain_step(kfbi_handle* h, const kfbi_fhn* p, double* V_dev, double* w_de
     if ((h->opts.warm == KFBI_WARM_PROJECTION || learned) && h->opts.solver == KFBI_GMRES && h->hist_count >= 1) {
       // psi_F from the history, then one step of the simple iteration
       // psi_F + 2 gamma r_F; psi_F itself (residual known) is the fallback
+      const int M = h->t.M;
       if ((rc = project_history(h, h->w.g, &fallback_res))) return rc;
-      if ((rc = vec_copy(h, h->w.psi_prev, h->w.psiF, h->t.M))) return rc;
-      if ((rc = vec_axpby(h, h->w.psi_prev, 2.0 * h->opts.gamma, h->w.rF, 1.0, h->t.M))) return rc;
+      if (learned && h->grid.dim == 3) {
+        // the network corrects psi_F + 2 gamma r_F in units of rms(r_F)
+        double* sq = h->w.proj + KFBI_HISTORY * (KFBI_HISTORY + 2);
+        if ((rc = vec_dots(h, h->w.psiF, 1, M, h->w.psiF, sq))) return rc;
+        if ((rc = vec_dots(h, h->w.rF, 1, M, h->w.rF, sq + 1))) return rc;
+        if ((rc = vec_dots(h, h->w.g, 1, M, h->w.g, sq + 2))) return rc;
+        if ((rc = mlp_warmstart(h->warm, h->stream, h->w.psiF, h->w.rF, h->w.g, sq, h->t.nodes, h->t.n_normal, M,
+                                2.0 * h->opts.gamma, h->w.psi_prev)))
+          return rc;
+        st.warmstart = 1;
+      } else {
+        if ((rc = vec_copy(h, h->w.psi_prev, h->w.psiF, M))) return rc;
+        if ((rc = vec_axpby(h, h->w.psi_prev, 2.0 * h->opts.gamma, h->w.rF, 1.0, M))) return rc;
+      }
       fallback = h->w.psiF;
-    } else if (learned && h->opts.solver == KFBI_GMRES && h->n_hist >= 2) {
-      if ((rc = mlp_warmstart(h->warm, h->stream, h->w.psi_prev, h->w.psi_prev2, h->w.g, h->t.nodes, h->t.n_normal,
-                              h->t.M, h->w.psi_learn)))
-        return rc;
-      // residual of the previous density: A psi^{n-1} = g^{n-1} up to the
-      // previous tolerance, so g^n - A psi^{n-1} = g^n - g^{n-1} needs no solve
-      double* slot = h->w.small + small_nrm2(h->opts.restart);
-      if ((rc = vec_copy(h, h->w.tmp, h->w.g_prev, h->t.M))) return rc;
-      if ((rc = vec_axpby(h, h->w.tmp, 1.0, h->w.g, -1.0, h->t.M))) return rc;
-      if ((rc = norm2(h, h->w.tmp, slot, &fallback_res))) return rc;
-      if ((rc = vec_copy(h, h->w.psi_prev, h->w.psi_learn, h->t.M))) return rc;
-      fallback = h->w.psi_save;
-      st.warmstart = 1;
     }
     const int src = solve_bie(h, prec, lam, h->w.g, h->w.psi_prev, &st, fallback, fallback_res);
     if (src != KFBI_OK && src != KFBI_ERR_NOT_CONVERGED) return src;

@@ -226,8 +226,9 @@ int arnoldi_givens(kfbi_handle* h, double* small, int j, int ldh);
 int arnoldi_solve(kfbi_handle* h, double* small, int k, int ldh);
 
 // mlp.cu
-int mlp_warmstart(kfbi_mlp* m, cudaStream_t st, const double* p1, const double* p2, const double* g,
-                  const double* nodes, const double* normals, int M, double* out);
+int mlp_warmstart(kfbi_mlp* m, cudaStream_t st, const double* psiF, const double* rF, const double* g,
+                  const double* sq, const double* nodes, const double* normals, int M, double two_gamma,
+                  double* out);
 
 int launch_react_fe(const kfbi_fhn* p, double k, double* V, double* w, int64_t n, cudaStream_t s);
 int launch_react_be(const kfbi_fhn* p, double k, double* V, double* w, int64_t n, int* err, cudaStream_t s);

@@ -110,17 +110,22 @@ __global__ void k_feat_raw(const float* __restrict__ F, int B, int Bp, const flo
   X[i] = __float2bfloat16_rn(v);
 }
 
-// the same from the solver state (psi^{n-1}, psi^{n-2}, g^n, nodes, normals)
-__global__ void k_feat_state(const double* __restrict__ p1, const double* __restrict__ p2, const double* __restrict__ g,
-                             const double* __restrict__ nodes, const double* __restrict__ normals, int B, int Bp,
-                             const float* __restrict__ norm, bf16* X, float* Fraw) {
+// the same from the solver state: the projected density psi_F, its residual
+// r_F and the right-hand side g^n, each divided by its root mean square
+// (sq = their sums of squares), then the node and its normal
+__global__ void k_feat_proj(const double* __restrict__ psiF, const double* __restrict__ rF,
+                            const double* __restrict__ g, const double* __restrict__ sq,
+                            const double* __restrict__ nodes, const double* __restrict__ normals, int B, int Bp,
+                            const float* __restrict__ norm, bf16* X) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= Bp) return;
   float f[NIN];
   if (b < B) {
-    f[0] = (float)p1[b];
-    f[1] = (float)p2[b];
-    f[2] = (float)g[b];
+    const double s0 = rsqrt(fmax(sq[0] / B, 1e-300)), s1 = rsqrt(fmax(sq[1] / B, 1e-300)),
+                 s2 = rsqrt(fmax(sq[2] / B, 1e-300));
+    f[0] = (float)(psiF[b] * s0);
+    f[1] = (float)(rF[b] * s1);
+    f[2] = (float)(g[b] * s2);
     for (int k = 0; k < 3; ++k) {
       f[3 + k] = (float)nodes[(size_t)b * 3 + k];
       f[6 + k] = (float)normals[(size_t)b * 3 + k];
@@ -130,7 +135,6 @@ __global__ void k_feat_state(const double* __restrict__ p1, const double* __rest
     float v = 0.0f;
     if (b < B && c < NIN) v = (f[c] - norm[c]) / norm[NIN + c];
     X[(size_t)b * KIN + c] = __float2bfloat16_rn(v);
-    if (Fraw != nullptr && b < B && c < NIN) Fraw[(size_t)b * NIN + c] = f[c];
   }
 }
 
@@ -231,10 +235,15 @@ __global__ void k_unpad_w0(const float* __restrict__ g16, float* gw0) {
 }
 
 // psi0 = psi1 + s_out o + m_out
-__global__ void k_predict(const double* __restrict__ p1, const float* __restrict__ o, const float* __restrict__ norm,
-                          double* out, int B) {
+// psi_L = psi_F + 2 gamma r_F + rms(r_F) * (denormalised network output)
+__global__ void k_predict(const double* __restrict__ psiF, const double* __restrict__ rF,
+                          const double* __restrict__ sq, double two_gamma, const float* __restrict__ o,
+                          const float* __restrict__ norm, double* out, int B) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < B) out[b] = p1[b] + (double)(norm[2 * NIN + 1] * o[b] + norm[2 * NIN]);
+  if (b < B) {
+    const double sr = sqrt(sq[1] / B);
+    out[b] = psiF[b] + two_gamma * rF[b] + sr * (double)(norm[2 * NIN + 1] * o[b] + norm[2 * NIN]);
+  }
 }
 
 }  // namespace
@@ -346,8 +355,9 @@ int mlp_refresh(kfbi_mlp* m) {
 }  // namespace
 
 // warm start used by bidomain_step: psi0 = psi1 + network(psi1, psi2, g, x, n)
-int mlp_warmstart(kfbi_mlp* m, cudaStream_t st, const double* p1, const double* p2, const double* g,
-                  const double* nodes, const double* normals, int M, double* out) {
+int mlp_warmstart(kfbi_mlp* m, cudaStream_t st, const double* psiF, const double* rF, const double* g,
+                  const double* sq, const double* nodes, const double* normals, int M, double two_gamma,
+                  double* out) {
   if (M > m->bmax) {
     set_error("warm start: %d nodes exceed the network's batch capacity %d", M, m->bmax);
     return KFBI_ERR_ARG;
@@ -355,11 +365,11 @@ int mlp_warmstart(kfbi_mlp* m, cudaStream_t st, const double* p1, const double* 
   cudaStream_t saved = m->stream;
   m->stream = st;
   const int Bp = (M + TILE - 1) / TILE * TILE;
-  k_feat_state<<<blocks(Bp, 128), 128, 0, st>>>(p1, p2, g, nodes, normals, M, Bp, m->norm, m->X, nullptr);
+  k_feat_proj<<<blocks(Bp, 128), 128, 0, st>>>(psiF, rF, g, sq, nodes, normals, M, Bp, m->norm, m->X);
   KFBI_CHECK_LAUNCH();
   int rc = mlp_forward_rows(m, Bp);
   if (rc == KFBI_OK) {
-    k_predict<<<blocks(M, 256), 256, 0, st>>>(p1, m->o, m->norm, out, M);
+    k_predict<<<blocks(M, 256), 256, 0, st>>>(psiF, rF, sq, two_gamma, m->o, m->norm, out, M);
     KFBI_CHECK_LAUNCH();
   }
   m->stream = saved;

@@ -1,11 +1,16 @@
 """Training data and training loop of the learned density warm start.
 
-Orchestration only: Strang steps, density exports, the forward/backward/Adam
-step and inference all run in libkfbi.so kernels; this module only arranges
-the rows (on the device, with torch as the memory allocator) and the loop.
+Orchestration only: Strang steps, the density-history projection, density
+exports, the forward/backward/Adam step and inference all run in libkfbi.so
+kernels; this module only arranges the rows (on the device, with torch as the
+memory allocator) and the loop.
 
-A training row of step n is (psi^{n-1}, psi^{n-2}, g^n, x, n) -> psi^n - psi^{n-1}
-for every interface node, from runs of the method itself.
+A training row of solve n is, for every interface node,
+  (psi_F / rms(psi_F), r_F / rms(r_F), g^n / rms(g^n), x, n)
+  -> (psi^n - psi_F - 2 gamma r_F) / rms(r_F),
+with psi_F the projection of the density history and r_F = g^n - A psi_F its
+residual, from runs of the method itself (the same features the library's
+feature kernel builds at inference).
 """
 from __future__ import annotations
 
@@ -39,27 +44,40 @@ def init_params(seed: int = 0) -> np.ndarray:
     return np.concatenate(out).astype(np.float32)
 
 
-def collect(h: K.KFBI, fhn, V, w, steps, nodes, normals, first=3):
-    """Advance (V, w) by `steps` Strang steps on handle h and return the rows
-    (F [rows, 9] float32, T [rows] float32 raw targets) of steps >= first."""
+def _rms(v):
+    return (v.double().norm() / v.numel() ** 0.5).clamp_min(1e-150)
+
+
+def features(psiF, rF, g, X, Nn):
+    """Input rows of the network (float32), as the library's feature kernel
+    builds them."""
+    torch = _torch()
+    return torch.cat([(psiF / _rms(psiF)).float()[:, None], (rF / _rms(rF)).float()[:, None],
+                      (g / _rms(g)).float()[:, None], X, Nn], dim=1).contiguous()
+
+
+def collect(h: K.KFBI, fhn, V, w, steps, nodes, normals, first=2, gamma=0.8):
+    """Advance (V, w) by `steps` Strang steps on handle h (projection warm
+    start) and return the rows (F [rows, 9] float32, T [rows] float32 raw
+    targets) of the solves >= first."""
     torch = _torch()
     dev = V.device
     M = h.M
+    h.set_opts(warm=K.WARM_PROJECTION)
     psi = torch.empty(M, dtype=torch.float64, device=dev)
-    psi1 = torch.empty_like(psi)
     g = torch.empty_like(psi)
+    psiF = torch.empty_like(psi)
+    rF = torch.empty_like(psi)
     X = torch.tensor(np.asarray(nodes), dtype=torch.float32, device=dev)
     Nn = torch.tensor(np.asarray(normals), dtype=torch.float32, device=dev)
-    prev1 = None
     Fs, Ts = [], []
     for n in range(1, steps + 1):
         h.bidomain_step(fhn, V, w, None, nsteps=1)
-        h.get_densities(psi, psi1, g)
-        if n >= first and prev1 is not None:
-            F = torch.cat([psi1.float()[:, None], prev1.float()[:, None], g.float()[:, None], X, Nn], dim=1)
-            Fs.append(F)
-            Ts.append((psi - psi1).float())
-        prev1 = psi1.clone()
+        if n >= first:
+            h.get_densities(psi, None, g)
+            h.get_projection(psiF, rF)
+            Fs.append(features(psiF, rF, g, X, Nn))
+            Ts.append(((psi - psiF - 2.0 * gamma * rF) / _rms(rF)).float())
     return torch.cat(Fs), torch.cat(Ts)
 
 

@@ -6,10 +6,10 @@
   the other bfloat16 neighbour), relative L2 within 1e-2 (forward) and 3e-2
   (gradients);
 * Adam training on the GPU lowers the loss;
-* a network trained on densities of shell runs with four stimulus locations
-  lowers the GMRES iterations of a run with a held-out stimulus location, and
-  the converged states agree with the plain warm start's to the solver
-  tolerance.
+* with a network trained on solves of shell runs from four stimulus
+  locations, a run from a held-out location needs fewer GMRES iterations
+  than with the previous-density start, and the converged states agree with
+  that start's to the solver tolerance.
 """
 import numpy as np
 import pytest
@@ -84,6 +84,12 @@ def _run(h, V0, w0, steps, precision):
 
 
 def test_learned_warm_start_reduces_iterations():
+    """Runs from a held-out stimulus: the previous-density start (the paper's),
+    the history projection, and the projection corrected by a network trained
+    on four other stimulus runs.  The learned start needs fewer GMRES
+    iterations than the previous-density start; its gain over the projection
+    alone is printed (the residual judge keeps the network's guess when its
+    residual is smaller, which is not always fewer iterations)."""
     N, steps = 64, 24
     geom, grid, cfg, _, _ = C.config2(N=N, steps=steps)
     normals = C.analytic_normals(geom)
@@ -104,16 +110,20 @@ def test_learned_warm_start_reduces_iterations():
     c = C.midwall_centers(C.HELDOUT_SEEDS[:1])[0]
     V0 = C.ball_stimulus(grid, c, 0.1)
     w0 = np.zeros_like(V0)
-    hp = K.KFBI(geom, grid, tol=cfg.tol, precision=K.MIXED)
-    Vp, wp, sp = _run(hp, V0, w0, steps, K.MIXED)
-    hl = K.KFBI(geom, grid, tol=cfg.tol, precision=K.MIXED_LEARNED)
-    hl.set_warmstart(m)
-    Vl, wl, sl = _run(hl, V0, w0, steps, K.MIXED_LEARNED)
-    ip = sum(s["iters"] for s in sp[2:])
-    il = sum(s["iters"] for s in sl[2:])
-    used = sum(s["warmstart"] for s in sl)
-    print(f"GMRES iterations, steps 3..{steps}: previous-density {ip}, learned {il} (learned guess used {used}x)")
-    assert used > 0 and il < ip
-    assert all(s["rel_res"] <= cfg.tol for s in sl)
+    runs = {}
+    for name, prec, warm in (("previous", K.MIXED, K.WARM_PREVIOUS), ("projection", K.MIXED, K.WARM_PROJECTION),
+                             ("learned", K.MIXED_LEARNED, K.WARM_PREVIOUS)):
+        hh = K.KFBI(geom, grid, tol=cfg.tol, precision=prec, warm=warm)
+        if prec == K.MIXED_LEARNED:
+            hh.set_warmstart(m)
+        runs[name] = _run(hh, V0, w0, steps, prec)
+        hh.close()
+    its = {k: sum(s["iters"] for s in r[2][2:]) for k, r in runs.items()}
+    used = sum(s["warmstart"] for s in runs["learned"][2])
+    print(f"GMRES iterations, steps 3..{steps}: {its} (network guess kept {used}x)")
+    assert its["learned"] < its["previous"] and its["projection"] < its["previous"]
+    assert all(s["rel_res"] <= cfg.tol for r in runs.values() for s in r[2])
+    Vp = runs["previous"][0]
     scale = float(Vp.abs().max())
-    assert float((Vl - Vp).abs().max()) < 1e-6 * scale
+    for k in ("projection", "learned"):
+        assert float((runs[k][0] - Vp).abs().max()) < 1e-6 * scale
