@@ -123,9 +123,16 @@ int refined_solve(kfbi_handle* h, const double* src, double alpha, const double*
   if (rc) return rc;
   const int rounds = refine_rounds(h);
   for (int r = 0; r < rounds; ++r) {
-    if ((rc = launch_residual(h, src, alpha, corr, u, lambda, h->w.res64))) return rc;
     SolveArgs sr;
-    sr.src = h->w.res64;
+    if (r == 0 && src == nullptr) {
+      // u is exactly the float32 grid of the solve just done: float-float
+      // residual, float32 result
+      if ((rc = launch_residual_ff(h, corr, h->w.grid32, u, lambda, h->w.res32))) return rc;
+      sr.src32 = h->w.res32;
+    } else {
+      if ((rc = launch_residual(h, src, alpha, corr, u, lambda, h->w.res64))) return rc;
+      sr.src = h->w.res64;
+    }
     sr.lambda = lambda;
     sr.out_user = u;
     sr.aux = u;
@@ -520,6 +527,7 @@ int kfbi_create(const kfbi_geometry* geom, const kfbi_grid* grid, double sigma_i
   cudaMemsetAsync(h->w.psi_prev2, 0, sizeof(double) * (size_t)M, h->stream);
   if ((rc = dalloc(h, &h->w.u64, (size_t)grid_points(h)))) return fail(rc);
   if ((rc = dalloc(h, &h->w.res64, (size_t)grid_points(h)))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.res32, (size_t)grid_points(h)))) return fail(rc);
   cudaMemsetAsync(h->w.psi_prev, 0, sizeof(double) * (size_t)M, h->stream);
   if ((rc = dalloc(h, &h->w.hist_psi, (size_t)KFBI_HISTORY * M))) return fail(rc);
   if ((rc = dalloc(h, &h->w.hist_g, (size_t)KFBI_HISTORY * M))) return fail(rc);

@@ -330,6 +330,7 @@ struct DivPost {
 // r = alpha*src + corrections on the fly.
 template <typename T, int N, int DIM>
 __global__ void __launch_bounds__(NT) k_xfwd(T* __restrict__ a, const double* __restrict__ src, double alpha,
+                                             const float* __restrict__ src32,
                                              const double* __restrict__ corr, const int32_t* __restrict__ irr,
                                              const int32_t* __restrict__ line_start, const T* __restrict__ tw_g) {
   using C = Cfg<T, N>;
@@ -343,14 +344,31 @@ __global__ void __launch_bounds__(NT) k_xfwd(T* __restrict__ a, const double* __
   load_sines<T, N>(sinv, tw_g);
   const int y0 = blockIdx.x * W;
   const int z = DIM == 3 ? blockIdx.y + 1 : 0;
-  for (int idx = threadIdx.x; idx < N * W; idx += NT) {
-    const int x = idx % N, c = idx / N, y = y0 + c;
-    T v = (T)0;
-    if (src != nullptr && x > 0 && y > 0) {
-      const size_t line = DIM == 3 ? (size_t)(z - 1) * n1 + (y - 1) : (size_t)(y - 1);
-      v = (T)(alpha * src[line * n1 + (x - 1)]);
+  // the branch on src stays outside the loops: inside, the compiler
+  // evaluates the (float64) scaling for every element, taken or not
+  if (src != nullptr) {
+    const T a_t = (T)alpha;
+    for (int idx = threadIdx.x; idx < N * W; idx += NT) {
+      const int x = idx % N, c = idx / N, y = y0 + c;
+      T v = (T)0;
+      if (x > 0 && y > 0) {
+        const size_t line = DIM == 3 ? (size_t)(z - 1) * n1 + (y - 1) : (size_t)(y - 1);
+        v = a_t * (T)src[line * n1 + (x - 1)];
+      }
+      s[x * RS + c] = v;
     }
-    s[x * RS + c] = v;
+  } else if (src32 != nullptr) {
+    for (int idx = threadIdx.x; idx < N * W; idx += NT) {
+      const int x = idx % N, c = idx / N, y = y0 + c;
+      T v = (T)0;
+      if (x > 0 && y > 0) {
+        const size_t line = DIM == 3 ? (size_t)(z - 1) * n1 + (y - 1) : (size_t)(y - 1);
+        v = (T)src32[line * n1 + (x - 1)];
+      }
+      s[x * RS + c] = v;
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < N * W; idx += NT) s[(idx % N) * RS + idx / N] = (T)0;
   }
   __syncthreads();
   if (corr != nullptr && threadIdx.x < W) {
@@ -396,16 +414,26 @@ __global__ void __launch_bounds__(NT) k_xinv(T* __restrict__ a, bool keep, doubl
   }
   __syncthreads();
   dst_tile<C>(s, tw, sinv, tot);
+  if (out == nullptr) {
+    if (keep)
+      for (int idx = threadIdx.x; idx < N * W; idx += NT) {
+        const int x = idx % N, c = idx / N;
+        a[plane + (size_t)(y0 + c) * N + x] = s[x * RS + c];
+      }
+    return;
+  }
+  // out = beta v + gamma aux with beta applied in T (one float64 operation
+  // per element without aux, two with)
+  const T b_t = (T)beta;
   for (int idx = threadIdx.x; idx < N * W; idx += NT) {
     const int x = idx % N, c = idx / N, y = y0 + c;
     const T v = s[x * RS + c];
     if (keep) a[plane + (size_t)y * N + x] = v;
-    if (out != nullptr && x > 0 && y > 0) {
+    if (x > 0 && y > 0) {
       const size_t line = DIM == 3 ? (size_t)(z - 1) * n1 + (y - 1) : (size_t)(y - 1);
       const size_t o = line * n1 + (x - 1);
-      double r = beta * (double)v;
-      if (aux != nullptr) r += gamma * aux[o];
-      out[o] = r;
+      const double bv = (double)(b_t * v);
+      out[o] = aux != nullptr ? fma(gamma, aux[o], bv) : bv;
     }
   }
 }
@@ -673,7 +701,7 @@ int run_solve(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1, const 
   if (dim == 3) {
     dim3 grid(N / W, N - 1);
     if ((rc = prep(k_xfwd<T, N, 3>, smem))) return rc;
-    k_xfwd<T, N, 3><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.corr, t.irr, t.line_start, tw);
+    k_xfwd<T, N, 3><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.src32, sa.corr, t.irr, t.line_start, tw);
     if ((rc = launch_strided3<T, N>(h, 0, false, work, mu1, lam, scale, tw))) return rc;
     if ((rc = launch_strided3<T, N>(h, 1, true, work, mu1, lam, scale, tw))) return rc;
     if ((rc = launch_strided3<T, N>(h, 0, false, work, mu1, lam, scale, tw))) return rc;
@@ -682,7 +710,7 @@ int run_solve(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1, const 
   } else {
     dim3 grid(N / W, 1);
     if ((rc = prep(k_xfwd<T, N, 2>, smem))) return rc;
-    k_xfwd<T, N, 2><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.corr, t.irr, t.line_start, tw);
+    k_xfwd<T, N, 2><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.src32, sa.corr, t.irr, t.line_start, tw);
     if ((rc = prep(k_strided<T, N, true, 2>, smem))) return rc;
     k_strided<T, N, true, 2><<<grid, NT, smem, st>>>(work, N, 0, 0, mu1, lam, scale, tw);
     if ((rc = prep(k_xinv<T, N, 2>, smem))) return rc;
@@ -709,7 +737,7 @@ int run_pass(kfbi_handle* h, int pass, double lambda, T* work, const T* mu1, con
   if (dim == 3) {
     if (pass == 0) {
       if ((rc = prep(k_xfwd<T, N, 3>, smem))) return rc;
-      k_xfwd<T, N, 3><<<grid, NT, smem, st>>>(work, nullptr, 1.0, nullptr, t.irr, t.line_start, tw);
+      k_xfwd<T, N, 3><<<grid, NT, smem, st>>>(work, nullptr, 1.0, nullptr, nullptr, t.irr, t.line_start, tw);
     } else if (pass == 1) {
       if ((rc = launch_strided3<T, N>(h, 0, false, work, mu1, lam, scale, tw))) return rc;
     } else if (pass == 2) {
@@ -722,7 +750,7 @@ int run_pass(kfbi_handle* h, int pass, double lambda, T* work, const T* mu1, con
   } else {
     if (pass == 0) {
       if ((rc = prep(k_xfwd<T, N, 2>, smem))) return rc;
-      k_xfwd<T, N, 2><<<grid, NT, smem, st>>>(work, nullptr, 1.0, nullptr, t.irr, t.line_start, tw);
+      k_xfwd<T, N, 2><<<grid, NT, smem, st>>>(work, nullptr, 1.0, nullptr, nullptr, t.irr, t.line_start, tw);
     } else if (pass == 1 || pass == 2) {
       if ((rc = prep(k_strided<T, N, true, 2>, smem))) return rc;
       k_strided<T, N, true, 2><<<grid, NT, smem, st>>>(work, N, 0, 0, mu1, lam, scale, tw);

@@ -131,6 +131,7 @@ struct Workspace {
   double* g_prev = nullptr;       // [M] right-hand side of the previous diffusion solve
   double* u64 = nullptr;          // user-layout float64 grid (refined solutions)
   double* res64 = nullptr;        // user-layout float64 grid (refinement residuals)
+  float* res32 = nullptr;         // user-layout float32 grid (refinement residuals)
   double* hist_psi = nullptr;     // [KFBI_HISTORY][M] densities of past solves
   double* hist_g = nullptr;       // [KFBI_HISTORY][M] their right-hand sides
   double* psiF = nullptr;         // [M] projected density
@@ -190,6 +191,7 @@ int setup_build(kfbi_handle* h, const kfbi_geometry* geom);
 //  keep    : true = leave the solution in the padded work grid
 struct SolveArgs {
   const double* src = nullptr;
+  const float* src32 = nullptr;   // float32 source on the user layout (alpha not applied)
   double alpha = 1.0;
   const double* corr = nullptr;
   double* out_user = nullptr;
@@ -213,6 +215,11 @@ int launch_scatter_grid(kfbi_handle* h, const double* corr, double* grid_user);
 int launch_limit_user(kfbi_handle* h, const double* u, const double* x, const double* base, double sgn, double* out);
 int launch_residual(kfbi_handle* h, const double* src, double alpha, const double* corr, const double* u, double lambda,
                     double* res);
+// r = corr - L_h u (float32 result) for u held exactly by the padded float32
+// grid u32 (the output of a float32 solve) and by u64 on the user layout;
+// float-float arithmetic away from the interface, float64 at irregular nodes
+int launch_residual_ff(kfbi_handle* h, const double* corr, const float* u32, const double* u64, double lambda,
+                       float* res);
 int launch_lincomb(kfbi_handle* h, double* y, double a, const double* x, double b, int64_t n);
 int launch_padded_to_user(kfbi_handle* h, const double* padded, double* user);
 

@@ -129,6 +129,78 @@ __global__ void k_residual(GridParams gr, const double* __restrict__ src, double
   }
 }
 
+// error-free transformations: Knuth's TwoSum (s + e = a + b exactly) and the
+// product error by a fused multiply-add (p + e = a b exactly)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
+
+// r = -L_h u for u given exactly by the padded float32 grid of a float32
+// solve (index 0 of each axis holds the zero boundary value), in float-float
+// arithmetic: the float64 pipe is 1/64 of the float32 rate here, and the
+// 6-point sum of float32 values, ih2 and the diagonal kept as float pairs
+// give L_h u to about 1e-14 of its terms, ample for a refinement residual
+// that is 1e-7 of them.  One block row per (y, z) line.
+__global__ void k_residual_ff(GridParams gr, const float* __restrict__ u32, float ih2_hi, float ih2_lo, float dg_hi,
+                              float dg_lo, float* __restrict__ res) {
+  const int N = gr.N, n1 = N - 1;
+  const int y = blockIdx.x, z = blockIdx.y;
+  const size_t NN = (size_t)N * N;
+  const size_t pbase = gr.dim == 3 ? (size_t)(z + 1) * NN + (size_t)(y + 1) * N : (size_t)(y + 1) * N;
+  const size_t ubase = gr.dim == 3 ? ((size_t)z * n1 + y) * n1 : (size_t)y * n1;
+  for (int x = threadIdx.x; x < n1; x += blockDim.x) {
+    const size_t p = pbase + x + 1;
+    const float uc = u32[p];
+    float s = u32[p - 1], e = 0.0f, t;
+    two_sum(s, x < n1 - 1 ? u32[p + 1] : 0.0f, s, t);
+    e += t;
+    two_sum(s, u32[p - N], s, t);
+    e += t;
+    two_sum(s, y < n1 - 1 ? u32[p + N] : 0.0f, s, t);
+    e += t;
+    if (gr.dim == 3) {
+      two_sum(s, u32[p - NN], s, t);
+      e += t;
+      two_sum(s, z < n1 - 1 ? u32[p + NN] : 0.0f, s, t);
+      e += t;
+    }
+    float p1, e1, p2, e2, hsum, e3;
+    two_prod(ih2_hi, s, p1, e1);
+    e1 += ih2_hi * e + ih2_lo * s;
+    two_prod(dg_hi, uc, p2, e2);
+    e2 += dg_lo * uc;
+    two_sum(p1, p2, hsum, e3);
+    res[ubase + x] = -(hsum + (e1 + e2 + e3));
+  }
+}
+
+// at the irregular nodes, where the correction makes r a small difference of
+// large terms: r = corr - L_h u in float64 from the float64 copy of u
+__global__ void k_residual_irr(GridParams gr, Tables t, const double* __restrict__ corr, const double* __restrict__ u,
+                               double lambda, float* __restrict__ res) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.n_irr) return;
+  const int n1 = gr.N - 1;
+  const double ih2 = 1.0 / (gr.h * gr.h);
+  const double diag = -2.0 * gr.dim * ih2 - lambda;
+  const int64_t f = t.irr[i];
+  const int64_t s = (int64_t)n1 * n1;
+  const int x = (int)(f % n1), y = (int)((f / n1) % n1);
+  double nb = (x > 0 ? u[f - 1] : 0.0) + (x < n1 - 1 ? u[f + 1] : 0.0);
+  nb += (y > 0 ? u[f - n1] : 0.0) + (y < n1 - 1 ? u[f + n1] : 0.0);
+  if (gr.dim == 3) {
+    const int z = (int)(f / s);
+    nb += (z > 0 ? u[f - s] : 0.0) + (z < n1 - 1 ? u[f + s] : 0.0);
+  }
+  res[f] = (float)(corr[i] - (nb * ih2 + diag * u[f]));
+}
+
 __global__ void k_scatter_add(Tables t, const double* __restrict__ corr, double* __restrict__ g) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < t.n_irr) g[t.irr[i]] += corr[i];
@@ -429,6 +501,21 @@ int launch_residual(kfbi_handle* h, const double* src, double alpha, const doubl
   k_residual<<<dim3(n1, h->grid.dim == 3 ? n1 : 1), 128, 0, h->stream>>>(h->grid, src, alpha, u, lambda, res);
   if (corr != nullptr && h->t.n_irr > 0)
     k_scatter_add<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->t, corr, res);
+  KFBI_CHECK_LAUNCH_N(corr != nullptr && h->t.n_irr > 0 ? 2 : 1);
+  return KFBI_OK;
+}
+
+int launch_residual_ff(kfbi_handle* h, const double* corr, const float* u32, const double* u64, double lambda,
+                       float* res) {
+  const int n1 = h->grid.N - 1;
+  const double ih2 = 1.0 / (h->grid.h * h->grid.h);
+  const double dg = -2.0 * h->grid.dim * ih2 - lambda;
+  const float ih2_hi = (float)ih2, dg_hi = (float)dg;
+  const float ih2_lo = (float)(ih2 - (double)ih2_hi), dg_lo = (float)(dg - (double)dg_hi);
+  k_residual_ff<<<dim3(n1, h->grid.dim == 3 ? n1 : 1), 128, 0, h->stream>>>(h->grid, u32, ih2_hi, ih2_lo, dg_hi,
+                                                                             dg_lo, res);
+  if (corr != nullptr && h->t.n_irr > 0)
+    k_residual_irr<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->grid, h->t, corr, u64, lambda, res);
   KFBI_CHECK_LAUNCH_N(corr != nullptr && h->t.n_irr > 0 ? 2 : 1);
   return KFBI_OK;
 }

@@ -4,8 +4,10 @@
 
 Sets up the prolate-shell workload (configs 2/3 geometry), then runs each
 transform pass of the box solver, one irregular-node correction and one
-interface-limit gather `reps` times on the library's stream.  No timing is
-reported: this only gives a profiler a short, representative launch list.
+interface-limit gather `reps` times on the library's stream, and with
+--strang one Strang step of the bidomain model (reactions, refinement
+residuals, GMRES).  No timing is reported: this only gives a profiler a
+short, representative launch list.
 """
 from __future__ import annotations
 
@@ -28,6 +30,7 @@ def main():
     ap.add_argument("--N", type=int, default=256)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--strang", action="store_true")
     a = ap.parse_args()
     prec = K.FP64 if a.precision == "fp64" else K.MIXED
     geom, grid, cfg, V0, w0 = C.config2(N=a.N)
@@ -40,6 +43,10 @@ def main():
         for p in (0, 1, 2, 3):
             h.transform_pass(p, lam, prec)
         h.apply_A(psi, out, lam, prec)
+    if a.strang:
+        V = torch.tensor(V0, device=dev)
+        w = torch.tensor(w0, device=dev)
+        h.bidomain_step(C.FHN_CONFIG, V, w, None, nsteps=1, precision=prec)
     torch.cuda.synchronize()
     print("ok")
 
