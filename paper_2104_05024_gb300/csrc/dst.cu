@@ -320,7 +320,9 @@ struct DivPost {
   float base;       // mu1[p] + mu1[q] - lambda
   float scale;
   bool zero;        // boundary column p = 0
+  bool on = true;   // false: identity (the inverse transform of the same body)
   __device__ __forceinline__ float operator()(int j, float v) const {
+    if (!on) return v;
     return zero ? 0.0f : v * __fdividef(scale, mu[j] + base);
   }
 };
@@ -499,7 +501,12 @@ __global__ void __launch_bounds__(NT) k_strided(T* __restrict__ a, size_t row_st
 // wait is bounded: on timeout the block records DEVERR_TIMEOUT and returns.
 constexpr int TMA_W = 32;
 constexpr long TMA_WAIT_CAP = 1L << 22;
-constexpr int TMA_BLOCKS = 2;  // resident blocks per SM (at 3 the register DST spills)
+// resident blocks per SM: the solve pass (one DST body run twice) fits
+// three without spills, the plain pass spills at three
+template <bool SOLVE>
+constexpr int tma_blocks() {
+  return SOLVE ? 3 : 2;
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -549,7 +556,7 @@ constexpr size_t tma_smem_bytes() {
 
 // mode 0: tiles [y][x-chunk] of plane z = q; mode 1: tiles [z][x-chunk] of row y = q
 template <int N, bool SOLVE>
-__global__ void __launch_bounds__(NT, TMA_BLOCKS) k_strided_tma(const __grid_constant__ CUtensorMap map, int mode,
+__global__ void __launch_bounds__(NT, tma_blocks<SOLVE>()) k_strided_tma(const __grid_constant__ CUtensorMap map, int mode,
                                                     const float* __restrict__ mu1, float lambda, float scale,
                                                     const float* __restrict__ tw_g, int* __restrict__ err) {
   using C = TmaTile<N>;
@@ -610,13 +617,17 @@ __global__ void __launch_bounds__(NT, TMA_BLOCKS) k_strided_tma(const __grid_con
       if (threadIdx.x == 0) atomicOr(err, DEVERR_TIMEOUT);
       return;
     }
-    if (SOLVE) {
-      // forward DST with the spectral divide applied to its outputs
+    {
+      // forward DST with the spectral divide applied to its outputs, then the
+      // inverse DST by the same (single inlined) body
       const int q = t / NX + 1, p = (t % NX) * W + (int)(threadIdx.x & 31);
-      const DivPost post{mus, mus[p] + mus[q] - lambda, scale, p == 0};
-      regdst::dst1_tile_reg<regdst::Geo<N, W>>(s, sinv, reinterpret_cast<const regdst::cf2*>(tw), tot, post);
+      DivPost post{mus, mus[p] + mus[q] - lambda, scale, p == 0, SOLVE};
+#pragma unroll 1
+      for (int rep = 0; rep < (SOLVE ? 2 : 1); ++rep) {
+        regdst::dst1_tile_reg<regdst::Geo<N, W>>(s, sinv, reinterpret_cast<const regdst::cf2*>(tw), tot, post);
+        post.on = false;
+      }
     }
-    regdst::dst1_tile_reg<regdst::Geo<N, W>>(s, sinv, reinterpret_cast<const regdst::cf2*>(tw), tot);
     fence_async_shared();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -661,7 +672,8 @@ int launch_strided3(kfbi_handle* h, int mode, bool solve, T* work, const T* mu1,
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       const int tiles = (N / TMA_W) * (N - 1);
-      const int grid = tiles < TMA_BLOCKS * sms ? tiles : TMA_BLOCKS * sms;
+      const int nb = (solve ? tma_blocks<true>() : tma_blocks<false>()) * sms;
+      const int grid = tiles < nb ? tiles : nb;
       if (solve) {
         if ((rc = prep(k_strided_tma<N, true>, smem))) return rc;
         k_strided_tma<N, true><<<grid, NT, smem, st>>>(map, mode, mu1, lam, scale, tw, h->w.err);

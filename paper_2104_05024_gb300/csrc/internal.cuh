@@ -215,11 +215,12 @@ int launch_scatter_grid(kfbi_handle* h, const double* corr, double* grid_user);
 int launch_limit_user(kfbi_handle* h, const double* u, const double* x, const double* base, double sgn, double* out);
 int launch_residual(kfbi_handle* h, const double* src, double alpha, const double* corr, const double* u, double lambda,
                     double* res);
-// r = corr - L_h u (float32 result) for u held exactly by the padded float32
-// grid u32 (the output of a float32 solve) and by u64 on the user layout;
-// float-float arithmetic away from the interface, float64 at irregular nodes
-int launch_residual_ff(kfbi_handle* h, const double* corr, const float* u32, const double* u64, double lambda,
-                       float* res);
+// r = alpha*src + corr - L_h u (float32 result) for u held exactly by the
+// padded float32 grid u32 (the output of a float32 solve) and by u64 on the
+// user layout; float-float arithmetic away from the interface, float64 at
+// irregular nodes
+int launch_residual_ff(kfbi_handle* h, const double* src, double alpha, const double* corr, const float* u32,
+                       const double* u64, double lambda, float* res);
 int launch_lincomb(kfbi_handle* h, double* y, double a, const double* x, double b, int64_t n);
 int launch_padded_to_user(kfbi_handle* h, const double* padded, double* user);
 

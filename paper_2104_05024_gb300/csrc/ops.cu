@@ -148,7 +148,8 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
 // give L_h u to about 1e-14 of its terms, ample for a refinement residual
 // that is 1e-7 of them.  One block row per (y, z) line.
 __global__ void k_residual_ff(GridParams gr, const float* __restrict__ u32, float ih2_hi, float ih2_lo, float dg_hi,
-                              float dg_lo, float* __restrict__ res) {
+                              float dg_lo, const double* __restrict__ src, float al_hi, float al_lo,
+                              float* __restrict__ res) {
   const int N = gr.N, n1 = N - 1;
   const int y = blockIdx.x, z = blockIdx.y;
   const size_t NN = (size_t)N * N;
@@ -176,14 +177,26 @@ __global__ void k_residual_ff(GridParams gr, const float* __restrict__ u32, floa
     two_prod(dg_hi, uc, p2, e2);
     e2 += dg_lo * uc;
     two_sum(p1, p2, hsum, e3);
-    res[ubase + x] = -(hsum + (e1 + e2 + e3));
+    float lo = e1 + e2 + e3;
+    if (src != nullptr) {
+      // + alpha * src, src split into a float pair (the only float64 work)
+      const double sv = src[ubase + x];
+      const float sh = (float)sv, sl = (float)(sv - (double)sh);
+      float q, eq, h2, e4;
+      two_prod(al_hi, sh, q, eq);
+      eq += al_hi * sl + al_lo * sh;
+      two_sum(q, -hsum, h2, e4);
+      res[ubase + x] = h2 + (e4 + eq - lo);
+    } else {
+      res[ubase + x] = -(hsum + lo);
+    }
   }
 }
 
 // at the irregular nodes, where the correction makes r a small difference of
 // large terms: r = corr - L_h u in float64 from the float64 copy of u
 __global__ void k_residual_irr(GridParams gr, Tables t, const double* __restrict__ corr, const double* __restrict__ u,
-                               double lambda, float* __restrict__ res) {
+                               double lambda, const double* __restrict__ src, double alpha, float* __restrict__ res) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= t.n_irr) return;
   const int n1 = gr.N - 1;
@@ -198,7 +211,8 @@ __global__ void k_residual_irr(GridParams gr, Tables t, const double* __restrict
     const int z = (int)(f / s);
     nb += (z > 0 ? u[f - s] : 0.0) + (z < n1 - 1 ? u[f + s] : 0.0);
   }
-  res[f] = (float)(corr[i] - (nb * ih2 + diag * u[f]));
+  const double a = src != nullptr ? alpha * src[f] : 0.0;
+  res[f] = (float)(a + corr[i] - (nb * ih2 + diag * u[f]));
 }
 
 __global__ void k_scatter_add(Tables t, const double* __restrict__ corr, double* __restrict__ g) {
@@ -378,11 +392,13 @@ __global__ void k_react_fe(kfbi_fhn p, double k, double* __restrict__ V, double*
 
 // Backward-Euler half step: w is eliminated (w1 = (w0 + k alpha v) / (1 + k
 // zeta)) and Newton solves the cubic in v.  Float32 Newton steps first bring
-// v to float32 resolution; float64 steps then use the exact float64 residual
-// with the float32 derivative (a quasi-Newton step whose contraction factor
-// is the derivative's relative error, ~1e-7), which converges to float64
-// resolution in two steps without any float64 division.  Converged means a
-// float64 step below 1e-10, as in the plain Newton iteration.
+// v to float32 resolution (error e0 <~ 1e-7 |v|); a float64 step then uses
+// the exact float64 residual with the float32 derivative (a quasi-Newton step:
+// error <~ 1e-7 e0 + C e0^2, about 1e-14), without any float64 division.
+// Converged: the float32 phase converged and that float64 step moved v by
+// less than 1e-5 (so a further step would move it by < 1e-10, the plain
+// Newton criterion); otherwise float64 steps continue until a step is below
+// 1e-10.
 __global__ void k_react_be(kfbi_fhn p, double k, double* __restrict__ V, double* __restrict__ w, int64_t n,
                            int* err) {
   const double c = k * p.H / p.Cm;
@@ -403,6 +419,12 @@ __global__ void k_react_be(kfbi_fhn p, double k, double* __restrict__ V, double*
       vf -= dv;
       if (fabsf(dv) <= 1e-6f * fmaxf(1.0f, fabsf(vf))) break;
     }
+    bool f32_ok = false;
+    {
+      const float q1 = (q0f + kaf * vf) * idf;
+      const float Fv = vf - v0f - cf * (vf * (vf - thf) * (1.0f - vf) - q1);
+      f32_ok = fabsf(Fv) <= 1e-5f;
+    }
     double v = vf;
     bool ok = false;
     for (int it = 0; it < 50; ++it) {
@@ -412,7 +434,7 @@ __global__ void k_react_be(kfbi_fhn p, double k, double* __restrict__ V, double*
       const double F = v - v0 - c * (v * (v - p.theta) * (1.0 - v) - q1);
       const double dv = F * rdF;
       v -= dv;
-      if (fabs(dv) < 1e-10) {
+      if (fabs(dv) < 1e-10 || (it == 0 && f32_ok && fabs(dv) < 1e-5)) {
         ok = true;
         break;
       }
@@ -505,17 +527,19 @@ int launch_residual(kfbi_handle* h, const double* src, double alpha, const doubl
   return KFBI_OK;
 }
 
-int launch_residual_ff(kfbi_handle* h, const double* corr, const float* u32, const double* u64, double lambda,
-                       float* res) {
+int launch_residual_ff(kfbi_handle* h, const double* src, double alpha, const double* corr, const float* u32,
+                       const double* u64, double lambda, float* res) {
   const int n1 = h->grid.N - 1;
   const double ih2 = 1.0 / (h->grid.h * h->grid.h);
   const double dg = -2.0 * h->grid.dim * ih2 - lambda;
   const float ih2_hi = (float)ih2, dg_hi = (float)dg;
   const float ih2_lo = (float)(ih2 - (double)ih2_hi), dg_lo = (float)(dg - (double)dg_hi);
+  const float al_hi = (float)alpha, al_lo = (float)(alpha - (double)al_hi);
   k_residual_ff<<<dim3(n1, h->grid.dim == 3 ? n1 : 1), 128, 0, h->stream>>>(h->grid, u32, ih2_hi, ih2_lo, dg_hi,
-                                                                             dg_lo, res);
+                                                                             dg_lo, src, al_hi, al_lo, res);
   if (corr != nullptr && h->t.n_irr > 0)
-    k_residual_irr<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->grid, h->t, corr, u64, lambda, res);
+    k_residual_irr<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->grid, h->t, corr, u64, lambda, src, alpha,
+                                                                    res);
   KFBI_CHECK_LAUNCH_N(corr != nullptr && h->t.n_irr > 0 ? 2 : 1);
   return KFBI_OK;
 }
