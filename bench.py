@@ -207,11 +207,14 @@ def run_gpu(args):
                 "achieved": z_flops / z_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz"}
     else:
-        roof = {"kernel": "k_strided<float,256,SOLVE> (z pass: DST, divide, DST)", "bound": "hbm",
+        roof = {"kernel": f"k_strided_tma<{N},SOLVE> (z pass: DST, divide, DST)", "bound": "hbm",
                 "achieved": z_bytes / z_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "peak_source": kind}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    # DRAM read + write per launch of the float32 z pass at 256^3, from one ncu
+    # capture of that kernel (cold cache); none for other cases
+    roof["traffic"] = 73.5e6 if (prec_pass != K.FP64 and N == 256) else None
+    roof["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, cold cache)"
     roof["pass_ms"] = {k: round(v, 4) for k, v in pass_ms.items()}
     roof["hbm_gbs_per_pass"] = {k: round(2.0 * N ** 3 * esize / (v / 1e3) / 1e9, 1) for k, v in pass_ms.items()}
 

@@ -290,9 +290,20 @@ __device__ __forceinline__ void load_twiddles(T* tw_s, const T* tw_g) {
   for (int i = threadIdx.x; i < 4 * N; i += NT) tw_s[i] = tw_g[i];
 }
 
-// float32 tiles of 32 <= N <= 256 lines take the register-resident DST
+// Tile loads as asynchronous element copies (cp.async, 4 or 8 bytes): every
+// copy of the tile is in flight at once instead of a few loads per thread,
+// which is what keeps HBM busy when the grid does not fit in L2.
+template <typename T>
+__device__ __forceinline__ void copy_async(T* dst_smem, const T* src) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "element copies of 4 or 8 bytes");
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst_smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(sizeof(T)) : "memory");
+}
+__device__ __forceinline__ void copy_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// float32 tiles of 32 <= N <= 512 lines take the register-resident DST
 template <typename T, int N>
-constexpr bool kRegDst = sizeof(T) == 4 && N >= 32 && N <= 256;
+constexpr bool kRegDst = sizeof(T) == 4 && N >= 32 && N <= 512;
 
 // sines sin(pi j / N) for the register path's pre-fold (imaginary parts of tw)
 template <typename T, int N>
@@ -412,8 +423,9 @@ __global__ void __launch_bounds__(NT) k_xinv(T* __restrict__ a, bool keep, doubl
   const size_t plane = (size_t)z * N * N;
   for (int idx = threadIdx.x; idx < N * W; idx += NT) {
     const int x = idx % N, c = idx / N;
-    s[x * RS + c] = a[plane + (size_t)(y0 + c) * N + x];
+    copy_async(&s[x * RS + c], &a[plane + (size_t)(y0 + c) * N + x]);
   }
+  copy_async_wait();
   __syncthreads();
   dst_tile<C>(s, tw, sinv, tot);
   if (out == nullptr) {
@@ -462,8 +474,9 @@ __global__ void __launch_bounds__(NT) k_strided(T* __restrict__ a, size_t row_st
   T* base = a + (size_t)q * plane_stride + x0;
   for (int idx = threadIdx.x; idx < N * W; idx += NT) {
     const int c = idx % W, k = idx / W;
-    s[k * RS + c] = base[(size_t)k * row_stride + c];
+    copy_async(&s[k * RS + c], &base[(size_t)k * row_stride + c]);
   }
+  copy_async_wait();
   __syncthreads();
   const T muq = DIM == 3 ? mu1[q] : (T)0;
   if constexpr (kRegDst<T, N>) {

@@ -54,6 +54,23 @@ struct Dft<2> {
   }
 };
 
+// b_p = sum_q a_q e^{+2 pi i p q / 3}
+template <>
+struct Dft<3> {
+  static KFBI_HD void run(float* xr, float* xi) {
+    const float s3 = 0.86602540378443864676f;
+    const float tr = xr[1] + xr[2], ti = xi[1] + xi[2];
+    const float ur = xr[1] - xr[2], ui = xi[1] - xi[2];
+    const float mr = xr[0] - 0.5f * tr, mi = xi[0] - 0.5f * ti;
+    xr[0] += tr;
+    xi[0] += ti;
+    xr[1] = mr - s3 * ui;  // m + i s3 u
+    xi[1] = mi + s3 * ur;
+    xr[2] = mr + s3 * ui;  // m - i s3 u
+    xi[2] = mi - s3 * ur;
+  }
+};
+
 template <>
 struct Dft<4> {
   static KFBI_HD void run(float* xr, float* xi) {
@@ -157,6 +174,66 @@ struct Dft<16> {
   }
 };
 
+// P = R1 R2 with twiddles from the shared table tw2 (tw2[j] = e^{i pi j/N},
+// so e^{2 pi i e / P} = tw2[e * 2N/P]): q = R2 q1 + q2, p = p1 + R1 p2;
+// radix R1 over q1, twiddle e^{2 pi i p1 q2 / P}, radix R2 over q2
+template <int R1, int R2>
+struct DftT {
+  static KFBI_HD void run(float* xr, float* xi, const cf2* tw2, int jstep) {
+    constexpr int P = R1 * R2;
+#pragma unroll
+    for (int q2 = 0; q2 < R2; ++q2) {
+      float tr[R1], ti[R1];
+#pragma unroll
+      for (int q1 = 0; q1 < R1; ++q1) {
+        tr[q1] = xr[q2 + R2 * q1];
+        ti[q1] = xi[q2 + R2 * q1];
+      }
+      Dft<R1>::run(tr, ti);
+#pragma unroll
+      for (int p1 = 0; p1 < R1; ++p1) {
+        const int e = (p1 * q2) % P;
+        if (e == 0) {
+          xr[q2 + R2 * p1] = tr[p1];
+          xi[q2 + R2 * p1] = ti[p1];
+        } else {
+          const cf2 w = tw2[e * jstep];
+          xr[q2 + R2 * p1] = tr[p1] * w.x - ti[p1] * w.y;
+          xi[q2 + R2 * p1] = tr[p1] * w.y + ti[p1] * w.x;
+        }
+      }
+    }
+    float outr[P], outi[P];
+#pragma unroll
+    for (int p1 = 0; p1 < R1; ++p1) {
+      Dft<R2>::run(xr + R2 * p1, xi + R2 * p1);
+#pragma unroll
+      for (int p2 = 0; p2 < R2; ++p2) {
+        outr[p1 + R1 * p2] = xr[R2 * p1 + p2];
+        outi[p1 + R1 * p2] = xi[R2 * p1 + p2];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      xr[i] = outr[i];
+      xi[i] = outi[i];
+    }
+  }
+};
+
+// the first-level DFT of length P (P = 2, 4, 8, 16 with constant twiddles;
+// 24 = 3 x 8 and 32 = 4 x 8 with the shared table)
+template <int P, int N>
+KFBI_HD void dft_first(float* xr, float* xi, const cf2* tw2) {
+  if constexpr (P == 24) {
+    DftT<3, 8>::run(xr, xi, tw2, 2 * N / P);
+  } else if constexpr (P == 32) {
+    DftT<4, 8>::run(xr, xi, tw2, 2 * N / P);
+  } else {
+    Dft<P>::run(xr, xi);
+  }
+}
+
 // Tile geometry: N rows (transform index), W = 32 columns, row stride RS;
 // 8 warps, P points per thread in the first level.
 template <int N_, int RS_>
@@ -191,7 +268,7 @@ KFBI_HD void phase_a1(State<G>& st, const float* s, const float* sinv, const cf2
     st.zr[q] = m > 0 ? sn.x * (x0 + r0) + 0.5f * (x0 - r0) : 0.0f;
     st.zi[q] = sn.y * (x1 + r1) + 0.5f * (x1 - r1);
   }
-  Dft<P>::run(st.zr, st.zi);
+  dft_first<P, N>(st.zr, st.zi, tw2);
 #pragma unroll
   for (int k1 = 1; k1 < P; ++k1) {
     const cf2 w = tw2[4 * a * k1];  // e^{2 pi i a k1 / L}

@@ -48,6 +48,8 @@ int main() {
     case 64: return pad ? run<64, 33>() : run<64, 32>();
     case 128: return pad ? run<128, 33>() : run<128, 32>();
     case 256: return pad ? run<256, 33>() : run<256, 32>();
+    case 384: return pad ? run<384, 33>() : run<384, 32>();
+    case 512: return pad ? run<512, 33>() : run<512, 32>();
     default: return 2;
   }
 }

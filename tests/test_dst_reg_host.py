@@ -24,7 +24,7 @@ def harness(tmp_path_factory):
     return exe
 
 
-@pytest.mark.parametrize("N", [32, 64, 128, 256])
+@pytest.mark.parametrize("N", [32, 64, 128, 256, 384, 512])
 @pytest.mark.parametrize("RS", [32, 33])
 def test_register_dst_matches_scipy(harness, N, RS):
     x = np.random.default_rng(N + RS).standard_normal((32, N - 1))
