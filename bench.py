@@ -4,7 +4,7 @@ the 256^3 prolate-shell workload, each diffusion solve converged to a 1e-8
 GMRES residual, through the KFBI library's C ABI on one GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl kfbi|reference]
-    python bench.py --workload star-sweep|shell-large|heldout
+    python bench.py --workload star-sweep|shell-large|heldout|stiff
 
 One JSON line on rank 0.  Multi-GPU runs are independent replicas (one
 stimulus location per rank, no data-path collective); `value` sums the ranks.
@@ -488,6 +488,37 @@ def run_heldout(args):
                       "unit": "steps/s", "training": info, "rows": rows}), flush=True)
 
 
+def run_stiff(args):
+    """The paper's stiff FitzHugh-Nagumo parameters (H 100, theta 0.25,
+    alpha 0.25, zeta 1, beta 1000) with dt = h on the shell at N^3, GMRES and
+    the simple iteration (gamma 0.8), float64 and float32 transforms with
+    refinement, tol 1e-8: Strang steps/s and iterations per step."""
+    import torch
+
+    import paper_2104_05024_gb300.kfbi as K
+    from kfbi_workloads import configs as C
+    dev = torch.device("cuda", 0)
+    geom, grid, cfg0, V0, w0 = C.config2(N=args.N)
+    dt = grid.h
+    rows = {}
+    for name, prec, solver, warm in (("fp64_gmres", K.FP64, K.GMRES, K.WARM_PREVIOUS),
+                                     ("fp64_simple", K.FP64, K.RICHARDSON, K.WARM_PREVIOUS),
+                                     ("mixed_gmres_projection", K.MIXED, K.GMRES, K.WARM_PROJECTION),
+                                     ("mixed_simple", K.MIXED, K.RICHARDSON, K.WARM_PREVIOUS)):
+        h = K.KFBI(geom, grid, sigma_i=1.0, sigma_e=2.0, dt=dt, tol=1e-8, precision=prec, solver=solver,
+                   restart=50, max_iter=2000, warm=warm)
+        V, w = torch.tensor(V0, device=dev), torch.tensor(w0, device=dev)
+        h.bidomain_step(C.FHN_PAPER, V, w, None, nsteps=2)
+        ms, st = _event_ms(lambda: h.bidomain_step(C.FHN_PAPER, V, w, None, nsteps=args.steps))
+        rows[name] = {"steps_per_s": round(1000.0 * args.steps / ms, 3),
+                      "iters_per_step": float(np.mean([s["iters"] for s in st]))}
+        h.close()
+    print(json.dumps({"metric": "stiff FHN Strang steps/s, GMRES vs simple iteration",
+                      "workload": f"shell {args.N}^3, FHN H 100 theta 0.25 alpha 0.25 zeta 1 beta 1000, "
+                                  f"dt = h = {dt:.5f}, tol 1e-8, {args.steps} steps after 2",
+                      "unit": "steps/s", "rows": rows}), flush=True)
+
+
 # -------------------------------------------------------------- CPU oracle
 
 def cpu_baseline(N, steps=1):
@@ -542,7 +573,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--train-steps", type=int, default=12, help="Strang steps per training stimulus (learned form)")
     ap.add_argument("--train-epochs", type=int, default=8)
-    ap.add_argument("--workload", default="strang", choices=["strang", "star-sweep", "shell-large", "heldout"],
+    ap.add_argument("--workload", default="strang",
+                    choices=["strang", "star-sweep", "shell-large", "heldout", "stiff"],
                     help="strang: the timed benchmark; the others print one result line each")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -553,6 +585,8 @@ def main():
         run_shell_large(args)
     elif args.workload == "heldout":
         run_heldout(args)
+    elif args.workload == "stiff":
+        run_stiff(args)
     else:
         run_gpu(args)
 

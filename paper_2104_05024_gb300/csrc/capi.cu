@@ -257,7 +257,10 @@ int richardson(kfbi_handle* h, int prec, double lambda, const double* g, double*
   int it = 0;
   double rel = 0.0;
   for (;;) {
-    if ((rc = apply_A(h, prec, lambda, psi, r, -1.0, g))) return rc;
+    // float32 transforms: float64-accurate residuals (refined solves), so
+    // the iteration reaches float64 tolerances
+    rc = prec == KFBI_FP64 ? apply_A(h, prec, lambda, psi, r, -1.0, g) : apply_A_acc(h, lambda, psi, r, -1.0, g);
+    if (rc) return rc;
     double rn;
     if ((rc = norm2(h, r, s + small_nrm2(m), &rn))) return rc;
     rel = rn / gnorm;

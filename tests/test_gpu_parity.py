@@ -157,6 +157,48 @@ def test_gmres_fixed_iterations(name, lam):
         assert abs(st["rel_res"] - info["rel_res"]) < 1e-9 * max(info["rel_res"], 1e-3)
 
 
+@pytest.mark.parametrize("name,lam", [("ellipse64", 60.0), ("star32", 40.0)])
+def test_richardson_fixed_iterations(name, lam):
+    """The simple iteration psi <- psi + 2 gamma (g - A psi), gamma = 0.8
+    (Eq. simple iteration, Section 7), against the oracle's at fixed counts."""
+    geom, grid, o, g = pair(name)
+    gv = np.random.default_rng(4).standard_normal(geom.M)
+    for its in (1, 5, 12):
+        x, info = krylov.richardson(lambda v: o.apply_A(v, lam), gv, np.zeros(geom.M), 0.0, max_iter=its)
+        psi = torch.zeros(geom.M, dtype=torch.float64, device=DEV)
+        st = g.solve_bie(cuda(gv), psi, lam, tol=0.0, max_iter=its, solver=K.RICHARDSON)
+        g.set_opts(solver=K.GMRES, max_iter=500)
+        assert st["iters"] == its
+        assert rel(psi.cpu().numpy(), x) < TOL64
+        assert abs(st["rel_res"] - info["rel_res"]) < 1e-9 * info["rel_res"]
+
+
+def test_strang_stiff_richardson():
+    """The paper's stiff FitzHugh-Nagumo parameters (H = 100, theta = 0.25,
+    alpha = 0.25, zeta = 1, beta = 1000, Section 7) with dt = h and the simple
+    iteration as the solver, on the config-0 ellipse: three Strang steps
+    against the oracle (GMRES there; both converged to 1e-12)."""
+    geom, grid, _, V0, w0 = C.config0()
+    dt = grid.h
+    cfg = C.StrangConfig(sigma_i=1.0, sigma_e=2.0, dt=dt, steps=3, tol=1e-12)
+    lam = C.helmholtz_lambda(cfg, C.FHN_PAPER)
+    bd = Bidomain(geom, grid, cfg, C.FHN_PAPER, lam)
+    V, w = V0.copy(), w0.copy()
+    for _ in range(cfg.steps):
+        V, w, info = bd.step(V, w)
+        assert info["converged"] and info["newton_ok"]
+    for prec, tol, bar in ((K.FP64, 1e-12, TOL64), (K.MIXED, 1e-10, 1e-8)):
+        h = K.KFBI(geom, grid, sigma_i=1.0, sigma_e=2.0, dt=dt, tol=tol, solver=K.RICHARDSON, max_iter=2000,
+                   precision=prec)
+        Vd, wd = cuda(V0), cuda(w0)
+        st = h.bidomain_step(C.FHN_PAPER, Vd, wd, None, nsteps=cfg.steps)
+        h.close()
+        print(f"stiff FHN, simple iteration, precision {prec}: iterations per step {[s['iters'] for s in st]}")
+        assert all(s["rel_res"] <= tol for s in st)
+        assert rel(Vd.cpu().numpy(), V) < bar
+        assert rel(wd.cpu().numpy(), w) < bar
+
+
 @pytest.mark.parametrize("name,lam", [("ellipse128", 60.0), ("star64", 40.0), ("shell64", 60.0), ("sphere32", 40.0)])
 def test_solve_neumann_manufactured(name, lam):
     geom, grid, o, g = pair(name)
