@@ -153,11 +153,11 @@ int apply_A_acc(kfbi_handle* h, double lambda, const double* psi, double* out, d
   return launch_limit_user(h, h->w.u64, x, base, sgn, out);
 }
 
-// g = gN - dv_V^+/dn with the refined volume solve
+// g = gN - dv_V^+/dn with the refined volume solve (v_V kept in vV64)
 int rhs_g_acc(kfbi_handle* h, double lambda, const double* src, double alpha, const double* gN, double* g) {
-  int rc = refined_solve(h, src, alpha, nullptr, lambda, h->w.u64);
+  int rc = refined_solve(h, src, alpha, nullptr, lambda, h->w.vV64);
   if (rc) return rc;
-  return launch_limit_user(h, h->w.u64, nullptr, gN, -1.0, g);
+  return launch_limit_user(h, h->w.vV64, nullptr, gN, -1.0, g);
 }
 
 // GMRES(m) with CGS2 Arnoldi on A psi = g; psi in: initial guess, out: solution.
@@ -531,6 +531,7 @@ int kfbi_create(const kfbi_geometry* geom, const kfbi_grid* grid, double sigma_i
   if ((rc = dalloc(h, &h->w.u64, (size_t)grid_points(h)))) return fail(rc);
   if ((rc = dalloc(h, &h->w.res64, (size_t)grid_points(h)))) return fail(rc);
   if ((rc = dalloc(h, &h->w.res32, (size_t)grid_points(h)))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.vV64, (size_t)grid_points(h)))) return fail(rc);
   cudaMemsetAsync(h->w.psi_prev, 0, sizeof(double) * (size_t)M, h->stream);
   if ((rc = dalloc(h, &h->w.hist_psi, (size_t)KFBI_HISTORY * M))) return fail(rc);
   if ((rc = dalloc(h, &h->w.hist_g, (size_t)KFBI_HISTORY * M))) return fail(rc);
@@ -805,11 +806,12 @@ int bidomain_step(kfbi_handle* h, const kfbi_fhn* p, double* V_dev, double* w_de
     if ((rc = push_history(h, h->w.psi_prev, h->w.g))) return rc;
     ++h->n_hist;
     if (src == KFBI_ERR_NOT_CONVERGED) final_rc = src;
-    // V <- 2 (v_V + v_B(psi)) - V, one solve of the combined right-hand side
-    const double* x;
-    if ((rc = density_vector(h, h->w.psi_prev, &x))) return rc;
-    if ((rc = launch_correction(h, x, h->w.corr))) return rc;
+    // V <- 2 (v_V + v_B(psi)) - V
     if (prec == KFBI_FP64) {
+      // one float64 solve of the combined right-hand side
+      const double* x;
+      if ((rc = density_vector(h, h->w.psi_prev, &x))) return rc;
+      if ((rc = launch_correction(h, x, h->w.corr))) return rc;
       SolveArgs sa;
       sa.src = V_dev;
       sa.alpha = -lam;
@@ -821,8 +823,9 @@ int bidomain_step(kfbi_handle* h, const kfbi_fhn* p, double* V_dev, double* w_de
       sa.gamma = -1.0;
       if ((rc = box_solve64(h, sa, h->w.grid64))) return rc;
     } else {
-      if ((rc = refined_solve(h, V_dev, -lam, h->w.corr, lam, h->w.u64))) return rc;
-      if ((rc = launch_lincomb(h, V_dev, 2.0, h->w.u64, -1.0, n))) return rc;
+      // the refined solver's last act was the float64-accurate residual at
+      // the final density, which left v_B(psi) in u64; v_V is in vV64
+      if ((rc = launch_midpoint(h, V_dev, h->w.vV64, h->w.u64, n))) return rc;
     }
     if ((rc = launch_react_be(p, k, V_dev, w_dev, n, h->w.err, h->stream))) return rc;
     st.true_rel_res = -1.0;

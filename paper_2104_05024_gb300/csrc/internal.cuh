@@ -131,6 +131,7 @@ struct Workspace {
   double* g_prev = nullptr;       // [M] right-hand side of the previous diffusion solve
   double* u64 = nullptr;          // user-layout float64 grid (refined solutions)
   double* res64 = nullptr;        // user-layout float64 grid (refinement residuals)
+  double* vV64 = nullptr;         // user-layout float64 volume solution v_V of the step
   float* res32 = nullptr;         // user-layout float32 grid (refinement residuals)
   double* hist_psi = nullptr;     // [KFBI_HISTORY][M] densities of past solves
   double* hist_g = nullptr;       // [KFBI_HISTORY][M] their right-hand sides
@@ -222,6 +223,8 @@ int launch_residual(kfbi_handle* h, const double* src, double alpha, const doubl
 int launch_residual_ff(kfbi_handle* h, const double* src, double alpha, const double* corr, const float* u32,
                        const double* u64, double lambda, float* res);
 int launch_lincomb(kfbi_handle* h, double* y, double a, const double* x, double b, int64_t n);
+// V <- 2 (vV + uB) - V (implicit midpoint from the two parts of u)
+int launch_midpoint(kfbi_handle* h, double* V, const double* vV, const double* uB, int64_t n);
 int launch_padded_to_user(kfbi_handle* h, const double* padded, double* user);
 
 // GMRES vector kernels (ops.cu)

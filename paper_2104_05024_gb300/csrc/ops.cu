@@ -220,6 +220,12 @@ __global__ void k_scatter_add(Tables t, const double* __restrict__ corr, double*
   if (i < t.n_irr) g[t.irr[i]] += corr[i];
 }
 
+__global__ void k_midpoint(double* __restrict__ V, const double* __restrict__ vV, const double* __restrict__ uB,
+                           int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    V[i] = 2.0 * (vV[i] + uB[i]) - V[i];
+}
+
 __global__ void k_lincomb(double* __restrict__ y, double a, const double* __restrict__ x, double b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = a * x[i] + b * y[i];
@@ -541,6 +547,12 @@ int launch_residual_ff(kfbi_handle* h, const double* src, double alpha, const do
     k_residual_irr<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->grid, h->t, corr, u64, lambda, src, alpha,
                                                                     res);
   KFBI_CHECK_LAUNCH_N(corr != nullptr && h->t.n_irr > 0 ? 2 : 1);
+  return KFBI_OK;
+}
+
+int launch_midpoint(kfbi_handle* h, double* V, const double* vV, const double* uB, int64_t n) {
+  k_midpoint<<<grid_blocks(n, 256), 256, 0, h->stream>>>(V, vV, uB, n);
+  KFBI_CHECK_LAUNCH();
   return KFBI_OK;
 }
 
