@@ -123,6 +123,19 @@ def config2(N: int = 256, steps: int = 200, n_surf: int | None = None):
     return geom, grid, cfg, V0, np.zeros_like(V0)
 
 
+def virtual_electrode(grid: Grid, v_stim: float = 10.0, offset: float = 0.3, radius: float = 0.25) -> np.ndarray:
+    """I_stim of the virtual electrode (Section 7): +v_stim within `radius` of
+    the anode at (-offset, 0[, 0]), -v_stim within `radius` of the cathode at
+    (+offset, 0[, 0]) (reading of the order of the two positions)."""
+    X = grid.coords()
+    ra = sum((X[a] - (-offset if a == 0 else 0.0)) ** 2 for a in range(grid.dim))
+    rc = sum((X[a] - (offset if a == 0 else 0.0)) ** 2 for a in range(grid.dim))
+    out = np.zeros(np.broadcast(*X).shape)
+    out[ra < radius * radius] = v_stim
+    out[rc < radius * radius] = -v_stim
+    return out
+
+
 def midwall_centers(seeds):
     """Stimulus centres uniform over the mid-wall ellipsoid (0.8, 0.5, 0.5):
     cos(theta) ~ U(-1, 1), phi ~ U(0, 2 pi) from default_rng(seed)."""

@@ -17,6 +17,16 @@ is constant and the extracellular potential with zero mean over Omega is
 The state (V, q) lives on every box node: the right-hand side -lambda V^n is
 the continuous extension of the source to the box (Section 5.1) and the
 diffusion result u = v_V + v_B is kept on all nodes.
+
+With the extracellular stimulus I_stim of the virtual electrode (Section 7),
+the same elimination of Eq. pde1 gives
+    Lap V - lambda V = -lambda V^n + beta I_stim / sigma_e,
+    Lap S = -beta I_stim,   S = sigma_i Phi_i + sigma_e Phi_e,
+both with homogeneous Neumann data; the S problem is a Poisson problem
+(lambda = 0, solved with the rank-one modification of the boundary operator)
+whose right-hand side does not change with time, so it is solved once.  Then
+Phi_e = (S - sigma_i V) / (sigma_i + sigma_e), reported with zero mean over
+Omega.
 """
 from __future__ import annotations
 
@@ -31,12 +41,39 @@ def extracellular(V, inside, sigma_i, sigma_e):
     return sigma_i * (mean - V) / (sigma_i + sigma_e)
 
 
+def extracellular_S(V, S, inside, sigma_i, sigma_e):
+    """Phi_e = (S - sigma_i V) / (sigma_i + sigma_e) with zero mean over Omega."""
+    phi = (S - sigma_i * V) / (sigma_i + sigma_e)
+    return phi - phi[inside].mean()
+
+
 class Bidomain:
-    def __init__(self, geom, grid, cfg, fhn, lam):
+    def __init__(self, geom, grid, cfg, fhn, lam, istim=None):
         self.k = KFBI(geom, grid)
         self.cfg, self.fhn, self.lam = cfg, fhn, lam
         self.psi_prev = np.zeros(geom.M)
         self.gN = np.zeros(geom.M)
+        self.istim = istim
+        self.S = None
+        self.S_info = None
+
+    def solve_S(self):
+        """The Poisson problem Lap S = -beta I_stim with homogeneous Neumann data."""
+        if self.S is None:
+            self.S, _, self.S_info = self.k.solve_neumann(-self.fhn.beta * self.istim, self.gN, 0.0,
+                                                          tol=self.cfg.tol)
+        return self.S
+
+    def diffuse(self, V, psi0=None):
+        """Backward-Euler half step of the diffusion (the midpoint's w)."""
+        cfg, fhn = self.cfg, self.fhn
+        x0 = self.psi_prev if psi0 is None else psi0
+        f = -self.lam * V
+        if self.istim is not None:
+            f = f + (fhn.beta / cfg.sigma_e) * self.istim
+        w, psi, info = self.k.solve_neumann(f, self.gN, self.lam, tol=cfg.tol, psi0=x0)
+        self.psi_prev = psi
+        return w, info
 
     def step(self, V, q, psi0=None):
         """One Strang step; returns (V, q, stats).  psi0 is the GMRES initial
@@ -44,9 +81,7 @@ class Bidomain:
         cfg, fhn = self.cfg, self.fhn
         kk = cfg.dt / 2.0
         V, q = reaction.forward_euler(V, q, kk, fhn)
-        x0 = self.psi_prev if psi0 is None else psi0
-        w, psi, info = self.k.solve_neumann(-self.lam * V, self.gN, self.lam, tol=cfg.tol, psi0=x0)
-        self.psi_prev = psi
+        w, info = self.diffuse(V, psi0)
         V = 2.0 * w - V
         V, q, ok = reaction.backward_euler(V, q, kk, fhn)
         info["newton_ok"] = bool(ok.all())

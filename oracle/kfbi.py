@@ -27,6 +27,16 @@ axis a lies across the crossing z, with d = x_{p'} - z,
     RHS(p) += -J(p')/h^2 if p is inside Omega, +J(p')/h^2 otherwise,
 summed over every crossing arm of the node.
 
+Poisson case (lambda = 0): A then has a one-dimensional null space and its
+range is orthogonal to constants (Green's identity: the boundary integral of
+dv_B^+/dn equals the volume integral of Lap v_B = 0).  The paper is silent;
+reading: the operator is replaced by the rank-one modification
+    A psi + <ds, psi> / |Gamma|,
+with ds the boundary quadrature weights (2-D: half the lengths of the two
+chords at a node; 3-D: a third of the areas of the incident triangles) and
+|Gamma| their sum, which is nonsingular and has the same solutions for
+compatible data.
+
 Interpolation (Section 5.4, Eqs. taylor-*, ji, je): at an interface node q,
 the quadratic Taylor polynomial of v^+ about q is fitted through a 6-point
 (2-D) / 10-point (3-D) stencil: the grid node c nearest to q, its 2d axis
@@ -77,6 +87,23 @@ def taylor_rows(xi: np.ndarray) -> np.ndarray:
     return np.stack(cols, axis=-1)
 
 
+def surface_weights(geom: G.Geometry) -> np.ndarray:
+    """Quadrature weights of the interface nodes: 2-D, half the lengths of the
+    chords to the two neighbouring nodes; 3-D, a third of the areas of the
+    triangles incident to the node."""
+    X = geom.nodes
+    if X.shape[1] == 2:
+        seg = np.linalg.norm(np.roll(X, -1, axis=0) - X, axis=1)
+        return 0.5 * (seg + np.roll(seg, 1))
+    tri = np.asarray(geom.tri, dtype=np.int64)
+    a, b, c = X[tri[:, 0]], X[tri[:, 1]], X[tri[:, 2]]
+    area = 0.5 * np.linalg.norm(np.cross(b - a, c - a), axis=1)
+    ds = np.zeros(X.shape[0])
+    for k in range(3):
+        np.add.at(ds, tri[:, k], area / 3.0)
+    return ds
+
+
 class KFBI:
     """Setup (Section 6) and integral evaluations for one geometry and grid."""
 
@@ -97,6 +124,8 @@ class KFBI:
                 self.n_int[m], self.S_int[m] = LS.normal_shape(geom, c, self.Pint[m])
         self.n_node, self.S_node = LS.normals_shapes_at_nodes(geom)
         self.center, self.sign = GR.cell_index(grid, geom.nodes)
+        self.ds = surface_weights(geom)
+        self.area = float(self.ds.sum())
         self._setup_stencils()
         self._setup_density()
 
@@ -217,10 +246,14 @@ class KFBI:
 
     # -------------------------------------------------------- operators
     def apply_A(self, psi: np.ndarray, lam: float) -> np.ndarray:
+        """A psi, plus the rank-one term <ds, psi>/|Gamma| when lam = 0."""
         (dv, ddv), (jg, jH) = self.jumps(psi)
         rhs = self.correction(np.zeros_like(dv), dv, ddv)
         vB = boxsolve.solve(rhs, lam, self.grid)
-        return self.interp(vB, (np.zeros(psi.size), jg, jH))
+        out = self.interp(vB, (np.zeros(psi.size), jg, jH))
+        if lam == 0.0:
+            out = out + (self.ds @ psi) / self.area
+        return out
 
     def volume(self, f: np.ndarray, lam: float) -> np.ndarray:
         return boxsolve.solve(f, lam, self.grid)

@@ -298,3 +298,95 @@ def test_green_identity_discrete():
     ds = 0.5 * (np.linalg.norm(seg, axis=1) + np.roll(np.linalg.norm(seg, axis=1), 1))
     flux = (gN * ds).sum()
     assert abs(vol - flux) < 0.05 * abs(flux) + 0.05
+
+
+# ------------------------------------------------ Poisson case and stimulus
+
+def test_surface_weights():
+    from oracle.kfbi import surface_weights
+    import scipy.integrate as si
+    geom = G.ellipse_config0(256)
+    per = si.quad(lambda t: math.hypot(0.7 * math.sin(t), 0.45 * math.cos(t)), 0.0, 2.0 * math.pi,
+                  epsabs=1e-13)[0]
+    assert abs(surface_weights(geom).sum() / per - 1.0) < 1e-4
+    # inscribed triangles: the area converges to 4 pi r^2 from below at second order
+    e = [4.0 * math.pi * 0.36 - surface_weights(G.sphere3(0.6, n)).sum() for n in (8, 16)]
+    assert 0.0 < e[1] < e[0] and 3.0 < e[0] / e[1] < 5.0
+
+
+def test_poisson_neumann_second_order_2d():
+    """lambda = 0 with the rank-one modification: the solution (up to its
+    constant) converges at second order, and <ds, psi> (the part of the
+    density that absorbs the discrete incompatibility of the data) vanishes
+    at second order."""
+    errs, dpsi = [], []
+    for N in (32, 64, 128):
+        geom, grid = G.ellipse_config0(2 * N), Grid(2, N)
+        f, u, gN = C.manufactured(geom, grid, 0.0)
+        k = KFBI(geom, grid)
+        uh, psi, info = k.solve_neumann(f, gN, 0.0, tol=1e-12)
+        assert info["converged"]
+        ins = k.inside
+        e = (uh - uh[ins].mean()) - (u - u[ins].mean())
+        errs.append(math.sqrt((e[ins] ** 2).mean()))
+        dpsi.append(abs(k.ds @ psi))
+    assert min(_rate(errs)) > 1.7
+    assert min(_rate(dpsi)) > 1.7
+
+
+def test_virtual_electrode_symmetry():
+    """On a disk the electrode is odd in x, so S + S(-x) is constant."""
+    from oracle.bidomain import Bidomain
+    geom, grid = G.disk2(0.6, 128), Grid(2, 64)
+    cfg = C.StrangConfig(sigma_i=1.0, sigma_e=2.0, dt=grid.h, steps=1, tol=1e-12)
+    bd = Bidomain(geom, grid, cfg, C.FHN_PAPER, C.helmholtz_lambda(cfg, C.FHN_PAPER),
+                  istim=C.virtual_electrode(grid))
+    S = bd.solve_S()
+    assert bd.S_info["converged"]
+    T = S + S[:, ::-1]
+    ins = bd.k.inside
+    assert np.abs(T[ins] - T[ins].mean()).max() < 1e-10 * np.abs(S[ins]).max()
+
+
+def test_virtual_electrode_coupled_equations():
+    """The elimination behind the V and S problems, checked against Eq. pde1
+    itself: with Phi_i = (S + sigma_e w)/(sigma_i + sigma_e) and
+    Phi_e = (S - sigma_i w)/(sigma_i + sigma_e) from the oracle's w and S,
+        sigma_i Lap_h Phi_i - kappa (w - V^n) = 0,
+        sigma_e Lap_h Phi_e + kappa (w - V^n) = -beta I_stim
+    hold at every regular node inside (where L_h u equals the right-hand side
+    exactly)."""
+    from oracle.bidomain import Bidomain
+    from oracle import boxsolve
+    geom, grid = G.ellipse_config0(256), Grid(2, 64)
+    cfg = C.StrangConfig(sigma_i=1.0, sigma_e=2.0, dt=grid.h, steps=1, tol=1e-12)
+    fhn = C.FHN_PAPER
+    I = C.virtual_electrode(grid)
+    bd = Bidomain(geom, grid, cfg, fhn, C.helmholtz_lambda(cfg, fhn), istim=I)
+    Vn = 0.3 * np.cos(3.0 * grid.coords()[0]) * np.ones(grid.shape)
+    w, info = bd.diffuse(Vn)
+    S = bd.solve_S()
+    si_, se_ = cfg.sigma_i, cfg.sigma_e
+    kappa = fhn.Cm * fhn.beta / (cfg.dt / 2.0)
+    phi_i = (S + se_ * w) / (si_ + se_)
+    phi_e = (S - si_ * w) / (si_ + se_)
+    lap = lambda v: boxsolve.apply_L(v, 0.0, grid)  # noqa: E731
+    reg = bd.k.inside.copy()
+    reg.ravel()[bd.k.irregular] = False
+    r1 = si_ * lap(phi_i) - kappa * (w - Vn)
+    r2 = se_ * lap(phi_e) + kappa * (w - Vn) + fhn.beta * I
+    scale = fhn.beta * np.abs(I).max()
+    assert np.abs(r1[reg]).max() < 1e-9 * scale
+    assert np.abs(r2[reg]).max() < 1e-9 * scale
+
+
+def test_extracellular_from_constant_S():
+    """Without a stimulus S is constant and the S-based potential reduces to
+    sigma_i (mean V - V)/(sigma_i + sigma_e)."""
+    from oracle.bidomain import extracellular, extracellular_S
+    rng = np.random.default_rng(2)
+    V = rng.standard_normal((20, 20))
+    inside = rng.random((20, 20)) < 0.6
+    a = extracellular(V, inside, 1.0, 2.0)
+    b = extracellular_S(V, np.full_like(V, 3.7), inside, 1.0, 2.0)
+    assert np.abs(a - b).max() < 1e-14
