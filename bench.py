@@ -4,7 +4,7 @@ the 256^3 prolate-shell workload, each diffusion solve converged to a 1e-8
 GMRES residual, through the KFBI library's C ABI on one GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl kfbi|reference]
-    python bench.py --workload star-sweep|shell-large|heldout|stiff
+    python bench.py --workload star-sweep|shell-large|heldout|stiff|stimulus
 
 One JSON line on rank 0.  Multi-GPU runs are independent replicas (one
 stimulus location per rank, no data-path collective); `value` sums the ranks.
@@ -519,6 +519,40 @@ def run_stiff(args):
                       "unit": "steps/s", "rows": rows}), flush=True)
 
 
+def run_stimulus(args):
+    """Virtual electrode (Section 7: +-10 in balls of radius 0.25 at
+    (-+0.3, 0, 0)) on a sphere of radius 0.6 at N^3 with the paper's
+    FitzHugh-Nagumo parameters, dt = h, tol 1e-8: the S Poisson problem
+    (solved once per call) and Strang steps/s, float64 and float32 transforms
+    with refinement and the history projection."""
+    import torch
+
+    import paper_2104_05024_gb300.kfbi as K
+    from kfbi_workloads import configs as C, geometry as G
+    dev = torch.device("cuda", 0)
+    N = args.N
+    geom, grid = G.sphere3(0.6, C.surface_res(N)), C.Grid(3, N)
+    I = torch.tensor(C.virtual_electrode(grid), device=dev)
+    rows = {}
+    for name, prec, warm in (("fp64", K.FP64, K.WARM_PREVIOUS), ("mixed_projection", K.MIXED, K.WARM_PROJECTION)):
+        h = K.KFBI(geom, grid, sigma_i=1.0, sigma_e=2.0, dt=grid.h, tol=1e-8, precision=prec, warm=warm,
+                   restart=50, max_iter=400)
+        V = torch.zeros(grid.shape, dtype=torch.float64, device=dev)
+        w = torch.zeros_like(V)
+        ue = torch.empty_like(V)
+        ms0, _ = _event_ms(lambda: h.bidomain_step(C.FHN_PAPER, V, w, ue, nsteps=1, istim=I))
+        ms, st = _event_ms(lambda: h.bidomain_step(C.FHN_PAPER, V, w, ue, nsteps=args.steps, istim=I))
+        ms_s = ms0 - ms / args.steps   # the S solve of a call, less one step
+        rows[name] = {"steps_per_s": round(1000.0 * args.steps / ms, 3),
+                      "iters_per_step": float(np.mean([s["iters"] for s in st])),
+                      "S_solve_ms": round(ms_s, 2), "V_max": float(V.abs().max()), "ue_max": float(ue.abs().max())}
+        h.close()
+    print(json.dumps({"metric": "virtual-electrode Strang steps/s and S Poisson solve",
+                      "workload": f"sphere r 0.6, {N}^3, FHN H 100 theta 0.25 alpha 0.25 zeta 1 beta 1000, "
+                                  f"dt = h, tol 1e-8, {args.steps} steps (one call)",
+                      "unit": "steps/s", "rows": rows}), flush=True)
+
+
 # -------------------------------------------------------------- CPU oracle
 
 def cpu_baseline(N, steps=1):
@@ -574,7 +608,7 @@ def main():
     ap.add_argument("--train-steps", type=int, default=12, help="Strang steps per training stimulus (learned form)")
     ap.add_argument("--train-epochs", type=int, default=8)
     ap.add_argument("--workload", default="strang",
-                    choices=["strang", "star-sweep", "shell-large", "heldout", "stiff"],
+                    choices=["strang", "star-sweep", "shell-large", "heldout", "stiff", "stimulus"],
                     help="strang: the timed benchmark; the others print one result line each")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -587,6 +621,8 @@ def main():
         run_heldout(args)
     elif args.workload == "stiff":
         run_stiff(args)
+    elif args.workload == "stimulus":
+        run_stimulus(args)
     else:
         run_gpu(args)
 

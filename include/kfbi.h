@@ -170,6 +170,12 @@ int kfbi_set_opts(kfbi_handle* h, const kfbi_opts* opts);
  * f given on every box node (its continuous extension, Section 5.1).
  * psi_dev: in = initial density (warm start), out = converged density.
  * u_dev:   out = u = v_V + v_B on every box node.
+ * lambda = 0 (Poisson): A then has a one-dimensional null space and its range
+ * is orthogonal to constants; every operator application uses the rank-one
+ * modification A psi + <ds, psi>/|Gamma| (ds the boundary quadrature weights:
+ * 2-D half the two chord lengths at a node, 3-D a third of the incident
+ * triangle areas), which has the same solutions for compatible data and
+ * absorbs the small incompatibility of discrete data.
  * Returns KFBI_ERR_NOT_CONVERGED (outputs still written) if max_iter is hit.
  */
 int kfbi_solve_neumann(kfbi_handle* h, double lambda, const double* f_dev, const double* gN_dev,
@@ -186,6 +192,17 @@ int kfbi_solve_neumann(kfbi_handle* h, double lambda, const double* f_dev, const
  */
 int bidomain_step(kfbi_handle* h, const kfbi_fhn* p, double* V_dev, double* w_dev, double* ue_dev,
                   int nsteps, kfbi_stats* per_step);
+/* bidomain_step with the extracellular stimulus of a virtual electrode
+ * (Section 7): istim_dev (user layout, float64) is I_stim on every interior
+ * node, constant in time.  The isotropic elimination of Eq. pde1 gives
+ *   Lap V - lambda V = -lambda V^n + beta I / sigma_e      (V problem),
+ *   Lap S = -beta I,  S = sigma_i Phi_i + sigma_e Phi_e     (S problem),
+ * both with homogeneous Neumann data.  The S problem (lambda = 0, with the
+ * rank-one modification described at kfbi_solve_neumann) is solved once per
+ * call; ue_dev (optional) receives Phi_e = (S - sigma_i V)/(sigma_i +
+ * sigma_e) with zero mean over Omega.  NULL istim_dev is bidomain_step.      */
+int kfbi_bidomain_step_stim(kfbi_handle* h, const kfbi_fhn* p, const double* istim_dev, double* V_dev,
+                            double* w_dev, double* ue_dev, int nsteps, kfbi_stats* per_step);
 
 /* ------------------------------------------------------------------
  * Step-level entry points (one per row of the hot path), used for parity

@@ -72,10 +72,14 @@ int apply_A(kfbi_handle* h, int prec, double lambda, const double* psi, double* 
   sa.lambda = lambda;
   if (prec == KFBI_FP64) {
     if ((rc = box_solve64(h, sa, h->w.grid64))) return rc;
-    return launch_limit64(h, h->w.grid64, x, base, sgn, out);
+    rc = launch_limit64(h, h->w.grid64, x, base, sgn, out);
+  } else {
+    if ((rc = box_solve32(h, sa, h->w.grid32))) return rc;
+    rc = launch_limit32(h, h->w.grid32, x, base, sgn, out);
   }
-  if ((rc = box_solve32(h, sa, h->w.grid32))) return rc;
-  return launch_limit32(h, h->w.grid32, x, base, sgn, out);
+  // Poisson case: A psi + <ds, psi>/|Gamma| (A alone is singular there)
+  if (rc == KFBI_OK && lambda == 0.0) rc = launch_rank_one(h, psi, out, sgn);
+  return rc;
 }
 
 // g = gN - dv_V^+/dn, v_V the box solve of alpha * src
@@ -150,7 +154,8 @@ int apply_A_acc(kfbi_handle* h, double lambda, const double* psi, double* out, d
   if (rc) return rc;
   if ((rc = launch_correction(h, x, h->w.corr))) return rc;
   if ((rc = refined_solve(h, nullptr, 1.0, h->w.corr, lambda, h->w.u64))) return rc;
-  return launch_limit_user(h, h->w.u64, x, base, sgn, out);
+  if ((rc = launch_limit_user(h, h->w.u64, x, base, sgn, out))) return rc;
+  return lambda == 0.0 ? launch_rank_one(h, psi, out, sgn) : KFBI_OK;
 }
 
 // g = gN - dv_V^+/dn with the refined volume solve (v_V kept in vV64)
@@ -537,7 +542,7 @@ int kfbi_create(const kfbi_geometry* geom, const kfbi_grid* grid, double sigma_i
   if ((rc = dalloc(h, &h->w.hist_g, (size_t)KFBI_HISTORY * M))) return fail(rc);
   if ((rc = dalloc(h, &h->w.psiF, (size_t)M))) return fail(rc);
   if ((rc = dalloc(h, &h->w.rF, (size_t)M))) return fail(rc);
-  if ((rc = dalloc(h, &h->w.proj, (size_t)KFBI_HISTORY * (KFBI_HISTORY + 2) + 4))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.proj, (size_t)KFBI_HISTORY * (KFBI_HISTORY + 2) + 8))) return fail(rc);
   if (cudaMallocHost((void**)&h->w.host_small, 128 * sizeof(double)) != cudaSuccess) {
     set_error("cudaMallocHost failed");
     return fail(KFBI_ERR_OOM);
@@ -750,8 +755,12 @@ int kfbi_solve_neumann(kfbi_handle* h, double lambda, const double* f_dev, const
   return solve_rc;
 }
 
-int bidomain_step(kfbi_handle* h, const kfbi_fhn* p, double* V_dev, double* w_dev, double* ue_dev, int nsteps,
-                  kfbi_stats* per_step) {
+// The Strang steps of bidomain_step; istim (may be NULL) is the extracellular
+// stimulus: it adds beta I / sigma_e to the V problem's source, and the
+// Poisson problem Lap S = -beta I (solved once per call, the stimulus does
+// not change with time) gives the extracellular potential.
+static int bidomain_impl(kfbi_handle* h, const kfbi_fhn* p, const double* istim, double* V_dev, double* w_dev,
+                         double* ue_dev, int nsteps, kfbi_stats* per_step) {
   if (int rc = check_handle(h)) return rc;
   if (!p || !V_dev || !w_dev || nsteps < 0) {
     set_error("null argument");
@@ -762,15 +771,38 @@ int bidomain_step(kfbi_handle* h, const kfbi_fhn* p, double* V_dev, double* w_de
   const double k = 0.5 * h->dt;
   int rc;
   int final_rc = KFBI_OK;
+  if (istim != nullptr) {
+    const int M = h->t.M;
+    if (!h->w.fsrc && (rc = dalloc(h, &h->w.fsrc, (size_t)n))) return rc;
+    if (!h->w.S64 && (rc = dalloc(h, &h->w.S64, (size_t)n))) return rc;
+    if (!h->w.psiS && (rc = dalloc(h, &h->w.psiS, (size_t)M))) return rc;
+    if (!h->w.zeroM && (rc = dalloc(h, &h->w.zeroM, (size_t)M))) return rc;
+    KFBI_CUDA(cudaMemsetAsync(h->w.zeroM, 0, sizeof(double) * (size_t)M, h->stream));
+    KFBI_CUDA(cudaMemsetAsync(h->w.psiS, 0, sizeof(double) * (size_t)M, h->stream));
+    // S problem: Lap S = -beta I, homogeneous Neumann data, lambda = 0
+    if ((rc = launch_stim_source(h, nullptr, 0.0, istim, -p->beta, h->w.fsrc, n))) return rc;
+    kfbi_stats sst{};
+    rc = kfbi_solve_neumann(h, 0.0, h->w.fsrc, h->w.zeroM, h->w.S64, h->w.psiS, &sst);
+    if (rc != KFBI_OK && rc != KFBI_ERR_NOT_CONVERGED) return rc;
+    if (rc == KFBI_ERR_NOT_CONVERGED) final_rc = rc;
+  }
   KFBI_CUDA(cudaMemsetAsync(h->w.err, 0, sizeof(int), h->stream));
   for (int s = 0; s < nsteps; ++s) {
     kfbi_stats st{};
     auto t0 = std::chrono::steady_clock::now();
     if ((rc = launch_react_fe(p, k, V_dev, w_dev, n, h->stream))) return rc;
     const int prec = h->opts.precision == KFBI_FP64 ? KFBI_FP64 : KFBI_MIXED;
-    // g = -dv_V^+/dn with v_V = L_h^{-1}(-lam V)
-    rc = prec == KFBI_FP64 ? rhs_g(h, lam, V_dev, -lam, nullptr, h->w.g)
-                           : rhs_g_acc(h, lam, V_dev, -lam, nullptr, h->w.g);
+    // source of the V problem: -lam V (+ beta I / sigma_e with a stimulus)
+    const double* vsrc = V_dev;
+    double alpha = -lam;
+    if (istim != nullptr) {
+      if ((rc = launch_stim_source(h, V_dev, lam, istim, p->beta / h->sigma_e, h->w.fsrc, n))) return rc;
+      vsrc = h->w.fsrc;
+      alpha = 1.0;
+    }
+    // g = -dv_V^+/dn with v_V = L_h^{-1}(source)
+    rc = prec == KFBI_FP64 ? rhs_g(h, lam, vsrc, alpha, nullptr, h->w.g)
+                           : rhs_g_acc(h, lam, vsrc, alpha, nullptr, h->w.g);
     if (rc) return rc;
     // initial density: the previous one, or the learned prediction when its
     // float32 residual is smaller
@@ -813,8 +845,8 @@ int bidomain_step(kfbi_handle* h, const kfbi_fhn* p, double* V_dev, double* w_de
       if ((rc = density_vector(h, h->w.psi_prev, &x))) return rc;
       if ((rc = launch_correction(h, x, h->w.corr))) return rc;
       SolveArgs sa;
-      sa.src = V_dev;
-      sa.alpha = -lam;
+      sa.src = vsrc;
+      sa.alpha = alpha;
       sa.corr = h->w.corr;
       sa.lambda = lam;
       sa.out_user = V_dev;
@@ -833,7 +865,7 @@ int bidomain_step(kfbi_handle* h, const kfbi_fhn* p, double* V_dev, double* w_de
     if (per_step) per_step[s] = st;
   }
   if (ue_dev) {
-    if ((rc = launch_ue(h, V_dev, ue_dev))) return rc;
+    if ((rc = istim != nullptr ? launch_ue_S(h, V_dev, h->w.S64, ue_dev) : launch_ue(h, V_dev, ue_dev))) return rc;
   }
   int herr = 0;
   KFBI_CUDA(cudaMemcpyAsync(&herr, h->w.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -847,6 +879,16 @@ int bidomain_step(kfbi_handle* h, const kfbi_fhn* p, double* V_dev, double* w_de
     return KFBI_ERR_NEWTON;
   }
   return final_rc;
+}
+
+int bidomain_step(kfbi_handle* h, const kfbi_fhn* p, double* V_dev, double* w_dev, double* ue_dev, int nsteps,
+                  kfbi_stats* per_step) {
+  return bidomain_impl(h, p, nullptr, V_dev, w_dev, ue_dev, nsteps, per_step);
+}
+
+int kfbi_bidomain_step_stim(kfbi_handle* h, const kfbi_fhn* p, const double* istim_dev, double* V_dev,
+                            double* w_dev, double* ue_dev, int nsteps, kfbi_stats* per_step) {
+  return bidomain_impl(h, p, istim_dev, V_dev, w_dev, ue_dev, nsteps, per_step);
 }
 
 int kfbi_set_warmstart(kfbi_handle* h, kfbi_mlp* m) {

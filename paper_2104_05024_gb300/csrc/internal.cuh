@@ -107,6 +107,8 @@ struct Tables {
   int n_inside = 0;
   double* nodes = nullptr;        // [M][dim] interface nodes
   double* n_normal = nullptr;     // [M][3] outward normals at the nodes
+  double* ds = nullptr;           // [M] boundary quadrature weights
+  double area = 0.0;              // their sum |Gamma|
 };
 
 struct Workspace {
@@ -132,6 +134,10 @@ struct Workspace {
   double* u64 = nullptr;          // user-layout float64 grid (refined solutions)
   double* res64 = nullptr;        // user-layout float64 grid (refinement residuals)
   double* vV64 = nullptr;         // user-layout float64 volume solution v_V of the step
+  double* fsrc = nullptr;         // user-layout float64 source of a stimulated step
+  double* S64 = nullptr;          // user-layout float64 S = sigma_i Phi_i + sigma_e Phi_e
+  double* psiS = nullptr;         // [M] density of the S problem
+  double* zeroM = nullptr;        // [M] zeros (homogeneous Neumann data)
   float* res32 = nullptr;         // user-layout float32 grid (refinement residuals)
   double* hist_psi = nullptr;     // [KFBI_HISTORY][M] densities of past solves
   double* hist_g = nullptr;       // [KFBI_HISTORY][M] their right-hand sides
@@ -225,6 +231,13 @@ int launch_residual_ff(kfbi_handle* h, const double* src, double alpha, const do
 int launch_lincomb(kfbi_handle* h, double* y, double a, const double* x, double b, int64_t n);
 // V <- 2 (vV + uB) - V (implicit midpoint from the two parts of u)
 int launch_midpoint(kfbi_handle* h, double* V, const double* vV, const double* uB, int64_t n);
+// out += sgn <ds, psi> / |Gamma| (the rank-one term of the Poisson operator)
+int launch_rank_one(kfbi_handle* h, const double* psi, double* out, double sgn);
+// f = -lambda V + c I (V may be NULL)
+int launch_stim_source(kfbi_handle* h, const double* V, double lambda, const double* I, double c, double* f,
+                       int64_t n);
+// ue = (S - sigma_i V) / (sigma_i + sigma_e) with zero mean over Omega
+int launch_ue_S(kfbi_handle* h, const double* V, const double* S, double* ue);
 int launch_padded_to_user(kfbi_handle* h, const double* padded, double* user);
 
 // GMRES vector kernels (ops.cu)

@@ -220,6 +220,30 @@ __global__ void k_scatter_add(Tables t, const double* __restrict__ corr, double*
   if (i < t.n_irr) g[t.irr[i]] += corr[i];
 }
 
+__global__ void k_add_scalar(double* __restrict__ out, const double* __restrict__ slot, double c, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] += c * slot[0];
+}
+
+__global__ void k_stim_source(const double* __restrict__ V, double lambda, const double* __restrict__ I, double c,
+                              double* __restrict__ f, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    f[i] = (V != nullptr ? -lambda * V[i] : 0.0) + c * I[i];
+}
+
+__global__ void k_phi_e(const double* __restrict__ V, const double* __restrict__ S, double si, double se,
+                        double* __restrict__ ue, int64_t n) {
+  const double inv = 1.0 / (si + se);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    ue[i] = (S[i] - si * V[i]) * inv;
+}
+
+__global__ void k_sub_mean(double* __restrict__ ue, const double* __restrict__ sum, double inv_count, int64_t n) {
+  const double mean = sum[0] * inv_count;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    ue[i] -= mean;
+}
+
 __global__ void k_midpoint(double* __restrict__ V, const double* __restrict__ vV, const double* __restrict__ uB,
                            int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -547,6 +571,36 @@ int launch_residual_ff(kfbi_handle* h, const double* src, double alpha, const do
     k_residual_irr<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->grid, h->t, corr, u64, lambda, src, alpha,
                                                                     res);
   KFBI_CHECK_LAUNCH_N(corr != nullptr && h->t.n_irr > 0 ? 2 : 1);
+  return KFBI_OK;
+}
+
+int launch_rank_one(kfbi_handle* h, const double* psi, double* out, double sgn) {
+  const int M = h->t.M;
+  double* slot = h->w.proj + KFBI_HISTORY * (KFBI_HISTORY + 2) + 4;
+  int rc = vec_dots(h, h->t.ds, 1, M, psi, slot);
+  if (rc) return rc;
+  k_add_scalar<<<(M + 255) / 256, 256, 0, h->stream>>>(out, slot, sgn / h->t.area, M);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+int launch_stim_source(kfbi_handle* h, const double* V, double lambda, const double* I, double c, double* f,
+                       int64_t n) {
+  k_stim_source<<<grid_blocks(n, 256), 256, 0, h->stream>>>(V, lambda, I, c, f, n);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+int launch_ue_S(kfbi_handle* h, const double* V, const double* S, double* ue) {
+  const int n1 = h->grid.N - 1;
+  const int64_t total = h->grid.dim == 3 ? (int64_t)n1 * n1 * n1 : (int64_t)n1 * n1;
+  const int nb = RED_BLOCKS;
+  k_phi_e<<<grid_blocks(total, 256), 256, 0, h->stream>>>(V, S, h->sigma_i, h->sigma_e, ue, total);
+  k_masked_sum<<<nb, 256, 0, h->stream>>>(ue, h->t.inside, total, h->w.partial);
+  k_dots_final<<<1, 256, 0, h->stream>>>(h->w.partial, nb, 1, h->w.partial + nb);
+  k_sub_mean<<<grid_blocks(total, 256), 256, 0, h->stream>>>(ue, h->w.partial + nb, 1.0 / (double)h->t.n_inside,
+                                                            total);
+  KFBI_CHECK_LAUNCH_N(4);
   return KFBI_OK;
 }
 

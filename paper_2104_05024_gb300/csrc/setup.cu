@@ -1051,6 +1051,39 @@ int setup_build(kfbi_handle* h, const kfbi_geometry* geom) {
     KFBI_CHECK_LAUNCH();
   }
 
+  // boundary quadrature weights (the rank-one term of the Poisson operator):
+  // 2-D half the lengths of the two chords at a node, 3-D a third of the
+  // areas of the incident triangles
+  {
+    const int M = t.M;
+    const double* X = geom->nodes;
+    std::vector<double> ds((size_t)M, 0.0);
+    if (d == 2) {
+      std::vector<double> seg((size_t)M);
+      for (int i = 0; i < M; ++i) {
+        const int j = (i + 1) % M;
+        const double dx = X[2 * j] - X[2 * i], dy = X[2 * j + 1] - X[2 * i + 1];
+        seg[i] = std::sqrt(dx * dx + dy * dy);
+      }
+      for (int i = 0; i < M; ++i) ds[i] = 0.5 * (seg[i] + seg[(i + M - 1) % M]);
+    } else {
+      for (int k = 0; k < geom->n_tri; ++k) {
+        const int32_t* v = geom->tri + 3 * (size_t)k;
+        const double* a = X + 3 * (size_t)v[0];
+        const double* b = X + 3 * (size_t)v[1];
+        const double* c = X + 3 * (size_t)v[2];
+        const double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+        const double w[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+        const double cr[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+        const double area = 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+        for (int q = 0; q < 3; ++q) ds[v[q]] += area / 3.0;
+      }
+    }
+    t.area = 0.0;
+    for (int i = 0; i < M; ++i) t.area += ds[i];
+    if ((rc = upload(h, &t.ds, ds.data(), ds.size()))) return rc;
+  }
+
   // transform tables
   {
     std::vector<double> mu(N), tw(4 * (size_t)N);

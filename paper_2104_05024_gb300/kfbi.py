@@ -67,7 +67,7 @@ EXPORTS = [
     "kfbi_transform_pass", "kfbi_launch_count", "kfbi_box_solve_noalloc", "kfbi_mlp_num_params",
     "kfbi_mlp_create", "kfbi_mlp_destroy", "kfbi_mlp_get", "kfbi_mlp_forward", "kfbi_mlp_grad",
     "kfbi_mlp_train_step", "kfbi_set_warmstart", "kfbi_get_densities", "kfbi_set_densities",
-    "kfbi_get_history", "kfbi_set_history", "kfbi_get_projection",
+    "kfbi_get_history", "kfbi_set_history", "kfbi_get_projection", "kfbi_bidomain_step_stim",
 ]
 
 
@@ -175,6 +175,7 @@ def load(path: str = LIB_PATH):
     lib.kfbi_get_history.argtypes = [vp, vp, vp, C.POINTER(C.c_int)]
     lib.kfbi_set_history.argtypes = [vp, vp, vp, ip]
     lib.kfbi_get_projection.argtypes = [vp, vp, vp]
+    lib.kfbi_bidomain_step_stim.argtypes = [vp, C.POINTER(FHNStruct), vp, vp, vp, vp, ip, C.POINTER(Stats)]
     for name in EXPORTS:
         if name not in ("kfbi_last_error", "kfbi_destroy", "kfbi_launch_count", "kfbi_mlp_destroy"):
             getattr(lib, name).restype = C.c_int
@@ -391,11 +392,16 @@ class KFBI:
                allow=(ERR_NOT_CONVERGED,))
         return st.as_dict()
 
-    def bidomain_step(self, fhn, V, w, ue=None, nsteps=1, **opts):
+    def bidomain_step(self, fhn, V, w, ue=None, nsteps=1, istim=None, **opts):
+        """Strang steps; istim (device field) adds the virtual-electrode stimulus."""
         self.set_opts(**opts)
         stats = (Stats * max(1, nsteps))()
-        _check(load().bidomain_step(self._h, C.byref(fhn_struct(fhn)), _ptr(V), _ptr(w), _ptr(ue), nsteps, stats),
-               allow=(ERR_NOT_CONVERGED,))
+        if istim is None:
+            _check(load().bidomain_step(self._h, C.byref(fhn_struct(fhn)), _ptr(V), _ptr(w), _ptr(ue), nsteps, stats),
+                   allow=(ERR_NOT_CONVERGED,))
+        else:
+            _check(load().kfbi_bidomain_step_stim(self._h, C.byref(fhn_struct(fhn)), _ptr(istim), _ptr(V), _ptr(w),
+                                                  _ptr(ue), nsteps, stats), allow=(ERR_NOT_CONVERGED,))
         return [stats[i].as_dict() for i in range(nsteps)]
 
 
