@@ -201,20 +201,22 @@ def run_gpu(args):
     z_flops = 2 * lines * fl_dst + 3.0 * (N - 1) ** 3
     z_s = pass_ms[2] / 1e3
     esize = 8 if prec_pass == K.FP64 else 4
-    z_bytes = 2.0 * N ** 3 * esize           # read + write of the padded grid
+    # the dominant kernel of the step's launch list: float64, the z solve pass
+    # (FP64-pipe bound); float32, the y pass (two launches per box solve)
     if prec_pass == K.FP64:
-        roof = {"kernel": "k_strided<double,256,SOLVE> (z pass: DST, divide, DST)", "bound": "alu",
+        roof = {"kernel": f"k_strided<double,{N},SOLVE> (z pass: DST, divide, DST)", "bound": "alu",
                 "achieved": z_flops / z_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz"}
+                "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz", "traffic": None}
     else:
-        roof = {"kernel": f"k_strided_tma<{N},SOLVE> (z pass: DST, divide, DST)", "bound": "hbm",
-                "achieved": z_bytes / z_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "peak_source": kind}
+        y_bytes = 2.0 * N ** 3 * esize           # read + write of the padded grid
+        roof = {"kernel": f"k_strided_tma<{N},0> (y pass: one DST per line)", "bound": "hbm",
+                "achieved": y_bytes / (pass_ms[1] / 1e3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "peak_source": kind,
+                # DRAM read + write per launch of this kernel at 256^3 from one
+                # ncu capture (cold cache); none for other sizes
+                "traffic": 72.7e6 if N == 256 else None,
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, cold cache)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    # DRAM read + write per launch of the float32 z pass at 256^3, from one ncu
-    # capture of that kernel (cold cache); none for other cases
-    roof["traffic"] = 73.5e6 if (prec_pass != K.FP64 and N == 256) else None
-    roof["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, cold cache)"
     roof["pass_ms"] = {k: round(v, 4) for k, v in pass_ms.items()}
     roof["hbm_gbs_per_pass"] = {k: round(2.0 * N ** 3 * esize / (v / 1e3) / 1e9, 1) for k, v in pass_ms.items()}
 

@@ -316,6 +316,14 @@ int kfbi_get_projection(kfbi_handle* h, double* psiF_dev, double* rF_dev);
  * grid content is arbitrary afterwards.                                      */
 int kfbi_transform_pass(kfbi_handle* h, int precision, int pass, double lambda);
 
+/* Self-test of the bounded waits of the TMA-fed transform kernels (no
+ * counterpart in the paper): one block polls an mbarrier that nothing ever
+ * completes, with the same wait as those kernels, capped at `polls` polls
+ * (1 .. 2^20).  *timed_out = 1 when the cap ended the wait and raised the
+ * timeout flag (the expected outcome); *ms (optional) is the kernel time.
+ * Allocates a 4-byte flag.                                                   */
+int kfbi_selftest_bounded_wait(int polls, int* timed_out, double* ms);
+
 /* Number of kernels this library has launched in the process so far
  * (instrumentation; every launch site adds its kernel count).                */
 int64_t kfbi_launch_count(void);

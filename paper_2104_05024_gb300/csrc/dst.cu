@@ -513,7 +513,9 @@ __global__ void __launch_bounds__(NT) k_strided(T* __restrict__ a, size_t row_st
 // current tile; the finished tile goes back by a TMA tensor store.  Every
 // wait is bounded: on timeout the block records DEVERR_TIMEOUT and returns.
 constexpr int TMA_W = 32;
-constexpr long TMA_WAIT_CAP = 1L << 22;
+// a poll of an incomplete mbarrier takes about 4 us here, so 2^18 polls give up
+// after about a second (a tile load completes in microseconds)
+constexpr long TMA_WAIT_CAP = 1L << 18;
 // resident blocks per SM: the solve pass (one DST body run twice) fits
 // three without spills, the plain pass spills at three
 template <bool SOLVE>
@@ -627,7 +629,15 @@ __global__ void __launch_bounds__(NT, tma_blocks<SOLVE>()) k_strided_tma(const _
         break;
       }
     if (!ok) {
-      if (threadIdx.x == 0) atomicOr(err, DEVERR_TIMEOUT);
+      if (threadIdx.x == 0) {
+        atomicOr(err, DEVERR_TIMEOUT);
+        // the copies this block issued finish before its shared memory goes:
+        // stores by their bulk group, the pending load by its barrier
+        tma_wait_all();
+        if (tn < ntiles)
+          for (long it = 0; it < TMA_WAIT_CAP; ++it)
+            if (mbar_try_wait(&bar[b ^ 1], (uint32_t)(((i + 1) >> 1) & 1))) break;
+      }
       return;
     }
     {
@@ -874,4 +884,57 @@ int box_solve32(kfbi_handle* h, const SolveArgs& a, float* work) {
   return dispatch<float>(h, a, work, h->t.mu32, h->t.tw32);
 }
 
+namespace {
+// an mbarrier that nothing ever completes, polled with the transform
+// kernels' bounded wait: the poll cap must end the wait and raise the flag
+__global__ void k_selftest_wait(long cap, int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  bool ok = false;
+  for (long it = 0; it < cap; ++it)
+    if (mbar_try_wait(&bar, 0u)) {
+      ok = true;
+      break;
+    }
+  if (!ok && threadIdx.x == 0) atomicOr(err, DEVERR_TIMEOUT);
+}
+}  // namespace
+
 }  // namespace kfbi
+
+extern "C" int kfbi_selftest_bounded_wait(int polls, int* timed_out, double* ms) {
+  using namespace kfbi;
+  if (polls < 1 || polls > (1 << 20) || !timed_out) {
+    set_error("polls must be in 1 .. 2^20");
+    return KFBI_ERR_ARG;
+  }
+  int* err = nullptr;
+  KFBI_CUDA(cudaMalloc(&err, sizeof(int)));
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaMemset(err, 0, sizeof(int));
+  cudaEventRecord(a);
+  k_selftest_wait<<<1, 32>>>((long)polls, err);
+  cudaEventRecord(b);
+  const cudaError_t e = cudaEventSynchronize(b);
+  int herr = 0;
+  if (e == cudaSuccess) cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
+  float t = 0.0f;
+  cudaEventElapsedTime(&t, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(err);
+  if (e != cudaSuccess) {
+    set_error("self-test launch failed: %s", cudaGetErrorString(e));
+    return KFBI_ERR_CUDA;
+  }
+  *timed_out = (herr & DEVERR_TIMEOUT) ? 1 : 0;
+  if (ms) *ms = t;
+  KFBI_COUNT(1);
+  return KFBI_OK;
+}

@@ -68,6 +68,7 @@ EXPORTS = [
     "kfbi_mlp_create", "kfbi_mlp_destroy", "kfbi_mlp_get", "kfbi_mlp_forward", "kfbi_mlp_grad",
     "kfbi_mlp_train_step", "kfbi_set_warmstart", "kfbi_get_densities", "kfbi_set_densities",
     "kfbi_get_history", "kfbi_set_history", "kfbi_get_projection", "kfbi_bidomain_step_stim",
+    "kfbi_selftest_bounded_wait",
 ]
 
 
@@ -124,6 +125,13 @@ def box_solve_noalloc(r, v, lam, dim, N, lo=-1.0, hi=1.0):
     _check(load().kfbi_box_solve_noalloc(dim, N, lo, hi, lam, _ptr(r), _ptr(v), _stream()))
 
 
+def selftest_bounded_wait(polls):
+    """(timed_out, ms) of a capped wait on an mbarrier that never completes."""
+    t, ms = C.c_int(), C.c_double()
+    _check(load().kfbi_selftest_bounded_wait(int(polls), C.byref(t), C.byref(ms)))
+    return bool(t.value), ms.value
+
+
 def launch_count() -> int:
     return int(load().kfbi_launch_count())
 
@@ -176,6 +184,7 @@ def load(path: str = LIB_PATH):
     lib.kfbi_set_history.argtypes = [vp, vp, vp, ip]
     lib.kfbi_get_projection.argtypes = [vp, vp, vp]
     lib.kfbi_bidomain_step_stim.argtypes = [vp, C.POINTER(FHNStruct), vp, vp, vp, vp, ip, C.POINTER(Stats)]
+    lib.kfbi_selftest_bounded_wait.argtypes = [ip, C.POINTER(C.c_int), C.POINTER(C.c_double)]
     for name in EXPORTS:
         if name not in ("kfbi_last_error", "kfbi_destroy", "kfbi_launch_count", "kfbi_mlp_destroy"):
             getattr(lib, name).restype = C.c_int
