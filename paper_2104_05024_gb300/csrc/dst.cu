@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(NT) k_strided(T* __restrict__ a, size_t row_st
 // current tile; the finished tile goes back by a TMA tensor store.  Every
 // wait is bounded: on timeout the block records DEVERR_TIMEOUT and returns.
 constexpr int TMA_W = 32;
-// a poll of an incomplete mbarrier takes about 4 us here, so 2^18 polls give up
+// a poll of an incomplete mbarrier takes about 4 us on GB300, so 2^18 polls give up
 // after about a second (a tile load completes in microseconds)
 constexpr long TMA_WAIT_CAP = 1L << 18;
 // resident blocks per SM: the solve pass (one DST body run twice) fits
