@@ -8,7 +8,7 @@ against the oracle:
 * Strang steps with the paper's stiff FitzHugh-Nagumo parameters, dt = h and
   the stimulus on the config-0 ellipse and a 3-D sphere: V, w and the
   extracellular potential from the S problem within 1e-10 (float64) / 1e-8
-  (refined float32).
+  (refined float32); and at the stimulus benchmark's size (sphere, 256^3).
 """
 import numpy as np
 import pytest
@@ -91,6 +91,37 @@ def test_virtual_electrode_strang(name):
         print(f"{name} precision {prec}: V {rel(Vd.cpu().numpy(), V):.2e} w {rel(wd.cpu().numpy(), w):.2e} "
               f"ue {rel(ue.cpu().numpy(), ue_ref):.2e}, iterations {[s['iters'] for s in st]}")
         assert all(s["rel_res"] <= tol for s in st)
+        assert rel(Vd.cpu().numpy(), V) < bar
+        assert rel(wd.cpu().numpy(), w) < bar
+        assert rel(ue.cpu().numpy(), ue_ref) < bar
+
+
+def test_virtual_electrode_sphere256():
+    """The stimulus workload at its benchmark size (sphere r = 0.6, 256^3,
+    n = 64): one float64 step (GMRES to 1e-12) within 1e-10 of the oracle, and
+    two steps of the float32 form with the history projection at the
+    benchmark's 1e-8 tolerance within 1e-7."""
+    geom, grid = G.sphere3(0.6, C.surface_res(256)), C.Grid(3, 256)
+    fhn = C.FHN_PAPER
+    I = C.virtual_electrode(grid)
+    for prec, warm, tol_gpu, tol_ref, steps, bar in ((K.FP64, K.WARM_PREVIOUS, 1e-12, 1e-12, 1, 1e-10),
+                                                     (K.MIXED, K.WARM_PROJECTION, 1e-8, 1e-10, 2, 1e-7)):
+        cfg = C.StrangConfig(sigma_i=1.0, sigma_e=2.0, dt=grid.h, steps=steps, tol=tol_ref)
+        bd = Bidomain(geom, grid, cfg, fhn, C.helmholtz_lambda(cfg, fhn), istim=I)
+        V, w = np.zeros(grid.shape), np.zeros(grid.shape)
+        for _ in range(steps):
+            V, w, info = bd.step(V, w)
+            assert info["converged"] and info["newton_ok"]
+        ue_ref = extracellular_S(V, bd.solve_S(), bd.k.inside, cfg.sigma_i, cfg.sigma_e)
+        h = K.KFBI(geom, grid, sigma_i=1.0, sigma_e=2.0, dt=grid.h, tol=tol_gpu, precision=prec, warm=warm)
+        Vd = torch.zeros(grid.shape, dtype=torch.float64, device=DEV)
+        wd = torch.zeros_like(Vd)
+        ue = torch.empty_like(Vd)
+        st = h.bidomain_step(fhn, Vd, wd, ue, nsteps=steps, istim=cuda(I))
+        h.close()
+        print(f"sphere 256^3 precision {prec}: V {rel(Vd.cpu().numpy(), V):.2e} w {rel(wd.cpu().numpy(), w):.2e} "
+              f"ue {rel(ue.cpu().numpy(), ue_ref):.2e}")
+        assert all(s["rel_res"] <= tol_gpu for s in st)
         assert rel(Vd.cpu().numpy(), V) < bar
         assert rel(wd.cpu().numpy(), w) < bar
         assert rel(ue.cpu().numpy(), ue_ref) < bar
