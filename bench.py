@@ -168,14 +168,24 @@ def run_gpu(args):
     with ClockSampler(local) as clk:
         barrier()
         torch.cuda.nvtx.range_push("timed")     # lets a profiler select the timed launches
+        # the K steps in up to five equal segments (events between them, no
+        # synchronisation inside the timed region) for a median per step
+        nseg = 5 if args.steps % 5 == 0 else 1
+        seg_ev = [torch.cuda.Event(enable_timing=True) for _ in range(nseg - 1)]
+        stats = []
         e0.record(stream)
-        stats = h.bidomain_step(fhn, V, w, None, nsteps=args.steps)
+        for sgi in range(nseg):
+            stats += h.bidomain_step(fhn, V, w, None, nsteps=args.steps // nseg)
+            if sgi < nseg - 1:
+                seg_ev[sgi].record(stream)
         e1.record(stream)
         torch.cuda.nvtx.range_pop()
         barrier()
     launches = K.launch_count() - l0
     V_main, w_main = V.clone(), w.clone()
     ms = e0.elapsed_time(e1)
+    marks = [e0] + seg_ev + [e1]
+    seg_ms = [marks[i].elapsed_time(marks[i + 1]) / (args.steps // nseg) for i in range(nseg)]
     ms_step, value = replica_time(ms / args.steps, world, dist, dev)
     iters = [s["iters"] for s in stats]
 
@@ -282,6 +292,8 @@ def run_gpu(args):
                    "l2": "inputs larger than L2 (V and w: %.0f MB each)" % (V.numel() * 8 / 1e6),
                    "setup_s": round(setup_s, 2), "n_irregular": h.info["n_irregular"],
                    "n_crossings": h.info["n_crossings"]},
+        "ms_per_step_segments": [round(x, 4) for x in seg_ms],
+        "ms_per_step_median": float(np.median(seg_ms)),
         "gmres_iters_per_step": float(np.mean(iters)),
         "outer_per_step": float(np.mean([s["outer"] for s in stats])),
         "forms": forms,

@@ -384,12 +384,15 @@ __global__ void __launch_bounds__(NT) k_xfwd(T* __restrict__ a, const double* __
     for (int idx = threadIdx.x; idx < N * W; idx += NT) s[(idx % N) * RS + idx / N] = (T)0;
   }
   __syncthreads();
-  if (corr != nullptr && threadIdx.x < W) {
-    const int c = threadIdx.x, y = y0 + c;
+  if (corr != nullptr) {
+    // the line's irregular nodes (distinct x, so distinct words) shared out
+    // over the NT / W threads of each column
+    constexpr int G = NT / W;
+    const int c = threadIdx.x % W, g = threadIdx.x / W, y = y0 + c;
     if (y > 0) {
       const int line = DIM == 3 ? (z - 1) * n1 + (y - 1) : (y - 1);
       const int i0 = line_start[line], i1 = line_start[line + 1];
-      for (int i = i0; i < i1; ++i) {
+      for (int i = i0 + g; i < i1; i += G) {
         const int x = irr[i] % n1 + 1;
         s[x * RS + c] += (T)corr[i];
       }
