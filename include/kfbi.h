@@ -200,7 +200,8 @@ int bidomain_step(kfbi_handle* h, const kfbi_fhn* p, double* V_dev, double* w_de
  * both with homogeneous Neumann data.  The S problem (lambda = 0, with the
  * rank-one modification described at kfbi_solve_neumann) is solved once per
  * call; ue_dev (optional) receives Phi_e = (S - sigma_i V)/(sigma_i +
- * sigma_e) with zero mean over Omega.  NULL istim_dev is bidomain_step.      */
+ * sigma_e) with zero mean over Omega.  NULL istim_dev is bidomain_step.  The
+ * first stimulated call on a handle allocates two grid-sized work arrays.    */
 int kfbi_bidomain_step_stim(kfbi_handle* h, const kfbi_fhn* p, const double* istim_dev, double* V_dev,
                             double* w_dev, double* ue_dev, int nsteps, kfbi_stats* per_step);
 
@@ -293,8 +294,10 @@ int kfbi_set_warmstart(kfbi_handle* h, kfbi_mlp* m);
 int kfbi_get_densities(kfbi_handle* h, double* psi_dev, double* psi_prev_dev, double* g_dev);
 /* Restore the density history saved by kfbi_get_densities (checkpoint /
  * resume): n_solves is the number of diffusion solves the history stands for
- * (0 clears it).  With the same state (V, w) a resumed float64 run repeats
- * the uninterrupted one bit for bit.                                         */
+ * (0 clears it).  With the same state (V, w) a resumed run with the
+ * previous-density start repeats the uninterrupted one bit for bit.  It
+ * empties the projection history; runs with KFBI_WARM_PROJECTION (or the
+ * learned form) resume through kfbi_get_history / kfbi_set_history instead.  */
 int kfbi_set_densities(kfbi_handle* h, const double* psi_dev, const double* psi_prev_dev, const double* g_dev,
                        int n_solves);
 /* The density history of the projection warm start: KFBI_HISTORY slots of

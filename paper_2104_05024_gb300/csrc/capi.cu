@@ -170,8 +170,10 @@ int rhs_g_acc(kfbi_handle* h, double lambda, const double* src, double alpha, co
 // fallback (optional): an alternative initial guess with known residual norm
 // fallback_res (relative to nothing: ||g - A fallback||); it replaces psi
 // when psi's first residual is larger.
+// gnorm_known (>= 0): ||g|| already read by the caller (saves a synchronisation).
 int gmres(kfbi_handle* h, int prec, double lambda, const double* g, double* psi, kfbi_stats* st, double tol,
-          int max_iter, bool zero_guess = false, const double* fallback = nullptr, double fallback_res = 0.0) {
+          int max_iter, bool zero_guess = false, const double* fallback = nullptr, double fallback_res = 0.0,
+          double gnorm_known = -1.0) {
   const int M = h->t.M;
   const int m = h->opts.restart;
   double* V = h->w.vecs;
@@ -180,8 +182,9 @@ int gmres(kfbi_handle* h, int prec, double lambda, const double* g, double* psi,
   double* r = h->w.r;
   double* s = h->w.small;
   int rc;
-  double gnorm;
-  if ((rc = norm2(h, g, s + small_nrm2(m), &gnorm))) return rc;
+  double gnorm = gnorm_known;
+  if (gnorm < 0.0 && (rc = norm2(h, g, s + small_nrm2(m), &gnorm))) return rc;
+  const double gnorm_raw = gnorm;
   if (gnorm == 0.0) gnorm = 1.0;
   int it = 0;
   double rel = 0.0;
@@ -193,9 +196,14 @@ int gmres(kfbi_handle* h, int prec, double lambda, const double* g, double* psi,
       return rc;
     }
     if ((rc = vec_dots(h, r, 1, M, r, s + small_nrm2(m)))) return rc;
-    double b2;
-    if ((rc = read_scalar(h, s + small_nrm2(m), &b2))) return rc;
-    const double beta = std::sqrt(b2);
+    double beta;
+    if (first && zero_guess) {
+      beta = gnorm_raw;  // r = g: the same reduction as ||g||, no second read
+    } else {
+      double b2;
+      if ((rc = read_scalar(h, s + small_nrm2(m), &b2))) return rc;
+      beta = std::sqrt(b2);
+    }
     if (first && fallback != nullptr && beta > fallback_res) {
       // the residual judges the guess: go back to the alternative
       if ((rc = vec_copy(h, psi, fallback, M))) return rc;
@@ -326,7 +334,7 @@ int gmres_ir(kfbi_handle* h, double lambda, const double* g, double* psi, kfbi_s
     if (tin > 0.5) tin = 0.5;
     KFBI_CUDA(cudaMemsetAsync(delta, 0, sizeof(double) * (size_t)M, h->stream));
     kfbi_stats in{};
-    rc = gmres(h, KFBI_MIXED, lambda, r, delta, &in, tin, h->opts.max_iter - inner_total, true);
+    rc = gmres(h, KFBI_MIXED, lambda, r, delta, &in, tin, h->opts.max_iter - inner_total, true, nullptr, 0.0, rn);
     if (rc != KFBI_OK && rc != KFBI_ERR_NOT_CONVERGED) return rc;
     inner_total += in.iters;
     if ((rc = vec_axpby(h, psi, 1.0, delta, 1.0, M))) return rc;
