@@ -519,11 +519,13 @@ constexpr int TMA_W = 32;
 // a poll of an incomplete mbarrier takes about 4 us on GB300, so 2^18 polls give up
 // after about a second (a tile load completes in microseconds)
 constexpr long TMA_WAIT_CAP = 1L << 18;
-// resident blocks per SM: the solve pass (one DST body run twice) fits
-// three without spills, the plain pass spills at three
+// resident blocks per SM: three (shared memory allows three at N = 256); at
+// 80 registers neither pass spills as long as the plain pass runs its single
+// transform inside the runtime-bounded loop (the compile-time bound of one
+// lets the compiler schedule it into spills)
 template <bool SOLVE>
 constexpr int tma_blocks() {
-  return SOLVE ? 3 : 2;
+  return 3;
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -576,7 +578,8 @@ constexpr size_t tma_smem_bytes() {
 template <int N, bool SOLVE>
 __global__ void __launch_bounds__(NT, tma_blocks<SOLVE>()) k_strided_tma(const __grid_constant__ CUtensorMap map, int mode,
                                                     const float* __restrict__ mu1, float lambda, float scale,
-                                                    const float* __restrict__ tw_g, int* __restrict__ err) {
+                                                    const float* __restrict__ tw_g, int* __restrict__ err,
+                                                    int reps) {
   using C = TmaTile<N>;
   constexpr int W = TMA_W, NX = N / TMA_W;
   constexpr int ntiles = NX * (N - 1);
@@ -649,7 +652,7 @@ __global__ void __launch_bounds__(NT, tma_blocks<SOLVE>()) k_strided_tma(const _
       const int q = t / NX + 1, p = (t % NX) * W + (int)(threadIdx.x & 31);
       DivPost post{mus, mus[p] + mus[q] - lambda, scale, p == 0, SOLVE};
 #pragma unroll 1
-      for (int rep = 0; rep < (SOLVE ? 2 : 1); ++rep) {
+      for (int rep = 0; rep < (SOLVE ? 2 : reps); ++rep) {
         regdst::dst1_tile_reg<regdst::Geo<N, W>>(s, sinv, reinterpret_cast<const regdst::cf2*>(tw), tot, post);
         post.on = false;
       }
@@ -702,10 +705,10 @@ int launch_strided3(kfbi_handle* h, int mode, bool solve, T* work, const T* mu1,
       const int grid = tiles < nb ? tiles : nb;
       if (solve) {
         if ((rc = prep(k_strided_tma<N, true>, smem))) return rc;
-        k_strided_tma<N, true><<<grid, NT, smem, st>>>(map, mode, mu1, lam, scale, tw, h->w.err);
+        k_strided_tma<N, true><<<grid, NT, smem, st>>>(map, mode, mu1, lam, scale, tw, h->w.err, 2);
       } else {
         if ((rc = prep(k_strided_tma<N, false>, smem))) return rc;
-        k_strided_tma<N, false><<<grid, NT, smem, st>>>(map, mode, mu1, lam, scale, tw, h->w.err);
+        k_strided_tma<N, false><<<grid, NT, smem, st>>>(map, mode, mu1, lam, scale, tw, h->w.err, 1);
       }
       return KFBI_OK;
     }
