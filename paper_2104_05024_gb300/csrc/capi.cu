@@ -165,6 +165,30 @@ int rhs_g_acc(kfbi_handle* h, double lambda, const double* src, double alpha, co
   return launch_limit_user(h, h->w.vV64, nullptr, gN, -1.0, g);
 }
 
+// Launches of one Arnoldi iteration (w = A v_j and the CGS2 step), all
+// carrying the stop flag as their skip flag; the residual estimate and the
+// device's stop decision go to the pinned host slots of iteration j.
+struct SkipScope {
+  kfbi_handle* h;
+  SkipScope(kfbi_handle* hh, const int* flag) : h(hh) { h->skip = flag; }
+  ~SkipScope() { h->skip = nullptr; }
+};
+
+int arnoldi_iteration(kfbi_handle* h, int prec, double lambda, int j, double gnorm, double tol) {
+  const int M = h->t.M, m = h->opts.restart;
+  double* V = h->w.vecs;
+  int rc;
+  {
+    SkipScope scope(h, h->w.stop);
+    if ((rc = apply_A(h, prec, lambda, V + (size_t)j * M, h->w.tmp, 1.0, nullptr))) return rc;
+    if ((rc = arnoldi_step(h, V, M, h->w.tmp, j, m, gnorm, tol))) return rc;
+  }
+  KFBI_CUDA(cudaMemcpyAsync(h->w.host_small + 128 + 2 * j, h->w.small + small_res(m), 2 * sizeof(double),
+                            cudaMemcpyDeviceToHost, h->stream));
+  KFBI_CUDA(cudaEventRecord(h->arn_ev[j & 1], h->stream));
+  return KFBI_OK;
+}
+
 // GMRES(m) with CGS2 Arnoldi on A psi = g; psi in: initial guess, out: solution.
 // zero_guess: psi is known to be zero, so the first residual is g itself.
 // fallback (optional): an alternative initial guess with known residual norm
@@ -178,7 +202,6 @@ int gmres(kfbi_handle* h, int prec, double lambda, const double* g, double* psi,
   const int m = h->opts.restart;
   double* V = h->w.vecs;
   const int ld = M;
-  double* wv = h->w.tmp;
   double* r = h->w.r;
   double* s = h->w.small;
   int rc;
@@ -225,29 +248,26 @@ int gmres(kfbi_handle* h, int prec, double lambda, const double* g, double* psi,
     if (rel <= tol || it >= max_iter || beta == 0.0) break;
     if ((rc = launch_init_arnoldi(h, s, m))) return rc;
     if ((rc = vec_scale_by_norm(h, V, r, s + small_nrm2(m), M))) return rc;
+    KFBI_CUDA(cudaMemsetAsync(h->w.stop, 0, sizeof(int), h->stream));
+    // Iteration j + 1 is enqueued before the residual estimate of iteration
+    // j reaches the host, so the device never waits for the host between
+    // iterations; its launches do nothing when iteration j set the stop flag.
+    if ((rc = arnoldi_iteration(h, prec, lambda, 0, gnorm, tol))) return rc;
     int jd = 0;
     for (int j = 0; j < m; ++j) {
-      double* vj = V + (size_t)j * ld;
-      if ((rc = apply_A(h, prec, lambda, vj, wv, 1.0, nullptr))) return rc;
+      const bool ahead = j + 1 < m && it + 2 <= max_iter;
+      if (ahead && (rc = arnoldi_iteration(h, prec, lambda, j + 1, gnorm, tol))) return rc;
+      KFBI_CUDA(cudaEventSynchronize(h->arn_ev[j & 1]));
+      const double res = h->w.host_small[128 + 2 * j];
+      const bool stop = h->w.host_small[128 + 2 * j + 1] != 0.0;
       ++it;
-      // classical Gram-Schmidt, twice
-      if ((rc = vec_dots(h, V, j + 1, ld, wv, s + small_hcol(m)))) return rc;
-      if ((rc = vec_update(h, wv, V, j + 1, ld, s + small_hcol(m), -1.0))) return rc;
-      if ((rc = vec_dots(h, V, j + 1, ld, wv, s + small_y(m)))) return rc;
-      if ((rc = vec_update(h, wv, V, j + 1, ld, s + small_y(m), -1.0))) return rc;
-      if ((rc = arnoldi_add(h, s, m, j + 1))) return rc;
-      if ((rc = vec_dots(h, wv, 1, M, wv, s + small_nrm2(m)))) return rc;
-      if ((rc = vec_scale_by_norm(h, V + (size_t)(j + 1) * ld, wv, s + small_nrm2(m), M))) return rc;
-      if ((rc = arnoldi_givens(h, s, j, m))) return rc;
-      double res;
-      if ((rc = read_scalar(h, s + small_res(m), &res))) return rc;
       rel = res / gnorm;
       jd = j + 1;
       if (!std::isfinite(rel)) {
         set_error("non-finite residual in GMRES");
         return KFBI_ERR_NAN;
       }
-      if (rel <= tol || it >= max_iter) break;
+      if (stop || rel <= tol || it >= max_iter || !ahead) break;
     }
     if ((rc = arnoldi_solve(h, s, jd, m))) return rc;
     if ((rc = vec_update(h, psi, V, jd, ld, s + small_y(m), 1.0))) return rc;
@@ -513,6 +533,18 @@ int kfbi_create(const kfbi_geometry* geom, const kfbi_grid* grid, double sigma_i
     return code;
   };
   if ((rc = dalloc(h, &h->w.err, 4))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.stop, 4))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.counter, 4))) return fail(rc);
+  if (cudaMemsetAsync(h->w.stop, 0, 4 * sizeof(int), h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->w.counter, 0, 4 * sizeof(unsigned), h->stream) != cudaSuccess) {
+    set_error("cudaMemset failed");
+    return fail(KFBI_ERR_CUDA);
+  }
+  for (cudaEvent_t& e : h->arn_ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      set_error("cudaEventCreate failed");
+      return fail(KFBI_ERR_CUDA);
+    }
   if ((rc = setup_build(h, geom))) return fail(rc);
   const int M = h->t.M, m = opts->restart;
   const int64_t P = padded_points(h);
@@ -551,7 +583,9 @@ int kfbi_create(const kfbi_geometry* geom, const kfbi_grid* grid, double sigma_i
   if ((rc = dalloc(h, &h->w.psiF, (size_t)M))) return fail(rc);
   if ((rc = dalloc(h, &h->w.rF, (size_t)M))) return fail(rc);
   if ((rc = dalloc(h, &h->w.proj, (size_t)KFBI_HISTORY * (KFBI_HISTORY + 2) + 8))) return fail(rc);
-  if (cudaMallocHost((void**)&h->w.host_small, 128 * sizeof(double)) != cudaSuccess) {
+  // [0, 128): scalars and the projection system; [128, 256): per-iteration
+  // residual estimates and stop flags of GMRES
+  if (cudaMallocHost((void**)&h->w.host_small, 256 * sizeof(double)) != cudaSuccess) {
     set_error("cudaMallocHost failed");
     return fail(KFBI_ERR_OOM);
   }
@@ -569,6 +603,8 @@ void kfbi_destroy(kfbi_handle* h) {
   else cudaDeviceSynchronize();
   for (void* p : h->allocations) cudaFree(p);
   if (h->w.host_small) cudaFreeHost(h->w.host_small);
+  for (cudaEvent_t e : h->arn_ev)
+    if (e) cudaEventDestroy(e);
   delete h;
 }
 

@@ -345,7 +345,8 @@ template <typename T, int N, int DIM>
 __global__ void __launch_bounds__(NT) k_xfwd(T* __restrict__ a, const double* __restrict__ src, double alpha,
                                              const float* __restrict__ src32,
                                              const double* __restrict__ corr, const int32_t* __restrict__ irr,
-                                             const int32_t* __restrict__ line_start, const T* __restrict__ tw_g) {
+                                             const int32_t* __restrict__ line_start, const T* __restrict__ tw_g,
+                                             const int* __restrict__ skip) {
   using C = Cfg<T, N>;
   constexpr int W = C::W, RS = C::RS, n1 = N - 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -353,8 +354,10 @@ __global__ void __launch_bounds__(NT) k_xfwd(T* __restrict__ a, const double* __
   T* tot = s + N * RS;
   T* tw = tot + C::G * W;
   T* sinv = tw + 4 * N;
+  const bool skipped = skip != nullptr && *skip != 0;  // read early, tested after the table loads
   load_twiddles<T, N>(tw, tw_g);
   load_sines<T, N>(sinv, tw_g);
+  if (skipped) return;
   const int y0 = blockIdx.x * W;
   const int z = DIM == 3 ? blockIdx.y + 1 : 0;
   // the branch on src stays outside the loops: inside, the compiler
@@ -411,7 +414,7 @@ __global__ void __launch_bounds__(NT) k_xfwd(T* __restrict__ a, const double* __
 template <typename T, int N, int DIM>
 __global__ void __launch_bounds__(NT) k_xinv(T* __restrict__ a, bool keep, double* __restrict__ out,
                                              const double* __restrict__ aux, double beta, double gamma,
-                                             const T* __restrict__ tw_g) {
+                                             const T* __restrict__ tw_g, const int* __restrict__ skip) {
   using C = Cfg<T, N>;
   constexpr int W = C::W, RS = C::RS, n1 = N - 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -419,6 +422,7 @@ __global__ void __launch_bounds__(NT) k_xinv(T* __restrict__ a, bool keep, doubl
   T* tot = s + N * RS;
   T* tw = tot + C::G * W;
   T* sinv = tw + 4 * N;
+  if (skip != nullptr && *skip != 0) return;
   load_twiddles<T, N>(tw, tw_g);
   load_sines<T, N>(sinv, tw_g);
   const int y0 = blockIdx.x * W;
@@ -462,7 +466,7 @@ __global__ void __launch_bounds__(NT) k_xinv(T* __restrict__ a, bool keep, doubl
 template <typename T, int N, bool SOLVE, int DIM>
 __global__ void __launch_bounds__(NT) k_strided(T* __restrict__ a, size_t row_stride, size_t plane_stride, int qoff,
                                                 const T* __restrict__ mu1, T lambda, T scale,
-                                                const T* __restrict__ tw_g) {
+                                                const T* __restrict__ tw_g, const int* __restrict__ skip) {
   using C = Cfg<T, N>;
   constexpr int W = C::W, RS = C::RS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -470,8 +474,10 @@ __global__ void __launch_bounds__(NT) k_strided(T* __restrict__ a, size_t row_st
   T* tot = s + N * RS;
   T* tw = tot + C::G * W;
   T* sinv = tw + 4 * N;
+  const bool skipped = skip != nullptr && *skip != 0;
   load_twiddles<T, N>(tw, tw_g);
   load_sines<T, N>(sinv, tw_g);
+  if (skipped) return;
   const int x0 = blockIdx.x * W;
   const int q = blockIdx.y + qoff;
   T* base = a + (size_t)q * plane_stride + x0;
@@ -579,7 +585,7 @@ template <int N, bool SOLVE>
 __global__ void __launch_bounds__(NT, tma_blocks<SOLVE>()) k_strided_tma(const __grid_constant__ CUtensorMap map, int mode,
                                                     const float* __restrict__ mu1, float lambda, float scale,
                                                     const float* __restrict__ tw_g, int* __restrict__ err,
-                                                    int reps) {
+                                                    int reps, const int* __restrict__ skip) {
   using C = TmaTile<N>;
   constexpr int W = TMA_W, NX = N / TMA_W;
   constexpr int ntiles = NX * (N - 1);
@@ -592,11 +598,15 @@ __global__ void __launch_bounds__(NT, tma_blocks<SOLVE>()) k_strided_tma(const _
   float* sinv = tw + 4 * N;
   float* mus = sinv + N;
   uint64_t* bar = reinterpret_cast<uint64_t*>(mus + N);
+  // an iteration enqueued ahead of the convergence test: nothing to do (the
+  // flag is read early and tested before any copy is issued)
+  const bool skipped = skip != nullptr && *skip != 0;
   for (int i = threadIdx.x; i < 4 * N; i += NT) tw[i] = tw_g[i];
   for (int i = threadIdx.x; i < N; i += NT) {
     sinv[i] = tw_g[2 * i + 1];
     mus[i] = mu1[i];
   }
+  if (skipped) return;
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -705,10 +715,10 @@ int launch_strided3(kfbi_handle* h, int mode, bool solve, T* work, const T* mu1,
       const int grid = tiles < nb ? tiles : nb;
       if (solve) {
         if ((rc = prep(k_strided_tma<N, true>, smem))) return rc;
-        k_strided_tma<N, true><<<grid, NT, smem, st>>>(map, mode, mu1, lam, scale, tw, h->w.err, 2);
+        k_strided_tma<N, true><<<grid, NT, smem, st>>>(map, mode, mu1, lam, scale, tw, h->w.err, 2, h->skip);
       } else {
         if ((rc = prep(k_strided_tma<N, false>, smem))) return rc;
-        k_strided_tma<N, false><<<grid, NT, smem, st>>>(map, mode, mu1, lam, scale, tw, h->w.err, 1);
+        k_strided_tma<N, false><<<grid, NT, smem, st>>>(map, mode, mu1, lam, scale, tw, h->w.err, 1, h->skip);
       }
       return KFBI_OK;
     }
@@ -719,11 +729,11 @@ int launch_strided3(kfbi_handle* h, int mode, bool solve, T* work, const T* mu1,
   if (solve) {
     if ((rc = prep(k_strided<T, N, true, 3>, smem))) return rc;
     k_strided<T, N, true, 3><<<grid, NT, smem, st>>>(work, mode == 0 ? N : NN, mode == 0 ? NN : N, 1, mu1, lam,
-                                                     scale, tw);
+                                                     scale, tw, h->skip);
   } else {
     if ((rc = prep(k_strided<T, N, false, 3>, smem))) return rc;
     k_strided<T, N, false, 3><<<grid, NT, smem, st>>>(work, mode == 0 ? N : NN, mode == 0 ? NN : N, 1, mu1, lam,
-                                                      scale, tw);
+                                                      scale, tw, h->skip);
   }
   return KFBI_OK;
 }
@@ -742,20 +752,22 @@ int run_solve(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1, const 
   if (dim == 3) {
     dim3 grid(N / W, N - 1);
     if ((rc = prep(k_xfwd<T, N, 3>, smem))) return rc;
-    k_xfwd<T, N, 3><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.src32, sa.corr, t.irr, t.line_start, tw);
+    k_xfwd<T, N, 3><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.src32, sa.corr, t.irr, t.line_start, tw,
+                                             h->skip);
     if ((rc = launch_strided3<T, N>(h, 0, false, work, mu1, lam, scale, tw))) return rc;
     if ((rc = launch_strided3<T, N>(h, 1, true, work, mu1, lam, scale, tw))) return rc;
     if ((rc = launch_strided3<T, N>(h, 0, false, work, mu1, lam, scale, tw))) return rc;
     if ((rc = prep(k_xinv<T, N, 3>, smem))) return rc;
-    k_xinv<T, N, 3><<<grid, NT, smem, st>>>(work, true, sa.out_user, sa.aux, sa.beta, sa.gamma, tw);
+    k_xinv<T, N, 3><<<grid, NT, smem, st>>>(work, true, sa.out_user, sa.aux, sa.beta, sa.gamma, tw, h->skip);
   } else {
     dim3 grid(N / W, 1);
     if ((rc = prep(k_xfwd<T, N, 2>, smem))) return rc;
-    k_xfwd<T, N, 2><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.src32, sa.corr, t.irr, t.line_start, tw);
+    k_xfwd<T, N, 2><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.src32, sa.corr, t.irr, t.line_start, tw,
+                                             h->skip);
     if ((rc = prep(k_strided<T, N, true, 2>, smem))) return rc;
-    k_strided<T, N, true, 2><<<grid, NT, smem, st>>>(work, N, 0, 0, mu1, lam, scale, tw);
+    k_strided<T, N, true, 2><<<grid, NT, smem, st>>>(work, N, 0, 0, mu1, lam, scale, tw, h->skip);
     if ((rc = prep(k_xinv<T, N, 2>, smem))) return rc;
-    k_xinv<T, N, 2><<<grid, NT, smem, st>>>(work, true, sa.out_user, sa.aux, sa.beta, sa.gamma, tw);
+    k_xinv<T, N, 2><<<grid, NT, smem, st>>>(work, true, sa.out_user, sa.aux, sa.beta, sa.gamma, tw, h->skip);
   }
   KFBI_CHECK_LAUNCH_N(dim == 3 ? 5 : 3);
   return KFBI_OK;
@@ -778,26 +790,26 @@ int run_pass(kfbi_handle* h, int pass, double lambda, T* work, const T* mu1, con
   if (dim == 3) {
     if (pass == 0) {
       if ((rc = prep(k_xfwd<T, N, 3>, smem))) return rc;
-      k_xfwd<T, N, 3><<<grid, NT, smem, st>>>(work, nullptr, 1.0, nullptr, nullptr, t.irr, t.line_start, tw);
+      k_xfwd<T, N, 3><<<grid, NT, smem, st>>>(work, nullptr, 1.0, nullptr, nullptr, t.irr, t.line_start, tw, nullptr);
     } else if (pass == 1) {
       if ((rc = launch_strided3<T, N>(h, 0, false, work, mu1, lam, scale, tw))) return rc;
     } else if (pass == 2) {
       if ((rc = launch_strided3<T, N>(h, 1, true, work, mu1, lam, scale, tw))) return rc;
     } else {
       if ((rc = prep(k_xinv<T, N, 3>, smem))) return rc;
-      k_xinv<T, N, 3><<<grid, NT, smem, st>>>(work, true, nullptr, nullptr, 1.0, 0.0, tw);
+      k_xinv<T, N, 3><<<grid, NT, smem, st>>>(work, true, nullptr, nullptr, 1.0, 0.0, tw, nullptr);
     }
     (void)NN;
   } else {
     if (pass == 0) {
       if ((rc = prep(k_xfwd<T, N, 2>, smem))) return rc;
-      k_xfwd<T, N, 2><<<grid, NT, smem, st>>>(work, nullptr, 1.0, nullptr, nullptr, t.irr, t.line_start, tw);
+      k_xfwd<T, N, 2><<<grid, NT, smem, st>>>(work, nullptr, 1.0, nullptr, nullptr, t.irr, t.line_start, tw, nullptr);
     } else if (pass == 1 || pass == 2) {
       if ((rc = prep(k_strided<T, N, true, 2>, smem))) return rc;
-      k_strided<T, N, true, 2><<<grid, NT, smem, st>>>(work, N, 0, 0, mu1, lam, scale, tw);
+      k_strided<T, N, true, 2><<<grid, NT, smem, st>>>(work, N, 0, 0, mu1, lam, scale, tw, nullptr);
     } else {
       if ((rc = prep(k_xinv<T, N, 2>, smem))) return rc;
-      k_xinv<T, N, 2><<<grid, NT, smem, st>>>(work, true, nullptr, nullptr, 1.0, 0.0, tw);
+      k_xinv<T, N, 2><<<grid, NT, smem, st>>>(work, true, nullptr, nullptr, 1.0, 0.0, tw, nullptr);
     }
   }
   KFBI_CHECK_LAUNCH();

@@ -146,6 +146,8 @@ struct Workspace {
   double* proj = nullptr;         // Gram matrix, right side, coefficients
   double* host_small = nullptr;   // pinned host scalars
   int* err = nullptr;             // device error word
+  int* stop = nullptr;            // Krylov stop flag (set by the Arnoldi step)
+  unsigned* counter = nullptr;    // ticket counter of the single-launch reductions
   int restart_cap = 0;
 };
 
@@ -168,6 +170,10 @@ struct kfbi_handle {
   // TMA descriptors of the float32 padded grid: [N x 32] tiles along y and z
   CUtensorMap tmap_y32, tmap_z32;
   bool tma = false;
+  // device flag handed to the launches of a Krylov iteration enqueued ahead
+  // of the host's convergence test (nullptr otherwise)
+  const int* skip = nullptr;
+  cudaEvent_t arn_ev[2] = {nullptr, nullptr};  // per-iteration completion events
 };
 
 namespace kfbi {
@@ -247,6 +253,7 @@ int vec_axpby(kfbi_handle* h, double* y, double a, const double* x, double b, in
 int vec_scale_by_norm(kfbi_handle* h, double* v, const double* w, const double* norm_dev, int n);
 int vec_copy(kfbi_handle* h, double* dst, const double* src, int n);
 int arnoldi_givens(kfbi_handle* h, double* small, int j, int ldh);
+int arnoldi_step(kfbi_handle* h, double* V, int ld, double* wv, int j, int m, double gnorm, double tol);
 int arnoldi_solve(kfbi_handle* h, double* small, int k, int ldh);
 
 // mlp.cu

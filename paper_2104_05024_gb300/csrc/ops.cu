@@ -16,9 +16,10 @@ namespace {
 
 constexpr int RED_BLOCKS = 152;  // one partial sum per SM for the dot products
 
-__global__ void k_correction(Tables t, const double* __restrict__ x, double* __restrict__ corr) {
+__global__ void k_correction(Tables t, const double* __restrict__ x, double* __restrict__ corr,
+                             const int* __restrict__ skip) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= t.n_irr) return;
+  if (i >= t.n_irr || (skip != nullptr && *skip)) return;
   const int na = t.irr_narm[i];
   double acc = 0.0;
   for (int a = 0; a < na; ++a) {
@@ -49,9 +50,10 @@ __global__ void k_spline(const double* __restrict__ gcol, const double* __restri
 // out_i = base_i + sgn * (sum_j wn_ij v(p_j) + sum_k dw_ik x[dpid_ik])
 template <typename T>
 __global__ void k_limit(Tables t, GridParams gr, const T* __restrict__ grid, const double* __restrict__ x,
-                        const double* __restrict__ base, double sgn, double* __restrict__ out) {
+                        const double* __restrict__ base, double sgn, double* __restrict__ out,
+                        const int* __restrict__ skip) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= t.M) return;
+  if (i >= t.M || (skip != nullptr && *skip)) return;
   const int d = gr.dim, N = gr.N;
   const int64_t sx = 1, sy = N, sz = (int64_t)N * N;
   const int64_t c = t.n_base[i];
@@ -331,7 +333,9 @@ __global__ void k_axpby(double* __restrict__ y, double a, const double* __restri
   if (i < n) y[i] = a * x[i] + b * y[i];
 }
 
-__global__ void k_scale_norm(double* __restrict__ v, const double* __restrict__ w, const double* __restrict__ nrm2, int n) {
+__global__ void k_scale_norm(double* __restrict__ v, const double* __restrict__ w, const double* __restrict__ nrm2, int n,
+                             const int* __restrict__ skip) {
+  if (skip != nullptr && *skip) return;
   const double s = sqrt(nrm2[0]);
   const double inv = s > 0.0 ? 1.0 / s : 0.0;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -354,7 +358,7 @@ struct SmallLayout {
 };
 
 // column j of H from hcol and sqrt(nrm2); apply rotations; new rotation; |g_{j+1}|
-__global__ void k_givens(double* s, int m, int j) {
+__device__ void givens_column(double* s, int m, int j) {
   SmallLayout L{m};
   double* H = s + L.H();
   double* cs = s + L.cs();
@@ -378,6 +382,121 @@ __global__ void k_givens(double* s, int m, int j) {
   g[j] = cs[j] * g[j];
   for (int i = 0; i <= j + 1; ++i) H[(size_t)j * (m + 1) + i] = col[i];
   s[L.res()] = fabs(g[j + 1]);
+}
+
+__global__ void k_givens(double* s, int m, int j) { givens_column(s, m, j); }
+
+// ---------------------------------------------- fused Arnoldi step (CGS2)
+// One Krylov step after w = A v_j takes four launches: h = V^T w; w -= V h
+// with y = V^T w; w -= V y with ||w||^2, H(:, j) = h + y and the Givens
+// update; v_{j+1} = w / ||w||.  Each block owns a contiguous slice of rows;
+// the last block to finish (a ticket counter, reset by that block) reduces
+// the per-block partial sums in a fixed order, so results do not depend on
+// block scheduling.  skip (optional): a device flag; when set, the kernel
+// does nothing (an iteration enqueued ahead of the convergence test).
+__device__ __forceinline__ void arn_rows(int n, int& r0, int& r1) {
+  const int per = ((n + (int)gridDim.x - 1) / (int)gridDim.x + 31) & ~31;
+  r0 = min(n, (int)blockIdx.x * per);
+  r1 = min(n, r0 + per);
+}
+
+// true in every thread of the block that finishes last
+__device__ __forceinline__ bool arn_last_block(unsigned* counter) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  return last;
+}
+
+// out[k] = sum_b partial[k][b] for k < nv, one warp per k
+__device__ __forceinline__ void arn_reduce(const double* partial, int nb, int nv, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = warp; k < nv; k += nw) {
+    double acc = 0.0;
+    for (int b = lane; b < nb; b += 32) acc += __ldcg(&partial[(size_t)k * nb + b]);
+    acc = warp_sum(acc);
+    if (lane == 0) out[k] = acc;
+  }
+}
+
+// [UPDATE: w -= sum_k coef[k] V_k;]  out[k] = V_k . w  (k < nv)
+template <bool UPDATE>
+__global__ void __launch_bounds__(256) k_arn_gs(double* __restrict__ w, const double* __restrict__ V, int ld, int n,
+                                                int nv, const double* __restrict__ coef, double* __restrict__ partial,
+                                                unsigned* __restrict__ counter, double* __restrict__ out,
+                                                const int* __restrict__ skip) {
+  if (skip != nullptr && *skip) return;
+  __shared__ double cs[MAX_RESTART + 2];
+  int r0, r1;
+  arn_rows(n, r0, r1);
+  if (UPDATE) {
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) cs[k] = coef[k];
+    __syncthreads();
+    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      double acc = 0.0;
+      for (int k = 0; k < nv; ++k) acc += cs[k] * V[(size_t)k * ld + i];
+      w[i] -= acc;
+    }
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = warp; k < nv; k += nw) {
+    const double* v = V + (size_t)k * ld;
+    double acc = 0.0;
+    for (int i = r0 + lane; i < r1; i += 32) acc += v[i] * w[i];
+    acc = warp_sum(acc);
+    if (lane == 0) partial[(size_t)k * gridDim.x + blockIdx.x] = acc;
+  }
+  if (!arn_last_block(counter)) return;
+  arn_reduce(partial, gridDim.x, nv, out);
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// w -= sum_k y[k] V_k; ||w||^2; hcol += y; Givens update of column j; the
+// residual estimate |g_{j+1}| and the stop flag (estimate / gnorm <= tol, or
+// not finite: the host's test, in the same float64 operations)
+__global__ void __launch_bounds__(256) k_arn_close(double* __restrict__ w, const double* __restrict__ V, int ld, int n,
+                                                   int nv, double* __restrict__ s, int m, int j,
+                                                   double* __restrict__ partial, unsigned* __restrict__ counter,
+                                                   double gnorm, double tol, int* stop, const int* skip) {
+  if (skip != nullptr && *skip) return;
+  SmallLayout L{m};
+  __shared__ double cs[MAX_RESTART + 2];
+  __shared__ double ws[32];
+  int r0, r1;
+  arn_rows(n, r0, r1);
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) cs[k] = s[L.y() + k];
+  __syncthreads();
+  double sq = 0.0;
+  for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    double acc = 0.0;
+    for (int k = 0; k < nv; ++k) acc += cs[k] * V[(size_t)k * ld + i];
+    const double wi = w[i] - acc;
+    w[i] = wi;
+    sq += wi * wi;
+  }
+  sq = warp_sum(sq);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+  }
+  if (!arn_last_block(counter)) return;
+  if (threadIdx.x < 32) arn_reduce(partial, gridDim.x, 1, s + L.nrm2());
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) s[L.hcol() + k] += cs[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    givens_column(s, m, j);
+    const double rel = s[L.res()] / gnorm;
+    const int done = !(rel > tol) || !isfinite(rel);
+    s[L.res() + 1] = done ? 1.0 : 0.0;
+    *stop = done;
+    *counter = 0u;
+  }
 }
 
 // y = R^{-1} g for the leading k x k block
@@ -407,23 +526,38 @@ __global__ void k_add_small(double* s, int m, int n) {
 }
 
 // ------------------------------------------------------------- reaction
-// FP64 work is scarce on this part (2 FMA per SM per clock), so the pointwise
-// kernels keep float64 for what must be float64 and fold the constants: the
-// forward-Euler half step has no division left.
+// FP64 work is scarce on this part (2 FMA per SM per clock): the pointwise
+// kernels keep float64 for what must be float64, write the cubic of the
+// ionic current in Horner form with the constants folded (one fused
+// multiply-add per power), and take branch decisions on integer bits.
+//
+// Forward-Euler half step: with a = k H / Cm,
+//   V1 = V + a (V (V - theta)(1 - V) - q)
+//      = ((-a V + a (1 + theta)) V - a theta) V + (V - a q),
+//   q1 = (1 - k zeta) q + k alpha V.
 __global__ void k_react_fe(kfbi_fhn p, double k, double* __restrict__ V, double* __restrict__ w, int64_t n) {
-  const double a = k * p.H / p.Cm, ka = k * p.alpha, kz = k * p.zeta;
+  const double a = k * p.H / p.Cm, ka = k * p.alpha, kz1 = 1.0 - k * p.zeta;
+  const double p1 = a * (1.0 + p.theta), p0 = -a * p.theta;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double v = V[i], q = w[i];
-    const double cubic = v * (v - p.theta) * (1.0 - v);
-    V[i] = v - a * (q - cubic);
-    w[i] = q + (ka * v - kz * q);
+    const double t = fma(fma(-a, v, p1), v, p0);
+    V[i] = fma(t, v, fma(-a, q, v));
+    w[i] = fma(ka, v, kz1 * q);
   }
 }
 
+// |x| < bound (bound > 0) on the bits: no float64 instruction; false for NaN
+__device__ __forceinline__ bool abs_below(double x, double bound) {
+  return (__double_as_longlong(x) & 0x7fffffffffffffffLL) < __double_as_longlong(bound);
+}
+
 // Backward-Euler half step: w is eliminated (w1 = (w0 + k alpha v) / (1 + k
-// zeta)) and Newton solves the cubic in v.  Float32 Newton steps first bring
-// v to float32 resolution (error e0 <~ 1e-7 |v|); a float64 step then uses
-// the exact float64 residual with the float32 derivative (a quasi-Newton step:
+// zeta)) and Newton solves the cubic in v,
+//   F(v) = v - v0 - c (v (v - theta)(1 - v) - w1(v))
+//        = ((c v - c (1 + theta)) v + (1 + c theta + c k alpha / den)) v + (c w0 / den - v0),
+// c = k H / Cm, den = 1 + k zeta.  Float32 Newton steps first bring v to
+// float32 resolution (error e0 <~ 1e-7 |v|); a float64 step then uses the
+// exact float64 residual with the float32 derivative (a quasi-Newton step:
 // error <~ 1e-7 e0 + C e0^2, about 1e-14), without any float64 division.
 // Converged: the float32 phase converged and that float64 step moved v by
 // less than 1e-5 (so a further step would move it by < 1e-10, the plain
@@ -435,6 +569,8 @@ __global__ void k_react_be(kfbi_fhn p, double k, double* __restrict__ V, double*
   const double den = 1.0 + k * p.zeta;
   const double inv_den = 1.0 / den;
   const double ka = k * p.alpha;
+  const double e2 = -c * (1.0 + p.theta), e1 = 1.0 + c * p.theta + c * ka * inv_den, cid = c * inv_den;
+  const double kid = ka * inv_den;
   const float cf = (float)c, rf = (float)(ka / den), thf = (float)p.theta, kaf = (float)ka, idf = (float)inv_den;
   const float th1 = 2.0f * (1.0f + thf);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -455,23 +591,24 @@ __global__ void k_react_be(kfbi_fhn p, double k, double* __restrict__ V, double*
       const float Fv = vf - v0f - cf * (vf * (vf - thf) * (1.0f - vf) - q1);
       f32_ok = fabsf(Fv) <= 1e-5f;
     }
+    const double a0 = fma(cid, q0, -v0);
     double v = vf;
+    float xf = vf;
     bool ok = false;
     for (int it = 0; it < 50; ++it) {
-      const float xf = (float)v;
       const double rdF = (double)(1.0f / (1.0f - cf * ((-3.0f * xf + th1) * xf - thf - rf)));
-      const double q1 = (q0 + ka * v) * inv_den;
-      const double F = v - v0 - c * (v * (v - p.theta) * (1.0 - v) - q1);
+      const double F = fma(fma(fma(c, v, e2), v, e1), v, a0);
       const double dv = F * rdF;
       v -= dv;
-      if (fabs(dv) < 1e-10 || (it == 0 && f32_ok && fabs(dv) < 1e-5)) {
+      if (abs_below(dv, 1e-10) || (it == 0 && f32_ok && abs_below(dv, 1e-5))) {
         ok = true;
         break;
       }
+      xf = (float)v;
     }
     if (!ok) atomicOr(err, DEVERR_NEWTON);
     V[i] = v;
-    w[i] = (q0 + ka * v) * inv_den;
+    w[i] = fma(kid, v, q0 * inv_den);
   }
 }
 
@@ -517,7 +654,7 @@ int small_y(int m) { return SmallLayout{m}.y(); }
 
 int launch_correction(kfbi_handle* h, const double* x, double* corr) {
   if (h->t.n_irr == 0) return KFBI_OK;
-  k_correction<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->t, x, corr);
+  k_correction<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->t, x, corr, h->skip);
   KFBI_CHECK_LAUNCH();
   return KFBI_OK;
 }
@@ -530,13 +667,13 @@ int launch_spline(kfbi_handle* h, const double* psi, double* x) {
 }
 
 int launch_limit64(kfbi_handle* h, const double* grid, const double* x, const double* base, double sgn, double* out) {
-  k_limit<double><<<(h->t.M + 127) / 128, 128, 0, h->stream>>>(h->t, h->grid, grid, x, base, sgn, out);
+  k_limit<double><<<(h->t.M + 127) / 128, 128, 0, h->stream>>>(h->t, h->grid, grid, x, base, sgn, out, h->skip);
   KFBI_CHECK_LAUNCH();
   return KFBI_OK;
 }
 
 int launch_limit32(kfbi_handle* h, const float* grid, const double* x, const double* base, double sgn, double* out) {
-  k_limit<float><<<(h->t.M + 127) / 128, 128, 0, h->stream>>>(h->t, h->grid, grid, x, base, sgn, out);
+  k_limit<float><<<(h->t.M + 127) / 128, 128, 0, h->stream>>>(h->t, h->grid, grid, x, base, sgn, out, h->skip);
   KFBI_CHECK_LAUNCH();
   return KFBI_OK;
 }
@@ -657,7 +794,7 @@ int vec_axpby(kfbi_handle* h, double* y, double a, const double* x, double b, in
 }
 
 int vec_scale_by_norm(kfbi_handle* h, double* v, const double* w, const double* norm_dev, int n) {
-  k_scale_norm<<<(n + 255) / 256, 256, 0, h->stream>>>(v, w, norm_dev, n);
+  k_scale_norm<<<(n + 255) / 256, 256, 0, h->stream>>>(v, w, norm_dev, n, nullptr);
   KFBI_CHECK_LAUNCH();
   return KFBI_OK;
 }
@@ -676,6 +813,28 @@ int arnoldi_givens(kfbi_handle* h, double* small, int j, int m) {
 int arnoldi_solve(kfbi_handle* h, double* small, int k, int m) {
   k_backsolve<<<1, 1, 0, h->stream>>>(small, m, k);
   KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+// one CGS2 Arnoldi step on wv = A v_j (basis V, leading dimension ld,
+// restart m): H(:, j), the Givens update, v_{j+1}, and at small[res],
+// small[res + 1] the residual estimate and the stop flag (also written to
+// h->w.stop).  Launches carry h->skip.
+int arnoldi_step(kfbi_handle* h, double* V, int ld, double* wv, int j, int m, double gnorm, double tol) {
+  const int n = h->t.M;
+  int nb = (n + 255) / 256;
+  if (nb > RED_BLOCKS) nb = RED_BLOCKS;
+  SmallLayout L{m};
+  double* s = h->w.small;
+  const int nv = j + 1;
+  k_arn_gs<false><<<nb, 256, 0, h->stream>>>(wv, V, ld, n, nv, nullptr, h->w.partial, h->w.counter, s + L.hcol(),
+                                             h->skip);
+  k_arn_gs<true><<<nb, 256, 0, h->stream>>>(wv, V, ld, n, nv, s + L.hcol(), h->w.partial, h->w.counter, s + L.y(),
+                                            h->skip);
+  k_arn_close<<<nb, 256, 0, h->stream>>>(wv, V, ld, n, nv, s, m, j, h->w.partial, h->w.counter, gnorm, tol, h->w.stop,
+                                         h->skip);
+  k_scale_norm<<<(n + 255) / 256, 256, 0, h->stream>>>(V + (size_t)(j + 1) * ld, wv, s + L.nrm2(), n, h->skip);
+  KFBI_CHECK_LAUNCH_N(4);
   return KFBI_OK;
 }
 

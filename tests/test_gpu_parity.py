@@ -157,6 +157,37 @@ def test_gmres_fixed_iterations(name, lam):
         assert abs(st["rel_res"] - info["rel_res"]) < 1e-9 * max(info["rel_res"], 1e-3)
 
 
+@pytest.mark.parametrize("name,lam", [("ellipse64", 60.0), ("sphere32", 40.0)])
+def test_gmres_restarted_and_early_stop(name, lam):
+    """Restarted GMRES(3) at fixed counts and tolerances met inside a cycle,
+    against the oracle's GMRES.  The library enqueues iteration j + 1 before
+    the host reads iteration j's residual estimate; the device's stop flag
+    must turn that iteration into no work without changing the result."""
+    geom, grid, o, _ = pair(name)
+    gv = np.random.default_rng(5).standard_normal(geom.M)
+    for restart in (3, 50):
+        g = K.KFBI(geom, grid, tol=1e-12, restart=restart, max_iter=300)
+        try:
+            if restart == 3:
+                for its in (3, 7):
+                    x, info = krylov.gmres(lambda v: o.apply_A(v, lam), gv, np.zeros(geom.M), 0.0, restart=3,
+                                           max_iter=its)
+                    psi = torch.zeros(geom.M, dtype=torch.float64, device=DEV)
+                    st = g.solve_bie(cuda(gv), psi, lam, tol=0.0, max_iter=its)
+                    assert st["iters"] == its
+                    assert rel(psi.cpu().numpy(), x) < TOL64
+            for tol in ((1e-6,) if restart == 3 else (1e-6, 1e-11)):
+                x, info = krylov.gmres(lambda v: o.apply_A(v, lam), gv, np.zeros(geom.M), tol, restart=restart,
+                                       max_iter=300)
+                psi = torch.zeros(geom.M, dtype=torch.float64, device=DEV)
+                st = g.solve_bie(cuda(gv), psi, lam, tol=tol, max_iter=300)
+                assert info["converged"] and st["rel_res"] <= tol
+                assert st["iters"] == info["iters"], (restart, tol, st["iters"], info["iters"])
+                assert rel(psi.cpu().numpy(), x) < max(TOL64, 1e-3 * tol)
+        finally:
+            g.close()
+
+
 @pytest.mark.parametrize("name,lam", [("ellipse64", 60.0), ("star32", 40.0)])
 def test_richardson_fixed_iterations(name, lam):
     """The simple iteration psi <- psi + 2 gamma (g - A psi), gamma = 0.8
