@@ -100,6 +100,16 @@ int read_scalar(kfbi_handle* h, const double* dev, double* out) {
   return KFBI_OK;
 }
 
+// two device scalars with one synchronisation
+int read_two(kfbi_handle* h, const double* a, const double* b, double* va, double* vb) {
+  KFBI_CUDA(cudaMemcpyAsync(h->w.host_small, a, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  KFBI_CUDA(cudaMemcpyAsync(h->w.host_small + 1, b, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  KFBI_CUDA(cudaStreamSynchronize(h->stream));
+  *va = h->w.host_small[0];
+  *vb = h->w.host_small[1];
+  return KFBI_OK;
+}
+
 int norm2(kfbi_handle* h, const double* v, double* slot, double* out) {
   int rc = vec_dots(h, v, 1, h->t.M, v, slot);
   if (rc) return rc;
@@ -142,6 +152,7 @@ int refined_solve(kfbi_handle* h, const double* src, double alpha, const double*
     sr.aux = u;
     sr.beta = 1.0;
     sr.gamma = 1.0;
+    sr.keep = false;  // only u is read after a refinement round
     if ((rc = box_solve32(h, sr, h->w.grid32))) return rc;
   }
   return KFBI_OK;
@@ -191,13 +202,14 @@ int arnoldi_iteration(kfbi_handle* h, int prec, double lambda, int j, double gno
 
 // GMRES(m) with CGS2 Arnoldi on A psi = g; psi in: initial guess, out: solution.
 // zero_guess: psi is known to be zero, so the first residual is g itself.
-// fallback (optional): an alternative initial guess with known residual norm
-// fallback_res (relative to nothing: ||g - A fallback||); it replaces psi
-// when psi's first residual is larger.
+// fallback (optional): an alternative initial guess whose squared residual
+// norm ||g - A fallback||^2 is in the device slot fallback_res2; it replaces
+// psi when psi's first residual is larger (both read with one
+// synchronisation).
 // gnorm_known (>= 0): ||g|| already read by the caller (saves a synchronisation).
 int gmres(kfbi_handle* h, int prec, double lambda, const double* g, double* psi, kfbi_stats* st, double tol,
-          int max_iter, bool zero_guess = false, const double* fallback = nullptr, double fallback_res = 0.0,
-          double gnorm_known = -1.0) {
+          int max_iter, bool zero_guess = false, const double* fallback = nullptr,
+          const double* fallback_res2 = nullptr, double gnorm_known = -1.0) {
   const int M = h->t.M;
   const int m = h->opts.restart;
   double* V = h->w.vecs;
@@ -219,13 +231,18 @@ int gmres(kfbi_handle* h, int prec, double lambda, const double* g, double* psi,
       return rc;
     }
     if ((rc = vec_dots(h, r, 1, M, r, s + small_nrm2(m)))) return rc;
-    double beta;
+    double beta, fallback_res = 0.0;
     if (first && zero_guess) {
       beta = gnorm_raw;  // r = g: the same reduction as ||g||, no second read
     } else {
-      double b2;
-      if ((rc = read_scalar(h, s + small_nrm2(m), &b2))) return rc;
+      double b2, f2 = 0.0;
+      if (first && fallback != nullptr) {
+        if ((rc = read_two(h, s + small_nrm2(m), fallback_res2, &b2, &f2))) return rc;
+      } else if ((rc = read_scalar(h, s + small_nrm2(m), &b2))) {
+        return rc;
+      }
       beta = std::sqrt(b2);
+      fallback_res = std::sqrt(f2);
     }
     if (first && fallback != nullptr && beta > fallback_res) {
       // the residual judges the guess: go back to the alternative
@@ -314,25 +331,34 @@ int richardson(kfbi_handle* h, int prec, double lambda, const double* g, double*
 // GMRES with iterative refinement (Carson and Higham): the outer residual
 // r = g - A psi uses float64-accurate box solves, the inner correction solve
 // A delta = r runs GMRES with float32 box solves and float64 Arnoldi.
-// fallback (optional): an alternative initial guess whose residual norm is
-// fallback_res; it replaces psi when psi's first residual is larger.
+// fallback (optional): an alternative initial guess whose squared residual
+// norm is in the device slot fallback_res2; it replaces psi when psi's first
+// residual is larger.  gnorm_known (>= 0): ||g|| already read by the caller.
 int gmres_ir(kfbi_handle* h, double lambda, const double* g, double* psi, kfbi_stats* st,
-             const double* fallback = nullptr, double fallback_res = 0.0) {
+             const double* fallback = nullptr, const double* fallback_res2 = nullptr, double gnorm_known = -1.0) {
   const int M = h->t.M;
   double* r = h->w.r2;
   double* delta = h->w.tmp2;
   double* slot = h->w.small + small_nrm2(h->opts.restart);
   const double tol = h->opts.tol;
   int rc;
-  double gnorm;
-  if ((rc = norm2(h, g, slot, &gnorm))) return rc;
+  double gnorm = gnorm_known;
+  if (gnorm < 0.0 && (rc = norm2(h, g, slot, &gnorm))) return rc;
   if (gnorm == 0.0) gnorm = 1.0;
   int inner_total = 0, outer = 0;
   double rel = 0.0;
   for (;;) {
     if ((rc = apply_A_acc(h, lambda, psi, r, -1.0, g))) return rc;
-    double rn;
-    if ((rc = norm2(h, r, slot, &rn))) return rc;
+    double rn, fallback_res = 0.0;
+    if (outer == 0 && fallback != nullptr) {
+      double rn2, f2;
+      if ((rc = vec_dots(h, r, 1, M, r, slot))) return rc;
+      if ((rc = read_two(h, slot, fallback_res2, &rn2, &f2))) return rc;
+      rn = std::sqrt(rn2);
+      fallback_res = std::sqrt(f2);
+    } else if ((rc = norm2(h, r, slot, &rn))) {
+      return rc;
+    }
     if (outer == 0 && fallback != nullptr && rn > fallback_res) {
       // the residual judges the guess: go back to the alternative
       if ((rc = vec_copy(h, psi, fallback, M))) return rc;
@@ -354,7 +380,7 @@ int gmres_ir(kfbi_handle* h, double lambda, const double* g, double* psi, kfbi_s
     if (tin > 0.5) tin = 0.5;
     KFBI_CUDA(cudaMemsetAsync(delta, 0, sizeof(double) * (size_t)M, h->stream));
     kfbi_stats in{};
-    rc = gmres(h, KFBI_MIXED, lambda, r, delta, &in, tin, h->opts.max_iter - inner_total, true, nullptr, 0.0, rn);
+    rc = gmres(h, KFBI_MIXED, lambda, r, delta, &in, tin, h->opts.max_iter - inner_total, true, nullptr, nullptr, rn);
     if (rc != KFBI_OK && rc != KFBI_ERR_NOT_CONVERGED) return rc;
     inner_total += in.iters;
     if ((rc = vec_axpby(h, psi, 1.0, delta, 1.0, M))) return rc;
@@ -367,10 +393,11 @@ int gmres_ir(kfbi_handle* h, double lambda, const double* g, double* psi, kfbi_s
 }
 
 int solve_bie(kfbi_handle* h, int prec, double lambda, const double* g, double* psi, kfbi_stats* st,
-              const double* fallback = nullptr, double fallback_res = 0.0) {
+              const double* fallback = nullptr, const double* fallback_res2 = nullptr, double gnorm_known = -1.0) {
   if (h->opts.solver == KFBI_RICHARDSON) return richardson(h, prec, lambda, g, psi, st);
-  if (prec != KFBI_FP64) return gmres_ir(h, lambda, g, psi, st, fallback, fallback_res);
-  return gmres(h, prec, lambda, g, psi, st, h->opts.tol, h->opts.max_iter, false, fallback, fallback_res);
+  if (prec != KFBI_FP64) return gmres_ir(h, lambda, g, psi, st, fallback, fallback_res2, gnorm_known);
+  return gmres(h, prec, lambda, g, psi, st, h->opts.tol, h->opts.max_iter, false, fallback, fallback_res2,
+               gnorm_known);
 }
 
 // ------------------------------------------------ projection warm start
@@ -380,23 +407,25 @@ int solve_bie(kfbi_handle* h, int prec, double lambda, const double* g, double* 
 // A.  c minimises that residual (normal equations of the k <= KFBI_HISTORY
 // stored g_s, Cholesky on the host, columns that are numerically dependent
 // on earlier ones dropped).
-int project_history(kfbi_handle* h, const double* g, double* rF_norm) {
+// out: gnorm = ||g||; rF2 = the device slot that receives ||r_F||^2 (read
+// by the solver together with its first residual).  One synchronisation.
+int project_history(kfbi_handle* h, const double* g, double* gnorm, const double** rF2) {
   const int M = h->t.M;
   const int k = h->hist_count < KFBI_HISTORY ? h->hist_count : KFBI_HISTORY;
   double* G = h->w.proj;             // [k][k]
   double* b = G + KFBI_HISTORY * KFBI_HISTORY;
   double* cdev = b + KFBI_HISTORY;
+  double* sq = cdev + KFBI_HISTORY;  // ||psi_F||^2 (learned form), ||r_F||^2, ||g||^2
   int rc;
   if ((rc = vec_copy(h, h->w.rF, g, M))) return rc;
   KFBI_CUDA(cudaMemsetAsync(h->w.psiF, 0, sizeof(double) * (size_t)M, h->stream));
+  if ((rc = launch_gram(h, h->w.hist_g, k, g, G, b, sq + 2))) return rc;
+  double* hs = h->w.host_small;
+  const int nread = KFBI_HISTORY * (KFBI_HISTORY + 2) + 3;
+  KFBI_CUDA(cudaMemcpyAsync(hs, G, sizeof(double) * (size_t)nread, cudaMemcpyDeviceToHost, h->stream));
+  KFBI_CUDA(cudaStreamSynchronize(h->stream));
+  *gnorm = std::sqrt(hs[nread - 1]);
   if (k > 0) {
-    for (int i = 0; i < k; ++i)
-      if ((rc = vec_dots(h, h->w.hist_g, k, M, h->w.hist_g + (size_t)i * M, G + i * k))) return rc;
-    if ((rc = vec_dots(h, h->w.hist_g, k, M, g, b))) return rc;
-    double* hs = h->w.host_small;
-    KFBI_CUDA(cudaMemcpyAsync(hs, G, sizeof(double) * (size_t)(KFBI_HISTORY * KFBI_HISTORY + KFBI_HISTORY),
-                              cudaMemcpyDeviceToHost, h->stream));
-    KFBI_CUDA(cudaStreamSynchronize(h->stream));
     double A[KFBI_HISTORY][KFBI_HISTORY], L[KFBI_HISTORY][KFBI_HISTORY] = {}, y[KFBI_HISTORY] = {},
                                           c[KFBI_HISTORY] = {}, rhs[KFBI_HISTORY];
     bool keep[KFBI_HISTORY];
@@ -440,7 +469,9 @@ int project_history(kfbi_handle* h, const double* g, double* rF_norm) {
     if ((rc = vec_update(h, h->w.psiF, h->w.hist_psi, k, M, cdev, 1.0))) return rc;
     if ((rc = vec_update(h, h->w.rF, h->w.hist_g, k, M, cdev, -1.0))) return rc;
   }
-  return norm2(h, h->w.rF, h->w.small + small_nrm2(h->opts.restart), rF_norm);
+  if ((rc = vec_dots(h, h->w.rF, 1, M, h->w.rF, sq + 1))) return rc;
+  *rF2 = sq + 1;
+  return KFBI_OK;
 }
 
 int push_history(kfbi_handle* h, const double* psi, const double* g) {
@@ -560,7 +591,7 @@ int kfbi_create(const kfbi_geometry* geom, const kfbi_grid* grid, double sigma_i
   if ((rc = dalloc(h, &h->w.xvec, (size_t)2 * M))) return fail(rc);
   if ((rc = dalloc(h, &h->w.vecs, (size_t)(m + 1) * M))) return fail(rc);
   if ((rc = dalloc(h, &h->w.small, (size_t)small_size(MAX_RESTART)))) return fail(rc);
-  if ((rc = dalloc(h, &h->w.partial, (size_t)152 * (MAX_RESTART + 2) + 16))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.partial, (size_t)KFBI_ARN_BLOCKS * (MAX_RESTART + 2) + 16))) return fail(rc);
   if ((rc = dalloc(h, &h->w.g, (size_t)M))) return fail(rc);
   if ((rc = dalloc(h, &h->w.r, (size_t)M))) return fail(rc);
   if ((rc = dalloc(h, &h->w.tmp, (size_t)M))) return fail(rc);
@@ -852,19 +883,19 @@ static int bidomain_impl(kfbi_handle* h, const kfbi_fhn* p, const double* istim,
     // float32 residual is smaller
     if ((rc = vec_copy(h, h->w.psi_save, h->w.psi_prev, h->t.M))) return rc;
     const double* fallback = nullptr;
-    double fallback_res = 0.0;
+    const double* fallback_res2 = nullptr;
+    double gnorm = -1.0;
     const bool learned = h->opts.precision == KFBI_MIXED_LEARNED && h->warm != nullptr;
     if ((h->opts.warm == KFBI_WARM_PROJECTION || learned) && h->opts.solver == KFBI_GMRES && h->hist_count >= 1) {
       // psi_F from the history, then one step of the simple iteration
       // psi_F + 2 gamma r_F; psi_F itself (residual known) is the fallback
       const int M = h->t.M;
-      if ((rc = project_history(h, h->w.g, &fallback_res))) return rc;
+      if ((rc = project_history(h, h->w.g, &gnorm, &fallback_res2))) return rc;
       if (learned && h->grid.dim == 3) {
         // the network corrects psi_F + 2 gamma r_F in units of rms(r_F)
+        // (||r_F||^2 and ||g||^2 are already in sq[1], sq[2])
         double* sq = h->w.proj + KFBI_HISTORY * (KFBI_HISTORY + 2);
         if ((rc = vec_dots(h, h->w.psiF, 1, M, h->w.psiF, sq))) return rc;
-        if ((rc = vec_dots(h, h->w.rF, 1, M, h->w.rF, sq + 1))) return rc;
-        if ((rc = vec_dots(h, h->w.g, 1, M, h->w.g, sq + 2))) return rc;
         if ((rc = mlp_warmstart(h->warm, h->stream, h->w.psiF, h->w.rF, h->w.g, sq, h->t.nodes, h->t.n_normal, M,
                                 2.0 * h->opts.gamma, h->w.psi_prev)))
           return rc;
@@ -875,7 +906,7 @@ static int bidomain_impl(kfbi_handle* h, const kfbi_fhn* p, const double* istim,
       }
       fallback = h->w.psiF;
     }
-    const int src = solve_bie(h, prec, lam, h->w.g, h->w.psi_prev, &st, fallback, fallback_res);
+    const int src = solve_bie(h, prec, lam, h->w.g, h->w.psi_prev, &st, fallback, fallback_res2, gnorm);
     if (src != KFBI_OK && src != KFBI_ERR_NOT_CONVERGED) return src;
     if ((rc = vec_copy(h, h->w.psi_prev2, h->w.psi_save, h->t.M))) return rc;
     if ((rc = vec_copy(h, h->w.g_prev, h->w.g, h->t.M))) return rc;

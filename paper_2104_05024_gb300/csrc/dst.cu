@@ -758,7 +758,8 @@ int run_solve(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1, const 
     if ((rc = launch_strided3<T, N>(h, 1, true, work, mu1, lam, scale, tw))) return rc;
     if ((rc = launch_strided3<T, N>(h, 0, false, work, mu1, lam, scale, tw))) return rc;
     if ((rc = prep(k_xinv<T, N, 3>, smem))) return rc;
-    k_xinv<T, N, 3><<<grid, NT, smem, st>>>(work, true, sa.out_user, sa.aux, sa.beta, sa.gamma, tw, h->skip);
+    k_xinv<T, N, 3><<<grid, NT, smem, st>>>(work, sa.keep || sa.out_user == nullptr, sa.out_user, sa.aux, sa.beta,
+                                             sa.gamma, tw, h->skip);
   } else {
     dim3 grid(N / W, 1);
     if ((rc = prep(k_xfwd<T, N, 2>, smem))) return rc;
@@ -767,7 +768,8 @@ int run_solve(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1, const 
     if ((rc = prep(k_strided<T, N, true, 2>, smem))) return rc;
     k_strided<T, N, true, 2><<<grid, NT, smem, st>>>(work, N, 0, 0, mu1, lam, scale, tw, h->skip);
     if ((rc = prep(k_xinv<T, N, 2>, smem))) return rc;
-    k_xinv<T, N, 2><<<grid, NT, smem, st>>>(work, true, sa.out_user, sa.aux, sa.beta, sa.gamma, tw, h->skip);
+    k_xinv<T, N, 2><<<grid, NT, smem, st>>>(work, sa.keep || sa.out_user == nullptr, sa.out_user, sa.aux, sa.beta,
+                                             sa.gamma, tw, h->skip);
   }
   KFBI_CHECK_LAUNCH_N(dim == 3 ? 5 : 3);
   return KFBI_OK;

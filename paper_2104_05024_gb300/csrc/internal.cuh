@@ -16,6 +16,7 @@ namespace kfbi {
 
 constexpr int PATCH_MAX = 16;   // points of one local surface fit
 constexpr int MAX_RESTART = 64;
+#define KFBI_ARN_BLOCKS 608  // 4 x 152 SMs: row blocks of the single-launch Krylov reductions
 
 // error-word bits written by device code
 constexpr int DEVERR_GEOMETRY = 1;
@@ -212,6 +213,7 @@ struct SolveArgs {
   double beta = 1.0;
   double gamma = 0.0;
   double lambda = 0.0;
+  bool keep = true;               // the x inverse pass also writes the padded work grid
 };
 int box_solve64(kfbi_handle* h, const SolveArgs& a, double* work);
 int box_solve32(kfbi_handle* h, const SolveArgs& a, float* work);
@@ -248,6 +250,7 @@ int launch_padded_to_user(kfbi_handle* h, const double* padded, double* user);
 
 // GMRES vector kernels (ops.cu)
 int vec_dots(kfbi_handle* h, const double* V, int nvec, int ld, const double* w, double* out_dev);
+int launch_gram(kfbi_handle* h, const double* H, int k, const double* g, double* G, double* b, double* gg);
 int vec_update(kfbi_handle* h, double* w, const double* V, int nvec, int ld, const double* coef_dev, double sign);
 int vec_axpby(kfbi_handle* h, double* y, double a, const double* x, double b, int n);
 int vec_scale_by_norm(kfbi_handle* h, double* v, const double* w, const double* norm_dev, int n);

@@ -15,6 +15,9 @@ namespace kfbi {
 namespace {
 
 constexpr int RED_BLOCKS = 152;  // one partial sum per SM for the dot products
+// blocks of the Arnoldi kernels (one row per thread up to 155,648 rows); the
+// partial-sum buffer holds ARN_BLOCKS x (MAX_RESTART + 2) values
+constexpr int ARN_BLOCKS = KFBI_ARN_BLOCKS;
 
 __global__ void k_correction(Tables t, const double* __restrict__ x, double* __restrict__ corr,
                              const int* __restrict__ skip) {
@@ -389,16 +392,11 @@ __global__ void k_givens(double* s, int m, int j) { givens_column(s, m, j); }
 // ---------------------------------------------- fused Arnoldi step (CGS2)
 // One Krylov step after w = A v_j takes four launches: h = V^T w; w -= V h
 // with y = V^T w; w -= V y with ||w||^2, H(:, j) = h + y and the Givens
-// update; v_{j+1} = w / ||w||.  Each block owns a contiguous slice of rows;
+// update; v_{j+1} = w / ||w||.  Each thread owns a grid-stride set of rows;
 // the last block to finish (a ticket counter, reset by that block) reduces
 // the per-block partial sums in a fixed order, so results do not depend on
 // block scheduling.  skip (optional): a device flag; when set, the kernel
 // does nothing (an iteration enqueued ahead of the convergence test).
-__device__ __forceinline__ void arn_rows(int n, int& r0, int& r1) {
-  const int per = ((n + (int)gridDim.x - 1) / (int)gridDim.x + 31) & ~31;
-  r0 = min(n, (int)blockIdx.x * per);
-  r1 = min(n, r0 + per);
-}
 
 // true in every thread of the block that finishes last
 __device__ __forceinline__ bool arn_last_block(unsigned* counter) {
@@ -421,6 +419,28 @@ __device__ __forceinline__ void arn_reduce(const double* partial, int nb, int nv
   }
 }
 
+constexpr int ARN_CH = 8;  // basis vectors per register chunk
+
+// w_i -= sum_{k < nv} cs[k] V_k[i] over a grid-stride set of rows; each
+// chunk's loads are independent, so a thread has ARN_CH of them in flight
+__device__ __forceinline__ void arn_update(double* __restrict__ w, const double* __restrict__ V, int ld, int n, int nv,
+                                           const double* cs, double* sq) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int k0 = 0; k0 < nv; k0 += ARN_CH) {
+      double x[ARN_CH];
+#pragma unroll
+      for (int u = 0; u < ARN_CH; ++u) x[u] = k0 + u < nv ? V[(size_t)(k0 + u) * ld + i] : 0.0;
+#pragma unroll
+      for (int u = 0; u < ARN_CH; ++u)
+        if (k0 + u < nv) acc += cs[k0 + u] * x[u];
+    }
+    const double wi = w[i] - acc;
+    w[i] = wi;
+    if (sq != nullptr) *sq += wi * wi;
+  }
+}
+
 // [UPDATE: w -= sum_k coef[k] V_k;]  out[k] = V_k . w  (k < nv)
 template <bool UPDATE>
 __global__ void __launch_bounds__(256) k_arn_gs(double* __restrict__ w, const double* __restrict__ V, int ld, int n,
@@ -429,25 +449,35 @@ __global__ void __launch_bounds__(256) k_arn_gs(double* __restrict__ w, const do
                                                 const int* __restrict__ skip) {
   if (skip != nullptr && *skip) return;
   __shared__ double cs[MAX_RESTART + 2];
-  int r0, r1;
-  arn_rows(n, r0, r1);
+  __shared__ double red[8][MAX_RESTART + 2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (UPDATE) {
     for (int k = threadIdx.x; k < nv; k += blockDim.x) cs[k] = coef[k];
     __syncthreads();
-    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-      double acc = 0.0;
-      for (int k = 0; k < nv; ++k) acc += cs[k] * V[(size_t)k * ld + i];
-      w[i] -= acc;
-    }
-    __syncthreads();
+    arn_update(w, V, ld, n, nv, cs, nullptr);
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int k = warp; k < nv; k += nw) {
-    const double* v = V + (size_t)k * ld;
-    double acc = 0.0;
-    for (int i = r0 + lane; i < r1; i += 32) acc += v[i] * w[i];
-    acc = warp_sum(acc);
-    if (lane == 0) partial[(size_t)k * gridDim.x + blockIdx.x] = acc;
+  // each thread reads back only the rows it updated itself
+  for (int k0 = 0; k0 < nv; k0 += ARN_CH) {
+    double d[ARN_CH];
+#pragma unroll
+    for (int u = 0; u < ARN_CH; ++u) d[u] = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      const double wi = w[i];
+#pragma unroll
+      for (int u = 0; u < ARN_CH; ++u)
+        if (k0 + u < nv) d[u] += V[(size_t)(k0 + u) * ld + i] * wi;
+    }
+#pragma unroll
+    for (int u = 0; u < ARN_CH; ++u) {
+      const double t = warp_sum(d[u]);
+      if (lane == 0 && k0 + u < nv) red[warp][k0 + u] = t;
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q][k];
+    partial[(size_t)k * gridDim.x + blockIdx.x] = t;
   }
   if (!arn_last_block(counter)) return;
   arn_reduce(partial, gridDim.x, nv, out);
@@ -465,18 +495,10 @@ __global__ void __launch_bounds__(256) k_arn_close(double* __restrict__ w, const
   SmallLayout L{m};
   __shared__ double cs[MAX_RESTART + 2];
   __shared__ double ws[32];
-  int r0, r1;
-  arn_rows(n, r0, r1);
   for (int k = threadIdx.x; k < nv; k += blockDim.x) cs[k] = s[L.y() + k];
   __syncthreads();
   double sq = 0.0;
-  for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-    double acc = 0.0;
-    for (int k = 0; k < nv; ++k) acc += cs[k] * V[(size_t)k * ld + i];
-    const double wi = w[i] - acc;
-    w[i] = wi;
-    sq += wi * wi;
-  }
+  arn_update(w, V, ld, n, nv, cs, &sq);
   sq = warp_sum(sq);
   if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = sq;
   __syncthreads();
@@ -495,6 +517,63 @@ __global__ void __launch_bounds__(256) k_arn_close(double* __restrict__ w, const
     const int done = !(rel > tol) || !isfinite(rel);
     s[L.res() + 1] = done ? 1.0 : 0.0;
     *stop = done;
+    *counter = 0u;
+  }
+}
+
+// Normal equations of the density-history projection in one launch:
+// G[u][v] = h_u . h_v (u, v < K), b[u] = h_u . g, gg = g . g, with h_u the
+// rows of H (leading dimension ld).  Per-thread sums over a grid-stride set
+// of rows, warp and block reductions, and the last block's fixed-order sum
+// of the per-block partials.
+template <int K>
+__global__ void __launch_bounds__(256) k_gram(const double* __restrict__ H, int ld, const double* __restrict__ g, int n,
+                                              double* __restrict__ partial, unsigned* __restrict__ counter,
+                                              double* __restrict__ G, double* __restrict__ b, double* __restrict__ gg) {
+  constexpr int NP = K * (K + 1) / 2 + K + 1;
+  double acc[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) acc[p] = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double x[K + 1];
+#pragma unroll
+    for (int u = 0; u < K; ++u) x[u] = H[(size_t)u * ld + i];
+    x[K] = g[i];
+    int p = 0;
+#pragma unroll
+    for (int u = 0; u < K; ++u)
+#pragma unroll
+      for (int v = u; v <= K; ++v) acc[p++] += x[u] * x[v];
+    acc[p] += x[K] * x[K];
+  }
+  __shared__ double red[8][NP];
+  __shared__ double fin[NP];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const double t = warp_sum(acc[p]);
+    if (lane == 0) red[warp][p] = t;
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < NP; p += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][p];
+    partial[(size_t)p * gridDim.x + blockIdx.x] = t;
+  }
+  if (!arn_last_block(counter)) return;
+  arn_reduce(partial, gridDim.x, NP, fin);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int p = 0;
+    for (int u = 0; u < K; ++u) {
+      for (int v = u; v < K; ++v) {
+        G[u * K + v] = fin[p];
+        G[v * K + u] = fin[p];
+        ++p;
+      }
+      b[u] = fin[p++];
+    }
+    *gg = fin[p];
     *counter = 0u;
   }
 }
@@ -770,6 +849,32 @@ int launch_padded_to_user(kfbi_handle* h, const double* padded, double* user) {
   return KFBI_OK;
 }
 
+// G = H H^T (k x k), b = H g, gg = g . g for the k <= KFBI_HISTORY stored
+// right-hand sides H (rows of length M), in one launch
+int launch_gram(kfbi_handle* h, const double* H, int k, const double* g, double* G, double* b, double* gg) {
+  const int n = h->t.M;
+  int nb = (n + 255) / 256;
+  if (nb > RED_BLOCKS) nb = RED_BLOCKS;
+  double* pt = h->w.partial;
+  unsigned* c = h->w.counter;
+  switch (k) {
+    case 0: k_gram<0><<<nb, 256, 0, h->stream>>>(H, n, g, n, pt, c, G, b, gg); break;
+    case 1: k_gram<1><<<nb, 256, 0, h->stream>>>(H, n, g, n, pt, c, G, b, gg); break;
+    case 2: k_gram<2><<<nb, 256, 0, h->stream>>>(H, n, g, n, pt, c, G, b, gg); break;
+    case 3: k_gram<3><<<nb, 256, 0, h->stream>>>(H, n, g, n, pt, c, G, b, gg); break;
+    case 4: k_gram<4><<<nb, 256, 0, h->stream>>>(H, n, g, n, pt, c, G, b, gg); break;
+    case 5: k_gram<5><<<nb, 256, 0, h->stream>>>(H, n, g, n, pt, c, G, b, gg); break;
+    case 6: k_gram<6><<<nb, 256, 0, h->stream>>>(H, n, g, n, pt, c, G, b, gg); break;
+    case 7: k_gram<7><<<nb, 256, 0, h->stream>>>(H, n, g, n, pt, c, G, b, gg); break;
+    case 8: k_gram<8><<<nb, 256, 0, h->stream>>>(H, n, g, n, pt, c, G, b, gg); break;
+    default:
+      set_error("history length %d above %d", k, KFBI_HISTORY);
+      return KFBI_ERR_ARG;
+  }
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
 int vec_dots(kfbi_handle* h, const double* V, int nvec, int ld, const double* w, double* out_dev) {
   const int n = h->t.M;
   int nb = (n + 255) / 256;
@@ -823,7 +928,7 @@ int arnoldi_solve(kfbi_handle* h, double* small, int k, int m) {
 int arnoldi_step(kfbi_handle* h, double* V, int ld, double* wv, int j, int m, double gnorm, double tol) {
   const int n = h->t.M;
   int nb = (n + 255) / 256;
-  if (nb > RED_BLOCKS) nb = RED_BLOCKS;
+  if (nb > ARN_BLOCKS) nb = ARN_BLOCKS;
   SmallLayout L{m};
   double* s = h->w.small;
   const int nv = j + 1;
