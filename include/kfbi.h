@@ -66,7 +66,7 @@ extern "C" {
 #define KFBI_WARM_PREVIOUS 0   /* the previous solve's density                */
 #define KFBI_WARM_PROJECTION 1 /* least-squares combination of the last
                                   KFBI_HISTORY densities, chosen by their known
-                                  right-hand sides, plus one step of the simple
+                                  images A psi_s, plus one step of the simple
                                   iteration (Section 4)                        */
 #define KFBI_HISTORY 8
 
@@ -301,15 +301,17 @@ int kfbi_get_densities(kfbi_handle* h, double* psi_dev, double* psi_prev_dev, do
 int kfbi_set_densities(kfbi_handle* h, const double* psi_dev, const double* psi_prev_dev, const double* g_dev,
                        int n_solves);
 /* The density history of the projection warm start: KFBI_HISTORY slots of
- * M doubles each (psi and its right-hand side g; the density of solve s sits
- * in slot s mod KFBI_HISTORY) and the number of solves it stands for.  get
+ * M doubles each (psi and its image A psi: with the float32 forms g - r, r the
+ * solve's final float64-accurate residual; with float64 the right-hand side
+ * g, equal to A psi to the tolerance; the density of solve s sits in slot
+ * s mod KFBI_HISTORY) and the number of solves it stands for.  get
  * copies out (device buffers of KFBI_HISTORY*M doubles, n_solves on the
  * host); set restores them (checkpoint / resume).                          */
 int kfbi_get_history(kfbi_handle* h, double* psi_hist_dev, double* g_hist_dev, int* n_solves);
 int kfbi_set_history(kfbi_handle* h, const double* psi_hist_dev, const double* g_hist_dev, int n_solves);
 /* After a projection (or learned) step: the projected density psi_F and its
  * residual r_F = g - A psi_F (known without an operator application from the
- * history's right-hand sides), M doubles each, device.                      */
+ * history's images), M doubles each, device.                                */
 int kfbi_get_projection(kfbi_handle* h, double* psiF_dev, double* rF_dev);
 
 /* One pass of the box solver on the handle's padded work grid, for timing

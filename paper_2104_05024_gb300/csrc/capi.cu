@@ -334,8 +334,14 @@ int richardson(kfbi_handle* h, int prec, double lambda, const double* g, double*
 // fallback (optional): an alternative initial guess whose squared residual
 // norm is in the device slot fallback_res2; it replaces psi when psi's first
 // residual is larger.  gnorm_known (>= 0): ||g|| already read by the caller.
+// rF (optional, with fallback): the fallback's residual vector g - A fallback
+// to float64 accuracy.  psi's first residual is then rF - A (psi - fallback)
+// with float32 transforms: the difference is small (of the order of rF), so
+// the float32 operator's relative error of ~1e-6 enters at ~1e-6 ||rF||, far
+// below the tolerance, and the first refined solve is saved.
 int gmres_ir(kfbi_handle* h, double lambda, const double* g, double* psi, kfbi_stats* st,
-             const double* fallback = nullptr, const double* fallback_res2 = nullptr, double gnorm_known = -1.0) {
+             const double* fallback = nullptr, const double* fallback_res2 = nullptr, double gnorm_known = -1.0,
+             const double* rF = nullptr) {
   const int M = h->t.M;
   double* r = h->w.r2;
   double* delta = h->w.tmp2;
@@ -347,10 +353,31 @@ int gmres_ir(kfbi_handle* h, double lambda, const double* g, double* psi, kfbi_s
   if (gnorm == 0.0) gnorm = 1.0;
   int inner_total = 0, outer = 0;
   double rel = 0.0;
+  bool approx = false;  // rn came from the residual by difference
   for (;;) {
-    if ((rc = apply_A_acc(h, lambda, psi, r, -1.0, g))) return rc;
     double rn, fallback_res = 0.0;
-    if (outer == 0 && fallback != nullptr) {
+    if (outer == 0 && fallback != nullptr && rF != nullptr) {
+      approx = true;
+      // residual by difference (no refined solve); the residual judges the
+      // guess, and the fallback's residual is rF itself
+      double rn2, f2;
+      if ((rc = vec_copy(h, delta, psi, M))) return rc;
+      if ((rc = vec_axpby(h, delta, -1.0, fallback, 1.0, M))) return rc;
+      if ((rc = apply_A(h, KFBI_MIXED, lambda, delta, r, -1.0, rF))) return rc;
+      if ((rc = vec_dots(h, r, 1, M, r, slot))) return rc;
+      if ((rc = read_two(h, slot, fallback_res2, &rn2, &f2))) return rc;
+      rn = std::sqrt(rn2);
+      fallback_res = std::sqrt(f2);
+      if (rn > fallback_res) {
+        if ((rc = vec_copy(h, psi, fallback, M))) return rc;
+        if ((rc = vec_copy(h, r, rF, M))) return rc;
+        rn = fallback_res;
+        st->warmstart = 0;
+      }
+      fallback = nullptr;
+    } else if ((rc = apply_A_acc(h, lambda, psi, r, -1.0, g))) {
+      return rc;
+    } else if (outer == 0 && fallback != nullptr) {
       double rn2, f2;
       if ((rc = vec_dots(h, r, 1, M, r, slot))) return rc;
       if ((rc = read_two(h, slot, fallback_res2, &rn2, &f2))) return rc;
@@ -373,7 +400,15 @@ int gmres_ir(kfbi_handle* h, double lambda, const double* g, double* psi, kfbi_s
       set_error("non-finite residual in GMRES-IR");
       return KFBI_ERR_NAN;
     }
-    if (rel <= tol || inner_total >= h->opts.max_iter || outer >= 20) break;
+    if (rel <= tol || inner_total >= h->opts.max_iter || outer >= 20) {
+      // the solver stops on a float64-accurate residual only (it also
+      // leaves v_B(psi) in u64 for the caller)
+      if (!approx) break;
+      approx = false;
+      rF = nullptr;
+      continue;
+    }
+    approx = false;
     // inner tolerance relative to ||r||: as far as the float32 operator can
     // go (six digits), or just what the target needs
     double tin = std::max(1e-6, 0.3 * tol * gnorm / rn);
@@ -393,9 +428,10 @@ int gmres_ir(kfbi_handle* h, double lambda, const double* g, double* psi, kfbi_s
 }
 
 int solve_bie(kfbi_handle* h, int prec, double lambda, const double* g, double* psi, kfbi_stats* st,
-              const double* fallback = nullptr, const double* fallback_res2 = nullptr, double gnorm_known = -1.0) {
+              const double* fallback = nullptr, const double* fallback_res2 = nullptr, double gnorm_known = -1.0,
+              const double* rF = nullptr) {
   if (h->opts.solver == KFBI_RICHARDSON) return richardson(h, prec, lambda, g, psi, st);
-  if (prec != KFBI_FP64) return gmres_ir(h, lambda, g, psi, st, fallback, fallback_res2, gnorm_known);
+  if (prec != KFBI_FP64) return gmres_ir(h, lambda, g, psi, st, fallback, fallback_res2, gnorm_known, rF);
   return gmres(h, prec, lambda, g, psi, st, h->opts.tol, h->opts.max_iter, false, fallback, fallback_res2,
                gnorm_known);
 }
@@ -474,12 +510,15 @@ int project_history(kfbi_handle* h, const double* g, double* gnorm, const double
   return KFBI_OK;
 }
 
-int push_history(kfbi_handle* h, const double* psi, const double* g) {
+// stores psi and its image A psi: g - r with r = g - A psi the solver's
+// final float64-accurate residual when given, else g (A psi to the tolerance)
+int push_history(kfbi_handle* h, const double* psi, const double* g, const double* r = nullptr) {
   const int M = h->t.M;
   const size_t slot = (size_t)(h->hist_count % KFBI_HISTORY) * M;
   int rc;
   if ((rc = vec_copy(h, h->w.hist_psi + slot, psi, M))) return rc;
   if ((rc = vec_copy(h, h->w.hist_g + slot, g, M))) return rc;
+  if (r != nullptr && (rc = vec_axpby(h, h->w.hist_g + slot, -1.0, r, 1.0, M))) return rc;
   ++h->hist_count;
   return KFBI_OK;
 }
@@ -906,11 +945,15 @@ static int bidomain_impl(kfbi_handle* h, const kfbi_fhn* p, const double* istim,
       }
       fallback = h->w.psiF;
     }
-    const int src = solve_bie(h, prec, lam, h->w.g, h->w.psi_prev, &st, fallback, fallback_res2, gnorm);
+    // mixed forms: the history holds exact images A psi_s, so r_F is the
+    // float64-accurate residual of psi_F
+    const bool ir = prec != KFBI_FP64 && h->opts.solver == KFBI_GMRES;
+    const int src = solve_bie(h, prec, lam, h->w.g, h->w.psi_prev, &st, fallback, fallback_res2, gnorm,
+                              ir ? h->w.rF : nullptr);
     if (src != KFBI_OK && src != KFBI_ERR_NOT_CONVERGED) return src;
     if ((rc = vec_copy(h, h->w.psi_prev2, h->w.psi_save, h->t.M))) return rc;
     if ((rc = vec_copy(h, h->w.g_prev, h->w.g, h->t.M))) return rc;
-    if ((rc = push_history(h, h->w.psi_prev, h->w.g))) return rc;
+    if ((rc = push_history(h, h->w.psi_prev, h->w.g, ir ? h->w.r2 : nullptr))) return rc;
     ++h->n_hist;
     if (src == KFBI_ERR_NOT_CONVERGED) final_rc = src;
     // V <- 2 (v_V + v_B(psi)) - V

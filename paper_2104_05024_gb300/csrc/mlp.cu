@@ -246,6 +246,94 @@ __global__ void k_predict(const double* __restrict__ psiF, const double* __restr
   }
 }
 
+// Inference of the whole network in one persistent kernel (the training
+// path keeps the layer-by-layer kernels, whose activations the backward pass
+// needs).  The bfloat16 weights are staged in shared memory once per block;
+// per tile of 64 rows each layer runs on the tensor cores from the tile's
+// activations in shared memory, the float32 products go to a shared staging
+// tile, and the epilogue adds the bias, applies SiLU and rounds to bfloat16
+// in place; the output layer is one warp dot product per row.  Same
+// operations and summation order per element as the layer-by-layer path.
+constexpr int IR = 64;                      // rows per tile
+constexpr int LDW = WID + 8, LDX = KIN + 8;  // padded bf16 leading dimensions
+constexpr int LDS = WID + 4;                 // padded float32 staging
+constexpr size_t INFER_SMEM = (size_t)3 * WID * LDW * 2 + (size_t)WID * LDX * 2 + (size_t)IR * LDW * 2 +
+                              (size_t)IR * LDX * 2 + (size_t)IR * LDS * 4 + (size_t)4 * WID * 4 + (size_t)WID * 4;
+
+__global__ void __launch_bounds__(256, 1) k_mlp_infer(const bf16* __restrict__ X, int Bp, const bf16* __restrict__ W0,
+                                                      const bf16* __restrict__ W1, const bf16* __restrict__ W2,
+                                                      const bf16* __restrict__ W3, const bf16* __restrict__ w4,
+                                                      const float* __restrict__ p, Offsets off, float* __restrict__ o) {
+  using namespace nvcuda;
+  extern __shared__ __align__(128) unsigned char sm_infer[];
+  bf16* sW = reinterpret_cast<bf16*>(sm_infer);  // 3 x [WID][LDW], B[n][k]
+  bf16* sW0 = sW + 3 * WID * LDW;                 // [WID][LDX]
+  bf16* sA = sW0 + WID * LDX;                     // [IR][LDW]
+  bf16* sX = sA + IR * LDW;                       // [IR][LDX]
+  float* sZ = reinterpret_cast<float*>(sX + IR * LDX);  // [IR][LDS]
+  float* sB = sZ + IR * LDS;                      // [4][WID]
+  float* sw4 = sB + 4 * WID;                      // [WID]
+  const int tid = threadIdx.x;
+  const bf16* Wg[3] = {W1, W2, W3};
+  for (int l = 0; l < 3; ++l)
+    for (int i = tid; i < WID * WID / 8; i += blockDim.x) {
+      const int n = i / (WID / 8), q = i % (WID / 8);
+      *reinterpret_cast<uint4*>(sW + (size_t)l * WID * LDW + n * LDW + 8 * q) =
+          *reinterpret_cast<const uint4*>(Wg[l] + (size_t)n * WID + 8 * q);
+    }
+  for (int i = tid; i < WID * KIN / 8; i += blockDim.x) {
+    const int n = i / (KIN / 8), q = i % (KIN / 8);
+    *reinterpret_cast<uint4*>(sW0 + n * LDX + 8 * q) = *reinterpret_cast<const uint4*>(W0 + (size_t)n * KIN + 8 * q);
+  }
+  for (int i = tid; i < 4 * WID; i += blockDim.x) sB[i] = p[off.b[i / WID] + i % WID];
+  for (int i = tid; i < WID; i += blockDim.x) sw4[i] = __bfloat162float(w4[i]);
+  const float b4 = p[off.b[4]];
+  const int warp = tid >> 5, lane = tid & 31;
+  const int rb = warp & 3, cb = (warp >> 2) * 4;  // 16-row block, four 16-column blocks
+  for (int tile = blockIdx.x; tile < Bp / IR; tile += gridDim.x) {
+    for (int i = tid; i < IR * KIN / 8; i += blockDim.x) {
+      const int r = i / (KIN / 8), q = i % (KIN / 8);
+      *reinterpret_cast<uint4*>(sX + r * LDX + 8 * q) =
+          *reinterpret_cast<const uint4*>(X + ((size_t)tile * IR + r) * KIN + 8 * q);
+    }
+    __syncthreads();
+    for (int l = 0; l < 4; ++l) {
+      const bf16* Ain = l == 0 ? sX : sA;
+      const int lda = l == 0 ? LDX : LDW, ldb = lda, K = l == 0 ? KIN : WID;
+      const bf16* Bw = l == 0 ? sW0 : sW + (size_t)(l - 1) * WID * LDW;
+      wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) wmma::fill_fragment(acc[j], 0.0f);
+      for (int k0 = 0; k0 < K; k0 += 16) {
+        wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::row_major> fa;
+        wmma::load_matrix_sync(fa, Ain + rb * 16 * lda + k0, lda);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::col_major> fb;
+          wmma::load_matrix_sync(fb, Bw + (cb + j) * 16 * ldb + k0, ldb);
+          wmma::mma_sync(acc[j], fa, fb, acc[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        wmma::store_matrix_sync(sZ + rb * 16 * LDS + (cb + j) * 16, acc[j], LDS, wmma::mem_row_major);
+      __syncthreads();  // every warp has read its inputs and written its products
+      for (int i = tid; i < IR * WID; i += blockDim.x) {
+        const int r = i / WID, c = i % WID;
+        sA[r * LDW + c] = __float2bfloat16_rn(silu_f(sZ[r * LDS + c] + sB[l * WID + c]));
+      }
+      __syncthreads();
+    }
+    for (int r = warp; r < IR; r += (int)(blockDim.x >> 5)) {
+      float acc = 0.0f;
+      for (int j = lane; j < WID; j += 32) acc += __bfloat162float(sA[r * LDW + j]) * sw4[j];
+      for (int sft = 16; sft > 0; sft >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, sft);
+      if (lane == 0) o[(size_t)tile * IR + r] = acc + b4;
+    }
+    __syncthreads();  // the next tile overwrites sX and sA
+  }
+}
+
 }  // namespace
 }  // namespace kfbi
 
@@ -293,6 +381,28 @@ int mlp_forward_rows(kfbi_mlp* m, int Bp) {
   }
   k_out<<<blocks((size_t)Bp * 32, 256), 256, 0, st>>>(m->A[3], m->w4, m->p + m->off.b[4], m->o, Bp);
   KFBI_CHECK_LAUNCH_N(9);
+  return KFBI_OK;
+}
+
+// inference over rows already placed in m->X (Bp a multiple of 64): m->o
+int mlp_infer_rows(kfbi_mlp* m, int Bp) {
+  static bool opted = false;
+  if (!opted) {
+    if (cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INFER_SMEM) !=
+        cudaSuccess) {
+      set_error("cudaFuncSetAttribute failed for the inference kernel");
+      return KFBI_ERR_CUDA;
+    }
+    opted = true;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles = Bp / IR;
+  const int grid = tiles < sms ? tiles : sms;
+  k_mlp_infer<<<grid, 256, INFER_SMEM, m->stream>>>(m->X, Bp, m->W0, m->W[0], m->W[1], m->W[2], m->w4, m->p, m->off,
+                                                    m->o);
+  KFBI_CHECK_LAUNCH();
   return KFBI_OK;
 }
 
@@ -367,7 +477,7 @@ int mlp_warmstart(kfbi_mlp* m, cudaStream_t st, const double* psiF, const double
   const int Bp = (M + TILE - 1) / TILE * TILE;
   k_feat_proj<<<blocks(Bp, 128), 128, 0, st>>>(psiF, rF, g, sq, nodes, normals, M, Bp, m->norm, m->X);
   KFBI_CHECK_LAUNCH();
-  int rc = mlp_forward_rows(m, Bp);
+  int rc = mlp_infer_rows(m, Bp);
   if (rc == KFBI_OK) {
     k_predict<<<blocks(M, 256), 256, 0, st>>>(psiF, rF, sq, two_gamma, m->o, m->norm, out, M);
     KFBI_CHECK_LAUNCH();
@@ -452,7 +562,7 @@ int kfbi_mlp_forward(kfbi_mlp* m, const float* F_dev, int B, float* o_dev) {
   }
   int Bp, rc;
   if ((rc = mlp_prepare_raw(m, F_dev, B, &Bp))) return rc;
-  if ((rc = mlp_forward_rows(m, Bp))) return rc;
+  if ((rc = mlp_infer_rows(m, Bp))) return rc;
   KFBI_CUDA(cudaMemcpyAsync(o_dev, m->o, sizeof(float) * B, cudaMemcpyDeviceToDevice, m->stream));
   return KFBI_OK;
 }
