@@ -609,7 +609,9 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed Strang steps (default: 200, the length of the config-2 run, for the strang "
+                         "workload; 40 for the others)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="kfbi", choices=["kfbi", "reference"])
     ap.add_argument("--precision", default="learned", choices=["fp64", "mixed", "projection", "learned"],
@@ -625,6 +627,8 @@ def main():
                     choices=["strang", "star-sweep", "shell-large", "heldout", "stiff", "stimulus"],
                     help="strang: the timed benchmark; the others print one result line each")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 200 if args.workload == "strang" and args.impl == "kfbi" else 40
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "star-sweep":
