@@ -224,7 +224,7 @@ def run_gpu(args):
                 "peak_source": kind,
                 # DRAM read + write per launch of this kernel at 256^3 from one
                 # ncu capture (cold cache); none for other sizes
-                "traffic": 73.0e6 if N == 256 else None,
+                "traffic": 72.8e6 if N == 256 else None,
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, cold cache)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["pass_ms"] = {k: round(v, 4) for k, v in pass_ms.items()}

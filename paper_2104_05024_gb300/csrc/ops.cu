@@ -19,13 +19,15 @@ constexpr int RED_BLOCKS = 152;  // one partial sum per SM for the dot products
 // partial-sum buffer holds ARN_BLOCKS x (MAX_RESTART + 2) values
 constexpr int ARN_BLOCKS = KFBI_ARN_BLOCKS;
 
+// Eight lanes per irregular node, one per crossing arm (at most six): the
+// arms' gathers run side by side and three shuffles add them up.
 __global__ void k_correction(Tables t, const double* __restrict__ x, double* __restrict__ corr,
                              const int* __restrict__ skip) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= t.n_irr || (skip != nullptr && *skip)) return;
-  const int na = t.irr_narm[i];
+  if (skip != nullptr && *skip) return;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (int)(gid >> 3), a = (int)(gid & 7);
   double acc = 0.0;
-  for (int a = 0; a < na; ++a) {
+  if (i < t.n_irr && a < t.irr_narm[i]) {
     const int code = t.irr_arm[(size_t)i * 6 + a];
     const int c = code >> 1;
     const double* w = (code & 1) ? t.c_whi : t.c_wlo;
@@ -33,7 +35,10 @@ __global__ void k_correction(Tables t, const double* __restrict__ x, double* __r
     const size_t o = (size_t)c * PATCH_MAX;
     for (int q = 0; q < K; ++q) acc += w[o + q] * x[t.c_pid[o + q]];
   }
-  corr[i] = acc;
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+  if (a == 0 && i < t.n_irr) corr[i] = acc;
 }
 
 // x = [psi; m] with m_i = sum_j gcol[(i - j) mod M] psi_j
@@ -421,6 +426,35 @@ __device__ __forceinline__ void arn_reduce(const double* partial, int nb, int nv
 
 constexpr int ARN_CH = 8;  // basis vectors per register chunk
 
+// Sums of eight per-lane values over the warp with nine float64 additions
+// per lane instead of forty (float64 issue is scarce on this part): each
+// halving step keeps half of the values and adds the partner lane's copy of
+// them, so that after offsets 16, 8 and 4 lane l holds vector (l >> 2) & 7
+// summed over the lanes that differ in bits 2-4; offsets 2 and 1 finish the
+// sum.  The lanes with (l & 3) == 0 return the totals.
+__device__ __forceinline__ double warp_sum8(double (&v)[ARN_CH]) {
+  const int lane = threadIdx.x & 31;
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const double send = b4 ? v[i] : v[i + 4], keep = b4 ? v[i + 4] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const double send = b3 ? v[i] : v[i + 2], keep = b3 ? v[i + 2] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  {
+    const double send = b2 ? v[0] : v[1], keep = b2 ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  double t = v[0];
+  t += __shfl_xor_sync(0xffffffffu, t, 2);
+  t += __shfl_xor_sync(0xffffffffu, t, 1);
+  return t;
+}
+
 // w_i -= sum_{k < nv} cs[k] V_k[i] over a grid-stride set of rows; each
 // chunk's loads are independent, so a thread has ARN_CH of them in flight
 __device__ __forceinline__ void arn_update(double* __restrict__ w, const double* __restrict__ V, int ld, int n, int nv,
@@ -467,11 +501,9 @@ __global__ void __launch_bounds__(256) k_arn_gs(double* __restrict__ w, const do
       for (int u = 0; u < ARN_CH; ++u)
         if (k0 + u < nv) d[u] += V[(size_t)(k0 + u) * ld + i] * wi;
     }
-#pragma unroll
-    for (int u = 0; u < ARN_CH; ++u) {
-      const double t = warp_sum(d[u]);
-      if (lane == 0 && k0 + u < nv) red[warp][k0 + u] = t;
-    }
+    const double t = warp_sum8(d);
+    const int u = lane >> 2;
+    if ((lane & 3) == 0 && k0 + u < nv) red[warp][k0 + u] = t;
   }
   __syncthreads();
   for (int k = threadIdx.x; k < nv; k += blockDim.x) {
@@ -733,7 +765,8 @@ int small_y(int m) { return SmallLayout{m}.y(); }
 
 int launch_correction(kfbi_handle* h, const double* x, double* corr) {
   if (h->t.n_irr == 0) return KFBI_OK;
-  k_correction<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->t, x, corr, h->skip);
+  const int64_t threads = (int64_t)h->t.n_irr * 8;
+  k_correction<<<(unsigned)((threads + 255) / 256), 256, 0, h->stream>>>(h->t, x, corr, h->skip);
   KFBI_CHECK_LAUNCH();
   return KFBI_OK;
 }
