@@ -19,15 +19,13 @@ constexpr int RED_BLOCKS = 152;  // one partial sum per SM for the dot products
 // partial-sum buffer holds ARN_BLOCKS x (MAX_RESTART + 2) values
 constexpr int ARN_BLOCKS = KFBI_ARN_BLOCKS;
 
-// Eight lanes per irregular node, one per crossing arm (at most six): the
-// arms' gathers run side by side and three shuffles add them up.
 __global__ void k_correction(Tables t, const double* __restrict__ x, double* __restrict__ corr,
                              const int* __restrict__ skip) {
-  if (skip != nullptr && *skip) return;
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = (int)(gid >> 3), a = (int)(gid & 7);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.n_irr || (skip != nullptr && *skip)) return;
+  const int na = t.irr_narm[i];
   double acc = 0.0;
-  if (i < t.n_irr && a < t.irr_narm[i]) {
+  for (int a = 0; a < na; ++a) {
     const int code = t.irr_arm[(size_t)i * 6 + a];
     const int c = code >> 1;
     const double* w = (code & 1) ? t.c_whi : t.c_wlo;
@@ -35,10 +33,7 @@ __global__ void k_correction(Tables t, const double* __restrict__ x, double* __r
     const size_t o = (size_t)c * PATCH_MAX;
     for (int q = 0; q < K; ++q) acc += w[o + q] * x[t.c_pid[o + q]];
   }
-  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-  if (a == 0 && i < t.n_irr) corr[i] = acc;
+  corr[i] = acc;
 }
 
 // x = [psi; m] with m_i = sum_j gcol[(i - j) mod M] psi_j
@@ -765,8 +760,7 @@ int small_y(int m) { return SmallLayout{m}.y(); }
 
 int launch_correction(kfbi_handle* h, const double* x, double* corr) {
   if (h->t.n_irr == 0) return KFBI_OK;
-  const int64_t threads = (int64_t)h->t.n_irr * 8;
-  k_correction<<<(unsigned)((threads + 255) / 256), 256, 0, h->stream>>>(h->t, x, corr, h->skip);
+  k_correction<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->t, x, corr, h->skip);
   KFBI_CHECK_LAUNCH();
   return KFBI_OK;
 }
