@@ -288,6 +288,8 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if precision == K.FP64 else "f32+f64", "data": "synthetic",
         "config": {"workload": f"config 2: FHN bidomain, prolate shell, {N}^3 grid, dt 0.05, GMRES tol 1e-8",
+                   "timed_steps": f"steps {args.warmup + 1}..{args.warmup + args.steps} of the run "
+                                  "(iterations per step fall as the projection history fills)",
                    "N": N, "M": geom.M, "precision": args.precision, "parallelism": "replicas" if world > 1 else "1gpu",
                    "l2": "inputs larger than L2 (V and w: %.0f MB each)" % (V.numel() * 8 / 1e6),
                    "setup_s": round(setup_s, 2), "n_irregular": h.info["n_irregular"],
