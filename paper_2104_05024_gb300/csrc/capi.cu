@@ -2,8 +2,8 @@
 // the boundary integral operator A psi (Algorithm 1), GMRES / simple
 // iteration on A psi = g (Section 4), the Neumann solve and the Strang step
 // (Section 3).  All arithmetic runs in the kernels of dst.cu, ops.cu and
-// setup.cu; the host only sequences launches and reads one residual per
-// Krylov iteration.
+// setup.cu; the host only sequences launches and reads one residual estimate
+// per Krylov iteration, one iteration behind the device.
 #include <cuda_runtime.h>
 
 #include <algorithm>
