@@ -194,7 +194,7 @@ def run_gpu(args):
     reps = 20
     pass_ms = {}
     prec_pass = K.FP64 if precision == K.FP64 else K.MIXED
-    lam = C.helmholtz_lambda(cfg)
+    lam = h.info["lambda"]
     for p in (0, 1, 2, 3):
         for _ in range(3):
             h.transform_pass(p, lam, prec_pass)
@@ -576,9 +576,8 @@ def cpu_baseline(N, steps=1):
     from kfbi_workloads import configs as C
     from oracle.bidomain import Bidomain
     geom, grid, cfg, V0, w0 = workload(N, 0)
-    lam = C.helmholtz_lambda(cfg)
     t0 = time.time()
-    bd = Bidomain(geom, grid, cfg, C.FHN_CONFIG, lam)
+    bd = Bidomain(geom, grid, cfg, C.FHN_CONFIG)
     setup = time.time() - t0
     V, w = V0.copy(), w0.copy()
     t0 = time.time()

@@ -142,6 +142,9 @@ typedef struct {
   int n_crossings;     /* interface / grid-line crossings       */
   int n_inside;        /* grid nodes inside Omega               */
   size_t device_bytes; /* workspace and tables held on the GPU  */
+  double lambda;       /* lambda = (2 / dt)(1/sigma_i + 1/sigma_e) of the
+                          implicit-midpoint V problem with Cm beta = 1
+                          (bidomain_step scales it by the kfbi_fhn's Cm beta) */
 } kfbi_info;
 
 typedef struct kfbi_handle kfbi_handle;

@@ -70,14 +70,6 @@ class StrangConfig:
     tol: float = 1e-10
 
 
-def helmholtz_lambda(cfg: StrangConfig, fhn: FHN = FHN_CONFIG) -> float:
-    """lambda of the decoupled transmembrane problem  Lap V - lambda V = -lambda V^n
-    for the implicit-midpoint half step: kappa = Cm beta / (dt/2), and
-    lambda = kappa (1/sigma_i + 1/sigma_e)."""
-    kappa = fhn.Cm * fhn.beta / (cfg.dt / 2.0)
-    return kappa * (1.0 / cfg.sigma_i + 1.0 / cfg.sigma_e)
-
-
 def ball_stimulus(grid: Grid, center, radius: float) -> np.ndarray:
     """V = 1 strictly inside the ball |x - center| < radius, else 0."""
     X = grid.coords()
@@ -147,6 +139,25 @@ def midwall_centers(seeds):
         st = math.sqrt(max(0.0, 1.0 - ct * ct))
         out.append((0.8 * st * math.cos(ph), 0.5 * st * math.sin(ph), 0.5 * ct))
     return out
+
+
+def mlp_init_params(seed: int = 0) -> np.ndarray:
+    """Seeded initial parameters of the warm-start network (9 inputs, 4 hidden
+    layers of width 128, 1 output), packed W0[128][9], b0, W1[128][128], b1,
+    ..., W4[1][128], b4 as float32: hidden weights uniform in
+    +-sqrt(6 / fan_in), biases and the output layer zero."""
+    rng = np.random.default_rng(seed)
+    dims = [9, 128, 128, 128, 128, 1]
+    out = []
+    for l in range(len(dims) - 1):
+        fan_in, fan_out = dims[l], dims[l + 1]
+        if fan_out > 1:
+            lim = np.sqrt(6.0 / fan_in)
+            out.append(rng.uniform(-lim, lim, fan_out * fan_in))
+        else:
+            out.append(np.zeros(fan_out * fan_in))
+        out.append(np.zeros(fan_out))
+    return np.concatenate(out).astype(np.float32)
 
 
 TRAIN_SEEDS = tuple(range(8))

@@ -19,5 +19,9 @@ Modules and the passages they follow:
               4, 5.1-5.4, Algorithm 1)
   krylov    - simple (Richardson) iteration and GMRES (Section 4)
   reaction  - FitzHugh-Nagumo forward/backward Euler half steps (Sections 3, 7)
-  bidomain  - the Strang step with the implicit midpoint diffusion (Section 3)
+  bidomain  - the Strang step with the implicit midpoint diffusion and the
+              lambda of its decoupled V problem (Section 3, Eq. pde1)
+  mlp       - the point-wise network of the learned warm start
+  warmstart - history projection, features, prediction and training
+              targets of the warm starts (not in the paper)
 """

@@ -36,6 +36,21 @@ from . import reaction
 from .kfbi import KFBI
 
 
+def helmholtz_lambda(sigma_i, sigma_e, dt, Cm, beta):
+    """lambda of the decoupled transmembrane problem of the implicit-midpoint
+    half step (Section 3): the backward-Euler step over dt/2 gives
+    kappa = Cm beta / (dt/2) in Eq. pde1, and dividing its rows by the
+    conductivities and subtracting gives Lap V - lambda V = -lambda V^n with
+    lambda = kappa (1/sigma_i + 1/sigma_e)."""
+    kappa = Cm * beta / (dt / 2.0)
+    return kappa * (1.0 / sigma_i + 1.0 / sigma_e)
+
+
+def lam_of(cfg, fhn):
+    """helmholtz_lambda of a workload (conductivities and dt) and membrane."""
+    return helmholtz_lambda(cfg.sigma_i, cfg.sigma_e, cfg.dt, fhn.Cm, fhn.beta)
+
+
 def extracellular(V, inside, sigma_i, sigma_e):
     mean = V[inside].mean()
     return sigma_i * (mean - V) / (sigma_i + sigma_e)
@@ -48,9 +63,10 @@ def extracellular_S(V, S, inside, sigma_i, sigma_e):
 
 
 class Bidomain:
-    def __init__(self, geom, grid, cfg, fhn, lam, istim=None):
+    def __init__(self, geom, grid, cfg, fhn, istim=None):
         self.k = KFBI(geom, grid)
-        self.cfg, self.fhn, self.lam = cfg, fhn, lam
+        self.cfg, self.fhn = cfg, fhn
+        self.lam = helmholtz_lambda(cfg.sigma_i, cfg.sigma_e, cfg.dt, fhn.Cm, fhn.beta)
         self.psi_prev = np.zeros(geom.M)
         self.gN = np.zeros(geom.M)
         self.istim = istim

@@ -1,20 +1,21 @@
 """Point-wise MLP of the learned density warm start (oracle).
 
-Test infrastructure only.  Per interface node the network maps the features
-    (psi^{n-1}, psi^{n-2}, g^n, x, y, z, n_x, n_y, n_z)
-(normalised by fixed means and standard deviations) through 4 hidden layers
-of width 128 with SiLU to one output o, and predicts
-    psi^n = psi^{n-1} + s_out * o + m_out.
-Weights are rounded to bfloat16, activations entering each matrix product
-are rounded to bfloat16, products accumulate in float32 -- the arithmetic
-of the GPU kernels.  GMRES still decides the converged density, so the
-network only changes the initial guess.
+Test infrastructure only.  Per interface node the network maps 9 input
+features (normalised by fixed means and standard deviations) through 4
+hidden layers of width 128 with SiLU to one output o; oracle.warmstart
+builds the features from the history projection and turns o into the
+initial density.  Weights are rounded to bfloat16, activations entering each
+matrix product are rounded to bfloat16, products accumulate in float32 --
+the arithmetic of the GPU kernels.  GMRES still decides the converged
+density, so the network only changes the initial guess.
 
 The backward pass is written out layer by layer; Adam follows Kingma & Ba.
 """
 from __future__ import annotations
 
 import numpy as np
+
+from kfbi_workloads.configs import mlp_init_params
 
 N_IN = 9
 WIDTH = 128
@@ -61,17 +62,10 @@ def pack(ps) -> np.ndarray:
 
 
 def init(seed: int = 0) -> np.ndarray:
-    """He-style uniform initialisation; the output layer starts at zero so the
-    untrained network predicts the plain previous-density warm start."""
-    rng = np.random.default_rng(seed)
-    ps = []
-    for s in shapes():
-        if len(s) == 2:
-            lim = np.sqrt(6.0 / s[1])
-            ps.append(rng.uniform(-lim, lim, s).astype(np.float32) if s[0] > 1 else np.zeros(s, np.float32))
-        else:
-            ps.append(np.zeros(s, np.float32))
-    return pack(ps)
+    """The seeded initial parameters of the workloads (He-uniform hidden
+    layers, zero biases, zero output layer: the untrained network adds
+    nothing to the projection)."""
+    return mlp_init_params(seed)
 
 
 def silu(z):
@@ -108,8 +102,10 @@ def forward(flat, X, keep=False):
     return (o, zs, acts) if keep else o
 
 
-def loss_and_grad(flat, X, t):
-    """Mean-squared error 0.5 mean (o - t)^2 and its gradient (float32)."""
+def loss_and_grad(flat, X, t, keep=False):
+    """Mean-squared error 0.5 mean (o - t)^2 and its gradient (float32);
+    keep=True also returns the forward cache (o, zs, acts) and the deltas
+    dL/dz of every layer (output layer first)."""
     ps = unpack(flat)
     o, zs, acts = forward(flat, X, keep=True)
     B = X.shape[0]
@@ -118,6 +114,7 @@ def loss_and_grad(flat, X, t):
     L = len(ps) // 2
     grads = [None] * len(ps)
     delta = (r / B)[:, None].astype(np.float32)              # dL/dz of the output layer
+    deltas = [delta]
     for l in range(L - 1, -1, -1):
         a_in = bf16(acts[l])
         # weight gradients from bfloat16 operands with float32 accumulation
@@ -127,6 +124,9 @@ def loss_and_grad(flat, X, t):
             W = bf16(ps[2 * l])
             da = (bf16(delta) @ W).astype(np.float32)
             delta = (da * dsilu(zs[l - 1])).astype(np.float32)
+            deltas.append(delta)
+    if keep:
+        return loss, pack(grads), (o, zs, acts), deltas
     return loss, pack(grads)
 
 
@@ -137,14 +137,3 @@ def adam(flat, grad, m, v, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     mh = m / (1 - b1 ** step)
     vh = v / (1 - b2 ** step)
     return (flat - lr * mh / (np.sqrt(vh) + eps)).astype(np.float32), m.astype(np.float32), v.astype(np.float32)
-
-
-def features(psi1, psi2, g, nodes, normals):
-    return np.concatenate([psi1[:, None], psi2[:, None], g[:, None], nodes, normals], axis=1).astype(np.float32)
-
-
-def predict(flat, norm, psi1, psi2, g, nodes, normals):
-    """psi^n predicted from the previous two densities and g^n."""
-    X = normalise(features(psi1, psi2, g, nodes, normals), norm)
-    o = forward(flat, X)
-    return psi1 + (norm[2 * N_IN + 1] * o + norm[2 * N_IN]).astype(np.float64)

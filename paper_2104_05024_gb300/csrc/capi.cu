@@ -691,6 +691,7 @@ int kfbi_query(kfbi_handle* h, kfbi_info* info) {
   info->n_crossings = h->t.n_int;
   info->n_inside = h->t.n_inside;
   info->device_bytes = h->device_bytes;
+  info->lambda = h->lambda;
   return KFBI_OK;
 }
 

@@ -35,7 +35,7 @@ def main():
     prec = K.FP64 if a.precision == "fp64" else K.MIXED
     geom, grid, cfg, V0, w0 = C.config2(N=a.N)
     h = K.KFBI(geom, grid, tol=cfg.tol)
-    lam = C.helmholtz_lambda(cfg)
+    lam = h.info["lambda"]
     dev = torch.device("cuda:0")
     psi = torch.ones(geom.M, dtype=torch.float64, device=dev)
     out = torch.empty(geom.M, dtype=torch.float64, device=dev)

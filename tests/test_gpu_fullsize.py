@@ -23,6 +23,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from kfbi_workloads import configs as C, geometry as G  # noqa: E402
+from oracle.bidomain import lam_of  # noqa: E402
 from oracle import boxsolve, mlp as OM  # noqa: E402
 from oracle.kfbi import KFBI as OK  # noqa: E402
 from oracle.bidomain import Bidomain  # noqa: E402
@@ -71,7 +72,7 @@ def test_shell256_setup_bit_exact(shell256):
 
 def test_shell256_operators(shell256):
     geom, grid, cfg, V0, w0, o, g = shell256
-    lam = C.helmholtz_lambda(cfg)
+    lam = lam_of(cfg, C.FHN_CONFIG)
     r = np.random.default_rng(256).standard_normal(grid.shape)
     ref = boxsolve.solve(r, lam, grid)
     v = torch.empty(grid.shape, dtype=torch.float64, device=DEV)
@@ -94,7 +95,7 @@ def test_shell256_operators(shell256):
 
 def _oracle_steps(geom, grid, cfg, V0, w0, steps, tol):
     c = C.StrangConfig(sigma_i=cfg.sigma_i, sigma_e=cfg.sigma_e, dt=cfg.dt, steps=steps, tol=tol)
-    bd = Bidomain(geom, grid, c, C.FHN_CONFIG, C.helmholtz_lambda(c))
+    bd = Bidomain(geom, grid, c, C.FHN_CONFIG)
     V, w = V0.copy(), w0.copy()
     for _ in range(steps):
         V, w, info = bd.step(V, w)

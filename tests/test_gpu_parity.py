@@ -12,6 +12,7 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 from kfbi_workloads import configs as C, geometry as G  # noqa: E402
+from oracle.bidomain import lam_of  # noqa: E402
 from oracle import boxsolve, krylov, reaction  # noqa: E402
 from oracle.kfbi import KFBI as OK  # noqa: E402
 from oracle.bidomain import Bidomain, extracellular  # noqa: E402
@@ -212,8 +213,8 @@ def test_strang_stiff_richardson():
     geom, grid, _, V0, w0 = C.config0()
     dt = grid.h
     cfg = C.StrangConfig(sigma_i=1.0, sigma_e=2.0, dt=dt, steps=3, tol=1e-12)
-    lam = C.helmholtz_lambda(cfg, C.FHN_PAPER)
-    bd = Bidomain(geom, grid, cfg, C.FHN_PAPER, lam)
+    lam = lam_of(cfg, C.FHN_PAPER)
+    bd = Bidomain(geom, grid, cfg, C.FHN_PAPER)
     V, w = V0.copy(), w0.copy()
     for _ in range(cfg.steps):
         V, w, info = bd.step(V, w)
@@ -264,7 +265,7 @@ def test_solve_neumann_mixed(name, lam):
 def test_strang_config0_mixed():
     geom, grid, cfg, V0, w0 = C.config0()
     cfg = C.StrangConfig(sigma_i=1.0, sigma_e=2.0, dt=0.05, steps=5, tol=1e-12)
-    bd = Bidomain(geom, grid, cfg, C.FHN_CONFIG, C.helmholtz_lambda(cfg))
+    bd = Bidomain(geom, grid, cfg, C.FHN_CONFIG)
     V, w = V0.copy(), w0.copy()
     for _ in range(cfg.steps):
         V, w, _ = bd.step(V, w)
@@ -296,8 +297,8 @@ def test_strang_config0_short():
     with a 1e-12 GMRES tolerance on both sides."""
     geom, grid, cfg, V0, w0 = C.config0()
     cfg = C.StrangConfig(sigma_i=1.0, sigma_e=2.0, dt=0.05, steps=5, tol=1e-12)
-    lam = C.helmholtz_lambda(cfg)
-    bd = Bidomain(geom, grid, cfg, C.FHN_CONFIG, lam)
+    lam = lam_of(cfg, C.FHN_CONFIG)
+    bd = Bidomain(geom, grid, cfg, C.FHN_CONFIG)
     V, w = V0.copy(), w0.copy()
     for _ in range(cfg.steps):
         V, w, _ = bd.step(V, w)

@@ -75,7 +75,7 @@ def test_virtual_electrode_strang(name):
     steps = 3
     cfg = C.StrangConfig(sigma_i=1.0, sigma_e=2.0, dt=grid.h, steps=steps, tol=1e-12)
     I = C.virtual_electrode(grid)
-    bd = Bidomain(geom, grid, cfg, fhn, C.helmholtz_lambda(cfg, fhn), istim=I)
+    bd = Bidomain(geom, grid, cfg, fhn, istim=I)
     V, w = np.zeros(grid.shape), np.zeros(grid.shape)
     for _ in range(steps):
         V, w, info = bd.step(V, w)
@@ -107,7 +107,7 @@ def test_virtual_electrode_sphere256():
     for prec, warm, tol_gpu, tol_ref, steps, bar in ((K.FP64, K.WARM_PREVIOUS, 1e-12, 1e-12, 1, 1e-10),
                                                      (K.MIXED, K.WARM_PROJECTION, 1e-8, 1e-10, 2, 1e-7)):
         cfg = C.StrangConfig(sigma_i=1.0, sigma_e=2.0, dt=grid.h, steps=steps, tol=tol_ref)
-        bd = Bidomain(geom, grid, cfg, fhn, C.helmholtz_lambda(cfg, fhn), istim=I)
+        bd = Bidomain(geom, grid, cfg, fhn, istim=I)
         V, w = np.zeros(grid.shape), np.zeros(grid.shape)
         for _ in range(steps):
             V, w, info = bd.step(V, w)

@@ -286,18 +286,23 @@ def test_second_order_convergence_sphere():
 
 
 def test_green_identity_discrete():
-    """For Lap u - lam u = f with du/dn = g^N: the boundary flux equals the
-    volume integral of f + lam u (checked to O(h) on the numerical solution)."""
-    N = 128
-    geom, grid = G.ellipse_config0(2 * N), Grid(2, N)
-    f, u, gN = C.manufactured(geom, grid, 60.0)
-    k = KFBI(geom, grid)
-    uh, psi, info = k.solve_neumann(f, gN, 60.0, tol=1e-10)
-    vol = ((f + 60.0 * uh) * k.inside).sum() * grid.h ** 2
-    seg = np.roll(geom.nodes, -1, 0) - geom.nodes
-    ds = 0.5 * (np.linalg.norm(seg, axis=1) + np.roll(np.linalg.norm(seg, axis=1), 1))
-    flux = (gN * ds).sum()
-    assert abs(vol - flux) < 0.05 * abs(flux) + 0.05
+    """For Lap u - lam u = f with du/dn = g^N, the boundary flux equals the
+    volume integral of f + lam u.  The node-sum quadrature of the volume
+    integral is only first-order accurate on the staircase of inside nodes,
+    so the flux balance of the numerical solution is compared with that of the
+    exact solution under the same quadrature: the difference (lam h^2 times
+    the summed error over the inside nodes) vanishes at second order."""
+    d = []
+    for N in (32, 64, 128):
+        geom, grid = G.ellipse_config0(2 * N), Grid(2, N)
+        f, u, gN = C.manufactured(geom, grid, 60.0)
+        k = KFBI(geom, grid)
+        uh, psi, info = k.solve_neumann(f, gN, 60.0, tol=1e-12)
+        vol_h = ((f + 60.0 * uh) * k.inside).sum() * grid.h ** 2
+        vol_x = ((f + 60.0 * u) * k.inside).sum() * grid.h ** 2
+        d.append(abs(vol_h - vol_x))
+    assert d[-1] < 5e-3 * abs(vol_x)
+    assert min(_rate(d)) > 1.7
 
 
 # ------------------------------------------------ Poisson case and stimulus
@@ -339,7 +344,7 @@ def test_virtual_electrode_symmetry():
     from oracle.bidomain import Bidomain
     geom, grid = G.disk2(0.6, 128), Grid(2, 64)
     cfg = C.StrangConfig(sigma_i=1.0, sigma_e=2.0, dt=grid.h, steps=1, tol=1e-12)
-    bd = Bidomain(geom, grid, cfg, C.FHN_PAPER, C.helmholtz_lambda(cfg, C.FHN_PAPER),
+    bd = Bidomain(geom, grid, cfg, C.FHN_PAPER,
                   istim=C.virtual_electrode(grid))
     S = bd.solve_S()
     assert bd.S_info["converged"]
@@ -362,7 +367,7 @@ def test_virtual_electrode_coupled_equations():
     cfg = C.StrangConfig(sigma_i=1.0, sigma_e=2.0, dt=grid.h, steps=1, tol=1e-12)
     fhn = C.FHN_PAPER
     I = C.virtual_electrode(grid)
-    bd = Bidomain(geom, grid, cfg, fhn, C.helmholtz_lambda(cfg, fhn), istim=I)
+    bd = Bidomain(geom, grid, cfg, fhn, istim=I)
     Vn = 0.3 * np.cos(3.0 * grid.coords()[0]) * np.ones(grid.shape)
     w, info = bd.diffuse(Vn)
     S = bd.solve_S()

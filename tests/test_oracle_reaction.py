@@ -4,6 +4,7 @@ import scipy.optimize
 
 from kfbi_workloads import configs as C, geometry as G
 from kfbi_workloads.configs import FHN_CONFIG as P, Grid
+from oracle.bidomain import lam_of  # noqa: E402
 from oracle import reaction
 from oracle.bidomain import Bidomain, extracellular
 
@@ -47,9 +48,9 @@ def test_backward_euler_against_brentq():
 def test_strang_zero_state_stays_zero_and_mean_zero_ue():
     geom, grid = G.ellipse_config0(64), Grid(2, 32)
     cfg = C.StrangConfig(steps=2)
-    lam = C.helmholtz_lambda(cfg)
+    lam = lam_of(cfg, C.FHN_CONFIG)
     assert lam == 60.0
-    bd = Bidomain(geom, grid, cfg, P, lam)
+    bd = Bidomain(geom, grid, cfg, P)
     V = np.zeros(grid.shape)
     q = np.zeros(grid.shape)
     V1, q1, info = bd.step(V, q)
@@ -69,7 +70,7 @@ def test_strang_constant_state_diffusion_is_identity():
     the Neumann problem Lap u - lam u = -lam c has u = c."""
     geom, grid = G.ellipse_config0(64), Grid(2, 32)
     cfg = C.StrangConfig(steps=1)
-    bd = Bidomain(geom, grid, cfg, P, C.helmholtz_lambda(cfg))
+    bd = Bidomain(geom, grid, cfg, P)
     c = 0.3
     w, psi, info = bd.k.solve_neumann(-60.0 * c * np.ones(grid.shape), np.zeros(geom.M), 60.0, tol=1e-12)
     assert np.abs(w[bd.k.inside] - c).max() < 2e-3        # O(h^2) discretisation error only
