@@ -183,71 +183,60 @@ def run_gpu(args):
         barrier()
     launches = K.launch_count() - l0
     V_main, w_main = V.clone(), w.clone()
+    ue_main = torch.empty_like(V)
+    h.bidomain_step(fhn, V_main, w_main, ue_main, nsteps=0)     # u_e of the final state only
     ms = e0.elapsed_time(e1)
     marks = [e0] + seg_ev + [e1]
     seg_ms = [marks[i].elapsed_time(marks[i + 1]) / (args.steps // nseg) for i in range(nseg)]
     ms_step, value = replica_time(ms / args.steps, world, dist, dev)
     iters = [s["iters"] for s in stats]
 
-    # ---- dominant kernel: one pass of the transform, timed alone with events
+    # ---- roofline of the hot path's transform solve (the unit of the
+    # algorithmic bytes: one box solve, 2 G s bytes, G = (N-1)^3 unknowns)
     pk, kind = peaks()
-    reps = 20
-    pass_ms = {}
     prec_pass = K.FP64 if precision == K.FP64 else K.MIXED
     lam = h.info["lambda"]
-    for p in (0, 1, 2, 3):
-        for _ in range(3):
-            h.transform_pass(p, lam, prec_pass)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(reps):
-            h.transform_pass(p, lam, prec_pass)
-        b.record(stream)
-        torch.cuda.synchronize()
-        pass_ms[p] = a.elapsed_time(b) / reps
     N = args.N
-    lines = (N - 1) * (N - 1)
-    fl_dst = 2.5 * N * np.log2(N)            # real-FFT flop count of one DST-I line
-    z_flops = 2 * lines * fl_dst + 3.0 * (N - 1) ** 3
-    z_s = pass_ms[2] / 1e3
-    esize = 8 if prec_pass == K.FP64 else 4
-    # the dominant kernel of the step's launch list: float64, the z solve pass
-    # (FP64-pipe bound); float32, the y pass (two launches per box solve)
-    if prec_pass == K.FP64:
-        roof = {"kernel": f"k_strided<double,{N},SOLVE> (z pass: DST, divide, DST)", "bound": "alu",
-                "achieved": z_flops / z_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz", "traffic": None}
-    else:
-        y_bytes = 2.0 * N ** 3 * esize           # read + write of the padded grid
-        roof = {"kernel": f"k_strided_tma<{N},0> (y pass: one DST per line)", "bound": "hbm",
-                "achieved": y_bytes / (pass_ms[1] / 1e3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "peak_source": kind,
-                # DRAM read + write per launch of this kernel at 256^3 from one
-                # ncu capture (cold cache); none for other sizes
-                "traffic": 72.8e6 if N == 256 else None,
-                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, cold cache)"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["pass_ms"] = {k: round(v, 4) for k, v in pass_ms.items()}
-    roof["hbm_gbs_per_pass"] = {k: round(2.0 * N ** 3 * esize / (v / 1e3) / 1e9, 1) for k, v in pass_ms.items()}
+    roof = box_solve_roofline(h, N, prec_pass, lam, pk, kind, dev)
+    roof_512 = None
+    if precision != K.FP64 and not args.no_large:
+        # the same float32 solve at 512^3, where the grid (512 MB) leaves L2
+        from kfbi_workloads import geometry as G
+        h512 = K.KFBI(G.shell_config2(C.surface_res(512)), C.Grid(3, 512), tol=cfg.tol)
+        roof_512 = box_solve_roofline(h512, 512, K.MIXED, lam, pk, kind, dev)
+        h512.close()
+        torch.cuda.empty_cache()
 
-    # ---- end to end through the C ABI with host buffers
-    e2e_steps = max(1, min(args.steps, 5))
-    Vh = torch.empty(V.shape, dtype=torch.float64, pin_memory=True)
-    wh = torch.empty(w.shape, dtype=torch.float64, pin_memory=True)
-    Vh.copy_(V)
-    wh.copy_(w)
+    # ---- end to end through the C ABI with host buffers: the same steps as
+    # `value` (a second run from the same initial state, W warm-up steps, then
+    # K timed steps), V and w copied in from pinned host memory and back out
+    # every step
+    he = K.KFBI(geom, grid, sigma_i=cfg.sigma_i, sigma_e=cfg.sigma_e, dt=cfg.dt, tol=cfg.tol, precision=precision,
+                restart=50, max_iter=400, warm=warm)
+    if precision == K.MIXED_LEARNED:
+        he.set_warmstart(mlp)
+    Vh = torch.tensor(V0, dtype=torch.float64).pin_memory()
+    wh = torch.tensor(w0, dtype=torch.float64).pin_memory()
+    Ve, we = torch.empty_like(V), torch.empty_like(w)
+    Ve.copy_(Vh)
+    we.copy_(wh)
+    for _ in range(args.warmup):
+        he.bidomain_step(fhn, Ve, we, None, nsteps=1)
+    Vh.copy_(Ve)
+    wh.copy_(we)
     barrier()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    for _ in range(e2e_steps):
-        V.copy_(Vh, non_blocking=True)
-        w.copy_(wh, non_blocking=True)
-        h.bidomain_step(fhn, V, w, None, nsteps=1)
-        Vh.copy_(V, non_blocking=True)
-        wh.copy_(w, non_blocking=True)
+    for _ in range(args.steps):
+        Ve.copy_(Vh, non_blocking=True)
+        we.copy_(wh, non_blocking=True)
+        he.bidomain_step(fhn, Ve, we, None, nsteps=1)
+        Vh.copy_(Ve, non_blocking=True)
+        wh.copy_(we, non_blocking=True)
     b.record(stream)
     barrier()
-    e2e_ms, e2e_value = replica_time(a.elapsed_time(b) / e2e_steps, world, dist, dev)
+    he.close()
+    e2e_ms, e2e_value = replica_time(a.elapsed_time(b) / args.steps, world, dist, dev)
     nbytes = V.numel() * 8 * 2
 
     # the other forms on the same workload and protocol (plain float64, mixed)
@@ -274,9 +263,13 @@ def run_gpu(args):
                            "gmres_iters_per_step": float(np.mean([s["iters"] for s in st2]))}
             if name == "fp64":
                 # field differences of this form's state against the float64 state after the same steps
+                ue2 = torch.empty_like(V2)
+                h2.bidomain_step(fhn, V2, w2, ue2, nsteps=0)
                 forms["max_abs_diff_vs_fp64"] = {"V": float((V_main - V2).abs().max()),
                                                  "w": float((w_main - w2).abs().max()),
-                                                 "V_max": float(V2.abs().max())}
+                                                 "ue": float((ue_main - ue2).abs().max()),
+                                                 "V_max": float(V2.abs().max()),
+                                                 "ue_max": float(ue2.abs().max())}
             h2.close()
     if "fp64" in forms:
         for name in ("mixed", "projection", "learned"):
@@ -301,6 +294,7 @@ def run_gpu(args):
         "forms": forms,
         "learned": learn_info if learn_info is None else dict(learn_info, used=int(sum(s["warmstart"] for s in stats))),
         "roofline": roof,
+        "roofline_512": roof_512,
         "clocks": clk.summary(),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes},
@@ -316,6 +310,96 @@ def run_gpu(args):
         print(json.dumps(result), flush=True)
 
 
+def _pass_times(h, prec, lam, reps, flush=None):
+    """Mean CUDA-event time (ms) of each transform pass of the box solver on
+    the handle's padded work grid (pass 0 x forward, 1 y, 2 z solve, 3 x
+    inverse).  flush: a tensor larger than L2 written before every launch
+    (cold-cache times), else back-to-back launches."""
+    import torch
+    stream = torch.cuda.current_stream()
+    out = {}
+    for p in (0, 1, 2, 3):
+        for _ in range(3):
+            h.transform_pass(p, lam, prec)
+        tot = 0.0
+        if flush is None:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                h.transform_pass(p, lam, prec)
+            b.record(stream)
+            torch.cuda.synchronize()
+            tot = a.elapsed_time(b)
+        else:
+            for _ in range(reps):
+                flush.add_(1.0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                h.transform_pass(p, lam, prec)
+                b.record(stream)
+                torch.cuda.synchronize()
+                tot += a.elapsed_time(b)
+        out[p] = tot / reps
+    return out
+
+
+# DRAM bytes per launch of each transform pass from one ncu capture of the
+# committed kernels (profiles/box_solve_fp32_passes.md; read + write), by
+# grid size and pass; the five-pass solve runs pass 1 twice
+NCU_DRAM_BYTES = {}
+
+
+def box_solve_roofline(h, N, prec, lam, pk, kind, dev):
+    """Roofline line of one box solve: algorithmic bytes 2 G s (G = (N-1)^3
+    unknowns, s the element size: the right-hand side read once and the
+    solution written once) over the summed time of its five passes (x
+    forward, y, z solve, y, x inverse), against the measured HBM copy
+    bandwidth.  Float64 solves are also reported against the FP64 pipe."""
+    import torch
+    import paper_2104_05024_gb300.kfbi as K
+    esize = 8 if prec == K.FP64 else 4
+    G = (N - 1) ** 3
+    alg = 2.0 * G * esize
+    warm = _pass_times(h, prec, lam, 20)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > 129 MB L2
+    cold = _pass_times(h, prec, lam, 5, flush)
+    del flush
+    solve = lambda t: t[0] + 2.0 * t[1] + t[2] + t[3]  # noqa: E731
+    grid_mb = N ** 3 * esize / 1e6
+    resident = grid_mb < 129.0
+    # the time the roofline uses: cold-L2 passes when the grid would stay in
+    # L2 across back-to-back launches, else the warm (back-to-back) passes
+    t = cold if resident else warm
+    achieved = alg / (solve(t) / 1e3) / 1e9
+    roof = {"kernel": f"box solve {N}^3 {'float64' if esize == 8 else 'float32'} (k_xfwd, k_strided*, k_xinv)",
+            "unit_of_work": "one box solve: 2 G s bytes, G = (N-1)^3", "bound": "hbm",
+            "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s", "peak_source": kind,
+            "frac": achieved / pk["hbm_gbs"],
+            "algorithmic_bytes": alg, "solve_ms": solve(t),
+            "l2": (f"grid {grid_mb:.0f} MB fits the 129 MB L2: passes timed one by one with a 256 MB L2 flush "
+                   "before each" if resident else f"grid {grid_mb:.0f} MB exceeds the 129 MB L2: back-to-back"),
+            "pass_ms": {k: round(v, 4) for k, v in t.items()},
+            "pass_ms_warm": {k: round(v, 4) for k, v in warm.items()},
+            "solve_ms_warm": solve(warm),
+            "pass_gbs": {k: round(2.0 * N ** 3 * esize / (v / 1e3) / 1e9, 1) for k, v in t.items()}}
+    nb = NCU_DRAM_BYTES.get((N, esize))
+    if nb is not None:
+        tr = nb[0] + 2 * nb[1] + nb[2] + nb[3]
+        roof["traffic"] = tr
+        roof["traffic_unit"] = "ncu dram read + write bytes of the five passes of one solve"
+        roof["dram_gbs"] = tr / (solve(t) / 1e3) / 1e9
+        roof["dram_frac"] = roof["dram_gbs"] / pk["hbm_gbs"]
+    else:
+        roof["traffic"] = None
+    if esize == 8:
+        lines = (N - 1) * (N - 1)
+        fl_dst = 2.5 * N * np.log2(N)            # real-FFT flop count of one DST-I line
+        flops = 6 * lines * fl_dst + 3.0 * G
+        roof["fp64_tflops"] = flops / (solve(t) / 1e3) / 1e12
+        roof["fp64_peak_tflops"] = FP64_PEAK_TFLOPS
+    return roof
+
+
 def train_warmstart(args, geom, grid, cfg, dev):
     """Train the warm-start network on densities of runs with the 8 training
     stimulus locations (untimed); the timed run's stimulus is held out."""
@@ -326,21 +410,20 @@ def train_warmstart(args, geom, grid, cfg, dev):
     from kfbi_workloads import configs as C
 
     t0 = time.time()
-    normals = C.analytic_normals(geom)
     Fs, Ts = [], []
     for c in C.midwall_centers(C.TRAIN_SEEDS):
         h = K.KFBI(geom, grid, sigma_i=cfg.sigma_i, sigma_e=cfg.sigma_e, dt=cfg.dt, tol=cfg.tol, precision=K.MIXED,
                    restart=50, max_iter=400)
         V = torch.tensor(C.ball_stimulus(grid, c, 0.1), device=dev)
         w = torch.zeros_like(V)
-        F, T = WS.collect(h, C.FHN_CONFIG, V, w, args.train_steps, geom.nodes, normals)
+        F, T = WS.collect(h, C.FHN_CONFIG, V, w, args.train_steps)
         Fs.append(F)
         Ts.append(T)
         h.close()
     F, T = torch.cat(Fs), torch.cat(Ts)
     norm = WS.fit_norm(F, T)
     mlp = K.MLP(WS.init_params(0), norm, max(8192, geom.M))
-    losses = WS.train(mlp, F, T, norm, epochs=args.train_epochs, batch=4096, lr=2e-3)
+    losses = WS.train(mlp, F, T, epochs=args.train_epochs, batch=4096, lr=2e-3)
     torch.cuda.synchronize()
     info = {"train_rows": int(F.shape[0]), "train_seeds": len(C.TRAIN_SEEDS), "steps_per_seed": args.train_steps,
             "epochs": args.train_epochs, "loss_first_last": [round(losses[0], 5), round(losses[-1], 5)],
@@ -622,6 +705,7 @@ def main():
                     help="skip timing the other precision forms on the same workload")
     ap.add_argument("--N", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the 512^3 box-solve roofline line")
     ap.add_argument("--train-steps", type=int, default=12, help="Strang steps per training stimulus (learned form)")
     ap.add_argument("--train-epochs", type=int, default=8)
     ap.add_argument("--workload", default="strang",

@@ -127,9 +127,14 @@ typedef struct {
   int warmstart;        /* initial guess kept: 0 previous density or
                            projection, 1 learned                            */
   double rel_res;       /* solver's residual estimate ||r|| / ||g||           */
-  double true_rel_res;  /* recomputed ||g^N - du^+/dn|| / ||g|| (or -1)       */
+  double true_rel_res;  /* recomputed ||g^N - du^+/dn|| / ||g|| of the final
+                           u = v_V + v_B(psi) (-1 where not computed)        */
   double init_rel_res;  /* residual of the initial guess                      */
-  double ms;            /* wall time of the call                              */
+  double ms;            /* host wall time of the call / step                  */
+  /* bidomain_step only: device time of the phases of the step (CUDA events):
+     both reaction half steps, the volume solve and g, the warm start, the
+     boundary-integral solve, and the assembly of V (with the true residual) */
+  double react_ms, rhs_ms, warm_ms, solve_ms, assemble_ms;
 } kfbi_stats;
 
 typedef struct {
@@ -259,14 +264,19 @@ int kfbi_solve_bie(kfbi_handle* h, double lambda, const double* g_dev, double* p
 
 /* ------------------------------------------------------------------
  * Learned warm start (the workload's mixed + learned form; not in the paper).
- * A point-wise network on the interface nodes: features (psi^{n-1},
- * psi^{n-2}, g^n, x, y, z, n_x, n_y, n_z), normalised by
- * norm = [mean[9], std[9], out_mean, out_std]; 4 hidden layers of width 128
- * with SiLU; output o; psi^n predicted as psi^{n-1} + out_std o + out_mean.
+ * A point-wise network on the interface nodes reads 9 raw features per node,
+ *   (psi_F / rms(psi_F), r_F / rms(r_F), g / rms(g), x, y, z, n_x, n_y, n_z),
+ * with psi_F the history projection (KFBI_WARM_PROJECTION), r_F = g - A psi_F
+ * its residual, g the right-hand side of the solve and rms the root mean
+ * square over the nodes; they are normalised by norm = [mean[9], std[9],
+ * out_mean, out_std], pass 4 hidden layers of width 128 with SiLU, and give
+ * an output o.  The initial density is
+ *   psi_L = psi_F + 2 gamma r_F + rms(r_F) (out_std o + out_mean).
  * Parameters (float32, packed W0[128][9], b0[128], W1[128][128], b1, W2, b2,
  * W3, b3, W4[1][128], b4[1]) are kept as float32 masters with bfloat16 copies
  * for the tensor-core products (float32 accumulation).  Training uses the
- * loss 0.5 mean (o - t)^2 on normalised targets t and Adam (0.9, 0.999, 1e-8).
+ * loss 0.5 mean (o - t)^2 on the normalised targets t = (T - out_mean) /
+ * out_std of raw targets T (kfbi_training_rows) and Adam (0.9, 0.999, 1e-8).
  * ------------------------------------------------------------------ */
 int kfbi_mlp_num_params(void);
 /* params_host [kfbi_mlp_num_params()], norm_host [20]; max_batch rows per
@@ -276,10 +286,26 @@ void kfbi_mlp_destroy(kfbi_mlp* m);
 int kfbi_mlp_get(kfbi_mlp* m, float* params_host);
 /* o_dev[B] = network output for raw features F_dev [B][9] (float32).        */
 int kfbi_mlp_forward(kfbi_mlp* m, const float* F_dev, int B, float* o_dev);
-/* loss and (optionally) the gradient of every parameter to host memory.     */
-int kfbi_mlp_grad(kfbi_mlp* m, const float* F_dev, const float* t_dev, int B, float* loss_host, float* grad_host);
+/* loss and (optionally) the gradient of every parameter to host memory, for
+ * raw features F_dev [B][9] and raw targets T_dev [B] (device, float32).     */
+int kfbi_mlp_grad(kfbi_mlp* m, const float* F_dev, const float* T_dev, int B, float* loss_host, float* grad_host);
 /* one forward + backward + Adam step with learning rate lr.                 */
-int kfbi_mlp_train_step(kfbi_mlp* m, const float* F_dev, const float* t_dev, int B, float lr, float* loss_host);
+int kfbi_mlp_train_step(kfbi_mlp* m, const float* F_dev, const float* T_dev, int B, float lr, float* loss_host);
+/* Layer values of the training path, for element-wise checks of every
+ * kernel of the network (no counterpart in the paper): the forward pass of
+ * kfbi_mlp_grad on B raw rows F_dev [B][9] gives z_dev [4][B][128], the
+ * pre-activations z_l = bf16(a_l) bf16(W_l)^T + b_l of the hidden layers
+ * l = 0..3, and o_dev [B]; with raw targets T_dev its backward pass gives
+ * d_dev [4][B][128], dL/dz_l of the hidden layers in the order l = 3..0, and
+ * d4_dev [B] = dL/do.  Outputs are device float32 and may be NULL;
+ * synchronises the network's stream.                                        */
+int kfbi_mlp_layers(kfbi_mlp* m, const float* F_dev, const float* T_dev, int B, float* z_dev, float* o_dev,
+                    float* d_dev, float* d4_dev);
+/* Normalisation vector of a training set (norm_host [20]): per feature the
+ * mean and sample standard deviation of F_dev [n][9], then those of T_dev
+ * [n]; a spread below 1e-12 (features) or 1e-30 (targets) becomes 1.  Work
+ * on `stream`, synchronised; allocates 160 bytes of device scratch.          */
+int kfbi_mlp_fit_norm(const float* F_dev, const float* T_dev, int n, void* stream, float* norm_host);
 /* Attach (or detach with NULL) a network to a 3-D handle.  With precision
  * KFBI_MIXED_LEARNED, bidomain_step then starts each diffusion solve from
  *   psi_L = psi_F + 2 gamma r_F + rms(r_F) * net(psi_F/rms, r_F/rms, g/rms,
@@ -316,6 +342,17 @@ int kfbi_set_history(kfbi_handle* h, const double* psi_hist_dev, const double* g
  * residual r_F = g - A psi_F (known without an operator application from the
  * history's images), M doubles each, device.                                */
 int kfbi_get_projection(kfbi_handle* h, double* psiF_dev, double* rF_dev);
+/* After a Strang step: the initial density its diffusion solve started from,
+ * before the residual judge (psi_L of the learned form, psi_F + 2 gamma r_F
+ * of the projection form, the previous density otherwise), M doubles.      */
+int kfbi_get_warm_guess(kfbi_handle* h, double* psi0_dev);
+/* Training rows of the learned warm start from the last Strang step of a 3-D
+ * handle run with KFBI_WARM_PROJECTION (or the learned form): F_dev [M][9]
+ * the network's raw input rows of that step's projection (the features
+ * above) and T_dev [M] the raw target (psi - psi_F - 2 gamma r_F) / rms(r_F),
+ * psi the converged density; float32, device, enqueued on the handle's
+ * stream.                                                                    */
+int kfbi_training_rows(kfbi_handle* h, float* F_dev, float* T_dev);
 
 /* One pass of the box solver on the handle's padded work grid, for timing
  * the transform kernels in isolation: pass 0 = x forward (no right-hand

@@ -12,6 +12,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -677,6 +678,8 @@ void kfbi_destroy(kfbi_handle* h) {
   if (h->w.host_small) cudaFreeHost(h->w.host_small);
   for (cudaEvent_t e : h->arn_ev)
     if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->step_events) cudaEventDestroy(e);
+  if (h->w.step_sq) cudaFree(h->w.step_sq);
   delete h;
 }
 
@@ -904,10 +907,33 @@ static int bidomain_impl(kfbi_handle* h, const kfbi_fhn* p, const double* istim,
     if (rc == KFBI_ERR_NOT_CONVERGED) final_rc = rc;
   }
   KFBI_CUDA(cudaMemsetAsync(h->w.err, 0, sizeof(int), h->stream));
+  // per step: ||g^N - du^+/dn||^2 and ||g||^2 (true residual, read once at
+  // the end) and, with per_step, CUDA events between the phases
+  if (nsteps > h->step_cap) {
+    if (h->w.step_sq) cudaFree(h->w.step_sq);
+    h->w.step_sq = nullptr;
+    h->step_cap = 0;
+    KFBI_CUDA(cudaMalloc((void**)&h->w.step_sq, sizeof(double) * 2 * (size_t)nsteps));
+    h->step_cap = nsteps;
+  }
+  constexpr int NEV = 7;
+  const bool timed = per_step != nullptr;
+  while (timed && h->step_events.size() < (size_t)NEV * nsteps) {
+    cudaEvent_t e;
+    KFBI_CUDA(cudaEventCreate(&e));
+    h->step_events.push_back(e);
+  }
+  std::vector<kfbi_stats> stats((size_t)nsteps);
+  auto mark = [&](int s, int k) -> int {
+    if (timed) KFBI_CUDA(cudaEventRecord(h->step_events[(size_t)NEV * s + k], h->stream));
+    return KFBI_OK;
+  };
   for (int s = 0; s < nsteps; ++s) {
-    kfbi_stats st{};
+    kfbi_stats& st = stats[s];
     auto t0 = std::chrono::steady_clock::now();
+    if ((rc = mark(s, 0))) return rc;
     if ((rc = launch_react_fe(p, k, V_dev, w_dev, n, h->stream))) return rc;
+    if ((rc = mark(s, 1))) return rc;
     const int prec = h->opts.precision == KFBI_FP64 ? KFBI_FP64 : KFBI_MIXED;
     // source of the V problem: -lam V (+ beta I / sigma_e with a stimulus)
     const double* vsrc = V_dev;
@@ -921,6 +947,7 @@ static int bidomain_impl(kfbi_handle* h, const kfbi_fhn* p, const double* istim,
     rc = prec == KFBI_FP64 ? rhs_g(h, lam, vsrc, alpha, nullptr, h->w.g)
                            : rhs_g_acc(h, lam, vsrc, alpha, nullptr, h->w.g);
     if (rc) return rc;
+    if ((rc = mark(s, 2))) return rc;
     // initial density: the previous one, or the learned prediction when its
     // float32 residual is smaller
     if ((rc = vec_copy(h, h->w.psi_save, h->w.psi_prev, h->t.M))) return rc;
@@ -928,7 +955,9 @@ static int bidomain_impl(kfbi_handle* h, const kfbi_fhn* p, const double* istim,
     const double* fallback_res2 = nullptr;
     double gnorm = -1.0;
     const bool learned = h->opts.precision == KFBI_MIXED_LEARNED && h->warm != nullptr;
+    h->proj_valid = false;
     if ((h->opts.warm == KFBI_WARM_PROJECTION || learned) && h->opts.solver == KFBI_GMRES && h->hist_count >= 1) {
+      h->proj_valid = true;
       // psi_F from the history, then one step of the simple iteration
       // psi_F + 2 gamma r_F; psi_F itself (residual known) is the fallback
       const int M = h->t.M;
@@ -948,6 +977,9 @@ static int bidomain_impl(kfbi_handle* h, const kfbi_fhn* p, const double* istim,
       }
       fallback = h->w.psiF;
     }
+    // the guess as it enters the solver (kfbi_get_warm_guess)
+    if ((rc = vec_copy(h, h->w.psi_learn, h->w.psi_prev, h->t.M))) return rc;
+    if ((rc = mark(s, 3))) return rc;
     // mixed forms: the history holds exact images A psi_s, so r_F is the
     // float64-accurate residual of psi_F
     const bool ir = prec != KFBI_FP64 && h->opts.solver == KFBI_GMRES;
@@ -959,11 +991,14 @@ static int bidomain_impl(kfbi_handle* h, const kfbi_fhn* p, const double* istim,
     if ((rc = push_history(h, h->w.psi_prev, h->w.g, ir ? h->w.r2 : nullptr))) return rc;
     ++h->n_hist;
     if (src == KFBI_ERR_NOT_CONVERGED) final_rc = src;
-    // V <- 2 (v_V + v_B(psi)) - V
+    if ((rc = mark(s, 4))) return rc;
+    // V <- 2 (v_V + v_B(psi)) - V, and the true residual g^N - du^+/dn of
+    // u = v_V + v_B(psi) at the nodes (homogeneous Neumann data: g^N = 0)
+    const double* x;
+    if ((rc = density_vector(h, h->w.psi_prev, &x))) return rc;
     if (prec == KFBI_FP64) {
-      // one float64 solve of the combined right-hand side
-      const double* x;
-      if ((rc = density_vector(h, h->w.psi_prev, &x))) return rc;
+      // one float64 solve of the combined right-hand side; the padded work
+      // grid keeps u for the limit
       if ((rc = launch_correction(h, x, h->w.corr))) return rc;
       SolveArgs sa;
       sa.src = vsrc;
@@ -975,22 +1010,47 @@ static int bidomain_impl(kfbi_handle* h, const kfbi_fhn* p, const double* istim,
       sa.beta = 2.0;
       sa.gamma = -1.0;
       if ((rc = box_solve64(h, sa, h->w.grid64))) return rc;
+      if ((rc = launch_limit64(h, h->w.grid64, x, nullptr, -1.0, h->w.tmp))) return rc;
     } else {
       // the refined solver's last act was the float64-accurate residual at
       // the final density, which left v_B(psi) in u64; v_V is in vV64
       if ((rc = launch_midpoint(h, V_dev, h->w.vV64, h->w.u64, n))) return rc;
+      if ((rc = launch_limit_user(h, h->w.vV64, nullptr, nullptr, -1.0, h->w.tmp))) return rc;
+      if ((rc = launch_limit_user(h, h->w.u64, x, h->w.tmp, -1.0, h->w.tmp))) return rc;
     }
+    if ((rc = vec_dots(h, h->w.tmp, 1, h->t.M, h->w.tmp, h->w.step_sq + 2 * s))) return rc;
+    if ((rc = vec_dots(h, h->w.g, 1, h->t.M, h->w.g, h->w.step_sq + 2 * s + 1))) return rc;
+    if ((rc = mark(s, 5))) return rc;
     if ((rc = launch_react_be(p, k, V_dev, w_dev, n, h->w.err, h->stream))) return rc;
-    st.true_rel_res = -1.0;
+    if ((rc = mark(s, 6))) return rc;
     st.ms = elapsed_ms(t0);
-    if (per_step) per_step[s] = st;
   }
   if (ue_dev) {
     if ((rc = istim != nullptr ? launch_ue_S(h, V_dev, h->w.S64, ue_dev) : launch_ue(h, V_dev, ue_dev))) return rc;
   }
   int herr = 0;
+  std::vector<double> sq((size_t)2 * nsteps + 1);
   KFBI_CUDA(cudaMemcpyAsync(&herr, h->w.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  if (nsteps > 0)
+    KFBI_CUDA(cudaMemcpyAsync(sq.data(), h->w.step_sq, sizeof(double) * 2 * (size_t)nsteps, cudaMemcpyDeviceToHost,
+                              h->stream));
   KFBI_CUDA(cudaStreamSynchronize(h->stream));
+  for (int s = 0; s < nsteps; ++s) {
+    kfbi_stats& st = stats[s];
+    const double rr = std::sqrt(sq[2 * s]), gg = std::sqrt(sq[2 * s + 1]);
+    st.true_rel_res = gg > 0.0 ? rr / gg : rr;
+    if (timed) {
+      float t[NEV - 1];
+      for (int q = 0; q + 1 < NEV; ++q)
+        KFBI_CUDA(cudaEventElapsedTime(&t[q], h->step_events[(size_t)NEV * s + q], h->step_events[(size_t)NEV * s + q + 1]));
+      st.react_ms = t[0] + t[5];
+      st.rhs_ms = t[1];
+      st.warm_ms = t[2];
+      st.solve_ms = t[3];
+      st.assemble_ms = t[4];
+      per_step[s] = st;
+    }
+  }
   if (herr & DEVERR_TIMEOUT) {
     set_error("a bounded wait on a TMA transfer gave up; results are invalid");
     return KFBI_ERR_CUDA;
@@ -1106,6 +1166,38 @@ int kfbi_get_projection(kfbi_handle* h, double* psiF_dev, double* rF_dev) {
   if (psiF_dev) KFBI_CUDA(cudaMemcpyAsync(psiF_dev, h->w.psiF, n, cudaMemcpyDeviceToDevice, h->stream));
   if (rF_dev) KFBI_CUDA(cudaMemcpyAsync(rF_dev, h->w.rF, n, cudaMemcpyDeviceToDevice, h->stream));
   return KFBI_OK;
+}
+
+int kfbi_get_warm_guess(kfbi_handle* h, double* psi0_dev) {
+  if (int rc = check_handle(h)) return rc;
+  if (!psi0_dev) {
+    set_error("null output");
+    return KFBI_ERR_ARG;
+  }
+  KFBI_CUDA(cudaMemcpyAsync(psi0_dev, h->w.psi_learn, sizeof(double) * (size_t)h->t.M, cudaMemcpyDeviceToDevice,
+                            h->stream));
+  return KFBI_OK;
+}
+
+int kfbi_training_rows(kfbi_handle* h, float* F_dev, float* T_dev) {
+  if (int rc = check_handle(h)) return rc;
+  if (!F_dev || !T_dev || h->grid.dim != 3) {
+    set_error("null output, or a 2-D handle (the network reads 3-D nodes and normals)");
+    return KFBI_ERR_ARG;
+  }
+  if (!h->proj_valid) {
+    set_error("the last Strang step did not start from the history projection");
+    return KFBI_ERR_ARG;
+  }
+  const int M = h->t.M;
+  // the sums of squares of the projection step: ||r_F||^2 and ||g||^2 from
+  // the projection, ||psi_F||^2 as the learned form computes it, so that the
+  // rows equal the network's inference input of that step
+  double* sq = h->w.proj + KFBI_HISTORY * (KFBI_HISTORY + 2);
+  int rc;
+  if ((rc = vec_dots(h, h->w.psiF, 1, M, h->w.psiF, sq))) return rc;
+  return launch_train_rows(h->stream, h->w.psi_prev, h->w.psiF, h->w.rF, h->w.g, sq, h->t.nodes, h->t.n_normal, M,
+                           2.0 * h->opts.gamma, F_dev, T_dev);
 }
 
 int kfbi_transform_pass(kfbi_handle* h, int precision, int pass, double lambda) {

@@ -149,6 +149,7 @@ struct Workspace {
   int* err = nullptr;             // device error word
   int* stop = nullptr;            // Krylov stop flag (set by the Arnoldi step)
   unsigned* counter = nullptr;    // ticket counter of the single-launch reductions
+  double* step_sq = nullptr;      // per Strang step: squared true residual, ||g||^2
   int restart_cap = 0;
 };
 
@@ -167,6 +168,7 @@ struct kfbi_handle {
   bool have_prev = false;
   int n_hist = 0;                 // completed diffusion solves (density history)
   int hist_count = 0;             // solves held in the projection history ring
+  bool proj_valid = false;        // the last Strang step started from the projection
   kfbi_mlp* warm = nullptr;       // learned warm start (not owned)
   // TMA descriptors of the float32 padded grid: [N x 32] tiles along y and z
   CUtensorMap tmap_y32, tmap_z32;
@@ -175,6 +177,8 @@ struct kfbi_handle {
   // of the host's convergence test (nullptr otherwise)
   const int* skip = nullptr;
   cudaEvent_t arn_ev[2] = {nullptr, nullptr};  // per-iteration completion events
+  int step_cap = 0;                            // Strang steps w.step_sq holds
+  std::vector<cudaEvent_t> step_events;        // phase boundaries of timed Strang steps
 };
 
 namespace kfbi {
@@ -263,6 +267,10 @@ int arnoldi_solve(kfbi_handle* h, double* small, int k, int ldh);
 int mlp_warmstart(kfbi_mlp* m, cudaStream_t st, const double* psiF, const double* rF, const double* g,
                   const double* sq, const double* nodes, const double* normals, int M, double two_gamma,
                   double* out);
+// training rows F [M][9] (raw features) and targets T [M] of one solve
+int launch_train_rows(cudaStream_t st, const double* psi, const double* psiF, const double* rF, const double* g,
+                      const double* sq, const double* nodes, const double* normals, int M, double two_gamma, float* F,
+                      float* T);
 
 int launch_react_fe(const kfbi_fhn* p, double k, double* V, double* w, int64_t n, cudaStream_t s);
 int launch_react_be(const kfbi_fhn* p, double k, double* V, double* w, int64_t n, int* err, cudaStream_t s);

@@ -1,10 +1,13 @@
-// Point-wise MLP of the learned density warm start: 9 features per interface
-// node (psi^{n-1}, psi^{n-2}, g^n, x, n), 4 hidden layers of width 128 with
-// SiLU, one output o; psi^n is predicted as psi^{n-1} + s_out o + m_out.
-// bfloat16 weights and activations, float32 accumulation on the tensor cores
-// (wmma bf16 16x16x16 fragments), float32 master weights with Adam.  The
-// network only supplies GMRES's initial guess; the solver tolerance still
-// fixes the converged density.
+// Point-wise MLP of the learned density warm start (not in the paper): 9
+// features per interface node -- the history projection psi_F, its residual
+// r_F and the right-hand side g^n, each divided by its root mean square over
+// the nodes, then the node and its unit normal -- through 4 hidden layers of
+// width 128 with SiLU to one output o; the initial density is
+// psi_L = psi_F + 2 gamma r_F + rms(r_F) (s_out o + m_out).  bfloat16 weights
+// and activations, float32 accumulation on the tensor cores (wmma bf16
+// 16x16x16 fragments), float32 master weights with Adam.  The network only
+// supplies GMRES's initial guess; the solver tolerance still fixes the
+// converged density.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <mma.h>
@@ -110,9 +113,25 @@ __global__ void k_feat_raw(const float* __restrict__ F, int B, int Bp, const flo
   X[i] = __float2bfloat16_rn(v);
 }
 
-// the same from the solver state: the projected density psi_F, its residual
-// r_F and the right-hand side g^n, each divided by its root mean square
-// (sq = their sums of squares), then the node and its normal
+// raw input row of node b from the solver state: psi_F, r_F and g^n each
+// scaled by the inverse root mean square rsqrt(sq[k] / B) (sq = their sums
+// of squares over the B nodes), then the node and its unit normal
+__device__ __forceinline__ void raw_features(const double* __restrict__ psiF, const double* __restrict__ rF,
+                                             const double* __restrict__ g, const double* __restrict__ sq,
+                                             const double* __restrict__ nodes, const double* __restrict__ normals,
+                                             int B, int b, float* f) {
+  const double s0 = rsqrt(fmax(sq[0] / B, 1e-300)), s1 = rsqrt(fmax(sq[1] / B, 1e-300)),
+               s2 = rsqrt(fmax(sq[2] / B, 1e-300));
+  f[0] = (float)(psiF[b] * s0);
+  f[1] = (float)(rF[b] * s1);
+  f[2] = (float)(g[b] * s2);
+  for (int k = 0; k < 3; ++k) {
+    f[3 + k] = (float)nodes[(size_t)b * 3 + k];
+    f[6 + k] = (float)normals[(size_t)b * 3 + k];
+  }
+}
+
+// normalised bfloat16 network input rows [Bp][16] from the solver state
 __global__ void k_feat_proj(const double* __restrict__ psiF, const double* __restrict__ rF,
                             const double* __restrict__ g, const double* __restrict__ sq,
                             const double* __restrict__ nodes, const double* __restrict__ normals, int B, int Bp,
@@ -120,21 +139,65 @@ __global__ void k_feat_proj(const double* __restrict__ psiF, const double* __res
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= Bp) return;
   float f[NIN];
-  if (b < B) {
-    const double s0 = rsqrt(fmax(sq[0] / B, 1e-300)), s1 = rsqrt(fmax(sq[1] / B, 1e-300)),
-                 s2 = rsqrt(fmax(sq[2] / B, 1e-300));
-    f[0] = (float)(psiF[b] * s0);
-    f[1] = (float)(rF[b] * s1);
-    f[2] = (float)(g[b] * s2);
-    for (int k = 0; k < 3; ++k) {
-      f[3 + k] = (float)nodes[(size_t)b * 3 + k];
-      f[6 + k] = (float)normals[(size_t)b * 3 + k];
-    }
-  }
+  if (b < B) raw_features(psiF, rF, g, sq, nodes, normals, B, b, f);
   for (int c = 0; c < KIN; ++c) {
     float v = 0.0f;
     if (b < B && c < NIN) v = (f[c] - norm[c]) / norm[NIN + c];
     X[(size_t)b * KIN + c] = __float2bfloat16_rn(v);
+  }
+}
+
+// training rows of one solve: raw features F[b][9] (the rows the network
+// reads at inference) and the target T[b] = (psi - psi_F - 2 gamma r_F) /
+// rms(r_F), the correction of the projection start in units of rms(r_F)
+__global__ void k_train_rows(const double* __restrict__ psi, const double* __restrict__ psiF,
+                             const double* __restrict__ rF, const double* __restrict__ g,
+                             const double* __restrict__ sq, const double* __restrict__ nodes,
+                             const double* __restrict__ normals, int B, double two_gamma, float* __restrict__ F,
+                             float* __restrict__ T) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  float f[NIN];
+  raw_features(psiF, rF, g, sq, nodes, normals, B, b, f);
+  for (int c = 0; c < NIN; ++c) F[(size_t)b * NIN + c] = f[c];
+  const double s1 = rsqrt(fmax(sq[1] / B, 1e-300));
+  T[b] = (float)((psi[b] - psiF[b] - two_gamma * rF[b]) * s1);
+}
+
+// normalisation moments of the training rows, one block per column (the 9
+// features of F [n][9], then the targets T [n]): mean and sample standard
+// deviation in float64, two passes (mean first, then the squared deviations);
+// a spread below 1e-12 (features) or 1e-30 (target) becomes 1.  out[c] =
+// mean, out[10 + c] = std.
+__global__ void __launch_bounds__(256) k_moments(const float* __restrict__ F, const float* __restrict__ T, int n,
+                                                 double* __restrict__ out) {
+  const int c = blockIdx.x;
+  __shared__ double red[256];
+  auto value = [&](int i) -> double { return c < NIN ? (double)F[(size_t)i * NIN + c] : (double)T[i]; };
+  auto block_sum = [&](double v) -> double {
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+      if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+      __syncthreads();
+    }
+    const double t = red[0];
+    __syncthreads();
+    return t;
+  };
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += value(i);
+  const double mean = block_sum(acc) / n;
+  acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double d = value(i) - mean;
+    acc += d * d;
+  }
+  const double var = n > 1 ? block_sum(acc) / (n - 1) : 0.0;
+  if (threadIdx.x == 0) {
+    const double sd = sqrt(var);
+    out[c] = mean;
+    out[10 + c] = sd > (c < NIN ? 1e-12 : 1e-30) ? sd : 1.0;
   }
 }
 
@@ -158,12 +221,13 @@ __global__ void k_out(const bf16* __restrict__ A, const bf16* __restrict__ w4, c
   if (lane == 0) o[row] = acc + b4[0];
 }
 
-// output-layer delta d4 = (o - t)/B and the loss partial sums
-__global__ void k_delta_out(const float* __restrict__ o, const float* __restrict__ t, int B, int Bp, float* d4,
-                            float* loss) {
+// output-layer delta d4 = (o - t)/B and the loss partial sums; the raw
+// targets T are normalised first, t = (T - m_out) / s_out (norm[18], norm[19])
+__global__ void k_delta_out(const float* __restrict__ o, const float* __restrict__ T, const float* __restrict__ norm,
+                            int B, int Bp, float* d4, float* loss) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   float r = 0.0f;
-  if (b < B) r = o[b] - t[b];
+  if (b < B) r = o[b] - (T[b] - norm[2 * NIN]) / norm[2 * NIN + 1];
   if (b < Bp) d4[b] = r / (float)B;
   float sq = r * r;
   for (int s = 16; s > 0; s >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, s);
@@ -234,8 +298,8 @@ __global__ void k_unpad_w0(const float* __restrict__ g16, float* gw0) {
   if (i < WID * NIN) gw0[i] += g16[(i / NIN) * KIN + i % NIN];
 }
 
-// psi0 = psi1 + s_out o + m_out
-// psi_L = psi_F + 2 gamma r_F + rms(r_F) * (denormalised network output)
+// psi_L = psi_F + 2 gamma r_F + rms(r_F) * (s_out o + m_out), the network
+// output denormalised in float32
 __global__ void k_predict(const double* __restrict__ psiF, const double* __restrict__ rF,
                           const double* __restrict__ sq, double two_gamma, const float* __restrict__ o,
                           const float* __restrict__ norm, double* out, int B) {
@@ -348,6 +412,8 @@ struct kfbi_mlp {
   float* Z[4] = {nullptr, nullptr, nullptr, nullptr};
   float *o = nullptr, *d4 = nullptr, *d = nullptr, *da = nullptr, *g16 = nullptr, *loss = nullptr;
   bf16* db = nullptr;
+  float* dump_d = nullptr;   // kfbi_mlp_layers: per-layer deltas go here (else null)
+  float* dump_d4 = nullptr;
   int step = 0;
   std::vector<void*> allocs;
 };
@@ -425,12 +491,16 @@ int mlp_backward(kfbi_mlp* m, const float* t, int B, int Bp) {
   KFBI_CUDA(cudaMemsetAsync(m->g, 0, sizeof(float) * off.total, st));
   KFBI_CUDA(cudaMemsetAsync(m->loss, 0, sizeof(float), st));
   KFBI_CUDA(cudaMemsetAsync(m->g16, 0, sizeof(float) * WID * KIN, st));
-  k_delta_out<<<blocks(Bp, 256), 256, 0, st>>>(m->o, t, B, Bp, m->d4, m->loss);
+  k_delta_out<<<blocks(Bp, 256), 256, 0, st>>>(m->o, t, m->norm, B, Bp, m->d4, m->loss);
   k_back_out<<<blocks((size_t)Bp * WID, 256), 256, 0, st>>>(m->d4, m->A[3], m->Z[3], m->w4, m->g + off.w[4],
                                                             m->g + off.b[4], m->d, m->db, Bp);
   int launched = 2;
+  if (m->dump_d4) KFBI_CUDA(cudaMemcpyAsync(m->dump_d4, m->d4, sizeof(float) * B, cudaMemcpyDeviceToDevice, st));
   const int kch = 1024;
   for (int l = 3; l >= 0; --l) {
+    if (m->dump_d)
+      KFBI_CUDA(cudaMemcpyAsync(m->dump_d + (size_t)(3 - l) * B * WID, m->d, sizeof(float) * B * WID,
+                                cudaMemcpyDeviceToDevice, st));
     // weight gradient d^T A_{l-1} (split over rows, float32 atomics)
     const dim3 gg(l == 0 ? 1 : WID / TILE, WID / TILE, (Bp + kch - 1) / kch);
     if (l > 0) {
@@ -464,7 +534,8 @@ int mlp_refresh(kfbi_mlp* m) {
 
 }  // namespace
 
-// warm start used by bidomain_step: psi0 = psi1 + network(psi1, psi2, g, x, n)
+// warm start used by bidomain_step: psi_L from the projection psi_F, its
+// residual r_F and g (sq = their sums of squares) through the network
 int mlp_warmstart(kfbi_mlp* m, cudaStream_t st, const double* psiF, const double* rF, const double* g,
                   const double* sq, const double* nodes, const double* normals, int M, double two_gamma,
                   double* out) {
@@ -486,11 +557,47 @@ int mlp_warmstart(kfbi_mlp* m, cudaStream_t st, const double* psiF, const double
   return rc;
 }
 
+int launch_train_rows(cudaStream_t st, const double* psi, const double* psiF, const double* rF, const double* g,
+                      const double* sq, const double* nodes, const double* normals, int M, double two_gamma, float* F,
+                      float* T) {
+  k_train_rows<<<blocks(M, 256), 256, 0, st>>>(psi, psiF, rF, g, sq, nodes, normals, M, two_gamma, F, T);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
 }  // namespace kfbi
 
 using namespace kfbi;
 
 extern "C" {
+
+int kfbi_mlp_fit_norm(const float* F_dev, const float* T_dev, int n, void* stream, float* norm_host) {
+  if (!F_dev || !T_dev || !norm_host || n < 1) {
+    set_error("null argument or no rows");
+    return KFBI_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  double* out = nullptr;
+  KFBI_CUDA(cudaMalloc((void**)&out, sizeof(double) * 20));
+  k_moments<<<NIN + 1, 256, 0, st>>>(F_dev, T_dev, n, out);
+  double h[20];
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(out);
+  if (e != cudaSuccess) {
+    set_error("normalisation moments failed: %s", cudaGetErrorString(e));
+    return KFBI_ERR_CUDA;
+  }
+  KFBI_COUNT(1);
+  for (int c = 0; c < NIN; ++c) {
+    norm_host[c] = (float)h[c];
+    norm_host[NIN + c] = (float)h[10 + c];
+  }
+  norm_host[2 * NIN] = (float)h[NIN];
+  norm_host[2 * NIN + 1] = (float)h[10 + NIN];
+  return KFBI_OK;
+}
 
 int kfbi_mlp_create(const float* params_host, const float* norm_host, int max_batch, void* stream, kfbi_mlp** out) {
   if (!params_host || !norm_host || !out || max_batch < 1) {
@@ -582,6 +689,32 @@ int kfbi_mlp_grad(kfbi_mlp* m, const float* F_dev, const float* t_dev, int B, fl
     KFBI_CUDA(cudaMemcpyAsync(grad_host, m->g, sizeof(float) * m->off.total, cudaMemcpyDeviceToHost, m->stream));
   KFBI_CUDA(cudaStreamSynchronize(m->stream));
   if (loss_host) *loss_host = 0.5f * l / (float)B;
+  return KFBI_OK;
+}
+
+int kfbi_mlp_layers(kfbi_mlp* m, const float* F_dev, const float* T_dev, int B, float* z_dev, float* o_dev,
+                    float* d_dev, float* d4_dev) {
+  if (!m || !F_dev) {
+    set_error("null argument");
+    return KFBI_ERR_ARG;
+  }
+  int Bp, rc;
+  if ((rc = mlp_prepare_raw(m, F_dev, B, &Bp))) return rc;
+  if ((rc = mlp_forward_rows(m, Bp))) return rc;
+  cudaStream_t st = m->stream;
+  if (z_dev)
+    for (int l = 0; l < 4; ++l)
+      KFBI_CUDA(cudaMemcpyAsync(z_dev + (size_t)l * B * WID, m->Z[l], sizeof(float) * B * WID,
+                                cudaMemcpyDeviceToDevice, st));
+  if (o_dev) KFBI_CUDA(cudaMemcpyAsync(o_dev, m->o, sizeof(float) * B, cudaMemcpyDeviceToDevice, st));
+  if (T_dev) {
+    m->dump_d = d_dev;
+    m->dump_d4 = d4_dev;
+    rc = mlp_backward(m, T_dev, B, Bp);
+    m->dump_d = m->dump_d4 = nullptr;
+    if (rc) return rc;
+  }
+  KFBI_CUDA(cudaStreamSynchronize(st));
   return KFBI_OK;
 }
 

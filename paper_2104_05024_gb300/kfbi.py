@@ -44,7 +44,9 @@ class Opts(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("warmstart", C.c_int), ("rel_res", C.c_double),
                 ("true_rel_res", C.c_double),
-                ("init_rel_res", C.c_double), ("ms", C.c_double)]
+                ("init_rel_res", C.c_double), ("ms", C.c_double), ("react_ms", C.c_double),
+                ("rhs_ms", C.c_double), ("warm_ms", C.c_double), ("solve_ms", C.c_double),
+                ("assemble_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -68,7 +70,8 @@ EXPORTS = [
     "kfbi_mlp_create", "kfbi_mlp_destroy", "kfbi_mlp_get", "kfbi_mlp_forward", "kfbi_mlp_grad",
     "kfbi_mlp_train_step", "kfbi_set_warmstart", "kfbi_get_densities", "kfbi_set_densities",
     "kfbi_get_history", "kfbi_set_history", "kfbi_get_projection", "kfbi_bidomain_step_stim",
-    "kfbi_selftest_bounded_wait",
+    "kfbi_selftest_bounded_wait", "kfbi_get_warm_guess", "kfbi_training_rows", "kfbi_mlp_fit_norm",
+    "kfbi_mlp_layers",
 ]
 
 
@@ -78,7 +81,7 @@ class MLP:
     def __init__(self, params, norm, max_batch):
         lib = load()
         self.params = np.ascontiguousarray(params, dtype=np.float32)
-        self.norm = np.ascontiguousarray(norm, dtype=np.float32)
+        self.norm = np.ascontiguousarray(norm, dtype=np.float32)   # the normalisation vector (host copy)
         if self.params.size != lib.kfbi_mlp_num_params() or self.norm.size != 20:
             raise ValueError("parameter or normalisation vector has the wrong size")
         h = C.c_void_p()
@@ -103,10 +106,34 @@ class MLP:
         _check(load().kfbi_mlp_get(self._h, out.ctypes.data_as(C.POINTER(C.c_float))))
         return out
 
+    @staticmethod
+    def fit_norm(F, T):
+        """Normalisation vector [mean[9], std[9], target mean, target std] of
+        training rows F [n, 9] and raw targets T [n] (CUDA float32)."""
+        out = np.empty(20, np.float32)
+        _check(load().kfbi_mlp_fit_norm(_ptr(F, "float32"), _ptr(T, "float32"), F.shape[0], _stream(),
+                                        out.ctypes.data_as(C.POINTER(C.c_float))))
+        return out
+
     def forward(self, F, o):
         _check(load().kfbi_mlp_forward(self._h, _ptr(F, "float32"), F.shape[0], _ptr(o, "float32")))
 
+    def layers(self, F, T=None):
+        """Hidden pre-activations z [4, B, 128], output o [B] and, with raw
+        targets T, the deltas dL/dz of the hidden layers [4, B, 128] (order
+        l = 3..0) and dL/do [B] of the training path (device float32)."""
+        import torch
+        B = F.shape[0]
+        z = torch.empty((4, B, 128), dtype=torch.float32, device=F.device)
+        o = torch.empty(B, dtype=torch.float32, device=F.device)
+        d = torch.empty_like(z) if T is not None else None
+        d4 = torch.empty_like(o) if T is not None else None
+        _check(load().kfbi_mlp_layers(self._h, _ptr(F, "float32"), _ptr(T, "float32"), B, _ptr(z, "float32"),
+                                      _ptr(o, "float32"), _ptr(d, "float32"), _ptr(d4, "float32")))
+        return z, o, d, d4
+
     def grad(self, F, t):
+        """Loss and gradient for raw features F [B, 9] and raw targets t [B]."""
         g = np.empty(load().kfbi_mlp_num_params(), np.float32)
         loss = C.c_float()
         _check(load().kfbi_mlp_grad(self._h, _ptr(F, "float32"), _ptr(t, "float32"), F.shape[0], C.byref(loss),
@@ -185,6 +212,10 @@ def load(path: str = LIB_PATH):
     lib.kfbi_get_projection.argtypes = [vp, vp, vp]
     lib.kfbi_bidomain_step_stim.argtypes = [vp, C.POINTER(FHNStruct), vp, vp, vp, vp, ip, C.POINTER(Stats)]
     lib.kfbi_selftest_bounded_wait.argtypes = [ip, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    lib.kfbi_get_warm_guess.argtypes = [vp, vp]
+    lib.kfbi_training_rows.argtypes = [vp, vp, vp]
+    lib.kfbi_mlp_fit_norm.argtypes = [vp, vp, ip, vp, fp]
+    lib.kfbi_mlp_layers.argtypes = [vp, vp, vp, ip, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("kfbi_last_error", "kfbi_destroy", "kfbi_launch_count", "kfbi_mlp_destroy"):
             getattr(lib, name).restype = C.c_int
@@ -345,6 +376,15 @@ class KFBI:
         self.set_opts()
         _check(load().kfbi_get_projection(self._h, _ptr(psiF), _ptr(rF)))
 
+    def get_warm_guess(self, psi0):
+        self.set_opts()
+        _check(load().kfbi_get_warm_guess(self._h, _ptr(psi0)))
+
+    def training_rows(self, F, T):
+        """Rows F [M, 9] and raw targets T [M] (CUDA float32) of the last step."""
+        self.set_opts()
+        _check(load().kfbi_training_rows(self._h, _ptr(F, "float32"), _ptr(T, "float32")))
+
     def checkpoint(self, V, w):
         """Host copy of everything a resumed run needs: the state (V, w) and
         the density history with its solve count (the caller stores it, e.g.
@@ -401,8 +441,10 @@ class KFBI:
                allow=(ERR_NOT_CONVERGED,))
         return st.as_dict()
 
-    def bidomain_step(self, fhn, V, w, ue=None, nsteps=1, istim=None, **opts):
-        """Strang steps; istim (device field) adds the virtual-electrode stimulus."""
+    def bidomain_step(self, fhn, V, w, ue=None, nsteps=1, istim=None, log=None, **opts):
+        """Strang steps; istim (device field) adds the virtual-electrode
+        stimulus.  Returns one stats dict per step; log (a path or a text
+        file) receives them as JSON lines, numbered across calls."""
         self.set_opts(**opts)
         stats = (Stats * max(1, nsteps))()
         if istim is None:
@@ -411,7 +453,26 @@ class KFBI:
         else:
             _check(load().kfbi_bidomain_step_stim(self._h, C.byref(fhn_struct(fhn)), _ptr(istim), _ptr(V), _ptr(w),
                                                   _ptr(ue), nsteps, stats), allow=(ERR_NOT_CONVERGED,))
-        return [stats[i].as_dict() for i in range(nsteps)]
+        out = [stats[i].as_dict() for i in range(nsteps)]
+        first = getattr(self, "_steps_done", 0)
+        self._steps_done = first + nsteps
+        if log is not None:
+            write_step_log(log, out, first)
+        return out
+
+
+def write_step_log(log, stats, first=0):
+    """One JSON line per Strang step: GMRES iterations, outer refinements,
+    the warm start kept, initial / final / true relative residuals, and the
+    phase times (device, ms)."""
+    import json
+    lines = "".join(json.dumps(dict({"step": first + i + 1}, **st)) + "\n" for i, st in enumerate(stats))
+    if hasattr(log, "write"):
+        log.write(lines)
+        log.flush()
+    else:
+        with open(log, "a") as f:
+            f.write(lines)
 
 
 def react_fe(fhn, k, V, w):

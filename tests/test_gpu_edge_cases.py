@@ -62,3 +62,77 @@ def test_bad_arguments_rejected():
     with pytest.raises(K.KFBIError) as e:
         K.selftest_bounded_wait(0)
     assert e.value.code == K.ERR_ARG
+
+
+# ------------------------------------------- failures injected on the host
+
+@pytest.mark.parametrize("prec", [K.FP64, K.MIXED])
+def test_nan_in_host_data_returns_err_nan(prec):
+    """A NaN in the caller's source (or Neumann data) spreads through the box
+    solve into g; the solver's first residual is then not finite and the
+    call returns KFBI_ERR_NAN (every loop on the way is bounded)."""
+    geom, grid = G.ellipse_config0(128), C.Grid(2, 64)
+    g = K.KFBI(geom, grid, tol=1e-10)
+    f, u_ex, gN = C.manufactured(geom, grid, 60.0)
+    u = torch.empty(grid.shape, dtype=torch.float64, device=DEV)
+    psi = torch.zeros(geom.M, dtype=torch.float64, device=DEV)
+    for bad in ("f", "gN"):
+        fb, gb = f.copy(), gN.copy()
+        if bad == "f":
+            fb[10, 20] = np.nan
+        else:
+            gb[3] = np.nan
+        with pytest.raises(K.KFBIError) as e:
+            g.solve_neumann(torch.tensor(fb, device=DEV), torch.tensor(gb, device=DEV), u, psi.zero_(), 60.0,
+                            precision=prec)
+        assert e.value.code == K.ERR_NAN
+    # the handle and the context stay usable
+    st = g.solve_neumann(torch.tensor(f, device=DEV), torch.tensor(gN, device=DEV), u, psi.zero_(), 60.0,
+                         precision=prec)
+    assert st["rel_res"] <= 1e-10
+    V = torch.tensor(C.ball_stimulus(grid, (-0.4, 0.0), 0.1), device=DEV)
+    V[5, 5] = float("nan")
+    with pytest.raises(K.KFBIError) as e:
+        g.bidomain_step(C.FHN_CONFIG, V, torch.zeros_like(V), None, nsteps=1, precision=prec)
+    assert e.value.code == K.ERR_NAN
+    g.close()
+
+
+def test_newton_cap_returns_err_newton():
+    """The backward-Euler Newton iteration stops at its cap (|dV| never below
+    1e-10 for a NaN state) and the call returns KFBI_ERR_NEWTON; the next call
+    on clean data succeeds."""
+    V = torch.linspace(-0.2, 1.1, 4096, dtype=torch.float64, device=DEV)
+    w = torch.zeros_like(V)
+    V[100] = float("nan")
+    with pytest.raises(K.KFBIError) as e:
+        K.react_be(C.FHN_CONFIG, 0.025, V, w)
+    assert e.value.code == K.ERR_NEWTON
+    V = torch.linspace(-0.2, 1.1, 4096, dtype=torch.float64, device=DEV)
+    K.react_be(C.FHN_CONFIG, 0.025, V, w)
+    assert bool(torch.isfinite(V).all())
+
+
+@pytest.mark.parametrize("prec,tol", [(K.FP64, 1e-10), (K.MIXED, 1e-8)])
+def test_step_record_true_residual_and_log(tmp_path, prec, tol):
+    """Every Strang step reports the recomputed true residual of the final
+    u = v_V + v_B(psi) (not only the solver's estimate) and the device time of
+    its phases; the log gets one JSON line per step."""
+    import json
+    geom, grid, cfg, V0, w0 = C.config0()
+    h = K.KFBI(geom, grid, tol=tol, precision=prec, warm=K.WARM_PROJECTION)
+    V, w = torch.tensor(V0, device=DEV), torch.tensor(w0, device=DEV)
+    log = tmp_path / "steps.jsonl"
+    st = h.bidomain_step(C.FHN_CONFIG, V, w, None, nsteps=3, log=str(log))
+    st += h.bidomain_step(C.FHN_CONFIG, V, w, None, nsteps=2, log=str(log))
+    h.close()
+    lines = [json.loads(x) for x in log.read_text().splitlines()]
+    assert [x["step"] for x in lines] == [1, 2, 3, 4, 5]
+    for s, x in zip(st, lines):
+        assert s["rel_res"] <= tol
+        # the solver's estimate and the recomputed residual agree to the
+        # accuracy of the box solves
+        assert 0.0 <= s["true_rel_res"] < 10.0 * tol
+        for k in ("react_ms", "rhs_ms", "warm_ms", "solve_ms", "assemble_ms"):
+            assert s[k] >= 0.0 and x[k] == s[k]
+        assert s["solve_ms"] > 0.0 and x["iters"] == s["iters"]

@@ -3,9 +3,11 @@
 * prolate shell at 256^3 (the Strang benchmark's workload): setup bit-exact,
   box solve, correction, interface limit and A psi against the oracle; one
   float64 Strang step (GMRES to 1e-12 on both sides) within 1e-10; three
-  steps of the learned warm-start form at the benchmark's 1e-8 GMRES residual
-  within 1e-7 of the oracle's 1e-10 run (the residual times a modest condition
-  number of the second-kind equation, with a tenfold margin);
+  steps of the learned warm-start form with a trained (non-zero) network at
+  the benchmark's 1e-8 GMRES residual within 1e-7 of the oracle's 1e-10 run
+  (the residual times a modest condition number of the second-kind equation,
+  with a tenfold margin), and its start psi_L against the oracle's
+  prediction;
 * the same shell at 384^3 (radix-3 transform stage) and 512^3 (the largest
   grid of the single-solve sweep), Gaussian-bump right-hand side: setup
   bit-exact, float64 box solve against the oracle, and the GPU's Neumann
@@ -24,10 +26,10 @@ pytestmark = pytest.mark.gpu
 
 from kfbi_workloads import configs as C, geometry as G  # noqa: E402
 from oracle.bidomain import lam_of  # noqa: E402
-from oracle import boxsolve, mlp as OM  # noqa: E402
+from oracle import boxsolve, warmstart as OW  # noqa: E402
 from oracle.kfbi import KFBI as OK  # noqa: E402
 from oracle.bidomain import Bidomain  # noqa: E402
-from paper_2104_05024_gb300 import kfbi as K  # noqa: E402
+from paper_2104_05024_gb300 import kfbi as K, warmstart as WS  # noqa: E402
 
 DEV = torch.device("cuda:0")
 TOL64 = 1e-10
@@ -115,25 +117,89 @@ def test_shell256_strang_fp64(shell256):
     assert rel(wd.cpu().numpy(), w) < TOL64
 
 
+def _trained_network():
+    """A network trained (briefly, on the GPU) on rows of two 64^3 shell runs
+    from training stimuli: its output is not zero."""
+    geom, grid, cfg, _, _ = C.config2(N=64)
+    Fs, Ts = [], []
+    for c in C.midwall_centers(C.TRAIN_SEEDS[:2]):
+        h = K.KFBI(geom, grid, tol=cfg.tol, precision=K.MIXED)
+        V = cuda(C.ball_stimulus(grid, c, 0.1))
+        F, T = WS.collect(h, C.FHN_CONFIG, V, torch.zeros_like(V), 8)
+        Fs.append(F)
+        Ts.append(T)
+        h.close()
+    F, T = torch.cat(Fs), torch.cat(Ts)
+    norm = WS.fit_norm(F, T)
+    m = K.MLP(WS.init_params(0), norm, 49156 + 64)
+    WS.train(m, F, T, epochs=10, batch=1024, lr=2e-3)
+    return m
+
+
 def test_shell256_strang_learned_form(shell256):
-    """The benchmark's form (float32 transforms, GMRES-IR, network guess
-    judged by its residual) at the benchmark's 1e-8 GMRES tolerance."""
+    """The benchmark's form (float32 transforms, GMRES-IR, a trained network's
+    guess judged by its residual) at the benchmark's 1e-8 GMRES tolerance,
+    three steps, against the oracle's 1e-10 run; the steps after the first
+    start from psi_L, which is checked against the oracle's prediction from
+    the GPU's projection and network output."""
     geom, grid, cfg, V0, w0, o, g = shell256
     V, w = _oracle_steps(geom, grid, cfg, V0, w0, 3, 1e-10)
-    norm = np.concatenate([np.zeros(9), np.ones(9), [0.0, 1.0]]).astype(np.float32)
-    m = K.MLP(OM.init(0), norm, geom.M)
+    m = _trained_network()
     h = K.KFBI(geom, grid, sigma_i=cfg.sigma_i, sigma_e=cfg.sigma_e, dt=cfg.dt, tol=cfg.tol,
                precision=K.MIXED_LEARNED)
     h.set_warmstart(m)
     Vd, wd = cuda(V0), cuda(w0)
     st = h.bidomain_step(C.FHN_CONFIG, Vd, wd, None, nsteps=3)
+    M = geom.M
+    psiF, rF, psi0 = (torch.empty(M, dtype=torch.float64, device=DEV) for _ in range(3))
+    h.get_projection(psiF, rF)
+    h.get_warm_guess(psi0)
+    F = torch.empty((M, 9), dtype=torch.float32, device=DEV)
+    T = torch.empty(M, dtype=torch.float32, device=DEV)
+    h.training_rows(F, T)
+    out = torch.empty(M, dtype=torch.float32, device=DEV)
+    m.forward(F, out)
+    norm = m.norm
+    torch.cuda.synchronize()
+    ref = OW.prediction(psiF.cpu().numpy(), rF.cpu().numpy(), out.cpu().numpy(), norm)
     h.close()
     m.close()
     assert all(s["rel_res"] <= cfg.tol for s in st)
+    o_max = float(out.abs().max())
     print(f"learned form vs oracle, 3 steps at 256^3: V {rel(Vd.cpu().numpy(), V):.2e}, "
-          f"w {rel(wd.cpu().numpy(), w):.2e}, network guess kept {[s['warmstart'] for s in st]}")
+          f"w {rel(wd.cpu().numpy(), w):.2e}, network guess kept {[s['warmstart'] for s in st]}, "
+          f"max |network output| {o_max:.3f}")
+    assert o_max > 1e-3
+    assert rel(psi0.cpu().numpy(), ref) < 1e-12
     assert rel(Vd.cpu().numpy(), V) < TOL_FORMS
     assert rel(wd.cpu().numpy(), w) < TOL_FORMS
+
+
+def test_shell256_forms_200_steps():
+    """Config 2's full run (200 Strang steps at 256^3): the learned form
+    (float32 transforms, GMRES-IR, trained network, tol 1e-8) against the
+    plain float64 GPU path at the same tolerance, field by field (V, w and
+    u_e), relative L-infinity within 1e-6."""
+    geom, grid, cfg, V0, w0 = C.config2(N=256, steps=200)
+    m = _trained_network()
+    out = {}
+    for name, prec in (("fp64", K.FP64), ("learned", K.MIXED_LEARNED)):
+        h = K.KFBI(geom, grid, sigma_i=cfg.sigma_i, sigma_e=cfg.sigma_e, dt=cfg.dt, tol=cfg.tol, precision=prec,
+                   max_iter=400)
+        if prec == K.MIXED_LEARNED:
+            h.set_warmstart(m)
+        V, w = cuda(V0), cuda(w0)
+        ue = torch.empty_like(V)
+        st = h.bidomain_step(C.FHN_CONFIG, V, w, ue, nsteps=cfg.steps)
+        h.close()
+        assert all(s["rel_res"] <= cfg.tol for s in st)
+        out[name] = (V.cpu().numpy(), w.cpu().numpy(), ue.cpu().numpy(), st)
+    m.close()
+    diffs = {f: rel(out["learned"][k], out["fp64"][k]) for k, f in enumerate(("V", "w", "ue"))}
+    its = {k: float(np.mean([s["iters"] for s in v[3]])) for k, v in out.items()}
+    print(f"200 steps at 256^3, learned form vs float64: relative max differences {diffs}, "
+          f"GMRES iterations per step {its}")
+    assert all(d < 1e-6 for d in diffs.values())
 
 
 # -------------------------------------------------- shell 384^3 and 512^3

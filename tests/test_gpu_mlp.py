@@ -1,15 +1,18 @@
 """GPU parity of the learned warm start's network and its effect.
 
-* forward outputs and every parameter's gradient against the CPU oracle MLP
-  (same bfloat16 rounding of weights and activations, float32 accumulation;
-  the remaining differences are summation order and activations that round to
-  the other bfloat16 neighbour), relative L2 within 1e-2 (forward) and 3e-2
-  (gradients);
+* every layer of the forward pass (training path), the output, the deltas of
+  the backward pass and every parameter's gradient, element by element
+  against the CPU oracle MLP applied to the GPU's own inputs of each layer,
+  within bounds derived from bfloat16 rounding and float32 summation order
+  (tests/mlp_bounds.py); the fused inference kernel against the training
+  path's output;
 * Adam training on the GPU lowers the loss;
 * with a network trained on solves of shell runs from four stimulus
-  locations, a run from a held-out location needs fewer GMRES iterations
-  than with the previous-density start, and the converged states agree with
-  that start's to the solver tolerance.
+  locations, runs from a held-out location: GMRES iterations of the
+  previous-density start (the paper's), the history projection and the
+  learned correction of the projection.  The learned start needs fewer
+  iterations than the previous density; against the projection it does not
+  gain (the measured ratio is printed and bounded, see the design notes).
 """
 import numpy as np
 import pytest
@@ -18,6 +21,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
+import mlp_bounds as MB  # noqa: E402
 from kfbi_workloads import configs as C  # noqa: E402
 from oracle import mlp as OM  # noqa: E402
 from paper_2104_05024_gb300 import kfbi as K, warmstart as WS  # noqa: E402
@@ -31,36 +35,55 @@ def _case(seed=0, B=700):
     flat = OM.init(seed) + 0.05 * rng.standard_normal(OM.n_params()).astype(np.float32)
     norm = np.concatenate([rng.uniform(-0.5, 0.5, 9), rng.uniform(0.5, 2.0, 9), [0.1, 2.0]]).astype(np.float32)
     F = rng.standard_normal((B, 9)).astype(np.float32)
-    t = rng.standard_normal(B).astype(np.float32)
-    return flat, norm, F, t
+    T = rng.standard_normal(B).astype(np.float32)
+    return flat, norm, F, T
 
 
-def _rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
-
-
-def test_forward_matches_oracle():
+def test_forward_layers_elementwise():
     flat, norm, F, _ = _case(1)
     m = K.MLP(flat, norm, 1024)
-    o = torch.empty(F.shape[0], dtype=torch.float32, device=DEV)
-    m.forward(torch.tensor(F, device=DEV), o)
+    Fd = torch.tensor(F, device=DEV)
+    z, o, _, _ = m.layers(Fd)
+    report = {}
+    MB.check_forward(flat, OM.normalise(F, norm), z.cpu().numpy(), o.cpu().numpy(), report)
+    # the fused inference kernel: same fragments, order and epilogue per element
+    o2 = torch.empty_like(o)
+    m.forward(Fd, o2)
+    d = float((o2 - o).abs().max())
+    print(f"per-layer (max |diff|, max bound, violations): {report}; fused vs layered max |diff| {d:.2e}")
+    assert d <= 1e-5 * (1.0 + float(o.abs().max()))
+    # the whole network against the oracle's, for scale: flips of bfloat16
+    # roundings compound over the layers, so this is a loose sanity check
     ref = OM.forward(flat, OM.normalise(F, norm))
-    assert _rel(o.cpu().numpy(), ref) < 1e-2
+    assert np.linalg.norm(o.cpu().numpy() - ref) < 1e-2 * np.linalg.norm(ref)
     m.close()
 
 
-def test_gradients_match_oracle():
-    flat, norm, F, t = _case(2, B=512)
+def test_backward_layers_and_gradients_elementwise():
+    flat, norm, F, T = _case(2, B=512)
     m = K.MLP(flat, norm, 1024)
-    loss, g = m.grad(torch.tensor(F, device=DEV), torch.tensor(t, device=DEV))
-    loss_ref, g_ref = OM.loss_and_grad(flat, OM.normalise(F, norm), t)
-    assert abs(loss - loss_ref) <= 1e-2 * loss_ref
-    off = 0
-    for s in OM.shapes():
-        k = int(np.prod(s))
-        assert _rel(g[off:off + k], g_ref[off:off + k]) < 3e-2, (s, _rel(g[off:off + k], g_ref[off:off + k]))
-        off += k
+    Fd, Td = torch.tensor(F, device=DEV), torch.tensor(T, device=DEV)
+    z, o, d, d4 = m.layers(Fd, Td)
+    loss, g = m.grad(Fd, Td)
+    X = OM.normalise(F, norm)
+    t = ((T - norm[18]) / norm[19]).astype(np.float32)
+    report = {}
+    zn, on = z.cpu().numpy(), o.cpu().numpy()
+    MB.check_forward(flat, X, zn, on, report)
+    MB.check_backward(flat, X, t, zn, on, d.cpu().numpy(), d4.cpu().numpy(), g, loss, report)
+    print(f"per-layer (max |diff|, max bound, violations): {report}")
     m.close()
+
+
+def test_fit_norm_matches_oracle():
+    from oracle import warmstart as OW
+    rng = np.random.default_rng(7)
+    F = (rng.standard_normal((5000, 9)) * rng.uniform(0.1, 3.0, 9) + rng.uniform(-2, 2, 9)).astype(np.float32)
+    F[:, 4] = 0.25                                   # zero spread -> 1
+    T = (0.3 * rng.standard_normal(5000) + 0.1).astype(np.float32)
+    got = K.MLP.fit_norm(torch.tensor(F, device=DEV), torch.tensor(T, device=DEV))
+    ref = OW.fit_norm(F, T)
+    assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max()
 
 
 def test_training_lowers_loss():
@@ -83,29 +106,29 @@ def _run(h, V0, w0, steps, precision):
     return V, w, st
 
 
-def test_learned_warm_start_reduces_iterations():
+def test_learned_warm_start_against_previous_and_projection():
     """Runs from a held-out stimulus: the previous-density start (the paper's),
     the history projection, and the projection corrected by a network trained
     on four other stimulus runs.  The learned start needs fewer GMRES
-    iterations than the previous-density start; its gain over the projection
-    alone is printed (the residual judge keeps the network's guess when its
-    residual is smaller, which is not always fewer iterations)."""
+    iterations than the previous density.  It does not beat the projection it
+    corrects: the residual judge keeps the network's guess when its residual
+    is smaller, but that guess's error is spread over more modes of A, which
+    GMRES resolves more slowly.  The measured ratio is printed and bounded."""
     N, steps = 64, 24
     geom, grid, cfg, _, _ = C.config2(N=N, steps=steps)
-    normals = C.analytic_normals(geom)
     Fs, Ts = [], []
     for c in C.midwall_centers(C.TRAIN_SEEDS[:4]):
         h = K.KFBI(geom, grid, tol=cfg.tol, precision=K.MIXED)
         V = torch.tensor(C.ball_stimulus(grid, c, 0.1), device=DEV)
         w = torch.zeros_like(V)
-        F, T = WS.collect(h, C.FHN_CONFIG, V, w, steps, geom.nodes, normals)
+        F, T = WS.collect(h, C.FHN_CONFIG, V, w, steps)
         Fs.append(F)
         Ts.append(T)
         h.close()
     F, T = torch.cat(Fs), torch.cat(Ts)
     norm = WS.fit_norm(F, T)
-    m = K.MLP(OM.init(0), norm, max(8192, geom.M))
-    losses = WS.train(m, F, T, norm, epochs=20, batch=4096, lr=2e-3)
+    m = K.MLP(WS.init_params(0), norm, max(8192, geom.M))
+    losses = WS.train(m, F, T, epochs=20, batch=4096, lr=2e-3)
     assert losses[-1] < 0.5 * losses[0]
     c = C.midwall_centers(C.HELDOUT_SEEDS[:1])[0]
     V0 = C.ball_stimulus(grid, c, 0.1)
@@ -120,8 +143,11 @@ def test_learned_warm_start_reduces_iterations():
         hh.close()
     its = {k: sum(s["iters"] for s in r[2][2:]) for k, r in runs.items()}
     used = sum(s["warmstart"] for s in runs["learned"][2])
-    print(f"GMRES iterations, steps 3..{steps}: {its} (network guess kept {used}x)")
+    ratio = its["learned"] / its["projection"]
+    print(f"GMRES iterations, steps 3..{steps}: {its} (network guess kept {used}x); "
+          f"learned / projection = {ratio:.3f}")
     assert its["learned"] < its["previous"] and its["projection"] < its["previous"]
+    assert ratio < 1.25
     assert all(s["rel_res"] <= cfg.tol for r in runs.values() for s in r[2])
     Vp = runs["previous"][0]
     scale = float(Vp.abs().max())
