@@ -818,6 +818,122 @@ int run_pass(kfbi_handle* h, int pass, double lambda, T* work, const T* mu1, con
   return KFBI_OK;
 }
 
+// ------------------------------------------ coupled anisotropic solve pass
+// Middle pass of the coupled box solve (3-D: along z, 2-D: along y) on the
+// two padded float64 work grids a (intracellular) and b (extracellular):
+// forward DST of both tiles, the per-mode 2 x 2 solve of Eq. pde1 with
+// diagonal conductivities (Section 5.2, Eq. FDE),
+//   [A_i - kappa, kappa; kappa, A_e - kappa] (v_i, v_e) = (r_i, r_e),
+//   A_c = sum_a d_c,a mu1(p_a),
+// scaled by (2/N)^d, then the inverse DST of both tiles.
+template <int N, int DIM>
+__global__ void __launch_bounds__(NT) k_strided_coupled(double* __restrict__ a, double* __restrict__ b,
+                                                        size_t row_stride, size_t plane_stride, int qoff,
+                                                        const double* __restrict__ mu1, Coupling cp,
+                                                        const double* __restrict__ tw_g,
+                                                        const int* __restrict__ skip) {
+  using C = Cfg<double, N>;
+  constexpr int W = C::W, RS = C::RS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sa = reinterpret_cast<double*>(smem_raw);
+  double* sb = sa + N * RS;
+  double* tot = sb + N * RS;
+  double* tw = tot + C::G * W;
+  const bool skipped = skip != nullptr && *skip != 0;
+  load_twiddles<double, N>(tw, tw_g);
+  if (skipped) return;
+  const int x0 = blockIdx.x * W;
+  const int q = blockIdx.y + qoff;
+  double* ba = a + (size_t)q * plane_stride + x0;
+  double* bb = b + (size_t)q * plane_stride + x0;
+  for (int idx = threadIdx.x; idx < N * W; idx += NT) {
+    const int c = idx % W, k = idx / W;
+    copy_async(&sa[k * RS + c], &ba[(size_t)k * row_stride + c]);
+    copy_async(&sb[k * RS + c], &bb[(size_t)k * row_stride + c]);
+  }
+  copy_async_wait();
+  __syncthreads();
+  dst1_tile<C>(sa, tw, tot);
+  dst1_tile<C>(sb, tw, tot);
+  const double muq = DIM == 3 ? mu1[q] : 0.0;
+  const double kap = cp.kappa;
+  for (int idx = threadIdx.x; idx < N * W; idx += NT) {
+    const int c = idx % W, k = idx / W, p = x0 + c;
+    double vi = 0.0, ve = 0.0;
+    if (k > 0 && p > 0) {
+      // modes: x = p; 3-D y = plane q, z = k; 2-D y = k
+      const double mx = mu1[p], my = DIM == 3 ? muq : mu1[k], mz = DIM == 3 ? mu1[k] : 0.0;
+      const double ai = cp.di[0] * mx + cp.di[1] * my + cp.di[2] * mz - kap;
+      const double ae = cp.de[0] * mx + cp.de[1] * my + cp.de[2] * mz - kap;
+      const double sc = cp.scale / (ai * ae - kap * kap);
+      const double ri = sa[k * RS + c], re = sb[k * RS + c];
+      vi = (ae * ri - kap * re) * sc;
+      ve = (ai * re - kap * ri) * sc;
+    }
+    sa[k * RS + c] = vi;
+    sb[k * RS + c] = ve;
+  }
+  __syncthreads();
+  dst1_tile<C>(sa, tw, tot);
+  dst1_tile<C>(sb, tw, tot);
+  for (int idx = threadIdx.x; idx < N * W; idx += NT) {
+    const int c = idx % W, k = idx / W;
+    ba[(size_t)k * row_stride + c] = sa[k * RS + c];
+    bb[(size_t)k * row_stride + c] = sb[k * RS + c];
+  }
+}
+
+template <int N>
+int run_solve_coupled(kfbi_handle* h, const SolveArgs& si, const SolveArgs& se, const Coupling& cp0, double* wa,
+                      double* wb) {
+  using C = Cfg<double, N>;
+  constexpr int W = C::W;
+  const size_t smem = C::smem_elems * sizeof(double);
+  const size_t smem2 = (2 * (size_t)N * C::RS + (size_t)C::G * W + 4 * (size_t)N) * sizeof(double);
+  const int dim = h->grid.dim;
+  cudaStream_t st = h->stream;
+  const Tables& t = h->t;
+  const double* mu1 = t.mu;
+  const double* tw = t.tw64;
+  Coupling cp = cp0;
+  cp.scale = dim == 3 ? (2.0 / N) * (2.0 / N) * (2.0 / N) : (2.0 / N) * (2.0 / N);
+  int rc;
+  const dim3 grid(N / W, dim == 3 ? N - 1 : 1);
+  if (dim == 3) {
+    if ((rc = prep(k_xfwd<double, N, 3>, smem))) return rc;
+    if ((rc = prep(k_strided_coupled<N, 3>, smem2))) return rc;
+    if ((rc = prep(k_xinv<double, N, 3>, smem))) return rc;
+    k_xfwd<double, N, 3><<<grid, NT, smem, st>>>(wa, si.src, si.alpha, nullptr, si.corr, t.irr, t.line_start, tw, h->skip);
+    k_xfwd<double, N, 3><<<grid, NT, smem, st>>>(wb, se.src, se.alpha, nullptr, se.corr, t.irr, t.line_start, tw, h->skip);
+    for (double* w : {wa, wb})
+      if ((rc = launch_strided3<double, N>(h, 0, false, w, mu1, 0.0, 1.0, tw))) return rc;
+    const size_t NN = (size_t)N * N;
+    k_strided_coupled<N, 3><<<grid, NT, smem2, st>>>(wa, wb, NN, N, 1, mu1, cp, tw, h->skip);
+    for (double* w : {wa, wb})
+      if ((rc = launch_strided3<double, N>(h, 0, false, w, mu1, 0.0, 1.0, tw))) return rc;
+  } else {
+    if ((rc = prep(k_xfwd<double, N, 2>, smem))) return rc;
+    if ((rc = prep(k_strided_coupled<N, 2>, smem2))) return rc;
+    if ((rc = prep(k_xinv<double, N, 2>, smem))) return rc;
+    k_xfwd<double, N, 2><<<grid, NT, smem, st>>>(wa, si.src, si.alpha, nullptr, si.corr, t.irr, t.line_start, tw, h->skip);
+    k_xfwd<double, N, 2><<<grid, NT, smem, st>>>(wb, se.src, se.alpha, nullptr, se.corr, t.irr, t.line_start, tw, h->skip);
+    k_strided_coupled<N, 2><<<grid, NT, smem2, st>>>(wa, wb, N, 0, 0, mu1, cp, tw, h->skip);
+  }
+  if (dim == 3) {
+    k_xinv<double, N, 3><<<grid, NT, smem, st>>>(wa, si.keep || si.out_user == nullptr, si.out_user, si.aux, si.beta,
+                                                  si.gamma, tw, h->skip);
+    k_xinv<double, N, 3><<<grid, NT, smem, st>>>(wb, se.keep || se.out_user == nullptr, se.out_user, se.aux, se.beta,
+                                                  se.gamma, tw, h->skip);
+  } else {
+    k_xinv<double, N, 2><<<grid, NT, smem, st>>>(wa, si.keep || si.out_user == nullptr, si.out_user, si.aux, si.beta,
+                                                  si.gamma, tw, h->skip);
+    k_xinv<double, N, 2><<<grid, NT, smem, st>>>(wb, se.keep || se.out_user == nullptr, se.out_user, se.aux, se.beta,
+                                                  se.gamma, tw, h->skip);
+  }
+  KFBI_CHECK_LAUNCH_N(dim == 3 ? 9 : 5);
+  return KFBI_OK;
+}
+
 template <typename T>
 int dispatch(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1, const T* tw) {
   switch (h->grid.N) {
@@ -902,6 +1018,22 @@ int box_solve64(kfbi_handle* h, const SolveArgs& a, double* work) {
 
 int box_solve32(kfbi_handle* h, const SolveArgs& a, float* work) {
   return dispatch<float>(h, a, work, h->t.mu32, h->t.tw32);
+}
+
+int box_solve_coupled64(kfbi_handle* h, const SolveArgs& si, const SolveArgs& se, const Coupling& cp, double* wa,
+                        double* wb) {
+  switch (h->grid.N) {
+    case 16: return run_solve_coupled<16>(h, si, se, cp, wa, wb);
+    case 32: return run_solve_coupled<32>(h, si, se, cp, wa, wb);
+    case 64: return run_solve_coupled<64>(h, si, se, cp, wa, wb);
+    case 128: return run_solve_coupled<128>(h, si, se, cp, wa, wb);
+    case 256: return run_solve_coupled<256>(h, si, se, cp, wa, wb);
+    case 384: return run_solve_coupled<384>(h, si, se, cp, wa, wb);
+    case 512: return run_solve_coupled<512>(h, si, se, cp, wa, wb);
+    default:
+      set_error("unsupported grid size N=%d for the coupled solve", h->grid.N);
+      return KFBI_ERR_ARG;
+  }
 }
 
 namespace {

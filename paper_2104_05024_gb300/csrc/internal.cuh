@@ -110,6 +110,9 @@ struct Tables {
   double* n_normal = nullptr;     // [M][3] outward normals at the nodes
   double* ds = nullptr;           // [M] boundary quadrature weights
   double area = 0.0;              // their sum |Gamma|
+  // diagonal conductivity of the component whose correction and limit rows
+  // these are (1, 1, 1 for the scalar problem)
+  double cond[3] = {1.0, 1.0, 1.0};
 };
 
 struct Workspace {
@@ -220,6 +223,17 @@ struct SolveArgs {
   bool keep = true;               // the x inverse pass also writes the padded work grid
 };
 int box_solve64(kfbi_handle* h, const SolveArgs& a, double* work);
+// coupled anisotropic system (Eq. pde1): per-axis conductivities of the two
+// components and the coupling kappa; scale is set by the solver
+struct Coupling {
+  double di[3] = {1.0, 1.0, 1.0}, de[3] = {1.0, 1.0, 1.0};
+  double kappa = 0.0, scale = 1.0;
+};
+// the float64 box solve of the coupled pair (sources / corrections / outputs
+// of the intracellular component in si, extracellular in se) on the padded
+// grids wa, wb
+int box_solve_coupled64(kfbi_handle* h, const SolveArgs& si, const SolveArgs& se, const Coupling& cp, double* wa,
+                        double* wb);
 int box_solve32(kfbi_handle* h, const SolveArgs& a, float* work);
 int dst_supported(int N);
 int transform_pass(kfbi_handle* h, int precision, int pass, double lambda);

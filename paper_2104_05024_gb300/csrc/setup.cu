@@ -491,9 +491,45 @@ struct DensityInputs {
   int M;
 };
 
-// per crossing: density row (psi at z and its surface-gradient component along
-// the crossing axis) folded with the jump formula into correction weights for
-// both end nodes
+// Coefficients of the single layer's jump polynomial of one component with
+// diagonal conductivity D at the displacement xi from a surface point with
+// outward normal n and shape operator S (d n / d t = S t):
+//   J(xi) = [grad v].xi + xi^T [D^2 v] xi / 2 = Apsi psi + Bg . grad_G psi,
+// from [grad v] = alpha n, alpha = psi / q, q = n.D n,
+//   grad_G alpha = grad_G psi / q - psi m,   m = 2 S D n / q^2,
+//   [D^2 v] = alpha S + n grad_G alpha^T + grad_G alpha n^T + c n n^T,
+//   c = -(alpha tr(D S) + 2 n.D grad_G alpha) / q
+// ([v] = 0 differentiated twice along the surface, n.D[grad v] = psi, and
+// the PDE jump tr(D [D^2 v]) = 0).  With D = I this is the isotropic
+// J = psi (n.xi + xi^T (S - tr S n n^T) xi / 2) + (n.xi)(xi . grad_G psi).
+__host__ __device__ void jump_poly(const double* n, const double (*S)[3], const double* D, int d, const double* xi,
+                                   double* Apsi, double* Bg) {
+  double Dn[3] = {0.0, 0.0, 0.0}, SDn[3] = {0.0, 0.0, 0.0};
+  double q = 0.0, nx = 0.0, xSx = 0.0, trDS = 0.0;
+  for (int a = 0; a < d; ++a) {
+    Dn[a] = D[a] * n[a];
+    q += n[a] * Dn[a];
+    nx += n[a] * xi[a];
+    trDS += D[a] * S[a][a];
+  }
+  for (int a = 0; a < d; ++a)
+    for (int b = 0; b < d; ++b) {
+      SDn[a] += S[a][b] * Dn[b];
+      xSx += xi[a] * S[a][b] * xi[b];
+    }
+  // u = xi - (n.xi) D n / q: J's grad_G alpha part is (n.xi) u . grad_G alpha
+  double um = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const double u = a < d ? xi[a] - nx * Dn[a] / q : 0.0;
+    Bg[a] = nx * u / q;
+    um += u * (a < d ? 2.0 * SDn[a] / (q * q) : 0.0);
+  }
+  *Apsi = (nx + 0.5 * xSx - 0.5 * nx * nx * trDS / q) / q - nx * um;
+}
+
+// per crossing: density row (psi at z and its surface gradient) folded with
+// the jump polynomial of the component (conductivity t.cond) into correction
+// weights for both end nodes
 __host__ __device__ int crossing_row(const GeomParams& gp, const GridParams& gr, const DensityInputs& di,
                                      const uint8_t* inside, const Tables& t, int i) {
   int errbits = 0;
@@ -508,13 +544,9 @@ __host__ __device__ int crossing_row(const GeomParams& gp, const GridParams& gr,
   P[a] = z;
   double n[3], S[3][3];
   normal_shape(gp, comp, P, n, S);
-  double trS = 0.0;
-  for (int q = 0; q < d; ++q) trS += S[q][q];
-  const double na = n[a];
-  const double Saa = S[a][a] - trS * na * na;  // [d_aa v] = psi Saa' + 2 n_a g_a
-  // density row: psi(z) = sum w0 x[pid], g_a = sum wa x[pid]
+  // density row: psi(z) = sum w0 x[pid], grad_G psi(z) = sum wg[.] x[pid]
   int pid[PATCH_MAX];
-  double w0[PATCH_MAX], wa[PATCH_MAX];
+  double w0[PATCH_MAX], wg[3][PATCH_MAX];
   int K = 0;
   if (d == 2) {
     const double* p = gp.p;
@@ -532,8 +564,9 @@ __host__ __device__ int crossing_row(const GeomParams& gp, const GridParams& gr,
     const double u = (tt - s * D) / D, w = 1.0 - u;
     const int sp = (s + 1) % M;
     const double speed = sqrt((p[0] * yr / p[1]) * (p[0] * yr / p[1]) + (p[1] * xr / p[0]) * (p[1] * xr / p[0]));
-    const double tau_a = a == 0 ? -n[1] : n[0];
-    const double ga = tau_a / speed;
+    // grad_G psi = psi_s tau, tau = (-n_y, n_x), psi_s = psi_t / speed
+    const double tau[2] = {-n[1], n[0]};
+    const double dw[4] = {-1.0 / D, 1.0 / D, -(D / 6.0) * (3.0 * w * w - 1.0), (D / 6.0) * (3.0 * u * u - 1.0)};
     K = 4;
     pid[0] = s;
     pid[1] = sp;
@@ -543,36 +576,42 @@ __host__ __device__ int crossing_row(const GeomParams& gp, const GridParams& gr,
     w0[1] = u;
     w0[2] = (D * D / 6.0) * (w * w * w - w);
     w0[3] = (D * D / 6.0) * (u * u * u - u);
-    wa[0] = -ga / D;
-    wa[1] = ga / D;
-    wa[2] = -ga * (D / 6.0) * (3.0 * w * w - 1.0);
-    wa[3] = ga * (D / 6.0) * (3.0 * u * u - 1.0);
+    for (int q = 0; q < 4; ++q) {
+      wg[0][q] = tau[0] / speed * dw[q];
+      wg[1][q] = tau[1] / speed * dw[q];
+      wg[2][q] = 0.0;
+    }
   } else {
     const int tri = locate_tri(gp, di.cube_t, comp, P);
     K = di.patch_cnt[tri];
     int ids[PATCH_MAX];
     for (int q = 0; q < K; ++q) ids[q] = di.patch_ids[(size_t)tri * PATCH_MAX + q];
-    double wg[3][PATCH_MAX];
     if (!fit_weights(di.nodes, ids, K, P, n, w0, wg)) errbits |= DEVERR_SINGULAR;
-    for (int q = 0; q < K; ++q) {
-      pid[q] = ids[q];
-      wa[q] = wg[a][q];
-    }
+    for (int q = 0; q < K; ++q) pid[q] = ids[q];
   }
-  // correction of end node e: -sigma_e/h^2 * (psi (n_a d + Saa d^2/2) + g_a n_a d^2), d = x_other - z
+  // correction of end node e: -+ d_a J(x_other - z) / h^2 (- inside Omega)
   const double ih2 = 1.0 / (gr.h * gr.h);
   const int64_t fh = f + axis_stride(a, n1);
-  const double sl = inside[f] ? -ih2 : ih2;
-  const double sh = inside[fh] ? -ih2 : ih2;
-  const double dl = xh - z, dh = xl - z;
-  const double cpl = sl * (na * dl + 0.5 * Saa * dl * dl), cgl = sl * (na * dl * dl);
-  const double cph = sh * (na * dh + 0.5 * Saa * dh * dh), cgh = sh * (na * dh * dh);
+  const double sl = (inside[f] ? -ih2 : ih2) * t.cond[a];
+  const double sh = (inside[fh] ? -ih2 : ih2) * t.cond[a];
+  double xil[3] = {0.0, 0.0, 0.0}, xih[3] = {0.0, 0.0, 0.0};
+  xil[a] = xh - z;
+  xih[a] = xl - z;
+  double Apl, Bgl[3], Aph, Bgh[3];
+  jump_poly(n, S, t.cond, d, xil, &Apl, Bgl);
+  jump_poly(n, S, t.cond, d, xih, &Aph, Bgh);
   t.c_cnt[i] = K;
   for (int q = 0; q < PATCH_MAX; ++q) {
     const bool on = q < K;
+    double gl = 0.0, gh = 0.0;
+    if (on)
+      for (int b = 0; b < d; ++b) {
+        gl += Bgl[b] * wg[b][q];
+        gh += Bgh[b] * wg[b][q];
+      }
     t.c_pid[(size_t)i * PATCH_MAX + q] = on ? pid[q] : 0;
-    t.c_wlo[(size_t)i * PATCH_MAX + q] = on ? cpl * w0[q] + cgl * wa[q] : 0.0;
-    t.c_whi[(size_t)i * PATCH_MAX + q] = on ? cph * w0[q] + cgh * wa[q] : 0.0;
+    t.c_wlo[(size_t)i * PATCH_MAX + q] = on ? sl * (Apl * w0[q] + gl) : 0.0;
+    t.c_whi[(size_t)i * PATCH_MAX + q] = on ? sh * (Aph * w0[q] + gh) : 0.0;
   }
   return errbits;
 }
@@ -609,8 +648,6 @@ __host__ __device__ int node_stencil_row(const GeomParams& gp, const GridParams&
     if (i >= gp.comp_vert_offset[cc]) comp = cc;
   double n[3], S[3][3];
   normal_shape(gp, comp, q, n, S);
-  double trS = 0.0;
-  for (int a = 0; a < d; ++a) trS += S[a][a];
   // stencil offsets in the oracle's order
   const int P = d == 2 ? 6 : 10;
   int off[10][3];
@@ -650,23 +687,21 @@ __host__ __device__ int node_stencil_row(const GeomParams& gp, const GridParams&
     if (d == 3) f += (int64_t)(c[2] + off[j][2] - 1) * n1 * n1;
     out[j] = inside[f] == 0;
   }
-  // wn solves A^T wn = n_ext / h with n_ext = (0, n_1..n_d, 0...)
+  // wn solves A^T wn = c / h with c = (0, n_1 D_1 .. n_d D_d, 0...): the
+  // conormal limit n.D grad v^+ of the component (D = t.cond)
   double At[100];
   for (int r = 0; r < P; ++r)
     for (int cc = 0; cc < P; ++cc) At[r * P + cc] = A[cc * P + r];
-  for (int r = 0; r < P; ++r) rhs[r] = (r >= 1 && r <= d) ? n[r - 1] / gr.h : 0.0;
+  for (int r = 0; r < P; ++r) rhs[r] = (r >= 1 && r <= d) ? n[r - 1] * t.cond[r - 1] / gr.h : 0.0;
   if (!gauss_solve(At, rhs, P, P)) errbits |= DEVERR_SINGULAR;
   double Ai = 0.0, Bi[3] = {0.0, 0.0, 0.0};
   for (int j = 0; j < P; ++j) {
     t.n_wn[(size_t)i * P + j] = rhs[j];
     if (!out[j]) continue;
-    double nx = 0.0;
-    for (int a = 0; a < d; ++a) nx += n[a] * xi[j][a];
-    double quad = 0.0;
-    for (int a = 0; a < d; ++a)
-      for (int b = 0; b < d; ++b) quad += xi[j][a] * (S[a][b] - trS * n[a] * n[b]) * xi[j][b];
-    Ai += rhs[j] * (nx + 0.5 * quad);
-    for (int a = 0; a < d; ++a) Bi[a] += rhs[j] * nx * xi[j][a];
+    double Ap, Bg[3];
+    jump_poly(n, S, t.cond, d, xi[j], &Ap, Bg);
+    Ai += rhs[j] * Ap;
+    for (int a = 0; a < d; ++a) Bi[a] += rhs[j] * Bg[a];
   }
   AB[(size_t)i * 4 + 0] = Ai;
   for (int a = 0; a < 3; ++a) AB[(size_t)i * 4 + 1 + a] = Bi[a];

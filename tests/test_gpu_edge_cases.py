@@ -109,6 +109,7 @@ def test_newton_cap_returns_err_newton():
         K.react_be(C.FHN_CONFIG, 0.025, V, w)
     assert e.value.code == K.ERR_NEWTON
     V = torch.linspace(-0.2, 1.1, 4096, dtype=torch.float64, device=DEV)
+    w = torch.zeros_like(V)                  # the failed call left a NaN in w too
     K.react_be(C.FHN_CONFIG, 0.025, V, w)
     assert bool(torch.isfinite(V).all())
 

@@ -170,7 +170,11 @@ def test_shell256_strang_learned_form(shell256):
           f"w {rel(wd.cpu().numpy(), w):.2e}, network guess kept {[s['warmstart'] for s in st]}, "
           f"max |network output| {o_max:.3f}")
     assert o_max > 1e-3
-    assert rel(psi0.cpu().numpy(), ref) < 1e-12
+    # the sum is float64; s_out o + m_out is float32 on both sides (the GPU
+    # may fuse it into one rounding)
+    rF_rms = float(np.sqrt(np.mean(rF.cpu().numpy() ** 2)))
+    corr = np.abs(norm[19] * out.cpu().numpy()) + abs(norm[18])
+    assert np.all(np.abs(psi0.cpu().numpy() - ref) <= 1e-13 * np.abs(ref).max() + 2.0 ** -22 * rF_rms * corr)
     assert rel(Vd.cpu().numpy(), V) < TOL_FORMS
     assert rel(wd.cpu().numpy(), w) < TOL_FORMS
 
