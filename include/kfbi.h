@@ -214,6 +214,46 @@ int kfbi_bidomain_step_stim(kfbi_handle* h, const kfbi_fhn* p, const double* ist
                             double* w_dev, double* ue_dev, int nsteps, kfbi_stats* per_step);
 
 /* ------------------------------------------------------------------
+ * Anisotropic coupled system (Section 5.2: fibres along the axes, diagonal
+ * conductivity tensors D_i = diag(D_i[0..dim-1]), D_e likewise; Eq. pde1).
+ * The backward-Euler half step of the diffusion is the vector Neumann
+ * problem
+ *   div(D_i grad Phi_i) - kappa (Phi_i - Phi_e) = f_i,
+ *   div(D_e grad Phi_e) + kappa (Phi_i - Phi_e) = f_e,
+ *   n.D_i grad Phi_i = gN_i,  n.D_e grad Phi_e = gN_e,
+ * solved by the KFBI method with the density pair psi = (psi_i, psi_e)
+ * (2M doubles, psi_i first): per-component corrections with the conormal
+ * jump relations of the component's D, a box solve by sine transforms with a
+ * 2 x 2 solve per mode, conormal limits n.D grad v^+.  Constants (c, c) solve
+ * the homogeneous problem, so every operator application adds the rank-one
+ * term (1, 1) <(ds, ds), psi> / (2 |Gamma|) (ds as at kfbi_solve_neumann);
+ * Phi_i and Phi_e are then fixed up to that common constant's choice, their
+ * difference is unique.  Float64 only (opts.precision = KFBI_FP64).
+ * ------------------------------------------------------------------ */
+/* Setup as kfbi_create for the coupled system; D_i, D_e: dim positive
+ * conductivities each (host).  bidomain_step and kfbi_bidomain_step_stim on
+ * this handle run the Strang step with the coupled diffusion (kappa = 2 Cm
+ * beta / dt, f = (-kappa V, kappa V - beta I_stim), warm start: the previous
+ * density pair, V <- 2 (Phi_i - Phi_e) - V); their ue_dev receives the last
+ * solve's Phi_e (the midpoint level t^n + dt/2) with zero mean over Omega.  */
+int kfbi_create_coupled(const kfbi_geometry* geom, const kfbi_grid* grid, const double* D_i, const double* D_e,
+                        double dt, const kfbi_opts* opts, kfbi_handle** out);
+/* The coupled Neumann problem: fi_dev, fe_dev on every box node (continuous
+ * extensions), gNi_dev, gNe_dev [M]; psi_dev [2M] in: initial guess, out:
+ * density pair; phi_i_dev, phi_e_dev: out on every box node.  stats as at
+ * kfbi_solve_neumann (true_rel_res includes the rank-one term).            */
+int kfbi_solve_coupled(kfbi_handle* h, double kappa, const double* fi_dev, const double* fe_dev,
+                       const double* gNi_dev, const double* gNe_dev, double* phi_i_dev, double* phi_e_dev,
+                       double* psi_dev, kfbi_stats* stats);
+/* (v_i, v_e) = L_h^{-1} (r_i, r_e) of the coupled 5/7-point operator with
+ * zero Dirichlet data on the box (Eq. FDE, float64).                       */
+int kfbi_box_solve_coupled(kfbi_handle* h, double kappa, const double* ri_dev, const double* re_dev, double* vi_dev,
+                           double* ve_dev);
+/* out [2M] = A psi [2M] of the coupled boundary integral equation (conormal
+ * limits of the single layer, plus the rank-one term).                     */
+int kfbi_apply_A_coupled(kfbi_handle* h, double kappa, const double* psi_dev, double* out_dev);
+
+/* ------------------------------------------------------------------
  * Step-level entry points (one per row of the hot path), used for parity
  * checks and benchmarks.  All act on the handle's geometry and grid.
  * ------------------------------------------------------------------ */

@@ -62,8 +62,95 @@ int density_vector(kfbi_handle* h, const double* psi, const double** x) {
   return KFBI_OK;
 }
 
+// density vector of one component into buf (2-D: [psi; spline moments])
+int density_vector_buf(kfbi_handle* h, const double* psi, double* buf, const double** x) {
+  if (h->grid.dim == 2) {
+    int rc = launch_spline(h, psi, buf);
+    if (rc) return rc;
+    *x = buf;
+  } else {
+    *x = psi;
+  }
+  return KFBI_OK;
+}
+
+// Coupled anisotropic system (Eq. pde1 with diagonal conductivities): out =
+// base + sgn * A psi for the density pair psi = (psi_i, psi_e) (2M): each
+// component's corrections from its own rows (t: D_i, t2: D_e), the coupled
+// box solve, each component's conormal limit, and the rank-one term
+// (1, 1) <(ds, ds), psi> / (2 |Gamma|) that removes the common-constant null
+// space of the coupled Neumann problem.
+int apply_A_coupled(kfbi_handle* h, double kappa, const double* psi, double* out, double sgn, const double* base) {
+  const int M = h->t.M;
+  const double *xi, *xe;
+  int rc;
+  if ((rc = density_vector_buf(h, psi, h->w.xvec, &xi))) return rc;
+  if ((rc = density_vector_buf(h, psi + M, h->w.xvec2, &xe))) return rc;
+  if ((rc = launch_correction_t(h, h->t, xi, h->w.corr))) return rc;
+  if ((rc = launch_correction_t(h, h->t2, xe, h->w.corr2))) return rc;
+  SolveArgs si, se;
+  si.corr = h->w.corr;
+  se.corr = h->w.corr2;
+  Coupling cp = h->cpl;
+  cp.kappa = kappa;
+  if ((rc = box_solve_coupled64(h, si, se, cp, h->w.grid64, h->w.grid64b))) return rc;
+  if ((rc = launch_limit64_t(h, h->t, h->w.grid64, xi, base, sgn, out))) return rc;
+  if ((rc = launch_limit64_t(h, h->t2, h->w.grid64b, xe, base ? base + M : nullptr, sgn, out + M))) return rc;
+  return launch_rank_one_coupled(h, psi, out, sgn);
+}
+
+// g = (gN_i, gN_e) - conormal limits of the coupled box solve of the sources
+// (alpha_i src_i, alpha_e src_e); the padded grids keep v_V
+int rhs_g_coupled(kfbi_handle* h, double kappa, const double* src_i, double a_i, const double* src_e, double a_e,
+                  const double* gNi, const double* gNe, double* g) {
+  const int M = h->t.M;
+  SolveArgs si, se;
+  si.src = src_i;
+  si.alpha = a_i;
+  se.src = src_e;
+  se.alpha = a_e;
+  Coupling cp = h->cpl;
+  cp.kappa = kappa;
+  int rc;
+  if ((rc = box_solve_coupled64(h, si, se, cp, h->w.grid64, h->w.grid64b))) return rc;
+  if ((rc = launch_limit64_t(h, h->t, h->w.grid64, nullptr, gNi, -1.0, g))) return rc;
+  return launch_limit64_t(h, h->t2, h->w.grid64b, nullptr, gNe, -1.0, g + M);
+}
+
+// (Phi_i, Phi_e) = v_V + v_B(psi) of the coupled problem in one coupled solve
+// of the combined right-hand sides; r (2M, optional) receives the true
+// residual g^N - n.D grad u^+ - rank-one term
+int assemble_coupled(kfbi_handle* h, double kappa, const double* src_i, double a_i, const double* src_e, double a_e,
+                     const double* psi, const double* gNi, const double* gNe, double* phi_i, double* phi_e,
+                     double* r) {
+  const int M = h->t.M;
+  const double *xi, *xe;
+  int rc;
+  if ((rc = density_vector_buf(h, psi, h->w.xvec, &xi))) return rc;
+  if ((rc = density_vector_buf(h, psi + M, h->w.xvec2, &xe))) return rc;
+  if ((rc = launch_correction_t(h, h->t, xi, h->w.corr))) return rc;
+  if ((rc = launch_correction_t(h, h->t2, xe, h->w.corr2))) return rc;
+  SolveArgs si, se;
+  si.src = src_i;
+  si.alpha = a_i;
+  si.corr = h->w.corr;
+  si.out_user = phi_i;
+  se.src = src_e;
+  se.alpha = a_e;
+  se.corr = h->w.corr2;
+  se.out_user = phi_e;
+  Coupling cp = h->cpl;
+  cp.kappa = kappa;
+  if ((rc = box_solve_coupled64(h, si, se, cp, h->w.grid64, h->w.grid64b))) return rc;
+  if (r == nullptr) return KFBI_OK;
+  if ((rc = launch_limit64_t(h, h->t, h->w.grid64, xi, gNi, -1.0, r))) return rc;
+  if ((rc = launch_limit64_t(h, h->t2, h->w.grid64b, xe, gNe, -1.0, r + M))) return rc;
+  return launch_rank_one_coupled(h, psi, r, -1.0);
+}
+
 // out = base + sgn * A psi    (A psi = dv_B^+/dn of the single layer)
 int apply_A(kfbi_handle* h, int prec, double lambda, const double* psi, double* out, double sgn, const double* base) {
+  if (h->coupled) return apply_A_coupled(h, lambda, psi, out, sgn, base);
   const double* x;
   int rc = density_vector(h, psi, &x);
   if (rc) return rc;
@@ -112,7 +199,7 @@ int read_two(kfbi_handle* h, const double* a, const double* b, double* va, doubl
 }
 
 int norm2(kfbi_handle* h, const double* v, double* slot, double* out) {
-  int rc = vec_dots(h, v, 1, h->t.M, v, slot);
+  int rc = vec_dots(h, v, 1, h->nk, v, slot);
   if (rc) return rc;
   double s;
   if ((rc = read_scalar(h, slot, &s))) return rc;
@@ -187,7 +274,7 @@ struct SkipScope {
 };
 
 int arnoldi_iteration(kfbi_handle* h, int prec, double lambda, int j, double gnorm, double tol) {
-  const int M = h->t.M, m = h->opts.restart;
+  const int M = h->nk, m = h->opts.restart;
   double* V = h->w.vecs;
   int rc;
   {
@@ -211,7 +298,7 @@ int arnoldi_iteration(kfbi_handle* h, int prec, double lambda, int j, double gno
 int gmres(kfbi_handle* h, int prec, double lambda, const double* g, double* psi, kfbi_stats* st, double tol,
           int max_iter, bool zero_guess = false, const double* fallback = nullptr,
           const double* fallback_res2 = nullptr, double gnorm_known = -1.0) {
-  const int M = h->t.M;
+  const int M = h->nk;
   const int m = h->opts.restart;
   double* V = h->w.vecs;
   const int ld = M;
@@ -297,7 +384,7 @@ int gmres(kfbi_handle* h, int prec, double lambda, const double* g, double* psi,
 }
 
 int richardson(kfbi_handle* h, int prec, double lambda, const double* g, double* psi, kfbi_stats* st) {
-  const int M = h->t.M;
+  const int M = h->nk;
   double* r = h->w.r;
   double* s = h->w.small;
   const int m = h->opts.restart;
@@ -343,7 +430,7 @@ int richardson(kfbi_handle* h, int prec, double lambda, const double* g, double*
 int gmres_ir(kfbi_handle* h, double lambda, const double* g, double* psi, kfbi_stats* st,
              const double* fallback = nullptr, const double* fallback_res2 = nullptr, double gnorm_known = -1.0,
              const double* rF = nullptr) {
-  const int M = h->t.M;
+  const int M = h->nk;
   double* r = h->w.r2;
   double* delta = h->w.tmp2;
   double* slot = h->w.small + small_nrm2(h->opts.restart);
@@ -449,7 +536,7 @@ int solve_bie(kfbi_handle* h, int prec, double lambda, const double* g, double* 
 // out: gnorm = ||g||; rF2 = the device slot that receives ||r_F||^2 (read
 // by the solver together with its first residual).  One synchronisation.
 int project_history(kfbi_handle* h, const double* g, double* gnorm, const double** rF2) {
-  const int M = h->t.M;
+  const int M = h->nk;
   const int k = h->hist_count < KFBI_HISTORY ? h->hist_count : KFBI_HISTORY;
   double* G = h->w.proj;             // [k][k]
   double* b = G + KFBI_HISTORY * KFBI_HISTORY;
@@ -516,7 +603,7 @@ int project_history(kfbi_handle* h, const double* g, double* gnorm, const double
 // stores psi and its image A psi: g - r with r = g - A psi the solver's
 // final float64-accurate residual when given, else g (A psi to the tolerance)
 int push_history(kfbi_handle* h, const double* psi, const double* g, const double* r = nullptr) {
-  const int M = h->t.M;
+  const int M = h->nk;
   const size_t slot = (size_t)(h->hist_count % KFBI_HISTORY) * M;
   int rc;
   if ((rc = vec_copy(h, h->w.hist_psi + slot, psi, M))) return rc;
@@ -547,8 +634,34 @@ extern "C" {
 
 const char* kfbi_last_error(void) { return kfbi::g_err; }
 
+static int create_impl(const kfbi_geometry* geom, const kfbi_grid* grid, double sigma_i, double sigma_e, double dt,
+                       const kfbi_opts* opts, kfbi_handle** out, const double* D_i, const double* D_e);
+
 int kfbi_create(const kfbi_geometry* geom, const kfbi_grid* grid, double sigma_i, double sigma_e, double dt,
                 const kfbi_opts* opts, kfbi_handle** out) {
+  return create_impl(geom, grid, sigma_i, sigma_e, dt, opts, out, nullptr, nullptr);
+}
+
+int kfbi_create_coupled(const kfbi_geometry* geom, const kfbi_grid* grid, const double* D_i, const double* D_e,
+                        double dt, const kfbi_opts* opts, kfbi_handle** out) {
+  if (!D_i || !D_e || !grid) {
+    set_error("null conductivities");
+    return KFBI_ERR_ARG;
+  }
+  for (int a = 0; a < grid->dim && a < 3; ++a)
+    if (!(D_i[a] > 0.0) || !(D_e[a] > 0.0)) {
+      set_error("conductivities must be positive");
+      return KFBI_ERR_ARG;
+    }
+  if (opts && opts->precision != KFBI_FP64) {
+    set_error("the coupled system is solved in float64 (KFBI_FP64)");
+    return KFBI_ERR_ARG;
+  }
+  return create_impl(geom, grid, D_i[0], D_e[0], dt, opts, out, D_i, D_e);
+}
+
+static int create_impl(const kfbi_geometry* geom, const kfbi_grid* grid, double sigma_i, double sigma_e, double dt,
+                       const kfbi_opts* opts, kfbi_handle** out, const double* D_i, const double* D_e) {
   if (!geom || !grid || !out || !opts) {
     set_error("null argument");
     return KFBI_ERR_ARG;
@@ -583,6 +696,14 @@ int kfbi_create(const kfbi_geometry* geom, const kfbi_grid* grid, double sigma_i
   h->sigma_e = sigma_e;
   h->dt = dt;
   h->lambda = (2.0 / dt) * (1.0 / sigma_i + 1.0 / sigma_e);
+  if (D_i != nullptr) {
+    h->coupled = true;
+    for (int a = 0; a < 3; ++a) {
+      h->cpl.di[a] = a < grid->dim ? D_i[a] : 1.0;
+      h->cpl.de[a] = a < grid->dim ? D_e[a] : 1.0;
+    }
+    h->cpl.kappa = 2.0 / dt;  // Cm beta / (dt/2) with Cm beta = 1
+  }
   GeomParams& gp = h->gp;
   memset(&gp, 0, sizeof(gp));
   gp.dim = geom->dim;
@@ -619,7 +740,11 @@ int kfbi_create(const kfbi_geometry* geom, const kfbi_grid* grid, double sigma_i
       return fail(KFBI_ERR_CUDA);
     }
   if ((rc = setup_build(h, geom))) return fail(rc);
-  const int M = h->t.M, m = opts->restart;
+  const int m = opts->restart;
+  // Krylov vectors, densities and their history: M entries, 2M for the
+  // coupled system's density pair
+  h->nk = h->coupled ? 2 * h->t.M : h->t.M;
+  const int M = h->nk;
   const int64_t P = padded_points(h);
   if ((rc = dalloc(h, &h->w.grid64, (size_t)P))) return fail(rc);
   if ((rc = dalloc(h, &h->w.grid32, (size_t)P))) return fail(rc);
@@ -630,7 +755,16 @@ int kfbi_create(const kfbi_geometry* geom, const kfbi_grid* grid, double sigma_i
   }
   if ((rc = make_tma_maps(h))) return fail(rc);
   if ((rc = dalloc(h, &h->w.corr, (size_t)h->t.n_irr))) return fail(rc);
-  if ((rc = dalloc(h, &h->w.xvec, (size_t)2 * M))) return fail(rc);
+  if ((rc = dalloc(h, &h->w.xvec, (size_t)2 * h->t.M))) return fail(rc);
+  if (h->coupled) {
+    if ((rc = dalloc(h, &h->w.corr2, (size_t)h->t.n_irr))) return fail(rc);
+    if ((rc = dalloc(h, &h->w.xvec2, (size_t)2 * h->t.M))) return fail(rc);
+    if ((rc = dalloc(h, &h->w.grid64b, (size_t)P))) return fail(rc);
+    if (cudaMemsetAsync(h->w.grid64b, 0, sizeof(double) * (size_t)P, h->stream) != cudaSuccess) {
+      set_error("cudaMemset failed");
+      return fail(KFBI_ERR_CUDA);
+    }
+  }
   if ((rc = dalloc(h, &h->w.vecs, (size_t)(m + 1) * M))) return fail(rc);
   if ((rc = dalloc(h, &h->w.small, (size_t)small_size(MAX_RESTART)))) return fail(rc);
   if ((rc = dalloc(h, &h->w.partial, (size_t)KFBI_ARN_BLOCKS * (MAX_RESTART + 2) + 16))) return fail(rc);
@@ -829,6 +963,10 @@ int kfbi_solve_neumann(kfbi_handle* h, double lambda, const double* f_dev, const
   if (int rc = check_handle(h)) return rc;
   if (!f_dev || !gN_dev || !u_dev || !psi_dev) {
     set_error("null argument");
+    return KFBI_ERR_ARG;
+  }
+  if (h->coupled) {
+    set_error("a coupled handle solves the vector problem: kfbi_solve_coupled");
     return KFBI_ERR_ARG;
   }
   kfbi_stats st{};
@@ -1062,13 +1200,194 @@ static int bidomain_impl(kfbi_handle* h, const kfbi_fhn* p, const double* istim,
   return final_rc;
 }
 
+// Strang steps with the coupled anisotropic diffusion step: forward-Euler
+// reaction over dt/2; the backward-Euler half step of Eq. pde1 with kappa =
+// Cm beta / (dt/2), f = (-kappa V, kappa V - beta I), solved for (Phi_i,
+// Phi_e) by GMRES on the density pair (warm start: the previous pair); V <-
+// 2 (Phi_i - Phi_e) - V; backward-Euler reaction over dt/2.  ue_dev receives
+// the last solve's Phi_e (the midpoint level) with zero mean over Omega.
+static int bidomain_coupled_impl(kfbi_handle* h, const kfbi_fhn* p, const double* istim, double* V_dev,
+                                 double* w_dev, double* ue_dev, int nsteps, kfbi_stats* per_step) {
+  if (h->opts.precision != KFBI_FP64 || h->opts.solver != KFBI_GMRES) {
+    set_error("the coupled system is solved in float64 with GMRES");
+    return KFBI_ERR_ARG;
+  }
+  const int64_t n = grid_points(h);
+  const int M = h->t.M, nk = h->nk;
+  const double kap = p->Cm * p->beta / (0.5 * h->dt);
+  const double k = 0.5 * h->dt;
+  int rc, final_rc = KFBI_OK;
+  if (istim != nullptr && !h->w.fsrc && (rc = dalloc(h, &h->w.fsrc, (size_t)n))) return rc;
+  if (!h->w.zeroM) {
+    if ((rc = dalloc(h, &h->w.zeroM, (size_t)M))) return rc;
+    KFBI_CUDA(cudaMemsetAsync(h->w.zeroM, 0, sizeof(double) * (size_t)M, h->stream));
+  }
+  KFBI_CUDA(cudaMemsetAsync(h->w.err, 0, sizeof(int), h->stream));
+  if (nsteps > h->step_cap) {
+    if (h->w.step_sq) cudaFree(h->w.step_sq);
+    h->w.step_sq = nullptr;
+    h->step_cap = 0;
+    KFBI_CUDA(cudaMalloc((void**)&h->w.step_sq, sizeof(double) * 2 * (size_t)nsteps));
+    h->step_cap = nsteps;
+  }
+  constexpr int NEV = 7;
+  const bool timed = per_step != nullptr;
+  while (timed && h->step_events.size() < (size_t)NEV * nsteps) {
+    cudaEvent_t e;
+    KFBI_CUDA(cudaEventCreate(&e));
+    h->step_events.push_back(e);
+  }
+  auto mark = [&](int s, int q) -> int {
+    if (timed) KFBI_CUDA(cudaEventRecord(h->step_events[(size_t)NEV * s + q], h->stream));
+    return KFBI_OK;
+  };
+  std::vector<kfbi_stats> stats((size_t)nsteps);
+  double* phi_i = h->w.u64;
+  double* phi_e = h->w.vV64;
+  for (int s = 0; s < nsteps; ++s) {
+    kfbi_stats& st = stats[s];
+    auto t0 = std::chrono::steady_clock::now();
+    if ((rc = mark(s, 0))) return rc;
+    if ((rc = launch_react_fe(p, k, V_dev, w_dev, n, h->stream))) return rc;
+    if ((rc = mark(s, 1))) return rc;
+    // f_i = -kappa V, f_e = kappa V (- beta I)
+    const double* src_e = V_dev;
+    double a_e = kap;
+    if (istim != nullptr) {
+      if ((rc = launch_stim_source(h, V_dev, -kap, istim, -p->beta, h->w.fsrc, n))) return rc;
+      src_e = h->w.fsrc;
+      a_e = 1.0;
+    }
+    if ((rc = rhs_g_coupled(h, kap, V_dev, -kap, src_e, a_e, h->w.zeroM, h->w.zeroM, h->w.g))) return rc;
+    if ((rc = mark(s, 2))) return rc;
+    if ((rc = vec_copy(h, h->w.psi_save, h->w.psi_prev, nk))) return rc;
+    if ((rc = vec_copy(h, h->w.psi_learn, h->w.psi_prev, nk))) return rc;
+    h->proj_valid = false;
+    if ((rc = mark(s, 3))) return rc;
+    const int src = solve_bie(h, KFBI_FP64, kap, h->w.g, h->w.psi_prev, &st);
+    if (src != KFBI_OK && src != KFBI_ERR_NOT_CONVERGED) return src;
+    if (src == KFBI_ERR_NOT_CONVERGED) final_rc = src;
+    if ((rc = vec_copy(h, h->w.psi_prev2, h->w.psi_save, nk))) return rc;
+    if ((rc = vec_copy(h, h->w.g_prev, h->w.g, nk))) return rc;
+    ++h->n_hist;
+    if ((rc = mark(s, 4))) return rc;
+    if ((rc = assemble_coupled(h, kap, V_dev, -kap, src_e, a_e, h->w.psi_prev, h->w.zeroM, h->w.zeroM, phi_i, phi_e,
+                               h->w.tmp)))
+      return rc;
+    if ((rc = launch_midpoint_diff(h, V_dev, phi_i, phi_e, n))) return rc;
+    if ((rc = vec_dots(h, h->w.tmp, 1, nk, h->w.tmp, h->w.step_sq + 2 * s))) return rc;
+    if ((rc = vec_dots(h, h->w.g, 1, nk, h->w.g, h->w.step_sq + 2 * s + 1))) return rc;
+    if ((rc = mark(s, 5))) return rc;
+    if ((rc = launch_react_be(p, k, V_dev, w_dev, n, h->w.err, h->stream))) return rc;
+    if ((rc = mark(s, 6))) return rc;
+    st.ms = elapsed_ms(t0);
+  }
+  if (ue_dev && (rc = launch_sub_mean(h, phi_e, ue_dev))) return rc;
+  int herr = 0;
+  std::vector<double> sq((size_t)2 * nsteps + 1);
+  KFBI_CUDA(cudaMemcpyAsync(&herr, h->w.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  if (nsteps > 0)
+    KFBI_CUDA(cudaMemcpyAsync(sq.data(), h->w.step_sq, sizeof(double) * 2 * (size_t)nsteps, cudaMemcpyDeviceToHost,
+                              h->stream));
+  KFBI_CUDA(cudaStreamSynchronize(h->stream));
+  for (int s = 0; s < nsteps; ++s) {
+    kfbi_stats& st = stats[s];
+    const double rr = std::sqrt(sq[2 * s]), gg = std::sqrt(sq[2 * s + 1]);
+    st.true_rel_res = gg > 0.0 ? rr / gg : rr;
+    if (timed) {
+      float t[NEV - 1];
+      for (int q = 0; q + 1 < NEV; ++q)
+        KFBI_CUDA(cudaEventElapsedTime(&t[q], h->step_events[(size_t)NEV * s + q], h->step_events[(size_t)NEV * s + q + 1]));
+      st.react_ms = t[0] + t[5];
+      st.rhs_ms = t[1];
+      st.warm_ms = t[2];
+      st.solve_ms = t[3];
+      st.assemble_ms = t[4];
+      per_step[s] = st;
+    }
+  }
+  if (herr & DEVERR_NEWTON) {
+    set_error("backward-Euler Newton iteration hit its cap");
+    return KFBI_ERR_NEWTON;
+  }
+  return final_rc;
+}
+
 int bidomain_step(kfbi_handle* h, const kfbi_fhn* p, double* V_dev, double* w_dev, double* ue_dev, int nsteps,
                   kfbi_stats* per_step) {
+  if (h != nullptr && h->coupled) {
+    if (!p || !V_dev || !w_dev || nsteps < 0) {
+      set_error("null argument");
+      return KFBI_ERR_ARG;
+    }
+    return bidomain_coupled_impl(h, p, nullptr, V_dev, w_dev, ue_dev, nsteps, per_step);
+  }
   return bidomain_impl(h, p, nullptr, V_dev, w_dev, ue_dev, nsteps, per_step);
+}
+
+int kfbi_solve_coupled(kfbi_handle* h, double kappa, const double* fi_dev, const double* fe_dev,
+                       const double* gNi_dev, const double* gNe_dev, double* phi_i_dev, double* phi_e_dev,
+                       double* psi_dev, kfbi_stats* stats) {
+  if (int rc = check_handle(h)) return rc;
+  if (!h->coupled || !fi_dev || !fe_dev || !gNi_dev || !gNe_dev || !phi_i_dev || !phi_e_dev || !psi_dev ||
+      !(kappa > 0.0)) {
+    set_error("kfbi_solve_coupled needs a coupled handle, kappa > 0 and every field");
+    return KFBI_ERR_ARG;
+  }
+  kfbi_stats st{};
+  auto t0 = std::chrono::steady_clock::now();
+  int rc;
+  if ((rc = rhs_g_coupled(h, kappa, fi_dev, 1.0, fe_dev, 1.0, gNi_dev, gNe_dev, h->w.g))) return rc;
+  const int solve_rc = solve_bie(h, KFBI_FP64, kappa, h->w.g, psi_dev, &st);
+  if (solve_rc != KFBI_OK && solve_rc != KFBI_ERR_NOT_CONVERGED) return solve_rc;
+  if ((rc = assemble_coupled(h, kappa, fi_dev, 1.0, fe_dev, 1.0, psi_dev, gNi_dev, gNe_dev, phi_i_dev, phi_e_dev,
+                             h->w.r)))
+    return rc;
+  double rn, gn;
+  double* slot = h->w.small + small_nrm2(h->opts.restart);
+  if ((rc = norm2(h, h->w.r, slot, &rn))) return rc;
+  if ((rc = norm2(h, h->w.g, slot, &gn))) return rc;
+  st.true_rel_res = gn > 0 ? rn / gn : rn;
+  st.ms = elapsed_ms(t0);
+  if (stats) *stats = st;
+  return solve_rc;
+}
+
+int kfbi_box_solve_coupled(kfbi_handle* h, double kappa, const double* ri_dev, const double* re_dev, double* vi_dev,
+                           double* ve_dev) {
+  if (int rc = check_handle(h)) return rc;
+  if (!h->coupled || !ri_dev || !re_dev || !vi_dev || !ve_dev) {
+    set_error("kfbi_box_solve_coupled needs a coupled handle and every field");
+    return KFBI_ERR_ARG;
+  }
+  SolveArgs si, se;
+  si.src = ri_dev;
+  si.out_user = vi_dev;
+  se.src = re_dev;
+  se.out_user = ve_dev;
+  Coupling cp = h->cpl;
+  cp.kappa = kappa;
+  return box_solve_coupled64(h, si, se, cp, h->w.grid64, h->w.grid64b);
+}
+
+int kfbi_apply_A_coupled(kfbi_handle* h, double kappa, const double* psi_dev, double* out_dev) {
+  if (int rc = check_handle(h)) return rc;
+  if (!h->coupled || !psi_dev || !out_dev) {
+    set_error("kfbi_apply_A_coupled needs a coupled handle");
+    return KFBI_ERR_ARG;
+  }
+  return apply_A_coupled(h, kappa, psi_dev, out_dev, 1.0, nullptr);
 }
 
 int kfbi_bidomain_step_stim(kfbi_handle* h, const kfbi_fhn* p, const double* istim_dev, double* V_dev,
                             double* w_dev, double* ue_dev, int nsteps, kfbi_stats* per_step) {
+  if (h != nullptr && h->coupled) {
+    if (!p || !V_dev || !w_dev || nsteps < 0) {
+      set_error("null argument");
+      return KFBI_ERR_ARG;
+    }
+    return bidomain_coupled_impl(h, p, istim_dev, V_dev, w_dev, ue_dev, nsteps, per_step);
+  }
   return bidomain_impl(h, p, istim_dev, V_dev, w_dev, ue_dev, nsteps, per_step);
 }
 
@@ -1084,7 +1403,7 @@ int kfbi_set_warmstart(kfbi_handle* h, kfbi_mlp* m) {
 
 int kfbi_get_densities(kfbi_handle* h, double* psi_dev, double* psi_prev_dev, double* g_dev) {
   if (int rc = check_handle(h)) return rc;
-  const size_t n = sizeof(double) * (size_t)h->t.M;
+  const size_t n = sizeof(double) * (size_t)h->nk;
   if (psi_dev) KFBI_CUDA(cudaMemcpyAsync(psi_dev, h->w.psi_prev, n, cudaMemcpyDeviceToDevice, h->stream));
   if (psi_prev_dev) KFBI_CUDA(cudaMemcpyAsync(psi_prev_dev, h->w.psi_prev2, n, cudaMemcpyDeviceToDevice, h->stream));
   if (g_dev) KFBI_CUDA(cudaMemcpyAsync(g_dev, h->w.g, n, cudaMemcpyDeviceToDevice, h->stream));
@@ -1098,7 +1417,7 @@ int kfbi_set_densities(kfbi_handle* h, const double* psi_dev, const double* psi_
     set_error("negative solve count");
     return KFBI_ERR_ARG;
   }
-  const size_t n = sizeof(double) * (size_t)h->t.M;
+  const size_t n = sizeof(double) * (size_t)h->nk;
   if (n_solves == 0) {
     KFBI_CUDA(cudaMemsetAsync(h->w.psi_prev, 0, n, h->stream));
     KFBI_CUDA(cudaMemsetAsync(h->w.psi_prev2, 0, n, h->stream));
@@ -1120,7 +1439,7 @@ int kfbi_set_densities(kfbi_handle* h, const double* psi_dev, const double* psi_
 
 int kfbi_get_history(kfbi_handle* h, double* psi_hist_dev, double* g_hist_dev, int* n_solves) {
   if (int rc = check_handle(h)) return rc;
-  const size_t n = sizeof(double) * (size_t)KFBI_HISTORY * h->t.M;
+  const size_t n = sizeof(double) * (size_t)KFBI_HISTORY * h->nk;
   if (psi_hist_dev) KFBI_CUDA(cudaMemcpyAsync(psi_hist_dev, h->w.hist_psi, n, cudaMemcpyDeviceToDevice, h->stream));
   if (g_hist_dev) KFBI_CUDA(cudaMemcpyAsync(g_hist_dev, h->w.hist_g, n, cudaMemcpyDeviceToDevice, h->stream));
   if (n_solves) *n_solves = h->hist_count;
@@ -1133,7 +1452,7 @@ int kfbi_set_history(kfbi_handle* h, const double* psi_hist_dev, const double* g
     set_error("bad density history");
     return KFBI_ERR_ARG;
   }
-  const int M = h->t.M;
+  const int M = h->nk;
   const size_t n = sizeof(double) * (size_t)KFBI_HISTORY * M;
   if (n_solves > 0) {
     KFBI_CUDA(cudaMemcpyAsync(h->w.hist_psi, psi_hist_dev, n, cudaMemcpyDeviceToDevice, h->stream));
@@ -1162,7 +1481,7 @@ int kfbi_set_history(kfbi_handle* h, const double* psi_hist_dev, const double* g
 
 int kfbi_get_projection(kfbi_handle* h, double* psiF_dev, double* rF_dev) {
   if (int rc = check_handle(h)) return rc;
-  const size_t n = sizeof(double) * (size_t)h->t.M;
+  const size_t n = sizeof(double) * (size_t)h->nk;
   if (psiF_dev) KFBI_CUDA(cudaMemcpyAsync(psiF_dev, h->w.psiF, n, cudaMemcpyDeviceToDevice, h->stream));
   if (rF_dev) KFBI_CUDA(cudaMemcpyAsync(rF_dev, h->w.rF, n, cudaMemcpyDeviceToDevice, h->stream));
   return KFBI_OK;
@@ -1174,7 +1493,7 @@ int kfbi_get_warm_guess(kfbi_handle* h, double* psi0_dev) {
     set_error("null output");
     return KFBI_ERR_ARG;
   }
-  KFBI_CUDA(cudaMemcpyAsync(psi0_dev, h->w.psi_learn, sizeof(double) * (size_t)h->t.M, cudaMemcpyDeviceToDevice,
+  KFBI_CUDA(cudaMemcpyAsync(psi0_dev, h->w.psi_learn, sizeof(double) * (size_t)h->nk, cudaMemcpyDeviceToDevice,
                             h->stream));
   return KFBI_OK;
 }

@@ -115,6 +115,13 @@ struct Tables {
   double cond[3] = {1.0, 1.0, 1.0};
 };
 
+// coupled anisotropic system (Eq. pde1): per-axis conductivities of the two
+// components and the coupling kappa; scale is set by the solver
+struct Coupling {
+  double di[3] = {1.0, 1.0, 1.0}, de[3] = {1.0, 1.0, 1.0};
+  double kappa = 0.0, scale = 1.0;
+};
+
 struct Workspace {
   double* grid64 = nullptr;       // padded N^dim work grid
   double* grid64b = nullptr;      // second padded grid (volume solution)
@@ -153,6 +160,11 @@ struct Workspace {
   int* stop = nullptr;            // Krylov stop flag (set by the Arnoldi step)
   unsigned* counter = nullptr;    // ticket counter of the single-launch reductions
   double* step_sq = nullptr;      // per Strang step: squared true residual, ||g||^2
+  // coupled anisotropic system: second correction array, second 2-D density
+  // vector, and (ds, ds) / 2 for its rank-one term
+  double* corr2 = nullptr;
+  double* xvec2 = nullptr;
+  double* ds2 = nullptr;
   int restart_cap = 0;
 };
 
@@ -172,6 +184,13 @@ struct kfbi_handle {
   int n_hist = 0;                 // completed diffusion solves (density history)
   int hist_count = 0;             // solves held in the projection history ring
   bool proj_valid = false;        // the last Strang step started from the projection
+  // coupled anisotropic system (kfbi_create_coupled): the rows of the
+  // extracellular component in t2 (t holds the intracellular ones), the
+  // conductivities, and the Krylov vector length nk = 2M (M otherwise)
+  bool coupled = false;
+  kfbi::Coupling cpl;
+  kfbi::Tables t2;
+  int nk = 0;
   kfbi_mlp* warm = nullptr;       // learned warm start (not owned)
   // TMA descriptors of the float32 padded grid: [N x 32] tiles along y and z
   CUtensorMap tmap_y32, tmap_z32;
@@ -223,12 +242,6 @@ struct SolveArgs {
   bool keep = true;               // the x inverse pass also writes the padded work grid
 };
 int box_solve64(kfbi_handle* h, const SolveArgs& a, double* work);
-// coupled anisotropic system (Eq. pde1): per-axis conductivities of the two
-// components and the coupling kappa; scale is set by the solver
-struct Coupling {
-  double di[3] = {1.0, 1.0, 1.0}, de[3] = {1.0, 1.0, 1.0};
-  double kappa = 0.0, scale = 1.0;
-};
 // the float64 box solve of the coupled pair (sources / corrections / outputs
 // of the intracellular component in si, extracellular in se) on the padded
 // grids wa, wb
@@ -241,6 +254,17 @@ int make_tma_maps(kfbi_handle* h);
 
 // ops.cu
 int launch_correction(kfbi_handle* h, const double* x, double* corr);
+// the same with an explicit row set (the coupled system's second component)
+int launch_correction_t(kfbi_handle* h, const Tables& t, const double* x, double* corr);
+int launch_limit64_t(kfbi_handle* h, const Tables& t, const double* grid, const double* x, const double* base, double sgn,
+                     double* out);
+int launch_limit_user_t(kfbi_handle* h, const Tables& t, const double* u, const double* x, const double* base,
+                        double sgn, double* out);
+int launch_rank_one_coupled(kfbi_handle* h, const double* psi, double* out, double sgn);
+// V <- 2 (a - b) - V
+int launch_midpoint_diff(kfbi_handle* h, double* V, const double* a, const double* b, int64_t n);
+// dst = src - mean over Omega of src
+int launch_sub_mean(kfbi_handle* h, const double* src, double* dst);
 int launch_spline(kfbi_handle* h, const double* psi, double* x);
 int launch_limit64(kfbi_handle* h, const double* grid, const double* x, const double* base, double sgn, double* out);
 int launch_limit32(kfbi_handle* h, const float* grid, const double* x, const double* base, double sgn, double* out);

@@ -758,9 +758,11 @@ int small_hcol(int m) { return SmallLayout{m}.hcol(); }
 int small_nrm2(int m) { return SmallLayout{m}.nrm2(); }
 int small_y(int m) { return SmallLayout{m}.y(); }
 
-int launch_correction(kfbi_handle* h, const double* x, double* corr) {
-  if (h->t.n_irr == 0) return KFBI_OK;
-  k_correction<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->t, x, corr, h->skip);
+int launch_correction(kfbi_handle* h, const double* x, double* corr) { return launch_correction_t(h, h->t, x, corr); }
+
+int launch_correction_t(kfbi_handle* h, const Tables& t, const double* x, double* corr) {
+  if (t.n_irr == 0) return KFBI_OK;
+  k_correction<<<(t.n_irr + 127) / 128, 128, 0, h->stream>>>(t, x, corr, h->skip);
   KFBI_CHECK_LAUNCH();
   return KFBI_OK;
 }
@@ -773,7 +775,12 @@ int launch_spline(kfbi_handle* h, const double* psi, double* x) {
 }
 
 int launch_limit64(kfbi_handle* h, const double* grid, const double* x, const double* base, double sgn, double* out) {
-  k_limit<double><<<(h->t.M + 127) / 128, 128, 0, h->stream>>>(h->t, h->grid, grid, x, base, sgn, out, h->skip);
+  return launch_limit64_t(h, h->t, grid, x, base, sgn, out);
+}
+
+int launch_limit64_t(kfbi_handle* h, const Tables& t, const double* grid, const double* x, const double* base,
+                     double sgn, double* out) {
+  k_limit<double><<<(t.M + 127) / 128, 128, 0, h->stream>>>(t, h->grid, grid, x, base, sgn, out, h->skip);
   KFBI_CHECK_LAUNCH();
   return KFBI_OK;
 }
@@ -785,7 +792,12 @@ int launch_limit32(kfbi_handle* h, const float* grid, const double* x, const dou
 }
 
 int launch_limit_user(kfbi_handle* h, const double* u, const double* x, const double* base, double sgn, double* out) {
-  k_limit_user<<<(h->t.M + 127) / 128, 128, 0, h->stream>>>(h->t, h->grid, u, x, base, sgn, out);
+  return launch_limit_user_t(h, h->t, u, x, base, sgn, out);
+}
+
+int launch_limit_user_t(kfbi_handle* h, const Tables& t, const double* u, const double* x, const double* base,
+                        double sgn, double* out) {
+  k_limit_user<<<(t.M + 127) / 128, 128, 0, h->stream>>>(t, h->grid, u, x, base, sgn, out);
   KFBI_CHECK_LAUNCH();
   return KFBI_OK;
 }
@@ -847,6 +859,47 @@ int launch_ue_S(kfbi_handle* h, const double* V, const double* S, double* ue) {
   return KFBI_OK;
 }
 
+// out += sgn (1, 1) <(ds, ds), psi> / (2 |Gamma|) over the 2M entries of a
+// coupled density pair (ds2 = (ds, ds) / 2 precomputed): the rank-one term
+// of the coupled Neumann operator
+int launch_rank_one_coupled(kfbi_handle* h, const double* psi, double* out, double sgn) {
+  const int n = h->nk;
+  double* slot = h->w.proj + KFBI_HISTORY * (KFBI_HISTORY + 2) + 4;
+  int rc = vec_dots(h, h->w.ds2, 1, n, psi, slot);
+  if (rc) return rc;
+  k_add_scalar<<<(n + 255) / 256, 256, 0, h->stream>>>(out, slot, sgn / h->t.area, n);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+// V <- 2 (a - b) - V (implicit midpoint from the potentials of the coupled
+// solve: w = Phi_i - Phi_e)
+__global__ void k_midpoint_diff(double* __restrict__ V, const double* __restrict__ a, const double* __restrict__ b,
+                                int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    V[i] = 2.0 * (a[i] - b[i]) - V[i];
+}
+
+int launch_midpoint_diff(kfbi_handle* h, double* V, const double* a, const double* b, int64_t n) {
+  k_midpoint_diff<<<grid_blocks(n, 256), 256, 0, h->stream>>>(V, a, b, n);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+// dst = src - mean_Omega(src)
+int launch_sub_mean(kfbi_handle* h, const double* src, double* dst) {
+  const int n1 = h->grid.N - 1;
+  const int64_t total = h->grid.dim == 3 ? (int64_t)n1 * n1 * n1 : (int64_t)n1 * n1;
+  const int nb = RED_BLOCKS;
+  if (dst != src) KFBI_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)total, cudaMemcpyDeviceToDevice, h->stream));
+  k_masked_sum<<<nb, 256, 0, h->stream>>>(dst, h->t.inside, total, h->w.partial);
+  k_dots_final<<<1, 256, 0, h->stream>>>(h->w.partial, nb, 1, h->w.partial + nb);
+  k_sub_mean<<<grid_blocks(total, 256), 256, 0, h->stream>>>(dst, h->w.partial + nb, 1.0 / (double)h->t.n_inside,
+                                                             total);
+  KFBI_CHECK_LAUNCH_N(3);
+  return KFBI_OK;
+}
+
 int launch_midpoint(kfbi_handle* h, double* V, const double* vV, const double* uB, int64_t n) {
   k_midpoint<<<grid_blocks(n, 256), 256, 0, h->stream>>>(V, vV, uB, n);
   KFBI_CHECK_LAUNCH();
@@ -879,7 +932,7 @@ int launch_padded_to_user(kfbi_handle* h, const double* padded, double* user) {
 // G = H H^T (k x k), b = H g, gg = g . g for the k <= KFBI_HISTORY stored
 // right-hand sides H (rows of length M), in one launch
 int launch_gram(kfbi_handle* h, const double* H, int k, const double* g, double* G, double* b, double* gg) {
-  const int n = h->t.M;
+  const int n = h->nk;
   int nb = (n + 255) / 256;
   if (nb > RED_BLOCKS) nb = RED_BLOCKS;
   double* pt = h->w.partial;
@@ -903,7 +956,7 @@ int launch_gram(kfbi_handle* h, const double* H, int k, const double* g, double*
 }
 
 int vec_dots(kfbi_handle* h, const double* V, int nvec, int ld, const double* w, double* out_dev) {
-  const int n = h->t.M;
+  const int n = h->nk;
   int nb = (n + 255) / 256;
   if (nb > RED_BLOCKS) nb = RED_BLOCKS;
   k_dots_partial<<<dim3(nb, nvec), 256, 0, h->stream>>>(V, ld, w, n, h->w.partial);
@@ -913,7 +966,7 @@ int vec_dots(kfbi_handle* h, const double* V, int nvec, int ld, const double* w,
 }
 
 int vec_update(kfbi_handle* h, double* w, const double* V, int nvec, int ld, const double* coef_dev, double sign) {
-  const int n = h->t.M;
+  const int n = h->nk;
   k_update<<<grid_blocks(n, 256), 256, 0, h->stream>>>(w, V, nvec, ld, coef_dev, sign, n);
   KFBI_CHECK_LAUNCH();
   return KFBI_OK;
@@ -953,7 +1006,7 @@ int arnoldi_solve(kfbi_handle* h, double* small, int k, int m) {
 // small[res + 1] the residual estimate and the stop flag (also written to
 // h->w.stop).  Launches carry h->skip.
 int arnoldi_step(kfbi_handle* h, double* V, int ld, double* wv, int j, int m, double gnorm, double tol) {
-  const int n = h->t.M;
+  const int n = h->nk;
   int nb = (n + 255) / 256;
   if (nb > ARN_BLOCKS) nb = ARN_BLOCKS;
   SmallLayout L{m};

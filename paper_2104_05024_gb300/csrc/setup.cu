@@ -1058,6 +1058,8 @@ int setup_build(kfbi_handle* h, const kfbi_geometry* geom) {
     host_spline_column(t.M, gcol);
     if ((rc = upload(h, &t.spline_G, gcol.data(), gcol.size()))) return rc;
   }
+  if (h->coupled)
+    for (int a = 0; a < 3; ++a) t.cond[a] = a < d ? h->cpl.di[a] : 1.0;
   if ((rc = dalloc(h, &t.c_cnt, (size_t)t.n_int))) return rc;
   if ((rc = dalloc(h, &t.c_pid, (size_t)t.n_int * PATCH_MAX))) return rc;
   if ((rc = dalloc(h, &t.c_wlo, (size_t)t.n_int * PATCH_MAX))) return rc;
@@ -1084,6 +1086,30 @@ int setup_build(kfbi_handle* h, const kfbi_geometry* geom) {
     KFBI_CUDA(cudaStreamSynchronize(st));
     cudaFree(AB);
     KFBI_CHECK_LAUNCH();
+  }
+
+  // coupled system: the extracellular component's correction and limit rows
+  // (conductivity D_e) in t2; everything else is shared with t
+  if (h->coupled) {
+    Tables& t2 = h->t2;
+    t2 = t;
+    for (int a = 0; a < 3; ++a) t2.cond[a] = a < d ? h->cpl.de[a] : 1.0;
+    if ((rc = dalloc(h, &t2.c_wlo, (size_t)t.n_int * PATCH_MAX))) return rc;
+    if ((rc = dalloc(h, &t2.c_whi, (size_t)t.n_int * PATCH_MAX))) return rc;
+    if ((rc = dalloc(h, &t2.n_wn, (size_t)t.M * t.P))) return rc;
+    if ((rc = dalloc(h, &t2.n_dw, (size_t)t.M * (PATCH_MAX + 1)))) return rc;
+    if (t.n_int > 0) k_crossing_rows<<<(t.n_int + 63) / 64, 64, 0, st>>>(gp, gr, di, t.inside, t2, err);
+    double* AB = nullptr;
+    KFBI_CUDA(cudaMalloc(&AB, sizeof(double) * 4 * (size_t)t.M));
+    k_node_stencil<<<(t.M + 63) / 64, 64, 0, st>>>(gp, gr, di, t.inside, AB, t2, err);
+    int herr = 0;
+    KFBI_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KFBI_CUDA(cudaStreamSynchronize(st));
+    if (!(herr & DEVERR_GEOMETRY))
+      k_node_density<<<(t.M + 63) / 64, 64, 0, st>>>(gp, gr, di, vtri_d, AB, t2, err);
+    KFBI_CUDA(cudaStreamSynchronize(st));
+    cudaFree(AB);
+    KFBI_CHECK_LAUNCH_N(3);
   }
 
   // boundary quadrature weights (the rank-one term of the Poisson operator):
@@ -1117,6 +1143,13 @@ int setup_build(kfbi_handle* h, const kfbi_geometry* geom) {
     t.area = 0.0;
     for (int i = 0; i < M; ++i) t.area += ds[i];
     if ((rc = upload(h, &t.ds, ds.data(), ds.size()))) return rc;
+    h->t2.ds = t.ds;
+    h->t2.area = t.area;
+    if (h->coupled) {
+      std::vector<double> ds2(2 * (size_t)M);
+      for (int i = 0; i < M; ++i) ds2[i] = ds2[M + i] = 0.5 * ds[i];
+      if ((rc = upload(h, &h->w.ds2, ds2.data(), ds2.size()))) return rc;
+    }
   }
 
   // transform tables
@@ -1135,6 +1168,10 @@ int setup_build(kfbi_handle* h, const kfbi_geometry* geom) {
     if ((rc = upload(h, &t.tw64, tw.data(), tw.size()))) return rc;
     if ((rc = upload(h, &t.mu32, mu32.data(), mu32.size()))) return rc;
     if ((rc = upload(h, &t.tw32, tw32.data(), tw32.size()))) return rc;
+    h->t2.mu = t.mu;
+    h->t2.tw64 = t.tw64;
+    h->t2.mu32 = t.mu32;
+    h->t2.tw32 = t.tw32;
   }
   // inside count
   {

@@ -71,7 +71,8 @@ EXPORTS = [
     "kfbi_mlp_train_step", "kfbi_set_warmstart", "kfbi_get_densities", "kfbi_set_densities",
     "kfbi_get_history", "kfbi_set_history", "kfbi_get_projection", "kfbi_bidomain_step_stim",
     "kfbi_selftest_bounded_wait", "kfbi_get_warm_guess", "kfbi_training_rows", "kfbi_mlp_fit_norm",
-    "kfbi_mlp_layers",
+    "kfbi_mlp_layers", "kfbi_create_coupled", "kfbi_solve_coupled", "kfbi_box_solve_coupled",
+    "kfbi_apply_A_coupled",
 ]
 
 
@@ -216,6 +217,11 @@ def load(path: str = LIB_PATH):
     lib.kfbi_training_rows.argtypes = [vp, vp, vp]
     lib.kfbi_mlp_fit_norm.argtypes = [vp, vp, ip, vp, fp]
     lib.kfbi_mlp_layers.argtypes = [vp, vp, vp, ip, vp, vp, vp, vp]
+    lib.kfbi_create_coupled.argtypes = [C.POINTER(Geometry), C.POINTER(GridStruct), dp, dp, C.c_double,
+                                        C.POINTER(Opts), C.POINTER(vp)]
+    lib.kfbi_solve_coupled.argtypes = [vp, C.c_double, vp, vp, vp, vp, vp, vp, vp, C.POINTER(Stats)]
+    lib.kfbi_box_solve_coupled.argtypes = [vp, C.c_double, vp, vp, vp, vp]
+    lib.kfbi_apply_A_coupled.argtypes = [vp, C.c_double, vp, vp]
     for name in EXPORTS:
         if name not in ("kfbi_last_error", "kfbi_destroy", "kfbi_launch_count", "kfbi_mlp_destroy"):
             getattr(lib, name).restype = C.c_int
@@ -263,7 +269,9 @@ class KFBI:
     tri_offset) -- e.g. kfbi_workloads.geometry.Geometry."""
 
     def __init__(self, geom, grid, sigma_i=1.0, sigma_e=2.0, dt=0.05, precision=FP64, solver=GMRES, tol=1e-10,
-                 restart=50, max_iter=500, gamma=0.8, lo=-1.0, hi=1.0, warm=WARM_PREVIOUS):
+                 restart=50, max_iter=500, gamma=0.8, lo=-1.0, hi=1.0, warm=WARM_PREVIOUS, D_i=None, D_e=None):
+        """D_i, D_e (sequences of dim conductivities): the anisotropic coupled
+        system (kfbi_create_coupled) instead of the isotropic decoupled one."""
         lib = load()
         self._keep = []
         g = Geometry()
@@ -296,7 +304,13 @@ class KFBI:
         gs = GridStruct(self.dim, self.N, float(getattr(grid, "lo", lo)), float(getattr(grid, "hi", hi)))
         self.opts = Opts(precision, solver, tol, restart, max_iter, gamma, _stream(), warm)
         h = C.c_void_p()
-        _check(lib.kfbi_create(C.byref(g), C.byref(gs), sigma_i, sigma_e, dt, C.byref(self.opts), C.byref(h)))
+        self.coupled = D_i is not None
+        if self.coupled:
+            di = (C.c_double * 3)(*[float(x) for x in list(D_i)[:3]] + [1.0] * (3 - len(list(D_i)[:3])))
+            de = (C.c_double * 3)(*[float(x) for x in list(D_e)[:3]] + [1.0] * (3 - len(list(D_e)[:3])))
+            _check(lib.kfbi_create_coupled(C.byref(g), C.byref(gs), di, de, dt, C.byref(self.opts), C.byref(h)))
+        else:
+            _check(lib.kfbi_create(C.byref(g), C.byref(gs), sigma_i, sigma_e, dt, C.byref(self.opts), C.byref(h)))
         self._h = h
         self.M = g.n_nodes
         info = Info()
@@ -427,6 +441,22 @@ class KFBI:
     def rhs_g(self, f, gN, g, lam):
         self.set_opts()
         _check(load().kfbi_rhs_g(self._h, lam, _ptr(f), _ptr(gN), _ptr(g)))
+
+    def solve_coupled(self, fi, fe, gNi, gNe, phi_i, phi_e, psi, kappa, **opts):
+        """The coupled Neumann problem (psi: 2M density pair, in/out)."""
+        self.set_opts(**opts)
+        st = Stats()
+        _check(load().kfbi_solve_coupled(self._h, kappa, _ptr(fi), _ptr(fe), _ptr(gNi), _ptr(gNe), _ptr(phi_i),
+                                         _ptr(phi_e), _ptr(psi), C.byref(st)), allow=(ERR_NOT_CONVERGED,))
+        return st.as_dict()
+
+    def box_solve_coupled(self, ri, re, vi, ve, kappa):
+        self.set_opts()
+        _check(load().kfbi_box_solve_coupled(self._h, kappa, _ptr(ri), _ptr(re), _ptr(vi), _ptr(ve)))
+
+    def apply_A_coupled(self, psi, out, kappa):
+        self.set_opts()
+        _check(load().kfbi_apply_A_coupled(self._h, kappa, _ptr(psi), _ptr(out)))
 
     def solve_bie(self, g, psi, lam, **opts):
         self.set_opts(**opts)

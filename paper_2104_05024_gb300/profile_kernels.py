@@ -1,6 +1,6 @@
 """Launch the hot-path kernels of one workload a few times each, for ncu.
 
-    python -m paper_2104_05024_gb300.profile_kernels [--N 256] [--precision fp64|mixed] [--reps 3]
+    python -m paper_2104_05024_gb300.profile_kernels [--N 256] [--precision fp64|mixed] [--reps 3] [--passes-only]
 
 Sets up the prolate-shell workload (configs 2/3 geometry), then runs each
 transform pass of the box solver, one irregular-node correction and one
@@ -31,6 +31,7 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--strang", action="store_true")
+    ap.add_argument("--passes-only", action="store_true", help="only the four transform passes (no A psi)")
     a = ap.parse_args()
     prec = K.FP64 if a.precision == "fp64" else K.MIXED
     geom, grid, cfg, V0, w0 = C.config2(N=a.N)
@@ -42,7 +43,8 @@ def main():
     for _ in range(a.reps):
         for p in (0, 1, 2, 3):
             h.transform_pass(p, lam, prec)
-        h.apply_A(psi, out, lam, prec)
+        if not a.passes_only:
+            h.apply_A(psi, out, lam, prec)
     if a.strang:
         V = torch.tensor(V0, device=dev)
         w = torch.tensor(w0, device=dev)
