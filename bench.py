@@ -4,7 +4,7 @@ the 256^3 prolate-shell workload, each diffusion solve converged to a 1e-8
 GMRES residual, through the KFBI library's C ABI on one GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl kfbi|reference]
-    python bench.py --workload star-sweep|shell-large|heldout|stiff|stimulus
+    python bench.py --workload star-sweep|shell-large|heldout|stiff|stimulus|coupled
 
 One JSON line on rank 0.  Multi-GPU runs are independent replicas (one
 stimulus location per rank, no data-path collective); `value` sums the ranks.
@@ -491,9 +491,27 @@ def run_star_sweep(args):
         rows.append(row)
         prev = row
         h.close()
+    # the stated node count (cube-sphere resolution n = N: about 6 N^2 nodes,
+    # spacing about 0.47 h), float64, 300 iterations at most
+    from kfbi_workloads import geometry as G
+    dense = []
+    for N in (32, 64):
+        geom, grid = G.star_config1(N), C.Grid(3, N)
+        lam, tol = 40.0, 1e-10
+        h = K.KFBI(geom, grid, tol=tol, restart=50, max_iter=300)
+        f, u_ex, gN = C.manufactured(geom, grid, lam)
+        inside = h.export_setup()["inside"]
+        u = torch.empty(grid.shape, dtype=torch.float64, device=dev)
+        psi = torch.zeros(geom.M, dtype=torch.float64, device=dev)
+        st = h.solve_neumann(torch.tensor(f, device=dev), torch.tensor(gN, device=dev), u, psi, lam, tol=tol,
+                             max_iter=300)
+        e = np.abs(u.cpu().numpy() - u_ex)
+        dense.append({"N": N, "M": geom.M, "iters": st["iters"], "rel_res": st["rel_res"],
+                      "converged": st["rel_res"] <= tol, "max_err": float(e[inside].max())})
+        h.close()
     print(json.dumps({"metric": "star-body Neumann solve: max error, observed order, time", "workload":
                       "config 1: star r = 0.6 + 0.1 sin(3 theta) cos(2 phi), lambda 40, tol 1e-10",
-                      "unit": "ms", "rows": rows}), flush=True)
+                      "unit": "ms", "rows": rows, "rows_6N2_nodes": dense}), flush=True)
 
 
 def run_shell_large(args):
@@ -652,6 +670,45 @@ def run_stimulus(args):
                       "unit": "steps/s", "rows": rows}), flush=True)
 
 
+def run_coupled(args):
+    """The anisotropic coupled system (Eq. pde1) with the paper's conductivity
+    tensors D_i = diag(30, 5, 5), D_e = diag(20, 10, 10) (Examples 1-3) on the
+    shell at N^3, FitzHugh-Nagumo of the workloads, dt 0.05, float64, GMRES
+    to 1e-8: Strang steps/s and iterations per step, and the coupled box solve
+    (two fields, per-mode 2 x 2 solve) against the scalar float64 one."""
+    import torch
+
+    import paper_2104_05024_gb300.kfbi as K
+    from kfbi_workloads import configs as C
+    dev = torch.device("cuda", 0)
+    N = args.N
+    geom, grid, cfg, V0, w0 = C.config2(N=N)
+    Di, De = (30.0, 5.0, 5.0), (20.0, 10.0, 10.0)
+    h = K.KFBI(geom, grid, D_i=Di, D_e=De, dt=cfg.dt, tol=cfg.tol, restart=50, max_iter=600)
+    V, w = torch.tensor(V0, device=dev), torch.tensor(w0, device=dev)
+    ue = torch.empty_like(V)
+    h.bidomain_step(C.FHN_CONFIG, V, w, None, nsteps=2)
+    ms, st = _event_ms(lambda: h.bidomain_step(C.FHN_CONFIG, V, w, ue, nsteps=args.steps))
+    r = torch.randn(grid.shape, dtype=torch.float64, device=dev)
+    vi, ve = torch.empty_like(r), torch.empty_like(r)
+    h.box_solve_coupled(r, r, vi, ve, 40.0)
+    box_ms, _ = _event_ms(lambda: h.box_solve_coupled(r, r, vi, ve, 40.0), reps=5)
+    h.close()
+    hs = K.KFBI(geom, grid, tol=cfg.tol)
+    hs.box_solve(r, vi, 60.0, precision=K.FP64)
+    box1_ms, _ = _event_ms(lambda: hs.box_solve(r, vi, 60.0, precision=K.FP64), reps=5)
+    hs.close()
+    print(json.dumps({"metric": "anisotropic coupled Strang steps/s (float64)",
+                      "workload": f"shell {N}^3, D_i diag(30, 5, 5), D_e diag(20, 10, 10), FHN of the workloads, "
+                                  f"dt 0.05, tol 1e-8, {args.steps} steps after 2",
+                      "unit": "steps/s", "steps_per_s": round(1000.0 * args.steps / ms, 3),
+                      "iters_per_step": float(np.mean([s["iters"] for s in st])),
+                      "true_rel_res_max": float(max(s["true_rel_res"] for s in st)),
+                      "V_max": float(V.abs().max()), "ue_max": float(ue.abs().max()),
+                      "coupled_box_solve_ms": round(box_ms, 3), "scalar_box_solve_ms": round(box1_ms, 3)}),
+          flush=True)
+
+
 # -------------------------------------------------------------- CPU oracle
 
 def cpu_baseline(N, steps=1):
@@ -709,7 +766,7 @@ def main():
     ap.add_argument("--train-steps", type=int, default=12, help="Strang steps per training stimulus (learned form)")
     ap.add_argument("--train-epochs", type=int, default=8)
     ap.add_argument("--workload", default="strang",
-                    choices=["strang", "star-sweep", "shell-large", "heldout", "stiff", "stimulus"],
+                    choices=["strang", "star-sweep", "shell-large", "heldout", "stiff", "stimulus", "coupled"],
                     help="strang: the timed benchmark; the others print one result line each")
     args = ap.parse_args()
     if args.steps is None:
@@ -726,6 +783,8 @@ def main():
         run_stiff(args)
     elif args.workload == "stimulus":
         run_stimulus(args)
+    elif args.workload == "coupled":
+        run_coupled(args)
     else:
         run_gpu(args)
 

@@ -77,6 +77,11 @@ struct Tables {
   int32_t* irr_arm = nullptr;     // [n_irr][6] arm codes: crossing*2 + end (end 0 = lower node)
   int8_t* irr_narm = nullptr;     // [n_irr]
   int32_t* line_start = nullptr;  // [(N-1)^(dim-1) + 1] first irregular index of each x-line
+  // each irregular node's correction as one row on the density vector: the
+  // rows of its crossing arms' end weights, concatenated (CSR)
+  int32_t* cr_ptr = nullptr;      // [n_irr + 1]
+  int32_t* cr_pid = nullptr;      // [nnz] density-vector indices
+  double* cr_w = nullptr;         // [nnz] weights
   // crossings, sorted by (axis, lower node)
   int n_int = 0;
   int32_t* c_axis = nullptr;
@@ -188,6 +193,7 @@ struct kfbi_handle {
   // extracellular component in t2 (t holds the intracellular ones), the
   // conductivities, and the Krylov vector length nk = 2M (M otherwise)
   bool coupled = false;
+  int cr_nnz = 0;                 // entries of the CSR correction rows
   kfbi::Coupling cpl;
   kfbi::Tables t2;
   int nk = 0;

@@ -19,20 +19,15 @@ constexpr int RED_BLOCKS = 152;  // one partial sum per SM for the dot products
 // partial-sum buffer holds ARN_BLOCKS x (MAX_RESTART + 2) values
 constexpr int ARN_BLOCKS = KFBI_ARN_BLOCKS;
 
+// corr_i = sum over the node's CSR row of w_k x[pid_k] (the row is its arms'
+// crossing rows concatenated, built at setup: two dependent loads per entry)
 __global__ void k_correction(Tables t, const double* __restrict__ x, double* __restrict__ corr,
                              const int* __restrict__ skip) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= t.n_irr || (skip != nullptr && *skip)) return;
-  const int na = t.irr_narm[i];
+  const int k0 = t.cr_ptr[i], k1 = t.cr_ptr[i + 1];
   double acc = 0.0;
-  for (int a = 0; a < na; ++a) {
-    const int code = t.irr_arm[(size_t)i * 6 + a];
-    const int c = code >> 1;
-    const double* w = (code & 1) ? t.c_whi : t.c_wlo;
-    const int K = t.c_cnt[c];
-    const size_t o = (size_t)c * PATCH_MAX;
-    for (int q = 0; q < K; ++q) acc += w[o + q] * x[t.c_pid[o + q]];
-  }
+  for (int k = k0; k < k1; ++k) acc += t.cr_w[k] * x[t.cr_pid[k]];
   corr[i] = acc;
 }
 

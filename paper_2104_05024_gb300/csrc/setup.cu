@@ -821,6 +821,24 @@ __global__ void k_irr_arms(GridParams gr, const uint8_t* inside, Tables t, const
   t.irr_narm[i] = (int8_t)na;
 }
 
+// CSR correction rows of the irregular nodes (pointers computed on the host)
+__global__ void k_corr_rows(Tables t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.n_irr) return;
+  int pos = t.cr_ptr[i];
+  const int na = t.irr_narm[i];
+  for (int a = 0; a < na; ++a) {
+    const int code = t.irr_arm[(size_t)i * 6 + a];
+    const int c = code >> 1;
+    const double* w = (code & 1) ? t.c_whi : t.c_wlo;
+    const int K = t.c_cnt[c];
+    for (int q = 0; q < K; ++q, ++pos) {
+      t.cr_pid[pos] = t.c_pid[(size_t)c * PATCH_MAX + q];
+      t.cr_w[pos] = w[(size_t)c * PATCH_MAX + q];
+    }
+  }
+}
+
 __global__ void k_line_start(const int32_t* irr, int n_irr, int n1, int n_lines, int32_t* line_start) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i > n_irr) return;
@@ -969,6 +987,36 @@ int upload(kfbi_handle* h, T** dst, const T* src, size_t n) {
 
 }  // namespace
 
+// the CSR correction rows of t (new_pattern: also the pointers and indices;
+// else they are shared with h->t and only the weights are built)
+int build_corr_csr(kfbi_handle* h, Tables& t, bool new_pattern) {
+  cudaStream_t st = h->stream;
+  int rc;
+  if (new_pattern) {
+    std::vector<int32_t> arm((size_t)t.n_irr * 6), cnt((size_t)t.n_int), ptr((size_t)t.n_irr + 1, 0);
+    std::vector<int8_t> narm((size_t)t.n_irr);
+    if (t.n_irr > 0) {
+      KFBI_CUDA(cudaMemcpyAsync(arm.data(), t.irr_arm, sizeof(int32_t) * arm.size(), cudaMemcpyDeviceToHost, st));
+      KFBI_CUDA(cudaMemcpyAsync(narm.data(), t.irr_narm, narm.size(), cudaMemcpyDeviceToHost, st));
+    }
+    if (t.n_int > 0)
+      KFBI_CUDA(cudaMemcpyAsync(cnt.data(), t.c_cnt, sizeof(int32_t) * cnt.size(), cudaMemcpyDeviceToHost, st));
+    KFBI_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < t.n_irr; ++i) {
+      int k = 0;
+      for (int a = 0; a < narm[i]; ++a) k += cnt[arm[(size_t)i * 6 + a] >> 1];
+      ptr[i + 1] = ptr[i] + k;
+    }
+    if ((rc = upload(h, &t.cr_ptr, ptr.data(), ptr.size()))) return rc;
+    if ((rc = dalloc(h, &t.cr_pid, (size_t)ptr[t.n_irr]))) return rc;
+    h->cr_nnz = ptr[t.n_irr];
+  }
+  if ((rc = dalloc(h, &t.cr_w, (size_t)h->cr_nnz))) return rc;
+  if (t.n_irr > 0) k_corr_rows<<<(t.n_irr + 127) / 128, 128, 0, st>>>(t);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
 int setup_build(kfbi_handle* h, const kfbi_geometry* geom) {
   const GridParams gr = h->grid;
   GeomParams& gp = h->gp;
@@ -1088,6 +1136,8 @@ int setup_build(kfbi_handle* h, const kfbi_geometry* geom) {
     KFBI_CHECK_LAUNCH();
   }
 
+  // CSR correction rows of the irregular nodes
+  if ((rc = build_corr_csr(h, t, true))) return rc;
   // coupled system: the extracellular component's correction and limit rows
   // (conductivity D_e) in t2; everything else is shared with t
   if (h->coupled) {
@@ -1110,6 +1160,7 @@ int setup_build(kfbi_handle* h, const kfbi_geometry* geom) {
     KFBI_CUDA(cudaStreamSynchronize(st));
     cudaFree(AB);
     KFBI_CHECK_LAUNCH_N(3);
+    if ((rc = build_corr_csr(h, t2, false))) return rc;
   }
 
   // boundary quadrature weights (the rank-one term of the Poisson operator):
