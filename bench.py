@@ -343,10 +343,14 @@ def _pass_times(h, prec, lam, reps, flush=None):
     return out
 
 
-# DRAM bytes per launch of each transform pass from one ncu capture of the
-# committed kernels (profiles/box_solve_fp32_passes.md; read + write), by
-# grid size and pass; the five-pass solve runs pass 1 twice
-NCU_DRAM_BYTES = {}
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum, caches flushed
+# before each launch) per launch of each transform pass of the current
+# kernels, by (N, element size) and pass 0..3; the five-pass solve runs pass 1
+# twice.  Kernels changed since the capture must drop their entry.
+NCU_DRAM_BYTES = {
+    (256, 4): (4.7e6, 70.3e6, 70.8e6, 71.5e6),
+    (512, 4): (472.7e6, 1007.1e6, 1007.2e6, 1006.6e6),
+}
 
 
 def box_solve_roofline(h, N, prec, lam, pk, kind, dev):
