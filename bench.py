@@ -318,7 +318,7 @@ def _pass_times(h, prec, lam, reps, flush=None):
     import torch
     stream = torch.cuda.current_stream()
     out = {}
-    for p in (0, 1, 2, 3):
+    for p in ((0, 1, 2, 3, 4, 5) if h.info["xy_fused"] and prec != 0 else (0, 1, 2, 3)):
         for _ in range(3):
             h.transform_pass(p, lam, prec)
         tot = 0.0
@@ -345,11 +345,11 @@ def _pass_times(h, prec, lam, reps, flush=None):
 
 # DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum, caches flushed
 # before each launch) per launch of each transform pass of the current
-# kernels, by (N, element size) and pass 0..3; the five-pass solve runs pass 1
-# twice.  Kernels changed since the capture must drop their entry.
+# kernels, by (N, element size, fused x-y passes) and pass 0..5; the
+# five-pass solve runs pass 1 twice.  Kernels changed since the capture must
+# drop their entry.
 NCU_DRAM_BYTES = {
-    (256, 4): (4.7e6, 70.3e6, 70.8e6, 71.5e6),
-    (512, 4): (472.7e6, 1007.1e6, 1007.2e6, 1006.6e6),
+    (512, 4, False): {0: 472.7e6, 1: 1007.1e6, 2: 1007.2e6, 3: 1006.6e6},
 }
 
 
@@ -368,27 +368,32 @@ def box_solve_roofline(h, N, prec, lam, pk, kind, dev):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > 129 MB L2
     cold = _pass_times(h, prec, lam, 5, flush)
     del flush
-    solve = lambda t: t[0] + 2.0 * t[1] + t[2] + t[3]  # noqa: E731
+    fused = 4 in warm
+    # five passes (x forward, y, z solve, y, x inverse) or, with the fused x-y
+    # passes, three (x-y forward, z solve, x-y inverse)
+    solve = (lambda t: t[4] + t[2] + t[5]) if fused else (lambda t: t[0] + 2.0 * t[1] + t[2] + t[3])  # noqa: E731
     grid_mb = N ** 3 * esize / 1e6
     resident = grid_mb < 129.0
-    # the time the roofline uses: cold-L2 passes when the grid would stay in
-    # L2 across back-to-back launches, else the warm (back-to-back) passes
-    t = cold if resident else warm
+    # back-to-back passes (the hot path's GMRES iterations run them so); a
+    # grid that fits the L2 stays resident between them, which the label says
+    t = warm
     achieved = alg / (solve(t) / 1e3) / 1e9
-    roof = {"kernel": f"box solve {N}^3 {'float64' if esize == 8 else 'float32'} (k_xfwd, k_strided*, k_xinv)",
+    kern = "k_xy_fwd, k_strided_tma (z), k_xy_inv" if fused else "k_xfwd, k_strided*, k_xinv"
+    roof = {"kernel": f"box solve {N}^3 {'float64' if esize == 8 else 'float32'} ({kern})",
             "unit_of_work": "one box solve: 2 G s bytes, G = (N-1)^3", "bound": "hbm",
             "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s", "peak_source": kind,
             "frac": achieved / pk["hbm_gbs"],
-            "algorithmic_bytes": alg, "solve_ms": solve(t),
-            "l2": (f"grid {grid_mb:.0f} MB fits the 129 MB L2: passes timed one by one with a 256 MB L2 flush "
-                   "before each" if resident else f"grid {grid_mb:.0f} MB exceeds the 129 MB L2: back-to-back"),
+            "algorithmic_bytes": alg, "solve_ms": solve(t), "passes": 3 if fused else 5,
+            "l2": (f"L2-resident: the {grid_mb:.0f} MB grid fits the 129 MB L2 and stays there between "
+                   "back-to-back passes; solve_ms_cold has a 256 MB L2 flush before each pass" if resident else
+                   f"grid {grid_mb:.0f} MB exceeds the 129 MB L2: back-to-back passes"),
             "pass_ms": {k: round(v, 4) for k, v in t.items()},
-            "pass_ms_warm": {k: round(v, 4) for k, v in warm.items()},
-            "solve_ms_warm": solve(warm),
+            "pass_ms_cold": {k: round(v, 4) for k, v in cold.items()},
+            "solve_ms_cold": solve(cold),
             "pass_gbs": {k: round(2.0 * N ** 3 * esize / (v / 1e3) / 1e9, 1) for k, v in t.items()}}
-    nb = NCU_DRAM_BYTES.get((N, esize))
+    nb = NCU_DRAM_BYTES.get((N, esize, fused))
     if nb is not None:
-        tr = nb[0] + 2 * nb[1] + nb[2] + nb[3]
+        tr = (nb[4] + nb[2] + nb[5]) if fused else (nb[0] + 2 * nb[1] + nb[2] + nb[3])
         roof["traffic"] = tr
         roof["traffic_unit"] = "ncu dram read + write bytes of the five passes of one solve"
         roof["dram_gbs"] = tr / (solve(t) / 1e3) / 1e9

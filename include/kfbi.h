@@ -150,6 +150,8 @@ typedef struct {
   double lambda;       /* lambda = (2 / dt)(1/sigma_i + 1/sigma_e) of the
                           implicit-midpoint V problem with Cm beta = 1
                           (bidomain_step scales it by the kfbi_fhn's Cm beta) */
+  int xy_fused;        /* 1: float32 3-D box solves take three passes (fused
+                          x-y forward, z solve, fused x-y inverse)           */
 } kfbi_info;
 
 typedef struct kfbi_handle kfbi_handle;
@@ -397,8 +399,9 @@ int kfbi_training_rows(kfbi_handle* h, float* F_dev, float* T_dev);
 /* One pass of the box solver on the handle's padded work grid, for timing
  * the transform kernels in isolation: pass 0 = x forward (no right-hand
  * side), 1 = y forward, 2 = z solve (forward, spectral divide, inverse; the
- * y solve in 2-D), 3 = x inverse.  precision KFBI_FP64 or KFBI_MIXED.  The
- * grid content is arbitrary afterwards.                                      */
+ * y solve in 2-D), 3 = x inverse; with kfbi_info.xy_fused also 4 = fused x-y
+ * forward and 5 = fused x-y inverse (KFBI_MIXED).  precision KFBI_FP64 or
+ * KFBI_MIXED.  The grid content is arbitrary afterwards.                     */
 int kfbi_transform_pass(kfbi_handle* h, int precision, int pass, double lambda);
 
 /* Self-test of the bounded waits of the TMA-fed transform kernels (no

@@ -829,6 +829,7 @@ int kfbi_query(kfbi_handle* h, kfbi_info* info) {
   info->n_inside = h->t.n_inside;
   info->device_bytes = h->device_bytes;
   info->lambda = h->lambda;
+  info->xy_fused = h->xy_fused ? 1 : 0;
   return KFBI_OK;
 }
 
@@ -1521,8 +1522,8 @@ int kfbi_training_rows(kfbi_handle* h, float* F_dev, float* T_dev) {
 
 int kfbi_transform_pass(kfbi_handle* h, int precision, int pass, double lambda) {
   if (int rc = check_handle(h)) return rc;
-  if (pass < 0 || pass > 3) {
-    set_error("pass must be 0..3");
+  if (pass < 0 || pass > 5) {
+    set_error("pass must be 0..5");
     return KFBI_ERR_ARG;
   }
   return transform_pass(h, precision, pass, lambda);

@@ -26,6 +26,8 @@
 
 #include <cudaTypedefs.h>
 
+#include <cooperative_groups.h>
+
 #include <cmath>
 
 #include "dst_reg.cuh"
@@ -679,6 +681,191 @@ __global__ void __launch_bounds__(NT, tma_blocks<SOLVE>()) k_strided_tma(const _
   if (threadIdx.x == 0) tma_wait_all();
 }
 
+// ------------------------------- fused x and y passes (thread-block clusters)
+// One z-plane of the padded float32 grid is transformed along x and then y
+// by a cluster of N / 32 blocks (N <= 256) that exchange the plane through
+// distributed shared memory, so the plane crosses global memory once per
+// direction instead of twice.  Block r of the cluster owns the 32 y-lines
+// y = 32 r + c (tile A: rows x, columns c) for the x transform and the 32
+// x-modes kx = 32 r + c (tile B: rows y, columns c) for the y transform.
+// Between the two, block r reads from every block q the 32 x 32 piece
+// A_q[32 r .. 32 r + 31][0 .. 31] (rows of 32 consecutive words in the
+// owner's shared memory) and writes it transposed into B rows 32 q ..
+// 32 q + 31; the row stride 33 keeps both sides free of bank conflicts.  A
+// cluster barrier after the first transform makes every A complete before it
+// is read; a second one after the exchange keeps each block's shared memory
+// alive until its peers have read it.
+namespace cg = cooperative_groups;
+
+template <int N>
+constexpr size_t xy_smem_bytes() {
+  using C = Cfg<float, N>;
+  return (2 * (size_t)N * C::RS + (size_t)C::G * C::W + 5 * (size_t)N) * sizeof(float);
+}
+
+// dst[(32 q + lane) RS + j] = src_q[(y0 + j) RS + lane] for every block q of
+// the cluster and j < 32: the transposed 32 x 32 pieces.  Warp w moves rows
+// j = w + 8 i; the distributed-shared-memory loads of four blocks are issued
+// together (16 in flight per thread) before their stores.
+template <int N>
+__device__ __forceinline__ void xy_exchange(const cg::cluster_group& cluster, float* src, float* dst, int y0) {
+  using C = Cfg<float, N>;
+  constexpr int W = C::W, RS = C::RS, CL = N / W, R = W / (NT / 32), QB = CL < 4 ? CL : 4;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll 1
+  for (int q0 = 0; q0 < CL; q0 += QB) {
+    float v[QB][R];
+#pragma unroll
+    for (int k = 0; k < QB; ++k) {
+      const float* ps = cluster.map_shared_rank(src, q0 + k);
+#pragma unroll
+      for (int i = 0; i < R; ++i) v[k][i] = ps[(y0 + warp + (NT / 32) * i) * RS + lane];
+    }
+#pragma unroll
+    for (int k = 0; k < QB; ++k)
+#pragma unroll
+      for (int i = 0; i < R; ++i) dst[((q0 + k) * W + lane) * RS + warp + (NT / 32) * i] = v[k][i];
+  }
+}
+
+// forward: r = alpha src + corrections (as k_xfwd), x DST, exchange, y DST
+template <int N>
+__global__ void __launch_bounds__(NT) k_xy_fwd(float* __restrict__ a, const double* __restrict__ src, double alpha,
+                                               const float* __restrict__ src32, const double* __restrict__ corr,
+                                               const int32_t* __restrict__ irr, const int32_t* __restrict__ line_start,
+                                               const float* __restrict__ tw_g, const int* __restrict__ skip) {
+  using C = Cfg<float, N>;
+  constexpr int W = C::W, RS = C::RS, n1 = N - 1, CL = N / W;
+  static_assert(W == 32 && N % W == 0 && CL <= 8, "one cluster of at most 8 blocks per plane");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sA = reinterpret_cast<float*>(smem_raw);
+  float* sB = sA + N * RS;
+  float* tot = sB + N * RS;
+  float* tw = tot + C::G * W;
+  float* sinv = tw + 4 * N;
+  cg::cluster_group cluster = cg::this_cluster();
+  // the flag is set before this launch by the stream's previous kernels, so
+  // every block of a cluster sees the same value
+  const bool skipped = skip != nullptr && *skip != 0;
+  load_twiddles<float, N>(tw, tw_g);
+  load_sines<float, N>(sinv, tw_g);
+  if (skipped) return;
+  const int r = (int)cluster.block_rank();
+  const int y0 = r * W;
+  const int z = blockIdx.y + 1;
+  if (src != nullptr) {
+    const float a_t = (float)alpha;
+    for (int idx = threadIdx.x; idx < N * W; idx += NT) {
+      const int x = idx % N, c = idx / N, y = y0 + c;
+      float v = 0.0f;
+      if (x > 0 && y > 0) v = a_t * (float)src[((size_t)(z - 1) * n1 + (y - 1)) * n1 + (x - 1)];
+      sA[x * RS + c] = v;
+    }
+  } else if (src32 != nullptr) {
+    for (int idx = threadIdx.x; idx < N * W; idx += NT) {
+      const int x = idx % N, c = idx / N, y = y0 + c;
+      float v = 0.0f;
+      if (x > 0 && y > 0) v = src32[((size_t)(z - 1) * n1 + (y - 1)) * n1 + (x - 1)];
+      sA[x * RS + c] = v;
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < N * W; idx += NT) sA[(idx % N) * RS + idx / N] = 0.0f;
+  }
+  __syncthreads();
+  if (corr != nullptr) {
+    constexpr int G = NT / W;
+    const int c = threadIdx.x % W, g = threadIdx.x / W, y = y0 + c;
+    if (y > 0) {
+      const int line = (z - 1) * n1 + (y - 1);
+      const int i0 = line_start[line], i1 = line_start[line + 1];
+      for (int i = i0 + g; i < i1; i += G) sA[(irr[i] % n1 + 1) * RS + c] += (float)corr[i];
+    }
+  }
+  __syncthreads();
+  dst_tile<C>(sA, tw, sinv, tot);
+  cluster.sync();
+  xy_exchange<N>(cluster, sA, sB, y0);
+  cluster.sync();
+  dst_tile<C>(sB, tw, sinv, tot);
+  const size_t plane = (size_t)z * N * N;
+  for (int idx = threadIdx.x; idx < N * W; idx += NT) {
+    const int c = idx % W, y = idx / W;
+    a[plane + (size_t)y * N + y0 + c] = sB[y * RS + c];
+  }
+}
+
+// inverse: y DST, exchange, x DST, output as k_xinv
+template <int N>
+__global__ void __launch_bounds__(NT) k_xy_inv(float* __restrict__ a, bool keep, double* __restrict__ out,
+                                               const double* __restrict__ aux, double beta, double gamma,
+                                               const float* __restrict__ tw_g, const int* __restrict__ skip) {
+  using C = Cfg<float, N>;
+  constexpr int W = C::W, RS = C::RS, n1 = N - 1, CL = N / W;
+  static_assert(W == 32 && N % W == 0 && CL <= 8, "one cluster of at most 8 blocks per plane");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sA = reinterpret_cast<float*>(smem_raw);
+  float* sB = sA + N * RS;
+  float* tot = sB + N * RS;
+  float* tw = tot + C::G * W;
+  float* sinv = tw + 4 * N;
+  cg::cluster_group cluster = cg::this_cluster();
+  const bool skipped = skip != nullptr && *skip != 0;
+  load_twiddles<float, N>(tw, tw_g);
+  load_sines<float, N>(sinv, tw_g);
+  if (skipped) return;
+  const int r = (int)cluster.block_rank();
+  const int y0 = r * W;
+  const int z = blockIdx.y + 1;
+  const size_t plane = (size_t)z * N * N;
+  for (int idx = threadIdx.x; idx < N * W; idx += NT) {
+    const int c = idx % W, y = idx / W;
+    copy_async(&sB[y * RS + c], &a[plane + (size_t)y * N + y0 + c]);
+  }
+  copy_async_wait();
+  __syncthreads();
+  dst_tile<C>(sB, tw, sinv, tot);
+  cluster.sync();
+  xy_exchange<N>(cluster, sB, sA, y0);
+  cluster.sync();
+  dst_tile<C>(sA, tw, sinv, tot);
+  if (out == nullptr) {
+    if (keep)
+      for (int idx = threadIdx.x; idx < N * W; idx += NT) {
+        const int x = idx % N, c = idx / N;
+        a[plane + (size_t)(y0 + c) * N + x] = sA[x * RS + c];
+      }
+    return;
+  }
+  const float b_t = (float)beta;
+  for (int idx = threadIdx.x; idx < N * W; idx += NT) {
+    const int x = idx % N, c = idx / N, y = y0 + c;
+    const float v = sA[x * RS + c];
+    if (keep) a[plane + (size_t)y * N + x] = v;
+    if (x > 0 && y > 0) {
+      const size_t o = ((size_t)(z - 1) * n1 + (y - 1)) * n1 + (x - 1);
+      const double bv = (double)(b_t * v);
+      out[o] = aux != nullptr ? fma(gamma, aux[o], bv) : bv;
+    }
+  }
+}
+
+template <typename K, typename... Args>
+cudaError_t launch_cluster(K kernel, int cl, dim3 grid, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(NT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // opt each kernel into its dynamic shared-memory size once per process
 template <typename K>
 int prep(K kernel, size_t smem) {
@@ -751,6 +938,30 @@ int run_solve(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1, const 
   int rc;
   if (dim == 3) {
     dim3 grid(N / W, N - 1);
+    if constexpr (sizeof(T) == 4 && N >= 32 && N <= 256) {
+      // fused x-y passes: three passes per solve (xy forward, z solve, xy inverse)
+      if (h->xy_fused) {
+        constexpr size_t sxy = xy_smem_bytes<N>();
+        if ((rc = prep(k_xy_fwd<N>, sxy))) return rc;
+        if ((rc = prep(k_xy_inv<N>, sxy))) return rc;
+        cudaError_t e = launch_cluster(k_xy_fwd<N>, N / 32, grid, sxy, st, work, sa.src, sa.alpha, sa.src32, sa.corr,
+                                       (const int32_t*)t.irr, (const int32_t*)t.line_start, tw, h->skip);
+        if (e == cudaSuccess) {
+          if ((rc = launch_strided3<T, N>(h, 1, true, work, mu1, lam, scale, tw))) return rc;
+          e = launch_cluster(k_xy_inv<N>, N / 32, grid, sxy, st, work, sa.keep || sa.out_user == nullptr,
+                             sa.out_user, sa.aux, sa.beta, sa.gamma, tw, h->skip);
+          if (e != cudaSuccess) {
+            set_error("cluster launch of the fused x-y inverse pass failed: %s", cudaGetErrorString(e));
+            return KFBI_ERR_CUDA;
+          }
+          KFBI_CHECK_LAUNCH_N(3);
+          return KFBI_OK;
+        }
+        // no cluster of this size fits: the five-pass path from now on
+        cudaGetLastError();
+        h->xy_fused = false;
+      }
+    }
     if ((rc = prep(k_xfwd<T, N, 3>, smem))) return rc;
     k_xfwd<T, N, 3><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.src32, sa.corr, t.irr, t.line_start, tw,
                                              h->skip);
@@ -797,9 +1008,35 @@ int run_pass(kfbi_handle* h, int pass, double lambda, T* work, const T* mu1, con
       if ((rc = launch_strided3<T, N>(h, 0, false, work, mu1, lam, scale, tw))) return rc;
     } else if (pass == 2) {
       if ((rc = launch_strided3<T, N>(h, 1, true, work, mu1, lam, scale, tw))) return rc;
-    } else {
+    } else if (pass == 3) {
       if ((rc = prep(k_xinv<T, N, 3>, smem))) return rc;
       k_xinv<T, N, 3><<<grid, NT, smem, st>>>(work, true, nullptr, nullptr, 1.0, 0.0, tw, nullptr);
+    } else {
+      // 4 / 5: the fused x-y forward / inverse pass
+      if constexpr (sizeof(T) == 4 && N >= 32 && N <= 256) {
+        if (h->xy_fused) {
+          constexpr size_t sxy = xy_smem_bytes<N>();
+          cudaError_t e;
+          if (pass == 4) {
+            if ((rc = prep(k_xy_fwd<N>, sxy))) return rc;
+            e = launch_cluster(k_xy_fwd<N>, N / 32, grid, sxy, st, work, (const double*)nullptr, 1.0,
+                               (const float*)nullptr, (const double*)nullptr, (const int32_t*)t.irr,
+                               (const int32_t*)t.line_start, tw, (const int*)nullptr);
+          } else {
+            if ((rc = prep(k_xy_inv<N>, sxy))) return rc;
+            e = launch_cluster(k_xy_inv<N>, N / 32, grid, sxy, st, work, true, (double*)nullptr,
+                               (const double*)nullptr, 1.0, 0.0, tw, (const int*)nullptr);
+          }
+          if (e != cudaSuccess) {
+            set_error("cluster launch failed: %s", cudaGetErrorString(e));
+            return KFBI_ERR_CUDA;
+          }
+          KFBI_CHECK_LAUNCH();
+          return KFBI_OK;
+        }
+      }
+      set_error("no fused x-y pass for this grid and precision");
+      return KFBI_ERR_ARG;
     }
     (void)NN;
   } else {
@@ -1000,6 +1237,16 @@ int make_tma_maps(kfbi_handle* h) {
     return KFBI_ERR_CUDA;
   }
   h->tma = true;
+  // fused x-y passes need cluster launches (a cluster of N/32 blocks per
+  // plane).  They pay off only for small planes: measured per float32 solve
+  // (CUDA events, back-to-back) 18.8 against 24.4 us at 64^3, 48.4 against
+  // 47.7 us at 128^3 and 211 against 172 us at 256^3, where the separate
+  // passes are bound by the transforms' instruction issue with the grid in
+  // L2, and the fused blocks add two cluster barriers and the exchange.
+  int dev = 0, cl = 0;
+  cudaGetDevice(&dev);
+  if (N <= 64 && cudaDeviceGetAttribute(&cl, cudaDevAttrClusterLaunch, dev) == cudaSuccess && cl) h->xy_fused = true;
+  cudaGetLastError();
   return KFBI_OK;
 }
 

@@ -201,6 +201,7 @@ struct kfbi_handle {
   // TMA descriptors of the float32 padded grid: [N x 32] tiles along y and z
   CUtensorMap tmap_y32, tmap_z32;
   bool tma = false;
+  bool xy_fused = false;          // float32 3-D solves use the cluster-fused x-y passes
   // device flag handed to the launches of a Krylov iteration enqueued ahead
   // of the host's convergence test (nullptr otherwise)
   const int* skip = nullptr;

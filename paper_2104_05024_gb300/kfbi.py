@@ -59,7 +59,7 @@ class FHNStruct(C.Structure):
 
 class Info(C.Structure):
     _fields_ = [("M", C.c_int), ("n_irregular", C.c_int), ("n_crossings", C.c_int), ("n_inside", C.c_int),
-                ("device_bytes", C.c_size_t), ("lambda", C.c_double)]
+                ("device_bytes", C.c_size_t), ("lambda", C.c_double), ("xy_fused", C.c_int)]
 
 
 EXPORTS = [
