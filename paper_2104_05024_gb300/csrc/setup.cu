@@ -821,21 +821,53 @@ __global__ void k_irr_arms(GridParams gr, const uint8_t* inside, Tables t, const
   t.irr_narm[i] = (int8_t)na;
 }
 
-// CSR correction rows of the irregular nodes (pointers computed on the host)
-__global__ void k_corr_rows(Tables t) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= t.n_irr) return;
-  int pos = t.cr_ptr[i];
+// CSR correction rows of the irregular nodes: the arms' crossing rows
+// concatenated, entries with the same density index merged (in order of first
+// appearance; neighbouring crossings share most of their surface-fit points).
+// count: the merged length only (pointers are then scanned on the host).
+__device__ int corr_row(const Tables& t, int i, int32_t* pid, double* w) {
   const int na = t.irr_narm[i];
+  int n = 0;
   for (int a = 0; a < na; ++a) {
     const int code = t.irr_arm[(size_t)i * 6 + a];
     const int c = code >> 1;
-    const double* w = (code & 1) ? t.c_whi : t.c_wlo;
+    const double* wc = (code & 1) ? t.c_whi : t.c_wlo;
     const int K = t.c_cnt[c];
-    for (int q = 0; q < K; ++q, ++pos) {
-      t.cr_pid[pos] = t.c_pid[(size_t)c * PATCH_MAX + q];
-      t.cr_w[pos] = w[(size_t)c * PATCH_MAX + q];
+    for (int q = 0; q < K; ++q) {
+      const int32_t p = t.c_pid[(size_t)c * PATCH_MAX + q];
+      const double v = wc[(size_t)c * PATCH_MAX + q];
+      int j = 0;
+      while (j < n && pid[j] != p) ++j;
+      if (j == n) {
+        pid[n] = p;
+        w[n] = v;
+        ++n;
+      } else {
+        w[j] += v;
+      }
     }
+  }
+  return n;
+}
+
+__global__ void k_corr_count(Tables t, int32_t* count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.n_irr) return;
+  int32_t pid[6 * PATCH_MAX];
+  double w[6 * PATCH_MAX];
+  count[i] = corr_row(t, i, pid, w);
+}
+
+__global__ void k_corr_rows(Tables t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.n_irr) return;
+  int32_t pid[6 * PATCH_MAX];
+  double w[6 * PATCH_MAX];
+  const int n = corr_row(t, i, pid, w);
+  const int o = t.cr_ptr[i];
+  for (int k = 0; k < n; ++k) {
+    t.cr_pid[o + k] = pid[k];
+    t.cr_w[o + k] = w[k];
   }
 }
 
@@ -993,20 +1025,19 @@ int build_corr_csr(kfbi_handle* h, Tables& t, bool new_pattern) {
   cudaStream_t st = h->stream;
   int rc;
   if (new_pattern) {
-    std::vector<int32_t> arm((size_t)t.n_irr * 6), cnt((size_t)t.n_int), ptr((size_t)t.n_irr + 1, 0);
-    std::vector<int8_t> narm((size_t)t.n_irr);
+    std::vector<int32_t> cnt((size_t)t.n_irr), ptr((size_t)t.n_irr + 1, 0);
     if (t.n_irr > 0) {
-      KFBI_CUDA(cudaMemcpyAsync(arm.data(), t.irr_arm, sizeof(int32_t) * arm.size(), cudaMemcpyDeviceToHost, st));
-      KFBI_CUDA(cudaMemcpyAsync(narm.data(), t.irr_narm, narm.size(), cudaMemcpyDeviceToHost, st));
+      int32_t* cnt_d = nullptr;
+      KFBI_CUDA(cudaMalloc((void**)&cnt_d, sizeof(int32_t) * (size_t)t.n_irr));
+      k_corr_count<<<(t.n_irr + 127) / 128, 128, 0, st>>>(t, cnt_d);
+      const cudaError_t e = cudaMemcpyAsync(cnt.data(), cnt_d, sizeof(int32_t) * cnt.size(), cudaMemcpyDeviceToHost, st);
+      const cudaError_t e2 = cudaStreamSynchronize(st);
+      cudaFree(cnt_d);
+      KFBI_CUDA(e);
+      KFBI_CUDA(e2);
+      KFBI_COUNT(1);
     }
-    if (t.n_int > 0)
-      KFBI_CUDA(cudaMemcpyAsync(cnt.data(), t.c_cnt, sizeof(int32_t) * cnt.size(), cudaMemcpyDeviceToHost, st));
-    KFBI_CUDA(cudaStreamSynchronize(st));
-    for (int i = 0; i < t.n_irr; ++i) {
-      int k = 0;
-      for (int a = 0; a < narm[i]; ++a) k += cnt[arm[(size_t)i * 6 + a] >> 1];
-      ptr[i + 1] = ptr[i] + k;
-    }
+    for (int i = 0; i < t.n_irr; ++i) ptr[i + 1] = ptr[i] + cnt[i];
     if ((rc = upload(h, &t.cr_ptr, ptr.data(), ptr.size()))) return rc;
     if ((rc = dalloc(h, &t.cr_pid, (size_t)ptr[t.n_irr]))) return rc;
     h->cr_nnz = ptr[t.n_irr];
