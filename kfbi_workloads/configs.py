@@ -17,24 +17,38 @@ from . import geometry as G
 
 @dataclass(frozen=True)
 class Grid:
-    """Uniform box grid on [lo, hi]^dim with N intervals per axis; the unknowns
-    are the (N-1)^dim interior nodes x_k = lo + k h, k = 1..N-1 (Section 5.2)."""
+    """Uniform box grid on [lo, hi]^dim with N intervals per axis, nodes
+    x_k = lo + k h (Section 5.2).  The box condition of the interface problems
+    picks the unknowns: bc = "dirichlet" (v = 0 on the box boundary) keeps the
+    (N-1)^dim interior nodes k = 1..N-1; bc = "neumann" (zero normal
+    derivative on the box boundary, the box Green's function of Section 4)
+    keeps all (N+1)^dim nodes k = 0..N."""
     dim: int
     N: int
     lo: float = -1.0
     hi: float = 1.0
+    bc: str = "dirichlet"
 
     @property
     def h(self) -> float:
         return (self.hi - self.lo) / self.N
 
     @property
+    def first(self) -> int:
+        """Node index k of array index 0 along every axis."""
+        return 0 if self.bc == "neumann" else 1
+
+    @property
+    def n(self) -> int:
+        """Nodes per axis held in a field."""
+        return self.N + 1 if self.bc == "neumann" else self.N - 1
+
+    @property
     def shape(self):
-        n = self.N - 1
-        return (n,) * self.dim          # [z][y][x] / [y][x], x fastest
+        return (self.n,) * self.dim     # [z][y][x] / [y][x], x fastest
 
     def axis(self) -> np.ndarray:
-        k = np.arange(1, self.N, dtype=np.float64)
+        k = np.arange(self.first, self.first + self.n, dtype=np.float64)
         return self.lo + k * self.h
 
     def coords(self):

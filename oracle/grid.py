@@ -3,9 +3,11 @@ nodes, grid-line intersections and interface-to-cell indexing (Section 5.3,
 Section 6).
 
 Grid: box [lo, hi]^d with N intervals per axis, h = (hi - lo)/N; node k has
-coordinate lo + k*h (one multiply, one add).  Arrays hold the (N-1)^d interior
-nodes, [z][y][x] with x fastest; box-boundary nodes carry the Dirichlet value 0
-and count as outside Omega.
+coordinate lo + k*h (one multiply, one add).  Arrays hold the grid's field
+nodes, [z][y][x] with x fastest: the (N-1)^d interior nodes of the Dirichlet
+box (box-boundary nodes carry the value 0 and count as outside Omega), or all
+(N+1)^d nodes of the Neumann box (Omega never reaches the box boundary, so
+those nodes are outside Omega and regular).
 
 * A node is irregular iff one of its 2d axis neighbours has the other
   inside/outside status (its 5/7-point stencil crosses the interface).
@@ -86,7 +88,7 @@ def intersections(geom: G.Geometry, grid: Grid, inside: np.ndarray):
       comp  int   surface component crossed
     """
     d = grid.dim
-    n1 = grid.N - 1
+    n1 = grid.n
     out = {k: [] for k in ("axis", "lo", "hi", "z", "comp")}
     flat = np.arange(inside.size).reshape(inside.shape)
     ncomp = LS.n_components(geom)
@@ -101,11 +103,11 @@ def intersections(geom: G.Geometry, grid: Grid, inside: np.ndarray):
         hi_idx = flat[tuple(sl1)][diff]
         if lo_idx.size == 0:
             continue
-        # integer node indices (1-based) of the lower node along each axis
+        # node indices k of the lower node along each axis
         multi = np.unravel_index(lo_idx, inside.shape)
         kk = [None] * d
         for g_ax in range(d):
-            kk[g_ax] = multi[_axis_of_flat(d, g_ax)] + 1
+            kk[g_ax] = multi[_axis_of_flat(d, g_ax)] + grid.first
         Xlo = [node_coord(grid, kk[g]) for g in range(d)]
         Xhi = list(Xlo)
         Xhi[a] = node_coord(grid, kk[a] + 1)
@@ -154,7 +156,7 @@ def intersection_points(grid: Grid, shape, ints) -> np.ndarray:
     multi = np.unravel_index(ints["lo"], shape)
     P = np.empty((ints["lo"].size, d))
     for g in range(d):
-        P[:, g] = node_coord(grid, multi[_axis_of_flat(d, g)] + 1)
+        P[:, g] = node_coord(grid, multi[_axis_of_flat(d, g)] + grid.first)
     for a in range(d):
         m = ints["axis"] == a
         P[m, a] = ints["z"][m]

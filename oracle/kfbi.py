@@ -139,7 +139,7 @@ class KFBI:
         self.st_xi = X - self.geom.nodes[:, None, :]             # physical offsets
         A = taylor_rows(self.st_xi / g.h)
         self.st_A = A
-        arr = tuple((pts[..., d - 1 - k] - 1) for k in range(d))  # array index order
+        arr = tuple((pts[..., d - 1 - k] - g.first) for k in range(d))  # array index order
         self.st_flat = np.ravel_multi_index(arr, self.inside.shape)
         self.st_out = ~self.inside.ravel()[self.st_flat]
 
@@ -216,7 +216,7 @@ class KFBI:
         k_a = np.empty(lo.size, dtype=np.int64)
         for ax in range(self.d):
             m = a == ax
-            k_a[m] = kk[self.d - 1 - ax][m] + 1
+            k_a[m] = kk[self.d - 1 - ax][m] + g.first
         xl = g.lo + k_a.astype(np.float64) * g.h
         xh = g.lo + (k_a + 1).astype(np.float64) * g.h
         for node, dist in ((lo, xh - z), (hi, xl - z)):

@@ -30,12 +30,15 @@ def _phi_derivs(geom, comp, P):
     return J.v, J.g, J.H
 
 
+@pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
 @pytest.mark.parametrize("case", ["ellipse", "ellipsoid"])
-def test_correction_exact_for_piecewise_quadratic(case):
+def test_correction_exact_for_piecewise_quadratic(case, bc):
+    """On both box layouts (interior nodes, or all nodes of the Neumann box)
+    the corrected operator reproduces the continuous operator of each side."""
     if case == "ellipse":
-        geom, grid = G.ellipse_config0(64), Grid(2, 32)
+        geom, grid = G.ellipse_config0(64), Grid(2, 32, bc=bc)
     else:
-        geom, grid = G.ellipsoid3(0.7, 0.5, 0.45, 6), Grid(3, 20)
+        geom, grid = G.ellipsoid3(0.7, 0.5, 0.45, 6), Grid(3, 20, bc=bc)
     k = KFBI(geom, grid)
     lam, K = 3.0, 0.7
     d = grid.dim
@@ -54,7 +57,8 @@ def test_correction_exact_for_piecewise_quadratic(case):
     _, _, Hphi = _phi_derivs(geom, 0, Xg.reshape(-1, d))
     lap_phi = np.trace(Hphi, axis1=1, axis2=2).reshape(grid.shape)
     rhs = np.where(k.inside, lapP - lam * Pq(Xg), lapP - K * lap_phi - lam * (Pq(Xg) - K * phi))
-    # away from the box boundary (zero Dirichlet data breaks the quadratic there)
+    # away from the box boundary (zero Dirichlet data or the mirrored ghost
+    # value breaks the quadratic there)
     interior = np.ones(grid.shape, dtype=bool)
     for ax in range(d):
         sl = [slice(None)] * d
@@ -66,12 +70,13 @@ def test_correction_exact_for_piecewise_quadratic(case):
     assert err.max() < 1e-9 * grid.N ** 2
 
 
+@pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
 @pytest.mark.parametrize("dim", [2, 3])
-def test_interpolation_exact_for_quadratics(dim):
+def test_interpolation_exact_for_quadratics(dim, bc):
     if dim == 2:
-        geom, grid = G.ellipse_config0(48), Grid(2, 32)
+        geom, grid = G.ellipse_config0(48), Grid(2, 32, bc=bc)
     else:
-        geom, grid = G.ellipsoid3(0.7, 0.5, 0.45, 6), Grid(3, 24)
+        geom, grid = G.ellipsoid3(0.7, 0.5, 0.45, 6), Grid(3, 24, bc=bc)
     k = KFBI(geom, grid)
     Xg = np.stack(np.broadcast_arrays(*grid.coords()), axis=-1)
     rng = np.random.default_rng(5)
@@ -257,6 +262,45 @@ def test_second_order_convergence_2d():
         e = (uh - u)[k.inside]
         errs.append(math.sqrt((e ** 2).mean()))
     assert min(_rate(errs)) > 1.7
+
+
+def test_neumann_box_second_order_and_box_independent():
+    """The solution in Omega does not depend on the box condition of the
+    Green's function (Section 4): with the Neumann box the KFBI solution
+    converges at second order, and it differs from the Dirichlet-box solution
+    by a second-order amount."""
+    errs, diffs = [], []
+    for N in (32, 64, 128):
+        geom = G.ellipse_config0(2 * N)
+        sol = {}
+        for bc in ("dirichlet", "neumann"):
+            grid = Grid(2, N, bc=bc)
+            f, u, gN = C.manufactured(geom, grid, 60.0)
+            k = KFBI(geom, grid)
+            uh, psi, info = k.solve_neumann(f, gN, 60.0, tol=1e-11)
+            assert info["converged"] and info["iters"] < 20
+            ins = k.inside
+            if bc == "neumann":
+                assert uh.shape == (N + 1, N + 1) and not ins[0].any() and not ins[:, -1].any()
+                e = (uh - u)[ins]
+                errs.append(math.sqrt((e ** 2).mean()))
+                sol[bc] = uh[1:-1, 1:-1][ins[1:-1, 1:-1]]
+            else:
+                sol[bc] = uh[ins]
+        diffs.append(np.abs(sol["neumann"] - sol["dirichlet"]).max())
+    # the max-norm difference is irregular from one grid to the next; its rate
+    # over the two refinements is second order
+    assert min(_rate(errs)) > 1.7 and math.log2(diffs[0] / diffs[-1]) / 2.0 > 1.6
+
+
+def test_neumann_box_gmres_matches_dense_lu():
+    geom, grid = G.ellipse_config0(24), Grid(2, 16, bc="neumann")
+    k = KFBI(geom, grid)
+    A = np.stack([k.apply_A(e, 60.0) for e in np.eye(geom.M)], axis=1)
+    g = np.random.default_rng(9).standard_normal(geom.M)
+    x_ref = np.linalg.solve(A, g)
+    x, info = krylov.gmres(lambda v: k.apply_A(v, 60.0), g, np.zeros(geom.M), 1e-13, restart=50)
+    assert info["converged"] and np.abs(x - x_ref).max() < 1e-10 * np.abs(x_ref).max()
 
 
 def test_second_order_convergence_disk_poisson_like():
