@@ -4,7 +4,7 @@ the 256^3 prolate-shell workload, each diffusion solve converged to a 1e-8
 GMRES residual, through the KFBI library's C ABI on one GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl kfbi|reference]
-    python bench.py --workload star-sweep|shell-large|heldout|stiff|stimulus|coupled
+    python bench.py --workload star-sweep|shell-large|heldout|stiff|stimulus|coupled|neumann
 
 One JSON line on rank 0.  Multi-GPU runs are independent replicas (one
 stimulus location per rank, no data-path collective); `value` sums the ranks.
@@ -723,6 +723,46 @@ def run_coupled(args):
           flush=True)
 
 
+def run_neumann(args):
+    """The Neumann box (zero normal derivative on the box boundary, the box
+    Green's function of Section 4; all (N+1)^3 nodes, cosine transforms)
+    against the Dirichlet box on the shell workload at N^3, float64,
+    projection warm start, tol 1e-8: Strang steps/s, iterations per step, the
+    float64 box solve time and its algorithmic bytes (read r, write v) per
+    second."""
+    import torch
+
+    import paper_2104_05024_gb300.kfbi as K
+    from kfbi_workloads import configs as C
+    dev = torch.device("cuda", 0)
+    N = args.N
+    rows = {}
+    for bc in ("dirichlet", "neumann"):
+        geom, grid, cfg, V0, w0 = C.config2(N=N, bc=bc)
+        h = K.KFBI(geom, grid, sigma_i=cfg.sigma_i, sigma_e=cfg.sigma_e, dt=cfg.dt, tol=cfg.tol, precision=K.FP64,
+                   warm=K.WARM_PROJECTION, restart=50, max_iter=500)
+        V, w = torch.tensor(V0, device=dev), torch.tensor(w0, device=dev)
+        ue = torch.empty_like(V)
+        h.bidomain_step(C.FHN_CONFIG, V, w, None, nsteps=3)
+        ms, st = _event_ms(lambda: h.bidomain_step(C.FHN_CONFIG, V, w, ue, nsteps=args.steps))
+        r = torch.randn(grid.shape, dtype=torch.float64, device=dev)
+        v = torch.empty_like(r)
+        h.box_solve(r, v, h.info["lambda"], precision=K.FP64)
+        box_ms, _ = _event_ms(lambda: h.box_solve(r, v, h.info["lambda"], precision=K.FP64), reps=5)
+        pts = int(np.prod(grid.shape))
+        rows[bc] = {"field_nodes": pts, "steps_per_s": round(1000.0 * args.steps / ms, 3),
+                    "iters_per_step": float(np.mean([s["iters"] for s in st])),
+                    "true_rel_res_max": float(max(s["true_rel_res"] for s in st)),
+                    "V_max": float(V.abs().max()), "ue_max": float(ue.abs().max()),
+                    "box_solve_ms": round(box_ms, 3),
+                    "box_solve_algorithmic_GBs": round(2 * 8 * pts / (box_ms * 1e-3) / 1e9, 1)}
+        h.close()
+    print(json.dumps({"metric": "Neumann-box Strang steps/s and float64 box solve (vs the Dirichlet box)",
+                      "workload": f"shell {N}^3, FHN of the workloads, dt 0.05, tol 1e-8, float64, projection "
+                                  f"warm start, {args.steps} steps after 3",
+                      "unit": "steps/s", "rows": rows}), flush=True)
+
+
 # -------------------------------------------------------------- CPU oracle
 
 def cpu_baseline(N, steps=1):
@@ -780,7 +820,7 @@ def main():
     ap.add_argument("--train-steps", type=int, default=12, help="Strang steps per training stimulus (learned form)")
     ap.add_argument("--train-epochs", type=int, default=8)
     ap.add_argument("--workload", default="strang",
-                    choices=["strang", "star-sweep", "shell-large", "heldout", "stiff", "stimulus", "coupled"],
+                    choices=["strang", "star-sweep", "shell-large", "heldout", "stiff", "stimulus", "coupled", "neumann"],
                     help="strang: the timed benchmark; the others print one result line each")
     args = ap.parse_args()
     if args.steps is None:
@@ -799,6 +839,8 @@ def main():
         run_stimulus(args)
     elif args.workload == "coupled":
         run_coupled(args)
+    elif args.workload == "neumann":
+        run_neumann(args)
     else:
         run_gpu(args)
 

@@ -10,10 +10,13 @@
  *    other pointers are host pointers owned by the caller and only read during
  *    the call.  The library owns its workspace and tables (freed by
  *    kfbi_destroy).
- *  - Box grids cover [lo, hi]^dim with N intervals per axis, h = (hi - lo)/N.
- *    Grid fields hold the (N-1)^dim interior nodes x_k = lo + k h, k = 1..N-1,
- *    row-major [z][y][x] (x fastest), float64, contiguous.  Box-boundary
- *    nodes carry the Dirichlet value 0 of the interface problems (Section 5.1).
+ *  - Box grids cover [lo, hi]^dim with N intervals per axis, h = (hi - lo)/N,
+ *    nodes x_k = lo + k h.  Grid fields are row-major [z][y][x] (x fastest),
+ *    float64, contiguous.  With the Dirichlet box (kfbi_grid.box =
+ *    KFBI_BOX_DIRICHLET) they hold the (N-1)^dim interior nodes k = 1..N-1
+ *    and box-boundary nodes carry the value 0 of the interface problems
+ *    (Section 5.1); with the Neumann box (KFBI_BOX_NEUMANN) they hold all
+ *    (N+1)^dim nodes k = 0..N.
  *  - Interface-node vectors (densities psi, Neumann data g^N, limits) hold M
  *    float64 values in the order of kfbi_geometry.nodes.
  *  - Work is enqueued on kfbi_opts.stream (NULL = the legacy default stream).
@@ -49,6 +52,14 @@ extern "C" {
 /* surface-component point-location maps of 3-D cube-sphere meshes */
 #define KFBI_MAP_RADIAL 0
 #define KFBI_MAP_ELLIPSOID 1
+
+/* box condition of the interface problems (kfbi_grid.box) */
+#define KFBI_BOX_DIRICHLET 0 /* v = 0 on the box boundary; sine transforms          */
+#define KFBI_BOX_NEUMANN 1   /* zero normal derivative on the box boundary, the box
+                                Green's function of Section 4: mirrored ghost rows,
+                                cosine (DCT-I) transforms.  Float64 only
+                                (KFBI_FP64), lambda > 0 (no Green's function of the
+                                Poisson operator), scalar problem only           */
 
 /* precision of the integral evaluations */
 #define KFBI_FP64 0          /* all transforms and corrections in float64        */
@@ -107,6 +118,7 @@ typedef struct {
   int N;
   double lo;
   double hi;
+  int box;  /* KFBI_BOX_DIRICHLET or KFBI_BOX_NEUMANN */
 } kfbi_grid;
 
 typedef struct {

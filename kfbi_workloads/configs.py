@@ -93,10 +93,11 @@ def ball_stimulus(grid: Grid, center, radius: float) -> np.ndarray:
 
 # --------------------------------------------------------------------- workloads
 
-def config0():
-    """2-D ellipse, 128^2, 256 nodes, 20 Strang steps of FHN, tol 1e-10."""
+def config0(bc: str = "dirichlet"):
+    """2-D ellipse, 128^2, 256 nodes, 20 Strang steps of FHN, tol 1e-10 (bc:
+    the box condition of the interface problems)."""
     geom = G.ellipse_config0(256)
-    grid = Grid(2, 128)
+    grid = Grid(2, 128, bc=bc)
     cfg = StrangConfig(sigma_i=1.0, sigma_e=2.0, dt=0.05, steps=20, tol=1e-10)
     V0 = ball_stimulus(grid, (-0.4, 0.0), 0.1)
     return geom, grid, cfg, V0, np.zeros_like(V0)
@@ -119,11 +120,11 @@ def config1(N: int):
     return G.star_config1(surface_res(N)), Grid(3, N), 40.0, 1e-10
 
 
-def config2(N: int = 256, steps: int = 200, n_surf: int | None = None):
+def config2(N: int = 256, steps: int = 200, n_surf: int | None = None, bc: str = "dirichlet"):
     """3-D prolate shell, N^3, FHN bidomain, tol 1e-8; stimulus ball of radius
-    0.1 centred on the mid-wall at (0.8, 0, 0)."""
+    0.1 centred on the mid-wall at (0.8, 0, 0) (bc: the box condition)."""
     geom = G.shell_config2(n_surf if n_surf is not None else surface_res(N))
-    grid = Grid(3, N)
+    grid = Grid(3, N, bc=bc)
     cfg = StrangConfig(sigma_i=1.0, sigma_e=2.0, dt=0.05, steps=steps, tol=1e-8)
     V0 = ball_stimulus(grid, (0.8, 0.0, 0.0), 0.1)
     return geom, grid, cfg, V0, np.zeros_like(V0)
@@ -228,6 +229,10 @@ def exact_grad(P: np.ndarray) -> np.ndarray:
 def analytic_normals(geom: G.Geometry) -> np.ndarray:
     """Outward unit normals of Omega at the interface nodes, from the analytic
     surface parametrisation (independent of any level-set code)."""
+    if geom.kind == G.MESH3:
+        if geom.exact_normals is not None:
+            return geom.exact_normals
+        return analytic_normals(geom.source)
     P = geom.nodes
     if geom.kind == G.ELLIPSE2:
         a, b, c, s = geom.params[:4]

@@ -17,6 +17,13 @@ Geometry kinds (the domain Omega, always inside the box [-1, 1]^d):
                  phi azimuth.
 * ``SHELL3``     3-D region between an outer and an inner axis-aligned
                  ellipsoid (a thick prolate shell).
+* ``MESH3``      3-D domain given only by a closed triangle mesh of its
+                 boundary (Section 5.3, Fig. 1 and Example 4: the method then
+                 uses nothing but the vertices and triangles): the vertices
+                 are the interface nodes, every triangle is wound
+                 counter-clockwise seen from outside Omega (face normals
+                 point out of Omega; on an inner wall they point into the
+                 hole), and the mesh is a closed manifold.
 
 Three-dimensional surfaces are meshed as equiangular cube-spheres of
 resolution n: 6 n^2 + 2 vertices and 12 n^2 triangles per surface component,
@@ -34,6 +41,7 @@ ELLIPSE2 = 1
 ELLIPSOID3 = 2
 STAR3 = 3
 SHELL3 = 4
+MESH3 = 5
 
 # surface-component map types used for locating a point on a cube-sphere mesh
 MAP_RADIAL = 0      # cube point = the position itself (star body, centred at 0)
@@ -63,6 +71,11 @@ class Geometry:
     cube_n: int = 0                    # cube-sphere resolution
     cube_t: np.ndarray | None = None   # float64[cube_n + 1], equiangular face coordinates
     components: list = field(default_factory=list)
+    # MESH3 only, input data for manufactured Neumann data (never read by the
+    # method): the analytic geometry the mesh was cut from, or the exact
+    # outward normals at the nodes
+    source: "Geometry | None" = None
+    exact_normals: np.ndarray | None = None
 
     @property
     def M(self) -> int:
@@ -225,3 +238,122 @@ SHELL_INNER = (0.7, 0.4, 0.4)
 
 def shell_config2(n: int) -> Geometry:
     return shell3(SHELL_OUTER, SHELL_INNER, n)
+
+
+# ------------------------------------------------------------ triangle meshes
+
+def mesh3(nodes: np.ndarray, tri: np.ndarray) -> Geometry:
+    """A MESH3 input: vertices (the interface nodes) and outward-wound
+    triangles, nothing else."""
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    comp = Component(-1, (1.0, 1.0, 1.0), False, 0, nodes.shape[0], 0, tri.shape[0])
+    return Geometry(dim=3, kind=MESH3, params=np.zeros(16), nodes=nodes, tri=tri, components=[comp])
+
+
+def as_mesh(geom: Geometry) -> Geometry:
+    """The cube-sphere triangulation of an analytic 3-D geometry handed over as
+    a bare mesh (the level set, the cube maps and the component structure are
+    dropped); triangles are rewound where needed so that every face normal
+    points out of Omega (decided from the analytic shape, which is input
+    preparation only)."""
+    tri = np.array(geom.tri, dtype=np.int64)
+    X = geom.nodes
+    a, b, c = X[tri[:, 0]], X[tri[:, 1]], X[tri[:, 2]]
+    fn = np.cross(b - a, c - a)
+    cen = (a + b + c) / 3.0
+    out_dir = np.empty_like(cen)
+    for C in geom.components:
+        sl = slice(C.tri_offset, C.tri_offset + C.n_tri)
+        ax = np.asarray(C.axes, dtype=np.float64)
+        g = cen[sl] / (ax * ax)[None, :] if C.map_type == MAP_ELLIPSOID else cen[sl]
+        out_dir[sl] = -g if C.flip else g
+    flip = (fn * out_dir).sum(axis=1) < 0.0
+    tri[flip] = tri[flip][:, ::-1]
+    m = mesh3(X, tri)
+    m.source = geom
+    return m
+
+
+def _icosahedron():
+    t = (1.0 + math.sqrt(5.0)) / 2.0
+    v = np.array([[-1, t, 0], [1, t, 0], [-1, -t, 0], [1, -t, 0], [0, -1, t], [0, 1, t], [0, -1, -t], [0, 1, -t],
+                  [t, 0, -1], [t, 0, 1], [-t, 0, -1], [-t, 0, 1]], dtype=np.float64)
+    f = np.array([[0, 11, 5], [0, 5, 1], [0, 1, 7], [0, 7, 10], [0, 10, 11], [1, 5, 9], [5, 11, 4], [11, 10, 2],
+                  [10, 7, 6], [7, 1, 8], [3, 9, 4], [3, 4, 2], [3, 2, 6], [3, 6, 8], [3, 8, 9], [4, 9, 5],
+                  [2, 4, 11], [6, 2, 10], [8, 6, 7], [9, 8, 1]], dtype=np.int64)
+    return v / np.linalg.norm(v, axis=1)[:, None], f
+
+
+def geodesic_sphere(level: int):
+    """Unit-sphere vertices and outward triangles of the icosahedron with every
+    edge split into `level` parts (10 level^2 + 2 vertices; the 12 original
+    vertices keep valence 5)."""
+    v0, f0 = _icosahedron()
+    verts = [tuple(p) for p in v0]
+    index = {}
+
+    def vid(p):
+        key = tuple(np.round(p, 12))
+        if key not in index:
+            index[key] = len(verts)
+            verts.append(tuple(p))
+        return index[key]
+
+    for i, p in enumerate(v0):
+        index[tuple(np.round(p, 12))] = i
+    faces = []
+    n = level
+    for a, b, c in f0:
+        A, B, C = v0[a], v0[b], v0[c]
+        grid = {}
+        for i in range(n + 1):
+            for j in range(n + 1 - i):
+                p = A + (B - A) * (i / n) + (C - A) * (j / n)
+                grid[(i, j)] = vid(p / np.linalg.norm(p))
+        for i in range(n):
+            for j in range(n - i):
+                faces.append((grid[(i, j)], grid[(i + 1, j)], grid[(i, j + 1)]))
+                if i + j < n - 1:
+                    faces.append((grid[(i + 1, j)], grid[(i + 1, j + 1)], grid[(i, j + 1)]))
+    V = np.array(verts, dtype=np.float64)
+    V = V / np.linalg.norm(V, axis=1)[:, None]
+    F = np.array(faces, dtype=np.int64)
+    fn = np.cross(V[F[:, 1]] - V[F[:, 0]], V[F[:, 2]] - V[F[:, 0]])
+    bad = (fn * (V[F[:, 0]] + V[F[:, 1]] + V[F[:, 2]])).sum(axis=1) < 0.0
+    F[bad] = F[bad][:, ::-1]
+    return V, F
+
+
+def bean_mesh(level: int) -> Geometry:
+    """A smooth, non-convex closed surface meshed as a geodesic sphere mapped
+    radially (a stand-in for a measured organ surface such as the left
+    ventricle of Example 4, which is not available): the unit direction d goes
+    to r(d) d with r = 0.55 (1 + 0.25 d_x^2 - 0.2 d_z) and the x axis
+    stretched by 1.2."""
+    V, F = geodesic_sphere(level)
+    m = mesh3(_bean_map(V), F)
+    # exact normals of the mapped sphere from two tangents by central
+    # differences (error ~1e-10, far below any discretisation error)
+    t1 = np.cross(V, np.where(np.abs(V[:, :1]) < 0.9, [[1.0, 0.0, 0.0]], [[0.0, 1.0, 0.0]]))
+    t1 /= np.linalg.norm(t1, axis=1)[:, None]
+    t2 = np.cross(V, t1)
+    eps = 1e-5
+
+    def on_sphere(d):
+        return d / np.linalg.norm(d, axis=1)[:, None]
+
+    T1 = _bean_map(on_sphere(V + eps * t1)) - _bean_map(on_sphere(V - eps * t1))
+    T2 = _bean_map(on_sphere(V + eps * t2)) - _bean_map(on_sphere(V - eps * t2))
+    n = np.cross(T1, T2)
+    n /= np.linalg.norm(n, axis=1)[:, None]
+    n *= np.sign((n * m.nodes).sum(axis=1))[:, None]
+    m.exact_normals = n
+    return m
+
+
+def _bean_map(d: np.ndarray) -> np.ndarray:
+    r = 0.55 * (1.0 + 0.25 * d[:, 0] ** 2 - 0.2 * d[:, 2])
+    X = d * r[:, None]
+    X[:, 0] *= 1.2
+    return X

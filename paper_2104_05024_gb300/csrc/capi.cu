@@ -39,15 +39,23 @@ int launch_init_arnoldi(kfbi_handle* h, double* small, int m);
 
 namespace {
 
-int64_t grid_points(const kfbi_handle* h) {
+// nodes of a field (user layout): (N-1)^d interior nodes of the Dirichlet
+// box, all (N+1)^d nodes of the Neumann box
+int64_t grid_points(const kfbi_handle* h) { return field_count(h->grid); }
+
+int64_t interior_points(const kfbi_handle* h) {
   const int64_t n1 = h->grid.N - 1;
   return h->grid.dim == 3 ? n1 * n1 * n1 : n1 * n1;
 }
 
+// nodes of a work grid: N^d (padded Dirichlet layout) or the (N+1)^d field
+// layout of the Neumann box
 int64_t padded_points(const kfbi_handle* h) {
-  const int64_t N = h->grid.N;
-  return h->grid.dim == 3 ? N * N * N : N * N;
+  const int64_t P = work_n(h->grid);
+  return h->grid.dim == 3 ? P * P * P : P * P;
 }
+
+bool neumann_box(const kfbi_handle* h) { return h->grid.bc == KFBI_BOX_NEUMANN; }
 
 // density vector x seen by the correction and jump rows: psi (3-D) or
 // [psi; spline moments] (2-D)
@@ -657,6 +665,10 @@ int kfbi_create_coupled(const kfbi_geometry* geom, const kfbi_grid* grid, const 
     set_error("the coupled system is solved in float64 (KFBI_FP64)");
     return KFBI_ERR_ARG;
   }
+  if (grid->box != KFBI_BOX_DIRICHLET) {
+    set_error("the coupled system is solved in the Dirichlet box");
+    return KFBI_ERR_ARG;
+  }
   return create_impl(geom, grid, D_i[0], D_e[0], dt, opts, out, D_i, D_e);
 }
 
@@ -687,6 +699,14 @@ static int create_impl(const kfbi_geometry* geom, const kfbi_grid* grid, double 
   }
   if (opts->restart < 1 || opts->restart > MAX_RESTART || !(sigma_i > 0) || !(sigma_e > 0) || !(dt > 0)) {
     set_error("bad options (restart in 1..%d, positive conductivities and dt)", MAX_RESTART);
+    return KFBI_ERR_ARG;
+  }
+  if (grid->box != KFBI_BOX_DIRICHLET && grid->box != KFBI_BOX_NEUMANN) {
+    set_error("box must be KFBI_BOX_DIRICHLET or KFBI_BOX_NEUMANN");
+    return KFBI_ERR_ARG;
+  }
+  if (grid->box == KFBI_BOX_NEUMANN && opts->precision != KFBI_FP64) {
+    set_error("the Neumann box is solved in float64 (KFBI_FP64)");
     return KFBI_ERR_ARG;
   }
   kfbi_handle* h = new kfbi_handle();
@@ -721,6 +741,7 @@ static int create_impl(const kfbi_geometry* geom, const kfbi_grid* grid, double 
   h->grid.N = grid->N;
   h->grid.lo = grid->lo;
   h->grid.h = (grid->hi - grid->lo) / grid->N;
+  h->grid.bc = grid->box;
   int rc;
   auto fail = [&](int code) {
     kfbi_destroy(h);
@@ -843,6 +864,10 @@ int kfbi_set_opts(kfbi_handle* h, const kfbi_opts* opts) {
     set_error("restart cannot grow after kfbi_create");
     return KFBI_ERR_ARG;
   }
+  if (neumann_box(h) && opts->precision != KFBI_FP64) {
+    set_error("the Neumann box is solved in float64 (KFBI_FP64)");
+    return KFBI_ERR_ARG;
+  }
   h->opts = *opts;
   h->stream = (cudaStream_t)opts->stream;
   return KFBI_OK;
@@ -854,7 +879,7 @@ int kfbi_export_setup(kfbi_handle* h, uint8_t* inside, int32_t* irregular, int32
   const Tables& t = h->t;
   const int d = h->grid.dim;
   cudaStream_t st = h->stream;
-  if (inside) KFBI_CUDA(cudaMemcpyAsync(inside, t.inside, (size_t)grid_points(h), cudaMemcpyDeviceToHost, st));
+  if (inside) KFBI_CUDA(cudaMemcpyAsync(inside, t.inside, (size_t)interior_points(h), cudaMemcpyDeviceToHost, st));
   if (irregular) KFBI_CUDA(cudaMemcpyAsync(irregular, t.irr, sizeof(int32_t) * t.n_irr, cudaMemcpyDeviceToHost, st));
   if (crossing_axis)
     KFBI_CUDA(cudaMemcpyAsync(crossing_axis, t.c_axis, sizeof(int32_t) * t.n_int, cudaMemcpyDeviceToHost, st));
@@ -893,6 +918,10 @@ int kfbi_box_solve(kfbi_handle* h, int precision, double lambda, const double* r
     set_error("null field");
     return KFBI_ERR_ARG;
   }
+  if (neumann_box(h) && precision != KFBI_FP64) {
+    set_error("the Neumann box is solved in float64 (KFBI_FP64)");
+    return KFBI_ERR_ARG;
+  }
   SolveArgs sa;
   sa.src = r_dev;
   sa.lambda = lambda;
@@ -922,8 +951,12 @@ int kfbi_interface_limit(kfbi_handle* h, const double* v_dev, const double* psi_
     if ((rc = density_vector(h, psi_dev, &x))) return rc;
   }
   const int N = h->grid.N, n1 = N - 1;
-  // user -> padded copy (rows of n1 values into rows of N)
-  if (h->grid.dim == 3) {
+  // user -> padded copy (rows of n1 values into rows of N); the Neumann box's
+  // work grid has the field layout
+  if (neumann_box(h)) {
+    KFBI_CUDA(cudaMemcpyAsync(h->w.grid64, v_dev, sizeof(double) * (size_t)grid_points(h), cudaMemcpyDeviceToDevice,
+                              h->stream));
+  } else if (h->grid.dim == 3) {
     cudaMemcpy3DParms prm = {};
     prm.srcPtr = make_cudaPitchedPtr((void*)v_dev, sizeof(double) * n1, n1, n1);
     prm.dstPtr = make_cudaPitchedPtr((void*)h->w.grid64, sizeof(double) * N, N, N);
@@ -1382,6 +1415,10 @@ int kfbi_apply_A_coupled(kfbi_handle* h, double kappa, const double* psi_dev, do
 
 int kfbi_bidomain_step_stim(kfbi_handle* h, const kfbi_fhn* p, const double* istim_dev, double* V_dev,
                             double* w_dev, double* ue_dev, int nsteps, kfbi_stats* per_step) {
+  if (h != nullptr && neumann_box(h) && istim_dev != nullptr) {
+    set_error("the stimulus's Poisson problem has no Neumann-box Green's function (lambda = 0)");
+    return KFBI_ERR_ARG;
+  }
   if (h != nullptr && h->coupled) {
     if (!p || !V_dev || !w_dev || nsteps < 0) {
       set_error("null argument");
@@ -1524,6 +1561,10 @@ int kfbi_transform_pass(kfbi_handle* h, int precision, int pass, double lambda) 
   if (int rc = check_handle(h)) return rc;
   if (pass < 0 || pass > 5) {
     set_error("pass must be 0..5");
+    return KFBI_ERR_ARG;
+  }
+  if (neumann_box(h)) {
+    set_error("single transform passes are those of the Dirichlet box");
     return KFBI_ERR_ARG;
   }
   return transform_pass(h, precision, pass, lambda);

@@ -1205,6 +1205,303 @@ int dispatch_pass(kfbi_handle* h, int pass, double lambda, T* work, const T* mu1
   }
 }
 
+// ------------------------------------------------------ Neumann box (DCT-I)
+// The box Green's function of Section 4 with zero normal derivative on the
+// box boundary: all (N+1)^d nodes are unknowns, the boundary rows use the
+// mirrored ghost value, and the cosine modes diagonalise the operator,
+//   v = (2/N)^d C( mu^{-1} o C r ),  C_{kp} = c_k cos(pi k p / N),
+//   c_0 = c_N = 1/2, c_k = 1 otherwise, k, p = 0..N,
+// with the same mu_p as the sine solve (p = 0..N).  Work and user grids share
+// the layout (N+1)^d, x fastest.  A tile holds N+1 transform rows by W lines.
+
+template <typename C>
+constexpr size_t dct_smem_elems() {
+  return (size_t)(C::N + 1) * C::RS + (size_t)C::G * C::W + 4 * (size_t)C::N + C::W;
+}
+
+// DCT-I X_p = sum_k c_k x_k cos(pi k p / N) of every column of the tile
+// s[N+1][RS] in place.  The same length-N/2 complex FFT as the sine
+// transform, after the cosine pre-fold
+//   y_0 = (x_0 + x_N)/2,  y_j = (x_j + x_{N-j})/2 - sin(pi j/N)(x_j - x_{N-j}),
+// gives Y_k = sum_j y_j e^{2 pi i j k / N} with X_{2k} = Re Y_k and
+// X_{2k+1} = X_{2k-1} + Im Y_k (from 2 sin a sin b = cos(a-b) - cos(a+b)),
+// started by X_1 = sum_k c_k x_k cos(pi k / N), summed directly.
+// x1 = scratch [W].
+template <typename C>
+__device__ void dct1_tile(typename C::T* s, const typename C::T* tw, typename C::T* tot, typename C::T* x1) {
+  using T = typename C::T;
+  constexpr int N = C::N, L = C::L, W = C::W, RS = C::RS, G = C::G;
+  {
+    constexpr int SEG = (N + 1 + G - 1) / G;
+    const int c = threadIdx.x % W, g = threadIdx.x / W;
+    const int j0 = g * SEG;
+    const int j1 = (j0 + SEG < N + 1) ? j0 + SEG : N + 1;
+    T acc = (T)0;
+    for (int j = j0; j < j1; ++j) {
+      T cw = tw[2 * j];
+      if (j == 0 || j == N) cw *= (T)0.5;
+      acc += cw * s[j * RS + c];
+    }
+    tot[g * W + c] = acc;
+    __syncthreads();
+    if (g == 0) {
+      T sum = (T)0;
+      for (int g2 = 0; g2 < G; ++g2) sum += tot[g2 * W + c];
+      x1[c] = sum;
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < (N / 2 + 1) * W; idx += NT) {
+    const int c = idx % W, j = idx / W;
+    if (j == 0) {
+      s[c] = (T)0.5 * (s[c] + s[N * RS + c]);
+    } else if (j < N / 2) {
+      const T a = s[j * RS + c], b = s[(N - j) * RS + c];
+      const T m = (T)0.5 * (a + b), d = tw[2 * j + 1] * (a - b);
+      s[j * RS + c] = m - d;
+      s[(N - j) * RS + c] = m + d;
+    }
+  }
+  __syncthreads();
+  Stages<C, 1, L>::run(s, tw);
+  // split into the real DFT: X_0, X_N from Z_0; X_{2k} in row 2k and the
+  // increments Im Y_k in row 2k+1
+  for (int idx = threadIdx.x; idx < (L / 2 + 1) * W; idx += NT) {
+    const int c = idx % W, k = idx / W;
+    if (k == 0) {
+      const T a = s[c], b = s[RS + c];
+      s[c] = a + b;
+      s[N * RS + c] = a - b;
+      s[RS + c] = (T)0;
+    } else {
+      const int kk = L - k;
+      const T Ar = s[(2 * k) * RS + c], Ai = s[(2 * k + 1) * RS + c];
+      const T Br = s[(2 * kk) * RS + c], Bi = s[(2 * kk + 1) * RS + c];
+      {
+        const T wr = tw[2 * (2 * k)], wi = tw[2 * (2 * k) + 1];
+        const T Sr = Ar + Br, Si = Ai - Bi, Dr = Ar - Br, Di = Ai + Bi;
+        s[(2 * k) * RS + c] = (T)0.5 * (Sr + wr * Di + wi * Dr);
+        s[(2 * k + 1) * RS + c] = (T)0.5 * (Si - wr * Dr + wi * Di);
+      }
+      if (kk != k) {
+        const T wr = tw[2 * (2 * kk)], wi = tw[2 * (2 * kk) + 1];
+        const T Sr = Br + Ar, Si = Bi - Ai, Dr = Br - Ar, Di = Bi + Ai;
+        s[(2 * kk) * RS + c] = (T)0.5 * (Sr + wr * Di + wi * Dr);
+        s[(2 * kk + 1) * RS + c] = (T)0.5 * (Si - wr * Dr + wi * Di);
+      }
+    }
+  }
+  __syncthreads();
+  // odd outputs: column-wise inclusive scan of the increments, plus X_1
+  {
+    constexpr int SEG = (L + G - 1) / G;
+    const int c = threadIdx.x % W, g = threadIdx.x / W;
+    const int k0 = g * SEG;
+    const int k1 = (k0 + SEG < L) ? k0 + SEG : L;
+    T acc = (T)0;
+    for (int k = k0; k < k1; ++k) {
+      acc += s[(2 * k + 1) * RS + c];
+      s[(2 * k + 1) * RS + c] = acc;
+    }
+    tot[g * W + c] = acc;
+    __syncthreads();
+    T off = x1[c];
+    for (int g2 = 0; g2 < g; ++g2) off += tot[g2 * W + c];
+    for (int k = k0; k < k1; ++k) s[(2 * k + 1) * RS + c] += off;
+    __syncthreads();
+  }
+}
+
+// x forward on the Neumann layout: W lines y0..y0+W-1 (y <= N) of plane z,
+// r = alpha*src + corrections assembled while loading.  The irregular nodes
+// (all interior) are listed per interior x-line in the interior numbering.
+template <typename T, int N, int DIM>
+__global__ void __launch_bounds__(NT) k_nxfwd(T* __restrict__ a, const double* __restrict__ src, double alpha,
+                                              const double* __restrict__ corr, const int32_t* __restrict__ irr,
+                                              const int32_t* __restrict__ line_start, const T* __restrict__ tw_g,
+                                              const int* __restrict__ skip) {
+  using C = Cfg<T, N>;
+  constexpr int W = C::W, RS = C::RS, P = N + 1, n1 = N - 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  T* tot = s + P * RS;
+  T* tw = tot + C::G * W;
+  T* x1 = tw + 4 * N;
+  const bool skipped = skip != nullptr && *skip != 0;
+  load_twiddles<T, N>(tw, tw_g);
+  if (skipped) return;
+  const int y0 = blockIdx.x * W;
+  const int z = DIM == 3 ? blockIdx.y : 0;
+  const size_t plane = (size_t)z * P * P;
+  for (int idx = threadIdx.x; idx < P * W; idx += NT) {
+    const int x = idx % P, c = idx / P, y = y0 + c;
+    T v = (T)0;
+    if (src != nullptr && y <= N) v = (T)(alpha * src[plane + (size_t)y * P + x]);
+    s[x * RS + c] = v;
+  }
+  __syncthreads();
+  if (corr != nullptr) {
+    constexpr int G = NT / W;
+    const int c = threadIdx.x % W, g = threadIdx.x / W, y = y0 + c;
+    if (y >= 1 && y <= n1 && (DIM == 2 || (z >= 1 && z <= n1))) {
+      const int line = DIM == 3 ? (z - 1) * n1 + (y - 1) : (y - 1);
+      const int i0 = line_start[line], i1 = line_start[line + 1];
+      for (int i = i0 + g; i < i1; i += G) {
+        const int x = irr[i] % n1 + 1;
+        s[x * RS + c] += (T)corr[i];
+      }
+    }
+  }
+  __syncthreads();
+  dct1_tile<C>(s, tw, tot, x1);
+  for (int idx = threadIdx.x; idx < P * W; idx += NT) {
+    const int x = idx % P, c = idx / P, y = y0 + c;
+    if (y <= N) a[plane + (size_t)y * P + x] = s[x * RS + c];
+  }
+}
+
+// x inverse on the Neumann layout: the work grid keeps v (keep) and/or
+// out = beta v + gamma aux
+template <typename T, int N, int DIM>
+__global__ void __launch_bounds__(NT) k_nxinv(T* __restrict__ a, bool keep, double* __restrict__ out,
+                                              const double* __restrict__ aux, double beta, double gamma,
+                                              const T* __restrict__ tw_g, const int* __restrict__ skip) {
+  using C = Cfg<T, N>;
+  constexpr int W = C::W, RS = C::RS, P = N + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  T* tot = s + P * RS;
+  T* tw = tot + C::G * W;
+  T* x1 = tw + 4 * N;
+  if (skip != nullptr && *skip != 0) return;
+  load_twiddles<T, N>(tw, tw_g);
+  const int y0 = blockIdx.x * W;
+  const int z = DIM == 3 ? blockIdx.y : 0;
+  const size_t plane = (size_t)z * P * P;
+  for (int idx = threadIdx.x; idx < P * W; idx += NT) {
+    const int x = idx % P, c = idx / P, y = y0 + c;
+    if (y <= N) copy_async(&s[x * RS + c], &a[plane + (size_t)y * P + x]);
+    else s[x * RS + c] = (T)0;
+  }
+  copy_async_wait();
+  __syncthreads();
+  dct1_tile<C>(s, tw, tot, x1);
+  for (int idx = threadIdx.x; idx < P * W; idx += NT) {
+    const int x = idx % P, c = idx / P, y = y0 + c;
+    if (y > N) continue;
+    const size_t o = plane + (size_t)y * P + x;
+    const T v = s[x * RS + c];
+    if (keep) a[o] = v;
+    if (out != nullptr) {
+      const double bv = beta * (double)v;
+      out[o] = aux != nullptr ? fma(gamma, aux[o], bv) : bv;
+    }
+  }
+}
+
+// strided (y / z) pass on the Neumann layout: rows k = 0..N at row_stride,
+// columns x0..x0+W-1 (x <= N) of plane q.  SOLVE: forward DCT, multiply by
+// scale / (mu1[k] + mu1[p] + mu1[q] - lambda), inverse DCT.
+template <typename T, int N, bool SOLVE, int DIM>
+__global__ void __launch_bounds__(NT) k_nstrided(T* __restrict__ a, size_t row_stride, size_t plane_stride,
+                                                 const T* __restrict__ mu1, T lambda, T scale,
+                                                 const T* __restrict__ tw_g, const int* __restrict__ skip) {
+  using C = Cfg<T, N>;
+  constexpr int W = C::W, RS = C::RS, P = N + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  T* tot = s + P * RS;
+  T* tw = tot + C::G * W;
+  T* x1 = tw + 4 * N;
+  const bool skipped = skip != nullptr && *skip != 0;
+  load_twiddles<T, N>(tw, tw_g);
+  if (skipped) return;
+  const int x0 = blockIdx.x * W;
+  const int q = blockIdx.y;
+  T* base = a + (size_t)q * plane_stride + x0;
+  for (int idx = threadIdx.x; idx < P * W; idx += NT) {
+    const int c = idx % W, k = idx / W;
+    if (x0 + c <= N) copy_async(&s[k * RS + c], &base[(size_t)k * row_stride + c]);
+    else s[k * RS + c] = (T)0;
+  }
+  copy_async_wait();
+  __syncthreads();
+  dct1_tile<C>(s, tw, tot, x1);
+  if (SOLVE) {
+    const T muq = DIM == 3 ? mu1[q] : (T)0;
+    for (int idx = threadIdx.x; idx < P * W; idx += NT) {
+      const int c = idx % W, k = idx / W, p = x0 + c;
+      if (p <= N) s[k * RS + c] *= scale / (mu1[k] + mu1[p] + muq - lambda);
+    }
+    __syncthreads();
+    dct1_tile<C>(s, tw, tot, x1);
+  }
+  for (int idx = threadIdx.x; idx < P * W; idx += NT) {
+    const int c = idx % W, k = idx / W;
+    if (x0 + c <= N) base[(size_t)k * row_stride + c] = s[k * RS + c];
+  }
+}
+
+template <typename T, int N>
+int run_solve_neumann(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1, const T* tw) {
+  using C = Cfg<T, N>;
+  constexpr int W = C::W, P = N + 1;
+  const size_t smem = dct_smem_elems<C>() * sizeof(T);
+  const int dim = h->grid.dim;
+  cudaStream_t st = h->stream;
+  const Tables& t = h->t;
+  const T scale = (T)(dim == 3 ? (2.0 / N) * (2.0 / N) * (2.0 / N) : (2.0 / N) * (2.0 / N));
+  const T lam = (T)sa.lambda;
+  const dim3 grid((P + W - 1) / W, dim == 3 ? P : 1);
+  const size_t PP = (size_t)P * P;
+  int rc;
+  if (dim == 3) {
+    if ((rc = prep(k_nxfwd<T, N, 3>, smem))) return rc;
+    if ((rc = prep(k_nstrided<T, N, false, 3>, smem))) return rc;
+    if ((rc = prep(k_nstrided<T, N, true, 3>, smem))) return rc;
+    if ((rc = prep(k_nxinv<T, N, 3>, smem))) return rc;
+    k_nxfwd<T, N, 3><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.corr, t.irr, t.line_start, tw, h->skip);
+    k_nstrided<T, N, false, 3><<<grid, NT, smem, st>>>(work, P, PP, mu1, lam, scale, tw, h->skip);
+    k_nstrided<T, N, true, 3><<<grid, NT, smem, st>>>(work, PP, P, mu1, lam, scale, tw, h->skip);
+    k_nstrided<T, N, false, 3><<<grid, NT, smem, st>>>(work, P, PP, mu1, lam, scale, tw, h->skip);
+    k_nxinv<T, N, 3><<<grid, NT, smem, st>>>(work, sa.keep || sa.out_user == nullptr, sa.out_user, sa.aux, sa.beta,
+                                              sa.gamma, tw, h->skip);
+    KFBI_CHECK_LAUNCH_N(5);
+  } else {
+    if ((rc = prep(k_nxfwd<T, N, 2>, smem))) return rc;
+    if ((rc = prep(k_nstrided<T, N, true, 2>, smem))) return rc;
+    if ((rc = prep(k_nxinv<T, N, 2>, smem))) return rc;
+    k_nxfwd<T, N, 2><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.corr, t.irr, t.line_start, tw, h->skip);
+    k_nstrided<T, N, true, 2><<<grid, NT, smem, st>>>(work, P, 0, mu1, lam, scale, tw, h->skip);
+    k_nxinv<T, N, 2><<<grid, NT, smem, st>>>(work, sa.keep || sa.out_user == nullptr, sa.out_user, sa.aux, sa.beta,
+                                              sa.gamma, tw, h->skip);
+    KFBI_CHECK_LAUNCH_N(3);
+  }
+  return KFBI_OK;
+}
+
+int box_solve_neumann64(kfbi_handle* h, const SolveArgs& sa, double* work) {
+  if (!(sa.lambda > 0.0)) {
+    set_error("the Neumann box needs lambda > 0 (no Green's function of the Poisson operator exists)");
+    return KFBI_ERR_ARG;
+  }
+  const double* mu1 = h->t.mu;
+  const double* tw = h->t.tw64;
+  switch (h->grid.N) {
+    case 8: return run_solve_neumann<double, 8>(h, sa, work, mu1, tw);
+    case 16: return run_solve_neumann<double, 16>(h, sa, work, mu1, tw);
+    case 32: return run_solve_neumann<double, 32>(h, sa, work, mu1, tw);
+    case 64: return run_solve_neumann<double, 64>(h, sa, work, mu1, tw);
+    case 128: return run_solve_neumann<double, 128>(h, sa, work, mu1, tw);
+    case 256: return run_solve_neumann<double, 256>(h, sa, work, mu1, tw);
+    case 384: return run_solve_neumann<double, 384>(h, sa, work, mu1, tw);
+    case 512: return run_solve_neumann<double, 512>(h, sa, work, mu1, tw);
+    default:
+      set_error("unsupported grid size N=%d", h->grid.N);
+      return KFBI_ERR_ARG;
+  }
+}
+
 }  // namespace
 
 // TMA descriptors of the padded float32 grid for the strided passes (3-D,
@@ -1260,6 +1557,7 @@ int dst_supported(int N) {
 }
 
 int box_solve64(kfbi_handle* h, const SolveArgs& a, double* work) {
+  if (h->grid.bc == KFBI_BOX_NEUMANN) return box_solve_neumann64(h, a, work);
   return dispatch<double>(h, a, work, h->t.mu, h->t.tw64);
 }
 

@@ -67,7 +67,21 @@ struct GeomParams {
 struct GridParams {
   int dim, N;
   double lo, h;
+  int bc = KFBI_BOX_DIRICHLET;  // box condition: field layout (N-1)^dim or (N+1)^dim
 };
+
+// field (user) layout of a grid: nodes per axis and the node index k of
+// array index 0 (interior nodes of the Dirichlet box, all nodes of the
+// Neumann box)
+__host__ __device__ inline int field_n(const GridParams& g) { return g.bc == KFBI_BOX_NEUMANN ? g.N + 1 : g.N - 1; }
+__host__ __device__ inline int field_first(const GridParams& g) { return g.bc == KFBI_BOX_NEUMANN ? 0 : 1; }
+// row length of the work grid: N (Dirichlet, padded), N + 1 (Neumann, the
+// field layout itself)
+__host__ __device__ inline int work_n(const GridParams& g) { return g.bc == KFBI_BOX_NEUMANN ? g.N + 1 : g.N; }
+__host__ __device__ inline int64_t field_count(const GridParams& g) {
+  const int64_t n = field_n(g);
+  return g.dim == 3 ? n * n * n : n * n;
+}
 
 // Sparse tables of the hot path (all device pointers).
 struct Tables {
@@ -109,7 +123,11 @@ struct Tables {
   double* tw64 = nullptr;         // [2N] complex e^{i pi j / N}
   float* mu32 = nullptr;
   float* tw32 = nullptr;
-  uint8_t* inside = nullptr;      // [(N-1)^dim]
+  uint8_t* inside = nullptr;      // [(N-1)^dim] interior nodes
+  // the same mask and the irregular nodes' flat indices on the field layout
+  // (aliases of inside and irr for the Dirichlet box)
+  uint8_t* inside_user = nullptr;
+  int32_t* irr_user = nullptr;
   int n_inside = 0;
   double* nodes = nullptr;        // [M][dim] interface nodes
   double* n_normal = nullptr;     // [M][3] outward normals at the nodes

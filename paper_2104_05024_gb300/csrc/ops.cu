@@ -52,8 +52,8 @@ __global__ void k_limit(Tables t, GridParams gr, const T* __restrict__ grid, con
                         const int* __restrict__ skip) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= t.M || (skip != nullptr && *skip)) return;
-  const int d = gr.dim, N = gr.N;
-  const int64_t sx = 1, sy = N, sz = (int64_t)N * N;
+  const int d = gr.dim, P = work_n(gr);
+  const int64_t sx = 1, sy = P, sz = (int64_t)P * P;
   const int64_t c = t.n_base[i];
   const int s0 = t.n_sign[(size_t)i * d], s1 = t.n_sign[(size_t)i * d + 1];
   const double* wn = t.n_wn + (size_t)i * t.P;
@@ -76,18 +76,19 @@ __global__ void k_limit(Tables t, GridParams gr, const T* __restrict__ grid, con
   out[i] = (base != nullptr ? base[i] : 0.0) + sgn * acc;
 }
 
-// same limit from a user-layout (N-1)^d grid (zero outside the interior)
+// same limit from a field-layout grid
 __global__ void k_limit_user(Tables t, GridParams gr, const double* __restrict__ u, const double* __restrict__ x,
                              const double* __restrict__ base, double sgn, double* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= t.M) return;
-  const int d = gr.dim, n1 = gr.N - 1;
+  const int d = gr.dim, n1 = field_n(gr), k0 = field_first(gr);
   const int* c = t.n_center + (size_t)i * d;
   const int8_t* sg = t.n_sign + (size_t)i * d;
   const double* wn = t.n_wn + (size_t)i * t.P;
   const int cx = c[0], cy = c[1], cz = d == 3 ? c[2] : 1;
   auto at = [&](int dx, int dy, int dz) -> double {
-    const int64_t f = (int64_t)(cx + dx - 1) + (int64_t)(cy + dy - 1) * n1 + (d == 3 ? (int64_t)(cz + dz - 1) * n1 * n1 : 0);
+    const int64_t f = (int64_t)(cx + dx - k0) + (int64_t)(cy + dy - k0) * n1 +
+                      (d == 3 ? (int64_t)(cz + dz - k0) * n1 * n1 : 0);
     return u[f];
   };
   double acc = wn[0] * at(0, 0, 0) + wn[1] * at(-1, 0, 0) + wn[2] * at(1, 0, 0) + wn[3] * at(0, -1, 0) +
@@ -261,7 +262,7 @@ __global__ void k_scatter(Tables t, const double* __restrict__ corr, double* __r
 }
 __global__ void k_scatter2(Tables t, const double* __restrict__ corr, double* __restrict__ g) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < t.n_irr) g[t.irr[i]] = corr[i];
+  if (i < t.n_irr) g[t.irr_user[i]] = corr[i];
 }
 
 __global__ void k_pad_to_user(GridParams gr, const double* __restrict__ p, double* __restrict__ u, int64_t total) {
@@ -842,11 +843,10 @@ int launch_stim_source(kfbi_handle* h, const double* V, double lambda, const dou
 }
 
 int launch_ue_S(kfbi_handle* h, const double* V, const double* S, double* ue) {
-  const int n1 = h->grid.N - 1;
-  const int64_t total = h->grid.dim == 3 ? (int64_t)n1 * n1 * n1 : (int64_t)n1 * n1;
+  const int64_t total = field_count(h->grid);
   const int nb = RED_BLOCKS;
   k_phi_e<<<grid_blocks(total, 256), 256, 0, h->stream>>>(V, S, h->sigma_i, h->sigma_e, ue, total);
-  k_masked_sum<<<nb, 256, 0, h->stream>>>(ue, h->t.inside, total, h->w.partial);
+  k_masked_sum<<<nb, 256, 0, h->stream>>>(ue, h->t.inside_user, total, h->w.partial);
   k_dots_final<<<1, 256, 0, h->stream>>>(h->w.partial, nb, 1, h->w.partial + nb);
   k_sub_mean<<<grid_blocks(total, 256), 256, 0, h->stream>>>(ue, h->w.partial + nb, 1.0 / (double)h->t.n_inside,
                                                             total);
@@ -883,11 +883,10 @@ int launch_midpoint_diff(kfbi_handle* h, double* V, const double* a, const doubl
 
 // dst = src - mean_Omega(src)
 int launch_sub_mean(kfbi_handle* h, const double* src, double* dst) {
-  const int n1 = h->grid.N - 1;
-  const int64_t total = h->grid.dim == 3 ? (int64_t)n1 * n1 * n1 : (int64_t)n1 * n1;
+  const int64_t total = field_count(h->grid);
   const int nb = RED_BLOCKS;
   if (dst != src) KFBI_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)total, cudaMemcpyDeviceToDevice, h->stream));
-  k_masked_sum<<<nb, 256, 0, h->stream>>>(dst, h->t.inside, total, h->w.partial);
+  k_masked_sum<<<nb, 256, 0, h->stream>>>(dst, h->t.inside_user, total, h->w.partial);
   k_dots_final<<<1, 256, 0, h->stream>>>(h->w.partial, nb, 1, h->w.partial + nb);
   k_sub_mean<<<grid_blocks(total, 256), 256, 0, h->stream>>>(dst, h->w.partial + nb, 1.0 / (double)h->t.n_inside,
                                                              total);
@@ -908,8 +907,7 @@ int launch_lincomb(kfbi_handle* h, double* y, double a, const double* x, double 
 }
 
 int launch_scatter_grid(kfbi_handle* h, const double* corr, double* grid_user) {
-  const int n1 = h->grid.N - 1;
-  const int64_t total = h->grid.dim == 3 ? (int64_t)n1 * n1 * n1 : (int64_t)n1 * n1;
+  const int64_t total = field_count(h->grid);
   k_scatter<<<grid_blocks(total, 256), 256, 0, h->stream>>>(h->t, corr, grid_user, total);
   if (h->t.n_irr > 0) k_scatter2<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->t, corr, grid_user);
   KFBI_CHECK_LAUNCH_N(h->t.n_irr > 0 ? 2 : 1);
@@ -1043,10 +1041,9 @@ int launch_react_be(const kfbi_fhn* p, double k, double* V, double* w, int64_t n
 }
 
 int launch_ue(kfbi_handle* h, const double* V, double* ue) {
-  const int n1 = h->grid.N - 1;
-  const int64_t total = h->grid.dim == 3 ? (int64_t)n1 * n1 * n1 : (int64_t)n1 * n1;
+  const int64_t total = field_count(h->grid);
   const int nb = RED_BLOCKS;
-  k_masked_sum<<<nb, 256, 0, h->stream>>>(V, h->t.inside, total, h->w.partial);
+  k_masked_sum<<<nb, 256, 0, h->stream>>>(V, h->t.inside_user, total, h->w.partial);
   k_dots_final<<<1, 256, 0, h->stream>>>(h->w.partial, nb, 1, h->w.partial + nb);
   k_ue<<<grid_blocks(total, 256), 256, 0, h->stream>>>(V, h->w.partial + nb, 1.0 / (double)h->t.n_inside,
                                                        h->sigma_i, h->sigma_e, ue, total);

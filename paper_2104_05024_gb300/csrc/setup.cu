@@ -642,7 +642,8 @@ __host__ __device__ int node_stencil_row(const GeomParams& gp, const GridParams&
     t.n_sign[(size_t)i * d + ax] = (int8_t)sg[ax];
   }
   if (errbits) return errbits;
-  t.n_base[i] = (int32_t)(((int64_t)(d == 3 ? c[2] : 0) * N + c[1]) * N + c[0]);
+  const int wn = work_n(gr);  // work-grid row length; node k sits at index k on both layouts
+  t.n_base[i] = (int32_t)(((int64_t)(d == 3 ? c[2] : 0) * wn + c[1]) * wn + c[0]);
   int comp = 0;
   for (int cc = 1; cc < gp.n_comp; ++cc)
     if (i >= gp.comp_vert_offset[cc]) comp = cc;
@@ -781,6 +782,25 @@ __global__ void k_node_density(GeomParams gp, GridParams gr, DensityInputs di, c
   if (i >= t.M) return;
   const int e = node_density_row(gp, gr, di, vtri, AB, t, i);
   if (e) atomicOr(err, e);
+}
+
+// interior flat index -> field-layout flat index (Neumann box: all nodes)
+__host__ __device__ inline int64_t interior_to_field(const GridParams& gr, int64_t f) {
+  const int n1 = gr.N - 1, P = gr.N + 1;
+  const int x = (int)(f % n1) + 1, y = (int)((f / n1) % n1) + 1;
+  const int z = gr.dim == 3 ? (int)(f / ((int64_t)n1 * n1)) + 1 : 0;
+  return ((int64_t)z * P + y) * P + x;
+}
+
+// the inside mask and the irregular nodes on the field layout of the Neumann
+// box (box-boundary nodes are outside Omega)
+__global__ void k_field_mask(GridParams gr, const uint8_t* inside, int64_t total, uint8_t* inside_user) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < total; f += (int64_t)gridDim.x * blockDim.x)
+    inside_user[interior_to_field(gr, f)] = inside[f];
+}
+__global__ void k_field_irr(GridParams gr, const int32_t* irr, int n, int32_t* irr_user) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) irr_user[i] = (int32_t)interior_to_field(gr, irr[i]);
 }
 
 // per irregular node: its crossing arms (binary search in the per-axis lists)
@@ -1101,6 +1121,20 @@ int setup_build(kfbi_handle* h, const kfbi_geometry* geom) {
   if (t.n_int > 0) k_bisect<<<(t.n_int + 127) / 128, 128, 0, st>>>(gp, gr, t.c_lo, t.c_axis, t.n_int, t.c_z, t.c_comp, err);
   KFBI_CHECK_LAUNCH();
 
+  // the mask and the irregular list on the field layout
+  if (gr.bc == KFBI_BOX_NEUMANN) {
+    const int64_t nf = field_count(gr);
+    if ((rc = dalloc(h, &t.inside_user, (size_t)nf))) return rc;
+    if ((rc = dalloc(h, &t.irr_user, (size_t)t.n_irr))) return rc;
+    KFBI_CUDA(cudaMemsetAsync(t.inside_user, 0, (size_t)nf, st));
+    k_field_mask<<<blocks_for(total, 256), 256, 0, st>>>(gr, t.inside, total, t.inside_user);
+    if (t.n_irr > 0) k_field_irr<<<(t.n_irr + 127) / 128, 128, 0, st>>>(gr, t.irr, t.n_irr, t.irr_user);
+    KFBI_CHECK_LAUNCH_N(2);
+  } else {
+    t.inside_user = t.inside;
+    t.irr_user = t.irr;
+  }
+
   // irregular arms and x-line offsets
   if ((rc = dalloc(h, &t.irr_arm, (size_t)t.n_irr * 6))) return rc;
   if ((rc = dalloc(h, &t.irr_narm, (size_t)t.n_irr))) return rc;
@@ -1236,8 +1270,10 @@ int setup_build(kfbi_handle* h, const kfbi_geometry* geom) {
 
   // transform tables
   {
-    std::vector<double> mu(N), tw(4 * (size_t)N);
-    for (int k = 0; k < N; ++k) {
+    // mu1[p], p = 0..N (the cosine modes of the Neumann box use all of
+    // them, the sine modes p = 1..N-1)
+    std::vector<double> mu(N + 1), tw(4 * (size_t)N);
+    for (int k = 0; k <= N; ++k) {
       const double s = std::sin(M_PI * k / (2.0 * N));
       mu[k] = -(4.0 / (gr.h * gr.h)) * s * s;
     }

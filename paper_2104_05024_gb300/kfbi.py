@@ -19,6 +19,7 @@ ELLIPSE2, ELLIPSOID3, STAR3, SHELL3 = 1, 2, 3, 4
 FP64, MIXED, MIXED_LEARNED, FP32 = 0, 1, 2, 3
 GMRES, RICHARDSON = 0, 1
 WARM_PREVIOUS, WARM_PROJECTION = 0, 1
+BOX_DIRICHLET, BOX_NEUMANN = 0, 1
 HISTORY = 8
 MAX_COMP = 4
 
@@ -33,7 +34,7 @@ class Geometry(C.Structure):
 
 
 class GridStruct(C.Structure):
-    _fields_ = [("dim", C.c_int), ("N", C.c_int), ("lo", C.c_double), ("hi", C.c_double)]
+    _fields_ = [("dim", C.c_int), ("N", C.c_int), ("lo", C.c_double), ("hi", C.c_double), ("box", C.c_int)]
 
 
 class Opts(C.Structure):
@@ -301,7 +302,8 @@ class KFBI:
         else:
             g.n_comp = 1
         self.dim, self.N = int(grid.dim), int(grid.N)
-        gs = GridStruct(self.dim, self.N, float(getattr(grid, "lo", lo)), float(getattr(grid, "hi", hi)))
+        box = BOX_NEUMANN if getattr(grid, "bc", "dirichlet") == "neumann" else BOX_DIRICHLET
+        gs = GridStruct(self.dim, self.N, float(getattr(grid, "lo", lo)), float(getattr(grid, "hi", hi)), box)
         self.opts = Opts(precision, solver, tol, restart, max_iter, gamma, _stream(), warm)
         h = C.c_void_p()
         self.coupled = D_i is not None

@@ -117,6 +117,34 @@ def test_shell256_strang_fp64(shell256):
     assert rel(wd.cpu().numpy(), w) < TOL64
 
 
+def test_shell256_neumann_box():
+    """The Neumann box at the bench size (257^3 nodes): cosine-transform box
+    solve at 1e-12, the operators at 1e-10, and one float64 Strang step
+    against the oracle's."""
+    geom, grid, cfg, V0, w0 = C.config2(N=256, steps=1, bc="neumann")
+    o = OK(geom, grid)
+    g = K.KFBI(geom, grid, sigma_i=cfg.sigma_i, sigma_e=cfg.sigma_e, dt=cfg.dt, tol=1e-12)
+    lam = lam_of(cfg, C.FHN_CONFIG)
+    r = np.random.default_rng(257).standard_normal(grid.shape)
+    ref = boxsolve.solve(r, lam, grid)
+    v = torch.empty(grid.shape, dtype=torch.float64, device=DEV)
+    g.box_solve(cuda(r), v, lam, precision=K.FP64)
+    assert rel(v.cpu().numpy(), ref) < 1e-12
+    X = geom.nodes
+    psi = np.cos(2.0 * X[:, 0]) + 0.3 * X[:, 1] * X[:, 2]
+    lim = torch.empty(geom.M, dtype=torch.float64, device=DEV)
+    g.apply_A(cuda(psi), lim, lam)
+    assert rel(lim.cpu().numpy(), o.apply_A(psi, lam)) < TOL64
+    del o
+    V, w = _oracle_steps(geom, grid, cfg, V0, w0, 1, 1e-12)
+    Vd, wd = cuda(V0), cuda(w0)
+    st = g.bidomain_step(C.FHN_CONFIG, Vd, wd, None, nsteps=1, tol=1e-12)
+    g.close()
+    assert st[0]["rel_res"] <= 1e-12
+    assert rel(Vd.cpu().numpy(), V) < TOL64
+    assert rel(wd.cpu().numpy(), w) < TOL64
+
+
 def _trained_network():
     """A network trained (briefly, on the GPU) on rows of two 64^3 shell runs
     from training stimuli: its output is not zero."""
