@@ -53,6 +53,7 @@ from kfbi_workloads import geometry as G
 from kfbi_workloads.configs import Grid
 from . import boxsolve, density, grid as GR, krylov
 from . import levelset as LS
+from . import mesh as MESH
 
 
 def stencil_offsets(d: int, s: np.ndarray) -> np.ndarray:
@@ -111,18 +112,33 @@ class KFBI:
         self.geom, self.grid = geom, grid
         d = grid.dim
         self.d = d
-        self.inside = GR.classify(geom, grid)
-        self.irregular = GR.irregular_list(self.inside)
-        self.ints = GR.intersections(geom, grid, self.inside)
+        self.mesh = geom.kind == G.MESH3
+        if self.mesh:
+            # the boundary is only a triangle mesh (Section 5.3, Example 4)
+            self.patch_ids, self.patch_cnt = density.patches(geom.tri, geom.M)
+            self.frames = MESH.tri_frames(geom, self.patch_ids, self.patch_cnt)
+            self.inside = MESH.classify(geom, grid)
+            self.irregular = GR.irregular_list(self.inside)
+            self.ints = MESH.intersections(geom, grid, self.inside, self.frames)
+        else:
+            self.inside = GR.classify(geom, grid)
+            self.irregular = GR.irregular_list(self.inside)
+            self.ints = GR.intersections(geom, grid, self.inside)
         self.Pint = GR.intersection_points(grid, self.inside.shape, self.ints)
         nI = self.Pint.shape[0]
         self.n_int = np.empty((nI, d))
         self.S_int = np.empty((nI, d, d))
-        for c in range(LS.n_components(geom)):
-            m = self.ints["comp"] == c
-            if np.any(m):
-                self.n_int[m], self.S_int[m] = LS.normal_shape(geom, c, self.Pint[m])
-        self.n_node, self.S_node = LS.normals_shapes_at_nodes(geom)
+        if self.mesh:
+            if nI:
+                self.n_int, self.S_int = MESH.normal_shape(self.frames, self.ints["tri"], self.Pint)
+            vt = density.vertex_triangle(geom.tri, geom.M)
+            self.n_node, self.S_node = MESH.normal_shape(self.frames, vt, geom.nodes)
+        else:
+            for c in range(LS.n_components(geom)):
+                m = self.ints["comp"] == c
+                if np.any(m):
+                    self.n_int[m], self.S_int[m] = LS.normal_shape(geom, c, self.Pint[m])
+            self.n_node, self.S_node = LS.normals_shapes_at_nodes(geom)
         self.center, self.sign = GR.cell_index(grid, geom.nodes)
         self.ds = surface_weights(geom)
         self.area = float(self.ds.sum())
@@ -154,11 +170,14 @@ class KFBI:
         ids, cnt = density.patches(geom.tri, geom.M)
         self.patch_ids, self.patch_cnt = ids, cnt
         vt = density.vertex_triangle(geom.tri, geom.M)
-        tri_int = np.empty(self.Pint.shape[0], dtype=np.int64)
-        for c in range(LS.n_components(geom)):
-            m = self.ints["comp"] == c
-            if np.any(m):
-                tri_int[m] = density.locate(geom, c, self.Pint[m])
+        if self.mesh:
+            tri_int = self.ints["tri"].copy()       # the triangle the ray crossed
+        else:
+            tri_int = np.empty(self.Pint.shape[0], dtype=np.int64)
+            for c in range(LS.n_components(geom)):
+                m = self.ints["comp"] == c
+                if np.any(m):
+                    tri_int[m] = density.locate(geom, c, self.Pint[m])
         self.tri_int, self.tri_node = tri_int, vt
         self.pid_int, self.w0_int, self.wg_int, self.cond_int = density.patch_weights(
             geom, ids, cnt, tri_int, self.Pint, self.n_int)
