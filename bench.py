@@ -4,7 +4,7 @@ the 256^3 prolate-shell workload, each diffusion solve converged to a 1e-8
 GMRES residual, through the KFBI library's C ABI on one GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl kfbi|reference]
-    python bench.py --workload star-sweep|shell-large|heldout|stiff|stimulus|coupled|neumann
+    python bench.py --workload star-sweep|shell-large|heldout|stiff|stimulus|coupled|neumann|mesh
 
 One JSON line on rank 0.  Multi-GPU runs are independent replicas (one
 stimulus location per rank, no data-path collective); `value` sums the ranks.
@@ -763,6 +763,47 @@ def run_neumann(args):
                       "unit": "steps/s", "rows": rows}), flush=True)
 
 
+def run_mesh(args):
+    """A domain given only by its boundary triangle mesh (Section 5.3,
+    Example 4; the left ventricle of the paper is not available, a smooth
+    non-convex geodesic mesh with valence-5 vertices stands in): setup time
+    of the mesh classification, crossings and local surfaces on the GPU, and
+    Strang steps/s at N^3 in float64 and in the float32-transform form with
+    the history projection, tol 1e-8."""
+    import time
+
+    import torch
+
+    import paper_2104_05024_gb300.kfbi as K
+    from kfbi_workloads import configs as C, geometry as G
+    dev = torch.device("cuda", 0)
+    N = args.N
+    geom, grid = G.bean_mesh(max(4, N // 4)), C.Grid(3, N)
+    V0 = C.ball_stimulus(grid, (0.45, 0.0, 0.0), 0.15)
+    rows = {}
+    for name, prec in (("fp64", K.FP64), ("mixed_projection", K.MIXED)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = K.KFBI(geom, grid, sigma_i=1.0, sigma_e=2.0, dt=0.05, tol=1e-8, precision=prec,
+                   warm=K.WARM_PROJECTION, restart=50, max_iter=500)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        V = torch.tensor(V0, device=dev)
+        w = torch.zeros_like(V)
+        h.bidomain_step(C.FHN_CONFIG, V, w, None, nsteps=3)
+        ms, st = _event_ms(lambda: h.bidomain_step(C.FHN_CONFIG, V, w, None, nsteps=args.steps))
+        rows[name] = {"setup_s": round(setup_s, 3), "steps_per_s": round(1000.0 * args.steps / ms, 3),
+                      "iters_per_step": float(np.mean([s["iters"] for s in st])),
+                      "true_rel_res_max": float(max(s["true_rel_res"] for s in st)),
+                      "V_max": float(V.abs().max()), "n_irregular": h.info["n_irregular"],
+                      "n_crossings": h.info["n_crossings"]}
+        h.close()
+    print(json.dumps({"metric": "mesh-only domain: setup and Strang steps/s",
+                      "workload": f"geodesic bean mesh, {geom.M} vertices / {geom.tri.shape[0]} triangles, {N}^3, "
+                                  f"FHN of the workloads, dt 0.05, tol 1e-8, {args.steps} steps after 3",
+                      "unit": "steps/s", "rows": rows}), flush=True)
+
+
 # -------------------------------------------------------------- CPU oracle
 
 def cpu_baseline(N, steps=1):
@@ -820,7 +861,7 @@ def main():
     ap.add_argument("--train-steps", type=int, default=12, help="Strang steps per training stimulus (learned form)")
     ap.add_argument("--train-epochs", type=int, default=8)
     ap.add_argument("--workload", default="strang",
-                    choices=["strang", "star-sweep", "shell-large", "heldout", "stiff", "stimulus", "coupled", "neumann"],
+                    choices=["strang", "star-sweep", "shell-large", "heldout", "stiff", "stimulus", "coupled", "neumann", "mesh"],
                     help="strang: the timed benchmark; the others print one result line each")
     args = ap.parse_args()
     if args.steps is None:
@@ -841,6 +882,8 @@ def main():
         run_coupled(args)
     elif args.workload == "neumann":
         run_neumann(args)
+    elif args.workload == "mesh":
+        run_mesh(args)
     else:
         run_gpu(args)
 

@@ -48,6 +48,10 @@ extern "C" {
 #define KFBI_ELLIPSOID3 2  /* params: a, b, c                                 */
 #define KFBI_STAR3 3       /* params: A, B of r = A + B sin(3 theta) cos(2 phi) */
 #define KFBI_SHELL3 4      /* params: outer a, b, c, inner a, b, c            */
+#define KFBI_MESH3 5       /* no params: Omega is bounded by the closed triangle
+                              mesh (nodes, tri) alone (Section 5.3, Example 4);
+                              triangles wound counter-clockwise seen from
+                              outside Omega; cube_t / cube_n / comp_* unused   */
 
 /* surface-component point-location maps of 3-D cube-sphere meshes */
 #define KFBI_MAP_RADIAL 0
@@ -93,6 +97,10 @@ extern "C" {
  *                         triangle ((f n + j) n + i) 2 + half of component c
  *                         at comp_tri_offset[c] (face f, quad (i, j), half 0 =
  *                         (v_ij, v_i+1j, v_ij+1), half 1 = (v_i+1j, v_i+1j+1, v_ij+1)).
+ *                         KFBI_MESH3: any closed, consistently wound manifold
+ *                         mesh whose vertices are the nodes (vertex ring of a
+ *                         triangle at most 16 points); it is the only
+ *                         description of the surface.
  *  cube_t  [cube_n + 1]   equiangular face coordinates (-1 ... 1).
  */
 typedef struct {

@@ -692,8 +692,13 @@ static int create_impl(const kfbi_geometry* geom, const kfbi_grid* grid, double 
     set_error("bad geometry or grid extents");
     return KFBI_ERR_ARG;
   }
-  if (grid->dim == 3 && (geom->tri == nullptr || geom->n_tri <= 0 || geom->cube_t == nullptr || geom->n_comp < 1 ||
-                         geom->n_comp > KFBI_MAX_COMP)) {
+  if (grid->dim == 3 && geom->kind == KFBI_MESH3) {
+    if (geom->tri == nullptr || geom->n_tri <= 0) {
+      set_error("a mesh domain needs its triangles");
+      return KFBI_ERR_ARG;
+    }
+  } else if (grid->dim == 3 && (geom->tri == nullptr || geom->n_tri <= 0 || geom->cube_t == nullptr ||
+                                geom->n_comp < 1 || geom->n_comp > KFBI_MAX_COMP)) {
     set_error("3-D geometry needs a triangle mesh and cube-sphere tables");
     return KFBI_ERR_ARG;
   }
@@ -728,9 +733,9 @@ static int create_impl(const kfbi_geometry* geom, const kfbi_grid* grid, double 
   memset(&gp, 0, sizeof(gp));
   gp.dim = geom->dim;
   gp.kind = geom->kind;
-  gp.n_comp = grid->dim == 3 ? geom->n_comp : 1;
+  gp.n_comp = grid->dim == 3 && geom->kind != KFBI_MESH3 ? geom->n_comp : 1;
   for (int i = 0; i < 16; ++i) gp.p[i] = geom->params[i];
-  for (int c = 0; c < KFBI_MAX_COMP; ++c) {
+  for (int c = 0; c < KFBI_MAX_COMP && geom->kind != KFBI_MESH3; ++c) {
     gp.comp_map[c] = geom->comp_map[c];
     for (int k = 0; k < 3; ++k) gp.comp_axes[c][k] = geom->comp_axes[c][k];
     gp.comp_tri_offset[c] = geom->comp_tri_offset[c];

@@ -102,6 +102,7 @@ struct Tables {
   int32_t* c_lo = nullptr;        // user-layout flat index of the lower node
   int8_t* c_comp = nullptr;
   double* c_z = nullptr;
+  int32_t* c_tri = nullptr;       // mesh-only domains: the triangle each crossing lies on
   int32_t* c_cnt = nullptr;       // entries of the crossing's density row
   int32_t* c_pid = nullptr;       // [n_int][PATCH_MAX] indices into x = psi (3-D) or [psi; m] (2-D)
   double* c_wlo = nullptr;        // [n_int][PATCH_MAX] correction weights for the lower node

@@ -489,7 +489,307 @@ struct DensityInputs {
   const int32_t* patch_cnt; // [n_tri]
   const double* cube_t;
   int M;
+  // mesh-only domains: each node's fit triangle and every triangle's local
+  // surface (see below)
+  const int32_t* vtri = nullptr;
+  const double* tri_fit = nullptr;
 };
+
+// ---- domains given only by a closed triangle mesh (KFBI_MESH3) ----
+// Section 5.3 / Example 4: the triangles are all there is.  Classification is
+// the parity of ray crossings along x; every edge is evaluated once, in its
+// canonical direction (lower vertex index first), as
+//   E(p) = (Q_u - P_u)(p_v - P_v) - (Q_v - P_v)(p_u - P_u)
+// (u, v the axes after the ray's axis), so the two triangles of an edge see
+// the same value; E = 0 takes the sign of the symbolic perturbation
+// p + (eps, eps^2).  A line meets a triangle iff the three signs, taken in
+// the triangle's winding direction, agree; the crossing coordinate is the
+// barycentric combination of the vertices' coordinates along the ray (the
+// centroid's for a triangle degenerate in projection), clamped to the
+// triangle.  A node is inside iff an odd number of its x-line's crossings lie
+// beyond it.  Crossing points are then moved onto the triangle's local
+// surface w = h(s, t): the quadratic height over the triangle's plane (frame:
+// centroid, unit face normal, tangents as for the density fit; coordinates
+// scaled by the patch radius ell) through the triangle's fit points.  The
+// surface is the zero set of phi = w - h, growing out of Omega, so normals and
+// shape operators follow as for the level sets.
+constexpr int MESH_NEWTON = 30;
+constexpr int TRI_FIT = 19;          // o[3], t1[3], t2[3], nf[3], ell, c[6]
+constexpr double MESH_NEAR = 1e-6;   // fallback window of a crossing, units of h
+
+__host__ __device__ inline int canon_sign(double Pu, double Pv, double Qu, double Qv, double pu, double pv,
+                                          double* E) {
+  const double d1 = Qu - Pu, d2 = pv - Pv, d3 = Qv - Pv, d4 = pu - Pu;
+  const double e = d1 * d2 - d3 * d4;
+  *E = e;
+  if (e > 0.0) return 1;
+  if (e < 0.0) return -1;
+  if (d3 != 0.0) return d3 < 0.0 ? 1 : -1;
+  return d1 > 0.0 ? 1 : -1;
+}
+
+// does the line through (pu, pv) along axis a meet triangle t?  *xh: where
+__host__ __device__ inline bool tri_hit(const double* X, const int32_t* T, int t, int a, double pu, double pv,
+                                        double* xh) {
+  const int u = (a + 1) % 3, v = (a + 2) % 3;
+  const int id[3] = {T[3 * t], T[3 * t + 1], T[3 * t + 2]};
+  double e[3];
+  int sg[3];
+  for (int k = 0; k < 3; ++k) {
+    const int A = id[k], B = id[(k + 1) % 3];
+    const double* PA = X + 3 * (size_t)A;
+    const double* PB = X + 3 * (size_t)B;
+    if (A < B) {
+      sg[k] = canon_sign(PA[u], PA[v], PB[u], PB[v], pu, pv, &e[k]);
+    } else {
+      sg[k] = -canon_sign(PB[u], PB[v], PA[u], PA[v], pu, pv, &e[k]);
+      e[k] = -e[k];
+    }
+  }
+  if (sg[0] != sg[1] || sg[1] != sg[2]) return false;
+  const double eAB = e[0], eBC = e[1], eCA = e[2];
+  const double den = (eBC + eCA) + eAB;
+  const double mag = (fabs(eBC) + fabs(eCA)) + fabs(eAB);
+  const double Aa = X[3 * (size_t)id[0] + a], Ba = X[3 * (size_t)id[1] + a], Ca = X[3 * (size_t)id[2] + a];
+  double x;
+  if (fabs(den) <= 1e-12 * mag) x = ((Aa + Ba) + Ca) / 3.0;
+  else x = ((eBC * Aa + eCA * Ba) + eAB * Ca) / den;
+  x = fmin(fmax(x, fmin(fmin(Aa, Ba), Ca)), fmax(fmax(Aa, Ba), Ca));
+  *xh = x;
+  return true;
+}
+
+// grid-line candidates of triangle t along axis a (interior node indices)
+__host__ __device__ inline void tri_lines(const double* X, const int32_t* T, int t, int a, const GridParams& gr,
+                                          int* ju0, int* ju1, int* jv0, int* jv1) {
+  const int u = (a + 1) % 3, v = (a + 2) % 3;
+  double umin = 1e300, umax = -1e300, vmin = 1e300, vmax = -1e300;
+  for (int k = 0; k < 3; ++k) {
+    const double* P = X + 3 * (size_t)T[3 * t + k];
+    umin = fmin(umin, P[u]);
+    umax = fmax(umax, P[u]);
+    vmin = fmin(vmin, P[v]);
+    vmax = fmax(vmax, P[v]);
+  }
+  const int n1 = gr.N - 1;
+  *ju0 = max(1, (int)floor((umin - gr.lo) / gr.h) - 1);
+  *ju1 = min(n1, (int)ceil((umax - gr.lo) / gr.h) + 1);
+  *jv0 = max(1, (int)floor((vmin - gr.lo) / gr.h) - 1);
+  *jv1 = min(n1, (int)ceil((vmax - gr.lo) / gr.h) + 1);
+}
+
+// per triangle: count its crossings with the lines along a (offs == nullptr)
+// or write them from offs[t] on: line (interior numbering k_v, k_u), x, t
+__global__ void k_mesh_hits(const double* X, const int32_t* T, int n_tri, GridParams gr, int a, const int* offs,
+                            int* counts, int32_t* line, double* xh, int32_t* tri) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tri) return;
+  int ju0, ju1, jv0, jv1;
+  tri_lines(X, T, t, a, gr, &ju0, &ju1, &jv0, &jv1);
+  const int n1 = gr.N - 1;
+  int c = 0;
+  for (int ju = ju0; ju <= ju1; ++ju)
+    for (int jv = jv0; jv <= jv1; ++jv) {
+      double x;
+      if (!tri_hit(X, T, t, a, node_coord(gr, ju), node_coord(gr, jv), &x)) continue;
+      if (offs != nullptr) {
+        const int o = offs[t] + c;
+        line[o] = (jv - 1) * n1 + (ju - 1);
+        xh[o] = x;
+        tri[o] = t;
+      }
+      ++c;
+    }
+  if (offs == nullptr) counts[t] = c;
+}
+
+// inside flags of the interior nodes from the sorted crossings of their
+// x-line: odd count beyond the node
+__global__ void k_mesh_classify(GridParams gr, const int32_t* ptr, const double* hx, uint8_t* inside) {
+  const int n1 = gr.N - 1;
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n1 * n1) return;
+  const int j0 = ptr[l], j1 = ptr[l + 1];
+  int j = j0;
+  uint8_t* row = inside + (size_t)l * n1;
+  for (int k = 1; k <= n1; ++k) {
+    const double xk = node_coord(gr, k);
+    while (j < j1 && hx[j] <= xk) ++j;
+    row[k - 1] = (uint8_t)((j1 - j) & 1);
+  }
+}
+
+__host__ __device__ inline void fit_height(const double* f, double s, double q, double* hs, double* hq,
+                                           double* hh) {
+  const double* c = f + 13;
+  *hh = c[0] + c[1] * s + c[2] * q + c[3] * s * s + c[4] * s * q + c[5] * q * q;
+  *hs = c[1] + 2.0 * c[3] * s + c[4] * q;
+  *hq = c[2] + c[4] * s + 2.0 * c[5] * q;
+}
+
+__host__ __device__ inline void fit_local(const double* f, const double* P, double* s, double* q, double* w) {
+  const double D0 = P[0] - f[0], D1 = P[1] - f[1], D2 = P[2] - f[2];
+  const double ell = f[12];
+  *s = (D0 * f[3] + D1 * f[4] + D2 * f[5]) / ell;
+  *q = (D0 * f[6] + D1 * f[7] + D2 * f[8]) / ell;
+  *w = (D0 * f[9] + D1 * f[10] + D2 * f[11]) / ell;
+}
+
+// outward normal and shape operator of triangle tri's local surface at P
+__host__ __device__ void mesh_normal_shape(const double* tri_fit, int tri, const double* P, double* n,
+                                           double S[3][3]) {
+  const double* f = tri_fit + (size_t)tri * TRI_FIT;
+  const double *t1 = f + 3, *t2 = f + 6, *nf = f + 9;
+  const double ell = f[12];
+  const double* c = f + 13;
+  double s, q, w, hs, hq, hh;
+  fit_local(f, P, &s, &q, &w);
+  fit_height(f, s, q, &hs, &hq, &hh);
+  double g[3];
+  for (int i = 0; i < 3; ++i) g[i] = (nf[i] - hs * t1[i] - hq * t2[i]) / ell;
+  const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+  for (int i = 0; i < 3; ++i) n[i] = g[i] / gn;
+  double H[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      H[i][j] = -(2.0 * c[3] * t1[i] * t1[j] + c[4] * (t1[i] * t2[j] + t2[i] * t1[j]) + 2.0 * c[5] * t2[i] * t2[j]) /
+                (ell * ell);
+  double Pm[3][3], Tm[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) Pm[i][j] = (i == j ? 1.0 : 0.0) - n[i] * n[j];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < 3; ++k) acc += Pm[i][k] * H[k][j];
+      Tm[i][j] = acc;
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < 3; ++k) acc += Tm[i][k] * Pm[k][j];
+      S[i][j] = acc / gn;
+    }
+}
+
+// per triangle: frame and height coefficients of its local surface
+__global__ void k_tri_fit(const double* X, const int32_t* T, int n_tri, const int32_t* patch_ids,
+                          const int32_t* patch_cnt, double* tri_fit, int* err) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tri) return;
+  const double* A = X + 3 * (size_t)T[3 * t];
+  const double* B = X + 3 * (size_t)T[3 * t + 1];
+  const double* C = X + 3 * (size_t)T[3 * t + 2];
+  double* f = tri_fit + (size_t)t * TRI_FIT;
+  double o[3], nf[3], t1[3], t2[3];
+  for (int i = 0; i < 3; ++i) o[i] = ((A[i] + B[i]) + C[i]) / 3.0;
+  const double u[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+  const double v[3] = {C[0] - A[0], C[1] - A[1], C[2] - A[2]};
+  nf[0] = u[1] * v[2] - u[2] * v[1];
+  nf[1] = u[2] * v[0] - u[0] * v[2];
+  nf[2] = u[0] * v[1] - u[1] * v[0];
+  const double ln = sqrt(nf[0] * nf[0] + nf[1] * nf[1] + nf[2] * nf[2]);
+  for (int i = 0; i < 3; ++i) nf[i] /= ln;
+  tangent_basis(nf, t1, t2);
+  const int K = patch_cnt[t];
+  double s[PATCH_MAX], q[PATCH_MAX], w[PATCH_MAX];
+  double ell = 0.0;
+  for (int k = 0; k < K; ++k) {
+    const double* P = X + 3 * (size_t)patch_ids[(size_t)t * PATCH_MAX + k];
+    const double D0 = P[0] - o[0], D1 = P[1] - o[1], D2 = P[2] - o[2];
+    ell = fmax(ell, sqrt(D0 * D0 + D1 * D1 + D2 * D2));
+    s[k] = D0 * t1[0] + D1 * t1[1] + D2 * t1[2];
+    q[k] = D0 * t2[0] + D1 * t2[1] + D2 * t2[2];
+    w[k] = D0 * nf[0] + D1 * nf[1] + D2 * nf[2];
+  }
+  double Gm[36], rhs[6];
+  for (int i = 0; i < 36; ++i) Gm[i] = 0.0;
+  for (int i = 0; i < 6; ++i) rhs[i] = 0.0;
+  for (int k = 0; k < K; ++k) {
+    const double sk = s[k] / ell, qk = q[k] / ell, wk = w[k] / ell;
+    const double r[6] = {1.0, sk, qk, sk * sk, sk * qk, qk * qk};
+    if (K == 6) {
+      for (int j = 0; j < 6; ++j) Gm[k * 6 + j] = r[j];
+      rhs[k] = wk;
+    } else {
+      for (int i = 0; i < 6; ++i) {
+        for (int j = 0; j < 6; ++j) Gm[i * 6 + j] += r[i] * r[j];
+        rhs[i] += r[i] * wk;
+      }
+    }
+  }
+  if (!gauss_solve(Gm, rhs, 6, 6)) atomicOr(err, DEVERR_SINGULAR);
+  for (int i = 0; i < 3; ++i) {
+    f[i] = o[i];
+    f[3 + i] = t1[i];
+    f[6 + i] = t2[i];
+    f[9 + i] = nf[i];
+  }
+  f[12] = ell;
+  for (int i = 0; i < 6; ++i) f[13 + i] = rhs[i];
+}
+
+// per crossing edge: its triangle (the line's single crossing in
+// (x_lo, x_hi], or the nearest within MESH_NEAR h) and the point where the
+// edge meets that triangle's local surface (Newton along the edge)
+struct MeshHits {
+  const int32_t* ptr[3];
+  const double* x[3];
+  const int32_t* tri[3];
+};
+
+__global__ void k_mesh_cross(GridParams gr, MeshHits mh, const double* tri_fit, const int32_t* c_lo,
+                             const int32_t* c_axis, int n, double* c_z, int8_t* c_comp, int32_t* c_tri, int* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int n1 = gr.N - 1;
+  const int64_t f = c_lo[i];
+  const int a = c_axis[i];
+  const int k[3] = {(int)(f % n1) + 1, (int)((f / n1) % n1) + 1, (int)(f / ((int64_t)n1 * n1)) + 1};
+  const int u = (a + 1) % 3, v = (a + 2) % 3;
+  const int line = (k[v] - 1) * n1 + (k[u] - 1);
+  const double xl = node_coord(gr, k[a]), xhi = node_coord(gr, k[a] + 1);
+  const int j0 = mh.ptr[a][line], j1 = mh.ptr[a][line + 1];
+  int cnt = 0, pick = -1, near = -1;
+  double best = 1e300;
+  for (int j = j0; j < j1; ++j) {
+    const double x = mh.x[a][j];
+    if (x > xl && x <= xhi) {
+      ++cnt;
+      pick = j;
+    }
+    const double d = fmax(xl - x, x - xhi);
+    if (d < best) {
+      best = d;
+      near = j;
+    }
+  }
+  if (cnt == 0 && near >= 0 && best <= MESH_NEAR * gr.h) pick = near;
+  c_comp[i] = 0;
+  if (cnt > 1 || pick < 0) {
+    atomicOr(err, DEVERR_GEOMETRY);
+    c_z[i] = 0.5 * (xl + xhi);
+    c_tri[i] = 0;
+    return;
+  }
+  const int t = mh.tri[a][pick];
+  c_tri[i] = t;
+  const double* fr = tri_fit + (size_t)t * TRI_FIT;
+  const double X0[3] = {node_coord(gr, k[0]), node_coord(gr, k[1]), node_coord(gr, k[2])};
+  double s0, q0, w0;
+  fit_local(fr, X0, &s0, &q0, &w0);
+  const double ell = fr[12];
+  const double ds = gr.h * fr[3 + a] / ell, dq = gr.h * fr[6 + a] / ell, dw = gr.h * fr[9 + a] / ell;
+  double tau = (mh.x[a][pick] - xl) / gr.h;
+  for (int it = 0; it < MESH_NEWTON; ++it) {
+    double hs, hq, hh;
+    const double s = s0 + tau * ds, q = q0 + tau * dq, w = w0 + tau * dw;
+    fit_height(fr, s, q, &hs, &hq, &hh);
+    const double fv = w - hh;
+    const double fp = dw - (hs * ds + hq * dq);
+    tau = tau - fv / fp;
+  }
+  c_z[i] = xl + tau * gr.h;
+}
 
 // Coefficients of the single layer's jump polynomial of one component with
 // diagonal conductivity D at the displacement xi from a surface point with
@@ -543,7 +843,8 @@ __host__ __device__ int crossing_row(const GeomParams& gp, const GridParams& gr,
   const double z = t.c_z[i];
   P[a] = z;
   double n[3], S[3][3];
-  normal_shape(gp, comp, P, n, S);
+  if (gp.kind == KFBI_MESH3) mesh_normal_shape(di.tri_fit, t.c_tri[i], P, n, S);
+  else normal_shape(gp, comp, P, n, S);
   // density row: psi(z) = sum w0 x[pid], grad_G psi(z) = sum wg[.] x[pid]
   int pid[PATCH_MAX];
   double w0[PATCH_MAX], wg[3][PATCH_MAX];
@@ -582,7 +883,7 @@ __host__ __device__ int crossing_row(const GeomParams& gp, const GridParams& gr,
       wg[2][q] = 0.0;
     }
   } else {
-    const int tri = locate_tri(gp, di.cube_t, comp, P);
+    const int tri = gp.kind == KFBI_MESH3 ? t.c_tri[i] : locate_tri(gp, di.cube_t, comp, P);
     K = di.patch_cnt[tri];
     int ids[PATCH_MAX];
     for (int q = 0; q < K; ++q) ids[q] = di.patch_ids[(size_t)tri * PATCH_MAX + q];
@@ -648,7 +949,8 @@ __host__ __device__ int node_stencil_row(const GeomParams& gp, const GridParams&
   for (int cc = 1; cc < gp.n_comp; ++cc)
     if (i >= gp.comp_vert_offset[cc]) comp = cc;
   double n[3], S[3][3];
-  normal_shape(gp, comp, q, n, S);
+  if (gp.kind == KFBI_MESH3) mesh_normal_shape(di.tri_fit, di.vtri[i], q, n, S);
+  else normal_shape(gp, comp, q, n, S);
   // stencil offsets in the oracle's order
   const int P = d == 2 ? 6 : 10;
   int off[10][3];
@@ -720,7 +1022,8 @@ __host__ __device__ int node_density_row(const GeomParams& gp, const GridParams&
   for (int cc = 1; cc < gp.n_comp; ++cc)
     if (i >= gp.comp_vert_offset[cc]) comp = cc;
   double n[3], S[3][3];
-  normal_shape(gp, comp, q, n, S);
+  if (gp.kind == KFBI_MESH3) mesh_normal_shape(di.tri_fit, di.vtri[i], q, n, S);
+  else normal_shape(gp, comp, q, n, S);
   for (int k = 0; k < 3; ++k) t.n_normal[(size_t)i * 3 + k] = n[k];
   const double Ai = AB[(size_t)i * 4];
   const double Bi[3] = {AB[(size_t)i * 4 + 1], AB[(size_t)i * 4 + 2], AB[(size_t)i * 4 + 3]};
@@ -1037,6 +1340,84 @@ int upload(kfbi_handle* h, T** dst, const T* src, size_t n) {
   return KFBI_OK;
 }
 
+// Mesh-only domain: every triangle's local surface, the ray crossings of
+// the grid lines along each axis sorted by (line, coordinate, triangle) into
+// per-line lists (the sort runs on the host), and the inside flags of the
+// interior nodes from the x-lines.
+int mesh_setup(kfbi_handle* h, const kfbi_geometry* geom, const double* X, const int32_t* T, const int32_t* ids,
+               const int32_t* cnt, double** tri_fit, MeshHits* mh) {
+  const GridParams gr = h->grid;
+  cudaStream_t st = h->stream;
+  const int nt = geom->n_tri, n1 = gr.N - 1, n_lines = n1 * n1;
+  int rc;
+  if ((rc = dalloc(h, tri_fit, (size_t)nt * TRI_FIT))) return rc;
+  k_tri_fit<<<(nt + 127) / 128, 128, 0, st>>>(X, T, nt, ids, cnt, *tri_fit, h->w.err);
+  KFBI_CHECK_LAUNCH();
+  int* counts = nullptr;
+  KFBI_CUDA(cudaMalloc((void**)&counts, sizeof(int) * 2 * (size_t)nt));
+  int* offs = counts + nt;
+  std::vector<int> hc(nt), ho(nt);
+  for (int a = 0; a < 3; ++a) {
+    k_mesh_hits<<<(nt + 127) / 128, 128, 0, st>>>(X, T, nt, gr, a, nullptr, counts, nullptr, nullptr, nullptr);
+    KFBI_CHECK_LAUNCH();
+    KFBI_CUDA(cudaMemcpyAsync(hc.data(), counts, sizeof(int) * (size_t)nt, cudaMemcpyDeviceToHost, st));
+    KFBI_CUDA(cudaStreamSynchronize(st));
+    int total = 0;
+    for (int t = 0; t < nt; ++t) {
+      ho[t] = total;
+      total += hc[t];
+    }
+    const size_t nb = (size_t)std::max(total, 1);
+    int32_t *line_d = nullptr, *tri_d = nullptr;
+    double* x_d = nullptr;
+    KFBI_CUDA(cudaMalloc((void**)&line_d, sizeof(int32_t) * nb));
+    KFBI_CUDA(cudaMalloc((void**)&tri_d, sizeof(int32_t) * nb));
+    KFBI_CUDA(cudaMalloc((void**)&x_d, sizeof(double) * nb));
+    KFBI_CUDA(cudaMemcpyAsync(offs, ho.data(), sizeof(int) * (size_t)nt, cudaMemcpyHostToDevice, st));
+    k_mesh_hits<<<(nt + 127) / 128, 128, 0, st>>>(X, T, nt, gr, a, offs, counts, line_d, x_d, tri_d);
+    std::vector<int32_t> hl((size_t)total), ht((size_t)total);
+    std::vector<double> hx((size_t)total);
+    KFBI_CUDA(cudaMemcpyAsync(hl.data(), line_d, sizeof(int32_t) * (size_t)total, cudaMemcpyDeviceToHost, st));
+    KFBI_CUDA(cudaMemcpyAsync(ht.data(), tri_d, sizeof(int32_t) * (size_t)total, cudaMemcpyDeviceToHost, st));
+    KFBI_CUDA(cudaMemcpyAsync(hx.data(), x_d, sizeof(double) * (size_t)total, cudaMemcpyDeviceToHost, st));
+    KFBI_CUDA(cudaStreamSynchronize(st));
+    cudaFree(line_d);
+    cudaFree(tri_d);
+    cudaFree(x_d);
+    KFBI_CHECK_LAUNCH();
+    std::vector<int> order((size_t)total);
+    for (int j = 0; j < total; ++j) order[j] = j;
+    std::sort(order.begin(), order.end(), [&](int p, int q) {
+      if (hl[p] != hl[q]) return hl[p] < hl[q];
+      if (hx[p] != hx[q]) return hx[p] < hx[q];
+      return ht[p] < ht[q];
+    });
+    std::vector<int32_t> ptr((size_t)n_lines + 1, 0), st_tri((size_t)nb, 0);
+    std::vector<double> st_x((size_t)nb, 0.0);
+    for (int j = 0; j < total; ++j) {
+      st_x[j] = hx[order[j]];
+      st_tri[j] = ht[order[j]];
+      ptr[hl[order[j]] + 1]++;
+    }
+    for (int l = 0; l < n_lines; ++l) ptr[l + 1] += ptr[l];
+    int32_t* ptr_d = nullptr;
+    int32_t* stri_d = nullptr;
+    double* sx_d = nullptr;
+    if ((rc = upload(h, &ptr_d, ptr.data(), ptr.size()))) break;
+    if ((rc = upload(h, &stri_d, st_tri.data(), st_tri.size()))) break;
+    if ((rc = upload(h, &sx_d, st_x.data(), st_x.size()))) break;
+    mh->ptr[a] = ptr_d;
+    mh->tri[a] = stri_d;
+    mh->x[a] = sx_d;
+    KFBI_CUDA(cudaStreamSynchronize(st));
+  }
+  cudaFree(counts);
+  if (rc) return rc;
+  k_mesh_classify<<<(n_lines + 127) / 128, 128, 0, st>>>(gr, mh->ptr[0], mh->x[0], h->t.inside);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
 }  // namespace
 
 // the CSR correction rows of t (new_pattern: also the pointers and indices;
@@ -1080,7 +1461,28 @@ int setup_build(kfbi_handle* h, const kfbi_geometry* geom) {
   int* err = h->w.err;
   KFBI_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
   if ((rc = dalloc(h, &t.inside, (size_t)total))) return rc;
-  k_classify<<<blocks_for(total, 256), 256, 0, st>>>(gp, gr, t.inside, total);
+  // interface nodes and (3-D) the point lists of every triangle's surface
+  // fit: the density fits, and the local surfaces of a mesh-only domain
+  t.M = geom->n_nodes;
+  double* nodes_d = nullptr;
+  if ((rc = upload(h, &nodes_d, geom->nodes, (size_t)t.M * d))) return rc;
+  int32_t *ids_d = nullptr, *cnt_d = nullptr, *vtri_d = nullptr, *tri_d = nullptr;
+  if (d == 3) {
+    std::vector<int32_t> ids, cnt, vtri;
+    if ((rc = host_patches(geom, ids, cnt, vtri))) return rc;
+    if ((rc = upload(h, &ids_d, ids.data(), ids.size()))) return rc;
+    if ((rc = upload(h, &cnt_d, cnt.data(), cnt.size()))) return rc;
+    if ((rc = upload(h, &vtri_d, vtri.data(), vtri.size()))) return rc;
+    if ((rc = upload(h, &tri_d, geom->tri, (size_t)geom->n_tri * 3))) return rc;
+  }
+  const bool mesh = gp.kind == KFBI_MESH3;
+  double* tri_fit = nullptr;
+  MeshHits mh{};
+  if (mesh) {
+    if ((rc = mesh_setup(h, geom, nodes_d, tri_d, ids_d, cnt_d, &tri_fit, &mh))) return rc;
+  } else {
+    k_classify<<<blocks_for(total, 256), 256, 0, st>>>(gp, gr, t.inside, total);
+  }
   uint8_t* flag = nullptr;
   KFBI_CUDA(cudaMalloc(&flag, (size_t)total));
   k_flags<<<blocks_for(total, 256), 256, 0, st>>>(gr, t.inside, total, 0, 0, flag, err);
@@ -1118,7 +1520,14 @@ int setup_build(kfbi_handle* h, const kfbi_geometry* geom) {
   if ((rc = upload(h, &axis_off, axis_off_h, 4))) return rc;
   if ((rc = dalloc(h, &t.c_z, (size_t)t.n_int))) return rc;
   if ((rc = dalloc(h, &t.c_comp, (size_t)t.n_int))) return rc;
-  if (t.n_int > 0) k_bisect<<<(t.n_int + 127) / 128, 128, 0, st>>>(gp, gr, t.c_lo, t.c_axis, t.n_int, t.c_z, t.c_comp, err);
+  if (mesh) {
+    if ((rc = dalloc(h, &t.c_tri, (size_t)std::max(t.n_int, 1)))) return rc;
+    if (t.n_int > 0)
+      k_mesh_cross<<<(t.n_int + 127) / 128, 128, 0, st>>>(gr, mh, tri_fit, t.c_lo, t.c_axis, t.n_int, t.c_z,
+                                                          t.c_comp, t.c_tri, err);
+  } else if (t.n_int > 0) {
+    k_bisect<<<(t.n_int + 127) / 128, 128, 0, st>>>(gp, gr, t.c_lo, t.c_axis, t.n_int, t.c_z, t.c_comp, err);
+  }
   KFBI_CHECK_LAUNCH();
 
   // the mask and the irregular list on the field layout
@@ -1145,27 +1554,19 @@ int setup_build(kfbi_handle* h, const kfbi_geometry* geom) {
   KFBI_CHECK_LAUNCH();
 
   // density inputs
-  t.M = geom->n_nodes;
   t.P = d == 2 ? 6 : 10;
   DensityInputs di{};
   di.M = t.M;
-  double* nodes_d = nullptr;
-  if ((rc = upload(h, &nodes_d, geom->nodes, (size_t)t.M * d))) return rc;
   di.nodes = nodes_d;
   t.nodes = nodes_d;
-  int32_t* vtri_d = nullptr;
   if (d == 3) {
-    std::vector<int32_t> ids, cnt, vtri;
-    if ((rc = host_patches(geom, ids, cnt, vtri))) return rc;
-    int32_t *ids_d = nullptr, *cnt_d = nullptr;
     double* ct_d = nullptr;
-    if ((rc = upload(h, &ids_d, ids.data(), ids.size()))) return rc;
-    if ((rc = upload(h, &cnt_d, cnt.data(), cnt.size()))) return rc;
-    if ((rc = upload(h, &vtri_d, vtri.data(), vtri.size()))) return rc;
-    if ((rc = upload(h, &ct_d, geom->cube_t, (size_t)geom->cube_n + 1))) return rc;
+    if (!mesh && (rc = upload(h, &ct_d, geom->cube_t, (size_t)geom->cube_n + 1))) return rc;
     di.patch_ids = ids_d;
     di.patch_cnt = cnt_d;
     di.cube_t = ct_d;
+    di.vtri = vtri_d;
+    di.tri_fit = tri_fit;
   } else {
     std::vector<double> gcol;
     host_spline_column(t.M, gcol);

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libkfbi.so")
 
 OK, ERR_ARG, ERR_GEOMETRY, ERR_NOT_CONVERGED, ERR_NAN, ERR_CUDA, ERR_OOM, ERR_NEWTON = range(8)
-ELLIPSE2, ELLIPSOID3, STAR3, SHELL3 = 1, 2, 3, 4
+ELLIPSE2, ELLIPSOID3, STAR3, SHELL3, MESH3 = 1, 2, 3, 4, 5
 FP64, MIXED, MIXED_LEARNED, FP32 = 0, 1, 2, 3
 GMRES, RICHARDSON = 0, 1
 WARM_PREVIOUS, WARM_PROJECTION = 0, 1
@@ -285,12 +285,14 @@ class KFBI:
         g.nodes = nodes.ctypes.data_as(C.POINTER(C.c_double))
         if g.dim == 3:
             tri = np.ascontiguousarray(geom.tri, dtype=np.int32)
-            ct = np.ascontiguousarray(geom.cube_t, dtype=np.float64)
-            self._keep += [tri, ct]
+            self._keep.append(tri)
             g.n_tri = tri.shape[0]
             g.tri = tri.ctypes.data_as(C.POINTER(C.c_int32))
-            g.cube_n = int(geom.cube_n)
-            g.cube_t = ct.ctypes.data_as(C.POINTER(C.c_double))
+            if geom.cube_t is not None:         # cube-sphere tables (not for bare meshes)
+                ct = np.ascontiguousarray(geom.cube_t, dtype=np.float64)
+                self._keep.append(ct)
+                g.cube_n = int(geom.cube_n)
+                g.cube_t = ct.ctypes.data_as(C.POINTER(C.c_double))
             g.n_comp = len(geom.components)
             for c, comp in enumerate(geom.components):
                 g.comp_map[c] = int(comp.map_type)
