@@ -747,6 +747,7 @@ static int create_impl(const kfbi_geometry* geom, const kfbi_grid* grid, double 
   h->grid.lo = grid->lo;
   h->grid.h = (grid->hi - grid->lo) / grid->N;
   h->grid.bc = grid->box;
+  h->rinv_ok = true;
   int rc;
   auto fail = [&](int code) {
     kfbi_destroy(h);

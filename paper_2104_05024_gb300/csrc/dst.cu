@@ -28,6 +28,7 @@
 
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "dst_reg.cuh"
@@ -468,7 +469,8 @@ __global__ void __launch_bounds__(NT) k_xinv(T* __restrict__ a, bool keep, doubl
 template <typename T, int N, bool SOLVE, int DIM>
 __global__ void __launch_bounds__(NT) k_strided(T* __restrict__ a, size_t row_stride, size_t plane_stride, int qoff,
                                                 const T* __restrict__ mu1, T lambda, T scale,
-                                                const T* __restrict__ tw_g, const int* __restrict__ skip) {
+                                                const T* __restrict__ tw_g, const int* __restrict__ skip,
+                                                const T* __restrict__ rinv = nullptr) {
   using C = Cfg<T, N>;
   constexpr int W = C::W, RS = C::RS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -501,10 +503,14 @@ __global__ void __launch_bounds__(NT) k_strided(T* __restrict__ a, size_t row_st
   } else {
     dst1_tile<C>(s, tw, tot);
     if (SOLVE) {
+      // the mode factor scale / mu_p from the table built for this lambda
+      // (same expression, so the same value), else divided here
+      const T* rq = rinv != nullptr ? rinv + (size_t)q * N * N : nullptr;
       for (int idx = threadIdx.x; idx < N * W; idx += NT) {
         const int c = idx % W, k = idx / W, p = x0 + c;
         T v = (T)0;
-        if (k > 0 && p > 0) v = s[k * RS + c] * (scale / (mu1[k] + mu1[p] + muq - lambda));
+        if (k > 0 && p > 0)
+          v = s[k * RS + c] * (rq != nullptr ? rq[(size_t)k * N + p] : (scale / (mu1[k] + mu1[p] + muq - lambda)));
         s[k * RS + c] = v;
       }
       __syncthreads();
@@ -886,7 +892,8 @@ int prep(K kernel, size_t smem) {
 // one strided 3-D pass (mode 0: along y, mode 1: along z); float32 grids of
 // 32 <= N <= 256 go through the TMA-fed persistent kernel
 template <typename T, int N>
-int launch_strided3(kfbi_handle* h, int mode, bool solve, T* work, const T* mu1, T lam, T scale, const T* tw) {
+int launch_strided3(kfbi_handle* h, int mode, bool solve, T* work, const T* mu1, T lam, T scale, const T* tw,
+                    const T* rinv = nullptr) {
   using C = Cfg<T, N>;
   cudaStream_t st = h->stream;
   int rc;
@@ -916,13 +923,56 @@ int launch_strided3(kfbi_handle* h, int mode, bool solve, T* work, const T* mu1,
   if (solve) {
     if ((rc = prep(k_strided<T, N, true, 3>, smem))) return rc;
     k_strided<T, N, true, 3><<<grid, NT, smem, st>>>(work, mode == 0 ? N : NN, mode == 0 ? NN : N, 1, mu1, lam,
-                                                     scale, tw, h->skip);
+                                                     scale, tw, h->skip, rinv);
   } else {
     if ((rc = prep(k_strided<T, N, false, 3>, smem))) return rc;
     k_strided<T, N, false, 3><<<grid, NT, smem, st>>>(work, mode == 0 ? N : NN, mode == 0 ? NN : N, 1, mu1, lam,
                                                       scale, tw, h->skip);
   }
   return KFBI_OK;
+}
+
+// scale / mu_p over the mode grid (q, k, p) of the float64 middle pass,
+// mu_p = (mu1[k] + mu1[p]) + mu1[q] (3-D) - lambda, in the pass's own order;
+// n modes per axis, mode 0 absent (sine modes) or present (cosine modes)
+__global__ void k_rinv(const double* __restrict__ mu1, double lambda, double scale, int n, int dim, bool mode0,
+                       double* __restrict__ out, int64_t total) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(i % n), k = (int)((i / n) % n), q = (int)(i / ((int64_t)n * n));
+    const double muq = dim == 3 ? mu1[q] : 0.0;
+    const bool on = mode0 || (k > 0 && p > 0 && (dim == 2 || q > 0));
+    out[i] = on ? scale / (mu1[k] + mu1[p] + muq - lambda) : 0.0;
+  }
+}
+
+// the float64 solve's mode factors for this lambda: built once per lambda
+// in a table of N^dim values that the handle owns (none for float32, nor for
+// handles that must not allocate)
+template <typename T, int N>
+const T* mode_factors(kfbi_handle* h, double lambda, double scale) {
+  if constexpr (sizeof(T) != 8) {
+    return nullptr;
+  } else {
+    if (!h->rinv_ok) return nullptr;
+    const bool cosine = h->grid.bc == KFBI_BOX_NEUMANN;
+    const int n = cosine ? N + 1 : N;
+    const int64_t total = h->grid.dim == 3 ? (int64_t)n * n * n : (int64_t)n * n;
+    if (h->rinv64 == nullptr) {
+      if (dalloc(h, &h->rinv64, (size_t)total) != KFBI_OK) {
+        cudaGetLastError();
+        h->rinv_ok = false;
+        return nullptr;
+      }
+      h->rinv_lambda = std::nan("");
+    }
+    if (!(h->rinv_lambda == lambda)) {
+      const int nb = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+      k_rinv<<<nb, 256, 0, h->stream>>>(h->t.mu, lambda, scale, n, h->grid.dim, cosine, h->rinv64, total);
+      KFBI_COUNT(1);
+      h->rinv_lambda = lambda;
+    }
+    return h->rinv64;
+  }
 }
 
 template <typename T, int N>
@@ -962,22 +1012,24 @@ int run_solve(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1, const 
         h->xy_fused = false;
       }
     }
+    const T* rinv = mode_factors<T, N>(h, sa.lambda, (double)scale);
     if ((rc = prep(k_xfwd<T, N, 3>, smem))) return rc;
     k_xfwd<T, N, 3><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.src32, sa.corr, t.irr, t.line_start, tw,
                                              h->skip);
     if ((rc = launch_strided3<T, N>(h, 0, false, work, mu1, lam, scale, tw))) return rc;
-    if ((rc = launch_strided3<T, N>(h, 1, true, work, mu1, lam, scale, tw))) return rc;
+    if ((rc = launch_strided3<T, N>(h, 1, true, work, mu1, lam, scale, tw, rinv))) return rc;
     if ((rc = launch_strided3<T, N>(h, 0, false, work, mu1, lam, scale, tw))) return rc;
     if ((rc = prep(k_xinv<T, N, 3>, smem))) return rc;
     k_xinv<T, N, 3><<<grid, NT, smem, st>>>(work, sa.keep || sa.out_user == nullptr, sa.out_user, sa.aux, sa.beta,
                                              sa.gamma, tw, h->skip);
   } else {
     dim3 grid(N / W, 1);
+    const T* rinv = mode_factors<T, N>(h, sa.lambda, (double)scale);
     if ((rc = prep(k_xfwd<T, N, 2>, smem))) return rc;
     k_xfwd<T, N, 2><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.src32, sa.corr, t.irr, t.line_start, tw,
                                              h->skip);
     if ((rc = prep(k_strided<T, N, true, 2>, smem))) return rc;
-    k_strided<T, N, true, 2><<<grid, NT, smem, st>>>(work, N, 0, 0, mu1, lam, scale, tw, h->skip);
+    k_strided<T, N, true, 2><<<grid, NT, smem, st>>>(work, N, 0, 0, mu1, lam, scale, tw, h->skip, rinv);
     if ((rc = prep(k_xinv<T, N, 2>, smem))) return rc;
     k_xinv<T, N, 2><<<grid, NT, smem, st>>>(work, sa.keep || sa.out_user == nullptr, sa.out_user, sa.aux, sa.beta,
                                              sa.gamma, tw, h->skip);
@@ -1007,7 +1059,8 @@ int run_pass(kfbi_handle* h, int pass, double lambda, T* work, const T* mu1, con
     } else if (pass == 1) {
       if ((rc = launch_strided3<T, N>(h, 0, false, work, mu1, lam, scale, tw))) return rc;
     } else if (pass == 2) {
-      if ((rc = launch_strided3<T, N>(h, 1, true, work, mu1, lam, scale, tw))) return rc;
+      const T* rinv = mode_factors<T, N>(h, lambda, (double)scale);
+      if ((rc = launch_strided3<T, N>(h, 1, true, work, mu1, lam, scale, tw, rinv))) return rc;
     } else if (pass == 3) {
       if ((rc = prep(k_xinv<T, N, 3>, smem))) return rc;
       k_xinv<T, N, 3><<<grid, NT, smem, st>>>(work, true, nullptr, nullptr, 1.0, 0.0, tw, nullptr);
@@ -1044,8 +1097,9 @@ int run_pass(kfbi_handle* h, int pass, double lambda, T* work, const T* mu1, con
       if ((rc = prep(k_xfwd<T, N, 2>, smem))) return rc;
       k_xfwd<T, N, 2><<<grid, NT, smem, st>>>(work, nullptr, 1.0, nullptr, nullptr, t.irr, t.line_start, tw, nullptr);
     } else if (pass == 1 || pass == 2) {
+      const T* rinv = mode_factors<T, N>(h, lambda, (double)scale);
       if ((rc = prep(k_strided<T, N, true, 2>, smem))) return rc;
-      k_strided<T, N, true, 2><<<grid, NT, smem, st>>>(work, N, 0, 0, mu1, lam, scale, tw, nullptr);
+      k_strided<T, N, true, 2><<<grid, NT, smem, st>>>(work, N, 0, 0, mu1, lam, scale, tw, nullptr, rinv);
     } else {
       if ((rc = prep(k_xinv<T, N, 2>, smem))) return rc;
       k_xinv<T, N, 2><<<grid, NT, smem, st>>>(work, true, nullptr, nullptr, 1.0, 0.0, tw, nullptr);
@@ -1405,7 +1459,8 @@ __global__ void __launch_bounds__(NT) k_nxinv(T* __restrict__ a, bool keep, doub
 template <typename T, int N, bool SOLVE, int DIM>
 __global__ void __launch_bounds__(NT) k_nstrided(T* __restrict__ a, size_t row_stride, size_t plane_stride,
                                                  const T* __restrict__ mu1, T lambda, T scale,
-                                                 const T* __restrict__ tw_g, const int* __restrict__ skip) {
+                                                 const T* __restrict__ tw_g, const int* __restrict__ skip,
+                                                 const T* __restrict__ rinv = nullptr) {
   using C = Cfg<T, N>;
   constexpr int W = C::W, RS = C::RS, P = N + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1429,9 +1484,11 @@ __global__ void __launch_bounds__(NT) k_nstrided(T* __restrict__ a, size_t row_s
   dct1_tile<C>(s, tw, tot, x1);
   if (SOLVE) {
     const T muq = DIM == 3 ? mu1[q] : (T)0;
+    const T* rq = rinv != nullptr ? rinv + (size_t)q * P * P : nullptr;
     for (int idx = threadIdx.x; idx < P * W; idx += NT) {
       const int c = idx % W, k = idx / W, p = x0 + c;
-      if (p <= N) s[k * RS + c] *= scale / (mu1[k] + mu1[p] + muq - lambda);
+      if (p <= N)
+        s[k * RS + c] *= rq != nullptr ? rq[(size_t)k * P + p] : scale / (mu1[k] + mu1[p] + muq - lambda);
     }
     __syncthreads();
     dct1_tile<C>(s, tw, tot, x1);
@@ -1454,6 +1511,7 @@ int run_solve_neumann(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1
   const T lam = (T)sa.lambda;
   const dim3 grid((P + W - 1) / W, dim == 3 ? P : 1);
   const size_t PP = (size_t)P * P;
+  const T* rinv = mode_factors<T, N>(h, sa.lambda, (double)scale);
   int rc;
   if (dim == 3) {
     if ((rc = prep(k_nxfwd<T, N, 3>, smem))) return rc;
@@ -1462,7 +1520,7 @@ int run_solve_neumann(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1
     if ((rc = prep(k_nxinv<T, N, 3>, smem))) return rc;
     k_nxfwd<T, N, 3><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.corr, t.irr, t.line_start, tw, h->skip);
     k_nstrided<T, N, false, 3><<<grid, NT, smem, st>>>(work, P, PP, mu1, lam, scale, tw, h->skip);
-    k_nstrided<T, N, true, 3><<<grid, NT, smem, st>>>(work, PP, P, mu1, lam, scale, tw, h->skip);
+    k_nstrided<T, N, true, 3><<<grid, NT, smem, st>>>(work, PP, P, mu1, lam, scale, tw, h->skip, rinv);
     k_nstrided<T, N, false, 3><<<grid, NT, smem, st>>>(work, P, PP, mu1, lam, scale, tw, h->skip);
     k_nxinv<T, N, 3><<<grid, NT, smem, st>>>(work, sa.keep || sa.out_user == nullptr, sa.out_user, sa.aux, sa.beta,
                                               sa.gamma, tw, h->skip);
@@ -1472,7 +1530,7 @@ int run_solve_neumann(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1
     if ((rc = prep(k_nstrided<T, N, true, 2>, smem))) return rc;
     if ((rc = prep(k_nxinv<T, N, 2>, smem))) return rc;
     k_nxfwd<T, N, 2><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.corr, t.irr, t.line_start, tw, h->skip);
-    k_nstrided<T, N, true, 2><<<grid, NT, smem, st>>>(work, P, 0, mu1, lam, scale, tw, h->skip);
+    k_nstrided<T, N, true, 2><<<grid, NT, smem, st>>>(work, P, 0, mu1, lam, scale, tw, h->skip, rinv);
     k_nxinv<T, N, 2><<<grid, NT, smem, st>>>(work, sa.keep || sa.out_user == nullptr, sa.out_user, sa.aux, sa.beta,
                                               sa.gamma, tw, h->skip);
     KFBI_CHECK_LAUNCH_N(3);

@@ -221,6 +221,11 @@ struct kfbi_handle {
   CUtensorMap tmap_y32, tmap_z32;
   bool tma = false;
   bool xy_fused = false;          // float32 3-D solves use the cluster-fused x-y passes
+  // float64 solves: the mode factors scale / mu_p for the lambda they were
+  // built for (rinv_ok: the handle may allocate the table; set at creation)
+  double* rinv64 = nullptr;
+  double rinv_lambda = 0.0;
+  bool rinv_ok = false;
   // device flag handed to the launches of a Krylov iteration enqueued ahead
   // of the host's convergence test (nullptr otherwise)
   const int* skip = nullptr;
