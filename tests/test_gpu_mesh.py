@@ -141,3 +141,47 @@ def test_mesh_strang_steps(prec, bar):
     h.close()
     assert all(s["rel_res"] <= cfg.tol for s in st)
     assert rel(Vd.cpu().numpy(), V) < bar and rel(wd.cpu().numpy(), w) < bar
+
+
+def test_mesh_in_the_neumann_box():
+    """The mesh-only setup and the Neumann box combine: operators and the
+    manufactured solve on the field layout of all (N+1)^3 nodes."""
+    geom, grid = G.bean_mesh(8), C.Grid(3, 32, bc="neumann")
+    o, g = OK(geom, grid), K.KFBI(geom, grid, tol=1e-12)
+    psi = _density(geom)
+    lim = torch.empty(geom.M, dtype=torch.float64, device=DEV)
+    g.apply_A(cuda(psi), lim, 40.0)
+    assert rel(lim.cpu().numpy(), o.apply_A(psi, 40.0)) < TOL64
+    f, u_ex, gN = C.manufactured(geom, grid, 40.0)
+    u_ref, psi_ref, info = o.solve_neumann(f, gN, 40.0, tol=1e-12)
+    u = torch.empty(grid.shape, dtype=torch.float64, device=DEV)
+    p = torch.zeros(geom.M, dtype=torch.float64, device=DEV)
+    st = g.solve_neumann(cuda(f), cuda(gN), u, p, 40.0, tol=1e-12)
+    g.close()
+    assert abs(st["iters"] - info["iters"]) <= 1
+    assert rel(u.cpu().numpy(), u_ref) < TOL64 and rel(p.cpu().numpy(), psi_ref) < TOL64
+
+
+def test_mesh_coupled_system():
+    """The anisotropic coupled system on a mesh-only domain: A psi of the
+    density pair and the coupled solve against the coupled oracle."""
+    from oracle import coupled as CP
+    DI, DE = (3.0, 0.5, 0.5), (2.0, 1.0, 1.0)
+    geom, grid = G.bean_mesh(8), C.Grid(3, 32)
+    o = CP.CoupledKFBI(geom, grid, DI, DE)
+    g = K.KFBI(geom, grid, D_i=DI, D_e=DE, tol=1e-12)
+    X = geom.nodes
+    psi = np.concatenate([1.0 + 0.5 * X[:, 0] - 0.3 * X[:, 1] ** 2, 0.4 - 0.2 * X[:, 1] + 0.3 * X[:, 2]])
+    out = torch.empty(2 * geom.M, dtype=torch.float64, device=DEV)
+    g.apply_A_coupled(cuda(psi), out, 40.0)
+    assert rel(out.cpu().numpy(), o.apply_A(psi, 40.0)) < TOL64
+    Xg = grid.coords()
+    V = np.exp(-((Xg[0] - 0.45) ** 2 + Xg[1] ** 2 + Xg[2] ** 2) / 0.05) * np.ones(grid.shape)
+    z = np.zeros(geom.M)
+    ui_o, ue_o, psi_o, info = o.solve_neumann(-40.0 * V, 40.0 * V, z, z, 40.0, tol=1e-12)
+    ui, ue = (torch.empty(grid.shape, dtype=torch.float64, device=DEV) for _ in range(2))
+    pd = torch.zeros(2 * geom.M, dtype=torch.float64, device=DEV)
+    st = g.solve_coupled(cuda(-40.0 * V), cuda(40.0 * V), cuda(z), cuda(z), ui, ue, pd, 40.0, tol=1e-12)
+    g.close()
+    assert abs(st["iters"] - info["iters"]) <= 1
+    assert rel(ui.cpu().numpy(), ui_o) < TOL64 and rel(ue.cpu().numpy(), ue_o) < TOL64
