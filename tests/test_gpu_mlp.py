@@ -12,7 +12,8 @@
   previous-density start (the paper's), the history projection and the
   learned correction of the projection.  The learned start needs fewer
   iterations than the previous density; against the projection it does not
-  gain (the measured ratio is printed and bounded, see the design notes).
+  gain: a point-wise network cannot represent the non-local correction the
+  projection leaves (the measured ratio is printed and bounded).
 """
 import numpy as np
 import pytest
