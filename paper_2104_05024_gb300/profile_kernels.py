@@ -1,13 +1,17 @@
 """Launch the hot-path kernels of one workload a few times each, for ncu.
 
     python -m paper_2104_05024_gb300.profile_kernels [--N 256] [--precision fp64|mixed] [--reps 3] [--passes-only]
+        [--box neumann] [--mesh]
 
 Sets up the prolate-shell workload (configs 2/3 geometry), then runs each
 transform pass of the box solver, one irregular-node correction and one
 interface-limit gather `reps` times on the library's stream, and with
 --strang one Strang step of the bidomain model (reactions, refinement
-residuals, GMRES).  No timing is reported: this only gives a profiler a
-short, representative launch list.
+residuals, GMRES).  --box neumann runs `reps` float64 box solves of the
+Neumann box (all (N+1)^3 nodes) instead; --mesh hands the shell over as a
+bare triangle mesh, so the handle's creation runs the mesh setup kernels.
+No timing is reported: this only gives a profiler a short, representative
+launch list.
 """
 from __future__ import annotations
 
@@ -32,12 +36,25 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--strang", action="store_true")
     ap.add_argument("--passes-only", action="store_true", help="only the four transform passes (no A psi)")
+    ap.add_argument("--box", default="dirichlet", choices=["dirichlet", "neumann"])
+    ap.add_argument("--mesh", action="store_true", help="the shell as a bare triangle mesh")
     a = ap.parse_args()
     prec = K.FP64 if a.precision == "fp64" else K.MIXED
-    geom, grid, cfg, V0, w0 = C.config2(N=a.N)
+    geom, grid, cfg, V0, w0 = C.config2(N=a.N, bc=a.box)
+    if a.mesh:
+        from kfbi_workloads import geometry as G
+        geom = G.as_mesh(geom)
     h = K.KFBI(geom, grid, tol=cfg.tol)
     lam = h.info["lambda"]
     dev = torch.device("cuda:0")
+    if a.box == "neumann":
+        r = torch.ones(grid.shape, dtype=torch.float64, device=dev)
+        v = torch.empty_like(r)
+        for _ in range(a.reps):
+            h.box_solve(r, v, lam, precision=K.FP64)
+        torch.cuda.synchronize()
+        print("ok")
+        return
     psi = torch.ones(geom.M, dtype=torch.float64, device=dev)
     out = torch.empty(geom.M, dtype=torch.float64, device=dev)
     for _ in range(a.reps):
