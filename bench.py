@@ -692,9 +692,10 @@ def run_coupled(args):
     tensors D_i = diag(30, 5, 5), D_e = diag(20, 10, 10) in the sphere of
     Example 3 (radius 0.9: the paper leaves it unstated and observes up to
     x = 0.875) at N^3, FitzHugh-Nagumo of the workloads with the stimulus ball
-    at (0.8, 0, 0), dt 0.05, float64, GMRES to 1e-8: Strang steps/s and
-    iterations per step, and the coupled box solve (two fields, per-mode 2 x 2
-    solve) against the scalar float64 one."""
+    at (0.8, 0, 0), dt 0.05, GMRES to 1e-8: Strang steps/s and iterations per
+    step in float64 and with float32 transforms (GMRES-IR), and the coupled
+    box solve (two fields, per-mode 2 x 2 solve) against the scalar float64
+    one."""
     import torch
 
     import paper_2104_05024_gb300.kfbi as K
@@ -702,31 +703,39 @@ def run_coupled(args):
     dev = torch.device("cuda", 0)
     N = args.N
     geom, grid = G.sphere3(0.9, C.surface_res(N)), C.Grid(3, N)
-    cfg = C.StrangConfig(sigma_i=1.0, sigma_e=2.0, dt=0.05, steps=args.steps, tol=1e-8)
     V0 = C.ball_stimulus(grid, (0.8, 0.0, 0.0), 0.1)
-    w0 = np.zeros_like(V0)
     Di, De = (30.0, 5.0, 5.0), (20.0, 10.0, 10.0)
-    h = K.KFBI(geom, grid, D_i=Di, D_e=De, dt=cfg.dt, tol=cfg.tol, restart=50, max_iter=600)
-    V, w = torch.tensor(V0, device=dev), torch.tensor(w0, device=dev)
-    ue = torch.empty_like(V)
-    h.bidomain_step(C.FHN_CONFIG, V, w, None, nsteps=2)
-    ms, st = _event_ms(lambda: h.bidomain_step(C.FHN_CONFIG, V, w, ue, nsteps=args.steps))
-    r = torch.randn(grid.shape, dtype=torch.float64, device=dev)
-    vi, ve = torch.empty_like(r), torch.empty_like(r)
-    h.box_solve_coupled(r, r, vi, ve, 40.0)
-    box_ms, _ = _event_ms(lambda: h.box_solve_coupled(r, r, vi, ve, 40.0), reps=5)
-    h.close()
-    hs = K.KFBI(geom, grid, tol=cfg.tol)
+    forms, fields = {}, {}
+    for name, prec in (("fp64", K.FP64), ("mixed", K.MIXED)):
+        h = K.KFBI(geom, grid, D_i=Di, D_e=De, dt=0.05, tol=1e-8, restart=50, max_iter=600, precision=prec)
+        V = torch.tensor(V0, device=dev)
+        w = torch.zeros_like(V)
+        ue = torch.empty_like(V)
+        h.bidomain_step(C.FHN_CONFIG, V, w, None, nsteps=2)
+        ms, st = _event_ms(lambda: h.bidomain_step(C.FHN_CONFIG, V, w, ue, nsteps=args.steps))
+        forms[name] = {"steps_per_s": round(1000.0 * args.steps / ms, 3),
+                       "iters_per_step": float(np.mean([s["iters"] for s in st])),
+                       "outer_per_step": float(np.mean([s["outer"] for s in st])),
+                       "true_rel_res_max": float(max(s["true_rel_res"] for s in st)),
+                       "V_max": float(V.abs().max()), "ue_max": float(ue.abs().max())}
+        fields[name] = (V, ue)
+        if name == "fp64":
+            r = torch.randn(grid.shape, dtype=torch.float64, device=dev)
+            vi, ve = torch.empty_like(r), torch.empty_like(r)
+            h.box_solve_coupled(r, r, vi, ve, 40.0)
+            box_ms, _ = _event_ms(lambda: h.box_solve_coupled(r, r, vi, ve, 40.0), reps=5)
+        h.close()
+    forms["mixed"]["speedup_vs_fp64"] = round(forms["mixed"]["steps_per_s"] / forms["fp64"]["steps_per_s"], 2)
+    diff = {"V": float((fields["mixed"][0] - fields["fp64"][0]).abs().max()),
+            "ue": float((fields["mixed"][1] - fields["fp64"][1]).abs().max())}
+    hs = K.KFBI(geom, grid, tol=1e-8)
     hs.box_solve(r, vi, 60.0, precision=K.FP64)
     box1_ms, _ = _event_ms(lambda: hs.box_solve(r, vi, 60.0, precision=K.FP64), reps=5)
     hs.close()
-    print(json.dumps({"metric": "anisotropic coupled Strang steps/s (float64)",
-                      "workload": f"sphere r 0.9 at {N}^3, D_i diag(30, 5, 5), D_e diag(20, 10, 10), FHN of the workloads, "
-                                  f"dt 0.05, tol 1e-8, {args.steps} steps after 2",
-                      "unit": "steps/s", "steps_per_s": round(1000.0 * args.steps / ms, 3),
-                      "iters_per_step": float(np.mean([s["iters"] for s in st])),
-                      "true_rel_res_max": float(max(s["true_rel_res"] for s in st)),
-                      "V_max": float(V.abs().max()), "ue_max": float(ue.abs().max()),
+    print(json.dumps({"metric": "anisotropic coupled Strang steps/s (float64 and float32 transforms with refinement)",
+                      "workload": f"sphere r 0.9 at {N}^3, D_i diag(30, 5, 5), D_e diag(20, 10, 10), FHN of the "
+                                  f"workloads, dt 0.05, tol 1e-8, {args.steps} steps after 2",
+                      "unit": "steps/s", "forms": forms, "max_abs_diff_mixed_vs_fp64": diff,
                       "coupled_box_solve_ms": round(box_ms, 3), "scalar_box_solve_ms": round(box1_ms, 3)}),
           flush=True)
 

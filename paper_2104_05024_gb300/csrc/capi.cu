@@ -156,9 +156,119 @@ int assemble_coupled(kfbi_handle* h, double kappa, const double* src_i, double a
   return launch_rank_one_coupled(h, psi, r, -1.0);
 }
 
+// the coupled A psi with float32 transforms (the inner operator of GMRES-IR;
+// the 2 x 2 mode solve and the limits stay float64)
+int apply_A_coupled32(kfbi_handle* h, double kappa, const double* psi, double* out, double sgn,
+                      const double* base) {
+  const int M = h->t.M;
+  const double *xi, *xe;
+  int rc;
+  if ((rc = density_vector_buf(h, psi, h->w.xvec, &xi))) return rc;
+  if ((rc = density_vector_buf(h, psi + M, h->w.xvec2, &xe))) return rc;
+  if ((rc = launch_correction_t(h, h->t, xi, h->w.corr))) return rc;
+  if ((rc = launch_correction_t(h, h->t2, xe, h->w.corr2))) return rc;
+  SolveArgs si, se;
+  si.corr = h->w.corr;
+  se.corr = h->w.corr2;
+  Coupling cp = h->cpl;
+  cp.kappa = kappa;
+  if ((rc = box_solve_coupled32(h, si, se, cp, h->w.grid32, h->w.grid32b))) return rc;
+  if ((rc = launch_limit32_t(h, h->t, h->w.grid32, xi, base, sgn, out))) return rc;
+  if ((rc = launch_limit32_t(h, h->t2, h->w.grid32b, xe, base ? base + M : nullptr, sgn, out + M))) return rc;
+  return launch_rank_one_coupled(h, psi, out, sgn);
+}
+
+// float64-accurate coupled box solve from float32 transforms: (u_i, u_e) =
+// L_h^{-1}(a_i src_i + corr_i, a_e src_e + corr_e) on the user layout, then
+// rounds of the float64 coupled residual, each solved in float32 and added
+int refine_rounds(const kfbi_handle* h);
+int refined_solve_coupled(kfbi_handle* h, double kappa, const double* src_i, double a_i, const double* src_e,
+                          double a_e, const double* corr_i, const double* corr_e, double* ui, double* ue) {
+  Coupling cp = h->cpl;
+  cp.kappa = kappa;
+  SolveArgs si, se;
+  si.src = src_i;
+  si.alpha = a_i;
+  si.corr = corr_i;
+  si.out_user = ui;
+  si.keep = false;
+  se.src = src_e;
+  se.alpha = a_e;
+  se.corr = corr_e;
+  se.out_user = ue;
+  se.keep = false;
+  int rc = box_solve_coupled32(h, si, se, cp, h->w.grid32, h->w.grid32b);
+  if (rc) return rc;
+  const int rounds = refine_rounds(h);
+  for (int r = 0; r < rounds; ++r) {
+    if ((rc = launch_residual_coupled(h, src_i, a_i, src_e, a_e, corr_i, corr_e, ui, ue, kappa, h->w.res64,
+                                      h->w.res64b)))
+      return rc;
+    SolveArgs ri, re;
+    ri.src = h->w.res64;
+    ri.out_user = ui;
+    ri.aux = ui;
+    ri.gamma = 1.0;
+    ri.keep = false;
+    re.src = h->w.res64b;
+    re.out_user = ue;
+    re.aux = ue;
+    re.gamma = 1.0;
+    re.keep = false;
+    if ((rc = box_solve_coupled32(h, ri, re, cp, h->w.grid32, h->w.grid32b))) return rc;
+  }
+  return KFBI_OK;
+}
+
+// coupled out = base + sgn * A psi with the refined solve (v_B of both
+// components left in u64, u64b)
+int apply_A_acc_coupled(kfbi_handle* h, double kappa, const double* psi, double* out, double sgn,
+                        const double* base) {
+  const int M = h->t.M;
+  const double *xi, *xe;
+  int rc;
+  if ((rc = density_vector_buf(h, psi, h->w.xvec, &xi))) return rc;
+  if ((rc = density_vector_buf(h, psi + M, h->w.xvec2, &xe))) return rc;
+  if ((rc = launch_correction_t(h, h->t, xi, h->w.corr))) return rc;
+  if ((rc = launch_correction_t(h, h->t2, xe, h->w.corr2))) return rc;
+  if ((rc = refined_solve_coupled(h, kappa, nullptr, 1.0, nullptr, 1.0, h->w.corr, h->w.corr2, h->w.u64, h->w.u64b)))
+    return rc;
+  if ((rc = launch_limit_user_t(h, h->t, h->w.u64, xi, base, sgn, out))) return rc;
+  if ((rc = launch_limit_user_t(h, h->t2, h->w.u64b, xe, base ? base + M : nullptr, sgn, out + M))) return rc;
+  return launch_rank_one_coupled(h, psi, out, sgn);
+}
+
+// coupled g with the refined volume solve (v_V of both components kept in
+// vV64, vV64b)
+int rhs_g_acc_coupled(kfbi_handle* h, double kappa, const double* src_i, double a_i, const double* src_e, double a_e,
+                      const double* gNi, const double* gNe, double* g) {
+  const int M = h->t.M;
+  int rc = refined_solve_coupled(h, kappa, src_i, a_i, src_e, a_e, nullptr, nullptr, h->w.vV64, h->w.vV64b);
+  if (rc) return rc;
+  if ((rc = launch_limit_user_t(h, h->t, h->w.vV64, nullptr, gNi, -1.0, g))) return rc;
+  return launch_limit_user_t(h, h->t2, h->w.vV64b, nullptr, gNe, -1.0, g + M);
+}
+
+// true residual r = g^N - n.D grad u^+ - rank-one term of the coupled
+// u = v_V + v_B(psi) left by the refined solves (vV64 + u64, vV64b + u64b)
+int true_residual_coupled_acc(kfbi_handle* h, const double* psi, const double* gNi, const double* gNe, double* r) {
+  const int M = h->t.M;
+  const double *xi, *xe;
+  int rc;
+  if ((rc = density_vector_buf(h, psi, h->w.xvec, &xi))) return rc;
+  if ((rc = density_vector_buf(h, psi + M, h->w.xvec2, &xe))) return rc;
+  if ((rc = launch_limit_user_t(h, h->t, h->w.vV64, nullptr, gNi, -1.0, r))) return rc;
+  if ((rc = launch_limit_user_t(h, h->t, h->w.u64, xi, r, -1.0, r))) return rc;
+  if ((rc = launch_limit_user_t(h, h->t2, h->w.vV64b, nullptr, gNe, -1.0, r + M))) return rc;
+  if ((rc = launch_limit_user_t(h, h->t2, h->w.u64b, xe, r + M, -1.0, r + M))) return rc;
+  return launch_rank_one_coupled(h, psi, r, -1.0);
+}
+
 // out = base + sgn * A psi    (A psi = dv_B^+/dn of the single layer)
 int apply_A(kfbi_handle* h, int prec, double lambda, const double* psi, double* out, double sgn, const double* base) {
-  if (h->coupled) return apply_A_coupled(h, lambda, psi, out, sgn, base);
+  if (h->coupled)
+    return prec == KFBI_FP64 ? apply_A_coupled(h, lambda, psi, out, sgn, base)
+                             : apply_A_coupled32(h, lambda, psi, out, sgn, base);
   const double* x;
   int rc = density_vector(h, psi, &x);
   if (rc) return rc;
@@ -256,6 +366,7 @@ int refined_solve(kfbi_handle* h, const double* src, double alpha, const double*
 
 // out = base + sgn * A psi with a float64-accurate (refined) box solve
 int apply_A_acc(kfbi_handle* h, double lambda, const double* psi, double* out, double sgn, const double* base) {
+  if (h->coupled) return apply_A_acc_coupled(h, lambda, psi, out, sgn, base);
   const double* x;
   int rc = density_vector(h, psi, &x);
   if (rc) return rc;
@@ -661,8 +772,8 @@ int kfbi_create_coupled(const kfbi_geometry* geom, const kfbi_grid* grid, const 
       set_error("conductivities must be positive");
       return KFBI_ERR_ARG;
     }
-  if (opts && opts->precision != KFBI_FP64) {
-    set_error("the coupled system is solved in float64 (KFBI_FP64)");
+  if (opts && opts->precision != KFBI_FP64 && opts->precision != KFBI_MIXED) {
+    set_error("the coupled system is solved in float64 (KFBI_FP64) or with float32 transforms (KFBI_MIXED)");
     return KFBI_ERR_ARG;
   }
   if (grid->box != KFBI_BOX_DIRICHLET) {
@@ -787,10 +898,14 @@ static int create_impl(const kfbi_geometry* geom, const kfbi_grid* grid, double 
     if ((rc = dalloc(h, &h->w.corr2, (size_t)h->t.n_irr))) return fail(rc);
     if ((rc = dalloc(h, &h->w.xvec2, (size_t)2 * h->t.M))) return fail(rc);
     if ((rc = dalloc(h, &h->w.grid64b, (size_t)P))) return fail(rc);
-    if (cudaMemsetAsync(h->w.grid64b, 0, sizeof(double) * (size_t)P, h->stream) != cudaSuccess) {
+    if ((rc = dalloc(h, &h->w.grid32b, (size_t)P))) return fail(rc);
+    if (cudaMemsetAsync(h->w.grid64b, 0, sizeof(double) * (size_t)P, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->w.grid32b, 0, sizeof(float) * (size_t)P, h->stream) != cudaSuccess) {
       set_error("cudaMemset failed");
       return fail(KFBI_ERR_CUDA);
     }
+    for (double** p : {&h->w.u64b, &h->w.vV64b, &h->w.res64b})
+      if ((rc = dalloc(h, p, (size_t)grid_points(h)))) return fail(rc);
   }
   if ((rc = dalloc(h, &h->w.vecs, (size_t)(m + 1) * M))) return fail(rc);
   if ((rc = dalloc(h, &h->w.small, (size_t)small_size(MAX_RESTART)))) return fail(rc);
@@ -1248,10 +1363,11 @@ static int bidomain_impl(kfbi_handle* h, const kfbi_fhn* p, const double* istim,
 // the last solve's Phi_e (the midpoint level) with zero mean over Omega.
 static int bidomain_coupled_impl(kfbi_handle* h, const kfbi_fhn* p, const double* istim, double* V_dev,
                                  double* w_dev, double* ue_dev, int nsteps, kfbi_stats* per_step) {
-  if (h->opts.precision != KFBI_FP64 || h->opts.solver != KFBI_GMRES) {
-    set_error("the coupled system is solved in float64 with GMRES");
+  if ((h->opts.precision != KFBI_FP64 && h->opts.precision != KFBI_MIXED) || h->opts.solver != KFBI_GMRES) {
+    set_error("the coupled system is solved with GMRES, in float64 or with float32 transforms");
     return KFBI_ERR_ARG;
   }
+  const int prec = h->opts.precision;
   const int64_t n = grid_points(h);
   const int M = h->t.M, nk = h->nk;
   const double kap = p->Cm * p->beta / (0.5 * h->dt);
@@ -1298,23 +1414,32 @@ static int bidomain_coupled_impl(kfbi_handle* h, const kfbi_fhn* p, const double
       src_e = h->w.fsrc;
       a_e = 1.0;
     }
-    if ((rc = rhs_g_coupled(h, kap, V_dev, -kap, src_e, a_e, h->w.zeroM, h->w.zeroM, h->w.g))) return rc;
+    rc = prec == KFBI_FP64 ? rhs_g_coupled(h, kap, V_dev, -kap, src_e, a_e, h->w.zeroM, h->w.zeroM, h->w.g)
+                           : rhs_g_acc_coupled(h, kap, V_dev, -kap, src_e, a_e, h->w.zeroM, h->w.zeroM, h->w.g);
+    if (rc) return rc;
     if ((rc = mark(s, 2))) return rc;
     if ((rc = vec_copy(h, h->w.psi_save, h->w.psi_prev, nk))) return rc;
     if ((rc = vec_copy(h, h->w.psi_learn, h->w.psi_prev, nk))) return rc;
     h->proj_valid = false;
     if ((rc = mark(s, 3))) return rc;
-    const int src = solve_bie(h, KFBI_FP64, kap, h->w.g, h->w.psi_prev, &st);
+    const int src = solve_bie(h, prec, kap, h->w.g, h->w.psi_prev, &st);
     if (src != KFBI_OK && src != KFBI_ERR_NOT_CONVERGED) return src;
     if (src == KFBI_ERR_NOT_CONVERGED) final_rc = src;
     if ((rc = vec_copy(h, h->w.psi_prev2, h->w.psi_save, nk))) return rc;
     if ((rc = vec_copy(h, h->w.g_prev, h->w.g, nk))) return rc;
     ++h->n_hist;
     if ((rc = mark(s, 4))) return rc;
-    if ((rc = assemble_coupled(h, kap, V_dev, -kap, src_e, a_e, h->w.psi_prev, h->w.zeroM, h->w.zeroM, phi_i, phi_e,
-                               h->w.tmp)))
-      return rc;
-    if ((rc = launch_midpoint_diff(h, V_dev, phi_i, phi_e, n))) return rc;
+    if (prec == KFBI_FP64) {
+      if ((rc = assemble_coupled(h, kap, V_dev, -kap, src_e, a_e, h->w.psi_prev, h->w.zeroM, h->w.zeroM, phi_i,
+                                 phi_e, h->w.tmp)))
+        return rc;
+      if ((rc = launch_midpoint_diff(h, V_dev, phi_i, phi_e, n))) return rc;
+    } else {
+      // GMRES-IR's last act was the refined residual at the final density:
+      // v_B of both components in u64, u64b, v_V in vV64, vV64b
+      if ((rc = launch_midpoint4(h, V_dev, h->w.vV64, h->w.u64, h->w.vV64b, h->w.u64b, n))) return rc;
+      if ((rc = true_residual_coupled_acc(h, h->w.psi_prev, h->w.zeroM, h->w.zeroM, h->w.tmp))) return rc;
+    }
     if ((rc = vec_dots(h, h->w.tmp, 1, nk, h->w.tmp, h->w.step_sq + 2 * s))) return rc;
     if ((rc = vec_dots(h, h->w.g, 1, nk, h->w.g, h->w.step_sq + 2 * s + 1))) return rc;
     if ((rc = mark(s, 5))) return rc;
@@ -1322,7 +1447,14 @@ static int bidomain_coupled_impl(kfbi_handle* h, const kfbi_fhn* p, const double
     if ((rc = mark(s, 6))) return rc;
     st.ms = elapsed_ms(t0);
   }
-  if (ue_dev && (rc = launch_sub_mean(h, phi_e, ue_dev))) return rc;
+  if (ue_dev && prec != KFBI_FP64 && nsteps > 0) {
+    // Phi_e = v_V + v_B of the extracellular component (the last solve)
+    KFBI_CUDA(cudaMemcpyAsync(ue_dev, h->w.vV64b, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, h->stream));
+    if ((rc = launch_lincomb(h, ue_dev, 1.0, h->w.u64b, 1.0, n))) return rc;
+    if ((rc = launch_sub_mean(h, ue_dev, ue_dev))) return rc;
+  } else if (ue_dev && (rc = launch_sub_mean(h, phi_e, ue_dev))) {
+    return rc;
+  }
   int herr = 0;
   std::vector<double> sq((size_t)2 * nsteps + 1);
   KFBI_CUDA(cudaMemcpyAsync(&herr, h->w.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -1377,12 +1509,25 @@ int kfbi_solve_coupled(kfbi_handle* h, double kappa, const double* fi_dev, const
   kfbi_stats st{};
   auto t0 = std::chrono::steady_clock::now();
   int rc;
-  if ((rc = rhs_g_coupled(h, kappa, fi_dev, 1.0, fe_dev, 1.0, gNi_dev, gNe_dev, h->w.g))) return rc;
-  const int solve_rc = solve_bie(h, KFBI_FP64, kappa, h->w.g, psi_dev, &st);
+  const int prec = h->opts.precision == KFBI_FP64 ? KFBI_FP64 : KFBI_MIXED;
+  rc = prec == KFBI_FP64 ? rhs_g_coupled(h, kappa, fi_dev, 1.0, fe_dev, 1.0, gNi_dev, gNe_dev, h->w.g)
+                         : rhs_g_acc_coupled(h, kappa, fi_dev, 1.0, fe_dev, 1.0, gNi_dev, gNe_dev, h->w.g);
+  if (rc) return rc;
+  const int solve_rc = solve_bie(h, prec, kappa, h->w.g, psi_dev, &st);
   if (solve_rc != KFBI_OK && solve_rc != KFBI_ERR_NOT_CONVERGED) return solve_rc;
-  if ((rc = assemble_coupled(h, kappa, fi_dev, 1.0, fe_dev, 1.0, psi_dev, gNi_dev, gNe_dev, phi_i_dev, phi_e_dev,
-                             h->w.r)))
-    return rc;
+  if (prec == KFBI_FP64) {
+    if ((rc = assemble_coupled(h, kappa, fi_dev, 1.0, fe_dev, 1.0, psi_dev, gNi_dev, gNe_dev, phi_i_dev, phi_e_dev,
+                               h->w.r)))
+      return rc;
+  } else {
+    // (Phi_i, Phi_e) = v_V + v_B from the refined solves GMRES-IR left
+    const int64_t n = grid_points(h);
+    KFBI_CUDA(cudaMemcpyAsync(phi_i_dev, h->w.vV64, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, h->stream));
+    KFBI_CUDA(cudaMemcpyAsync(phi_e_dev, h->w.vV64b, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, h->stream));
+    if ((rc = launch_lincomb(h, phi_i_dev, 1.0, h->w.u64, 1.0, n))) return rc;
+    if ((rc = launch_lincomb(h, phi_e_dev, 1.0, h->w.u64b, 1.0, n))) return rc;
+    if ((rc = true_residual_coupled_acc(h, psi_dev, gNi_dev, gNe_dev, h->w.r))) return rc;
+  }
   double rn, gn;
   double* slot = h->w.small + small_nrm2(h->opts.restart);
   if ((rc = norm2(h, h->w.r, slot, &rn))) return rc;

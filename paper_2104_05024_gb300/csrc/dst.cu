@@ -1111,32 +1111,34 @@ int run_pass(kfbi_handle* h, int pass, double lambda, T* work, const T* mu1, con
 
 // ------------------------------------------ coupled anisotropic solve pass
 // Middle pass of the coupled box solve (3-D: along z, 2-D: along y) on the
-// two padded float64 work grids a (intracellular) and b (extracellular):
-// forward DST of both tiles, the per-mode 2 x 2 solve of Eq. pde1 with
-// diagonal conductivities (Section 5.2, Eq. FDE),
+// two padded work grids a (intracellular) and b (extracellular): forward
+// DST of both tiles, the per-mode 2 x 2 solve of Eq. pde1 with diagonal
+// conductivities (Section 5.2, Eq. FDE),
 //   [A_i - kappa, kappa; kappa, A_e - kappa] (v_i, v_e) = (r_i, r_e),
 //   A_c = sum_a d_c,a mu1(p_a),
-// scaled by (2/N)^d, then the inverse DST of both tiles.
-template <int N, int DIM>
-__global__ void __launch_bounds__(NT) k_strided_coupled(double* __restrict__ a, double* __restrict__ b,
-                                                        size_t row_stride, size_t plane_stride, int qoff,
-                                                        const double* __restrict__ mu1, Coupling cp,
-                                                        const double* __restrict__ tw_g,
+// scaled by (2/N)^d, then the inverse DST of both tiles.  The mode sums and
+// the 2 x 2 solve are float64 for both element types.
+template <typename T, int N, int DIM>
+__global__ void __launch_bounds__(NT) k_strided_coupled(T* __restrict__ a, T* __restrict__ b, size_t row_stride,
+                                                        size_t plane_stride, int qoff, const double* __restrict__ mu1,
+                                                        Coupling cp, const T* __restrict__ tw_g,
                                                         const int* __restrict__ skip) {
-  using C = Cfg<double, N>;
+  using C = Cfg<T, N>;
   constexpr int W = C::W, RS = C::RS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* sa = reinterpret_cast<double*>(smem_raw);
-  double* sb = sa + N * RS;
-  double* tot = sb + N * RS;
-  double* tw = tot + C::G * W;
+  T* sa = reinterpret_cast<T*>(smem_raw);
+  T* sb = sa + N * RS;
+  T* tot = sb + N * RS;
+  T* tw = tot + C::G * W;
+  T* sinv = tw + 4 * N;
   const bool skipped = skip != nullptr && *skip != 0;
-  load_twiddles<double, N>(tw, tw_g);
+  load_twiddles<T, N>(tw, tw_g);
+  load_sines<T, N>(sinv, tw_g);
   if (skipped) return;
   const int x0 = blockIdx.x * W;
   const int q = blockIdx.y + qoff;
-  double* ba = a + (size_t)q * plane_stride + x0;
-  double* bb = b + (size_t)q * plane_stride + x0;
+  T* ba = a + (size_t)q * plane_stride + x0;
+  T* bb = b + (size_t)q * plane_stride + x0;
   for (int idx = threadIdx.x; idx < N * W; idx += NT) {
     const int c = idx % W, k = idx / W;
     copy_async(&sa[k * RS + c], &ba[(size_t)k * row_stride + c]);
@@ -1144,8 +1146,8 @@ __global__ void __launch_bounds__(NT) k_strided_coupled(double* __restrict__ a, 
   }
   copy_async_wait();
   __syncthreads();
-  dst1_tile<C>(sa, tw, tot);
-  dst1_tile<C>(sb, tw, tot);
+  dst_tile<C>(sa, tw, sinv, tot);
+  dst_tile<C>(sb, tw, sinv, tot);
   const double muq = DIM == 3 ? mu1[q] : 0.0;
   const double kap = cp.kappa;
   for (int idx = threadIdx.x; idx < N * W; idx += NT) {
@@ -1157,16 +1159,16 @@ __global__ void __launch_bounds__(NT) k_strided_coupled(double* __restrict__ a, 
       const double ai = cp.di[0] * mx + cp.di[1] * my + cp.di[2] * mz - kap;
       const double ae = cp.de[0] * mx + cp.de[1] * my + cp.de[2] * mz - kap;
       const double sc = cp.scale / (ai * ae - kap * kap);
-      const double ri = sa[k * RS + c], re = sb[k * RS + c];
+      const double ri = (double)sa[k * RS + c], re = (double)sb[k * RS + c];
       vi = (ae * ri - kap * re) * sc;
       ve = (ai * re - kap * ri) * sc;
     }
-    sa[k * RS + c] = vi;
-    sb[k * RS + c] = ve;
+    sa[k * RS + c] = (T)vi;
+    sb[k * RS + c] = (T)ve;
   }
   __syncthreads();
-  dst1_tile<C>(sa, tw, tot);
-  dst1_tile<C>(sb, tw, tot);
+  dst_tile<C>(sa, tw, sinv, tot);
+  dst_tile<C>(sb, tw, sinv, tot);
   for (int idx = threadIdx.x; idx < N * W; idx += NT) {
     const int c = idx % W, k = idx / W;
     ba[(size_t)k * row_stride + c] = sa[k * RS + c];
@@ -1174,52 +1176,53 @@ __global__ void __launch_bounds__(NT) k_strided_coupled(double* __restrict__ a, 
   }
 }
 
-template <int N>
-int run_solve_coupled(kfbi_handle* h, const SolveArgs& si, const SolveArgs& se, const Coupling& cp0, double* wa,
-                      double* wb) {
-  using C = Cfg<double, N>;
+// the coupled box solve on two padded grids of element type T: x forward
+// (sources and corrections), y, the coupled z solve, y, x inverse (outputs).
+// The y passes of both fields use the plain strided kernel (the tensor maps
+// describe only the handle's first float grid).
+template <typename T, int N>
+int run_solve_coupled(kfbi_handle* h, const SolveArgs& si, const SolveArgs& se, const Coupling& cp0, T* wa, T* wb,
+                      const T* mu1T, const T* tw) {
+  using C = Cfg<T, N>;
   constexpr int W = C::W;
-  const size_t smem = C::smem_elems * sizeof(double);
-  const size_t smem2 = (2 * (size_t)N * C::RS + (size_t)C::G * W + 4 * (size_t)N) * sizeof(double);
+  const size_t smem = C::smem_elems * sizeof(T);
+  const size_t smem2 = (2 * (size_t)N * C::RS + (size_t)C::G * W + 5 * (size_t)N) * sizeof(T);
   const int dim = h->grid.dim;
   cudaStream_t st = h->stream;
   const Tables& t = h->t;
   const double* mu1 = t.mu;
-  const double* tw = t.tw64;
   Coupling cp = cp0;
   cp.scale = dim == 3 ? (2.0 / N) * (2.0 / N) * (2.0 / N) : (2.0 / N) * (2.0 / N);
   int rc;
   const dim3 grid(N / W, dim == 3 ? N - 1 : 1);
   if (dim == 3) {
-    if ((rc = prep(k_xfwd<double, N, 3>, smem))) return rc;
-    if ((rc = prep(k_strided_coupled<N, 3>, smem2))) return rc;
-    if ((rc = prep(k_xinv<double, N, 3>, smem))) return rc;
-    k_xfwd<double, N, 3><<<grid, NT, smem, st>>>(wa, si.src, si.alpha, nullptr, si.corr, t.irr, t.line_start, tw, h->skip);
-    k_xfwd<double, N, 3><<<grid, NT, smem, st>>>(wb, se.src, se.alpha, nullptr, se.corr, t.irr, t.line_start, tw, h->skip);
-    for (double* w : {wa, wb})
-      if ((rc = launch_strided3<double, N>(h, 0, false, w, mu1, 0.0, 1.0, tw))) return rc;
+    if ((rc = prep(k_xfwd<T, N, 3>, smem))) return rc;
+    if ((rc = prep(k_strided_coupled<T, N, 3>, smem2))) return rc;
+    if ((rc = prep(k_xinv<T, N, 3>, smem))) return rc;
+    if ((rc = prep(k_strided<T, N, false, 3>, smem))) return rc;
+    k_xfwd<T, N, 3><<<grid, NT, smem, st>>>(wa, si.src, si.alpha, nullptr, si.corr, t.irr, t.line_start, tw, h->skip);
+    k_xfwd<T, N, 3><<<grid, NT, smem, st>>>(wb, se.src, se.alpha, nullptr, se.corr, t.irr, t.line_start, tw, h->skip);
     const size_t NN = (size_t)N * N;
-    k_strided_coupled<N, 3><<<grid, NT, smem2, st>>>(wa, wb, NN, N, 1, mu1, cp, tw, h->skip);
-    for (double* w : {wa, wb})
-      if ((rc = launch_strided3<double, N>(h, 0, false, w, mu1, 0.0, 1.0, tw))) return rc;
+    for (T* w : {wa, wb})
+      k_strided<T, N, false, 3><<<grid, NT, smem, st>>>(w, N, NN, 1, mu1T, (T)0, (T)1, tw, h->skip);
+    k_strided_coupled<T, N, 3><<<grid, NT, smem2, st>>>(wa, wb, NN, N, 1, mu1, cp, tw, h->skip);
+    for (T* w : {wa, wb})
+      k_strided<T, N, false, 3><<<grid, NT, smem, st>>>(w, N, NN, 1, mu1T, (T)0, (T)1, tw, h->skip);
+    k_xinv<T, N, 3><<<grid, NT, smem, st>>>(wa, si.keep || si.out_user == nullptr, si.out_user, si.aux, si.beta,
+                                             si.gamma, tw, h->skip);
+    k_xinv<T, N, 3><<<grid, NT, smem, st>>>(wb, se.keep || se.out_user == nullptr, se.out_user, se.aux, se.beta,
+                                             se.gamma, tw, h->skip);
   } else {
-    if ((rc = prep(k_xfwd<double, N, 2>, smem))) return rc;
-    if ((rc = prep(k_strided_coupled<N, 2>, smem2))) return rc;
-    if ((rc = prep(k_xinv<double, N, 2>, smem))) return rc;
-    k_xfwd<double, N, 2><<<grid, NT, smem, st>>>(wa, si.src, si.alpha, nullptr, si.corr, t.irr, t.line_start, tw, h->skip);
-    k_xfwd<double, N, 2><<<grid, NT, smem, st>>>(wb, se.src, se.alpha, nullptr, se.corr, t.irr, t.line_start, tw, h->skip);
-    k_strided_coupled<N, 2><<<grid, NT, smem2, st>>>(wa, wb, N, 0, 0, mu1, cp, tw, h->skip);
-  }
-  if (dim == 3) {
-    k_xinv<double, N, 3><<<grid, NT, smem, st>>>(wa, si.keep || si.out_user == nullptr, si.out_user, si.aux, si.beta,
-                                                  si.gamma, tw, h->skip);
-    k_xinv<double, N, 3><<<grid, NT, smem, st>>>(wb, se.keep || se.out_user == nullptr, se.out_user, se.aux, se.beta,
-                                                  se.gamma, tw, h->skip);
-  } else {
-    k_xinv<double, N, 2><<<grid, NT, smem, st>>>(wa, si.keep || si.out_user == nullptr, si.out_user, si.aux, si.beta,
-                                                  si.gamma, tw, h->skip);
-    k_xinv<double, N, 2><<<grid, NT, smem, st>>>(wb, se.keep || se.out_user == nullptr, se.out_user, se.aux, se.beta,
-                                                  se.gamma, tw, h->skip);
+    if ((rc = prep(k_xfwd<T, N, 2>, smem))) return rc;
+    if ((rc = prep(k_strided_coupled<T, N, 2>, smem2))) return rc;
+    if ((rc = prep(k_xinv<T, N, 2>, smem))) return rc;
+    k_xfwd<T, N, 2><<<grid, NT, smem, st>>>(wa, si.src, si.alpha, nullptr, si.corr, t.irr, t.line_start, tw, h->skip);
+    k_xfwd<T, N, 2><<<grid, NT, smem, st>>>(wb, se.src, se.alpha, nullptr, se.corr, t.irr, t.line_start, tw, h->skip);
+    k_strided_coupled<T, N, 2><<<grid, NT, smem2, st>>>(wa, wb, N, 0, 0, mu1, cp, tw, h->skip);
+    k_xinv<T, N, 2><<<grid, NT, smem, st>>>(wa, si.keep || si.out_user == nullptr, si.out_user, si.aux, si.beta,
+                                             si.gamma, tw, h->skip);
+    k_xinv<T, N, 2><<<grid, NT, smem, st>>>(wb, se.keep || se.out_user == nullptr, se.out_user, se.aux, se.beta,
+                                             se.gamma, tw, h->skip);
   }
   KFBI_CHECK_LAUNCH_N(dim == 3 ? 9 : 5);
   return KFBI_OK;
@@ -1623,20 +1626,33 @@ int box_solve32(kfbi_handle* h, const SolveArgs& a, float* work) {
   return dispatch<float>(h, a, work, h->t.mu32, h->t.tw32);
 }
 
-int box_solve_coupled64(kfbi_handle* h, const SolveArgs& si, const SolveArgs& se, const Coupling& cp, double* wa,
-                        double* wb) {
+namespace {
+template <typename T>
+int dispatch_coupled(kfbi_handle* h, const SolveArgs& si, const SolveArgs& se, const Coupling& cp, T* wa, T* wb,
+                     const T* mu1T, const T* tw) {
   switch (h->grid.N) {
-    case 16: return run_solve_coupled<16>(h, si, se, cp, wa, wb);
-    case 32: return run_solve_coupled<32>(h, si, se, cp, wa, wb);
-    case 64: return run_solve_coupled<64>(h, si, se, cp, wa, wb);
-    case 128: return run_solve_coupled<128>(h, si, se, cp, wa, wb);
-    case 256: return run_solve_coupled<256>(h, si, se, cp, wa, wb);
-    case 384: return run_solve_coupled<384>(h, si, se, cp, wa, wb);
-    case 512: return run_solve_coupled<512>(h, si, se, cp, wa, wb);
+    case 16: return run_solve_coupled<T, 16>(h, si, se, cp, wa, wb, mu1T, tw);
+    case 32: return run_solve_coupled<T, 32>(h, si, se, cp, wa, wb, mu1T, tw);
+    case 64: return run_solve_coupled<T, 64>(h, si, se, cp, wa, wb, mu1T, tw);
+    case 128: return run_solve_coupled<T, 128>(h, si, se, cp, wa, wb, mu1T, tw);
+    case 256: return run_solve_coupled<T, 256>(h, si, se, cp, wa, wb, mu1T, tw);
+    case 384: return run_solve_coupled<T, 384>(h, si, se, cp, wa, wb, mu1T, tw);
+    case 512: return run_solve_coupled<T, 512>(h, si, se, cp, wa, wb, mu1T, tw);
     default:
       set_error("unsupported grid size N=%d for the coupled solve", h->grid.N);
       return KFBI_ERR_ARG;
   }
+}
+}  // namespace
+
+int box_solve_coupled64(kfbi_handle* h, const SolveArgs& si, const SolveArgs& se, const Coupling& cp, double* wa,
+                        double* wb) {
+  return dispatch_coupled<double>(h, si, se, cp, wa, wb, h->t.mu, h->t.tw64);
+}
+
+int box_solve_coupled32(kfbi_handle* h, const SolveArgs& si, const SolveArgs& se, const Coupling& cp, float* wa,
+                        float* wb) {
+  return dispatch_coupled<float>(h, si, se, cp, wa, wb, h->t.mu32, h->t.tw32);
 }
 
 namespace {

@@ -189,6 +189,12 @@ struct Workspace {
   double* corr2 = nullptr;
   double* xvec2 = nullptr;
   double* ds2 = nullptr;
+  // coupled float32 forms: the second float grid and the extracellular
+  // counterparts of u64 / vV64 / res64
+  float* grid32b = nullptr;
+  double* u64b = nullptr;
+  double* vV64b = nullptr;
+  double* res64b = nullptr;
   int restart_cap = 0;
 };
 
@@ -279,6 +285,9 @@ int box_solve64(kfbi_handle* h, const SolveArgs& a, double* work);
 int box_solve_coupled64(kfbi_handle* h, const SolveArgs& si, const SolveArgs& se, const Coupling& cp, double* wa,
                         double* wb);
 int box_solve32(kfbi_handle* h, const SolveArgs& a, float* work);
+// the same with float32 transforms (the 2 x 2 mode solve stays float64)
+int box_solve_coupled32(kfbi_handle* h, const SolveArgs& si, const SolveArgs& se, const Coupling& cp, float* wa,
+                        float* wb);
 int dst_supported(int N);
 int transform_pass(kfbi_handle* h, int precision, int pass, double lambda);
 int make_tma_maps(kfbi_handle* h);
@@ -292,6 +301,15 @@ int launch_limit64_t(kfbi_handle* h, const Tables& t, const double* grid, const 
 int launch_limit_user_t(kfbi_handle* h, const Tables& t, const double* u, const double* x, const double* base,
                         double sgn, double* out);
 int launch_rank_one_coupled(kfbi_handle* h, const double* psi, double* out, double sgn);
+int launch_limit32_t(kfbi_handle* h, const Tables& t, const float* grid, const double* x, const double* base,
+                     double sgn, double* out);
+// float64 residual of the coupled system (both components) plus corrections
+int launch_residual_coupled(kfbi_handle* h, const double* src_i, double a_i, const double* src_e, double a_e,
+                            const double* corr_i, const double* corr_e, const double* ui, const double* ue,
+                            double kappa, double* ri, double* re);
+// V <- 2 ((a + b) - (c + d)) - V
+int launch_midpoint4(kfbi_handle* h, double* V, const double* a, const double* b, const double* c, const double* d,
+                     int64_t n);
 // V <- 2 (a - b) - V
 int launch_midpoint_diff(kfbi_handle* h, double* V, const double* a, const double* b, int64_t n);
 // dst = src - mean over Omega of src

@@ -781,6 +781,13 @@ int launch_limit64_t(kfbi_handle* h, const Tables& t, const double* grid, const 
   return KFBI_OK;
 }
 
+int launch_limit32_t(kfbi_handle* h, const Tables& t, const float* grid, const double* x, const double* base,
+                     double sgn, double* out) {
+  k_limit<float><<<(t.M + 127) / 128, 128, 0, h->stream>>>(t, h->grid, grid, x, base, sgn, out, h->skip);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
 int launch_limit32(kfbi_handle* h, const float* grid, const double* x, const double* base, double sgn, double* out) {
   k_limit<float><<<(h->t.M + 127) / 128, 128, 0, h->stream>>>(h->t, h->grid, grid, x, base, sgn, out, h->skip);
   KFBI_CHECK_LAUNCH();
@@ -863,6 +870,78 @@ int launch_rank_one_coupled(kfbi_handle* h, const double* psi, double* out, doub
   int rc = vec_dots(h, h->w.ds2, 1, n, psi, slot);
   if (rc) return rc;
   k_add_scalar<<<(n + 255) / 256, 256, 0, h->stream>>>(out, slot, sgn / h->t.area, n);
+  KFBI_CHECK_LAUNCH();
+  return KFBI_OK;
+}
+
+// Float64 residual of the coupled 5/7-point system on the user layout (zero
+// Dirichlet data), both components at once (Section 5.2, Eq. FDE):
+//   r_i = a_i src_i - (sum_a d_i,a (u_i(+e_a) - 2 u_i + u_i(-e_a)) / h^2 - kappa (u_i - u_e)),
+//   r_e = a_e src_e - (sum_a d_e,a (...) / h^2 + kappa (u_i - u_e));
+// the corrections are added by a scatter afterwards.  One block row per
+// (y, z) grid line.
+__global__ void k_residual_coupled(GridParams gr, Coupling cp, const double* __restrict__ src_i, double a_i,
+                                   const double* __restrict__ src_e, double a_e, const double* __restrict__ ui,
+                                   const double* __restrict__ ue, double* __restrict__ ri, double* __restrict__ re) {
+  const int n1 = gr.N - 1;
+  const double ih2 = 1.0 / (gr.h * gr.h);
+  const int y = blockIdx.x, z = blockIdx.y;
+  const int64_t s = (int64_t)n1 * n1;
+  const int64_t base = (int64_t)z * s + (int64_t)y * n1;
+  const double* u[2] = {ui, ue};
+  const double* dd[2] = {cp.di, cp.de};
+  for (int x = threadIdx.x; x < n1; x += blockDim.x) {
+    const int64_t f = base + x;
+    double Lc[2];
+    for (int c = 0; c < 2; ++c) {
+      const double* v = u[c];
+      const double vc = v[f];
+      double acc = dd[c][0] * ((x > 0 ? v[f - 1] : 0.0) + (x < n1 - 1 ? v[f + 1] : 0.0) - 2.0 * vc);
+      acc += dd[c][1] * ((y > 0 ? v[f - n1] : 0.0) + (y < n1 - 1 ? v[f + n1] : 0.0) - 2.0 * vc);
+      if (gr.dim == 3) acc += dd[c][2] * ((z > 0 ? v[f - s] : 0.0) + (z < n1 - 1 ? v[f + s] : 0.0) - 2.0 * vc);
+      Lc[c] = acc * ih2;
+    }
+    const double w = cp.kappa * (ui[f] - ue[f]);
+    ri[f] = (src_i != nullptr ? a_i * src_i[f] : 0.0) - (Lc[0] - w);
+    re[f] = (src_e != nullptr ? a_e * src_e[f] : 0.0) - (Lc[1] + w);
+  }
+}
+
+int launch_residual_coupled(kfbi_handle* h, const double* src_i, double a_i, const double* src_e, double a_e,
+                            const double* corr_i, const double* corr_e, const double* ui, const double* ue,
+                            double kappa, double* ri, double* re) {
+  const int n1 = h->grid.N - 1;
+  Coupling cp = h->cpl;
+  cp.kappa = kappa;
+  k_residual_coupled<<<dim3(n1, h->grid.dim == 3 ? n1 : 1), 256, 0, h->stream>>>(h->grid, cp, src_i, a_i, src_e, a_e,
+                                                                                  ui, ue, ri, re);
+  int n = 1;
+  if (h->t.n_irr > 0) {
+    if (corr_i) {
+      k_scatter_add<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->t, corr_i, ri);
+      ++n;
+    }
+    if (corr_e) {
+      k_scatter_add<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->t, corr_e, re);
+      ++n;
+    }
+  }
+  KFBI_CHECK_LAUNCH_N(n);
+  return KFBI_OK;
+}
+
+// V <- 2 ((a + b) - (c + d)) - V: the midpoint of the coupled float32 forms
+// from both parts of each potential (v_V of the refined volume solve, v_B of
+// the last refined residual)
+__global__ void k_midpoint4(double* __restrict__ V, const double* __restrict__ a, const double* __restrict__ b,
+                            const double* __restrict__ c, const double* __restrict__ d, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    V[i] = 2.0 * ((a[i] + b[i]) - (c[i] + d[i])) - V[i];
+}
+
+int launch_midpoint4(kfbi_handle* h, double* V, const double* a, const double* b, const double* c, const double* d,
+                     int64_t n) {
+  k_midpoint4<<<grid_blocks(n, 256), 256, 0, h->stream>>>(V, a, b, c, d, n);
   KFBI_CHECK_LAUNCH();
   return KFBI_OK;
 }

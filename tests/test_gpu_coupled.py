@@ -43,6 +43,7 @@ CASES = {
     "ellipse128": lambda: (G.ellipse_config0(256), C.Grid(2, 128)),
     "star32": lambda: (G.star_config1(C.surface_res(32)), C.Grid(3, 32)),
     "shell64": lambda: (G.shell_config2(C.surface_res(64)), C.Grid(3, 64)),
+    "sphere128": lambda: (G.sphere3(0.9, C.surface_res(128)), C.Grid(3, 128)),
 }
 _cache = {}
 
@@ -167,3 +168,54 @@ def test_isotropic_coupled_matches_decoupled_gpu():
     hc.close()
     assert rel(Vc.cpu().numpy(), Vs.cpu().numpy()) < 1e-9
     assert rel(wc.cpu().numpy(), ws.cpu().numpy()) < 1e-9
+
+
+# --------------------------------- float32 transforms with refinement (GMRES-IR)
+
+@pytest.mark.parametrize("name", ["ellipse128", "shell64"])
+def test_coupled_mixed_solve(name):
+    """The coupled solve with float32 transforms inside GMRES and float64
+    refinement: the float64-accurate residual reaches the tolerance and the
+    potentials match the float64 oracle to 1e-8."""
+    import test_oracle_coupled as T
+    geom, grid, o, _ = pair(name)
+    kappa = 40.0
+    d = grid.dim
+    if d == 2:
+        fi, fe, gNi, gNe, _, _ = T._manufactured(geom, grid, kappa, DI, DE)
+    else:
+        fi, fe, gNi, gNe = _shell_data(geom, grid)
+    ui_o, ue_o, psi_o, info = o.solve_neumann(fi, fe, gNi, gNe, kappa, tol=1e-12)
+    g = K.KFBI(geom, grid, D_i=DI[:d], D_e=DE[:d], tol=1e-10, precision=K.MIXED)
+    ui = torch.empty(grid.shape, dtype=torch.float64, device=DEV)
+    ue = torch.empty_like(ui)
+    psi = torch.zeros(2 * geom.M, dtype=torch.float64, device=DEV)
+    st = g.solve_coupled(cuda(fi), cuda(fe), cuda(gNi), cuda(gNe), ui, ue, psi, kappa)
+    g.close()
+    print(f"{name}: mixed iterations {st['iters']} outer {st['outer']}, float64 oracle {info['iters']}, "
+          f"true residual {st['true_rel_res']:.2e}")
+    assert st["rel_res"] <= 1e-10 and st["true_rel_res"] < 1e-9 and st["outer"] >= 1
+    assert rel(ui.cpu().numpy(), ui_o) < 1e-8 and rel(ue.cpu().numpy(), ue_o) < 1e-8
+
+
+@pytest.mark.parametrize("name,steps", [("ellipse128", 4), ("shell64", 2)])
+def test_coupled_mixed_strang_steps(name, steps):
+    geom, grid, o, _ = pair(name)
+    d = grid.dim
+    dt = 0.05
+    V0 = C.ball_stimulus(grid, (-0.4, 0.0), 0.1) if d == 2 else C.ball_stimulus(grid, (0.8, 0.0, 0.0), 0.1)
+    w0 = np.zeros_like(V0)
+    cb = CP.CoupledBidomain(geom, grid, DI[:d], DE[:d], dt, C.FHN_CONFIG, tol=1e-12)
+    V, w = V0.copy(), w0.copy()
+    for _ in range(steps):
+        V, w, ue_o, info = cb.step(V, w)
+    h = K.KFBI(geom, grid, D_i=DI[:d], D_e=DE[:d], dt=dt, tol=1e-10, precision=K.MIXED)
+    Vd, wd = cuda(V0), cuda(w0)
+    ued = torch.empty_like(Vd)
+    st = h.bidomain_step(C.FHN_CONFIG, Vd, wd, ued, nsteps=steps)
+    h.close()
+    print(f"coupled mixed {name}: iterations {[s['iters'] for s in st]}, outer {[s['outer'] for s in st]}, "
+          f"V {rel(Vd.cpu().numpy(), V):.2e} ue {rel(ued.cpu().numpy(), ue_o):.2e}")
+    assert all(s["rel_res"] <= 1e-10 and s["true_rel_res"] < 1e-9 for s in st)
+    assert rel(Vd.cpu().numpy(), V) < 1e-8 and rel(wd.cpu().numpy(), w) < 1e-8
+    assert rel(ued.cpu().numpy(), ue_o) < 1e-8

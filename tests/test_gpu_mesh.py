@@ -45,6 +45,7 @@ CASES = {
     "bean32": lambda: (G.bean_mesh(8), C.Grid(3, 32)),
     "bean64": lambda: (G.bean_mesh(16), C.Grid(3, 64)),
     "shell_mesh64": lambda: (G.as_mesh(G.shell_config2(C.surface_res(64))), C.Grid(3, 64)),
+    "bean128": lambda: (G.bean_mesh(32), C.Grid(3, 128)),
 }
 _cache = {}
 
