@@ -1419,14 +1419,30 @@ static int bidomain_coupled_impl(kfbi_handle* h, const kfbi_fhn* p, const double
     if (rc) return rc;
     if ((rc = mark(s, 2))) return rc;
     if ((rc = vec_copy(h, h->w.psi_save, h->w.psi_prev, nk))) return rc;
-    if ((rc = vec_copy(h, h->w.psi_learn, h->w.psi_prev, nk))) return rc;
+    // initial density pair: the previous one, or (KFBI_WARM_PROJECTION) the
+    // history projection plus one step of the simple iteration, with the
+    // projection itself as the fallback the first residual decides on
+    const double* fallback = nullptr;
+    const double* fallback_res2 = nullptr;
+    double gnorm = -1.0;
     h->proj_valid = false;
+    if (h->opts.warm == KFBI_WARM_PROJECTION && h->hist_count >= 1) {
+      h->proj_valid = true;
+      if ((rc = project_history(h, h->w.g, &gnorm, &fallback_res2))) return rc;
+      if ((rc = vec_copy(h, h->w.psi_prev, h->w.psiF, nk))) return rc;
+      if ((rc = vec_axpby(h, h->w.psi_prev, 2.0 * h->opts.gamma, h->w.rF, 1.0, nk))) return rc;
+      fallback = h->w.psiF;
+    }
+    if ((rc = vec_copy(h, h->w.psi_learn, h->w.psi_prev, nk))) return rc;
     if ((rc = mark(s, 3))) return rc;
-    const int src = solve_bie(h, prec, kap, h->w.g, h->w.psi_prev, &st);
+    const bool ir = prec != KFBI_FP64;
+    const int src = solve_bie(h, prec, kap, h->w.g, h->w.psi_prev, &st, fallback, fallback_res2, gnorm,
+                              ir ? h->w.rF : nullptr);
     if (src != KFBI_OK && src != KFBI_ERR_NOT_CONVERGED) return src;
     if (src == KFBI_ERR_NOT_CONVERGED) final_rc = src;
     if ((rc = vec_copy(h, h->w.psi_prev2, h->w.psi_save, nk))) return rc;
     if ((rc = vec_copy(h, h->w.g_prev, h->w.g, nk))) return rc;
+    if ((rc = push_history(h, h->w.psi_prev, h->w.g, ir ? h->w.r2 : nullptr))) return rc;
     ++h->n_hist;
     if ((rc = mark(s, 4))) return rc;
     if (prec == KFBI_FP64) {

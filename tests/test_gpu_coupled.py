@@ -219,3 +219,33 @@ def test_coupled_mixed_strang_steps(name, steps):
     assert all(s["rel_res"] <= 1e-10 and s["true_rel_res"] < 1e-9 for s in st)
     assert rel(Vd.cpu().numpy(), V) < 1e-8 and rel(wd.cpu().numpy(), w) < 1e-8
     assert rel(ued.cpu().numpy(), ue_o) < 1e-8
+
+
+@pytest.mark.parametrize("name,prec,bar", [("ellipse128", K.FP64, TOL64), ("shell64", K.MIXED, 1e-8)])
+def test_coupled_projection_warm_start(name, prec, bar):
+    """The density-history projection (least squares over the last density
+    pairs by their images, plus one simple-iteration step) starts the coupled
+    solves: the converged steps are the oracle's, in fewer iterations than
+    from the previous density pair."""
+    geom, grid, o, _ = pair(name)
+    d = grid.dim
+    steps = 6
+    V0 = C.ball_stimulus(grid, (-0.4, 0.0), 0.1) if d == 2 else C.ball_stimulus(grid, (0.8, 0.0, 0.0), 0.1)
+    w0 = np.zeros_like(V0)
+    tol = 1e-12 if prec == K.FP64 else 1e-10
+    cb = CP.CoupledBidomain(geom, grid, DI[:d], DE[:d], 0.05, C.FHN_CONFIG, tol=1e-12)
+    V, w = V0.copy(), w0.copy()
+    for _ in range(steps):
+        V, w, ue_o, info = cb.step(V, w)
+    its = {}
+    for warm in (K.WARM_PREVIOUS, K.WARM_PROJECTION):
+        h = K.KFBI(geom, grid, D_i=DI[:d], D_e=DE[:d], dt=0.05, tol=tol, precision=prec, warm=warm)
+        Vd, wd = cuda(V0), cuda(w0)
+        st = h.bidomain_step(C.FHN_CONFIG, Vd, wd, None, nsteps=steps)
+        h.close()
+        its[warm] = sum(s["iters"] for s in st[2:])
+        assert all(s["rel_res"] <= tol for s in st)
+        assert rel(Vd.cpu().numpy(), V) < bar and rel(wd.cpu().numpy(), w) < bar
+    print(f"coupled {name}: iterations over steps 3..{steps}: previous {its[K.WARM_PREVIOUS]}, "
+          f"projection {its[K.WARM_PROJECTION]}")
+    assert its[K.WARM_PROJECTION] < its[K.WARM_PREVIOUS]
