@@ -747,10 +747,10 @@ def run_coupled(args):
 def run_neumann(args):
     """The Neumann box (zero normal derivative on the box boundary, the box
     Green's function of Section 4; all (N+1)^3 nodes, cosine transforms)
-    against the Dirichlet box on the shell workload at N^3, float64,
-    projection warm start, tol 1e-8: Strang steps/s, iterations per step, the
-    float64 box solve time and its algorithmic bytes (read r, write v) per
-    second."""
+    against the Dirichlet box on the shell workload at N^3, in float64 and
+    with float32 transforms (GMRES-IR), projection warm start, tol 1e-8:
+    Strang steps/s, iterations per step, the box solve time (float64, or
+    plain float32) and its algorithmic bytes (read r, write v) per second."""
     import torch
 
     import paper_2104_05024_gb300.kfbi as K
@@ -758,9 +758,9 @@ def run_neumann(args):
     dev = torch.device("cuda", 0)
     N = args.N
     rows = {}
-    for bc in ("dirichlet", "neumann"):
+    for bc, prec in (("dirichlet", K.FP64), ("neumann", K.FP64), ("dirichlet", K.MIXED), ("neumann", K.MIXED)):
         geom, grid, cfg, V0, w0 = C.config2(N=N, bc=bc)
-        h = K.KFBI(geom, grid, sigma_i=cfg.sigma_i, sigma_e=cfg.sigma_e, dt=cfg.dt, tol=cfg.tol, precision=K.FP64,
+        h = K.KFBI(geom, grid, sigma_i=cfg.sigma_i, sigma_e=cfg.sigma_e, dt=cfg.dt, tol=cfg.tol, precision=prec,
                    warm=K.WARM_PROJECTION, restart=50, max_iter=500)
         V, w = torch.tensor(V0, device=dev), torch.tensor(w0, device=dev)
         ue = torch.empty_like(V)
@@ -768,19 +768,21 @@ def run_neumann(args):
         ms, st = _event_ms(lambda: h.bidomain_step(C.FHN_CONFIG, V, w, ue, nsteps=args.steps))
         r = torch.randn(grid.shape, dtype=torch.float64, device=dev)
         v = torch.empty_like(r)
-        h.box_solve(r, v, h.info["lambda"], precision=K.FP64)
-        box_ms, _ = _event_ms(lambda: h.box_solve(r, v, h.info["lambda"], precision=K.FP64), reps=5)
+        bprec = K.FP64 if prec == K.FP64 else K.FP32
+        h.box_solve(r, v, h.info["lambda"], precision=bprec)
+        box_ms, _ = _event_ms(lambda: h.box_solve(r, v, h.info["lambda"], precision=bprec), reps=5)
         pts = int(np.prod(grid.shape))
-        rows[bc] = {"field_nodes": pts, "steps_per_s": round(1000.0 * args.steps / ms, 3),
+        key = bc + ("_fp64" if prec == K.FP64 else "_mixed")
+        rows[key] = {"field_nodes": pts, "steps_per_s": round(1000.0 * args.steps / ms, 3),
                     "iters_per_step": float(np.mean([s["iters"] for s in st])),
                     "true_rel_res_max": float(max(s["true_rel_res"] for s in st)),
                     "V_max": float(V.abs().max()), "ue_max": float(ue.abs().max()),
                     "box_solve_ms": round(box_ms, 3),
                     "box_solve_algorithmic_GBs": round(2 * 8 * pts / (box_ms * 1e-3) / 1e9, 1)}
         h.close()
-    print(json.dumps({"metric": "Neumann-box Strang steps/s and float64 box solve (vs the Dirichlet box)",
-                      "workload": f"shell {N}^3, FHN of the workloads, dt 0.05, tol 1e-8, float64, projection "
-                                  f"warm start, {args.steps} steps after 3",
+    print(json.dumps({"metric": "Neumann-box Strang steps/s and box solve (vs the Dirichlet box)",
+                      "workload": f"shell {N}^3, FHN of the workloads, dt 0.05, tol 1e-8, float64 and float32 "
+                                  f"transforms, projection warm start, {args.steps} steps after 3",
                       "unit": "steps/s", "rows": rows}), flush=True)
 
 

@@ -61,9 +61,9 @@ extern "C" {
 #define KFBI_BOX_DIRICHLET 0 /* v = 0 on the box boundary; sine transforms          */
 #define KFBI_BOX_NEUMANN 1   /* zero normal derivative on the box boundary, the box
                                 Green's function of Section 4: mirrored ghost rows,
-                                cosine (DCT-I) transforms.  Float64 only
-                                (KFBI_FP64), lambda > 0 (no Green's function of the
-                                Poisson operator), scalar problem only           */
+                                cosine (DCT-I) transforms; every precision,
+                                lambda > 0 (no Green's function of the Poisson
+                                operator), scalar problem only                    */
 
 /* precision of the integral evaluations */
 #define KFBI_FP64 0          /* all transforms and corrections in float64        */

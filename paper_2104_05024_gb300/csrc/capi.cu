@@ -344,7 +344,7 @@ int refined_solve(kfbi_handle* h, const double* src, double alpha, const double*
   const int rounds = refine_rounds(h);
   for (int r = 0; r < rounds; ++r) {
     SolveArgs sr;
-    if (r == 0) {
+    if (r == 0 && !neumann_box(h)) {
       // u is exactly the float32 grid of the solve just done: float-float
       // residual, float32 result
       if ((rc = launch_residual_ff(h, src, alpha, corr, h->w.grid32, u, lambda, h->w.res32))) return rc;
@@ -821,10 +821,7 @@ static int create_impl(const kfbi_geometry* geom, const kfbi_grid* grid, double 
     set_error("box must be KFBI_BOX_DIRICHLET or KFBI_BOX_NEUMANN");
     return KFBI_ERR_ARG;
   }
-  if (grid->box == KFBI_BOX_NEUMANN && opts->precision != KFBI_FP64) {
-    set_error("the Neumann box is solved in float64 (KFBI_FP64)");
-    return KFBI_ERR_ARG;
-  }
+
   kfbi_handle* h = new kfbi_handle();
   h->opts = *opts;
   h->stream = (cudaStream_t)opts->stream;
@@ -985,10 +982,7 @@ int kfbi_set_opts(kfbi_handle* h, const kfbi_opts* opts) {
     set_error("restart cannot grow after kfbi_create");
     return KFBI_ERR_ARG;
   }
-  if (neumann_box(h) && opts->precision != KFBI_FP64) {
-    set_error("the Neumann box is solved in float64 (KFBI_FP64)");
-    return KFBI_ERR_ARG;
-  }
+
   h->opts = *opts;
   h->stream = (cudaStream_t)opts->stream;
   return KFBI_OK;
@@ -1039,10 +1033,7 @@ int kfbi_box_solve(kfbi_handle* h, int precision, double lambda, const double* r
     set_error("null field");
     return KFBI_ERR_ARG;
   }
-  if (neumann_box(h) && precision != KFBI_FP64) {
-    set_error("the Neumann box is solved in float64 (KFBI_FP64)");
-    return KFBI_ERR_ARG;
-  }
+
   SolveArgs sa;
   sa.src = r_dev;
   sa.lambda = lambda;

@@ -1541,22 +1541,25 @@ int run_solve_neumann(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1
   return KFBI_OK;
 }
 
-int box_solve_neumann64(kfbi_handle* h, const SolveArgs& sa, double* work) {
+template <typename T>
+int box_solve_neumann(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1, const T* tw) {
   if (!(sa.lambda > 0.0)) {
     set_error("the Neumann box needs lambda > 0 (no Green's function of the Poisson operator exists)");
     return KFBI_ERR_ARG;
   }
-  const double* mu1 = h->t.mu;
-  const double* tw = h->t.tw64;
+  if (sa.src32 != nullptr) {
+    set_error("the Neumann box takes float64 sources");
+    return KFBI_ERR_ARG;
+  }
   switch (h->grid.N) {
-    case 8: return run_solve_neumann<double, 8>(h, sa, work, mu1, tw);
-    case 16: return run_solve_neumann<double, 16>(h, sa, work, mu1, tw);
-    case 32: return run_solve_neumann<double, 32>(h, sa, work, mu1, tw);
-    case 64: return run_solve_neumann<double, 64>(h, sa, work, mu1, tw);
-    case 128: return run_solve_neumann<double, 128>(h, sa, work, mu1, tw);
-    case 256: return run_solve_neumann<double, 256>(h, sa, work, mu1, tw);
-    case 384: return run_solve_neumann<double, 384>(h, sa, work, mu1, tw);
-    case 512: return run_solve_neumann<double, 512>(h, sa, work, mu1, tw);
+    case 8: return run_solve_neumann<T, 8>(h, sa, work, mu1, tw);
+    case 16: return run_solve_neumann<T, 16>(h, sa, work, mu1, tw);
+    case 32: return run_solve_neumann<T, 32>(h, sa, work, mu1, tw);
+    case 64: return run_solve_neumann<T, 64>(h, sa, work, mu1, tw);
+    case 128: return run_solve_neumann<T, 128>(h, sa, work, mu1, tw);
+    case 256: return run_solve_neumann<T, 256>(h, sa, work, mu1, tw);
+    case 384: return run_solve_neumann<T, 384>(h, sa, work, mu1, tw);
+    case 512: return run_solve_neumann<T, 512>(h, sa, work, mu1, tw);
     default:
       set_error("unsupported grid size N=%d", h->grid.N);
       return KFBI_ERR_ARG;
@@ -1618,11 +1621,12 @@ int dst_supported(int N) {
 }
 
 int box_solve64(kfbi_handle* h, const SolveArgs& a, double* work) {
-  if (h->grid.bc == KFBI_BOX_NEUMANN) return box_solve_neumann64(h, a, work);
+  if (h->grid.bc == KFBI_BOX_NEUMANN) return box_solve_neumann<double>(h, a, work, h->t.mu, h->t.tw64);
   return dispatch<double>(h, a, work, h->t.mu, h->t.tw64);
 }
 
 int box_solve32(kfbi_handle* h, const SolveArgs& a, float* work) {
+  if (h->grid.bc == KFBI_BOX_NEUMANN) return box_solve_neumann<float>(h, a, work, h->t.mu32, h->t.tw32);
   return dispatch<float>(h, a, work, h->t.mu32, h->t.tw32);
 }
 

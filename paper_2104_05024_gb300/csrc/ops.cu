@@ -218,7 +218,30 @@ __global__ void k_residual_irr(GridParams gr, Tables t, const double* __restrict
 
 __global__ void k_scatter_add(Tables t, const double* __restrict__ corr, double* __restrict__ g) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < t.n_irr) g[t.irr[i]] += corr[i];
+  if (i < t.n_irr) g[t.irr_user[i]] += corr[i];
+}
+
+// r = alpha*src - L_h u on the Neumann box's field layout (all (N+1)^d
+// nodes; a neighbour beyond the box is the mirror image across it)
+__global__ void k_residual_neumann(GridParams gr, const double* __restrict__ src, double alpha,
+                                   const double* __restrict__ u, double lambda, double* __restrict__ res) {
+  const int P = gr.N + 1;
+  const double ih2 = 1.0 / (gr.h * gr.h);
+  const double diag = -2.0 * gr.dim * ih2 - lambda;
+  const int y = blockIdx.x, z = blockIdx.y;
+  const int64_t s = (int64_t)P * P;
+  const int64_t base = (int64_t)z * s + (int64_t)y * P;
+  const int64_t ym = y > 0 ? -P : P, yp = y < P - 1 ? P : -P;
+  const int64_t zm = z > 0 ? -s : s, zp = z < P - 1 ? s : -s;
+  for (int x = threadIdx.x; x < P; x += blockDim.x) {
+    const int64_t f = base + x;
+    const double uc = u[f];
+    double nb = u[f + (x > 0 ? -1 : 1)] + u[f + (x < P - 1 ? 1 : -1)];
+    nb += u[f + ym] + u[f + yp];
+    if (gr.dim == 3) nb += u[f + zm] + u[f + zp];
+    const double Lu = nb * ih2 + diag * uc;
+    res[f] = (src != nullptr ? alpha * src[f] : 0.0) - Lu;
+  }
 }
 
 __global__ void k_add_scalar(double* __restrict__ out, const double* __restrict__ slot, double c, int n) {
@@ -808,7 +831,13 @@ int launch_limit_user_t(kfbi_handle* h, const Tables& t, const double* u, const 
 int launch_residual(kfbi_handle* h, const double* src, double alpha, const double* corr, const double* u, double lambda,
                     double* res) {
   const int n1 = h->grid.N - 1;
-  k_residual<<<dim3(n1, h->grid.dim == 3 ? n1 : 1), 128, 0, h->stream>>>(h->grid, src, alpha, u, lambda, res);
+  if (h->grid.bc == KFBI_BOX_NEUMANN) {
+    const int P = h->grid.N + 1;
+    k_residual_neumann<<<dim3(P, h->grid.dim == 3 ? P : 1), 128, 0, h->stream>>>(h->grid, src, alpha, u, lambda,
+                                                                                   res);
+  } else {
+    k_residual<<<dim3(n1, h->grid.dim == 3 ? n1 : 1), 128, 0, h->stream>>>(h->grid, src, alpha, u, lambda, res);
+  }
   if (corr != nullptr && h->t.n_irr > 0)
     k_scatter_add<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->t, corr, res);
   KFBI_CHECK_LAUNCH_N(corr != nullptr && h->t.n_irr > 0 ? 2 : 1);

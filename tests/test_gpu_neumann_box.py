@@ -11,6 +11,8 @@ rows, cosine transforms) through the C ABI against the oracle.
 * Strang steps (config 0 for its 20 steps, the 3-D shell for 2): V, w and
   u_e within 1e-10;
 * the solution inside Omega agrees with the Dirichlet box's to second order;
+* float32 transforms: the plain float32 solve within 2e-5, refined solves,
+  GMRES-IR and the float32 Strang forms within 1e-8 of the float64 oracle;
 * what the Neumann box does not support is rejected with KFBI_ERR_ARG.
 """
 import numpy as np
@@ -188,22 +190,61 @@ def test_strang_shell64_neumann_box_projection():
 def test_unsupported_forms_rejected():
     geom, grid = G.ellipse_config0(128), ngrid(2, 64)
     with pytest.raises(K.KFBIError) as e:
-        K.KFBI(geom, grid, precision=K.MIXED)
-    assert e.value.code == K.ERR_ARG
-    with pytest.raises(K.KFBIError) as e:
         K.KFBI(geom, grid, D_i=(1.0, 1.0), D_e=(2.0, 2.0))
     assert e.value.code == K.ERR_ARG
     g = K.KFBI(geom, grid)
     r = torch.zeros(grid.shape, dtype=torch.float64, device=DEV)
     v = torch.empty_like(r)
-    for prec in (K.MIXED, K.FP32):
-        with pytest.raises(K.KFBIError) as e:
-            g.box_solve(r, v, 60.0, precision=prec)
-        assert e.value.code == K.ERR_ARG
     with pytest.raises(K.KFBIError) as e:        # no Poisson Green's function
         g.box_solve(r, v, 0.0, precision=K.FP64)
     assert e.value.code == K.ERR_ARG
-    with pytest.raises(K.KFBIError) as e:
-        g.set_opts(precision=K.MIXED)
-    assert e.value.code == K.ERR_ARG
     g.close()
+
+
+# ----------------------------------------- float32 transforms, refinement, GMRES-IR
+
+@pytest.mark.parametrize("dim,N", [(2, 128), (3, 64), (3, 128)])
+def test_dct_box_solve_float32_and_refined(dim, N):
+    geom = G.ellipse_config0(64) if dim == 2 else G.sphere3(0.5, 4)
+    grid = ngrid(dim, N)
+    g = K.KFBI(geom, grid, tol=1e-10)
+    r = np.random.default_rng(N + 7).standard_normal(grid.shape)
+    ref = boxsolve.solve(r, 60.0, grid)
+    v = torch.empty(grid.shape, dtype=torch.float64, device=DEV)
+    g.box_solve(cuda(r), v, 60.0, precision=K.FP32)
+    assert rel(v.cpu().numpy(), ref) < 2e-5
+    g.box_solve(cuda(r), v, 60.0, precision=K.MIXED)   # float32 transforms + float64 residual rounds
+    g.close()
+    assert rel(v.cpu().numpy(), ref) < 1e-10
+
+
+@pytest.mark.parametrize("name,lam", [("ellipse128", 60.0), ("shell64", 60.0)])
+def test_solve_neumann_mixed(name, lam):
+    geom, grid, o, _ = pair(name)
+    f, u_ex, gN = C.manufactured(geom, grid, lam)
+    u_ref, psi_ref, info = o.solve_neumann(f, gN, lam, tol=1e-12)
+    g = K.KFBI(geom, grid, tol=1e-10, precision=K.MIXED)
+    u = torch.empty(grid.shape, dtype=torch.float64, device=DEV)
+    psi = torch.zeros(geom.M, dtype=torch.float64, device=DEV)
+    st = g.solve_neumann(cuda(f), cuda(gN), u, psi, lam)
+    g.close()
+    assert st["rel_res"] <= 1e-10 and st["true_rel_res"] < 1e-9 and st["outer"] >= 1
+    assert rel(u.cpu().numpy(), u_ref) < 1e-8
+
+
+def test_strang_config0_neumann_box_mixed_learned_forms():
+    """Config 0 in the Neumann box with float32 transforms, from the previous
+    density and from the history projection: V, w within 1e-8 of the oracle."""
+    geom, grid, cfg, V0, w0 = C.config0(bc="neumann")
+    cfg = C.StrangConfig(sigma_i=1.0, sigma_e=2.0, dt=0.05, steps=10, tol=1e-12)
+    bd = Bidomain(geom, grid, cfg, C.FHN_CONFIG)
+    V, w = V0.copy(), w0.copy()
+    for _ in range(cfg.steps):
+        V, w, _ = bd.step(V, w)
+    for warm in (K.WARM_PREVIOUS, K.WARM_PROJECTION):
+        h = K.KFBI(geom, grid, tol=1e-10, precision=K.MIXED, warm=warm)
+        Vd, wd = cuda(V0), cuda(w0)
+        st = h.bidomain_step(C.FHN_CONFIG, Vd, wd, None, nsteps=cfg.steps)
+        h.close()
+        assert all(s["rel_res"] <= 1e-10 and s["true_rel_res"] < 1e-9 for s in st)
+        assert rel(Vd.cpu().numpy(), V) < 1e-8 and rel(wd.cpu().numpy(), w) < 1e-8
