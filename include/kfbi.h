@@ -250,14 +250,19 @@ int kfbi_bidomain_step_stim(kfbi_handle* h, const kfbi_fhn* p, const double* ist
  * the homogeneous problem, so every operator application adds the rank-one
  * term (1, 1) <(ds, ds), psi> / (2 |Gamma|) (ds as at kfbi_solve_neumann);
  * Phi_i and Phi_e are then fixed up to that common constant's choice, their
- * difference is unique.  Float64 only (opts.precision = KFBI_FP64).
+ * difference is unique.  opts.precision KFBI_FP64 (float64 throughout) or
+ * KFBI_MIXED (float32 transforms inside GMRES with the float64 2 x 2 mode
+ * solve, float64 Arnoldi, and refinement of the float64 coupled residual
+ * for g, the outer residuals and the final potentials).  Dirichlet box only.
  * ------------------------------------------------------------------ */
 /* Setup as kfbi_create for the coupled system; D_i, D_e: dim positive
  * conductivities each (host).  bidomain_step and kfbi_bidomain_step_stim on
  * this handle run the Strang step with the coupled diffusion (kappa = 2 Cm
  * beta / dt, f = (-kappa V, kappa V - beta I_stim), warm start: the previous
- * density pair, V <- 2 (Phi_i - Phi_e) - V); their ue_dev receives the last
- * solve's Phi_e (the midpoint level t^n + dt/2) with zero mean over Omega.  */
+ * density pair, or with opts.warm = KFBI_WARM_PROJECTION the history
+ * projection of the density pairs; V <- 2 (Phi_i - Phi_e) - V); their ue_dev
+ * receives the last solve's Phi_e (the midpoint level t^n + dt/2) with zero
+ * mean over Omega.                                                           */
 int kfbi_create_coupled(const kfbi_geometry* geom, const kfbi_grid* grid, const double* D_i, const double* D_e,
                         double dt, const kfbi_opts* opts, kfbi_handle** out);
 /* The coupled Neumann problem: fi_dev, fe_dev on every box node (continuous
@@ -297,11 +302,13 @@ int kfbi_export_setup(kfbi_handle* h, uint8_t* inside, int32_t* irregular, int32
 int kfbi_export_tables(kfbi_handle* h, double* node_wn, int32_t* node_cnt, int32_t* node_pid, double* node_w,
                        int32_t* cross_cnt, int32_t* cross_pid, double* cross_wlo, double* cross_whi);
 
-/* Box solve (Sections 5.2-5.3): v = L_h^{-1} r, 5/7-point operator with zero
- * Dirichlet data, by sine transforms.  precision KFBI_FP64 (float64
- * transforms), KFBI_MIXED / KFBI_MIXED_LEARNED (float32 transforms refined
- * by three rounds of the float64 residual: float64-accurate) or KFBI_FP32
- * (float32 transforms only).                                                */
+/* Box solve (Sections 5.2-5.3): v = L_h^{-1} r, 5/7-point operator with the
+ * handle's box condition (zero Dirichlet data by sine transforms, or the
+ * Neumann box's mirrored ghost rows by cosine transforms).  precision
+ * KFBI_FP64 (float64 transforms), KFBI_MIXED / KFBI_MIXED_LEARNED (float32
+ * transforms refined by one round of the float64 residual, two when the
+ * handle's tolerance is below 1e-9: float64-accurate) or KFBI_FP32 (float32
+ * transforms only).                                                         */
 int kfbi_box_solve(kfbi_handle* h, int precision, double lambda, const double* r_dev, double* v_dev);
 
 /* Irregular-node correction (Section 5.3, Eq. correct): rhs_dev (grid, fully
