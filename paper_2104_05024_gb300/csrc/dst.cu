@@ -1273,7 +1273,8 @@ int dispatch_pass(kfbi_handle* h, int pass, double lambda, T* work, const T* mu1
 
 template <typename C>
 constexpr size_t dct_smem_elems() {
-  return (size_t)(C::N + 1) * C::RS + (size_t)C::G * C::W + 4 * (size_t)C::N + C::W;
+  // tile, scan totals, twiddles, X_1 per column, sines (register path)
+  return (size_t)(C::N + 1) * C::RS + (size_t)C::G * C::W + 4 * (size_t)C::N + C::W + C::N;
 }
 
 // DCT-I X_p = sum_k c_k x_k cos(pi k p / N) of every column of the tile
@@ -1369,6 +1370,19 @@ __device__ void dct1_tile(typename C::T* s, const typename C::T* tw, typename C:
   }
 }
 
+// the cosine transform of every column of the tile, rows 0..N: the
+// register-resident path for float32 tiles of 32 <= N <= 512 lines, the
+// shared-memory FFT otherwise
+template <typename C>
+__device__ __forceinline__ void dct_tile(typename C::T* s, const typename C::T* tw, const typename C::T* sinv,
+                                         typename C::T* tot, typename C::T* x1) {
+  if constexpr (kRegDst<typename C::T, C::N>) {
+    regdst::dct1_tile_reg<regdst::Geo<C::N, C::RS>>(s, sinv, reinterpret_cast<const regdst::cf2*>(tw), tot, x1);
+  } else {
+    dct1_tile<C>(s, tw, tot, x1);
+  }
+}
+
 // x forward on the Neumann layout: W lines y0..y0+W-1 (y <= N) of plane z,
 // r = alpha*src + corrections assembled while loading.  The irregular nodes
 // (all interior) are listed per interior x-line in the interior numbering.
@@ -1384,8 +1398,10 @@ __global__ void __launch_bounds__(NT) k_nxfwd(T* __restrict__ a, const double* _
   T* tot = s + P * RS;
   T* tw = tot + C::G * W;
   T* x1 = tw + 4 * N;
+  T* sinv = x1 + W;
   const bool skipped = skip != nullptr && *skip != 0;
   load_twiddles<T, N>(tw, tw_g);
+  load_sines<T, N>(sinv, tw_g);
   if (skipped) return;
   const int y0 = blockIdx.x * W;
   const int z = DIM == 3 ? blockIdx.y : 0;
@@ -1410,7 +1426,7 @@ __global__ void __launch_bounds__(NT) k_nxfwd(T* __restrict__ a, const double* _
     }
   }
   __syncthreads();
-  dct1_tile<C>(s, tw, tot, x1);
+  dct_tile<C>(s, tw, sinv, tot, x1);
   for (int idx = threadIdx.x; idx < P * W; idx += NT) {
     const int x = idx % P, c = idx / P, y = y0 + c;
     if (y <= N) a[plane + (size_t)y * P + x] = s[x * RS + c];
@@ -1430,8 +1446,10 @@ __global__ void __launch_bounds__(NT) k_nxinv(T* __restrict__ a, bool keep, doub
   T* tot = s + P * RS;
   T* tw = tot + C::G * W;
   T* x1 = tw + 4 * N;
+  T* sinv = x1 + W;
   if (skip != nullptr && *skip != 0) return;
   load_twiddles<T, N>(tw, tw_g);
+  load_sines<T, N>(sinv, tw_g);
   const int y0 = blockIdx.x * W;
   const int z = DIM == 3 ? blockIdx.y : 0;
   const size_t plane = (size_t)z * P * P;
@@ -1442,7 +1460,7 @@ __global__ void __launch_bounds__(NT) k_nxinv(T* __restrict__ a, bool keep, doub
   }
   copy_async_wait();
   __syncthreads();
-  dct1_tile<C>(s, tw, tot, x1);
+  dct_tile<C>(s, tw, sinv, tot, x1);
   for (int idx = threadIdx.x; idx < P * W; idx += NT) {
     const int x = idx % P, c = idx / P, y = y0 + c;
     if (y > N) continue;
@@ -1471,8 +1489,10 @@ __global__ void __launch_bounds__(NT) k_nstrided(T* __restrict__ a, size_t row_s
   T* tot = s + P * RS;
   T* tw = tot + C::G * W;
   T* x1 = tw + 4 * N;
+  T* sinv = x1 + W;
   const bool skipped = skip != nullptr && *skip != 0;
   load_twiddles<T, N>(tw, tw_g);
+  load_sines<T, N>(sinv, tw_g);
   if (skipped) return;
   const int x0 = blockIdx.x * W;
   const int q = blockIdx.y;
@@ -1484,7 +1504,7 @@ __global__ void __launch_bounds__(NT) k_nstrided(T* __restrict__ a, size_t row_s
   }
   copy_async_wait();
   __syncthreads();
-  dct1_tile<C>(s, tw, tot, x1);
+  dct_tile<C>(s, tw, sinv, tot, x1);
   if (SOLVE) {
     const T muq = DIM == 3 ? mu1[q] : (T)0;
     const T* rq = rinv != nullptr ? rinv + (size_t)q * P * P : nullptr;
@@ -1494,7 +1514,7 @@ __global__ void __launch_bounds__(NT) k_nstrided(T* __restrict__ a, size_t row_s
         s[k * RS + c] *= rq != nullptr ? rq[(size_t)k * P + p] : scale / (mu1[k] + mu1[p] + muq - lambda);
     }
     __syncthreads();
-    dct1_tile<C>(s, tw, tot, x1);
+    dct_tile<C>(s, tw, sinv, tot, x1);
   }
   for (int idx = threadIdx.x; idx < P * W; idx += NT) {
     const int c = idx % W, k = idx / W;

@@ -407,6 +407,127 @@ struct Identity {
   KFBI_HD float operator()(int, float v) const { return v; }
 };
 
+// ---- cosine transform (DCT-I of the N + 1 rows 0..N, the Neumann box) ----
+// X_p = sum_k c_k x_k cos(pi k p / N), c_0 = c_N = 1/2.  The same two-level
+// FFT after the cosine pre-fold
+//   y_j = (x_j + x_{N-j}) / 2 - sin(pi j / N)(x_j - x_{N-j})   (y_0 = (x_0 + x_N) / 2),
+// then X_{2k} = Re Y_k (X_0 and X_N from Z_0) and the odd outputs by the scan
+// X_{2k+1} = X_{2k-1} + Im Y_k (2 sin a sin b = cos(a - b) - cos(a + b)),
+// started at X_1 = sum_k c_k x_k cos(pi k / N), whose terms phase A1 sums
+// while it reads the rows (each thread its rows 2m, 2m + 1; warp 0 row N).
+
+// phase A1 (cosine): pre-fold, partial X_1 to part[a][c], radix-P DFT, twiddle
+template <class G>
+KFBI_HD void phase_a1_cos(State<G>& st, const float* s, const float* sinv, const cf2* tw2, float* part, int a,
+                          int c) {
+  constexpr int N = G::N, RS = G::RS, T = G::T, P = G::P, W = G::W;
+  float x1 = 0.0f;
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    const int m = a + T * q, j = 2 * m;
+    const float x0 = s[j * RS + c], xa = s[(j + 1) * RS + c];
+    const float r0 = s[(N - j) * RS + c], r1 = s[(N - j - 1) * RS + c];
+    const cf2 sn = reinterpret_cast<const cf2*>(sinv)[m];  // sin(pi j/N), sin(pi (j+1)/N)
+    st.zr[q] = 0.5f * (x0 + r0) - sn.x * (x0 - r0);
+    st.zi[q] = 0.5f * (xa + r1) - sn.y * (xa - r1);
+    x1 += (m > 0 ? tw2[j].x : 0.5f) * x0 + tw2[j + 1].x * xa;
+  }
+  if (a == 0) x1 -= 0.5f * s[N * RS + c];
+  part[a * W + c] = x1;
+  dft_first<P, N>(st.zr, st.zi, tw2);
+#pragma unroll
+  for (int k1 = 1; k1 < P; ++k1) {
+    const cf2 w = tw2[4 * a * k1];
+    const float t = st.zr[k1] * w.x - st.zi[k1] * w.y;
+    st.zi[k1] = st.zr[k1] * w.y + st.zi[k1] * w.x;
+    st.zr[k1] = t;
+  }
+}
+
+// X_1 of every column from the partial sums (warp 0; after a barrier)
+template <class G>
+KFBI_HD void phase_x1(const float* part, float* x1v, int a, int c) {
+  if (a != 0) return;
+  float v = 0.0f;
+  for (int b = 0; b < G::T; ++b) v += part[b * G::W + c];
+  x1v[c] = v;
+}
+
+// Y_k from A = Z_k, B = Z_{L-k}: Re Y_k = X_{2k} to row 2k, Im Y_k (scan
+// input) to row 2k+1
+template <class G, class Post>
+KFBI_HD void split_store_cos(float* s, const cf2* tw2, int k, float Ar, float Ai, float Br, float Bi, int c,
+                             const Post& post) {
+  constexpr int RS = G::RS;
+  const cf2 w = tw2[2 * k];
+  const float Sr = Ar + Br, Si = Ai - Bi, Dr = Ar - Br, Di = Ai + Bi;
+  const float Yr = 0.5f * (Sr + w.x * Di + w.y * Dr);
+  const float Yi = 0.5f * (Si - w.x * Dr + w.y * Di);
+  s[(2 * k) * RS + c] = post(2 * k, Yr);
+  s[(2 * k + 1) * RS + c] = Yi;
+}
+
+// phase D (cosine): real-DFT split of the owned pairs; X_0, X_N from Z_0
+template <class G, class Post>
+KFBI_HD void phase_d_cos(const State<G>& st, float* s, const cf2* tw2, int a, int c, const Post& post) {
+  constexpr int N = G::N, T = G::T, P = G::P, L = G::L, RS = G::RS;
+#pragma unroll
+  for (int gi = 0; gi < G::GPT; ++gi) {
+    const int g = a + T * gi;
+    if (g >= G::NG) continue;
+    int kA, kB;
+    group_k1<G>(g, kA, kB);
+    if (g == 0) {
+      s[c] = post(0, st.Ar[gi][0] + st.Ai[gi][0]);
+      s[N * RS + c] = post(N, st.Ar[gi][0] - st.Ai[gi][0]);
+      s[RS + c] = 0.0f;
+#pragma unroll
+      for (int k2 = 1; k2 <= 4; ++k2) {
+        const int k = P * k2, kk = L - k;
+        split_store_cos<G>(s, tw2, k, st.Ar[gi][k2], st.Ai[gi][k2], st.Ar[gi][(8 - k2) & 7],
+                           st.Ai[gi][(8 - k2) & 7], c, post);
+        if (kk != k)
+          split_store_cos<G>(s, tw2, kk, st.Ar[gi][(8 - k2) & 7], st.Ai[gi][(8 - k2) & 7], st.Ar[gi][k2],
+                             st.Ai[gi][k2], c, post);
+      }
+      if (P > 1) {
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) {
+          const int k = kB + P * k2, kk = L - k;
+          split_store_cos<G>(s, tw2, k, st.Br[gi][k2], st.Bi[gi][k2], st.Br[gi][7 - k2], st.Bi[gi][7 - k2], c,
+                             post);
+          split_store_cos<G>(s, tw2, kk, st.Br[gi][7 - k2], st.Bi[gi][7 - k2], st.Br[gi][k2], st.Bi[gi][k2], c,
+                             post);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k2 = 0; k2 < 8; ++k2) {
+        const int k = kA + P * k2;
+        split_store_cos<G>(s, tw2, k, st.Ar[gi][k2], st.Ai[gi][k2], st.Br[gi][7 - k2], st.Bi[gi][7 - k2], c,
+                           post);
+        const int kk = kB + P * k2;
+        split_store_cos<G>(s, tw2, kk, st.Br[gi][k2], st.Bi[gi][k2], st.Ar[gi][7 - k2], st.Ai[gi][7 - k2], c,
+                           post);
+      }
+    }
+  }
+}
+
+// phase E2 (cosine): X_1 plus the preceding segments' totals, odd outputs
+template <class G, class Post>
+KFBI_HD void phase_e2_cos(const State<G>& st, float* s, const float* tot, const float* x1v, int a, int c,
+                          const Post& post) {
+  constexpr int P = G::P, RS = G::RS, W = G::W;
+  float off = x1v[c];
+  for (int b = 0; b < a; ++b) off += tot[b * W + c];
+#pragma unroll
+  for (int i = 0; i < P; ++i) {
+    const int j = 2 * (a * P + i) + 1;
+    s[j * RS + c] = post(j, st.v[i] + off);
+  }
+}
+
 #ifdef __CUDACC__
 // The whole transform of the tile s[N][RS] (rows 1..N-1 in and out, row 0
 // holds 0) by 256 threads.  ex aliases s (N * W floats), tot holds 8 * 32
@@ -428,6 +549,29 @@ __device__ __forceinline__ void dst1_tile_reg(float* s, const float* sinv, const
   phase_e1<G>(st, s, tot, a, c);
   __syncthreads();
   phase_e2<G>(st, s, tot, a, c, post);
+  __syncthreads();
+}
+
+// The cosine transform of the tile s[N + 1][RS] (rows 0..N in and out) by
+// 256 threads; ex aliases rows 0..N-1, tot holds 8 * 32 floats, x1v 32.
+template <class G, class Post = Identity>
+__device__ __forceinline__ void dct1_tile_reg(float* s, const float* sinv, const cf2* tw2, float* tot, float* x1v,
+                                              const Post& post = Post()) {
+  const int a = threadIdx.x >> 5, c = threadIdx.x & 31;
+  State<G> st;
+  cf2* ex = reinterpret_cast<cf2*>(s);
+  phase_a1_cos<G>(st, s, sinv, tw2, tot, a, c);
+  __syncthreads();
+  phase_a2<G>(st, ex, a, c);
+  __syncthreads();
+  phase_x1<G>(tot, x1v, a, c);
+  phase_c<G>(st, ex, a, c);
+  __syncthreads();
+  phase_d_cos<G>(st, s, tw2, a, c, post);
+  __syncthreads();
+  phase_e1<G>(st, s, tot, a, c);
+  __syncthreads();
+  phase_e2_cos<G>(st, s, tot, x1v, a, c, post);
   __syncthreads();
 }
 #endif
