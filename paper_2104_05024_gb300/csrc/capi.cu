@@ -344,7 +344,7 @@ int refined_solve(kfbi_handle* h, const double* src, double alpha, const double*
   const int rounds = refine_rounds(h);
   for (int r = 0; r < rounds; ++r) {
     SolveArgs sr;
-    if (r == 0 && !neumann_box(h)) {
+    if (r == 0) {
       // u is exactly the float32 grid of the solve just done: float-float
       // residual, float32 result
       if ((rc = launch_residual_ff(h, src, alpha, corr, h->w.grid32, u, lambda, h->w.res32))) return rc;

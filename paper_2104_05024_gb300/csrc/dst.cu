@@ -1388,6 +1388,7 @@ __device__ __forceinline__ void dct_tile(typename C::T* s, const typename C::T* 
 // (all interior) are listed per interior x-line in the interior numbering.
 template <typename T, int N, int DIM>
 __global__ void __launch_bounds__(NT) k_nxfwd(T* __restrict__ a, const double* __restrict__ src, double alpha,
+                                              const float* __restrict__ src32,
                                               const double* __restrict__ corr, const int32_t* __restrict__ irr,
                                               const int32_t* __restrict__ line_start, const T* __restrict__ tw_g,
                                               const int* __restrict__ skip) {
@@ -1409,7 +1410,10 @@ __global__ void __launch_bounds__(NT) k_nxfwd(T* __restrict__ a, const double* _
   for (int idx = threadIdx.x; idx < P * W; idx += NT) {
     const int x = idx % P, c = idx / P, y = y0 + c;
     T v = (T)0;
-    if (src != nullptr && y <= N) v = (T)(alpha * src[plane + (size_t)y * P + x]);
+    if (y <= N) {
+      if (src != nullptr) v = (T)(alpha * src[plane + (size_t)y * P + x]);
+      else if (src32 != nullptr) v = (T)src32[plane + (size_t)y * P + x];
+    }
     s[x * RS + c] = v;
   }
   __syncthreads();
@@ -1541,7 +1545,8 @@ int run_solve_neumann(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1
     if ((rc = prep(k_nstrided<T, N, false, 3>, smem))) return rc;
     if ((rc = prep(k_nstrided<T, N, true, 3>, smem))) return rc;
     if ((rc = prep(k_nxinv<T, N, 3>, smem))) return rc;
-    k_nxfwd<T, N, 3><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.corr, t.irr, t.line_start, tw, h->skip);
+    k_nxfwd<T, N, 3><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.src32, sa.corr, t.irr, t.line_start, tw,
+                                                h->skip);
     k_nstrided<T, N, false, 3><<<grid, NT, smem, st>>>(work, P, PP, mu1, lam, scale, tw, h->skip);
     k_nstrided<T, N, true, 3><<<grid, NT, smem, st>>>(work, PP, P, mu1, lam, scale, tw, h->skip, rinv);
     k_nstrided<T, N, false, 3><<<grid, NT, smem, st>>>(work, P, PP, mu1, lam, scale, tw, h->skip);
@@ -1552,7 +1557,8 @@ int run_solve_neumann(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1
     if ((rc = prep(k_nxfwd<T, N, 2>, smem))) return rc;
     if ((rc = prep(k_nstrided<T, N, true, 2>, smem))) return rc;
     if ((rc = prep(k_nxinv<T, N, 2>, smem))) return rc;
-    k_nxfwd<T, N, 2><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.corr, t.irr, t.line_start, tw, h->skip);
+    k_nxfwd<T, N, 2><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.src32, sa.corr, t.irr, t.line_start, tw,
+                                                h->skip);
     k_nstrided<T, N, true, 2><<<grid, NT, smem, st>>>(work, P, 0, mu1, lam, scale, tw, h->skip, rinv);
     k_nxinv<T, N, 2><<<grid, NT, smem, st>>>(work, sa.keep || sa.out_user == nullptr, sa.out_user, sa.aux, sa.beta,
                                               sa.gamma, tw, h->skip);
@@ -1565,10 +1571,6 @@ template <typename T>
 int box_solve_neumann(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1, const T* tw) {
   if (!(sa.lambda > 0.0)) {
     set_error("the Neumann box needs lambda > 0 (no Green's function of the Poisson operator exists)");
-    return KFBI_ERR_ARG;
-  }
-  if (sa.src32 != nullptr) {
-    set_error("the Neumann box takes float64 sources");
     return KFBI_ERR_ARG;
   }
   switch (h->grid.N) {

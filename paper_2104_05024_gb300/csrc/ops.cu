@@ -216,6 +216,73 @@ __global__ void k_residual_irr(GridParams gr, Tables t, const double* __restrict
   res[f] = (float)(a + corr[i] - (nb * ih2 + diag * u[f]));
 }
 
+// the float-float residual on the Neumann box's field layout: u32 is the
+// float32 work grid itself (all (N+1)^d nodes), a neighbour beyond the box
+// its mirror image
+__global__ void k_residual_ff_neumann(GridParams gr, const float* __restrict__ u32, float ih2_hi, float ih2_lo,
+                                      float dg_hi, float dg_lo, const double* __restrict__ src, float al_hi,
+                                      float al_lo, float* __restrict__ res) {
+  const int P = gr.N + 1;
+  const int y = blockIdx.x, z = blockIdx.y;
+  const int64_t PP = (int64_t)P * P;
+  const int64_t base = (int64_t)z * PP + (int64_t)y * P;
+  const int64_t ym = y > 0 ? -P : P, yp = y < P - 1 ? P : -P;
+  const int64_t zm = z > 0 ? -PP : PP, zp = z < P - 1 ? PP : -PP;
+  for (int x = threadIdx.x; x < P; x += blockDim.x) {
+    const int64_t f = base + x;
+    const float uc = u32[f];
+    float sm = u32[f + (x > 0 ? -1 : 1)], e = 0.0f, t;
+    two_sum(sm, u32[f + (x < P - 1 ? 1 : -1)], sm, t);
+    e += t;
+    two_sum(sm, u32[f + ym], sm, t);
+    e += t;
+    two_sum(sm, u32[f + yp], sm, t);
+    e += t;
+    if (gr.dim == 3) {
+      two_sum(sm, u32[f + zm], sm, t);
+      e += t;
+      two_sum(sm, u32[f + zp], sm, t);
+      e += t;
+    }
+    float p1, e1, p2, e2, hsum, e3;
+    two_prod(ih2_hi, sm, p1, e1);
+    e1 += ih2_hi * e + ih2_lo * sm;
+    two_prod(dg_hi, uc, p2, e2);
+    e2 += dg_lo * uc;
+    two_sum(p1, p2, hsum, e3);
+    const float lo = e1 + e2 + e3;
+    if (src != nullptr) {
+      const double sv = src[f];
+      const float sh = (float)sv, sl = (float)(sv - (double)sh);
+      float q, eq, h2, e4;
+      two_prod(al_hi, sh, q, eq);
+      eq += al_hi * sl + al_lo * sh;
+      two_sum(q, -hsum, h2, e4);
+      res[f] = h2 + (e4 + eq - lo);
+    } else {
+      res[f] = -(hsum + lo);
+    }
+  }
+}
+
+// the irregular nodes of the Neumann box in float64 (interior nodes: no
+// mirrored neighbour)
+__global__ void k_residual_irr_neumann(GridParams gr, Tables t, const double* __restrict__ corr,
+                                       const double* __restrict__ u, double lambda, const double* __restrict__ src,
+                                       double alpha, float* __restrict__ res) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.n_irr) return;
+  const int P = gr.N + 1;
+  const double ih2 = 1.0 / (gr.h * gr.h);
+  const double diag = -2.0 * gr.dim * ih2 - lambda;
+  const int64_t f = t.irr_user[i];
+  const int64_t PP = (int64_t)P * P;
+  double nb = u[f - 1] + u[f + 1] + u[f - P] + u[f + P];
+  if (gr.dim == 3) nb += u[f - PP] + u[f + PP];
+  const double a = src != nullptr ? alpha * src[f] : 0.0;
+  res[f] = (float)(a + corr[i] - (nb * ih2 + diag * u[f]));
+}
+
 __global__ void k_scatter_add(Tables t, const double* __restrict__ corr, double* __restrict__ g) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < t.n_irr) g[t.irr_user[i]] += corr[i];
@@ -852,11 +919,20 @@ int launch_residual_ff(kfbi_handle* h, const double* src, double alpha, const do
   const float ih2_hi = (float)ih2, dg_hi = (float)dg;
   const float ih2_lo = (float)(ih2 - (double)ih2_hi), dg_lo = (float)(dg - (double)dg_hi);
   const float al_hi = (float)alpha, al_lo = (float)(alpha - (double)al_hi);
-  k_residual_ff<<<dim3(n1, h->grid.dim == 3 ? n1 : 1), 128, 0, h->stream>>>(h->grid, u32, ih2_hi, ih2_lo, dg_hi,
-                                                                             dg_lo, src, al_hi, al_lo, res);
-  if (corr != nullptr && h->t.n_irr > 0)
-    k_residual_irr<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->grid, h->t, corr, u64, lambda, src, alpha,
-                                                                    res);
+  if (h->grid.bc == KFBI_BOX_NEUMANN) {
+    const int P = h->grid.N + 1;
+    k_residual_ff_neumann<<<dim3(P, h->grid.dim == 3 ? P : 1), 128, 0, h->stream>>>(
+        h->grid, u32, ih2_hi, ih2_lo, dg_hi, dg_lo, src, al_hi, al_lo, res);
+    if (corr != nullptr && h->t.n_irr > 0)
+      k_residual_irr_neumann<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->grid, h->t, corr, u64, lambda, src,
+                                                                              alpha, res);
+  } else {
+    k_residual_ff<<<dim3(n1, h->grid.dim == 3 ? n1 : 1), 128, 0, h->stream>>>(h->grid, u32, ih2_hi, ih2_lo, dg_hi,
+                                                                               dg_lo, src, al_hi, al_lo, res);
+    if (corr != nullptr && h->t.n_irr > 0)
+      k_residual_irr<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->grid, h->t, corr, u64, lambda, src, alpha,
+                                                                      res);
+  }
   KFBI_CHECK_LAUNCH_N(corr != nullptr && h->t.n_irr > 0 ? 2 : 1);
   return KFBI_OK;
 }
