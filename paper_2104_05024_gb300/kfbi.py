@@ -267,7 +267,10 @@ class KFBI:
 
     geom: any object with dim, kind, params, nodes [M, dim] and, in 3-D, tri,
     cube_n, cube_t and components (map_type, axes, vert_offset, n_vert,
-    tri_offset) -- e.g. kfbi_workloads.geometry.Geometry."""
+    tri_offset) -- e.g. kfbi_workloads.geometry.Geometry; kind MESH3 needs
+    only nodes and tri (a closed, outward-wound triangle mesh).
+    grid: dim, N, lo, hi and optionally bc ("dirichlet" or "neumann": the box
+    condition; Neumann-box fields hold all (N+1)^dim nodes)."""
 
     def __init__(self, geom, grid, sigma_i=1.0, sigma_e=2.0, dt=0.05, precision=FP64, solver=GMRES, tol=1e-10,
                  restart=50, max_iter=500, gamma=0.8, lo=-1.0, hi=1.0, warm=WARM_PREVIOUS, D_i=None, D_e=None):
