@@ -1116,12 +1116,13 @@ int run_pass(kfbi_handle* h, int pass, double lambda, T* work, const T* mu1, con
 // conductivities (Section 5.2, Eq. FDE),
 //   [A_i - kappa, kappa; kappa, A_e - kappa] (v_i, v_e) = (r_i, r_e),
 //   A_c = sum_a d_c,a mu1(p_a),
-// scaled by (2/N)^d, then the inverse DST of both tiles.  The mode sums and
-// the 2 x 2 solve are float64 for both element types.
+// scaled by (2/N)^d, then the inverse DST of both tiles.  The solve takes
+// its three factors per mode (v_i = f0 r_i + f1 r_e, v_e = f1 r_i + f2 r_e)
+// from a table built once per kappa in float64 (k_cpl_factors).
 template <typename T, int N, int DIM>
 __global__ void __launch_bounds__(NT) k_strided_coupled(T* __restrict__ a, T* __restrict__ b, size_t row_stride,
-                                                        size_t plane_stride, int qoff, const double* __restrict__ mu1,
-                                                        Coupling cp, const T* __restrict__ tw_g,
+                                                        size_t plane_stride, int qoff, const T* __restrict__ cf,
+                                                        size_t cf_stride, const T* __restrict__ tw_g,
                                                         const int* __restrict__ skip) {
   using C = Cfg<T, N>;
   constexpr int W = C::W, RS = C::RS;
@@ -1148,23 +1149,15 @@ __global__ void __launch_bounds__(NT) k_strided_coupled(T* __restrict__ a, T* __
   __syncthreads();
   dst_tile<C>(sa, tw, sinv, tot);
   dst_tile<C>(sb, tw, sinv, tot);
-  const double muq = DIM == 3 ? mu1[q] : 0.0;
-  const double kap = cp.kappa;
+  // table row of this plane: modes (q, k, p), p fastest
+  const T* f0 = cf + (size_t)q * N * N + x0;
   for (int idx = threadIdx.x; idx < N * W; idx += NT) {
-    const int c = idx % W, k = idx / W, p = x0 + c;
-    double vi = 0.0, ve = 0.0;
-    if (k > 0 && p > 0) {
-      // modes: x = p; 3-D y = plane q, z = k; 2-D y = k
-      const double mx = mu1[p], my = DIM == 3 ? muq : mu1[k], mz = DIM == 3 ? mu1[k] : 0.0;
-      const double ai = cp.di[0] * mx + cp.di[1] * my + cp.di[2] * mz - kap;
-      const double ae = cp.de[0] * mx + cp.de[1] * my + cp.de[2] * mz - kap;
-      const double sc = cp.scale / (ai * ae - kap * kap);
-      const double ri = (double)sa[k * RS + c], re = (double)sb[k * RS + c];
-      vi = (ae * ri - kap * re) * sc;
-      ve = (ai * re - kap * ri) * sc;
-    }
-    sa[k * RS + c] = (T)vi;
-    sb[k * RS + c] = (T)ve;
+    const int c = idx % W, k = idx / W;
+    const size_t o = (size_t)k * N + c;
+    const T g0 = f0[o], g1 = f0[o + cf_stride], g2 = f0[o + 2 * cf_stride];
+    const T ri = sa[k * RS + c], re = sb[k * RS + c];
+    sa[k * RS + c] = g0 * ri + g1 * re;
+    sb[k * RS + c] = g1 * ri + g2 * re;
   }
   __syncthreads();
   dst_tile<C>(sa, tw, sinv, tot);
@@ -1174,6 +1167,59 @@ __global__ void __launch_bounds__(NT) k_strided_coupled(T* __restrict__ a, T* __
     ba[(size_t)k * row_stride + c] = sa[k * RS + c];
     bb[(size_t)k * row_stride + c] = sb[k * RS + c];
   }
+}
+
+// factors of the per-mode 2 x 2 solve over the mode grid (q, k, p) of the
+// middle pass (3-D: y = q, z = k; 2-D: y = k, q = 0), x = p:
+//   [A_i - kappa, kappa; kappa, A_e - kappa]^{-1} scale
+//     = (scale / det) [A_e - kappa, -kappa; -kappa, A_i - kappa],
+//   A_c = sum_a d_c,a mu1(p_a), det = (A_i - kappa)(A_e - kappa) - kappa^2,
+// computed in float64 and stored as T (0 for the absent sine modes)
+template <typename T>
+__global__ void k_cpl_factors(const double* __restrict__ mu1, Coupling cp, int N, int dim, T* __restrict__ cf,
+                              int64_t total) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(i % N), k = (int)((i / N) % N), q = (int)(i / ((int64_t)N * N));
+    double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    if (k > 0 && p > 0 && (dim == 2 || q > 0)) {
+      const double mx = mu1[p], my = dim == 3 ? mu1[q] : mu1[k], mz = dim == 3 ? mu1[k] : 0.0;
+      const double ai = cp.di[0] * mx + cp.di[1] * my + cp.di[2] * mz - cp.kappa;
+      const double ae = cp.de[0] * mx + cp.de[1] * my + cp.de[2] * mz - cp.kappa;
+      const double sc = cp.scale / (ai * ae - cp.kappa * cp.kappa);
+      g0 = ae * sc;
+      g1 = -cp.kappa * sc;
+      g2 = ai * sc;
+    }
+    cf[i] = (T)g0;
+    cf[i + total] = (T)g1;
+    cf[i + 2 * total] = (T)g2;
+  }
+}
+
+// the handle's factor table of element type T for this kappa (built when
+// kappa changes)
+template <typename T>
+const T* coupled_factors(kfbi_handle* h, const Coupling& cp, int N, int64_t total) {
+  T** tab;
+  double* kap;
+  if constexpr (sizeof(T) == 8) {
+    tab = &h->cpl64;
+    kap = &h->cpl64_kappa;
+  } else {
+    tab = &h->cpl32;
+    kap = &h->cpl32_kappa;
+  }
+  if (*tab == nullptr) {
+    if (dalloc(h, tab, (size_t)(3 * total)) != KFBI_OK) return nullptr;
+    *kap = std::nan("");
+  }
+  if (!(*kap == cp.kappa)) {
+    const int nb = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    k_cpl_factors<T><<<nb, 256, 0, h->stream>>>(h->t.mu, cp, N, h->grid.dim, *tab, total);
+    KFBI_COUNT(1);
+    *kap = cp.kappa;
+  }
+  return *tab;
 }
 
 // the coupled box solve on two padded grids of element type T: x forward
@@ -1190,11 +1236,16 @@ int run_solve_coupled(kfbi_handle* h, const SolveArgs& si, const SolveArgs& se, 
   const int dim = h->grid.dim;
   cudaStream_t st = h->stream;
   const Tables& t = h->t;
-  const double* mu1 = t.mu;
   Coupling cp = cp0;
   cp.scale = dim == 3 ? (2.0 / N) * (2.0 / N) * (2.0 / N) : (2.0 / N) * (2.0 / N);
   int rc;
   const dim3 grid(N / W, dim == 3 ? N - 1 : 1);
+  const int64_t total = dim == 3 ? (int64_t)N * N * N : (int64_t)N * N;
+  const T* cf = coupled_factors<T>(h, cp, N, total);
+  if (cf == nullptr) {
+    set_error("allocation of the coupled solve's factor table failed");
+    return KFBI_ERR_OOM;
+  }
   if (dim == 3) {
     if ((rc = prep(k_xfwd<T, N, 3>, smem))) return rc;
     if ((rc = prep(k_strided_coupled<T, N, 3>, smem2))) return rc;
@@ -1205,7 +1256,7 @@ int run_solve_coupled(kfbi_handle* h, const SolveArgs& si, const SolveArgs& se, 
     const size_t NN = (size_t)N * N;
     for (T* w : {wa, wb})
       k_strided<T, N, false, 3><<<grid, NT, smem, st>>>(w, N, NN, 1, mu1T, (T)0, (T)1, tw, h->skip);
-    k_strided_coupled<T, N, 3><<<grid, NT, smem2, st>>>(wa, wb, NN, N, 1, mu1, cp, tw, h->skip);
+    k_strided_coupled<T, N, 3><<<grid, NT, smem2, st>>>(wa, wb, NN, N, 1, cf, (size_t)total, tw, h->skip);
     for (T* w : {wa, wb})
       k_strided<T, N, false, 3><<<grid, NT, smem, st>>>(w, N, NN, 1, mu1T, (T)0, (T)1, tw, h->skip);
     k_xinv<T, N, 3><<<grid, NT, smem, st>>>(wa, si.keep || si.out_user == nullptr, si.out_user, si.aux, si.beta,
@@ -1218,7 +1269,7 @@ int run_solve_coupled(kfbi_handle* h, const SolveArgs& si, const SolveArgs& se, 
     if ((rc = prep(k_xinv<T, N, 2>, smem))) return rc;
     k_xfwd<T, N, 2><<<grid, NT, smem, st>>>(wa, si.src, si.alpha, nullptr, si.corr, t.irr, t.line_start, tw, h->skip);
     k_xfwd<T, N, 2><<<grid, NT, smem, st>>>(wb, se.src, se.alpha, nullptr, se.corr, t.irr, t.line_start, tw, h->skip);
-    k_strided_coupled<T, N, 2><<<grid, NT, smem2, st>>>(wa, wb, N, 0, 0, mu1, cp, tw, h->skip);
+    k_strided_coupled<T, N, 2><<<grid, NT, smem2, st>>>(wa, wb, N, 0, 0, cf, (size_t)total, tw, h->skip);
     k_xinv<T, N, 2><<<grid, NT, smem, st>>>(wa, si.keep || si.out_user == nullptr, si.out_user, si.aux, si.beta,
                                              si.gamma, tw, h->skip);
     k_xinv<T, N, 2><<<grid, NT, smem, st>>>(wb, se.keep || se.out_user == nullptr, se.out_user, se.aux, se.beta,

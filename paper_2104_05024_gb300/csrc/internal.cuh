@@ -232,6 +232,11 @@ struct kfbi_handle {
   double* rinv64 = nullptr;
   double rinv_lambda = 0.0;
   bool rinv_ok = false;
+  // coupled solves: the per-mode 2 x 2 solve factors for the kappa they were
+  // built for, one table per element type (3 N^dim values each)
+  double* cpl64 = nullptr;
+  float* cpl32 = nullptr;
+  double cpl64_kappa = 0.0, cpl32_kappa = 0.0;
   // device flag handed to the launches of a Krylov iteration enqueued ahead
   // of the host's convergence test (nullptr otherwise)
   const int* skip = nullptr;

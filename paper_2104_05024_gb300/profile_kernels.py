@@ -1,7 +1,7 @@
 """Launch the hot-path kernels of one workload a few times each, for ncu.
 
     python -m paper_2104_05024_gb300.profile_kernels [--N 256] [--precision fp64|mixed] [--reps 3] [--passes-only]
-        [--box neumann] [--mesh]
+        [--box neumann] [--mesh] [--coupled]
 
 Sets up the prolate-shell workload (configs 2/3 geometry), then runs each
 transform pass of the box solver, one irregular-node correction and one
@@ -9,8 +9,10 @@ interface-limit gather `reps` times on the library's stream, and with
 --strang one Strang step of the bidomain model (reactions, refinement
 residuals, GMRES).  --box neumann runs `reps` float64 box solves of the
 Neumann box (all (N+1)^3 nodes) instead; --mesh hands the shell over as a
-bare triangle mesh, so the handle's creation runs the mesh setup kernels.
-No timing is reported: this only gives a profiler a short, representative
+bare triangle mesh, so the handle's creation runs the mesh setup kernels;
+--coupled runs `reps` Strang steps of the anisotropic coupled system (the
+paper's conductivities, Example 3's sphere) in the given precision with the
+history projection.  No timing is reported: this only gives a profiler a short, representative
 launch list.
 """
 from __future__ import annotations
@@ -38,7 +40,20 @@ def main():
     ap.add_argument("--passes-only", action="store_true", help="only the four transform passes (no A psi)")
     ap.add_argument("--box", default="dirichlet", choices=["dirichlet", "neumann"])
     ap.add_argument("--mesh", action="store_true", help="the shell as a bare triangle mesh")
+    ap.add_argument("--coupled", action="store_true", help="coupled Strang steps on the sphere")
     a = ap.parse_args()
+    if a.coupled:
+        from kfbi_workloads import geometry as G
+        geom, grid = G.sphere3(0.9, C.surface_res(a.N)), C.Grid(3, a.N)
+        h = K.KFBI(geom, grid, D_i=(30.0, 5.0, 5.0), D_e=(20.0, 10.0, 10.0), dt=0.05, tol=1e-8,
+                   precision=K.FP64 if a.precision == "fp64" else K.MIXED, warm=K.WARM_PROJECTION)
+        dev = torch.device("cuda:0")
+        V = torch.tensor(C.ball_stimulus(grid, (0.8, 0.0, 0.0), 0.1), device=dev)
+        w = torch.zeros_like(V)
+        h.bidomain_step(C.FHN_CONFIG, V, w, None, nsteps=a.reps)
+        torch.cuda.synchronize()
+        print("ok")
+        return
     prec = K.FP64 if a.precision == "fp64" else K.MIXED
     geom, grid, cfg, V0, w0 = C.config2(N=a.N, bc=a.box)
     if a.mesh:
