@@ -191,26 +191,35 @@ int refined_solve_coupled(kfbi_handle* h, double kappa, const double* src_i, dou
   si.alpha = a_i;
   si.corr = corr_i;
   si.out_user = ui;
-  si.keep = false;
   se.src = src_e;
   se.alpha = a_e;
   se.corr = corr_e;
   se.out_user = ue;
-  se.keep = false;
+  // the float grids keep the solution for the first round's float-float
+  // residual
   int rc = box_solve_coupled32(h, si, se, cp, h->w.grid32, h->w.grid32b);
   if (rc) return rc;
   const int rounds = refine_rounds(h);
   for (int r = 0; r < rounds; ++r) {
-    if ((rc = launch_residual_coupled(h, src_i, a_i, src_e, a_e, corr_i, corr_e, ui, ue, kappa, h->w.res64,
-                                      h->w.res64b)))
-      return rc;
     SolveArgs ri, re;
-    ri.src = h->w.res64;
+    if (r == 0) {
+      // (u_i, u_e) is exactly the pair of float grids just solved
+      if ((rc = launch_residual_ff_coupled(h, src_i, a_i, src_e, a_e, corr_i, corr_e, ui, ue, kappa, h->w.res32,
+                                           h->w.res32b)))
+        return rc;
+      ri.src32 = h->w.res32;
+      re.src32 = h->w.res32b;
+    } else {
+      if ((rc = launch_residual_coupled(h, src_i, a_i, src_e, a_e, corr_i, corr_e, ui, ue, kappa, h->w.res64,
+                                        h->w.res64b)))
+        return rc;
+      ri.src = h->w.res64;
+      re.src = h->w.res64b;
+    }
     ri.out_user = ui;
     ri.aux = ui;
     ri.gamma = 1.0;
     ri.keep = false;
-    re.src = h->w.res64b;
     re.out_user = ue;
     re.aux = ue;
     re.gamma = 1.0;
@@ -903,6 +912,7 @@ static int create_impl(const kfbi_geometry* geom, const kfbi_grid* grid, double 
     }
     for (double** p : {&h->w.u64b, &h->w.vV64b, &h->w.res64b})
       if ((rc = dalloc(h, p, (size_t)grid_points(h)))) return fail(rc);
+    if ((rc = dalloc(h, &h->w.res32b, (size_t)grid_points(h)))) return fail(rc);
   }
   if ((rc = dalloc(h, &h->w.vecs, (size_t)(m + 1) * M))) return fail(rc);
   if ((rc = dalloc(h, &h->w.small, (size_t)small_size(MAX_RESTART)))) return fail(rc);

@@ -1251,8 +1251,8 @@ int run_solve_coupled(kfbi_handle* h, const SolveArgs& si, const SolveArgs& se, 
     if ((rc = prep(k_strided_coupled<T, N, 3>, smem2))) return rc;
     if ((rc = prep(k_xinv<T, N, 3>, smem))) return rc;
     if ((rc = prep(k_strided<T, N, false, 3>, smem))) return rc;
-    k_xfwd<T, N, 3><<<grid, NT, smem, st>>>(wa, si.src, si.alpha, nullptr, si.corr, t.irr, t.line_start, tw, h->skip);
-    k_xfwd<T, N, 3><<<grid, NT, smem, st>>>(wb, se.src, se.alpha, nullptr, se.corr, t.irr, t.line_start, tw, h->skip);
+    k_xfwd<T, N, 3><<<grid, NT, smem, st>>>(wa, si.src, si.alpha, si.src32, si.corr, t.irr, t.line_start, tw, h->skip);
+    k_xfwd<T, N, 3><<<grid, NT, smem, st>>>(wb, se.src, se.alpha, se.src32, se.corr, t.irr, t.line_start, tw, h->skip);
     const size_t NN = (size_t)N * N;
     for (T* w : {wa, wb})
       k_strided<T, N, false, 3><<<grid, NT, smem, st>>>(w, N, NN, 1, mu1T, (T)0, (T)1, tw, h->skip);
@@ -1267,8 +1267,8 @@ int run_solve_coupled(kfbi_handle* h, const SolveArgs& si, const SolveArgs& se, 
     if ((rc = prep(k_xfwd<T, N, 2>, smem))) return rc;
     if ((rc = prep(k_strided_coupled<T, N, 2>, smem2))) return rc;
     if ((rc = prep(k_xinv<T, N, 2>, smem))) return rc;
-    k_xfwd<T, N, 2><<<grid, NT, smem, st>>>(wa, si.src, si.alpha, nullptr, si.corr, t.irr, t.line_start, tw, h->skip);
-    k_xfwd<T, N, 2><<<grid, NT, smem, st>>>(wb, se.src, se.alpha, nullptr, se.corr, t.irr, t.line_start, tw, h->skip);
+    k_xfwd<T, N, 2><<<grid, NT, smem, st>>>(wa, si.src, si.alpha, si.src32, si.corr, t.irr, t.line_start, tw, h->skip);
+    k_xfwd<T, N, 2><<<grid, NT, smem, st>>>(wb, se.src, se.alpha, se.src32, se.corr, t.irr, t.line_start, tw, h->skip);
     k_strided_coupled<T, N, 2><<<grid, NT, smem2, st>>>(wa, wb, N, 0, 0, cf, (size_t)total, tw, h->skip);
     k_xinv<T, N, 2><<<grid, NT, smem, st>>>(wa, si.keep || si.out_user == nullptr, si.out_user, si.aux, si.beta,
                                              si.gamma, tw, h->skip);

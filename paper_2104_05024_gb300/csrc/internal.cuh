@@ -192,6 +192,7 @@ struct Workspace {
   // coupled float32 forms: the second float grid and the extracellular
   // counterparts of u64 / vV64 / res64
   float* grid32b = nullptr;
+  float* res32b = nullptr;
   double* u64b = nullptr;
   double* vV64b = nullptr;
   double* res64b = nullptr;
@@ -330,6 +331,9 @@ int launch_residual(kfbi_handle* h, const double* src, double alpha, const doubl
 // padded float32 grid u32 (the output of a float32 solve) and by u64 on the
 // user layout; float-float arithmetic away from the interface, float64 at
 // irregular nodes
+int launch_residual_ff_coupled(kfbi_handle* h, const double* src_i, double a_i, const double* src_e, double a_e,
+                               const double* corr_i, const double* corr_e, const double* ui, const double* ue,
+                               double kappa, float* ri, float* re);
 int launch_residual_ff(kfbi_handle* h, const double* src, double alpha, const double* corr, const float* u32,
                        const double* u64, double lambda, float* res);
 int launch_lincomb(kfbi_handle* h, double* y, double a, const double* x, double b, int64_t n);

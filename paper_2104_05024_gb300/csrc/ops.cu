@@ -984,42 +984,62 @@ int launch_rank_one_coupled(kfbi_handle* h, const double* psi, double* out, doub
 //   r_i = a_i src_i - (sum_a d_i,a (u_i(+e_a) - 2 u_i + u_i(-e_a)) / h^2 - kappa (u_i - u_e)),
 //   r_e = a_e src_e - (sum_a d_e,a (...) / h^2 + kappa (u_i - u_e));
 // the corrections are added by a scatter afterwards.  One block row per
-// (y, z) grid line.
-__global__ void k_residual_coupled(GridParams gr, Coupling cp, const double* __restrict__ src_i, double a_i,
+// (y, z) grid line.  The conductivities come pre-scaled by 1/h^2 (ci, ce)
+// with the diagonals dgi = -2 sum ci - kappa, dge likewise.
+struct CoupledStencil {
+  double ci[3], ce[3], dgi, dge, kappa;
+};
+
+__device__ __forceinline__ double stencil_axes(const double* __restrict__ v, int64_t f, int x, int y, int z, int n1,
+                                               int64_t s, int dim, double c0, double c1, double c2) {
+  double acc = c0 * ((x > 0 ? v[f - 1] : 0.0) + (x < n1 - 1 ? v[f + 1] : 0.0));
+  acc = fma(c1, (y > 0 ? v[f - n1] : 0.0) + (y < n1 - 1 ? v[f + n1] : 0.0), acc);
+  if (dim == 3) acc = fma(c2, (z > 0 ? v[f - s] : 0.0) + (z < n1 - 1 ? v[f + s] : 0.0), acc);
+  return acc;
+}
+
+__global__ void k_residual_coupled(GridParams gr, CoupledStencil cs, const double* __restrict__ src_i, double a_i,
                                    const double* __restrict__ src_e, double a_e, const double* __restrict__ ui,
                                    const double* __restrict__ ue, double* __restrict__ ri, double* __restrict__ re) {
   const int n1 = gr.N - 1;
-  const double ih2 = 1.0 / (gr.h * gr.h);
   const int y = blockIdx.x, z = blockIdx.y;
   const int64_t s = (int64_t)n1 * n1;
   const int64_t base = (int64_t)z * s + (int64_t)y * n1;
-  const double* u[2] = {ui, ue};
-  const double* dd[2] = {cp.di, cp.de};
   for (int x = threadIdx.x; x < n1; x += blockDim.x) {
     const int64_t f = base + x;
-    double Lc[2];
-    for (int c = 0; c < 2; ++c) {
-      const double* v = u[c];
-      const double vc = v[f];
-      double acc = dd[c][0] * ((x > 0 ? v[f - 1] : 0.0) + (x < n1 - 1 ? v[f + 1] : 0.0) - 2.0 * vc);
-      acc += dd[c][1] * ((y > 0 ? v[f - n1] : 0.0) + (y < n1 - 1 ? v[f + n1] : 0.0) - 2.0 * vc);
-      if (gr.dim == 3) acc += dd[c][2] * ((z > 0 ? v[f - s] : 0.0) + (z < n1 - 1 ? v[f + s] : 0.0) - 2.0 * vc);
-      Lc[c] = acc * ih2;
-    }
-    const double w = cp.kappa * (ui[f] - ue[f]);
-    ri[f] = (src_i != nullptr ? a_i * src_i[f] : 0.0) - (Lc[0] - w);
-    re[f] = (src_e != nullptr ? a_e * src_e[f] : 0.0) - (Lc[1] + w);
+    const double vi = ui[f], ve = ue[f];
+    double Li = stencil_axes(ui, f, x, y, z, n1, s, gr.dim, cs.ci[0], cs.ci[1], cs.ci[2]);
+    double Le = stencil_axes(ue, f, x, y, z, n1, s, gr.dim, cs.ce[0], cs.ce[1], cs.ce[2]);
+    Li = fma(cs.dgi, vi, fma(cs.kappa, ve, Li));
+    Le = fma(cs.dge, ve, fma(cs.kappa, vi, Le));
+    ri[f] = (src_i != nullptr ? a_i * src_i[f] : 0.0) - Li;
+    re[f] = (src_e != nullptr ? a_e * src_e[f] : 0.0) - Le;
   }
+}
+
+CoupledStencil coupled_stencil(const kfbi_handle* h, double kappa) {
+  CoupledStencil cs;
+  const double ih2 = 1.0 / (h->grid.h * h->grid.h);
+  double si = 0.0, se = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const bool on = a < h->grid.dim;
+    cs.ci[a] = on ? h->cpl.di[a] * ih2 : 0.0;
+    cs.ce[a] = on ? h->cpl.de[a] * ih2 : 0.0;
+    si += cs.ci[a];
+    se += cs.ce[a];
+  }
+  cs.dgi = -2.0 * si - kappa;
+  cs.dge = -2.0 * se - kappa;
+  cs.kappa = kappa;
+  return cs;
 }
 
 int launch_residual_coupled(kfbi_handle* h, const double* src_i, double a_i, const double* src_e, double a_e,
                             const double* corr_i, const double* corr_e, const double* ui, const double* ue,
                             double kappa, double* ri, double* re) {
   const int n1 = h->grid.N - 1;
-  Coupling cp = h->cpl;
-  cp.kappa = kappa;
-  k_residual_coupled<<<dim3(n1, h->grid.dim == 3 ? n1 : 1), 256, 0, h->stream>>>(h->grid, cp, src_i, a_i, src_e, a_e,
-                                                                                  ui, ue, ri, re);
+  k_residual_coupled<<<dim3(n1, h->grid.dim == 3 ? n1 : 1), 256, 0, h->stream>>>(
+      h->grid, coupled_stencil(h, kappa), src_i, a_i, src_e, a_e, ui, ue, ri, re);
   int n = 1;
   if (h->t.n_irr > 0) {
     if (corr_i) {
@@ -1030,6 +1050,140 @@ int launch_residual_coupled(kfbi_handle* h, const double* src_i, double a_i, con
       k_scatter_add<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->t, corr_e, re);
       ++n;
     }
+  }
+  KFBI_CHECK_LAUNCH_N(n);
+  return KFBI_OK;
+}
+
+// float pair (hi + lo) of a float64 constant
+struct FPair {
+  float hi, lo;
+};
+FPair fpair(double v) {
+  const float hi = (float)v;
+  return {hi, (float)(v - (double)hi)};
+}
+
+struct CoupledStencilFF {
+  FPair ci[3], ce[3], dgi, dge, kappa, ai, ae;
+};
+
+// (acc, lo) += (c.hi + c.lo)(s + e) in float-float arithmetic
+__device__ __forceinline__ void ff_mac(float& acc, float& lo, FPair c, float s, float e) {
+  float p, ep, t;
+  two_prod(c.hi, s, p, ep);
+  ep = fmaf(c.hi, e, fmaf(c.lo, s, ep));
+  two_sum(acc, p, acc, t);
+  lo += t + ep;
+}
+
+// (s, e) = a + b exactly
+__device__ __forceinline__ void ff_pair(float a, float b, float& s, float& e) { two_sum(a, b, s, e); }
+
+// one component's L u in float-float from the padded float grid u (index 0
+// of each axis the zero boundary value), plus kappa times the other
+// component's value uo at the node
+__device__ __forceinline__ void coupled_L_ff(const float* __restrict__ u, size_t p, int x, int y, int z, int n1,
+                                             int N, size_t NN, int dim, const FPair* c, FPair dg, FPair kap,
+                                             float uo, float& acc, float& lo) {
+  float s, e;
+  acc = 0.0f;
+  lo = 0.0f;
+  ff_pair(u[p - 1], x < n1 - 1 ? u[p + 1] : 0.0f, s, e);
+  ff_mac(acc, lo, c[0], s, e);
+  ff_pair(u[p - N], y < n1 - 1 ? u[p + N] : 0.0f, s, e);
+  ff_mac(acc, lo, c[1], s, e);
+  if (dim == 3) {
+    ff_pair(u[p - NN], z < n1 - 1 ? u[p + NN] : 0.0f, s, e);
+    ff_mac(acc, lo, c[2], s, e);
+  }
+  ff_mac(acc, lo, dg, u[p], 0.0f);
+  ff_mac(acc, lo, kap, uo, 0.0f);
+}
+
+// r = a src - L u as a float (the float64 source split into a float pair)
+__device__ __forceinline__ float ff_residual(const double* __restrict__ src, size_t f, FPair al, float acc, float lo) {
+  if (src == nullptr) return -(acc + lo);
+  const double sv = src[f];
+  const float sh = (float)sv, sl = (float)(sv - (double)sh);
+  float q, eq, h2, e4;
+  two_prod(al.hi, sh, q, eq);
+  eq = fmaf(al.hi, sl, fmaf(al.lo, sh, eq));
+  two_sum(q, -acc, h2, e4);
+  return h2 + (e4 + eq - lo);
+}
+
+// The coupled residual of a first refinement round, when (u_i, u_e) is
+// exactly the pair of padded float grids of the float32 coupled solve just
+// done: float-float arithmetic as in the scalar case (the float64 pipe is
+// 1/64 of the float32 rate here), float32 result.  The irregular nodes are
+// redone in float64 with their corrections by k_residual_irr_coupled.
+__global__ void k_residual_ff_coupled(GridParams gr, CoupledStencilFF cs, const float* __restrict__ ui32,
+                                      const float* __restrict__ ue32, const double* __restrict__ src_i,
+                                      const double* __restrict__ src_e, float* __restrict__ ri,
+                                      float* __restrict__ re) {
+  const int N = gr.N, n1 = N - 1;
+  const int y = blockIdx.x, z = blockIdx.y;
+  const size_t NN = (size_t)N * N;
+  const size_t pbase = gr.dim == 3 ? (size_t)(z + 1) * NN + (size_t)(y + 1) * N : (size_t)(y + 1) * N;
+  const size_t ubase = gr.dim == 3 ? ((size_t)z * n1 + y) * n1 : (size_t)y * n1;
+  for (int x = threadIdx.x; x < n1; x += blockDim.x) {
+    const size_t p = pbase + x + 1;
+    const float vi = ui32[p], ve = ue32[p];
+    float acc, lo;
+    coupled_L_ff(ui32, p, x, y, z, n1, N, NN, gr.dim, cs.ci, cs.dgi, cs.kappa, ve, acc, lo);
+    ri[ubase + x] = ff_residual(src_i, ubase + x, cs.ai, acc, lo);
+    coupled_L_ff(ue32, p, x, y, z, n1, N, NN, gr.dim, cs.ce, cs.dge, cs.kappa, vi, acc, lo);
+    re[ubase + x] = ff_residual(src_e, ubase + x, cs.ae, acc, lo);
+  }
+}
+
+// the irregular nodes of the coupled residual in float64 from the float64
+// copies of (u_i, u_e), with their corrections
+__global__ void k_residual_irr_coupled(GridParams gr, Tables t, CoupledStencil cs, const double* __restrict__ corr_i,
+                                       const double* __restrict__ corr_e, const double* __restrict__ ui,
+                                       const double* __restrict__ ue, const double* __restrict__ src_i, double a_i,
+                                       const double* __restrict__ src_e, double a_e, float* __restrict__ ri,
+                                       float* __restrict__ re) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.n_irr) return;
+  const int n1 = gr.N - 1;
+  const int64_t f = t.irr[i];
+  const int64_t s = (int64_t)n1 * n1;
+  const int x = (int)(f % n1), y = (int)((f / n1) % n1), z = gr.dim == 3 ? (int)(f / s) : 0;
+  const double vi = ui[f], ve = ue[f];
+  double Li = stencil_axes(ui, f, x, y, z, n1, s, gr.dim, cs.ci[0], cs.ci[1], cs.ci[2]);
+  double Le = stencil_axes(ue, f, x, y, z, n1, s, gr.dim, cs.ce[0], cs.ce[1], cs.ce[2]);
+  Li = fma(cs.dgi, vi, fma(cs.kappa, ve, Li));
+  Le = fma(cs.dge, ve, fma(cs.kappa, vi, Le));
+  const double bi = (src_i != nullptr ? a_i * src_i[f] : 0.0) + (corr_i != nullptr ? corr_i[i] : 0.0);
+  const double be = (src_e != nullptr ? a_e * src_e[f] : 0.0) + (corr_e != nullptr ? corr_e[i] : 0.0);
+  ri[f] = (float)(bi - Li);
+  re[f] = (float)(be - Le);
+}
+
+int launch_residual_ff_coupled(kfbi_handle* h, const double* src_i, double a_i, const double* src_e, double a_e,
+                               const double* corr_i, const double* corr_e, const double* ui, const double* ue,
+                               double kappa, float* ri, float* re) {
+  const int n1 = h->grid.N - 1;
+  const CoupledStencil cs = coupled_stencil(h, kappa);
+  CoupledStencilFF cf;
+  for (int a = 0; a < 3; ++a) {
+    cf.ci[a] = fpair(cs.ci[a]);
+    cf.ce[a] = fpair(cs.ce[a]);
+  }
+  cf.dgi = fpair(cs.dgi);
+  cf.dge = fpair(cs.dge);
+  cf.kappa = fpair(kappa);
+  cf.ai = fpair(a_i);
+  cf.ae = fpair(a_e);
+  k_residual_ff_coupled<<<dim3(n1, h->grid.dim == 3 ? n1 : 1), 128, 0, h->stream>>>(
+      h->grid, cf, h->w.grid32, h->w.grid32b, src_i, src_e, ri, re);
+  int n = 1;
+  if (h->t.n_irr > 0 && (corr_i != nullptr || corr_e != nullptr)) {
+    k_residual_irr_coupled<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->grid, h->t, cs, corr_i, corr_e, ui, ue,
+                                                                            src_i, a_i, src_e, a_e, ri, re);
+    ++n;
   }
   KFBI_CHECK_LAUNCH_N(n);
   return KFBI_OK;
