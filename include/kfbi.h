@@ -251,9 +251,13 @@ int kfbi_bidomain_step_stim(kfbi_handle* h, const kfbi_fhn* p, const double* ist
  * term (1, 1) <(ds, ds), psi> / (2 |Gamma|) (ds as at kfbi_solve_neumann);
  * Phi_i and Phi_e are then fixed up to that common constant's choice, their
  * difference is unique.  opts.precision KFBI_FP64 (float64 throughout) or
- * KFBI_MIXED (float32 transforms inside GMRES with the float64 2 x 2 mode
- * solve, float64 Arnoldi, and refinement of the float64 coupled residual
- * for g, the outer residuals and the final potentials).  Dirichlet box only.
+ * KFBI_MIXED (float32 transforms inside GMRES, float64 Arnoldi, and
+ * refinement of the coupled residual, its first round in float-float
+ * arithmetic, for g, the outer residuals and the final potentials).  The
+ * 2 x 2 mode solve multiplies by three factors per mode, computed in float64
+ * once per kappa into a device table of 3 N^dim values of the transform's
+ * type that the handle allocates on first use and frees at kfbi_destroy.
+ * Dirichlet box only.
  * ------------------------------------------------------------------ */
 /* Setup as kfbi_create for the coupled system; D_i, D_e: dim positive
  * conductivities each (host).  bidomain_step and kfbi_bidomain_step_stim on
