@@ -341,6 +341,41 @@ struct DivPost {
   }
 };
 
+// ------------------------------------------ programmatic dependent launch
+// The float32 transform passes are launched with programmatic stream
+// serialization: a pass may start while the one before it in the stream is
+// still finishing, load its constant tables (twiddles, sines, mu1: written
+// once at setup), and then wait in pdl_wait() until that predecessor has
+// completed and its writes are visible.  Everything else a pass reads (the
+// grid, sources, corrections, the skip flag, mode-factor tables) is read
+// after the wait.  pdl_launch_next() lets the next pass launch: persistent
+// passes call it after their wait (their blocks are all resident), the
+// others at the end of each block, so a waiting successor never takes an SM
+// from blocks of its predecessor that have not started.  Without the launch
+// attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename K, typename... Args>
+cudaError_t launch_pdl(K kernel, dim3 grid, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(NT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+int launch_failed(const char* what) {
+  set_error("launch of the %s failed: %s", what, cudaGetErrorString(cudaGetLastError()));
+  return KFBI_ERR_CUDA;
+}
+
 // ------------------------------------------------------------- x forward
 // Tile: W consecutive lines y0..y0+W-1 of plane z; assembles
 // r = alpha*src + corrections on the fly.
@@ -357,10 +392,10 @@ __global__ void __launch_bounds__(NT) k_xfwd(T* __restrict__ a, const double* __
   T* tot = s + N * RS;
   T* tw = tot + C::G * W;
   T* sinv = tw + 4 * N;
-  const bool skipped = skip != nullptr && *skip != 0;  // read early, tested after the table loads
   load_twiddles<T, N>(tw, tw_g);
   load_sines<T, N>(sinv, tw_g);
-  if (skipped) return;
+  pdl_wait();
+  if (skip != nullptr && *skip != 0) return;
   const int y0 = blockIdx.x * W;
   const int z = DIM == 3 ? blockIdx.y + 1 : 0;
   // the branch on src stays outside the loops: inside, the compiler
@@ -406,6 +441,7 @@ __global__ void __launch_bounds__(NT) k_xfwd(T* __restrict__ a, const double* __
   }
   __syncthreads();
   dst_tile<C>(s, tw, sinv, tot);
+  pdl_launch_next();
   const size_t plane = (size_t)z * N * N;
   for (int idx = threadIdx.x; idx < N * W; idx += NT) {
     const int x = idx % N, c = idx / N;
@@ -425,9 +461,10 @@ __global__ void __launch_bounds__(NT) k_xinv(T* __restrict__ a, bool keep, doubl
   T* tot = s + N * RS;
   T* tw = tot + C::G * W;
   T* sinv = tw + 4 * N;
-  if (skip != nullptr && *skip != 0) return;
   load_twiddles<T, N>(tw, tw_g);
   load_sines<T, N>(sinv, tw_g);
+  pdl_wait();
+  if (skip != nullptr && *skip != 0) return;
   const int y0 = blockIdx.x * W;
   const int z = DIM == 3 ? blockIdx.y + 1 : 0;
   const size_t plane = (size_t)z * N * N;
@@ -438,6 +475,7 @@ __global__ void __launch_bounds__(NT) k_xinv(T* __restrict__ a, bool keep, doubl
   copy_async_wait();
   __syncthreads();
   dst_tile<C>(s, tw, sinv, tot);
+  pdl_launch_next();
   if (out == nullptr) {
     if (keep)
       for (int idx = threadIdx.x; idx < N * W; idx += NT) {
@@ -478,10 +516,10 @@ __global__ void __launch_bounds__(NT) k_strided(T* __restrict__ a, size_t row_st
   T* tot = s + N * RS;
   T* tw = tot + C::G * W;
   T* sinv = tw + 4 * N;
-  const bool skipped = skip != nullptr && *skip != 0;
   load_twiddles<T, N>(tw, tw_g);
   load_sines<T, N>(sinv, tw_g);
-  if (skipped) return;
+  pdl_wait();
+  if (skip != nullptr && *skip != 0) return;
   const int x0 = blockIdx.x * W;
   const int q = blockIdx.y + qoff;
   T* base = a + (size_t)q * plane_stride + x0;
@@ -517,6 +555,7 @@ __global__ void __launch_bounds__(NT) k_strided(T* __restrict__ a, size_t row_st
       dst1_tile<C>(s, tw, tot);
     }
   }
+  pdl_launch_next();
   for (int idx = threadIdx.x; idx < N * W; idx += NT) {
     const int c = idx % W, k = idx / W;
     base[(size_t)k * row_stride + c] = s[k * RS + c];
@@ -606,20 +645,21 @@ __global__ void __launch_bounds__(NT, tma_blocks<SOLVE>()) k_strided_tma(const _
   float* sinv = tw + 4 * N;
   float* mus = sinv + N;
   uint64_t* bar = reinterpret_cast<uint64_t*>(mus + N);
-  // an iteration enqueued ahead of the convergence test: nothing to do (the
-  // flag is read early and tested before any copy is issued)
-  const bool skipped = skip != nullptr && *skip != 0;
   for (int i = threadIdx.x; i < 4 * N; i += NT) tw[i] = tw_g[i];
   for (int i = threadIdx.x; i < N; i += NT) {
     sinv[i] = tw_g[2 * i + 1];
     mus[i] = mu1[i];
   }
-  if (skipped) return;
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     mbar_fence_init();
   }
+  pdl_wait();
+  // an iteration enqueued ahead of the convergence test: nothing to do (the
+  // flag is tested before any copy is issued)
+  if (skip != nullptr && *skip != 0) return;
+  pdl_launch_next();
   __syncthreads();
   auto coords = [&](int t, int& x, int& y, int& z) {
     const int q = t / NX + 1;
@@ -901,25 +941,38 @@ int launch_strided3(kfbi_handle* h, int mode, bool solve, T* work, const T* mu1,
     if (h->tma) {
       constexpr size_t smem = tma_smem_bytes<N>();
       const CUtensorMap& map = mode == 0 ? h->tmap_y32 : h->tmap_z32;
-      int dev = 0, sms = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       const int tiles = (N / TMA_W) * (N - 1);
-      const int nb = (solve ? tma_blocks<true>() : tma_blocks<false>()) * sms;
+      const int nb = (solve ? tma_blocks<true>() : tma_blocks<false>()) * h->sms;
       const int grid = tiles < nb ? tiles : nb;
+      cudaError_t e;
       if (solve) {
         if ((rc = prep(k_strided_tma<N, true>, smem))) return rc;
-        k_strided_tma<N, true><<<grid, NT, smem, st>>>(map, mode, mu1, lam, scale, tw, h->w.err, 2, h->skip);
+        e = launch_pdl(k_strided_tma<N, true>, dim3(grid), smem, st, map, mode, mu1, lam, scale, tw, h->w.err, 2,
+                       (const int*)h->skip);
       } else {
         if ((rc = prep(k_strided_tma<N, false>, smem))) return rc;
-        k_strided_tma<N, false><<<grid, NT, smem, st>>>(map, mode, mu1, lam, scale, tw, h->w.err, 1, h->skip);
+        e = launch_pdl(k_strided_tma<N, false>, dim3(grid), smem, st, map, mode, mu1, lam, scale, tw, h->w.err, 1,
+                       (const int*)h->skip);
       }
-      return KFBI_OK;
+      return e == cudaSuccess ? KFBI_OK : launch_failed("TMA strided pass");
     }
   }
   const size_t smem = C::smem_elems * sizeof(T);
   const size_t NN = (size_t)N * N;
   dim3 grid(N / C::W, N - 1);
+  if constexpr (sizeof(T) == 4) {
+    cudaError_t e;
+    if (solve) {
+      if ((rc = prep(k_strided<T, N, true, 3>, smem))) return rc;
+      e = launch_pdl(k_strided<T, N, true, 3>, grid, smem, st, work, (size_t)(mode == 0 ? N : NN),
+                     (size_t)(mode == 0 ? NN : N), 1, mu1, lam, scale, tw, (const int*)h->skip, rinv);
+    } else {
+      if ((rc = prep(k_strided<T, N, false, 3>, smem))) return rc;
+      e = launch_pdl(k_strided<T, N, false, 3>, grid, smem, st, work, (size_t)(mode == 0 ? N : NN),
+                     (size_t)(mode == 0 ? NN : N), 1, mu1, lam, scale, tw, (const int*)h->skip, (const T*)nullptr);
+    }
+    return e == cudaSuccess ? KFBI_OK : launch_failed("strided pass");
+  }
   if (solve) {
     if ((rc = prep(k_strided<T, N, true, 3>, smem))) return rc;
     k_strided<T, N, true, 3><<<grid, NT, smem, st>>>(work, mode == 0 ? N : NN, mode == 0 ? NN : N, 1, mu1, lam,
@@ -1014,14 +1067,27 @@ int run_solve(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1, const 
     }
     const T* rinv = mode_factors<T, N>(h, sa.lambda, (double)scale);
     if ((rc = prep(k_xfwd<T, N, 3>, smem))) return rc;
-    k_xfwd<T, N, 3><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.src32, sa.corr, t.irr, t.line_start, tw,
-                                             h->skip);
+    if ((rc = prep(k_xinv<T, N, 3>, smem))) return rc;
+    if constexpr (sizeof(T) == 4) {
+      // float32: the five passes chained by programmatic dependent launch
+      if (launch_pdl(k_xfwd<T, N, 3>, grid, smem, st, work, sa.src, sa.alpha, sa.src32, sa.corr,
+                     (const int32_t*)t.irr, (const int32_t*)t.line_start, tw, (const int*)h->skip) != cudaSuccess)
+        return launch_failed("x forward pass");
+    } else {
+      k_xfwd<T, N, 3><<<grid, NT, smem, st>>>(work, sa.src, sa.alpha, sa.src32, sa.corr, t.irr, t.line_start, tw,
+                                               h->skip);
+    }
     if ((rc = launch_strided3<T, N>(h, 0, false, work, mu1, lam, scale, tw))) return rc;
     if ((rc = launch_strided3<T, N>(h, 1, true, work, mu1, lam, scale, tw, rinv))) return rc;
     if ((rc = launch_strided3<T, N>(h, 0, false, work, mu1, lam, scale, tw))) return rc;
-    if ((rc = prep(k_xinv<T, N, 3>, smem))) return rc;
-    k_xinv<T, N, 3><<<grid, NT, smem, st>>>(work, sa.keep || sa.out_user == nullptr, sa.out_user, sa.aux, sa.beta,
-                                             sa.gamma, tw, h->skip);
+    if constexpr (sizeof(T) == 4) {
+      if (launch_pdl(k_xinv<T, N, 3>, grid, smem, st, work, sa.keep || sa.out_user == nullptr, sa.out_user,
+                     (const double*)sa.aux, sa.beta, sa.gamma, tw, (const int*)h->skip) != cudaSuccess)
+        return launch_failed("x inverse pass");
+    } else {
+      k_xinv<T, N, 3><<<grid, NT, smem, st>>>(work, sa.keep || sa.out_user == nullptr, sa.out_user, sa.aux, sa.beta,
+                                               sa.gamma, tw, h->skip);
+    }
   } else {
     dim3 grid(N / W, 1);
     const T* rinv = mode_factors<T, N>(h, sa.lambda, (double)scale);
@@ -1645,6 +1711,13 @@ int box_solve_neumann(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1
 // 32 <= N <= 256): boxes of 32 x-values by N rows along y or along z.
 int make_tma_maps(kfbi_handle* h) {
   h->tma = false;
+  {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+      h->sms = sms;
+    cudaGetLastError();
+  }
   const int N = h->grid.N;
   if (h->grid.dim != 3 || N < TMA_W || N > 256) return KFBI_OK;
   void* fn = nullptr;

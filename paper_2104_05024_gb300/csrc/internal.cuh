@@ -227,6 +227,7 @@ struct kfbi_handle {
   // TMA descriptors of the float32 padded grid: [N x 32] tiles along y and z
   CUtensorMap tmap_y32, tmap_z32;
   bool tma = false;
+  int sms = 152;                  // the device's multiprocessor count (persistent grids)
   bool xy_fused = false;          // float32 3-D solves use the cluster-fused x-y passes
   // float64 solves: the mode factors scale / mu_p for the lambda they were
   // built for (rinv_ok: the handle may allocate the table; set at creation)
