@@ -373,8 +373,8 @@ NCU_DRAM_BYTES = {
     # ncu captures each launch cold (caches flushed before it), so at 256^3
     # every pass reads the grid from DRAM once; back-to-back passes in the
     # timed region find it in L2 (the cold-capture bytes go with solve_ms_cold)
-    (256, 4, False): {0: 4.74e6, 1: 70.3e6, 2: 70.8e6, 3: 71.5e6},
-    (512, 4, False): {0: 472.7e6, 1: 1007.1e6, 2: 1007.2e6, 3: 1006.6e6},
+    (256, 4, False): {0: 4.62e6, 1: 70.2e6, 2: 70.65e6, 3: 71.3e6},
+    (512, 4, False): {0: 473.1e6, 1: 1007.06e6, 2: 1007.27e6, 3: 1006.37e6},
 }
 
 

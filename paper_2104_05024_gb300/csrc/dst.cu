@@ -341,41 +341,6 @@ struct DivPost {
   }
 };
 
-// ------------------------------------------ programmatic dependent launch
-// The float32 transform passes are launched with programmatic stream
-// serialization: a pass may start while the one before it in the stream is
-// still finishing, load its constant tables (twiddles, sines, mu1: written
-// once at setup), and then wait in pdl_wait() until that predecessor has
-// completed and its writes are visible.  Everything else a pass reads (the
-// grid, sources, corrections, the skip flag, mode-factor tables) is read
-// after the wait.  pdl_launch_next() lets the next pass launch: persistent
-// passes call it after their wait (their blocks are all resident), the
-// others at the end of each block, so a waiting successor never takes an SM
-// from blocks of its predecessor that have not started.  Without the launch
-// attribute both are no-ops.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
-template <typename K, typename... Args>
-cudaError_t launch_pdl(K kernel, dim3 grid, size_t smem, cudaStream_t st, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = dim3(NT, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, args...);
-}
-
-int launch_failed(const char* what) {
-  set_error("launch of the %s failed: %s", what, cudaGetErrorString(cudaGetLastError()));
-  return KFBI_ERR_CUDA;
-}
-
 // ------------------------------------------------------------- x forward
 // Tile: W consecutive lines y0..y0+W-1 of plane z; assembles
 // r = alpha*src + corrections on the fly.
@@ -947,12 +912,12 @@ int launch_strided3(kfbi_handle* h, int mode, bool solve, T* work, const T* mu1,
       cudaError_t e;
       if (solve) {
         if ((rc = prep(k_strided_tma<N, true>, smem))) return rc;
-        e = launch_pdl(k_strided_tma<N, true>, dim3(grid), smem, st, map, mode, mu1, lam, scale, tw, h->w.err, 2,
-                       (const int*)h->skip);
+        e = launch_pdl(k_strided_tma<N, true>, dim3(grid), dim3(NT), smem, st, map, mode, mu1, lam, scale, tw,
+                       h->w.err, 2, (const int*)h->skip);
       } else {
         if ((rc = prep(k_strided_tma<N, false>, smem))) return rc;
-        e = launch_pdl(k_strided_tma<N, false>, dim3(grid), smem, st, map, mode, mu1, lam, scale, tw, h->w.err, 1,
-                       (const int*)h->skip);
+        e = launch_pdl(k_strided_tma<N, false>, dim3(grid), dim3(NT), smem, st, map, mode, mu1, lam, scale, tw,
+                       h->w.err, 1, (const int*)h->skip);
       }
       return e == cudaSuccess ? KFBI_OK : launch_failed("TMA strided pass");
     }
@@ -964,11 +929,11 @@ int launch_strided3(kfbi_handle* h, int mode, bool solve, T* work, const T* mu1,
     cudaError_t e;
     if (solve) {
       if ((rc = prep(k_strided<T, N, true, 3>, smem))) return rc;
-      e = launch_pdl(k_strided<T, N, true, 3>, grid, smem, st, work, (size_t)(mode == 0 ? N : NN),
+      e = launch_pdl(k_strided<T, N, true, 3>, grid, dim3(NT), smem, st, work, (size_t)(mode == 0 ? N : NN),
                      (size_t)(mode == 0 ? NN : N), 1, mu1, lam, scale, tw, (const int*)h->skip, rinv);
     } else {
       if ((rc = prep(k_strided<T, N, false, 3>, smem))) return rc;
-      e = launch_pdl(k_strided<T, N, false, 3>, grid, smem, st, work, (size_t)(mode == 0 ? N : NN),
+      e = launch_pdl(k_strided<T, N, false, 3>, grid, dim3(NT), smem, st, work, (size_t)(mode == 0 ? N : NN),
                      (size_t)(mode == 0 ? NN : N), 1, mu1, lam, scale, tw, (const int*)h->skip, (const T*)nullptr);
     }
     return e == cudaSuccess ? KFBI_OK : launch_failed("strided pass");
@@ -1070,7 +1035,7 @@ int run_solve(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1, const 
     if ((rc = prep(k_xinv<T, N, 3>, smem))) return rc;
     if constexpr (sizeof(T) == 4) {
       // float32: the five passes chained by programmatic dependent launch
-      if (launch_pdl(k_xfwd<T, N, 3>, grid, smem, st, work, sa.src, sa.alpha, sa.src32, sa.corr,
+      if (launch_pdl(k_xfwd<T, N, 3>, grid, dim3(NT), smem, st, work, sa.src, sa.alpha, sa.src32, sa.corr,
                      (const int32_t*)t.irr, (const int32_t*)t.line_start, tw, (const int*)h->skip) != cudaSuccess)
         return launch_failed("x forward pass");
     } else {
@@ -1081,7 +1046,7 @@ int run_solve(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1, const 
     if ((rc = launch_strided3<T, N>(h, 1, true, work, mu1, lam, scale, tw, rinv))) return rc;
     if ((rc = launch_strided3<T, N>(h, 0, false, work, mu1, lam, scale, tw))) return rc;
     if constexpr (sizeof(T) == 4) {
-      if (launch_pdl(k_xinv<T, N, 3>, grid, smem, st, work, sa.keep || sa.out_user == nullptr, sa.out_user,
+      if (launch_pdl(k_xinv<T, N, 3>, grid, dim3(NT), smem, st, work, sa.keep || sa.out_user == nullptr, sa.out_user,
                      (const double*)sa.aux, sa.beta, sa.gamma, tw, (const int*)h->skip) != cudaSuccess)
         return launch_failed("x inverse pass");
     } else {

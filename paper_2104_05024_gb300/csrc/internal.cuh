@@ -26,6 +26,43 @@ constexpr int DEVERR_TIMEOUT = 8;   // a bounded wait on a TMA transfer gave up
 
 void set_error(const char* fmt, ...);
 
+// Programmatic dependent launch.  The hot kernels of a solve and of a
+// Krylov iteration are launched with programmatic stream serialization: a
+// kernel may start while the one before it in the stream is still
+// finishing, load its constant tables (twiddles, sines, mu1: written once at
+// setup), and then wait in pdl_wait() until that predecessor has completed
+// and its writes are visible.  Everything else it touches (grids, vectors,
+// sources, corrections, the skip flag, mode-factor tables) it reads or
+// writes only after the wait.  pdl_launch_next() lets the next kernel launch:
+// kernels whose blocks are all resident at once (persistent passes, the
+// single-wave Krylov and gather kernels) call it right after their wait,
+// multi-wave passes at the end of each block, so a waiting successor never
+// takes an SM from blocks of its predecessor that have not started.  Without
+// the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename K, typename... Args>
+cudaError_t launch_pdl(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// error status of a failed launch (reads and clears the launch error)
+inline int launch_failed(const char* what) {
+  set_error("launch of the %s failed: %s", what, cudaGetErrorString(cudaGetLastError()));
+  return KFBI_ERR_CUDA;
+}
+
 // kernels launched by this library (instrumentation for benchmarks)
 extern std::atomic<long long> g_launches;
 #define KFBI_COUNT(n) (::kfbi::g_launches.fetch_add((n), std::memory_order_relaxed))

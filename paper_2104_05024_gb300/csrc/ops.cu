@@ -23,6 +23,8 @@ constexpr int ARN_BLOCKS = KFBI_ARN_BLOCKS;
 // crossing rows concatenated, built at setup: two dependent loads per entry)
 __global__ void k_correction(Tables t, const double* __restrict__ x, double* __restrict__ corr,
                              const int* __restrict__ skip) {
+  pdl_wait();
+  pdl_launch_next();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= t.n_irr || (skip != nullptr && *skip)) return;
   const int k0 = t.cr_ptr[i], k1 = t.cr_ptr[i + 1];
@@ -50,6 +52,8 @@ template <typename T>
 __global__ void k_limit(Tables t, GridParams gr, const T* __restrict__ grid, const double* __restrict__ x,
                         const double* __restrict__ base, double sgn, double* __restrict__ out,
                         const int* __restrict__ skip) {
+  pdl_wait();
+  pdl_launch_next();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= t.M || (skip != nullptr && *skip)) return;
   const int d = gr.dim, P = work_n(gr);
@@ -424,6 +428,8 @@ __global__ void k_axpby(double* __restrict__ y, double a, const double* __restri
 
 __global__ void k_scale_norm(double* __restrict__ v, const double* __restrict__ w, const double* __restrict__ nrm2, int n,
                              const int* __restrict__ skip) {
+  pdl_wait();
+  pdl_launch_next();
   if (skip != nullptr && *skip) return;
   const double s = sqrt(nrm2[0]);
   const double inv = s > 0.0 ? 1.0 / s : 0.0;
@@ -562,6 +568,8 @@ __global__ void __launch_bounds__(256) k_arn_gs(double* __restrict__ w, const do
                                                 int nv, const double* __restrict__ coef, double* __restrict__ partial,
                                                 unsigned* __restrict__ counter, double* __restrict__ out,
                                                 const int* __restrict__ skip) {
+  pdl_wait();
+  pdl_launch_next();
   if (skip != nullptr && *skip) return;
   __shared__ double cs[MAX_RESTART + 2];
   __shared__ double red[8][MAX_RESTART + 2];
@@ -604,6 +612,8 @@ __global__ void __launch_bounds__(256) k_arn_close(double* __restrict__ w, const
                                                    int nv, double* __restrict__ s, int m, int j,
                                                    double* __restrict__ partial, unsigned* __restrict__ counter,
                                                    double gnorm, double tol, int* stop, const int* skip) {
+  pdl_wait();
+  pdl_launch_next();
   if (skip != nullptr && *skip) return;
   SmallLayout L{m};
   __shared__ double cs[MAX_RESTART + 2];
@@ -848,7 +858,9 @@ int launch_correction(kfbi_handle* h, const double* x, double* corr) { return la
 
 int launch_correction_t(kfbi_handle* h, const Tables& t, const double* x, double* corr) {
   if (t.n_irr == 0) return KFBI_OK;
-  k_correction<<<(t.n_irr + 127) / 128, 128, 0, h->stream>>>(t, x, corr, h->skip);
+  if (launch_pdl(k_correction, dim3((t.n_irr + 127) / 128), dim3(128), 0, h->stream, t, x, corr,
+                 (const int*)h->skip) != cudaSuccess)
+    return launch_failed("correction");
   KFBI_CHECK_LAUNCH();
   return KFBI_OK;
 }
@@ -866,20 +878,26 @@ int launch_limit64(kfbi_handle* h, const double* grid, const double* x, const do
 
 int launch_limit64_t(kfbi_handle* h, const Tables& t, const double* grid, const double* x, const double* base,
                      double sgn, double* out) {
-  k_limit<double><<<(t.M + 127) / 128, 128, 0, h->stream>>>(t, h->grid, grid, x, base, sgn, out, h->skip);
+  if (launch_pdl(k_limit<double>, dim3((t.M + 127) / 128), dim3(128), 0, h->stream, t, h->grid, grid, x, base, sgn,
+                 out, (const int*)h->skip) != cudaSuccess)
+    return launch_failed("interface limit");
   KFBI_CHECK_LAUNCH();
   return KFBI_OK;
 }
 
 int launch_limit32_t(kfbi_handle* h, const Tables& t, const float* grid, const double* x, const double* base,
                      double sgn, double* out) {
-  k_limit<float><<<(t.M + 127) / 128, 128, 0, h->stream>>>(t, h->grid, grid, x, base, sgn, out, h->skip);
+  if (launch_pdl(k_limit<float>, dim3((t.M + 127) / 128), dim3(128), 0, h->stream, t, h->grid, grid, x, base, sgn,
+                 out, (const int*)h->skip) != cudaSuccess)
+    return launch_failed("interface limit");
   KFBI_CHECK_LAUNCH();
   return KFBI_OK;
 }
 
 int launch_limit32(kfbi_handle* h, const float* grid, const double* x, const double* base, double sgn, double* out) {
-  k_limit<float><<<(h->t.M + 127) / 128, 128, 0, h->stream>>>(h->t, h->grid, grid, x, base, sgn, out, h->skip);
+  if (launch_pdl(k_limit<float>, dim3((h->t.M + 127) / 128), dim3(128), 0, h->stream, h->t, h->grid, grid, x, base,
+                 sgn, out, (const int*)h->skip) != cudaSuccess)
+    return launch_failed("interface limit");
   KFBI_CHECK_LAUNCH();
   return KFBI_OK;
 }
@@ -1343,13 +1361,17 @@ int arnoldi_step(kfbi_handle* h, double* V, int ld, double* wv, int j, int m, do
   SmallLayout L{m};
   double* s = h->w.small;
   const int nv = j + 1;
-  k_arn_gs<false><<<nb, 256, 0, h->stream>>>(wv, V, ld, n, nv, nullptr, h->w.partial, h->w.counter, s + L.hcol(),
-                                             h->skip);
-  k_arn_gs<true><<<nb, 256, 0, h->stream>>>(wv, V, ld, n, nv, s + L.hcol(), h->w.partial, h->w.counter, s + L.y(),
-                                            h->skip);
-  k_arn_close<<<nb, 256, 0, h->stream>>>(wv, V, ld, n, nv, s, m, j, h->w.partial, h->w.counter, gnorm, tol, h->w.stop,
-                                         h->skip);
-  k_scale_norm<<<(n + 255) / 256, 256, 0, h->stream>>>(V + (size_t)(j + 1) * ld, wv, s + L.nrm2(), n, h->skip);
+  const int* skip = h->skip;
+  cudaStream_t st = h->stream;
+  if (launch_pdl(k_arn_gs<false>, dim3(nb), dim3(256), 0, st, wv, (const double*)V, ld, n, nv, (const double*)nullptr,
+                 h->w.partial, h->w.counter, s + L.hcol(), skip) != cudaSuccess ||
+      launch_pdl(k_arn_gs<true>, dim3(nb), dim3(256), 0, st, wv, (const double*)V, ld, n, nv,
+                 (const double*)(s + L.hcol()), h->w.partial, h->w.counter, s + L.y(), skip) != cudaSuccess ||
+      launch_pdl(k_arn_close, dim3(nb), dim3(256), 0, st, wv, (const double*)V, ld, n, nv, s, m, j, h->w.partial,
+                 h->w.counter, gnorm, tol, h->w.stop, skip) != cudaSuccess ||
+      launch_pdl(k_scale_norm, dim3((n + 255) / 256), dim3(256), 0, st, V + (size_t)(j + 1) * ld, (const double*)wv,
+                 (const double*)(s + L.nrm2()), n, skip) != cudaSuccess)
+    return launch_failed("Arnoldi step");
   KFBI_CHECK_LAUNCH_N(4);
   return KFBI_OK;
 }
