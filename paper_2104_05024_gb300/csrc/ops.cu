@@ -9,6 +9,7 @@
 //  - extracellular potential with zero mean over Omega.
 #include <cuda_runtime.h>
 
+#include "ffloat.cuh"
 #include "internal.cuh"
 
 namespace kfbi {
@@ -758,51 +759,67 @@ __device__ __forceinline__ bool abs_below(double x, double bound) {
 //   F(v) = v - v0 - c (v (v - theta)(1 - v) - w1(v))
 //        = ((c v - c (1 + theta)) v + (1 + c theta + c k alpha / den)) v + (c w0 / den - v0),
 // c = k H / Cm, den = 1 + k zeta.  Float32 Newton steps first bring v to
-// float32 resolution (error e0 <~ 1e-7 |v|); a float64 step then uses the
-// exact float64 residual with the float32 derivative (a quasi-Newton step:
-// error <~ 1e-7 e0 + C e0^2, about 1e-14), without any float64 division.
-// Converged: the float32 phase converged and that float64 step moved v by
-// less than 1e-5 (so a further step would move it by < 1e-10, the plain
-// Newton criterion); otherwise float64 steps continue until a step is below
-// 1e-10.
-__global__ void k_react_be(kfbi_fhn p, double k, double* __restrict__ V, double* __restrict__ w, int64_t n,
-                           int* err) {
-  const double c = k * p.H / p.Cm;
-  const double den = 1.0 + k * p.zeta;
-  const double inv_den = 1.0 / den;
-  const double ka = k * p.alpha;
-  const double e2 = -c * (1.0 + p.theta), e1 = 1.0 + c * p.theta + c * ka * inv_den, cid = c * inv_den;
-  const double kid = ka * inv_den;
-  const float cf = (float)c, rf = (float)(ka / den), thf = (float)p.theta, kaf = (float)ka, idf = (float)inv_den;
-  const float th1 = 2.0f * (1.0f + thf);
+// float32 resolution (error e0 <~ 1e-7 |v|); one more step then uses the
+// residual F(v_f) evaluated in float-float arithmetic (v0 and w0 split into
+// float pairs on their bits, about 48 significant bits, F to ~1e-14 of its
+// O(1) terms) with the float32 derivative (a quasi-Newton step: error <~
+// 1e-7 e0 + C e0^2 + 1e-14), and w1 is formed as a float pair too.  The
+// state meets float64 arithmetic in three additions only (v1 = v_f - dv as
+// the sum of three exactly widened floats, w1 from its pair).  Converged:
+// the float32 phase converged and the float-float step moved v by less than
+// 1e-5 (so a further step would move it by < 1e-10, the plain Newton
+// criterion); otherwise float64 Newton steps continue from v_f until a step
+// is below 1e-10 (also for inputs outside the pairs' range or not finite).
+struct BeConsts {
+  double c, e2, e1, cid, kid, inv_den;  // float64 fallback
+  float cf, rf, thf, kaf, idf, th1;     // float32 Newton
+  ffl::ff cP, e2P, e1P, cidP, kaP, idP; // float-float residual and w1
+};
+
+__global__ void k_react_be(BeConsts K, double* __restrict__ V, double* __restrict__ w, int64_t n, int* err) {
+  using namespace ffl;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double v0 = V[i], q0 = w[i];
-    const float v0f = (float)v0, q0f = (float)q0;
-    float vf = v0f;
-    for (int it = 0; it < 12; ++it) {
-      const float q1 = (q0f + kaf * vf) * idf;
-      const float Fv = vf - v0f - cf * (vf * (vf - thf) * (1.0f - vf) - q1);
-      const float dF = 1.0f - cf * ((-3.0f * vf + th1) * vf - thf - rf);
-      const float dv = Fv / dF;
-      vf -= dv;
-      if (fabsf(dv) <= 1e-6f * fmaxf(1.0f, fabsf(vf))) break;
-    }
-    bool f32_ok = false;
-    {
-      const float q1 = (q0f + kaf * vf) * idf;
-      const float Fv = vf - v0f - cf * (vf * (vf - thf) * (1.0f - vf) - q1);
-      f32_ok = fabsf(Fv) <= 1e-5f;
-    }
-    const double a0 = fma(cid, q0, -v0);
-    double v = vf;
-    float xf = vf;
+    ff v0p, q0p;
+    double v = v0;
     bool ok = false;
+    if (split(v0, v0p) && split(q0, q0p)) {
+      const float v0f = v0p.h, q0f = q0p.h;
+      float vf = v0f;
+      for (int it = 0; it < 12; ++it) {
+        const float q1 = (q0f + K.kaf * vf) * K.idf;
+        const float Fv = vf - v0f - K.cf * (vf * (vf - K.thf) * (1.0f - vf) - q1);
+        const float dF = 1.0f - K.cf * ((-3.0f * vf + K.th1) * vf - K.thf - K.rf);
+        const float dv = Fv / dF;
+        vf -= dv;
+        if (fabsf(dv) <= 1e-6f * fmaxf(1.0f, fabsf(vf))) break;
+      }
+      const float q1 = (q0f + K.kaf * vf) * K.idf;
+      const bool f32_ok = fabsf(vf - v0f - K.cf * (vf * (vf - K.thf) * (1.0f - vf) - q1)) <= 1e-5f;
+      // F(v_f) = ((c v_f + e2) v_f + e1) v_f + (c w0 / den - v0) on float pairs
+      const ff a0 = add(mul(K.cidP, q0p), neg(v0p));
+      const ff F = add(mul(add(mul(add(mul(K.cP, vf), K.e2P), vf), K.e1P), vf), a0);
+      const float rdF = 1.0f / (1.0f - K.cf * ((-3.0f * vf + K.th1) * vf - K.thf - K.rf));
+      const ff dv = mul(F, rdF);
+      if (f32_ok && fabsf(dv.h) < 1e-5f) {
+        v = (widen(vf) - widen(dv.h)) - widen(dv.l);
+        // w1 = (w0 + k alpha v1) / den with v1 ~ v_f - dv.h (dv.l k alpha is below 1e-19)
+        const ff W = mul(add(q0p, mul(K.kaP, ff{vf, -dv.h})), K.idP);
+        V[i] = v;
+        w[i] = widen(W.h) + widen(W.l);
+        continue;
+      }
+      v = widen(vf);
+    }
+    // float64 Newton steps with the float32 derivative
+    const double a0 = fma(K.cid, q0, -v0);
+    float xf = (float)v;
     for (int it = 0; it < 50; ++it) {
-      const double rdF = (double)(1.0f / (1.0f - cf * ((-3.0f * xf + th1) * xf - thf - rf)));
-      const double F = fma(fma(fma(c, v, e2), v, e1), v, a0);
+      const double rdF = (double)(1.0f / (1.0f - K.cf * ((-3.0f * xf + K.th1) * xf - K.thf - K.rf)));
+      const double F = fma(fma(fma(K.c, v, K.e2), v, K.e1), v, a0);
       const double dv = F * rdF;
       v -= dv;
-      if (abs_below(dv, 1e-10) || (it == 0 && f32_ok && abs_below(dv, 1e-5))) {
+      if (abs_below(dv, 1e-10)) {
         ok = true;
         break;
       }
@@ -810,7 +827,7 @@ __global__ void k_react_be(kfbi_fhn p, double k, double* __restrict__ V, double*
     }
     if (!ok) atomicOr(err, DEVERR_NEWTON);
     V[i] = v;
-    w[i] = fma(kid, v, q0 * inv_den);
+    w[i] = fma(K.kid, v, q0 * K.inv_den);
   }
 }
 
@@ -1394,8 +1411,33 @@ int launch_react_fe(const kfbi_fhn* p, double k, double* V, double* w, int64_t n
   return KFBI_OK;
 }
 
+static ffl::ff to_pair(double x) {
+  const float h = (float)x;
+  return ffl::ff{h, (float)(x - (double)h)};
+}
+
 int launch_react_be(const kfbi_fhn* p, double k, double* V, double* w, int64_t n, int* err, cudaStream_t s) {
-  k_react_be<<<grid_blocks(n, 256), 256, 0, s>>>(*p, k, V, w, n, err);
+  BeConsts K;
+  K.c = k * p->H / p->Cm;
+  const double den = 1.0 + k * p->zeta, ka = k * p->alpha;
+  K.inv_den = 1.0 / den;
+  K.e2 = -K.c * (1.0 + p->theta);
+  K.e1 = 1.0 + K.c * p->theta + K.c * ka * K.inv_den;
+  K.cid = K.c * K.inv_den;
+  K.kid = ka * K.inv_den;
+  K.cf = (float)K.c;
+  K.rf = (float)(ka / den);
+  K.thf = (float)p->theta;
+  K.kaf = (float)ka;
+  K.idf = (float)K.inv_den;
+  K.th1 = 2.0f * (1.0f + K.thf);
+  K.cP = to_pair(K.c);
+  K.e2P = to_pair(K.e2);
+  K.e1P = to_pair(K.e1);
+  K.cidP = to_pair(K.cid);
+  K.kaP = to_pair(ka);
+  K.idP = to_pair(K.inv_den);
+  k_react_be<<<grid_blocks(n, 256), 256, 0, s>>>(K, V, w, n, err);
   KFBI_CHECK_LAUNCH();
   return KFBI_OK;
 }
