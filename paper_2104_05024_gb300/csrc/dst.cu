@@ -32,12 +32,30 @@
 #include <cmath>
 
 #include "dst_reg.cuh"
+#include "ffloat.cuh"
 #include "internal.cuh"
 
 namespace kfbi {
 namespace {
 
 constexpr int NT = 256;
+
+// float64 <-> T for float T on the bit patterns (a float64 conversion
+// instruction costs as much as a float64 add here); identities for double
+template <typename T>
+__device__ __forceinline__ T to_T(double x) {
+  if constexpr (sizeof(T) == 4)
+    return ffl::narrow(x);
+  else
+    return x;
+}
+template <typename T>
+__device__ __forceinline__ double to_double(T v) {
+  if constexpr (sizeof(T) == 4)
+    return ffl::widen(v);
+  else
+    return v;
+}
 
 // Tile geometry: N transform rows by W independent lines, row stride RS
 // (W + 1 pads against bank conflicts of transposed loads; W for dense TMA
@@ -372,7 +390,7 @@ __global__ void __launch_bounds__(NT) k_xfwd(T* __restrict__ a, const double* __
       T v = (T)0;
       if (x > 0 && y > 0) {
         const size_t line = DIM == 3 ? (size_t)(z - 1) * n1 + (y - 1) : (size_t)(y - 1);
-        v = a_t * (T)src[line * n1 + (x - 1)];
+        v = a_t * to_T<T>(src[line * n1 + (x - 1)]);
       }
       s[x * RS + c] = v;
     }
@@ -459,7 +477,7 @@ __global__ void __launch_bounds__(NT) k_xinv(T* __restrict__ a, bool keep, doubl
     if (x > 0 && y > 0) {
       const size_t line = DIM == 3 ? (size_t)(z - 1) * n1 + (y - 1) : (size_t)(y - 1);
       const size_t o = line * n1 + (x - 1);
-      const double bv = (double)(b_t * v);
+      const double bv = to_double(b_t * v);
       out[o] = aux != nullptr ? fma(gamma, aux[o], bv) : bv;
     }
   }
@@ -769,7 +787,7 @@ __global__ void __launch_bounds__(NT) k_xy_fwd(float* __restrict__ a, const doub
     for (int idx = threadIdx.x; idx < N * W; idx += NT) {
       const int x = idx % N, c = idx / N, y = y0 + c;
       float v = 0.0f;
-      if (x > 0 && y > 0) v = a_t * (float)src[((size_t)(z - 1) * n1 + (y - 1)) * n1 + (x - 1)];
+      if (x > 0 && y > 0) v = a_t * ffl::narrow(src[((size_t)(z - 1) * n1 + (y - 1)) * n1 + (x - 1)]);
       sA[x * RS + c] = v;
     }
   } else if (src32 != nullptr) {
@@ -854,7 +872,7 @@ __global__ void __launch_bounds__(NT) k_xy_inv(float* __restrict__ a, bool keep,
     if (keep) a[plane + (size_t)y * N + x] = v;
     if (x > 0 && y > 0) {
       const size_t o = ((size_t)(z - 1) * n1 + (y - 1)) * n1 + (x - 1);
-      const double bv = (double)(b_t * v);
+      const double bv = ffl::widen(b_t * v);
       out[o] = aux != nullptr ? fma(gamma, aux[o], bv) : bv;
     }
   }
@@ -1493,7 +1511,7 @@ __global__ void __launch_bounds__(NT) k_nxfwd(T* __restrict__ a, const double* _
     const int x = idx % P, c = idx / P, y = y0 + c;
     T v = (T)0;
     if (y <= N) {
-      if (src != nullptr) v = (T)(alpha * src[plane + (size_t)y * P + x]);
+      if (src != nullptr) v = (T)alpha * to_T<T>(src[plane + (size_t)y * P + x]);
       else if (src32 != nullptr) v = (T)src32[plane + (size_t)y * P + x];
     }
     s[x * RS + c] = v;
@@ -1554,7 +1572,7 @@ __global__ void __launch_bounds__(NT) k_nxinv(T* __restrict__ a, bool keep, doub
     const T v = s[x * RS + c];
     if (keep) a[o] = v;
     if (out != nullptr) {
-      const double bv = beta * (double)v;
+      const double bv = to_double((T)beta * v);
       out[o] = aux != nullptr ? fma(gamma, aux[o], bv) : bv;
     }
   }

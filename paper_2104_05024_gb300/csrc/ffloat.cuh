@@ -86,7 +86,7 @@ struct ff {
 // x = h + l + r exactly with h the top 24 significant bits of x (truncated),
 // l the remaining 29 bits rounded to 24 significant bits, |r| <= 2^-48 |x|.
 // For |x| < 2^-60 h = l = 0 (absolute error below 8.7e-19).  Returns false
-// for |x| >= 2^100, infinities and NaN (the caller's float64 path).
+// for |x| >= 2^128 (beyond the float range), infinities and NaN.
 FF_HD bool split(double x, ff& out) {
   const uint64_t b = bits64(x);
   const int E = (int)((b >> 52) & 0x7ff);  // biased exponent
@@ -95,7 +95,7 @@ FF_HD bool split(double x, ff& out) {
     out.l = 0.0f;
     return true;
   }
-  if (E >= 1023 + 100) return false;
+  if (E >= 1023 + 128) return false;
   const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
   const uint64_t m = b & 0xFFFFFFFFFFFFFull;  // 52 fraction bits
   // float exponent field E - 1023 + 127; the top 23 fraction bits
@@ -104,6 +104,18 @@ FF_HD bool split(double x, ff& out) {
   const float scale = from_bits32(sign | ((uint32_t)(E - 948) << 23));
   out.l = u29_to_float((uint32_t)(m & 0x1FFFFFFFu)) * scale;
   return true;
+}
+
+// the float nearest to x (from its pair: off by one unit only within 2^-48
+// |x| of a rounding tie; 0 below 2^-60; infinities beyond the float range
+// and for infinite x; NaN for NaN)
+FF_HD float narrow(double x) {
+  ff p;
+  if (split(x, p)) return p.h + p.l;
+  const uint64_t b = bits64(x);
+  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  const bool nan = ((b >> 52) & 0x7ff) == 0x7ff && (b & 0xFFFFFFFFFFFFFull) != 0;
+  return from_bits32(sign | (nan ? 0x7fc00000u : 0x7f800000u));
 }
 
 // the double equal to the float f (subnormal floats, below 2^-126, to zero)

@@ -147,6 +147,20 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
   e = fmaf(a, b, -p);
 }
 
+// a float64 source value as a float pair, split on its bits (a float64
+// conversion costs as much as a float64 add here); sources beyond the float
+// range or not finite become infinities or NaN
+__device__ __forceinline__ void src_pair(double sv, float& sh, float& sl) {
+  ffl::ff p;
+  if (ffl::split(sv, p)) {
+    sh = p.h;
+    sl = p.l;
+  } else {
+    sh = ffl::narrow(sv);
+    sl = 0.0f;
+  }
+}
+
 // r = -L_h u for u given exactly by the padded float32 grid of a float32
 // solve (index 0 of each axis holds the zero boundary value), in float-float
 // arithmetic: the float64 pipe is 1/64 of the float32 rate here, and the
@@ -185,9 +199,10 @@ __global__ void k_residual_ff(GridParams gr, const float* __restrict__ u32, floa
     two_sum(p1, p2, hsum, e3);
     float lo = e1 + e2 + e3;
     if (src != nullptr) {
-      // + alpha * src, src split into a float pair (the only float64 work)
+      // + alpha * src, src split into a float pair on its bits
       const double sv = src[ubase + x];
-      const float sh = (float)sv, sl = (float)(sv - (double)sh);
+      float sh, sl;
+      src_pair(sv, sh, sl);
       float q, eq, h2, e4;
       two_prod(al_hi, sh, q, eq);
       eq += al_hi * sl + al_lo * sh;
@@ -258,7 +273,8 @@ __global__ void k_residual_ff_neumann(GridParams gr, const float* __restrict__ u
     const float lo = e1 + e2 + e3;
     if (src != nullptr) {
       const double sv = src[f];
-      const float sh = (float)sv, sl = (float)(sv - (double)sh);
+      float sh, sl;
+      src_pair(sv, sh, sl);
       float q, eq, h2, e4;
       two_prod(al_hi, sh, q, eq);
       eq += al_hi * sl + al_lo * sh;
@@ -1136,11 +1152,12 @@ __device__ __forceinline__ void coupled_L_ff(const float* __restrict__ u, size_t
   ff_mac(acc, lo, kap, uo, 0.0f);
 }
 
-// r = a src - L u as a float (the float64 source split into a float pair)
+// r = a src - L u as a float (the float64 source split into a float pair on its bits)
 __device__ __forceinline__ float ff_residual(const double* __restrict__ src, size_t f, FPair al, float acc, float lo) {
   if (src == nullptr) return -(acc + lo);
   const double sv = src[f];
-  const float sh = (float)sv, sl = (float)(sv - (double)sh);
+  float sh, sl;
+      src_pair(sv, sh, sl);
   float q, eq, h2, e4;
   two_prod(al.hi, sh, q, eq);
   eq = fmaf(al.hi, sl, fmaf(al.lo, sh, eq));

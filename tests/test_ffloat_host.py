@@ -30,7 +30,8 @@ def _inputs():
     xs = list(rng.uniform(-1.5, 1.5, 4000))
     xs += list(rng.choice([-1.0, 1.0], 4000) * 10.0 ** rng.uniform(-25, 28, 4000))
     xs += [0.0, -0.0, 1.0, -1.0, 0.1, 2.0 ** -60, -(2.0 ** -60), 2.0 ** -61, 2.0 ** -60 * (1 - 2 ** -52),
-           2.0 ** 99 * 1.75, 2.0 ** 100, -(2.0 ** 100), math.inf, -math.inf, math.nan,
+           2.0 ** 99 * 1.75, 2.0 ** 100, -(2.0 ** 100), 2.0 ** 127 * 1.999, 2.0 ** 128, -(2.0 ** 129),
+           1e300, math.inf, -math.inf, math.nan,
            1.0 + 2.0 ** -52, 1.0 - 2.0 ** -53, float.fromhex("0x1.fffffffffffffp-1"),
            float.fromhex("0x1.00000ffffffffp0"), float.fromhex("0x1.000001fffffffp0")]
     return xs
@@ -45,14 +46,22 @@ def test_split_widen_and_products_exact_bounds(harness):
     for x, line in zip(xs, out):
         f = line.split()
         ok = f[0] == "1"
-        h, l, hw, sh, sl, qh, ql, rh, rl = (float.fromhex(t) for t in f[1:])
-        if not math.isfinite(x) or abs(x) >= 2.0 ** 100:
+        h, l, hw, sh, sl, qh, ql, rh, rl, nw = (float.fromhex(t) if t not in ("nan", "-nan") else math.nan
+                                                for t in f[1:])
+        if not math.isfinite(x) or abs(x) >= 2.0 ** 128:
             assert not ok, x
+            # narrowing: infinities, NaN for NaN
+            assert math.isnan(nw) if math.isnan(x) else nw == math.copysign(math.inf, x)
             continue
         assert ok, x
         if abs(x) < 2.0 ** -60:
-            assert h == 0.0 and l == 0.0, x
+            assert h == 0.0 and l == 0.0 and nw == 0.0, x
             continue
+        # narrowing: the nearest float, or a neighbour of it within 2^-48 |x| of a tie
+        if abs(x) < 2.0 ** 127:
+            near = float(np.float32(x))
+            assert nw == near or (abs(Fraction(x) - (Fraction(near) + Fraction(nw)) / 2)
+                                  <= abs(Fraction(x)) * Fraction(1, 2 ** 48)), (x, nw, near)
         X = Fraction(x)
         H, L = Fraction(h), Fraction(l)
         # hi: x truncated to 24 significant bits
