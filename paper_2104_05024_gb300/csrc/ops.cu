@@ -777,18 +777,22 @@ __device__ __forceinline__ bool abs_below(double x, double bound) {
 // c = k H / Cm, den = 1 + k zeta.  Float32 Newton steps first bring v to
 // float32 resolution (error e0 <~ 1e-7 |v|); one more step then uses the
 // residual F(v_f) evaluated in float-float arithmetic (v0 and w0 split into
-// float pairs on their bits, about 48 significant bits, F to ~1e-14 of its
-// O(1) terms) with the float32 derivative (a quasi-Newton step: error <~
-// 1e-7 e0 + C e0^2 + 1e-14), and w1 is formed as a float pair too.  The
-// state meets float64 arithmetic in three additions only (v1 = v_f - dv as
-// the sum of three exactly widened floats, w1 from its pair).  Converged:
-// the float32 phase converged and the float-float step moved v by less than
-// 1e-5 (so a further step would move it by < 1e-10, the plain Newton
-// criterion); otherwise float64 Newton steps continue from v_f until a step
-// is below 1e-10 (also for inputs outside the pairs' range or not finite).
+// float pairs on their bits, about 48 significant bits, F to ~1e-14 of the
+// sum S of its terms' sizes) with the float32 derivative (a quasi-Newton
+// step: error <~ 1e-7 e0 + C e0^2 + 1e-14 S / |F'|), and w1 is formed as a
+// float pair too.  The state meets float64 arithmetic in three additions only
+// (v1 = v_f - dv as the sum of three exactly widened floats, w1 from its
+// pair).  Converged: the float32 phase converged, the float-float step dv is
+// below 1e-5 and small enough that the step's second-order error |F'' / 2F'|
+// dv^2 stays below 1e-13, and S < 8 |F'| (away from a fold of the cubic,
+// where the pairs' error and the float32 derivative's, divided by F', grow);
+// otherwise plain float64 Newton steps continue from v_f until a step is
+// below 1e-10 (also for inputs outside the pairs' range or not finite).
 struct BeConsts {
   double c, e2, e1, cid, kid, inv_den;  // float64 fallback
   float cf, rf, thf, kaf, idf, th1;     // float32 Newton
+  float c3f, e2f, e1f;                  // |c|, |e2|, |e1|: sizes of the residual's terms
+  float e2x2;                           // 2 e2 (second derivative 6 c v + 2 e2)
   ffl::ff cP, e2P, e1P, cidP, kaP, idP; // float-float residual and w1
 };
 
@@ -815,9 +819,17 @@ __global__ void k_react_be(BeConsts K, double* __restrict__ V, double* __restric
       // F(v_f) = ((c v_f + e2) v_f + e1) v_f + (c w0 / den - v0) on float pairs
       const ff a0 = add(mul(K.cidP, q0p), neg(v0p));
       const ff F = add(mul(add(mul(add(mul(K.cP, vf), K.e2P), vf), K.e1P), vf), a0);
-      const float rdF = 1.0f / (1.0f - K.cf * ((-3.0f * vf + K.th1) * vf - K.thf - K.rf));
-      const ff dv = mul(F, rdF);
-      if (f32_ok && fabsf(dv.h) < 1e-5f) {
+      const float dFf = 1.0f - K.cf * ((-3.0f * vf + K.th1) * vf - K.thf - K.rf);
+      const ff dv = mul(F, 1.0f / dFf);
+      // the float pairs carry F to ~1e-14 of the sum of its terms' sizes S;
+      // near a fold of the cubic (F' small against S) that error, divided by
+      // F', is too large, and float64 steps take over
+      const float av = fabsf(vf);
+      const float S = ((K.c3f * av + K.e2f) * av + K.e1f) * av + fabsf(a0.h);
+      // the quasi-Newton step leaves about (F'' / 2 F') dv^2: below 1e-13
+      const float d2F = 6.0f * K.cf * vf + K.e2x2;
+      if (f32_ok && fabsf(dv.h) < 1e-5f && S < 8.0f * fabsf(dFf) &&
+          dv.h * dv.h * fabsf(d2F) < 2e-13f * fabsf(dFf)) {
         v = (widen(vf) - widen(dv.h)) - widen(dv.l);
         // w1 = (w0 + k alpha v1) / den with v1 ~ v_f - dv.h (dv.l k alpha is below 1e-19)
         const ff W = mul(add(q0p, mul(K.kaP, ff{vf, -dv.h})), K.idP);
@@ -827,19 +839,18 @@ __global__ void k_react_be(BeConsts K, double* __restrict__ V, double* __restric
       }
       v = widen(vf);
     }
-    // float64 Newton steps with the float32 derivative
+    // float64 Newton steps (rare: near folds of the cubic, unconverged
+    // float32 phases, inputs outside the pairs' range)
     const double a0 = fma(K.cid, q0, -v0);
-    float xf = (float)v;
     for (int it = 0; it < 50; ++it) {
-      const double rdF = (double)(1.0f / (1.0f - K.cf * ((-3.0f * xf + K.th1) * xf - K.thf - K.rf)));
       const double F = fma(fma(fma(K.c, v, K.e2), v, K.e1), v, a0);
-      const double dv = F * rdF;
+      const double dF = fma(fma(3.0 * K.c, v, 2.0 * K.e2), v, K.e1);
+      const double dv = F / dF;
       v -= dv;
       if (abs_below(dv, 1e-10)) {
         ok = true;
         break;
       }
-      xf = (float)v;
     }
     if (!ok) atomicOr(err, DEVERR_NEWTON);
     V[i] = v;
@@ -1448,6 +1459,10 @@ int launch_react_be(const kfbi_fhn* p, double k, double* V, double* w, int64_t n
   K.kaf = (float)ka;
   K.idf = (float)K.inv_den;
   K.th1 = 2.0f * (1.0f + K.thf);
+  K.c3f = (float)std::fabs(K.c);
+  K.e2f = (float)std::fabs(K.e2);
+  K.e1f = (float)std::fabs(K.e1);
+  K.e2x2 = (float)(2.0 * K.e2);
   K.cP = to_pair(K.c);
   K.e2P = to_pair(K.e2);
   K.e1P = to_pair(K.e1);

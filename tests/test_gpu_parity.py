@@ -292,6 +292,28 @@ def test_reaction_half_steps():
         assert rel(V.cpu().numpy(), Vr) < 1e-12 and rel(q.cpu().numpy(), qr) < 1e-12
 
 
+def test_reaction_be_float_pair_paths():
+    """Backward Euler on the float-pair path and its float64 fallback against
+    the oracle: states at and below the pairs' range (zeros, |v| < 2^-60,
+    1e-17), ordinary states, and stiff half steps (c = k H / Cm up to 3.5)
+    whose float32 Newton phase may not settle, so that float64 steps finish
+    them.  V and q within 1e-12 of the oracle (max-normalised) and, for the
+    tiny states, within 1e-17 absolute."""
+    rng = np.random.default_rng(23)
+    tiny = np.array([0.0, -0.0, 1e-25, -3e-20, 5e-19, -1e-17, 2.0 ** -60, 1e-12])
+    V0 = np.concatenate([tiny, rng.uniform(-0.3, 1.2, 20_000)])
+    q0 = np.concatenate([tiny[::-1], rng.uniform(-0.1, 0.3, 20_000)])
+    for fhn, k in ((C.FHN_CONFIG, 0.025), (C.FHN_PAPER, 0.002), (C.FHN_PAPER, 0.02), (C.FHN_PAPER, 0.035)):
+        Vr, qr, ok = reaction.backward_euler(V0, q0, k, fhn)
+        assert ok.all()
+        V, q = cuda(V0), cuda(q0)
+        K.react_be(fhn, k, V, q)
+        Vg, qg = V.cpu().numpy(), q.cpu().numpy()
+        assert rel(Vg, Vr) < 1e-12 and rel(qg, qr) < 1e-12, (fhn, k)
+        n = tiny.size
+        assert np.abs(Vg[:n] - Vr[:n]).max() < 1e-17 and np.abs(qg[:n] - qr[:n]).max() < 1e-17, (fhn, k)
+
+
 def test_strang_config0():
     """Config 0 (2-D ellipse, 128^2) for its 20 Strang steps against the
     oracle, with a 1e-12 GMRES tolerance on both sides: V, w and u_e within
