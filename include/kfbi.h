@@ -153,7 +153,9 @@ typedef struct {
   double ms;            /* host wall time of the call / step                  */
   /* bidomain_step only: device time of the phases of the step (CUDA events):
      both reaction half steps, the volume solve and g, the warm start, the
-     boundary-integral solve, and the assembly of V (with the true residual) */
+     boundary-integral solve, and the assembly of V (with the true residual;
+     the float32 forms of the scalar step form the midpoint of V inside the
+     backward-Euler pass, so there it counts as reaction time) */
   double react_ms, rhs_ms, warm_ms, solve_ms, assemble_ms;
 } kfbi_stats;
 

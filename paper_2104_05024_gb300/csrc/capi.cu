@@ -1307,15 +1307,20 @@ static int bidomain_impl(kfbi_handle* h, const kfbi_fhn* p, const double* istim,
       if ((rc = launch_limit64(h, h->w.grid64, x, nullptr, -1.0, h->w.tmp))) return rc;
     } else {
       // the refined solver's last act was the float64-accurate residual at
-      // the final density, which left v_B(psi) in u64; v_V is in vV64
-      if ((rc = launch_midpoint(h, V_dev, h->w.vV64, h->w.u64, n))) return rc;
+      // the final density, which left v_B(psi) in u64; v_V is in vV64.  The
+      // midpoint 2 (v_V + v_B) - V is formed by the backward-Euler pass below
+      // (nothing reads V in between)
       if ((rc = launch_limit_user(h, h->w.vV64, nullptr, nullptr, -1.0, h->w.tmp))) return rc;
       if ((rc = launch_limit_user(h, h->w.u64, x, h->w.tmp, -1.0, h->w.tmp))) return rc;
     }
     if ((rc = vec_dots(h, h->w.tmp, 1, h->t.M, h->w.tmp, h->w.step_sq + 2 * s))) return rc;
     if ((rc = vec_dots(h, h->w.g, 1, h->t.M, h->w.g, h->w.step_sq + 2 * s + 1))) return rc;
     if ((rc = mark(s, 5))) return rc;
-    if ((rc = launch_react_be(p, k, V_dev, w_dev, n, h->w.err, h->stream))) return rc;
+    if (prec == KFBI_FP64) {
+      if ((rc = launch_react_be(p, k, V_dev, w_dev, n, h->w.err, h->stream))) return rc;
+    } else if ((rc = launch_react_be(p, k, V_dev, w_dev, n, h->w.err, h->stream, h->w.vV64, h->w.u64))) {
+      return rc;
+    }
     if ((rc = mark(s, 6))) return rc;
     st.ms = elapsed_ms(t0);
   }

@@ -375,8 +375,6 @@ int launch_residual_ff_coupled(kfbi_handle* h, const double* src_i, double a_i, 
 int launch_residual_ff(kfbi_handle* h, const double* src, double alpha, const double* corr, const float* u32,
                        const double* u64, double lambda, float* res);
 int launch_lincomb(kfbi_handle* h, double* y, double a, const double* x, double b, int64_t n);
-// V <- 2 (vV + uB) - V (implicit midpoint from the two parts of u)
-int launch_midpoint(kfbi_handle* h, double* V, const double* vV, const double* uB, int64_t n);
 // out += sgn <ds, psi> / |Gamma| (the rank-one term of the Poisson operator)
 int launch_rank_one(kfbi_handle* h, const double* psi, double* out, double sgn);
 // f = -lambda V + c I (V may be NULL)
@@ -407,7 +405,10 @@ int launch_train_rows(cudaStream_t st, const double* psi, const double* psiF, co
                       float* T);
 
 int launch_react_fe(const kfbi_fhn* p, double k, double* V, double* w, int64_t n, cudaStream_t s);
-int launch_react_be(const kfbi_fhn* p, double k, double* V, double* w, int64_t n, int* err, cudaStream_t s);
+// backward Euler of (V, w); with vV, vB: of the midpoint 2 (vV + vB) - V,
+// formed in the same pass
+int launch_react_be(const kfbi_fhn* p, double k, double* V, double* w, int64_t n, int* err, cudaStream_t s,
+                    const double* vV = nullptr, const double* vB = nullptr);
 int launch_ue(kfbi_handle* h, const double* V, double* ue);
 
 }  // namespace kfbi

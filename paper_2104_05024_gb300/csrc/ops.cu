@@ -356,12 +356,6 @@ __global__ void k_sub_mean(double* __restrict__ ue, const double* __restrict__ s
     ue[i] -= mean;
 }
 
-__global__ void k_midpoint(double* __restrict__ V, const double* __restrict__ vV, const double* __restrict__ uB,
-                           int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    V[i] = 2.0 * (vV[i] + uB[i]) - V[i];
-}
-
 __global__ void k_lincomb(double* __restrict__ y, double a, const double* __restrict__ x, double b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = a * x[i] + b * y[i];
@@ -796,21 +790,81 @@ struct BeConsts {
   ffl::ff cP, e2P, e1P, cidP, kaP, idP; // float-float residual and w1
 };
 
-__global__ void k_react_be(BeConsts K, double* __restrict__ V, double* __restrict__ w, int64_t n, int* err) {
+// float64 Newton steps from v (from v0 when start_f32 is false) for the
+// nodes the float-pair step does not take, v0 = 2 (a + b) - c with MID, else
+// c: kept out of line so that none of its float64 work is hoisted into the
+// common path
+template <bool MID>
+__device__ __noinline__ void be_newton64(const BeConsts& K, double a, double b, double c, double q0, bool start_f32,
+                                         double v, double* Vout, double* wout, int* err) {
+  const double v0 = MID ? 2.0 * (a + b) - c : c;
+  if (!start_f32) v = v0;
+  const double a0 = fma(K.cid, q0, -v0);
+  bool ok = false;
+  for (int it = 0; it < 50; ++it) {
+    const double F = fma(fma(fma(K.c, v, K.e2), v, K.e1), v, a0);
+    const double dF = fma(fma(3.0 * K.c, v, 2.0 * K.e2), v, K.e1);
+    const double dv = F / dF;
+    v -= dv;
+    if (abs_below(dv, 1e-10)) {
+      ok = true;
+      break;
+    }
+  }
+  if (!ok) atomicOr(err, DEVERR_NEWTON);
+  *Vout = v;
+  *wout = fma(K.kid, v, q0 * K.inv_den);
+}
+
+// MID: v0 is the implicit-midpoint assembly 2 (v_V + v_B) - V of the
+// float32 forms, formed here on float pairs from the three float64 fields
+// (the midpoint value itself is never stored; it enters only this step).
+template <bool MID>
+__global__ void k_react_be(BeConsts K, double* __restrict__ V, double* __restrict__ w, const double* __restrict__ vV,
+                           const double* __restrict__ vB, int64_t n, int* err) {
   using namespace ffl;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double v0 = V[i], q0 = w[i];
+  // the next node's inputs are loaded before the current node is computed
+  // (the Newton work between a node's loads and its stores is long)
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double nV = 0.0, nq = 0.0, na = 0.0, nb = 0.0;
+  if (i < n) {
+    nV = V[i];
+    nq = w[i];
+    if constexpr (MID) {
+      na = vV[i];
+      nb = vB[i];
+    }
+  }
+  for (; i < n; i += stride) {
+    const double Vi = nV, q0 = nq, a = na, b = nb;
+    if (i + stride < n) {
+      nV = V[i + stride];
+      nq = w[i + stride];
+      if constexpr (MID) {
+        na = vV[i + stride];
+        nb = vB[i + stride];
+      }
+    }
     ff v0p, q0p;
-    double v = v0;
-    bool ok = false;
-    if (split(v0, v0p) && split(q0, q0p)) {
+    bool pairs = split(q0, q0p);
+    if constexpr (MID) {
+      ff ap{0.0f, 0.0f}, bp{0.0f, 0.0f}, cp{0.0f, 0.0f};
+      pairs = split(a, ap) & split(b, bp) & split(Vi, cp) & pairs;
+      const ff sum = add(ap, bp);
+      v0p = add(add(sum, sum), neg(cp));
+    } else {
+      pairs = split(Vi, v0p) & pairs;
+    }
+    double v = 0.0;
+    if (pairs) {
       const float v0f = v0p.h, q0f = q0p.h;
       float vf = v0f;
       for (int it = 0; it < 12; ++it) {
         const float q1 = (q0f + K.kaf * vf) * K.idf;
         const float Fv = vf - v0f - K.cf * (vf * (vf - K.thf) * (1.0f - vf) - q1);
         const float dF = 1.0f - K.cf * ((-3.0f * vf + K.th1) * vf - K.thf - K.rf);
-        const float dv = Fv / dF;
+        const float dv = __fdividef(Fv, dF);  // a Newton step needs no correctly rounded quotient
         vf -= dv;
         if (fabsf(dv) <= 1e-6f * fmaxf(1.0f, fabsf(vf))) break;
       }
@@ -820,7 +874,7 @@ __global__ void k_react_be(BeConsts K, double* __restrict__ V, double* __restric
       const ff a0 = add(mul(K.cidP, q0p), neg(v0p));
       const ff F = add(mul(add(mul(add(mul(K.cP, vf), K.e2P), vf), K.e1P), vf), a0);
       const float dFf = 1.0f - K.cf * ((-3.0f * vf + K.th1) * vf - K.thf - K.rf);
-      const ff dv = mul(F, 1.0f / dFf);
+      const ff dv = mul(F, __fdividef(1.0f, dFf));
       // the float pairs carry F to ~1e-14 of the sum of its terms' sizes S;
       // near a fold of the cubic (F' small against S) that error, divided by
       // F', is too large, and float64 steps take over
@@ -830,7 +884,8 @@ __global__ void k_react_be(BeConsts K, double* __restrict__ V, double* __restric
       const float d2F = 6.0f * K.cf * vf + K.e2x2;
       if (f32_ok && fabsf(dv.h) < 1e-5f && S < 8.0f * fabsf(dFf) &&
           dv.h * dv.h * fabsf(d2F) < 2e-13f * fabsf(dFf)) {
-        v = (widen(vf) - widen(dv.h)) - widen(dv.l);
+        const ff v1 = add(ff{vf, 0.0f}, neg(dv));
+        v = widen(v1.h) + widen(v1.l);
         // w1 = (w0 + k alpha v1) / den with v1 ~ v_f - dv.h (dv.l k alpha is below 1e-19)
         const ff W = mul(add(q0p, mul(K.kaP, ff{vf, -dv.h})), K.idP);
         V[i] = v;
@@ -841,20 +896,7 @@ __global__ void k_react_be(BeConsts K, double* __restrict__ V, double* __restric
     }
     // float64 Newton steps (rare: near folds of the cubic, unconverged
     // float32 phases, inputs outside the pairs' range)
-    const double a0 = fma(K.cid, q0, -v0);
-    for (int it = 0; it < 50; ++it) {
-      const double F = fma(fma(fma(K.c, v, K.e2), v, K.e1), v, a0);
-      const double dF = fma(fma(3.0 * K.c, v, 2.0 * K.e2), v, K.e1);
-      const double dv = F / dF;
-      v -= dv;
-      if (abs_below(dv, 1e-10)) {
-        ok = true;
-        break;
-      }
-    }
-    if (!ok) atomicOr(err, DEVERR_NEWTON);
-    V[i] = v;
-    w[i] = fma(K.kid, v, q0 * K.inv_den);
+    be_newton64<MID>(K, a, b, Vi, q0, pairs, v, V + i, w + i, err);
   }
 }
 
@@ -1295,12 +1337,6 @@ int launch_sub_mean(kfbi_handle* h, const double* src, double* dst) {
   return KFBI_OK;
 }
 
-int launch_midpoint(kfbi_handle* h, double* V, const double* vV, const double* uB, int64_t n) {
-  k_midpoint<<<grid_blocks(n, 256), 256, 0, h->stream>>>(V, vV, uB, n);
-  KFBI_CHECK_LAUNCH();
-  return KFBI_OK;
-}
-
 int launch_lincomb(kfbi_handle* h, double* y, double a, const double* x, double b, int64_t n) {
   k_lincomb<<<grid_blocks(n, 256), 256, 0, h->stream>>>(y, a, x, b, n);
   KFBI_CHECK_LAUNCH();
@@ -1444,7 +1480,8 @@ static ffl::ff to_pair(double x) {
   return ffl::ff{h, (float)(x - (double)h)};
 }
 
-int launch_react_be(const kfbi_fhn* p, double k, double* V, double* w, int64_t n, int* err, cudaStream_t s) {
+int launch_react_be(const kfbi_fhn* p, double k, double* V, double* w, int64_t n, int* err, cudaStream_t s,
+                    const double* vV, const double* vB) {
   BeConsts K;
   K.c = k * p->H / p->Cm;
   const double den = 1.0 + k * p->zeta, ka = k * p->alpha;
@@ -1469,7 +1506,10 @@ int launch_react_be(const kfbi_fhn* p, double k, double* V, double* w, int64_t n
   K.cidP = to_pair(K.cid);
   K.kaP = to_pair(ka);
   K.idP = to_pair(K.inv_den);
-  k_react_be<<<grid_blocks(n, 256), 256, 0, s>>>(K, V, w, n, err);
+  if (vV != nullptr)
+    k_react_be<true><<<grid_blocks(n, 256), 256, 0, s>>>(K, V, w, vV, vB, n, err);
+  else
+    k_react_be<false><<<grid_blocks(n, 256), 256, 0, s>>>(K, V, w, nullptr, nullptr, n, err);
   KFBI_CHECK_LAUNCH();
   return KFBI_OK;
 }
