@@ -342,17 +342,33 @@ int norm2(kfbi_handle* h, const double* v, double* slot, double* out) {
 int refine_rounds(const kfbi_handle* h) { return h->opts.tol < 1e-9 ? 2 : 1; }
 
 int refined_solve(kfbi_handle* h, const double* src, double alpha, const double* corr, double lambda, double* u) {
+  // Dirichlet box, separate x and y passes: the first solve's float result
+  // stays in the padded grid grid32 alone (no float64 copy), the correction
+  // solve runs in grid32b and writes u = its result + grid32 in float64
+  const bool split = h->grid.bc == KFBI_BOX_DIRICHLET && !(h->xy_fused && h->grid.dim == 3);
   SolveArgs sa;
   sa.src = src;
   sa.alpha = alpha;
   sa.corr = corr;
   sa.lambda = lambda;
-  sa.out_user = u;
+  sa.out_user = split ? nullptr : u;
   int rc = box_solve32(h, sa, h->w.grid32);
   if (rc) return rc;
   const int rounds = refine_rounds(h);
   for (int r = 0; r < rounds; ++r) {
     SolveArgs sr;
+    if (r == 0 && split) {
+      // float-float residual of the float grid, float32 result; the
+      // irregular nodes from the padded grid too
+      if ((rc = launch_residual_ff(h, src, alpha, corr, h->w.grid32, nullptr, lambda, h->w.res32))) return rc;
+      sr.src32 = h->w.res32;
+      sr.lambda = lambda;
+      sr.out_user = u;
+      sr.aux32 = h->w.grid32;
+      sr.keep = false;
+      if ((rc = box_solve32(h, sr, h->w.grid32b))) return rc;
+      continue;
+    }
     if (r == 0) {
       // u is exactly the float32 grid of the solve just done: float-float
       // residual, float32 result
@@ -892,8 +908,13 @@ static int create_impl(const kfbi_geometry* geom, const kfbi_grid* grid, double 
   const int64_t P = padded_points(h);
   if ((rc = dalloc(h, &h->w.grid64, (size_t)P))) return fail(rc);
   if ((rc = dalloc(h, &h->w.grid32, (size_t)P))) return fail(rc);
+  // the second float grid: the extracellular field of coupled solves, the
+  // correction solve of a refined scalar solve (the first solve's float
+  // result stays in grid32)
+  if ((rc = dalloc(h, &h->w.grid32b, (size_t)P))) return fail(rc);
   if (cudaMemsetAsync(h->w.grid64, 0, sizeof(double) * (size_t)P, h->stream) != cudaSuccess ||
-      cudaMemsetAsync(h->w.grid32, 0, sizeof(float) * (size_t)P, h->stream) != cudaSuccess) {
+      cudaMemsetAsync(h->w.grid32, 0, sizeof(float) * (size_t)P, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->w.grid32b, 0, sizeof(float) * (size_t)P, h->stream) != cudaSuccess) {
     set_error("cudaMemset failed");
     return fail(KFBI_ERR_CUDA);
   }
@@ -904,9 +925,7 @@ static int create_impl(const kfbi_geometry* geom, const kfbi_grid* grid, double 
     if ((rc = dalloc(h, &h->w.corr2, (size_t)h->t.n_irr))) return fail(rc);
     if ((rc = dalloc(h, &h->w.xvec2, (size_t)2 * h->t.M))) return fail(rc);
     if ((rc = dalloc(h, &h->w.grid64b, (size_t)P))) return fail(rc);
-    if ((rc = dalloc(h, &h->w.grid32b, (size_t)P))) return fail(rc);
-    if (cudaMemsetAsync(h->w.grid64b, 0, sizeof(double) * (size_t)P, h->stream) != cudaSuccess ||
-        cudaMemsetAsync(h->w.grid32b, 0, sizeof(float) * (size_t)P, h->stream) != cudaSuccess) {
+    if (cudaMemsetAsync(h->w.grid64b, 0, sizeof(double) * (size_t)P, h->stream) != cudaSuccess) {
       set_error("cudaMemset failed");
       return fail(KFBI_ERR_CUDA);
     }

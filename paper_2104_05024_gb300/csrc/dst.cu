@@ -436,7 +436,8 @@ __global__ void __launch_bounds__(NT) k_xfwd(T* __restrict__ a, const double* __
 template <typename T, int N, int DIM>
 __global__ void __launch_bounds__(NT) k_xinv(T* __restrict__ a, bool keep, double* __restrict__ out,
                                              const double* __restrict__ aux, double beta, double gamma,
-                                             const T* __restrict__ tw_g, const int* __restrict__ skip) {
+                                             const T* __restrict__ tw_g, const int* __restrict__ skip,
+                                             const float* __restrict__ aux32 = nullptr) {
   using C = Cfg<T, N>;
   constexpr int W = C::W, RS = C::RS, n1 = N - 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -468,17 +469,22 @@ __global__ void __launch_bounds__(NT) k_xinv(T* __restrict__ a, bool keep, doubl
     return;
   }
   // out = beta v + gamma aux with beta applied in T (one float64 operation
-  // per element without aux, two with)
+  // per element without aux, two with), or out = beta v + aux32 with aux32 a
+  // padded float grid of the same layout as a (one float64 addition)
   const T b_t = (T)beta;
   for (int idx = threadIdx.x; idx < N * W; idx += NT) {
     const int x = idx % N, c = idx / N, y = y0 + c;
     const T v = s[x * RS + c];
-    if (keep) a[plane + (size_t)y * N + x] = v;
+    const size_t pidx = plane + (size_t)y * N + x;
+    if (keep) a[pidx] = v;
     if (x > 0 && y > 0) {
       const size_t line = DIM == 3 ? (size_t)(z - 1) * n1 + (y - 1) : (size_t)(y - 1);
       const size_t o = line * n1 + (x - 1);
       const double bv = to_double(b_t * v);
-      out[o] = aux != nullptr ? fma(gamma, aux[o], bv) : bv;
+      if (aux32 != nullptr)
+        out[o] = bv + ffl::widen(aux32[pidx]);
+      else
+        out[o] = aux != nullptr ? fma(gamma, aux[o], bv) : bv;
     }
   }
 }
@@ -921,9 +927,12 @@ int launch_strided3(kfbi_handle* h, int mode, bool solve, T* work, const T* mu1,
   cudaStream_t st = h->stream;
   int rc;
   if constexpr (sizeof(T) == 4 && N >= TMA_W && N <= 256) {
-    if (h->tma) {
+    // the handle's second float grid has its own tensor maps
+    const bool second = (const void*)work == (const void*)h->w.grid32b;
+    if (h->tma && (!second || h->tma_b)) {
       constexpr size_t smem = tma_smem_bytes<N>();
-      const CUtensorMap& map = mode == 0 ? h->tmap_y32 : h->tmap_z32;
+      const CUtensorMap& map =
+          mode == 0 ? (second ? h->tmap_y32b : h->tmap_y32) : (second ? h->tmap_z32b : h->tmap_z32);
       const int tiles = (N / TMA_W) * (N - 1);
       const int nb = (solve ? tma_blocks<true>() : tma_blocks<false>()) * h->sms;
       const int grid = tiles < nb ? tiles : nb;
@@ -1065,11 +1074,11 @@ int run_solve(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1, const 
     if ((rc = launch_strided3<T, N>(h, 0, false, work, mu1, lam, scale, tw))) return rc;
     if constexpr (sizeof(T) == 4) {
       if (launch_pdl(k_xinv<T, N, 3>, grid, dim3(NT), smem, st, work, sa.keep || sa.out_user == nullptr, sa.out_user,
-                     (const double*)sa.aux, sa.beta, sa.gamma, tw, (const int*)h->skip) != cudaSuccess)
+                     (const double*)sa.aux, sa.beta, sa.gamma, tw, (const int*)h->skip, sa.aux32) != cudaSuccess)
         return launch_failed("x inverse pass");
     } else {
       k_xinv<T, N, 3><<<grid, NT, smem, st>>>(work, sa.keep || sa.out_user == nullptr, sa.out_user, sa.aux, sa.beta,
-                                               sa.gamma, tw, h->skip);
+                                               sa.gamma, tw, h->skip, sa.aux32);
     }
   } else {
     dim3 grid(N / W, 1);
@@ -1081,7 +1090,7 @@ int run_solve(kfbi_handle* h, const SolveArgs& sa, T* work, const T* mu1, const 
     k_strided<T, N, true, 2><<<grid, NT, smem, st>>>(work, N, 0, 0, mu1, lam, scale, tw, h->skip, rinv);
     if ((rc = prep(k_xinv<T, N, 2>, smem))) return rc;
     k_xinv<T, N, 2><<<grid, NT, smem, st>>>(work, sa.keep || sa.out_user == nullptr, sa.out_user, sa.aux, sa.beta,
-                                             sa.gamma, tw, h->skip);
+                                             sa.gamma, tw, h->skip, sa.aux32);
   }
   KFBI_CHECK_LAUNCH_N(dim == 3 ? 5 : 3);
   return KFBI_OK;
@@ -1727,6 +1736,15 @@ int make_tma_maps(kfbi_handle* h) {
     return KFBI_ERR_CUDA;
   }
   h->tma = true;
+  if (h->w.grid32b != nullptr) {
+    r1 = encode(&h->tmap_y32b, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->w.grid32b, dims, strides, box_y, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    r2 = encode(&h->tmap_z32b, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->w.grid32b, dims, strides, box_z, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    h->tma_b = r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS;
+  }
   // fused x-y passes need cluster launches (a cluster of N/32 blocks per
   // plane).  They pay off only for small planes: measured per float32 solve
   // (CUDA events, back-to-back) 18.8 against 24.4 us at 64^3, 48.4 against

@@ -263,6 +263,8 @@ struct kfbi_handle {
   kfbi_mlp* warm = nullptr;       // learned warm start (not owned)
   // TMA descriptors of the float32 padded grid: [N x 32] tiles along y and z
   CUtensorMap tmap_y32, tmap_z32;
+  CUtensorMap tmap_y32b, tmap_z32b;  // the same for the second float grid
+  bool tma_b = false;
   bool tma = false;
   int sms = 152;                  // the device's multiprocessor count (persistent grids)
   bool xy_fused = false;          // float32 3-D solves use the cluster-fused x-y passes
@@ -321,6 +323,7 @@ struct SolveArgs {
   double gamma = 0.0;
   double lambda = 0.0;
   bool keep = true;               // the x inverse pass also writes the padded work grid
+  const float* aux32 = nullptr;   // float32 solves: out_user = beta v + aux32 (a padded float grid)
 };
 int box_solve64(kfbi_handle* h, const SolveArgs& a, double* work);
 // the float64 box solve of the coupled pair (sources / corrections / outputs

@@ -215,25 +215,36 @@ __global__ void k_residual_ff(GridParams gr, const float* __restrict__ u32, floa
 }
 
 // at the irregular nodes, where the correction makes r a small difference of
-// large terms: r = corr - L_h u in float64 from the float64 copy of u
+// large terms: r = corr - L_h u in float64, from the float64 copy of u, or
+// (u == nullptr) from the padded float grid u32 that holds u exactly
 __global__ void k_residual_irr(GridParams gr, Tables t, const double* __restrict__ corr, const double* __restrict__ u,
-                               double lambda, const double* __restrict__ src, double alpha, float* __restrict__ res) {
+                               double lambda, const double* __restrict__ src, double alpha, float* __restrict__ res,
+                               const float* __restrict__ u32) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= t.n_irr) return;
-  const int n1 = gr.N - 1;
+  const int N = gr.N, n1 = N - 1;
   const double ih2 = 1.0 / (gr.h * gr.h);
   const double diag = -2.0 * gr.dim * ih2 - lambda;
   const int64_t f = t.irr[i];
   const int64_t s = (int64_t)n1 * n1;
-  const int x = (int)(f % n1), y = (int)((f / n1) % n1);
-  double nb = (x > 0 ? u[f - 1] : 0.0) + (x < n1 - 1 ? u[f + 1] : 0.0);
-  nb += (y > 0 ? u[f - n1] : 0.0) + (y < n1 - 1 ? u[f + n1] : 0.0);
-  if (gr.dim == 3) {
-    const int z = (int)(f / s);
-    nb += (z > 0 ? u[f - s] : 0.0) + (z < n1 - 1 ? u[f + s] : 0.0);
+  const int x = (int)(f % n1), y = (int)((f / n1) % n1), z = gr.dim == 3 ? (int)(f / s) : 0;
+  double uc, nb;
+  if (u != nullptr) {
+    uc = u[f];
+    nb = (x > 0 ? u[f - 1] : 0.0) + (x < n1 - 1 ? u[f + 1] : 0.0);
+    nb += (y > 0 ? u[f - n1] : 0.0) + (y < n1 - 1 ? u[f + n1] : 0.0);
+    if (gr.dim == 3) nb += (z > 0 ? u[f - s] : 0.0) + (z < n1 - 1 ? u[f + s] : 0.0);
+  } else {
+    // padded index of (x, y, z): index 0 of each axis is the zero boundary
+    const size_t NN = (size_t)N * N;
+    const size_t p = gr.dim == 3 ? ((size_t)(z + 1) * N + (y + 1)) * N + (x + 1) : (size_t)(y + 1) * N + (x + 1);
+    uc = ffl::widen(u32[p]);
+    nb = ffl::widen(u32[p - 1]) + (x < n1 - 1 ? ffl::widen(u32[p + 1]) : 0.0);
+    nb += ffl::widen(u32[p - N]) + (y < n1 - 1 ? ffl::widen(u32[p + N]) : 0.0);
+    if (gr.dim == 3) nb += ffl::widen(u32[p - NN]) + (z < n1 - 1 ? ffl::widen(u32[p + NN]) : 0.0);
   }
   const double a = src != nullptr ? alpha * src[f] : 0.0;
-  res[f] = (float)(a + corr[i] - (nb * ih2 + diag * u[f]));
+  res[f] = (float)(a + corr[i] - (nb * ih2 + diag * uc));
 }
 
 // the float-float residual on the Neumann box's field layout: u32 is the
@@ -1035,7 +1046,7 @@ int launch_residual_ff(kfbi_handle* h, const double* src, double alpha, const do
                                                                                dg_lo, src, al_hi, al_lo, res);
     if (corr != nullptr && h->t.n_irr > 0)
       k_residual_irr<<<(h->t.n_irr + 127) / 128, 128, 0, h->stream>>>(h->grid, h->t, corr, u64, lambda, src, alpha,
-                                                                      res);
+                                                                      res, u32);
   }
   KFBI_CHECK_LAUNCH_N(corr != nullptr && h->t.n_irr > 0 ? 2 : 1);
   return KFBI_OK;
