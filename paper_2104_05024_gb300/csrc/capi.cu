@@ -958,9 +958,11 @@ static int create_impl(const kfbi_geometry* geom, const kfbi_grid* grid, double 
   if ((rc = dalloc(h, &h->w.psiF, (size_t)M))) return fail(rc);
   if ((rc = dalloc(h, &h->w.rF, (size_t)M))) return fail(rc);
   if ((rc = dalloc(h, &h->w.proj, (size_t)KFBI_HISTORY * (KFBI_HISTORY + 2) + 8))) return fail(rc);
-  // [0, 128): scalars and the projection system; [128, 256): per-iteration
-  // residual estimates and stop flags of GMRES
-  if (cudaMallocHost((void**)&h->w.host_small, 256 * sizeof(double)) != cudaSuccess) {
+  // [0, 128): scalars and the projection system (which may run past 128 for
+  // long histories: it is read before GMRES starts); [128, 128 + 2
+  // MAX_RESTART): per-iteration residual estimates and stop flags of GMRES
+  constexpr int host_small_n = std::max(128 + 2 * MAX_RESTART, KFBI_HISTORY * (KFBI_HISTORY + 2) + 3);
+  if (cudaMallocHost((void**)&h->w.host_small, host_small_n * sizeof(double)) != cudaSuccess) {
     set_error("cudaMallocHost failed");
     return fail(KFBI_ERR_OOM);
   }
