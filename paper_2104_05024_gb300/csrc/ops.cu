@@ -522,12 +522,24 @@ __device__ __forceinline__ bool arn_last_block(unsigned* counter) {
   return last;
 }
 
-// out[k] = sum_b partial[k][b] for k < nv, one warp per k
+// out[k] = sum_b partial[k][b] for k < nv, one warp per k; each lane keeps
+// four independent L2 loads in flight (the partials were written by other
+// blocks just before, so every load is a round trip to L2), in a fixed order
 __device__ __forceinline__ void arn_reduce(const double* partial, int nb, int nv, double* out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int k = warp; k < nv; k += nw) {
-    double acc = 0.0;
-    for (int b = lane; b < nb; b += 32) acc += __ldcg(&partial[(size_t)k * nb + b]);
+    const double* pk = partial + (size_t)k * nb;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int b = lane;
+    for (; b + 96 < nb; b += 128) {
+      const double x0 = __ldcg(&pk[b]), x1 = __ldcg(&pk[b + 32]), x2 = __ldcg(&pk[b + 64]), x3 = __ldcg(&pk[b + 96]);
+      a0 += x0;
+      a1 += x1;
+      a2 += x2;
+      a3 += x3;
+    }
+    for (; b < nb; b += 32) a0 += __ldcg(&pk[b]);
+    double acc = (a0 + a1) + (a2 + a3);
     acc = warp_sum(acc);
     if (lane == 0) out[k] = acc;
   }
