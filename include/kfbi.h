@@ -155,7 +155,9 @@ typedef struct {
      both reaction half steps, the volume solve and g, the warm start, the
      boundary-integral solve, and the assembly of V (with the true residual;
      the float32 forms of the scalar step form the midpoint of V inside the
-     backward-Euler pass, so there it counts as reaction time) */
+     backward-Euler pass, so there it counts as reaction time; within one
+     call the forward half step of every step after the first runs in the
+     previous step's backward pass and is timed with it) */
   double react_ms, rhs_ms, warm_ms, solve_ms, assemble_ms;
 } kfbi_stats;
 

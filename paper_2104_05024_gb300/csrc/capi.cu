@@ -1250,7 +1250,9 @@ static int bidomain_impl(kfbi_handle* h, const kfbi_fhn* p, const double* istim,
     kfbi_stats& st = stats[s];
     auto t0 = std::chrono::steady_clock::now();
     if ((rc = mark(s, 0))) return rc;
-    if ((rc = launch_react_fe(p, k, V_dev, w_dev, n, h->stream))) return rc;
+    // the forward half step of steps after the first ran in the previous
+    // step's backward pass
+    if (s == 0 && (rc = launch_react_fe(p, k, V_dev, w_dev, n, h->stream))) return rc;
     if ((rc = mark(s, 1))) return rc;
     const int prec = h->opts.precision == KFBI_FP64 ? KFBI_FP64 : KFBI_MIXED;
     // source of the V problem: -lam V (+ beta I / sigma_e with a stimulus)
@@ -1340,9 +1342,12 @@ static int bidomain_impl(kfbi_handle* h, const kfbi_fhn* p, const double* istim,
     if ((rc = vec_dots(h, h->w.tmp, 1, h->t.M, h->w.tmp, h->w.step_sq + 2 * s))) return rc;
     if ((rc = vec_dots(h, h->w.g, 1, h->t.M, h->w.g, h->w.step_sq + 2 * s + 1))) return rc;
     if ((rc = mark(s, 5))) return rc;
+    // backward half step, and the next step's forward half step in the same
+    // pass (not after the last step)
+    const bool fe_next = s + 1 < nsteps;
     if (prec == KFBI_FP64) {
-      if ((rc = launch_react_be(p, k, V_dev, w_dev, n, h->w.err, h->stream))) return rc;
-    } else if ((rc = launch_react_be(p, k, V_dev, w_dev, n, h->w.err, h->stream, h->w.vV64, h->w.u64))) {
+      if ((rc = launch_react_be(p, k, V_dev, w_dev, n, h->w.err, h->stream, nullptr, nullptr, fe_next))) return rc;
+    } else if ((rc = launch_react_be(p, k, V_dev, w_dev, n, h->w.err, h->stream, h->w.vV64, h->w.u64, fe_next))) {
       return rc;
     }
     if ((rc = mark(s, 6))) return rc;

@@ -409,9 +409,10 @@ int launch_train_rows(cudaStream_t st, const double* psi, const double* psiF, co
 
 int launch_react_fe(const kfbi_fhn* p, double k, double* V, double* w, int64_t n, cudaStream_t s);
 // backward Euler of (V, w); with vV, vB: of the midpoint 2 (vV + vB) - V,
-// formed in the same pass
+// formed in the same pass; fe_next: followed in the same pass by the forward
+// Euler half step (same k) that opens the next Strang step
 int launch_react_be(const kfbi_fhn* p, double k, double* V, double* w, int64_t n, int* err, cudaStream_t s,
-                    const double* vV = nullptr, const double* vB = nullptr);
+                    const double* vV = nullptr, const double* vB = nullptr, bool fe_next = false);
 int launch_ue(kfbi_handle* h, const double* V, double* ue);
 
 }  // namespace kfbi

@@ -811,6 +811,12 @@ struct BeConsts {
   float c3f, e2f, e1f;                  // |c|, |e2|, |e1|: sizes of the residual's terms
   float e2x2;                           // 2 e2 (second derivative 6 c v + 2 e2)
   ffl::ff cP, e2P, e1P, cidP, kaP, idP; // float-float residual and w1
+  // the next step's forward-Euler half step (see k_react_fe), when fused
+  double fa, fp1, fp0, fka, fkz1;
+};
+
+struct VW {
+  double v, w;
 };
 
 // float64 Newton steps from v (from v0 when start_f32 is false) for the
@@ -818,8 +824,8 @@ struct BeConsts {
 // c: kept out of line so that none of its float64 work is hoisted into the
 // common path
 template <bool MID>
-__device__ __noinline__ void be_newton64(const BeConsts& K, double a, double b, double c, double q0, bool start_f32,
-                                         double v, double* Vout, double* wout, int* err) {
+__device__ __noinline__ VW be_newton64(const BeConsts& K, double a, double b, double c, double q0, bool start_f32,
+                                       double v, int* err) {
   const double v0 = MID ? 2.0 * (a + b) - c : c;
   if (!start_f32) v = v0;
   const double a0 = fma(K.cid, q0, -v0);
@@ -835,14 +841,17 @@ __device__ __noinline__ void be_newton64(const BeConsts& K, double a, double b, 
     }
   }
   if (!ok) atomicOr(err, DEVERR_NEWTON);
-  *Vout = v;
-  *wout = fma(K.kid, v, q0 * K.inv_den);
+  return VW{v, fma(K.kid, v, q0 * K.inv_den)};
 }
 
 // MID: v0 is the implicit-midpoint assembly 2 (v_V + v_B) - V of the
 // float32 forms, formed here on float pairs from the three float64 fields
 // (the midpoint value itself is never stored; it enters only this step).
-template <bool MID>
+// FE: the forward-Euler half step that opens the next Strang step follows in
+// the same pass (the same float64 operations as k_react_fe), so that V and w
+// cross memory once for both half steps and the forward step's float64 work
+// overlaps the backward step's float32 work.
+template <bool MID, bool FE>
 __global__ void k_react_be(BeConsts K, double* __restrict__ V, double* __restrict__ w, const double* __restrict__ vV,
                            const double* __restrict__ vB, int64_t n, int* err) {
   using namespace ffl;
@@ -880,6 +889,8 @@ __global__ void k_react_be(BeConsts K, double* __restrict__ V, double* __restric
       pairs = split(Vi, v0p) & pairs;
     }
     double v = 0.0;
+    VW res{0.0, 0.0};
+    bool done = false;
     if (pairs) {
       const float v0f = v0p.h, q0f = q0p.h;
       float vf = v0f;
@@ -908,18 +919,26 @@ __global__ void k_react_be(BeConsts K, double* __restrict__ V, double* __restric
       if (f32_ok && fabsf(dv.h) < 1e-5f && S < 8.0f * fabsf(dFf) &&
           dv.h * dv.h * fabsf(d2F) < 2e-13f * fabsf(dFf)) {
         const ff v1 = add(ff{vf, 0.0f}, neg(dv));
-        v = widen(v1.h) + widen(v1.l);
+        res.v = widen(v1.h) + widen(v1.l);
         // w1 = (w0 + k alpha v1) / den with v1 ~ v_f - dv.h (dv.l k alpha is below 1e-19)
         const ff W = mul(add(q0p, mul(K.kaP, ff{vf, -dv.h})), K.idP);
-        V[i] = v;
-        w[i] = widen(W.h) + widen(W.l);
-        continue;
+        res.w = widen(W.h) + widen(W.l);
+        done = true;
+      } else {
+        v = widen(vf);
       }
-      v = widen(vf);
     }
     // float64 Newton steps (rare: near folds of the cubic, unconverged
     // float32 phases, inputs outside the pairs' range)
-    be_newton64<MID>(K, a, b, Vi, q0, pairs, v, V + i, w + i, err);
+    if (!done) res = be_newton64<MID>(K, a, b, Vi, q0, pairs, v, err);
+    if constexpr (FE) {
+      const double t = fma(fma(-K.fa, res.v, K.fp1), res.v, K.fp0);
+      const double v2 = fma(t, res.v, fma(-K.fa, res.w, res.v));
+      res.w = fma(K.fka, res.v, K.fkz1 * res.w);
+      res.v = v2;
+    }
+    V[i] = res.v;
+    w[i] = res.w;
   }
 }
 
@@ -1504,7 +1523,7 @@ static ffl::ff to_pair(double x) {
 }
 
 int launch_react_be(const kfbi_fhn* p, double k, double* V, double* w, int64_t n, int* err, cudaStream_t s,
-                    const double* vV, const double* vB) {
+                    const double* vV, const double* vB, bool fe_next) {
   BeConsts K;
   K.c = k * p->H / p->Cm;
   const double den = 1.0 + k * p->zeta, ka = k * p->alpha;
@@ -1529,10 +1548,23 @@ int launch_react_be(const kfbi_fhn* p, double k, double* V, double* w, int64_t n
   K.cidP = to_pair(K.cid);
   K.kaP = to_pair(ka);
   K.idP = to_pair(K.inv_den);
-  if (vV != nullptr)
-    k_react_be<true><<<grid_blocks(n, 256), 256, 0, s>>>(K, V, w, vV, vB, n, err);
-  else
-    k_react_be<false><<<grid_blocks(n, 256), 256, 0, s>>>(K, V, w, nullptr, nullptr, n, err);
+  // the next step's forward Euler: the constants of k_react_fe
+  K.fa = k * p->H / p->Cm;
+  K.fka = k * p->alpha;
+  K.fkz1 = 1.0 - k * p->zeta;
+  K.fp1 = K.fa * (1.0 + p->theta);
+  K.fp0 = -K.fa * p->theta;
+  const int nb = grid_blocks(n, 256);
+  if (vV != nullptr) {
+    if (fe_next)
+      k_react_be<true, true><<<nb, 256, 0, s>>>(K, V, w, vV, vB, n, err);
+    else
+      k_react_be<true, false><<<nb, 256, 0, s>>>(K, V, w, vV, vB, n, err);
+  } else if (fe_next) {
+    k_react_be<false, true><<<nb, 256, 0, s>>>(K, V, w, nullptr, nullptr, n, err);
+  } else {
+    k_react_be<false, false><<<nb, 256, 0, s>>>(K, V, w, nullptr, nullptr, n, err);
+  }
   KFBI_CHECK_LAUNCH();
   return KFBI_OK;
 }
