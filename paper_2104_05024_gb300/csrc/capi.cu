@@ -1439,7 +1439,9 @@ static int bidomain_coupled_impl(kfbi_handle* h, const kfbi_fhn* p, const double
     kfbi_stats& st = stats[s];
     auto t0 = std::chrono::steady_clock::now();
     if ((rc = mark(s, 0))) return rc;
-    if ((rc = launch_react_fe(p, k, V_dev, w_dev, n, h->stream))) return rc;
+    // after the first step the forward half step ran in the previous
+    // step's backward pass
+    if (s == 0 && (rc = launch_react_fe(p, k, V_dev, w_dev, n, h->stream))) return rc;
     if ((rc = mark(s, 1))) return rc;
     // f_i = -kappa V, f_e = kappa V (- beta I)
     const double* src_e = V_dev;
@@ -1494,7 +1496,8 @@ static int bidomain_coupled_impl(kfbi_handle* h, const kfbi_fhn* p, const double
     if ((rc = vec_dots(h, h->w.tmp, 1, nk, h->w.tmp, h->w.step_sq + 2 * s))) return rc;
     if ((rc = vec_dots(h, h->w.g, 1, nk, h->w.g, h->w.step_sq + 2 * s + 1))) return rc;
     if ((rc = mark(s, 5))) return rc;
-    if ((rc = launch_react_be(p, k, V_dev, w_dev, n, h->w.err, h->stream))) return rc;
+    if ((rc = launch_react_be(p, k, V_dev, w_dev, n, h->w.err, h->stream, nullptr, nullptr, s + 1 < nsteps)))
+      return rc;
     if ((rc = mark(s, 6))) return rc;
     st.ms = elapsed_ms(t0);
   }

@@ -156,6 +156,25 @@ def test_coupled_strang_steps(name, steps):
     assert rel(ued.cpu().numpy(), ue_o) < TOL64
 
 
+@pytest.mark.parametrize("prec", [K.FP64, K.MIXED])
+def test_coupled_fused_reaction_pass_same_as_separate_calls(prec):
+    """The coupled step runs the next step's forward half step in the
+    backward pass as well: three steps in one call equal three one-step
+    calls bit for bit."""
+    geom, grid = CASES["ellipse128"]()
+    V0 = C.ball_stimulus(grid, (-0.4, 0.0), 0.1)
+    w0 = np.zeros_like(V0)
+    out = []
+    for calls in ((3,), (1, 1, 1)):
+        h = K.KFBI(geom, grid, D_i=DI[:2], D_e=DE[:2], dt=0.05, tol=1e-10, precision=prec)
+        Vd, wd = cuda(V0), cuda(w0)
+        for n in calls:
+            h.bidomain_step(C.FHN_CONFIG, Vd, wd, None, nsteps=n)
+        h.close()
+        out.append((Vd.cpu().numpy(), wd.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
 def test_isotropic_coupled_matches_decoupled_gpu():
     geom, grid, cfg, V0, w0 = C.config0()
     hs = K.KFBI(geom, grid, sigma_i=1.0, sigma_e=2.0, dt=0.05, tol=1e-12)

@@ -276,6 +276,24 @@ def test_strang_config0_mixed():
     assert rel(wd.cpu().numpy(), w) < 1e-8
 
 
+@pytest.mark.parametrize("prec,warm", [(K.FP64, K.WARM_PREVIOUS), (K.MIXED, K.WARM_PROJECTION)])
+def test_fused_reaction_pass_same_as_separate_calls(prec, warm):
+    """Within one call the forward half step of every step after the first
+    runs in the previous step's backward pass (and, for the float32 forms,
+    the midpoint too): the same float64 operations as the separate passes, so
+    three steps in one call equal three one-step calls bit for bit."""
+    geom, grid, cfg, V0, w0 = C.config0()
+    out = []
+    for calls in ((3,), (1, 1, 1)):
+        h = K.KFBI(geom, grid, sigma_i=1.0, sigma_e=2.0, dt=0.05, tol=1e-10, precision=prec, warm=warm)
+        Vd, wd = cuda(V0), cuda(w0)
+        for n in calls:
+            h.bidomain_step(C.FHN_CONFIG, Vd, wd, None, nsteps=n)
+        h.close()
+        out.append((Vd.cpu().numpy(), wd.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
 def test_reaction_half_steps():
     rng = np.random.default_rng(11)
     V0 = rng.uniform(-0.3, 1.2, 100_003)
