@@ -890,7 +890,7 @@ __global__ void k_react_be(BeConsts K, double* __restrict__ V, double* __restric
     }
     double v = 0.0;
     VW res{0.0, 0.0};
-    bool done = false;
+    bool done = false, from_f32 = false;
     if (pairs) {
       const float v0f = v0p.h, q0f = q0p.h;
       float vf = v0f;
@@ -924,13 +924,15 @@ __global__ void k_react_be(BeConsts K, double* __restrict__ V, double* __restric
         const ff W = mul(add(q0p, mul(K.kaP, ff{vf, -dv.h})), K.idP);
         res.w = widen(W.h) + widen(W.l);
         done = true;
-      } else {
+      } else if (isfinite(vf)) {
         v = widen(vf);
+        from_f32 = true;
       }
     }
     // float64 Newton steps (rare: near folds of the cubic, unconverged
-    // float32 phases, inputs outside the pairs' range)
-    if (!done) res = be_newton64<MID>(K, a, b, Vi, q0, pairs, v, err);
+    // float32 phases, inputs outside the pairs' range), from v_f when the
+    // float32 phase left a finite value, else from v0
+    if (!done) res = be_newton64<MID>(K, a, b, Vi, q0, from_f32, v, err);
     if constexpr (FE) {
       const double t = fma(fma(-K.fa, res.v, K.fp1), res.v, K.fp0);
       const double v2 = fma(t, res.v, fma(-K.fa, res.w, res.v));
