@@ -644,8 +644,8 @@ int gmres_ir(kfbi_handle* h, double lambda, const double* g, double* psi, kfbi_s
     // inner tolerance relative to ||r||: as far as the float32 operator can
     // go (six digits), or what the target needs with a factor of 1.25 to
     // spare (the inner solve overshoots its target, and the float32
-    // operator adds ~1e-5 ||r|| to the next outer residual).  Measured on
-    // config 2 (steps 6-25): factors 0.1 / 0.25 / 0.5 / 0.8 / 1.0 gave 11.8 /
+    // operator adds ~1e-5 ||r|| to the next outer residual).  Measured on the
+    // 256^3 prolate shell (steps 6-25): factors 0.1 / 0.25 / 0.5 / 0.8 / 1.0 gave 11.8 /
     // 10.6 / 9.8 / 9.25 / 9.2 inner iterations and 1.25 / 1.25 / 1.25 / 1.3
     // / 1.35 outer rounds per step, 0.8 the shortest step.
     double tin = std::max(1e-6, 0.8 * tol * gnorm / rn);
